@@ -1,0 +1,262 @@
+"""FP64 oracle of the reduced-order step (Algorithms 2, 3, 5, 6, 7).  Test infrastructure only.
+
+Algorithm 2: (1) full-space kinematics at quadrature points (Algorithm 3,
+Lagrangian quadrature), (2) full-space dynamics of the sample material points
+(Algorithm 5), (3) reduced-space dynamics by projection (Algorithm 6,
+position-velocity, or Algorithm 7, velocity-only).
+
+Algorithm 3: x_n^p = g(X^p; xhat_n) for the samples; the basis set I is every
+node whose basis function is non-zero at a sample; the neighbour set N holds
+every other material point with a non-zero basis function in I; at P u N the
+deformation gradient is dg/dX and the velocity (dg/dxhat) vhat_n; quadrature
+masses are the particle masses.
+
+Algorithm 5: particle-to-grid from the quadrature points onto I (no affine
+velocity term), the grid update of Algorithm 1 on I, grid-to-particle to the
+samples only: v_trial, x_trial = x_n + dt v_trial.  F is not evolved (it comes
+from the decoder, Remark in Section 3.2.3).
+
+Algorithm 6: vhat_{n+1} = argmin sum_P |(dg/dxhat)(X^p; xhat_n) vhat - v_trial|^2;
+xhat_{n+1} = argmin sum_P |g(X^p; xhat) - x_trial|^2 by Gauss-Newton with
+backtracking, initial guess 2 xhat_n - xhat_{n-1} (Section 5).
+Algorithm 7: vhat_{n+1} as above, xhat_{n+1} = xhat_n + dt vhat_{n+1}.
+
+Readings where the paper is silent (listed in the design notes):
+  * sampling: uniform without replacement, re-drawn every step (Section 3.2.1),
+    as the k particles with the smallest 64-bit hash h(seed, instance, step, p),
+    ties broken by p; h chains three SplitMix64 outputs (Steele, Lea and Flood
+    2014): h = out(out(out(seed, instance), step), p) where out(s, k) is the
+    (k+1)-th output of the SplitMix64 generator seeded with s;
+  * stencil membership (integer) decides "N_i != 0" (equal except on the
+    zero-weight support boundary);
+  * Gauss-Newton: a fixed number of iterations (3); the step solves the
+    linearised least-squares problem; Armijo backtracking with c = 1e-4 and
+    step halving, at most 10 halvings; if no trial decreases the objective the
+    iterate is kept and the ``no_decrease`` flag is raised;
+  * at the first step xhat_{-1} = xhat_0 - dt vhat_0;
+  * initial latent state by the least-squares fit of Eq. essentialSpecInt over
+    all particles (Gauss-Newton from zero, then a linear least-squares fit of
+    the initial velocity).
+
+Pins (tests/test_oracle_rom.py): SplitMix64 known answers, bottom-k against a
+full sort, sampling uniformity, neighbour sets against brute-force
+enumeration, exact reproduction of the full-order free fall with a hand-set
+linear decoder g = X + xhat, Gauss-Newton against a QR least-squares solve for
+a linear decoder, O(dt^2) agreement of the two projections (Appendix A), the
+error metric on a hand-computed toy.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import decoder as D
+from . import mpm as M
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64_out(state, k):
+    """(k+1)-th output of SplitMix64 seeded with ``state`` (uint64 arrays, wrapping)."""
+    with np.errstate(over="ignore"):
+        z = np.asarray(state, np.uint64) + GOLDEN * (np.asarray(k, np.uint64) + np.uint64(1))
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def sample_hash(seed, inst, step, p):
+    s = splitmix64_out(np.uint64(seed), np.uint64(inst))
+    s = splitmix64_out(s, np.uint64(step))
+    return splitmix64_out(s, np.asarray(p, np.uint64))
+
+
+def sample_set(seed, inst, step, n_particles, k):
+    """Indices of the k particles with the smallest hash (ties by index), ascending."""
+    h = sample_hash(seed, inst, step, np.arange(n_particles, dtype=np.uint64))
+    order = np.lexsort((np.arange(n_particles), h))
+    return np.sort(order[:k])
+
+
+def stencil_nodes(x, dx, n_grid):
+    """Linear node ids (n, 3^d) of the quadratic stencils at positions x."""
+    d = x.shape[1]
+    base = M.stencil_base(x, dx)
+    out = []
+    for off in M.stencil_offsets(d):
+        node = base + np.array(off)
+        lin = np.zeros(len(x), np.int64)
+        for k in range(d):
+            lin = lin * n_grid + node[:, k]
+        out.append(lin)
+    return np.stack(out, axis=1)
+
+
+def neighbourhood(x_all, samples, dx, n_grid):
+    """Algorithm 3 sets: basis set I (sorted node ids) and neighbour set N (sorted particle ids)."""
+    nodes = stencil_nodes(x_all, dx, n_grid)
+    basis = np.unique(nodes[samples])
+    hit = np.isin(nodes, basis).any(axis=1)
+    hit[samples] = False
+    return basis, np.nonzero(hit)[0]
+
+
+@dataclasses.dataclass
+class RomScene:
+    """Static data of one reduced-order instance."""
+    X: np.ndarray            # (P, d) reference positions
+    mass: float
+    vol: float
+    E: float
+    nu: float
+    dx: float
+    dt: float
+    n_grid: int
+    gravity: np.ndarray
+    bc: int
+    bc_width: int
+    material: int
+    transfer: int
+    n_samples: int
+    seed: int
+    inst: int = 0
+    gn_iters: int = 3
+    armijo_c: float = 1e-4
+    max_halvings: int = 10
+    projection: str = "position-velocity"   # or "velocity-only"
+
+
+@dataclasses.dataclass
+class RomState:
+    xhat: np.ndarray
+    vhat: np.ndarray
+    xhat_prev: np.ndarray
+    step: int = 0
+    no_decrease: bool = False
+
+
+def local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_all):
+    """Algorithms 3 and 5: trial velocities and positions of the samples.
+
+    Returns (v_trial, x_trial, basis, neighbours).
+    """
+    basis, neigh = neighbourhood(x_all, samples, rs.dx, rs.n_grid)
+    quad = np.concatenate([samples, neigh])
+    _, FX, _ = D.jacobians(dec, rs.X[quad], xhat)
+    _, vq = D.jvp_latent(dec, rs.X[quad], xhat, vhat)
+    xq = x_all[quad]
+    d = xq.shape[1]
+    mu, lam = M.lame(rs.E, rs.nu)
+    m, p = M.p2g(xq, vq, FX, np.zeros((len(quad), d, d)), rs.mass, rs.vol, mu, lam, dx=rs.dx,
+                 dt=rs.dt, n_grid=rs.n_grid, material=rs.material, transfer=rs.transfer)
+    vg = M.grid_update(m, p, dt=rs.dt, gravity=rs.gravity, bc=rs.bc, bc_width=rs.bc_width)
+    xs = x_all[samples]
+    base = M.stencil_base(xs, rs.dx)
+    w, _ = M.bspline(xs / rs.dx - base)
+    v_trial = np.zeros((len(samples), d))
+    for off in M.stencil_offsets(d):
+        node = base + np.array(off)
+        weight = np.ones(len(samples))
+        for k in range(d):
+            weight = weight * w[:, k, off[k]]
+        v_trial += weight[:, None] * vg[tuple(node[:, k] for k in range(d))]
+    x_trial = xs + rs.dt * v_trial
+    return v_trial, x_trial, basis, neigh
+
+
+def lstsq(A, b):
+    return np.linalg.lstsq(A, b, rcond=None)[0]
+
+
+def project_velocity(dec, Xs, xhat_n, v_trial):
+    """Eq. nonlinear_projection:vel / linear_projection: LSQ fit of v_trial by dg/dxhat at xhat_n."""
+    _, _, Jq = D.jacobians(dec, Xs, xhat_n)
+    return lstsq(Jq.reshape(-1, dec.r), v_trial.reshape(-1))
+
+
+def gauss_newton(dec, Xs, x_trial, xhat0, iters, c=1e-4, max_halvings=10):
+    """Eq. nonlinear_projection:pos by Gauss-Newton with backtracking; returns (xhat, no_decrease)."""
+    xh = np.array(xhat0, np.float64)
+    flag = False
+    target = x_trial.reshape(-1)
+    for _ in range(iters):
+        g, _, Jq = D.jacobians(dec, Xs, xh)
+        res = g.reshape(-1) - target
+        J = Jq.reshape(-1, dec.r)
+        delta = lstsq(J, -res)
+        f0 = res @ res
+        slope = 2.0 * res @ (J @ delta)
+        alpha = 1.0
+        accepted = False
+        for _h in range(max_halvings + 1):
+            r1 = D.decode(dec, Xs, xh + alpha * delta).reshape(-1) - target
+            if r1 @ r1 <= f0 + c * alpha * slope:
+                accepted = True
+                break
+            alpha *= 0.5
+        if accepted:
+            xh = xh + alpha * delta
+        elif np.linalg.norm(delta) > 1e-10 * (1.0 + np.linalg.norm(xh)):
+            flag = True
+    return xh, flag
+
+
+def rom_step(dec, rs: RomScene, st: RomState, record=None):
+    """Algorithm 2 with Lagrangian quadrature; returns the new RomState."""
+    P = len(rs.X)
+    samples = sample_set(rs.seed, rs.inst, st.step, P, rs.n_samples)
+    x_all = D.decode(dec, rs.X, st.xhat)
+    v_trial, x_trial, basis, neigh = local_dynamics(dec, rs, st.xhat, st.vhat, samples, x_all)
+    Xs = rs.X[samples]
+    vhat_new = project_velocity(dec, Xs, st.xhat, v_trial)
+    if rs.projection == "velocity-only":
+        xhat_new, flag = st.xhat + rs.dt * vhat_new, False
+    else:
+        guess = 2.0 * st.xhat - st.xhat_prev
+        xhat_new, flag = gauss_newton(dec, Xs, x_trial, guess, rs.gn_iters, rs.armijo_c, rs.max_halvings)
+    if record is not None:
+        record.update(samples=samples, basis=basis, neigh=neigh, x_all=x_all, v_trial=v_trial,
+                      x_trial=x_trial)
+    return RomState(xhat=xhat_new, vhat=vhat_new, xhat_prev=st.xhat.copy(), step=st.step + 1,
+                    no_decrease=st.no_decrease or flag)
+
+
+def rom_init(dec, X, V0, dt, xhat_guess=None, iters=30):
+    """Eq. essentialSpecInt: least-squares fit of xhat_0 (to X) and vhat_0 (to V0) over all particles."""
+    xh = np.zeros(dec.r) if xhat_guess is None else np.array(xhat_guess, np.float64)
+    for _ in range(iters):
+        g, _, Jq = D.jacobians(dec, X, xh)
+        res = (g - X).reshape(-1)
+        J = Jq.reshape(-1, dec.r)
+        delta = lstsq(J, -res)
+        f0 = res @ res
+        alpha = 1.0
+        for _h in range(20):
+            r1 = (D.decode(dec, X, xh + alpha * delta) - X).reshape(-1)
+            if r1 @ r1 <= f0 + 1e-4 * alpha * 2.0 * res @ (J @ delta):
+                break
+            alpha *= 0.5
+        xh = xh + alpha * delta
+        if np.linalg.norm(alpha * delta) < 1e-13 * (1 + np.linalg.norm(xh)):
+            break
+    _, _, Jq = D.jacobians(dec, X, xh)
+    vh = lstsq(Jq.reshape(-1, dec.r), np.broadcast_to(V0, X.shape).reshape(-1))
+    return RomState(xhat=xh, vhat=vh, xhat_prev=xh - dt * vh, step=0)
+
+
+class PositionError:
+    """Accumulated position error of Section 5 (in percent)."""
+
+    def __init__(self):
+        self.num = 0.0
+        self.den = 0.0
+
+    def add(self, x_rom, x_fom):
+        self.num += float(np.sum((np.asarray(x_rom) - np.asarray(x_fom)) ** 2))
+        self.den += float(np.sum(np.asarray(x_fom) ** 2))
+
+    def percent(self):
+        return 100.0 * np.sqrt(self.num) / np.sqrt(self.den)

@@ -1,0 +1,128 @@
+"""Pins of the FP64 reduced-order oracle (Algorithms 2, 3, 5, 6, 7)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle.decoder as D
+import oracle.mpm as M
+import oracle.rom as R
+import synth.scenes as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_splitmix64_known_answers():
+    vals = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if l.startswith("0x")]
+    got = [int(R.splitmix64_out(np.uint64(0), np.uint64(k))) for k in range(3)]
+    assert got == vals
+
+
+def test_bottom_k_against_full_sort_and_uniformity():
+    P, k = 500, 37
+    h = R.sample_hash(5, 2, 9, np.arange(P, dtype=np.uint64))
+    ref = sorted(range(P), key=lambda p: (int(h[p]), p))[:k]
+    assert list(R.sample_set(5, 2, 9, P, k)) == sorted(ref)
+    # every particle is drawn with probability k / P
+    counts = np.zeros(P)
+    steps = 400
+    for s in range(steps):
+        counts[R.sample_set(1, 0, s, P, k)] += 1
+    expect = steps * k / P
+    chi2 = np.sum((counts - expect) ** 2 / expect)
+    assert chi2 < P + 5 * np.sqrt(2 * P)          # chi-square with P-1 dof, ~5 sigma bound
+    assert len(np.unique(R.sample_set(1, 0, 0, P, k))) == k
+
+
+def test_neighbourhood_brute_force():
+    rng = np.random.default_rng(3)
+    for d in (2, 3):
+        n, dx = 16, 1.0 / 16
+        x = 0.3 + 0.4 * rng.uniform(size=(64, d))
+        samples = np.array(sorted(rng.choice(64, 6, replace=False)))
+        basis, neigh = R.neighbourhood(x, samples, dx, n)
+        # brute force: explicit node tuples
+        def stencil(p):
+            b = [int(np.floor(x[p, k] / dx - 0.5)) for k in range(d)]
+            out = set()
+            for off in np.ndindex(*(3,) * d):
+                out.add(tuple(b[k] + off[k] for k in range(d)))
+            return out
+        I = set()
+        for p in samples:
+            I |= stencil(p)
+        lin = sorted(sum(t[k] * n ** (d - 1 - k) for k in range(d)) for t in I)
+        assert list(basis) == lin
+        Nset = [q for q in range(64) if q not in set(samples) and stencil(q) & I]
+        assert list(neigh) == Nset
+
+
+def _translation_decoder(d, X_min, X_range):
+    """g(X; xhat) = X + xhat as a one-layer linear network (r = d)."""
+    dec = S.xavier_decoder(0, d, d, 8, 0, D.IDENTITY, X_min=X_min, X_range=X_range)
+    dec.W[0] = np.concatenate([np.diag(X_range), np.eye(d)], axis=1)
+    dec.b[0] = np.array(X_min, np.float64)
+    return dec
+
+
+def test_rom_reproduces_free_fall_exactly():
+    sc = S.block_2d(side=16, dt=5e-5, v0=np.array([0.2, 0.3]))
+    X = sc.x.copy()
+    dec = _translation_decoder(2, X.min(0), X.max(0) - X.min(0))
+    rs = R.RomScene(X=X, mass=sc.p_mass, vol=sc.p_vol, E=1e4, nu=0.3, dx=sc.dx, dt=sc.dt, n_grid=sc.n_grid,
+                    gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width, material=sc.material,
+                    transfer=sc.transfer, n_samples=12, seed=4)
+    st = R.rom_init(dec, X, sc.v[0], sc.dt)
+    np.testing.assert_allclose(st.xhat, 0.0, atol=1e-14)
+    np.testing.assert_allclose(st.vhat, sc.v[0], atol=1e-14)
+    fom = sc.copy()
+    for n in range(1, 11):
+        st = R.rom_step(dec, rs, st)
+        M.step(fom, 1)
+        np.testing.assert_allclose(D.decode(dec, X, st.xhat), fom.x, atol=1e-13)
+    assert not st.no_decrease
+    g = sc.gravity[:2]
+    np.testing.assert_allclose(st.vhat, sc.v[0] + 10 * sc.dt * g, atol=1e-12)
+
+
+def test_gauss_newton_equals_qr_least_squares_for_linear_decoder():
+    rng = np.random.default_rng(6)
+    d, r = 3, 2          # a linear decoder's latent Jacobian is shared by all points: rank <= d
+    dec = S.xavier_decoder(9, d, r, 8, 0, D.IDENTITY, bias_scale=0.5)
+    Xs = rng.uniform(size=(11, d))
+    target = rng.uniform(size=(11, d))
+    xh, flag = R.gauss_newton(dec, Xs, target, rng.normal(size=r), iters=1)
+    assert not flag
+    # closed form via QR of the affine map xhat -> g
+    _, _, J = D.jacobians(dec, Xs, np.zeros(r))
+    A = J.reshape(-1, r)
+    b = (target - D.decode(dec, Xs, np.zeros(r))).reshape(-1)
+    Q, Rm = np.linalg.qr(A)
+    sol = np.linalg.solve(Rm, Q.T @ b)
+    np.testing.assert_allclose(xh, sol, rtol=1e-12, atol=1e-12)
+
+
+def test_velocity_only_matches_position_velocity_to_second_order():
+    rng = np.random.default_rng(1)
+    d, r = 2, 3
+    dec = S.xavier_decoder(2, d, r, 16, 3, D.ELU, bias_scale=0.3)
+    Xs = rng.uniform(size=(20, d))
+    xh = 0.3 * rng.normal(size=r)
+    v_trial = rng.normal(size=(20, d))
+    diffs = []
+    for dt in (2e-3, 1e-3, 5e-4):
+        x_trial = D.decode(dec, Xs, xh) + dt * v_trial
+        vh = R.project_velocity(dec, Xs, xh, v_trial)
+        x_vo = xh + dt * vh
+        x_pv, _ = R.gauss_newton(dec, Xs, x_trial, xh, iters=6)
+        diffs.append(np.linalg.norm(x_pv - x_vo))
+    assert diffs[0] / diffs[1] == pytest.approx(4.0, rel=0.1)
+    assert diffs[1] / diffs[2] == pytest.approx(4.0, rel=0.1)
+
+
+def test_position_error_toy():
+    err = R.PositionError()
+    err.add(np.array([[1.0, 0.0], [0.0, 2.0], [1.0, 1.0]]), np.array([[1.0, 0.0], [0.0, 2.0], [1.0, 0.0]]))
+    err.add(np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 0.0]]), np.array([[0.0, 1.0], [3.0, 0.0], [0.0, 0.0]]))
+    # numerator: 1 + 1 = 2; denominator: 1 + 4 + 1 + 1 + 9 = 16 -> 100 * sqrt(2) / 4
+    assert err.percent() == pytest.approx(100 * np.sqrt(2) / 4, rel=1e-15)
