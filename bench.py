@@ -1,0 +1,290 @@
+"""Benchmark of the hot path: MPM particle-steps/s on the 3D fixed-corotated cube.
+
+Workload (N = 1): 262,144 particles (64^3 jittered lattice at dx/2), 128^3
+grid, fixed-corotated material with FP64-refined polar factor, slip floor,
+dt = 5e-5, MLS-MPM.  A step is one explicit MPM step of every instance
+(binning, particle-to-grid, grid update, grid-to-particle).  Inputs are
+resident in HBM when the timed region starts; L2 is flushed (a 256 MiB write)
+before every timed step, outside its CUDA-event interval.
+
+With torchrun (N > 1) every rank runs an independent replica of the workload
+(the single-scene step does not shard; batched instances would shard by
+instance with no exchange): weak scaling, max time over ranks.
+
+``--impl reference`` times the FP64 CPU oracle (the deliberately slow,
+obviously correct restatement of the paper's algorithm) on the host cores
+instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth.scenes as S  # noqa: E402
+
+METRIC = "MPM particle-steps/s"
+UNIT = "particle-steps/s"
+WORKLOAD = "3D fixed-corotated cube, 262144 particles, 128^3 grid, MLS-MPM, FP64-refined polar, dt=5e-5, slip floor"
+# algorithmic bytes per particle-step (3D): particle state read + written once,
+# x, v (3 each), F, C (9 each) in FP32 = 2 x 96 B; active grid nodes ~1/8 per
+# particle x 56 B (clear + scatter 16, update 28, gather 12) = 7 B
+ALGO_BYTES_3D = 2 * 96 + 7
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline_fom(sc, max_seconds=20.0):
+    """FP64 oracle, as it stands, on the full 262,144-particle state: whole steps until ~max_seconds."""
+    import oracle.mpm as OM
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter = threadpool_limits(1)
+    except Exception:  # pragma: no cover
+        limiter = None
+    ref = sc.copy()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        OM.step(ref, 1)
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds or steps >= 3:
+            break
+    dt = time.perf_counter() - t0
+    if limiter is not None:
+        limiter.unregister() if hasattr(limiter, "unregister") else None
+    return {"value": sc.n_particles * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full step(s) of the {sc.n_particles}-particle cube in FP64 numpy, single thread"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    sc = S.cube_3d()
+    for _ in range(args.warmup if args.warmup < 1 else 0):
+        pass
+    times = []
+    import oracle.mpm as OM
+    ref = sc.copy()
+    # each timed step: one oracle step of a 1/8 sub-block of the workload (bounded CPU time)
+    sub = sc.copy()
+    side_mask = (sc.x[:, 0] < 0.5) & (sc.x[:, 2] < 0.5) & (sc.x[:, 1] < 0.05 + 0.125)
+    sub.x, sub.v, sub.F, sub.C = sc.x[side_mask], sc.v[side_mask], sc.F[side_mask], sc.C[side_mask]
+    sub.inst_offsets = np.array([0, int(side_mask.sum())])
+    for _ in range(max(0, min(args.warmup, 1))):
+        OM.step(sub.copy(), 1)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        OM.step(sub, 1)
+        times.append(time.perf_counter() - t0)
+    per = float(np.mean(times))
+    value = sub.n_particles / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{sub.n_particles}-particle corner sub-block per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one FP64 oracle step of a {sub.n_particles}-particle sub-block of the cube"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2109_12390_gb300.mpm import MPM
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sc = S.cube_3d()
+    P = sc.n_particles
+    ctx = MPM.from_scene(sc)
+    stream = torch.cuda.current_stream()
+    ctx.load_numpy(sc.x, sc.v, sc.F, sc.C)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.step_profiled(1)
+    assert ctx.status() == 0, "unstable state during warm-up"
+    kern = []
+    step_ms = []
+    barrier()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            k = ctx.step_profiled(1)
+            s1.record(stream)
+            s1.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+            kern.append(k[0])
+    barrier()
+    status = ctx.status()
+    total_ms = float(np.sum(step_ms))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    kern = np.array(kern)
+    fused_ms = float(kern[:, 0].mean())
+    peak, peak_kind = _peaks()
+    achieved = ALGO_BYTES_3D * P / (fused_ms * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host state in, one step, state out
+    d = sc.dim
+    hx = torch.from_numpy(sc.x.astype(np.float32)).pin_memory()
+    hv = torch.from_numpy(sc.v.astype(np.float32)).pin_memory()
+    hF = torch.from_numpy(sc.F.astype(np.float32).reshape(P, d * d)).pin_memory()
+    hC = torch.from_numpy(sc.C.astype(np.float32).reshape(P, d * d)).pin_memory()
+    ox, ov, oF, oC = [torch.empty_like(t).pin_memory() for t in (hx, hv, hF, hC)]
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_state(hx, hv, hF, hC)
+        ctx.step(1)
+        ctx.get_state(ox, ov, oF, oC)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = float(np.sum(e2e_ms))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    bytes_io = 4 * P * (2 * d + 2 * d * d)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ws * P * args.steps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles": P, "grid": "128^3", "l2": "flushed before every timed step",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "mpm_g2p2g",
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "algorithmic_bytes_per_launch": ALGO_BYTES_3D * P, "kernel_ms": fused_ms},
+            "kernels_ms": {"mpm_g2p2g": fused_ms, "mpm_scan": float(kern[:, 1].mean()),
+                           "mpm_permute": float(kern[:, 2].mean())},
+            "e2e": {"value": ws * P * args.steps / (e2e_total * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk.summary(),
+            "status_word": status,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_fom(sc)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,269 @@
+/*
+ * mpmrom: C ABI of a GB300 (sm_103a) implementation of the data-parallel hot
+ * path of "Model reduction for the material point method via an implicit
+ * neural representation of the deformation map" (Chen, Chiaramonte,
+ * Grinspun, Carlberg).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns an mpm_status; MPM_OK is 0.  On failure a message is
+ *   available from mpm_last_error() (thread-local, valid until the next call
+ *   on the same thread).  No C++ exception crosses this boundary.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are asynchronous on that stream unless stated otherwise.
+ * - Pointers marked "host or device" are copied with cudaMemcpyAsync(...,
+ *   cudaMemcpyDefault): they may be device memory or (pinned or pageable)
+ *   host memory.  The caller keeps ownership and must keep them alive until
+ *   the stream reaches the copy.
+ * - Contexts own every work buffer they need; they allocate only in *_init
+ *   and free in *_destroy.  Step calls allocate nothing.
+ * - Failures detected on the device (non-finite values, inverted elements,
+ *   particles leaving the grid, solver breakdown) are OR-ed into a device
+ *   status word; read it with the *_status call of the object.
+ * - All floating-point arrays are float32, row-major, C order.
+ */
+#ifndef MPMROM_H
+#define MPMROM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mpm_status;
+enum {
+  MPM_OK = 0,
+  MPM_EINVAL = 1,      /* invalid argument or configuration */
+  MPM_ENOMEM = 2,      /* device allocation failed */
+  MPM_ECUDA = 3,       /* CUDA runtime error (message has the details) */
+  MPM_EUNSTABLE = 4,   /* simulation produced non-finite or inverted state */
+  MPM_ENOCONV = 5,     /* Gauss-Newton made no progress */
+  MPM_ETIMEOUT = 6,    /* a bounded device wait ran out */
+  MPM_ENOTIMPL = 7     /* option not available in this build */
+};
+
+/* Device status bits reported by mpm_status_word / rom_status_word. */
+enum {
+  MPM_STATUS_NONFINITE = 1 << 0,
+  MPM_STATUS_INVERTED = 1 << 1,
+  MPM_STATUS_OUT_OF_GRID = 1 << 2,
+  MPM_STATUS_GN_NO_DECREASE = 1 << 3,
+  MPM_STATUS_CHOLESKY = 1 << 4,
+  MPM_STATUS_TIMEOUT = 1 << 5,
+  MPM_STATUS_CAPACITY = 1 << 6
+};
+
+enum { MPM_TRANSFER_MLS = 0, MPM_TRANSFER_PIC = 1 };
+enum { MPM_NEO_HOOKEAN = 0, MPM_FIXED_COROTATED = 1 };
+enum { MPM_BC_STICKY = 0, MPM_BC_SLIP_FLOOR = 1 };
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* mpm_last_error(void);
+
+/* ======================================================================
+ * Full-order model: explicit MPM step (Algorithm 1, Section 2.2)
+ * ====================================================================== */
+
+/*
+ * Configuration of a batch of independent MPM instances that share the grid
+ * geometry, the time step and the material law, each on its own grid.
+ *   dim           2 or 3.
+ *   n_grid        grid nodes per axis; node i sits at i*dx (i = 0..n_grid-1).
+ *                 Must be a multiple of 8 (2D) or 4 (3D).
+ *   dx, dt        grid spacing and time step.
+ *   gravity[3]    body acceleration g (the external force of Algorithm 1 is
+ *                 f^e_i = m_i g); only the first dim entries are used.
+ *   bc            MPM_BC_STICKY: nodes with any index < bc_width or
+ *                 > n_grid-1-bc_width get zero velocity.  MPM_BC_SLIP_FLOOR:
+ *                 the low-y band clamps v_y >= 0; the other walls are sticky.
+ *   material      MPM_NEO_HOOKEAN or MPM_FIXED_COROTATED (Stomakhin et al.
+ *                 2012, the material of Section 5); Lame parameters from
+ *                 (E, nu) per instance.
+ *   transfer      MPM_TRANSFER_MLS (MLS-MPM with APIC affine velocity, the
+ *                 default) or MPM_TRANSFER_PIC (the literal transfers of
+ *                 Algorithm 1 with exact basis gradients).
+ *   rho, p_vol    density and particle reference volume V0; the particle
+ *                 mass is rho * p_vol.
+ *   n_inst        number of instances (>= 1).
+ *   E, nu         host arrays of n_inst Young's moduli and Poisson ratios.
+ *   inst_offsets  host array of n_inst+1 int64: particles of instance k are
+ *                 rows inst_offsets[k] .. inst_offsets[k+1]-1 of the state
+ *                 arrays.
+ */
+typedef struct mpm_config {
+  int32_t dim;
+  int32_t n_grid;
+  float dx;
+  float dt;
+  float gravity[3];
+  int32_t bc;
+  int32_t bc_width;
+  int32_t material;
+  int32_t transfer;
+  float rho;
+  float p_vol;
+  int32_t n_inst;
+  const float* E;
+  const float* nu;
+  const int64_t* inst_offsets;
+} mpm_config;
+
+typedef struct mpm_ctx mpm_ctx;
+
+/*
+ * Creates a context (allocates all device buffers: two particle-state
+ * buffers, two grids per instance, binning tables).  The configuration is
+ * copied; the host arrays in it may be freed after the call.  Synchronous.
+ * Errors: MPM_EINVAL (bad sizes or parameters), MPM_ENOMEM, MPM_ECUDA.
+ */
+mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out);
+
+/* Frees the context and everything it owns.  NULL is allowed. */
+void mpm_destroy(mpm_ctx* ctx);
+
+/*
+ * Loads the particle state {x, v, F, C} (Algorithm 1, Data) in the caller's
+ * particle order: x and v are (P, dim), F and C are (P, dim, dim) with
+ * F[p][i][j] = F_ij.  C is the APIC affine velocity (ignored and zeroed in PIC
+ * mode; may be NULL, meaning zero).  Host or device pointers.  The context
+ * then bins the particles by grid block and performs the particle-to-grid
+ * transfer of the loaded state, so that the next mpm_step starts from it.
+ */
+mpm_status mpm_set_state(mpm_ctx* ctx, const float* x, const float* v, const float* F,
+                         const float* C, void* stream);
+
+/*
+ * Copies the current particle state back in the caller's original particle
+ * order (same layouts as mpm_set_state).  Any pointer may be NULL to skip
+ * that quantity.  Host or device pointers.
+ */
+mpm_status mpm_get_state(mpm_ctx* ctx, float* x, float* v, float* F, float* C, void* stream);
+
+/*
+ * Advances every instance by n_steps symplectic-Euler steps of Algorithm 1:
+ * particle-to-grid, grid update with gravity and walls, grid-to-particle with
+ * the velocity / affine / deformation-gradient update, advection.  Each step
+ * is one fused kernel that finishes step n (grid update + grid-to-particle)
+ * and starts step n+1 (particle-to-grid of the new state into the other
+ * grid), followed by the re-binning of the particles.
+ */
+mpm_status mpm_step(mpm_ctx* ctx, int n_steps, void* stream);
+
+/*
+ * mpm_step with CUDA events recorded around each kernel of every step on
+ * `stream`; synchronises after each step and writes the device durations in
+ * milliseconds of [fused step kernel, scan, re-binning] for step k to
+ * kernel_ms[3k .. 3k+2] (host array of 3 * n_steps floats).  For measurement.
+ */
+mpm_status mpm_step_profiled(mpm_ctx* ctx, int n_steps, float* kernel_ms, void* stream);
+
+/*
+ * Synchronises `stream`, then returns the OR of MPM_STATUS_* bits raised by
+ * the device since the last clear in *out (clears it when `clear` != 0).
+ */
+mpm_status mpm_status_word(mpm_ctx* ctx, uint32_t* out, int clear, void* stream);
+
+/*
+ * Diagnostics of the binning step (the cell sort).  For the current state,
+ * in the caller's particle order: cell_keys[p] = linear index of the lowest
+ * stencil node floor(x/dx - 0.5) (first axis slowest) and block_keys[p] =
+ * instance * n_blocks + grid block of that node.  block_offsets (n_keys+1
+ * entries, may be NULL) gets the start of every block's run in the binned
+ * order.  Device or host pointers.  Synchronous.
+ */
+mpm_status mpm_debug_bins(mpm_ctx* ctx, int32_t* cell_keys, int32_t* block_keys,
+                          int32_t* block_offsets, void* stream);
+
+/* Number of block keys (instances x blocks per grid); for sizing block_offsets. */
+int64_t mpm_num_block_keys(const mpm_ctx* ctx);
+
+/*
+ * Diagnostics of the grid: for the current state, the particle-to-grid
+ * result of Algorithm 1 step 1 and the grid update of step 2, dense per
+ * instance: mass (n_inst, n_grid^dim), momentum (n_inst, n_grid^dim, dim)
+ * = m_i v_i + dt f_i, velocity (n_inst, n_grid^dim, dim) after gravity and
+ * walls.  Any pointer may be NULL.  Synchronous.
+ */
+mpm_status mpm_debug_grid(mpm_ctx* ctx, float* mass, float* momentum, float* velocity,
+                          void* stream);
+
+/* ======================================================================
+ * Implicit neural decoder g(X; xhat) and its Jacobians
+ * (Section 3.1, Eqs. kinematicRestriction, defGrad, timederOne; Section 4,
+ * Table 1; input/output scaling of Appendix B)
+ * ====================================================================== */
+
+/*
+ *   d           spatial dimension (2 or 3).
+ *   r           latent dimension (d + r <= 40).
+ *   width       hidden width; must be 128 when n_hidden >= 1.
+ *   n_hidden    number of hidden (activated) layers, 0..5.  0 is the linear
+ *               manifold of Section 5 (one linear map, no activation).
+ *   activation  0 = ELU (the paper's choice), 1 = identity.
+ * Layers: [d + r] -> width (n_hidden times, activated) -> d (linear).
+ */
+typedef struct decoder_desc {
+  int32_t d;
+  int32_t r;
+  int32_t width;
+  int32_t n_hidden;
+  int32_t activation;
+} decoder_desc;
+
+typedef struct mpm_decoder mpm_decoder;
+
+/* Allocates a decoder (parameters zero).  Synchronous. */
+mpm_status decoder_create(const decoder_desc* desc, mpm_decoder** out);
+void decoder_destroy(mpm_decoder* dec);
+
+/* Number of FP32 parameters: sum over layers of out*in + out. */
+int64_t decoder_num_params(const mpm_decoder* dec);
+
+/*
+ * Sets the FP32 master parameters and the scaling.  `params` holds, layer by
+ * layer, W (out x in, row-major) then b (out); `norm` holds 4*d floats:
+ * X_min[d], X_range[d], out_shift[d], out_scale[d]; the network evaluates
+ * g = out_scale * MLP((X - X_min) / X_range, xhat) + out_shift.  Host or
+ * device pointers.  Also refreshes the BF16 copies used by the tensor cores.
+ */
+mpm_status decoder_set_params(mpm_decoder* dec, const float* params, const float* norm, void* stream);
+mpm_status decoder_get_params(const mpm_decoder* dec, float* params, float* norm, void* stream);
+
+/* Row kinds of decoder_eval. */
+enum {
+  DECODER_PRIMAL = 0,     /* g(X; xhat) */
+  /* 1 .. d:          dg/dX_k, k = kind - 1                             */
+  /* d+1 .. d+r:      dg/dxhat_j, j = kind - d - 1                      */
+  DECODER_JVP = 1000,     /* (dg/dxhat) u with u = dirs[lat_idx[p]]       */
+  DECODER_SECANT = 1001   /* g(X; xhat + u) - g(X; xhat), u = dirs[lat_idx[p]] */
+};
+
+/*
+ * Evaluates the decoder and derivatives at n points.  Device pointers:
+ *   X        (n, d) reference positions.
+ *   lat_idx  (n) int32 row of `latents` (and `dirs`) per point, or NULL (row 0).
+ *   latents  (n_lat, r) latent coordinates xhat.
+ *   dirs     (n_lat, r) directions for DECODER_JVP / DECODER_SECANT rows
+ *            (NULL if none is requested).
+ *   kinds    host array of R row kinds (R in 1..64); kinds[0] must be
+ *            DECODER_PRIMAL.
+ *   out      (R, n, d): out[k][p] = the quantity of kinds[k] at point p.
+ * The square hidden layers run as BF16 x BF16 -> FP32 tcgen05 GEMMs; the
+ * first layer (K = d + r) and the output layer (N = d) in FP32.
+ * Derivative rows propagate with the primal pre-activations of the same
+ * point (forward-mode chain rule); secant rows propagate the exact
+ * difference act(z + dz) - act(z), so they resolve latent increments far
+ * below BF16 resolution.
+ */
+mpm_status decoder_eval(const mpm_decoder* dec, const float* X, const int32_t* lat_idx, const float* latents,
+                        const float* dirs, const int32_t* kinds, int R, int64_t n, float* out, void* stream);
+
+/* Synchronises `stream`; OR of MPM_STATUS_* bits raised by decoder kernels. */
+mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPMROM_H */

@@ -1,0 +1,544 @@
+// Implicit neural decoder g(X; xhat) (Section 3.1, Eq. kinematicRestriction;
+// Section 4, Table 1) with its Jacobians (Eq. defGrad: dg/dX; Eq. timederOne:
+// dg/dxhat) on sm_103a tensor cores.
+//
+// Network: h0 = act(W0 [Xn, xhat] + b0), h_l = act(W_l h_{l-1} + b_l) for the
+// square hidden layers, y = Wout h + bout, g = out_scale * y + out_shift,
+// Xn = (X - X_min) / X_range (min-max input scaling and output
+// standardisation of Appendix B), act = ELU.
+//
+// Derivatives are propagated forward as extra rows of the same GEMMs: every
+// point contributes R rows to a 128-row tile (kind-major: rows kind*Pt + q),
+//   kind 0          primal              h = act(z)
+//   tangent kinds   dg along an input direction   t = act'(z) . (W t_prev)
+//   secant kind     g(xhat + delta) - g(xhat)     s = act(z + W s_prev) - act(z)
+// where z is the primal pre-activation of the same point, exchanged through
+// shared memory.  The secant rows give differences of decoder outputs without
+// the BF16 rounding of the two absolute evaluations (the Gauss-Newton
+// residual needs differences far below BF16 resolution).
+//
+// Per tile: layer 0 (K = d + r <= 35) and the output layer (N = d) run in
+// FP32 on the CUDA cores; each square 128 x 128 layer is one M=128, N=128,
+// K=128 tcgen05.mma chain (BF16 operands from shared memory in the 128-byte
+// swizzled K-major layout, FP32 accumulator in tensor memory), read back with
+// tcgen05.ld for the bias/activation/tangent epilogue, which writes the next
+// layer's BF16 operand tile in place.  All square-layer weights stay resident
+// in shared memory (loaded once per CTA with bulk async copies); the kernel
+// is persistent over tiles.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace mpmrom {
+
+constexpr int kW = 128;          // hidden width of the tensor-core layers
+constexpr int kMaxTC = 4;        // square layers resident in shared memory
+constexpr int kMaxR = 64;        // row kinds per point
+constexpr int kLayerBytes = kW * kW * 2;
+
+struct DecArgs {
+  int d, r, n_tc, act;
+  const float* W0;    // (W, d + r)
+  const float* b0;    // (W)
+  const float* bh;    // (n_tc, W)
+  const float* Wout;  // (d, W)
+  const float* bout;  // (d)
+  const float* norm;  // X_min[d], X_range[d], out_shift[d], out_scale[d]
+  const uint8_t* wimg;
+  const float* X;
+  const int32_t* lat;
+  const float* latents;
+  const float* dirs;
+  int64_t n;
+  int R, Pt;
+  int kinds[kMaxR];
+  float* out;         // (R, n, d)
+  uint32_t* status;
+  // linear decoder (no hidden layer): y = W0 [Xn, xhat] + b0 with W0 (d, d + r)
+  int linear;
+};
+
+__device__ __forceinline__ float elu(float z) { return z > 0.f ? z : expm1f(z); }
+__device__ __forceinline__ float elu_d1(float z) { return z > 0.f ? 1.f : __expf(z); }
+// act(z + dz) - act(z) without cancellation on the negative branch
+__device__ __forceinline__ float elu_secant(float z, float dz) {
+  float z1 = z + dz;
+  if (z > 0.f && z1 > 0.f) return dz;
+  if (z <= 0.f && z1 <= 0.f) return __expf(z) * expm1f(dz);
+  return elu(z1) - elu(z);
+}
+
+__device__ __forceinline__ float act_f(int act, float z) { return act == 0 ? elu(z) : z; }
+__device__ __forceinline__ float act_d1(int act, float z) { return act == 0 ? elu_d1(z) : 1.f; }
+__device__ __forceinline__ float act_sec(int act, float z, float dz) { return act == 0 ? elu_secant(z, dz) : dz; }
+
+// row-kind codes (see decoder_eval in include/mpmrom.h)
+constexpr int KIND_PRIMAL = 0;
+constexpr int KIND_JVP = 1000;
+constexpr int KIND_SECANT = 1001;
+
+struct RowInfo {
+  int kind;      // code
+  int cls;       // 0 primal, 1 tangent, 2 secant, -1 padding
+  int q;         // point within tile
+  int64_t p;     // global point index
+};
+
+__device__ __forceinline__ RowInfo row_info(const DecArgs& a, int t, int64_t tile_first) {
+  RowInfo ri;
+  ri.q = t % a.Pt;
+  int k = t / a.Pt;
+  ri.p = tile_first + ri.q;
+  if (k >= a.R || ri.p >= a.n) {
+    ri.cls = -1;
+    ri.kind = -1;
+    return ri;
+  }
+  ri.kind = a.kinds[k];
+  ri.cls = ri.kind == KIND_PRIMAL ? 0 : (ri.kind == KIND_SECANT ? 2 : 1);
+  return ri;
+}
+
+// Input vector (normalised) and direction of one row.
+__device__ __forceinline__ void row_inputs(const DecArgs& a, const RowInfo& ri, float* in, float* dir) {
+  const int d = a.d, r = a.r;
+  const int li = a.lat ? a.lat[ri.p] : 0;
+  for (int i = 0; i < d; ++i) {
+    in[i] = (a.X[ri.p * d + i] - a.norm[i]) / a.norm[d + i];
+    dir[i] = 0.f;
+  }
+  for (int j = 0; j < r; ++j) {
+    in[d + j] = a.latents[(int64_t)li * r + j];
+    dir[d + j] = 0.f;
+  }
+  if (ri.cls == 1) {
+    if (ri.kind >= 1 && ri.kind <= d) dir[ri.kind - 1] = 1.f / a.norm[d + ri.kind - 1];
+    else if (ri.kind > d && ri.kind <= d + r) dir[ri.kind - 1] = 1.f;
+    else if (ri.kind == KIND_JVP)
+      for (int j = 0; j < r; ++j) dir[d + j] = a.dirs[(int64_t)li * r + j];
+  } else if (ri.cls == 2) {
+    for (int j = 0; j < r; ++j) dir[d + j] = a.dirs[(int64_t)li * r + j];
+  }
+}
+
+// --------------------------------------------------------------------------
+// Decoders without square layers (linear, or a single hidden layer): SIMT.
+// --------------------------------------------------------------------------
+__global__ void decoder_simt(DecArgs a) {
+  const int64_t rows = a.n * a.R;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < rows; g += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(g / a.n);
+    RowInfo ri;
+    ri.p = g % a.n;
+    ri.q = 0;
+    ri.kind = a.kinds[k];
+    ri.cls = ri.kind == KIND_PRIMAL ? 0 : (ri.kind == KIND_SECANT ? 2 : 1);
+    float in[40], dir[40];
+    row_inputs(a, ri, in, dir);
+    const int K = a.d + a.r;
+    float y[3] = {0.f, 0.f, 0.f};
+    if (a.linear) {
+      for (int i = 0; i < a.d; ++i) {
+        float z = 0.f;
+        for (int c = 0; c < K; ++c) z = fmaf(a.W0[i * K + c], ri.cls == 0 ? in[c] : dir[c], z);
+        y[i] = z + (ri.cls == 0 ? a.b0[i] : 0.f);
+      }
+    } else {
+      for (int c = 0; c < kW; ++c) {
+        float z = a.b0[c], zd = 0.f;
+        for (int i = 0; i < K; ++i) {
+          z = fmaf(a.W0[c * K + i], in[i], z);
+          zd = fmaf(a.W0[c * K + i], dir[i], zd);
+        }
+        float h = ri.cls == 0 ? act_f(a.act, z) : (ri.cls == 1 ? act_d1(a.act, z) * zd : act_sec(a.act, z, zd));
+        for (int i = 0; i < a.d; ++i) y[i] = fmaf(a.Wout[i * kW + c], h, y[i]);
+      }
+      if (ri.cls == 0)
+        for (int i = 0; i < a.d; ++i) y[i] += a.bout[i];
+    }
+    float* o = a.out + ((int64_t)k * a.n + ri.p) * a.d;
+    for (int i = 0; i < a.d; ++i) o[i] = y[i] * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Tensor-core decoder kernel: 128 threads, thread t owns row t of the tile
+// (tensor-memory lane t).
+// --------------------------------------------------------------------------
+struct __align__(8) DecSmemTail {
+  uint64_t bar_w;
+  uint64_t bar_mma;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ void store_bf16x8(uint8_t* tile, int row, int col, const float* v) {
+  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
+  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]);
+  __nv_bfloat162 p3 = __floats2bfloat162_rn(v[6], v[7]);
+  uint4 u;
+  u.x = *reinterpret_cast<uint32_t*>(&p0);
+  u.y = *reinterpret_cast<uint32_t*>(&p1);
+  u.z = *reinterpret_cast<uint32_t*>(&p2);
+  u.w = *reinterpret_cast<uint32_t*>(&p3);
+  *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row, col, kW)) = u;
+}
+
+__global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte alignment for the swizzled operand tiles
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* wsm = smem;                                   // n_tc x 32 KB
+  uint8_t* atile = smem + kMaxTC * kLayerBytes;          // 32 KB
+  float* zx = (float*)(atile + kLayerBytes);             // Pt x 128 fp32 (if R > 1)
+  DecSmemTail* tail = (DecSmemTail*)(zx + 64 * kW);
+  const int t = threadIdx.x, warp = t >> 5;
+
+  if (t == 0) {
+    tc::mbar_init(&tail->bar_w, 1);
+    tc::mbar_init(&tail->bar_mma, 1);
+    tail->abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc<kW>(&tail->tmem);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tail->tmem;
+
+  // resident weights of the square layers
+  if (t == 0) {
+    tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(a.n_tc * kLayerBytes));
+    for (int l = 0; l < a.n_tc; ++l)
+      tc::bulk_g2s(wsm + l * kLayerBytes, a.wimg + (size_t)l * kLayerBytes, kLayerBytes, &tail->bar_w);
+  }
+  if (!tc::mbar_wait(&tail->bar_w, 0)) {
+    raise_status(a.status, STATUS_TIMEOUT);
+    atomicExch(&tail->abort, 1);
+  }
+  __syncthreads();
+
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kW);
+  uint32_t mma_phase = 0;
+  const int64_t n_tiles = (a.n + a.Pt - 1) / a.Pt;
+  const int K0 = a.d + a.r;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !tail->abort; tile += gridDim.x) {
+    const int64_t first = tile * a.Pt;
+    const RowInfo ri = row_info(a, t, first);
+    float in[40], dir[40];
+    if (ri.cls >= 0) row_inputs(a, ri, in, dir);
+
+    // ---- layer 0 on the CUDA cores (FP32), 8 columns at a time
+    for (int c0 = 0; c0 < kW; c0 += 8) {
+      float h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = c0 + j;
+        float z = __ldg(&a.b0[c]), zd = 0.f;
+        if (ri.cls >= 0) {
+          for (int i = 0; i < K0; ++i) {
+            const float w = __ldg(&a.W0[c * K0 + i]);
+            z = fmaf(w, in[i], z);
+            zd = fmaf(w, dir[i], zd);
+          }
+          h[j] = ri.cls == 0 ? act_f(a.act, z) : (ri.cls == 1 ? act_d1(a.act, z) * zd : act_sec(a.act, z, zd));
+        } else {
+          h[j] = 0.f;
+        }
+      }
+      store_bf16x8(atile, t, c0, h);
+    }
+
+    float y[3] = {0.f, 0.f, 0.f};
+    for (int l = 0; l < a.n_tc; ++l) {
+      // make the generic-proxy writes of the operand tile visible to the tensor core
+      tc::fence_async_smem();
+      tc::tc_fence_before();
+      __syncthreads();
+      if (t == 0) {
+        tc::tc_fence_after();
+        const uint32_t a_base = tc::smem_addr(atile), b_base = tc::smem_addr(wsm + l * kLayerBytes);
+#pragma unroll
+        for (int k = 0; k < kW / 16; ++k) {
+          const uint32_t koff = (uint32_t)((k >> 2) * (kW * 128) + (k & 3) * 32);
+          tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + koff), tc::smem_desc_sw128(b_base + koff), idesc,
+                       k > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(&tail->bar_mma);
+      }
+      if (!tc::mbar_wait(&tail->bar_mma, mma_phase)) {
+        raise_status(a.status, STATUS_TIMEOUT);
+        atomicExch(&tail->abort, 1);
+      }
+      mma_phase ^= 1u;
+      tc::tc_fence_after();
+      __syncthreads();
+      if (tail->abort) break;
+      const bool last = (l == a.n_tc - 1);
+      const float* bl = a.bh + l * kW;
+      for (int ch = 0; ch < kW / 32; ++ch) {
+        float acc[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, acc);
+        // primal rows: z = acc + b; publish z for the derivative rows of the same point
+        if (ri.cls == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            acc[i] += __ldg(&bl[ch * 32 + i]);
+            if (a.R > 1) zx[ri.q * kW + ch * 32 + i] = acc[i];
+            acc[i] = act_f(a.act, acc[i]);
+          }
+        }
+        if (a.R > 1) __syncthreads();
+        if (ri.cls == 1) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] *= act_d1(a.act, zx[ri.q * kW + ch * 32 + i]);
+        } else if (ri.cls == 2) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] = act_sec(a.act, zx[ri.q * kW + ch * 32 + i], acc[i]);
+        } else if (ri.cls < 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+        }
+        if (last) {
+          // output layer fused into the last epilogue (FP32)
+          for (int o = 0; o < a.d; ++o) {
+            float s = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) s = fmaf(__ldg(&a.Wout[o * kW + ch * 32 + i]), acc[i], s);
+            y[o] += s;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; j += 8) store_bf16x8(atile, t, ch * 32 + j, acc + j);
+        }
+        if (a.R > 1) __syncthreads();
+      }
+      tc::tc_fence_before();
+    }
+    if (tail->abort) break;
+    if (ri.cls >= 0) {
+      const int kidx = t / a.Pt;  // position of this row's kind in `kinds`
+      float* o = a.out + ((int64_t)kidx * a.n + ri.p) * a.d;
+      for (int i = 0; i < a.d; ++i) {
+        float v = y[i] + (ri.cls == 0 ? __ldg(&a.bout[i]) : 0.f);
+        o[i] = v * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_free<kW>(tmem);
+}
+
+// Packs the square-layer weights (FP32, (out, in) row-major) into BF16 images
+// in the 128-byte swizzled K-major layout the MMA reads.
+__global__ void decoder_pack(const float* W, int n_layers, int64_t stride, uint8_t* img) {
+  const int64_t total = (int64_t)n_layers * kW * kW;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int l = (int)(i / (kW * kW));
+    int rem = (int)(i % (kW * kW));
+    int row = rem / kW, k = rem % kW;
+    __nv_bfloat16 v = __float2bfloat16_rn(W[l * stride + rem]);
+    *reinterpret_cast<__nv_bfloat16*>(img + (size_t)l * kLayerBytes + tc::sw128_offset(row, k, kW)) = v;
+  }
+}
+
+}  // namespace mpmrom
+
+using namespace mpmrom;
+
+struct mpm_decoder {
+  int d = 0, r = 0, width = 0, n_hidden = 0, act = 0;
+  int n_tc = 0;
+  int64_t n_params = 0;
+  std::vector<int64_t> w_off, b_off;  // per linear layer offsets into params
+  float* params = nullptr;            // FP32 master copy
+  float* norm = nullptr;
+  float* wsq = nullptr;               // square-layer weights gathered contiguously (n_tc, W, W)
+  float* bsq = nullptr;               // their biases (n_tc, W)
+  uint8_t* wimg = nullptr;            // BF16 swizzled images
+  uint32_t* status = nullptr;
+  int n_sm = 0;
+  size_t smem = 0;
+};
+
+namespace {
+
+size_t dec_smem_bytes() {
+  return 1024 + kMaxTC * kLayerBytes + kLayerBytes + 64 * kW * sizeof(float) + sizeof(DecSmemTail);
+}
+
+mpm_status refresh_derived(mpm_decoder* dec, cudaStream_t s) {
+  if (dec->n_tc == 0) return MPM_OK;
+  for (int l = 0; l < dec->n_tc; ++l) {
+    MPM_CUDA_TRY(cudaMemcpyAsync(dec->wsq + (size_t)l * kW * kW, dec->params + dec->w_off[1 + l],
+                                 sizeof(float) * kW * kW, cudaMemcpyDeviceToDevice, s));
+    MPM_CUDA_TRY(cudaMemcpyAsync(dec->bsq + (size_t)l * kW, dec->params + dec->b_off[1 + l], sizeof(float) * kW,
+                                 cudaMemcpyDeviceToDevice, s));
+  }
+  decoder_pack<<<std::max(1, std::min(dec->n_sm * 4, dec->n_tc * 64)), 256, 0, s>>>(dec->wsq, dec->n_tc,
+                                                                                    (int64_t)kW * kW, dec->wimg);
+  MPM_CUDA_TRY(cudaGetLastError());
+  return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpm_status decoder_create(const decoder_desc* desc, mpm_decoder** out) {
+  MPM_CHECK_ARG(desc && out, "null argument");
+  *out = nullptr;
+  MPM_CHECK_ARG(desc->d == 2 || desc->d == 3, "d must be 2 or 3");
+  MPM_CHECK_ARG(desc->r >= 0 && desc->d + desc->r <= 40, "d + r must be <= 40");
+  MPM_CHECK_ARG(desc->n_hidden >= 0, "n_hidden >= 0");
+  MPM_CHECK_ARG(desc->activation == 0 || desc->activation == 1, "activation: 0 ELU, 1 identity");
+  MPM_CHECK_ARG(desc->n_hidden == 0 || desc->width == kW, "hidden width must be 128");
+  MPM_CHECK_ARG(desc->n_hidden <= kMaxTC + 1, "at most 5 hidden layers");
+  auto* dec = new mpm_decoder();
+  dec->d = desc->d;
+  dec->r = desc->r;
+  dec->width = desc->width;
+  dec->n_hidden = desc->n_hidden;
+  dec->act = desc->activation;
+  dec->n_tc = std::max(0, desc->n_hidden - 1);
+  std::vector<int> dims;
+  dims.push_back(dec->d + dec->r);
+  for (int l = 0; l < dec->n_hidden; ++l) dims.push_back(kW);
+  dims.push_back(dec->d);
+  int64_t off = 0;
+  for (size_t l = 0; l + 1 < dims.size(); ++l) {
+    dec->w_off.push_back(off);
+    off += (int64_t)dims[l] * dims[l + 1];
+    dec->b_off.push_back(off);
+    off += dims[l + 1];
+  }
+  dec->n_params = off;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&dec->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  dec->smem = dec_smem_bytes();
+  cudaError_t e = cudaMalloc((void**)&dec->params, sizeof(float) * dec->n_params);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dec->norm, sizeof(float) * 4 * dec->d);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dec->status, sizeof(uint32_t));
+  if (e == cudaSuccess && dec->n_tc > 0) {
+    e = cudaMalloc((void**)&dec->wsq, sizeof(float) * dec->n_tc * kW * kW);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dec->bsq, sizeof(float) * dec->n_tc * kW);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dec->wimg, (size_t)dec->n_tc * kLayerBytes);
+  }
+  if (e == cudaSuccess) e = cudaMemset(dec->params, 0, sizeof(float) * dec->n_params);
+  if (e == cudaSuccess) e = cudaMemset(dec->status, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(decoder_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec->smem);
+  if (e != cudaSuccess) {
+    decoder_destroy(dec);
+    return set_error(MPM_ENOMEM, std::string("decoder_create: ") + cudaGetErrorString(e));
+  }
+  *out = dec;
+  return MPM_OK;
+}
+
+void decoder_destroy(mpm_decoder* dec) {
+  if (!dec) return;
+  cudaFree(dec->params);
+  cudaFree(dec->norm);
+  cudaFree(dec->wsq);
+  cudaFree(dec->bsq);
+  cudaFree(dec->wimg);
+  cudaFree(dec->status);
+  delete dec;
+}
+
+int64_t decoder_num_params(const mpm_decoder* dec) { return dec ? dec->n_params : 0; }
+
+mpm_status decoder_set_params(mpm_decoder* dec, const float* params, const float* norm, void* stream) {
+  MPM_CHECK_ARG(dec && params && norm, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  MPM_CUDA_TRY(cudaMemcpyAsync(dec->params, params, sizeof(float) * dec->n_params, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(dec->norm, norm, sizeof(float) * 4 * dec->d, cudaMemcpyDefault, s));
+  return refresh_derived(dec, s);
+}
+
+mpm_status decoder_get_params(const mpm_decoder* dec, float* params, float* norm, void* stream) {
+  MPM_CHECK_ARG(dec, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (params) MPM_CUDA_TRY(cudaMemcpyAsync(params, dec->params, sizeof(float) * dec->n_params, cudaMemcpyDefault, s));
+  if (norm) MPM_CUDA_TRY(cudaMemcpyAsync(norm, dec->norm, sizeof(float) * 4 * dec->d, cudaMemcpyDefault, s));
+  return MPM_OK;
+}
+
+mpm_status decoder_eval(const mpm_decoder* dec, const float* X, const int32_t* lat_idx, const float* latents,
+                        const float* dirs, const int32_t* kinds, int R, int64_t n, float* out, void* stream) {
+  MPM_CHECK_ARG(dec && kinds, "null argument");
+  MPM_CHECK_ARG(R >= 1 && R <= kMaxR && R <= 128, "R must be in [1, 64]");
+  MPM_CHECK_ARG(n >= 0, "n >= 0");
+  if (n == 0) return MPM_OK;
+  MPM_CHECK_ARG(X && latents && out, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  DecArgs a{};
+  a.d = dec->d;
+  a.r = dec->r;
+  a.n_tc = dec->n_tc;
+  a.act = dec->act;
+  a.linear = dec->n_hidden == 0;
+  a.W0 = dec->params + dec->w_off[0];
+  a.b0 = dec->params + dec->b_off[0];
+  a.bh = dec->bsq;
+  const int L = (int)dec->w_off.size();
+  a.Wout = dec->params + dec->w_off[L - 1];
+  a.bout = dec->params + dec->b_off[L - 1];
+  a.norm = dec->norm;
+  a.wimg = dec->wimg;
+  a.X = X;
+  a.lat = lat_idx;
+  a.latents = latents;
+  a.dirs = dirs;
+  a.n = n;
+  a.R = R;
+  a.Pt = 128 / R;
+  bool need_dirs = false;
+  for (int k = 0; k < R; ++k) {
+    const int c = kinds[k];
+    MPM_CHECK_ARG(c == KIND_PRIMAL || (c >= 1 && c <= dec->d + dec->r) || c == KIND_JVP || c == KIND_SECANT,
+                  "unknown row kind");
+    need_dirs |= (c == KIND_JVP || c == KIND_SECANT);
+    a.kinds[k] = c;
+  }
+  MPM_CHECK_ARG(!need_dirs || dirs, "JVP / secant rows need dirs");
+  MPM_CHECK_ARG(kinds[0] == KIND_PRIMAL || dec->n_tc == 0, "the first row kind must be the primal (0)");
+  a.out = out;
+  a.status = dec->status;
+  if (dec->n_tc == 0) {
+    int64_t rows = n * R;
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, dec->n_sm * 8));
+    decoder_simt<<<blocks, 128, 0, s>>>(a);
+  } else {
+    const int64_t tiles = (n + a.Pt - 1) / a.Pt;
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));
+    decoder_tc<<<blocks, 128, dec->smem, s>>>(a);
+  }
+  MPM_CUDA_TRY(cudaGetLastError());
+  return MPM_OK;
+}
+
+mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void* stream) {
+  MPM_CHECK_ARG(dec && out, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t h = 0;
+  MPM_CUDA_TRY(cudaMemcpyAsync(&h, dec->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (clear) MPM_CUDA_TRY(cudaMemsetAsync(dec->status, 0, sizeof(uint32_t), s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = h;
+  return MPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1131 @@
+// Full-order explicit MPM step (Algorithm 1, Section 2.2) on sm_103a.
+//
+// Data layout in HBM (all owned by mpm_ctx):
+//   state[2]   particle state, structure of arrays, one float stream per
+//              component: x[D], v[D], F[D*D], C[D*D]  (stream c at base + c*P),
+//              plus id[P] (the caller's particle index).  Two buffers: a step
+//              gathers from one and writes the other in block order.
+//   key[P]     grid-block key of every particle of the current buffer:
+//              inst * nblk + block of floor(x/dx - 0.5).
+//   perm[P]    binned order: perm[j] = index in the current buffer of the
+//              j-th particle when sorted by key.
+//   grid[2]    per instance a dense n^D array of float4 {m, p_x, p_y, p_z}
+//              (p = m v + dt f, the momentum after the internal-force impulse).
+//              grid[g] holds the particle-to-grid transfer of the current
+//              state; grid[1-g] is zero except for blocks flagged in touched.
+//
+// One step = three kernels, captured in a CUDA graph by the caller if wanted:
+//   mpm_g2p2g      per work item (<= 256 particles of one grid block): load
+//                  the block's node tile of grid[g], apply the grid update of
+//                  Algorithm 1 (v = p/m + dt g, walls) while loading, gather to
+//                  the particles (grid-to-particle + advection), write the new
+//                  state contiguously, then scatter the new state's
+//                  particle-to-grid contributions into a shared-memory node
+//                  tile and flush it with vector atomics into grid[1-g]
+//                  (= the first half of the next step).  New keys are counted
+//                  with warp-aggregated atomics.
+//   mpm_scan       single-pass exclusive scan of the key counts (decoupled
+//                  look-back over tiles of 1024 keys), work list.
+//   mpm_permute    binned order of the new keys (warp-aggregated slot
+//                  claims) and clearing of the grid that was just consumed.
+// Particle state therefore moves through HBM once per step (gather-read of
+// x, F; write of x, v, F, C), and the grid update costs no pass of its own.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "mpm_math.cuh"
+
+namespace mpmrom {
+
+constexpr int kChunk = 256;  // particles per work item = threads per CTA
+
+template <int D> struct Blk;
+template <> struct Blk<2> { static constexpr int B = 8; };
+template <> struct Blk<3> { static constexpr int B = 4; };
+
+struct DevParams {
+  int P;
+  int n;            // grid nodes per axis
+  int nb;           // blocks per axis
+  int nblk;         // blocks per instance
+  int n_keys;       // n_inst * nblk
+  int64_t gnodes;   // nodes per instance
+  float dx, inv_dx, dt;
+  float g[3];
+  int bc, bc_width;
+  float mass, vol;
+  const float2* mu_lam;  // per instance
+};
+
+struct StateView {
+  float* base;  // component c at base + c * P
+  int32_t* id;
+};
+
+template <int D>
+__device__ __forceinline__ int key_of_base(const int b[D], int inst, const DevParams& p) {
+  constexpr int B = Blk<D>::B;
+  int k = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) k = k * p.nb + b[a] / B;
+  return inst * p.nblk + k;
+}
+
+// Grid update of Algorithm 1 for one node: v = p/m + dt g if m > 0, then walls.
+template <int D>
+__device__ __forceinline__ void node_velocity(float4 mp, const int node[D], const DevParams& p, float v[D]) {
+  float comp[3] = {mp.y, mp.z, mp.w};
+  if (mp.x > 0.f) {
+    float im = 1.0f / mp.x;
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = comp[a] * im + p.dt * p.g[a];
+  } else {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = 0.f;
+  }
+  const int lo = p.bc_width, hi = p.n - 1 - p.bc_width;
+  bool sticky = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    bool l = node[a] < lo, h = node[a] > hi;
+    if (p.bc == MPM_BC_SLIP_FLOOR && a == 1) {
+      sticky |= h;
+      if (l) v[1] = fmaxf(v[1], 0.f);
+    } else {
+      sticky |= (l | h);
+    }
+  }
+  if (sticky) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = 0.f;
+  }
+}
+
+// Tile of nodes [b0 - lo_pad, b0 + B + hi_pad)^D, flattened row-major.
+template <int D, int T>
+__device__ __forceinline__ int tile_index(const int rel[D]) {
+  int t = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) t = t * T + rel[a];
+  return t;
+}
+
+template <int D>
+__device__ __forceinline__ int64_t grid_index(const int node[D], int inst, const DevParams& p) {
+  int64_t g = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) g = g * p.n + node[a];
+  return (int64_t)inst * p.gnodes + g;
+}
+
+__device__ __forceinline__ void atomic_add_node(float4* addr, float4 val) {
+  atomicAdd(addr, val);  // vector red.global (sm_90+)
+}
+
+// Particle-to-grid contribution of one particle into the shared tile (or, if
+// its stencil leaves the tile, straight into the global grid).
+//   MLS:  m_i += w m;  p_i += w (m v + A (x_i - x_p)),  A = m C - dt V0 (4/dx^2) tau
+//   PIC:  m_i += w m;  p_i += w m v - dt V0 tau grad N_i
+template <int D, int TRANSFER, int TP>
+__device__ __forceinline__ void scatter_particle(const float x[D], const float v[D], const float C[D * D],
+                                                 const float tau[D * D], const int tile_lo[D], int inst,
+                                                 float* s_m, float* s_p, float4* grid, uint8_t* touched,
+                                                 const DevParams& p, uint32_t* status) {
+  constexpr int B = Blk<D>::B;
+  constexpr int NT = (D == 2) ? TP * TP : TP * TP * TP;
+  int base[D];
+  float w[D][3], dw[D][3], fx[D];
+  bool out_of_grid = false, in_tile = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    base[a] = stencil_base(x[a], p.inv_dx);
+    fx[a] = x[a] * p.inv_dx - (float)base[a];
+    bspline_w(fx[a], w[a]);
+    if (TRANSFER == MPM_TRANSFER_PIC) bspline_dw(fx[a], dw[a]);
+    out_of_grid |= (base[a] < 0) | (base[a] + 2 > p.n - 1);
+    int r = base[a] - tile_lo[a];
+    in_tile &= (r >= 0) & (r + 2 < TP);
+  }
+  if (out_of_grid) {
+    raise_status(status, STATUS_OUT_OF_GRID);
+    return;
+  }
+  float A[D * D];
+  if (TRANSFER == MPM_TRANSFER_MLS) {
+    const float k = p.dt * p.vol * 4.0f * p.inv_dx * p.inv_dx;
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) A[i] = p.mass * C[i] - k * tau[i];
+  }
+  const int NS = (D == 2) ? 9 : 27;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    int off[D];
+    if (D == 2) {
+      off[0] = s / 3;
+      off[1] = s % 3;
+    } else {
+      off[0] = s / 9;
+      off[D - 2] = (s / 3) % 3;
+      off[D - 1] = s % 3;
+    }
+    float wt = 1.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) wt *= w[a][off[a]];
+    float mom[D];
+    if (TRANSFER == MPM_TRANSFER_MLS) {
+      float dpos[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) dpos[a] = (float)(base[a] + off[a]) * p.dx - x[a];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float q = p.mass * v[a];
+#pragma unroll
+        for (int b = 0; b < D; ++b) q = fmaf(A[a * D + b], dpos[b], q);
+        mom[a] = wt * q;
+      }
+    } else {
+      float grad[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float gg = dw[a][off[a]] * p.inv_dx;
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+          if (b != a) gg *= w[b][off[b]];
+        grad[a] = gg;
+      }
+      const float k = p.dt * p.vol;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float f = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) f = fmaf(tau[a * D + b], grad[b], f);
+        mom[a] = wt * p.mass * v[a] - k * f;
+      }
+    }
+    if (in_tile) {
+      int rel[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) rel[a] = base[a] + off[a] - tile_lo[a];
+      int t = tile_index<D, TP>(rel);
+      atomicAdd(&s_m[t], wt * p.mass);
+#pragma unroll
+      for (int a = 0; a < D; ++a) atomicAdd(&s_p[a * NT + t], mom[a]);
+    } else {
+      int node[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) node[a] = base[a] + off[a];
+      float4 val = make_float4(wt * p.mass, mom[0], D > 1 ? mom[1] : 0.f, D > 2 ? mom[D - 1] : 0.f);
+      atomic_add_node(&grid[grid_index<D>(node, inst, p)], val);
+      uint8_t* f = &touched[key_of_base<D>(node, inst, p)];
+      if (*f == 0) *f = 1;
+    }
+  }
+}
+
+// Flushes a shared P2G tile into the global grid (non-empty nodes only) and
+// flags the grid blocks it wrote.
+template <int D, int TP>
+__device__ __forceinline__ void flush_tile(const float* s_m, const float* s_p, const int tile_lo[D], int inst,
+                                           float4* grid, uint8_t* touched, const DevParams& p) {
+  constexpr int NT = (D == 2) ? TP * TP : TP * TP * TP;
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    float m = s_m[t];
+    if (m == 0.f) continue;
+    int node[D];
+    int r = t;
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      node[a] = tile_lo[a] + r % TP;
+      r /= TP;
+    }
+    float4 val = make_float4(m, s_p[t], D > 1 ? s_p[NT + t] : 0.f, D > 2 ? s_p[2 * NT + t] : 0.f);
+    atomic_add_node(&grid[grid_index<D>(node, inst, p)], val);
+    uint8_t* f = &touched[key_of_base<D>(node, inst, p)];
+    if (*f == 0) *f = 1;
+  }
+}
+
+__device__ __forceinline__ void count_key_aggregated(int key, int32_t* counts) {
+  unsigned active = __activemask();
+  unsigned peers = __match_any_sync(active, key);
+  int leader = __ffs(peers) - 1;
+  if ((int)(threadIdx.x & 31) == leader && key >= 0) atomicAdd(&counts[key], __popc(peers));
+}
+
+// --------------------------------------------------------------------------
+// The fused step kernel.  FIRST = true runs only the particle-to-grid half
+// (the transfer of a freshly loaded state).
+// --------------------------------------------------------------------------
+template <int D, int MATERIAL, int TRANSFER, bool FIRST, bool FP64_POLAR>
+__global__ void __launch_bounds__(kChunk) mpm_g2p2g(DevParams p, StateView src, StateView dst,
+                                                     const int32_t* __restrict__ perm,
+                                                     const int4* __restrict__ work, const int32_t* n_work,
+                                                     const float4* __restrict__ grid_cur, float4* grid_nxt,
+                                                     uint8_t* touched_nxt, int32_t* key_out,
+                                                     int32_t* counts, uint32_t* status) {
+  constexpr int B = Blk<D>::B;
+  constexpr int TG = B + 2;  // grid-to-particle tile: nodes [b0, b0 + B + 2)
+  constexpr int TP = B + 4;  // particle-to-grid tile: nodes [b0 - 1, b0 + B + 3)
+  constexpr int NG = (D == 2) ? TG * TG : TG * TG * TG;
+  constexpr int NT = (D == 2) ? TP * TP : TP * TP * TP;
+  constexpr int DD = D * D;
+  __shared__ float s_v[D * NG];
+  __shared__ float s_m[NT];
+  __shared__ float s_p[D * NT];
+
+  const int nw = *n_work;
+  const int P = p.P;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const int4 item = work[w];  // {key, start, count, -}
+    const int key = item.x;
+    const int inst = key / p.nblk;
+    int bk = key - inst * p.nblk;
+    int b0[D];
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      b0[a] = (bk % p.nb) * B;
+      bk /= p.nb;
+    }
+    const float2 ml = p.mu_lam[inst];
+    int tile_lo[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) tile_lo[a] = b0[a] - 1;
+    // grid-to-particle tile with the grid update applied on load
+    if (!FIRST) {
+      for (int t = threadIdx.x; t < NG; t += blockDim.x) {
+        int node[D];
+        int r = t;
+        bool inside = true;
+#pragma unroll
+        for (int a = D - 1; a >= 0; --a) {
+          node[a] = b0[a] + r % TG;
+          r /= TG;
+          inside &= node[a] < p.n;
+        }
+        float v[D];
+        if (inside) {
+          node_velocity<D>(grid_cur[grid_index<D>(node, inst, p)], node, p, v);
+        } else {
+#pragma unroll
+          for (int a = 0; a < D; ++a) v[a] = 0.f;
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) s_v[a * NG + t] = v[a];
+      }
+    }
+    for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+      s_m[t] = 0.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) s_p[a * NT + t] = 0.f;
+    }
+    __syncthreads();
+
+    const int j = item.y + threadIdx.x;
+    const bool active = threadIdx.x < item.z;
+    int new_key = -1;
+    if (active) {
+      const int s = perm[j];
+      float x[D], v[D], F[DD], C[DD];
+#pragma unroll
+      for (int a = 0; a < D; ++a) x[a] = src.base[(size_t)a * P + s];
+#pragma unroll
+      for (int i = 0; i < DD; ++i) F[i] = src.base[(size_t)(2 * D + i) * P + s];
+      const int pid = src.id[s];
+      if (FIRST) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) v[a] = src.base[(size_t)(D + a) * P + s];
+#pragma unroll
+        for (int i = 0; i < DD; ++i) C[i] = src.base[(size_t)(2 * D + DD + i) * P + s];
+      } else {
+        // grid-to-particle (Algorithm 1 step 3) from the tile
+        int base[D];
+        float w[D][3], dw[D][3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          base[a] = stencil_base(x[a], p.inv_dx);
+          float fx = x[a] * p.inv_dx - (float)base[a];
+          bspline_w(fx, w[a]);
+          if (TRANSFER == MPM_TRANSFER_PIC) bspline_dw(fx, dw[a]);
+        }
+        float Bm[DD];
+#pragma unroll
+        for (int a = 0; a < D; ++a) v[a] = 0.f;
+#pragma unroll
+        for (int i = 0; i < DD; ++i) Bm[i] = 0.f;
+        const int NS = (D == 2) ? 9 : 27;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          int off[D];
+          if (D == 2) {
+            off[0] = q / 3;
+            off[1] = q % 3;
+          } else {
+            off[0] = q / 9;
+            off[D - 2] = (q / 3) % 3;
+            off[D - 1] = q % 3;
+          }
+          int rel[D];
+          float wt = 1.f;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            // in range for every particle binned to this block; the clamp only
+            // keeps clamped out-of-grid particles (already flagged) in bounds
+            rel[a] = min(max(base[a] - b0[a], 0), B - 1) + off[a];
+            wt *= w[a][off[a]];
+          }
+          const int t = tile_index<D, TG>(rel);
+          float vi[D];
+#pragma unroll
+          for (int a = 0; a < D; ++a) vi[a] = s_v[a * NG + t];
+#pragma unroll
+          for (int a = 0; a < D; ++a) v[a] = fmaf(wt, vi[a], v[a]);
+          if (TRANSFER == MPM_TRANSFER_MLS) {
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+              float dp = (float)(base[b] + off[b]) * p.dx - x[b];
+#pragma unroll
+              for (int a = 0; a < D; ++a) Bm[a * D + b] = fmaf(wt * vi[a], dp, Bm[a * D + b]);
+            }
+          } else {
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+              float gg = dw[b][off[b]] * p.inv_dx;
+#pragma unroll
+              for (int c = 0; c < D; ++c)
+                if (c != b) gg *= w[c][off[c]];
+#pragma unroll
+              for (int a = 0; a < D; ++a) Bm[a * D + b] = fmaf(vi[a], gg, Bm[a * D + b]);
+            }
+          }
+        }
+        float G[DD];  // velocity gradient used for F
+        if (TRANSFER == MPM_TRANSFER_MLS) {
+          const float k = 4.0f * p.inv_dx * p.inv_dx;
+#pragma unroll
+          for (int i = 0; i < DD; ++i) {
+            C[i] = k * Bm[i];
+            G[i] = C[i];
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < DD; ++i) {
+            C[i] = 0.f;
+            G[i] = Bm[i];
+          }
+        }
+        // F <- (I + dt G) F
+        float Fn[DD];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            float acc = F[a * D + b];
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc = fmaf(p.dt * G[a * D + c], F[c * D + b], acc);
+            Fn[a * D + b] = acc;
+          }
+#pragma unroll
+        for (int i = 0; i < DD; ++i) F[i] = Fn[i];
+#pragma unroll
+        for (int a = 0; a < D; ++a) x[a] = fmaf(p.dt, v[a], x[a]);
+        // write the new state contiguously (block order of the old keys)
+#pragma unroll
+        for (int a = 0; a < D; ++a) dst.base[(size_t)a * P + j] = x[a];
+#pragma unroll
+        for (int a = 0; a < D; ++a) dst.base[(size_t)(D + a) * P + j] = v[a];
+#pragma unroll
+        for (int i = 0; i < DD; ++i) dst.base[(size_t)(2 * D + i) * P + j] = F[i];
+#pragma unroll
+        for (int i = 0; i < DD; ++i) dst.base[(size_t)(2 * D + DD + i) * P + j] = C[i];
+        dst.id[j] = pid;
+        // health checks
+        bool finite = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) finite &= isfinite(x[a]) && isfinite(v[a]);
+#pragma unroll
+        for (int i = 0; i < DD; ++i) finite &= isfinite(F[i]);
+        if (!finite) raise_status(status, STATUS_NONFINITE);
+        else if (det_minus_one<D>(F) <= -1.0f) raise_status(status, STATUS_INVERTED);
+        // new key (clamped into the grid so that binning stays in range)
+        int nbse[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float xs = finite ? x[a] : 0.f;
+          int b = stencil_base(xs, p.inv_dx);
+          nbse[a] = min(max(b, 0), p.n - 1);
+        }
+        new_key = key_of_base<D>(nbse, inst, p);
+        key_out[j] = new_key;
+      }
+      // particle-to-grid of the (new) state into the next grid
+      float tau[DD];
+      kirchhoff<D, MATERIAL, FP64_POLAR>(F, ml.x, ml.y, tau);
+      scatter_particle<D, TRANSFER, TP>(x, v, C, tau, tile_lo, inst, s_m, s_p, grid_nxt, touched_nxt, p, status);
+    }
+    if (!FIRST) count_key_aggregated(new_key, counts);
+    __syncthreads();
+    flush_tile<D, TP>(s_m, s_p, tile_lo, inst, grid_nxt, touched_nxt, p);
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of the key counts and work list: single pass over tiles of
+// 1024 keys with decoupled look-back (Merrill and Garland 2016).  Each CTA
+// publishes its tile aggregate, then its inclusive prefix, in one 64-bit word
+// per tile: bits 0-31 particle count, bits 32-61 work items, bits 62-63 flag
+// (1 = aggregate, 2 = inclusive prefix).  Predecessor polls are bounded; on
+// timeout the CTA raises TIMEOUT and treats the missing prefix as zero.
+// Work item = {key, start, count, 0}.  Counts and cursors are zeroed.
+constexpr int kScanTile = 1024;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kScanTile) mpm_scan(int n_keys, int P, int32_t* counts, int32_t* offsets,
+                                                       int32_t* cursor, int4* work, int32_t* n_work, int max_work,
+                                                       unsigned long long* tile_state, uint32_t* status) {
+  __shared__ int s_a[32], s_b[32];
+  __shared__ long long s_prefix[2];
+  const int tile = blockIdx.x;
+  const int k = tile * kScanTile + threadIdx.x;
+  const int c = k < n_keys ? counts[k] : 0;
+  const int nw = (c + kChunk - 1) / kChunk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int a = c, b = nw;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int ya = __shfl_up_sync(0xffffffffu, a, o), yb = __shfl_up_sync(0xffffffffu, b, o);
+    if (lane >= o) {
+      a += ya;
+      b += yb;
+    }
+  }
+  if (lane == 31) {
+    s_a[warp] = a;
+    s_b[warp] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int sa = s_a[lane], sb = s_b[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int ya = __shfl_up_sync(0xffffffffu, sa, o), yb = __shfl_up_sync(0xffffffffu, sb, o);
+      if (lane >= o) {
+        sa += ya;
+        sb += yb;
+      }
+    }
+    s_a[lane] = sa;
+    s_b[lane] = sb;
+    if (lane == 31) {
+      // look back over the predecessor tiles
+      const unsigned long long agg = (unsigned long long)(uint32_t)sa | ((unsigned long long)(uint32_t)sb << 32);
+      st_release_u64(&tile_state[tile], agg | (1ull << 62));
+      long long pa = 0, pb = 0;
+      for (int q = tile - 1; q >= 0; --q) {
+        unsigned long long v = 0;
+        uint32_t tries = 0;
+        do {
+          v = ld_acquire_u64(&tile_state[q]);
+        } while ((v >> 62) == 0 && ++tries < (1u << 24));
+        if ((v >> 62) == 0) {
+          raise_status(status, STATUS_TIMEOUT);
+          break;
+        }
+        pa += (long long)(v & 0xffffffffull);
+        pb += (long long)((v >> 32) & 0x3fffffffull);
+        if ((v >> 62) == 2) break;
+      }
+      const unsigned long long inc = (unsigned long long)(uint32_t)(pa + sa) |
+                                     ((unsigned long long)(uint32_t)(pb + sb) << 32);
+      st_release_u64(&tile_state[tile], inc | (2ull << 62));
+      s_prefix[0] = pa;
+      s_prefix[1] = pb;
+    }
+  }
+  __syncthreads();
+  const int off = (int)s_prefix[0] + a - c + (warp > 0 ? s_a[warp - 1] : 0);
+  int woff = (int)s_prefix[1] + b - nw + (warp > 0 ? s_b[warp - 1] : 0);
+  if (k < n_keys) {
+    offsets[k] = off;
+    for (int q = 0; q < nw; ++q) {
+      if (woff < max_work) work[woff] = make_int4(k, off + q * kChunk, min(kChunk, c - q * kChunk), 0);
+      ++woff;
+    }
+    counts[k] = 0;
+    cursor[k] = 0;
+  }
+  if (tile == gridDim.x - 1 && threadIdx.x == kScanTile - 1) {
+    const int total = (int)s_prefix[0] + s_a[31];
+    const int wtotal = (int)s_prefix[1] + s_b[31];
+    offsets[n_keys] = total;
+    *n_work = min(wtotal, max_work);
+    if (wtotal > max_work || total != P) raise_status(status, STATUS_CAPACITY);
+  }
+}
+
+// Binned order of the keys (warp-aggregated slot claims; the order inside a
+// block is not specified) and clearing of the consumed grid.
+template <int D>
+__global__ void mpm_permute(DevParams p, const int32_t* __restrict__ key, const int32_t* __restrict__ offsets,
+                            int32_t* cursor, int32_t* perm, float4* grid_clear, uint8_t* touched_clear,
+                            unsigned long long* tile_state, int n_tiles) {
+  constexpr int B = Blk<D>::B;
+  constexpr int BN = (D == 2) ? B * B : B * B * B;
+  const int stride = gridDim.x * blockDim.x;
+  // the scan that produced `offsets` has finished: reset its look-back words
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_tiles; q += stride) tile_state[q] = 0ull;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i - (int)threadIdx.x < p.P; i += stride) {
+    int k = i < p.P ? key[i] : -1;
+    unsigned peers = __match_any_sync(0xffffffffu, k);
+    int leader = __ffs(peers) - 1;
+    int lane = threadIdx.x & 31;
+    int basev = 0;
+    if (lane == leader && k >= 0) basev = atomicAdd(&cursor[k], __popc(peers));
+    basev = __shfl_sync(0xffffffffu, basev, leader);
+    if (k >= 0) {
+      int rank = __popc(peers & ((1u << lane) - 1u));
+      perm[offsets[k] + basev + rank] = i;
+    }
+  }
+  // clear flagged blocks of the consumed grid
+  if (grid_clear == nullptr) return;
+  const int warps_total = stride / 32;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  for (int k = gw; k < p.n_keys; k += warps_total) {
+    if (!touched_clear[k]) continue;
+    const int inst = k / p.nblk;
+    int bk = k - inst * p.nblk;
+    int b0[D];
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      b0[a] = (bk % p.nb) * B;
+      bk /= p.nb;
+    }
+    for (int t = lane; t < BN; t += 32) {
+      int node[D];
+      int r = t;
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+        node[a] = b0[a] + r % B;
+        r /= B;
+      }
+      grid_clear[grid_index<D>(node, inst, p)] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    if (lane == 0) touched_clear[k] = 0;
+  }
+}
+
+// Caller layout (AoS rows) -> internal SoA, keys and counts.
+template <int D>
+__global__ void mpm_load(DevParams p, const float* __restrict__ x, const float* __restrict__ v,
+                         const float* __restrict__ F, const float* __restrict__ C, StateView dst,
+                         const int64_t* __restrict__ inst_offsets, int n_inst, int32_t* key, int32_t* counts,
+                         int zero_C, uint32_t* status) {
+  constexpr int DD = D * D;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i - (int)threadIdx.x < p.P; i += gridDim.x * blockDim.x) {
+    int k = -1;
+    if (i < p.P) {
+      // instance of particle i (n_inst is small; linear search over offsets)
+      int inst = 0;
+      while (inst + 1 < n_inst && inst_offsets[inst + 1] <= i) ++inst;
+      int b[D];
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float xa = x[(size_t)i * D + a];
+        dst.base[(size_t)a * p.P + i] = xa;
+        dst.base[(size_t)(D + a) * p.P + i] = v[(size_t)i * D + a];
+        ok &= isfinite(xa);
+        int bb = stencil_base(ok ? xa : 0.f, p.inv_dx);
+        if (bb < 0 || bb + 2 > p.n - 1) raise_status(status, STATUS_OUT_OF_GRID);
+        b[a] = min(max(bb, 0), p.n - 1);
+      }
+      if (!ok) raise_status(status, STATUS_NONFINITE);
+#pragma unroll
+      for (int q = 0; q < DD; ++q) {
+        dst.base[(size_t)(2 * D + q) * p.P + i] = F[(size_t)i * DD + q];
+        dst.base[(size_t)(2 * D + DD + q) * p.P + i] = (zero_C || C == nullptr) ? 0.f : C[(size_t)i * DD + q];
+      }
+      dst.id[i] = i;
+      k = key_of_base<D>(b, inst, p);
+      key[i] = k;
+    }
+    count_key_aggregated(k, counts);
+  }
+}
+
+// Internal SoA -> caller layout in the caller's particle order.
+template <int D>
+__global__ void mpm_store(DevParams p, StateView src, float* x, float* v, float* F, float* C) {
+  constexpr int DD = D * D;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += gridDim.x * blockDim.x) {
+    int q = src.id[i];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (x) x[(size_t)q * D + a] = src.base[(size_t)a * p.P + i];
+      if (v) v[(size_t)q * D + a] = src.base[(size_t)(D + a) * p.P + i];
+    }
+#pragma unroll
+    for (int r = 0; r < DD; ++r) {
+      if (F) F[(size_t)q * DD + r] = src.base[(size_t)(2 * D + r) * p.P + i];
+      if (C) C[(size_t)q * DD + r] = src.base[(size_t)(2 * D + DD + r) * p.P + i];
+    }
+  }
+}
+
+template <int D>
+__global__ void mpm_bins(DevParams p, StateView src, const int32_t* key, int32_t* cell_keys, int32_t* block_keys) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += gridDim.x * blockDim.x) {
+    int q = src.id[i];
+    int c = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) c = c * p.n + stencil_base(src.base[(size_t)a * p.P + i], p.inv_dx);
+    cell_keys[q] = c;
+    block_keys[q] = key[i];
+  }
+}
+
+template <int D>
+__global__ void mpm_grid_dump(DevParams p, int n_inst, const float4* grid, float* mass, float* mom, float* vel) {
+  const int64_t total = (int64_t)n_inst * p.gnodes;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    float4 mp = grid[g];
+    int64_t r = g % p.gnodes;
+    int node[D];
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      node[a] = (int)(r % p.n);
+      r /= p.n;
+    }
+    if (mass) mass[g] = mp.x;
+    float comp[3] = {mp.y, mp.z, mp.w};
+    if (mom)
+#pragma unroll
+      for (int a = 0; a < D; ++a) mom[g * D + a] = comp[a];
+    if (vel) {
+      float v[D];
+      node_velocity<D>(mp, node, p, v);
+#pragma unroll
+      for (int a = 0; a < D; ++a) vel[g * D + a] = v[a];
+    }
+  }
+}
+
+}  // namespace mpmrom
+
+// ============================================================================
+// Host runtime and C ABI
+// ============================================================================
+using namespace mpmrom;
+
+struct mpm_ctx {
+  int D = 0, n = 0, B = 0, nb = 0, nblk = 0, n_keys = 0, P = 0, n_inst = 0;
+  int material = 0, transfer = 0;
+  int64_t gnodes = 0;
+  mpm_config cfg{};
+  std::vector<float> E, nu;
+  std::vector<int64_t> offs;
+  int n_sm = 0, fused_grid = 0, max_work = 0;
+  // device
+  float* state[2] = {nullptr, nullptr};
+  int32_t* id[2] = {nullptr, nullptr};
+  int32_t *key = nullptr, *perm = nullptr, *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
+  int4* work = nullptr;
+  int32_t* n_work = nullptr;
+  unsigned long long* tile_state = nullptr;
+  int n_scan_tiles = 0;
+  float4* grid[2] = {nullptr, nullptr};
+  uint8_t* touched[2] = {nullptr, nullptr};
+  float2* mu_lam = nullptr;
+  int64_t* d_offs = nullptr;
+  uint32_t* status = nullptr;
+  float* staging = nullptr;  // AoS x, v, F, C
+  int cur = 0, g = 0;
+  bool loaded = false;
+  DevParams dp{};
+};
+
+namespace {
+
+template <typename T>
+mpm_status dalloc(T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return set_error(MPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  return MPM_OK;
+}
+
+#define MPM_TRY(expr)            \
+  do {                           \
+    mpm_status _s = (expr);      \
+    if (_s != MPM_OK) return _s; \
+  } while (0)
+
+template <int D, int MAT, int TR, bool FIRST, bool FP64>
+mpm_status launch_fused_t(mpm_ctx* c, cudaStream_t s) {
+  StateView src{c->state[c->cur], c->id[c->cur]};
+  StateView dst{c->state[1 - c->cur], c->id[1 - c->cur]};
+  float4* gcur = c->grid[c->g];
+  float4* gnxt = FIRST ? c->grid[c->g] : c->grid[1 - c->g];
+  uint8_t* tn = FIRST ? c->touched[c->g] : c->touched[1 - c->g];
+  mpm_g2p2g<D, MAT, TR, FIRST, FP64><<<c->fused_grid, kChunk, 0, s>>>(
+      c->dp, src, dst, c->perm, c->work, c->n_work, gcur, gnxt, tn, c->key, c->counts, c->status);
+  MPM_CUDA_TRY(cudaGetLastError());
+  return MPM_OK;
+}
+
+template <bool FIRST>
+mpm_status launch_fused(mpm_ctx* c, cudaStream_t s) {
+  const int D = c->D, M = c->material, T = c->transfer;
+#define CASE(d, m, t)                                        \
+  if (D == d && M == m && T == t) return launch_fused_t<d, m, t, FIRST, true>(c, s);
+  CASE(2, 0, 0) CASE(2, 0, 1) CASE(2, 1, 0) CASE(2, 1, 1)
+  CASE(3, 0, 0) CASE(3, 0, 1) CASE(3, 1, 0) CASE(3, 1, 1)
+#undef CASE
+  return set_error(MPM_EINVAL, "unsupported (dim, material, transfer)");
+}
+
+mpm_status launch_scan_permute(mpm_ctx* c, cudaStream_t s, bool clear_consumed) {
+  mpm_scan<<<c->n_scan_tiles, kScanTile, 0, s>>>(c->n_keys, c->P, c->counts, c->offsets, c->cursor, c->work,
+                                                 c->n_work, c->max_work, c->tile_state, c->status);
+  MPM_CUDA_TRY(cudaGetLastError());
+  int blocks = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 8));
+  float4* gclr = clear_consumed ? c->grid[c->g] : nullptr;
+  uint8_t* tclr = clear_consumed ? c->touched[c->g] : nullptr;
+  if (c->D == 2)
+    mpm_permute<2><<<blocks, 256, 0, s>>>(c->dp, c->key, c->offsets, c->cursor, c->perm, gclr, tclr, c->tile_state,
+                                          c->n_scan_tiles);
+  else
+    mpm_permute<3><<<blocks, 256, 0, s>>>(c->dp, c->key, c->offsets, c->cursor, c->perm, gclr, tclr, c->tile_state,
+                                          c->n_scan_tiles);
+  MPM_CUDA_TRY(cudaGetLastError());
+  return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
+  MPM_CHECK_ARG(cfg && out, "null argument");
+  *out = nullptr;
+  MPM_CHECK_ARG(cfg->dim == 2 || cfg->dim == 3, "dim must be 2 or 3");
+  const int B = cfg->dim == 2 ? Blk<2>::B : Blk<3>::B;
+  MPM_CHECK_ARG(cfg->n_grid >= 8 && cfg->n_grid % B == 0, "n_grid must be a multiple of 8 (2D) / 4 (3D)");
+  MPM_CHECK_ARG(cfg->n_inst >= 1 && cfg->E && cfg->nu && cfg->inst_offsets, "instances");
+  MPM_CHECK_ARG(cfg->dx > 0 && cfg->dt > 0 && cfg->rho > 0 && cfg->p_vol > 0, "dx, dt, rho, p_vol must be > 0");
+  MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
+  MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
+  MPM_CHECK_ARG(cfg->bc == MPM_BC_STICKY || cfg->bc == MPM_BC_SLIP_FLOOR, "bc");
+  MPM_CHECK_ARG(cfg->bc_width >= 0, "bc_width");
+  MPM_CHECK_ARG(cfg->inst_offsets[0] == 0, "inst_offsets[0] must be 0");
+  for (int k = 0; k < cfg->n_inst; ++k)
+    MPM_CHECK_ARG(cfg->inst_offsets[k + 1] >= cfg->inst_offsets[k], "inst_offsets must be non-decreasing");
+  const int64_t P64 = cfg->inst_offsets[cfg->n_inst];
+  MPM_CHECK_ARG(P64 >= 1 && P64 < (1ll << 30), "particle count out of range");
+  auto* c = new mpm_ctx();
+  c->cfg = *cfg;
+  c->D = cfg->dim;
+  c->n = cfg->n_grid;
+  c->B = B;
+  c->nb = c->n / B;
+  c->nblk = c->D == 2 ? c->nb * c->nb : c->nb * c->nb * c->nb;
+  c->n_inst = cfg->n_inst;
+  const int64_t nk = (int64_t)c->n_inst * c->nblk;
+  if (nk >= (1ll << 30)) {
+    delete c;
+    return set_error(MPM_EINVAL, "too many grid blocks");
+  }
+  c->n_keys = (int)nk;
+  c->P = (int)P64;
+  c->material = cfg->material;
+  c->transfer = cfg->transfer;
+  c->gnodes = c->D == 2 ? (int64_t)c->n * c->n : (int64_t)c->n * c->n * c->n;
+  c->E.assign(cfg->E, cfg->E + c->n_inst);
+  c->nu.assign(cfg->nu, cfg->nu + c->n_inst);
+  c->offs.assign(cfg->inst_offsets, cfg->inst_offsets + c->n_inst + 1);
+  c->cfg.E = nullptr;
+  c->cfg.nu = nullptr;
+  c->cfg.inst_offsets = nullptr;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  c->max_work = ceil_div(c->P, kChunk) + std::min(c->n_keys, c->P) + 1;
+
+  const int D = c->D, DD = D * D;
+  const size_t comps = 2 * D + 2 * DD;
+  mpm_status st = MPM_OK;
+  auto fail = [&](mpm_status s) {
+    mpm_destroy(c);
+    return s;
+  };
+  for (int b = 0; b < 2; ++b) {
+    if ((st = dalloc(&c->state[b], comps * c->P)) != MPM_OK) return fail(st);
+    if ((st = dalloc(&c->id[b], c->P)) != MPM_OK) return fail(st);
+    if ((st = dalloc(&c->grid[b], (size_t)c->n_inst * c->gnodes)) != MPM_OK) return fail(st);
+    if ((st = dalloc(&c->touched[b], c->n_keys)) != MPM_OK) return fail(st);
+  }
+  if ((st = dalloc(&c->key, c->P)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->perm, c->P)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->counts, c->n_keys)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->cursor, c->n_keys)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->offsets, c->n_keys + 1)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->work, c->max_work)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->n_work, 1)) != MPM_OK) return fail(st);
+  c->n_scan_tiles = ceil_div(c->n_keys, kScanTile);
+  if ((st = dalloc(&c->tile_state, c->n_scan_tiles)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->mu_lam, c->n_inst)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->d_offs, c->n_inst + 1)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->status, 1)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->staging, comps * c->P)) != MPM_OK) return fail(st);
+  std::vector<float2> ml(c->n_inst);
+  for (int k = 0; k < c->n_inst; ++k) {
+    double E = c->E[k], nu = c->nu[k];
+    if (!(E > 0) || !(nu > -1 && nu < 0.5)) return fail(set_error(MPM_EINVAL, "E must be > 0 and -1 < nu < 0.5"));
+    ml[k] = make_float2((float)(E / (2 * (1 + nu))), (float)(E * nu / ((1 + nu) * (1 - 2 * nu))));
+  }
+  cudaError_t e = cudaSuccess;
+  e = cudaMemcpy(c->mu_lam, ml.data(), sizeof(float2) * c->n_inst, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_offs, c->offs.data(), sizeof(int64_t) * (c->n_inst + 1), cudaMemcpyHostToDevice);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMemset(c->grid[b], 0, sizeof(float4) * (size_t)c->n_inst * c->gnodes);
+    if (e == cudaSuccess) e = cudaMemset(c->touched[b], 0, c->n_keys);
+  }
+  if (e == cudaSuccess) e = cudaMemset(c->counts, 0, sizeof(int32_t) * c->n_keys);
+  if (e == cudaSuccess) e = cudaMemset(c->cursor, 0, sizeof(int32_t) * c->n_keys);
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->n_work, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->tile_state, 0, sizeof(unsigned long long) * c->n_scan_tiles);
+  if (e != cudaSuccess) return fail(set_error(MPM_ECUDA, std::string("init: ") + cudaGetErrorString(e)));
+
+  DevParams& p = c->dp;
+  p.P = c->P;
+  p.n = c->n;
+  p.nb = c->nb;
+  p.nblk = c->nblk;
+  p.n_keys = c->n_keys;
+  p.gnodes = c->gnodes;
+  p.dx = cfg->dx;
+  p.inv_dx = (float)(1.0 / cfg->dx);
+  p.dt = cfg->dt;
+  for (int a = 0; a < 3; ++a) p.g[a] = cfg->gravity[a];
+  p.bc = cfg->bc;
+  p.bc_width = cfg->bc_width;
+  p.mass = cfg->rho * cfg->p_vol;
+  p.vol = cfg->p_vol;
+  p.mu_lam = c->mu_lam;
+  c->fused_grid = std::max(1, std::min(c->max_work, c->n_sm * 8));
+  *out = c;
+  return MPM_OK;
+}
+
+void mpm_destroy(mpm_ctx* c) {
+  if (!c) return;
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(c->state[b]);
+    cudaFree(c->id[b]);
+    cudaFree(c->grid[b]);
+    cudaFree(c->touched[b]);
+  }
+  cudaFree(c->key);
+  cudaFree(c->perm);
+  cudaFree(c->counts);
+  cudaFree(c->cursor);
+  cudaFree(c->offsets);
+  cudaFree(c->work);
+  cudaFree(c->n_work);
+  cudaFree(c->tile_state);
+  cudaFree(c->mu_lam);
+  cudaFree(c->d_offs);
+  cudaFree(c->status);
+  cudaFree(c->staging);
+  delete c;
+}
+
+mpm_status mpm_set_state(mpm_ctx* c, const float* x, const float* v, const float* F, const float* C, void* stream) {
+  MPM_CHECK_ARG(c && x && v && F, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int D = c->D, DD = D * D;
+  const size_t P = c->P;
+  float* sx = c->staging;
+  float* sv = sx + P * D;
+  float* sF = sv + P * D;
+  float* sC = sF + P * DD;
+  MPM_CUDA_TRY(cudaMemcpyAsync(sx, x, sizeof(float) * P * D, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(sv, v, sizeof(float) * P * D, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(sF, F, sizeof(float) * P * DD, cudaMemcpyDefault, s));
+  const bool zeroC = (C == nullptr) || c->transfer == MPM_TRANSFER_PIC;
+  if (!zeroC) MPM_CUDA_TRY(cudaMemcpyAsync(sC, C, sizeof(float) * P * DD, cudaMemcpyDefault, s));
+  // a fresh start: both grids zero, no pending clears
+  for (int b = 0; b < 2; ++b) {
+    MPM_CUDA_TRY(cudaMemsetAsync(c->grid[b], 0, sizeof(float4) * (size_t)c->n_inst * c->gnodes, s));
+    MPM_CUDA_TRY(cudaMemsetAsync(c->touched[b], 0, c->n_keys, s));
+  }
+  MPM_CUDA_TRY(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * c->n_keys, s));
+  c->cur = 0;
+  c->g = 0;
+  StateView dst{c->state[0], c->id[0]};
+  int blocks = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 8));
+  if (D == 2)
+    mpm_load<2><<<blocks, 256, 0, s>>>(c->dp, sx, sv, sF, sC, dst, c->d_offs, c->n_inst, c->key, c->counts,
+                                       zeroC ? 1 : 0, c->status);
+  else
+    mpm_load<3><<<blocks, 256, 0, s>>>(c->dp, sx, sv, sF, sC, dst, c->d_offs, c->n_inst, c->key, c->counts,
+                                       zeroC ? 1 : 0, c->status);
+  MPM_CUDA_TRY(cudaGetLastError());
+  MPM_TRY(launch_scan_permute(c, s, /*clear_consumed=*/false));
+  MPM_TRY(launch_fused<true>(c, s));
+  c->loaded = true;
+  return MPM_OK;
+}
+
+mpm_status mpm_step(mpm_ctx* c, int n_steps, void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  MPM_CHECK_ARG(c->loaded, "mpm_set_state must be called first");
+  MPM_CHECK_ARG(n_steps >= 0, "n_steps must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int k = 0; k < n_steps; ++k) {
+    MPM_TRY(launch_fused<false>(c, s));
+    // the new state lives in the other buffer; the consumed grid is cleared
+    c->cur = 1 - c->cur;
+    MPM_TRY(launch_scan_permute(c, s, /*clear_consumed=*/true));
+    c->g = 1 - c->g;
+  }
+  return MPM_OK;
+}
+
+mpm_status mpm_step_profiled(mpm_ctx* c, int n_steps, float* kernel_ms, void* stream) {
+  MPM_CHECK_ARG(c && kernel_ms, "null argument");
+  MPM_CHECK_ARG(c->loaded, "mpm_set_state must be called first");
+  MPM_CHECK_ARG(n_steps >= 0, "n_steps must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) MPM_CUDA_TRY(cudaEventCreate(&ev[i]));
+  mpm_status st = MPM_OK;
+  for (int k = 0; k < n_steps && st == MPM_OK; ++k) {
+    cudaEventRecord(ev[0], s);
+    st = launch_fused<false>(c, s);
+    if (st != MPM_OK) break;
+    c->cur = 1 - c->cur;
+    cudaEventRecord(ev[1], s);
+    mpm_scan<<<c->n_scan_tiles, kScanTile, 0, s>>>(c->n_keys, c->P, c->counts, c->offsets, c->cursor, c->work,
+                                                   c->n_work, c->max_work, c->tile_state, c->status);
+    cudaEventRecord(ev[2], s);
+    int blocks = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 8));
+    if (c->D == 2)
+      mpm_permute<2><<<blocks, 256, 0, s>>>(c->dp, c->key, c->offsets, c->cursor, c->perm, c->grid[c->g],
+                                            c->touched[c->g], c->tile_state, c->n_scan_tiles);
+    else
+      mpm_permute<3><<<blocks, 256, 0, s>>>(c->dp, c->key, c->offsets, c->cursor, c->perm, c->grid[c->g],
+                                            c->touched[c->g], c->tile_state, c->n_scan_tiles);
+    cudaEventRecord(ev[3], s);
+    c->g = 1 - c->g;
+    if (cudaEventSynchronize(ev[3]) != cudaSuccess) {
+      st = set_error(MPM_ECUDA, "event sync");
+      break;
+    }
+    for (int q = 0; q < 3; ++q) cudaEventElapsedTime(&kernel_ms[3 * k + q], ev[q], ev[q + 1]);
+  }
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  MPM_CUDA_TRY(cudaGetLastError());
+  return st;
+}
+
+mpm_status mpm_get_state(mpm_ctx* c, float* x, float* v, float* F, float* C, void* stream) {
+  MPM_CHECK_ARG(c && c->loaded, "no state loaded");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int D = c->D, DD = D * D;
+  const size_t P = c->P;
+  float* sx = c->staging;
+  float* sv = sx + P * D;
+  float* sF = sv + P * D;
+  float* sC = sF + P * DD;
+  StateView src{c->state[c->cur], c->id[c->cur]};
+  int blocks = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 8));
+  if (D == 2)
+    mpm_store<2><<<blocks, 256, 0, s>>>(c->dp, src, sx, sv, sF, sC);
+  else
+    mpm_store<3><<<blocks, 256, 0, s>>>(c->dp, src, sx, sv, sF, sC);
+  MPM_CUDA_TRY(cudaGetLastError());
+  if (x) MPM_CUDA_TRY(cudaMemcpyAsync(x, sx, sizeof(float) * P * D, cudaMemcpyDefault, s));
+  if (v) MPM_CUDA_TRY(cudaMemcpyAsync(v, sv, sizeof(float) * P * D, cudaMemcpyDefault, s));
+  if (F) MPM_CUDA_TRY(cudaMemcpyAsync(F, sF, sizeof(float) * P * DD, cudaMemcpyDefault, s));
+  if (C) MPM_CUDA_TRY(cudaMemcpyAsync(C, sC, sizeof(float) * P * DD, cudaMemcpyDefault, s));
+  return MPM_OK;
+}
+
+mpm_status mpm_status_word(mpm_ctx* c, uint32_t* out, int clear, void* stream) {
+  MPM_CHECK_ARG(c && out, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t h = 0;
+  MPM_CUDA_TRY(cudaMemcpyAsync(&h, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (clear) MPM_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(uint32_t), s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = h;
+  return MPM_OK;
+}
+
+int64_t mpm_num_block_keys(const mpm_ctx* c) { return c ? c->n_keys : 0; }
+
+mpm_status mpm_debug_bins(mpm_ctx* c, int32_t* cell_keys, int32_t* block_keys, int32_t* block_offsets, void* stream) {
+  MPM_CHECK_ARG(c && c->loaded && cell_keys && block_keys, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t *dc = nullptr, *db = nullptr;
+  MPM_CUDA_TRY(cudaMallocAsync((void**)&dc, sizeof(int32_t) * c->P, s));
+  MPM_CUDA_TRY(cudaMallocAsync((void**)&db, sizeof(int32_t) * c->P, s));
+  StateView src{c->state[c->cur], c->id[c->cur]};
+  int blocks = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 8));
+  if (c->D == 2)
+    mpm_bins<2><<<blocks, 256, 0, s>>>(c->dp, src, c->key, dc, db);
+  else
+    mpm_bins<3><<<blocks, 256, 0, s>>>(c->dp, src, c->key, dc, db);
+  MPM_CUDA_TRY(cudaGetLastError());
+  MPM_CUDA_TRY(cudaMemcpyAsync(cell_keys, dc, sizeof(int32_t) * c->P, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(block_keys, db, sizeof(int32_t) * c->P, cudaMemcpyDefault, s));
+  if (block_offsets)
+    MPM_CUDA_TRY(cudaMemcpyAsync(block_offsets, c->offsets, sizeof(int32_t) * (c->n_keys + 1), cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaFreeAsync(dc, s));
+  MPM_CUDA_TRY(cudaFreeAsync(db, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return MPM_OK;
+}
+
+mpm_status mpm_debug_grid(mpm_ctx* c, float* mass, float* momentum, float* velocity, void* stream) {
+  MPM_CHECK_ARG(c && c->loaded, "no state loaded");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)c->n_inst * c->gnodes;
+  float *dm = nullptr, *dp = nullptr, *dv = nullptr;
+  if (mass) MPM_CUDA_TRY(cudaMallocAsync((void**)&dm, sizeof(float) * N, s));
+  if (momentum) MPM_CUDA_TRY(cudaMallocAsync((void**)&dp, sizeof(float) * N * c->D, s));
+  if (velocity) MPM_CUDA_TRY(cudaMallocAsync((void**)&dv, sizeof(float) * N * c->D, s));
+  int blocks = std::max(1, std::min(ceil_div((long long)N, 256), c->n_sm * 16));
+  if (c->D == 2)
+    mpm_grid_dump<2><<<blocks, 256, 0, s>>>(c->dp, c->n_inst, c->grid[c->g], dm, dp, dv);
+  else
+    mpm_grid_dump<3><<<blocks, 256, 0, s>>>(c->dp, c->n_inst, c->grid[c->g], dm, dp, dv);
+  MPM_CUDA_TRY(cudaGetLastError());
+  if (mass) MPM_CUDA_TRY(cudaMemcpyAsync(mass, dm, sizeof(float) * N, cudaMemcpyDefault, s));
+  if (momentum) MPM_CUDA_TRY(cudaMemcpyAsync(momentum, dp, sizeof(float) * N * c->D, cudaMemcpyDefault, s));
+  if (velocity) MPM_CUDA_TRY(cudaMemcpyAsync(velocity, dv, sizeof(float) * N * c->D, cudaMemcpyDefault, s));
+  if (dm) MPM_CUDA_TRY(cudaFreeAsync(dm, s));
+  if (dp) MPM_CUDA_TRY(cudaFreeAsync(dp, s));
+  if (dv) MPM_CUDA_TRY(cudaFreeAsync(dv, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return MPM_OK;
+}
+
+}  // extern "C"

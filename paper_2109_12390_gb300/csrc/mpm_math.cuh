@@ -1,0 +1,199 @@
+// Device math of the explicit MPM step: quadratic B-spline stencil, Lame
+// parameters, Kirchhoff stress of the neo-Hookean and fixed-corotated laws,
+// polar factor of F.  Used by the full-order kernels and by the local step of
+// the reduced model.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace mpmrom {
+
+// Quadratic B-spline (the basis reading of Section 2.2): node k of the
+// stencil sits at t = fx - k cells, fx = x/dx - base in [0.5, 1.5).
+__device__ __forceinline__ void bspline_w(float fx, float w[3]) {
+  float a = 1.5f - fx, b = fx - 1.0f, c = fx - 0.5f;
+  w[0] = 0.5f * a * a;
+  w[1] = 0.75f - b * b;
+  w[2] = 0.5f * c * c;
+}
+// Derivative dN/dfx of the three stencil weights (per cell).
+__device__ __forceinline__ void bspline_dw(float fx, float dw[3]) {
+  dw[0] = fx - 1.5f;
+  dw[1] = -2.0f * (fx - 1.0f);
+  dw[2] = fx - 0.5f;
+}
+
+// floor(x * inv_dx - 0.5); exact for power-of-two dx (x * inv_dx is a scaling
+// by a power of two and the subtraction of 0.5 is exact), the same integer the
+// FP64 definition gives.
+__device__ __forceinline__ int stencil_base(float x, float inv_dx) {
+  return (int)floorf(x * inv_dx - 0.5f);
+}
+
+// det(F) - 1 without cancellation (fma keeps the product exact before the -1).
+template <int D>
+__device__ __forceinline__ float det_minus_one(const float F[D * D]);
+
+template <>
+__device__ __forceinline__ float det_minus_one<2>(const float F[4]) {
+  return fmaf(F[0], F[3], -1.0f) - F[1] * F[2];
+}
+
+template <>
+__device__ __forceinline__ float det_minus_one<3>(const float F[9]) {
+  // det = F00 (F11 F22 - F12 F21) - F01 (F10 F22 - F12 F20) + F02 (F10 F21 - F11 F20)
+  float c0 = fmaf(F[4], F[8], -F[5] * F[7]);
+  float c1 = fmaf(F[3], F[8], -F[5] * F[6]);
+  float c2 = fmaf(F[3], F[7], -F[4] * F[6]);
+  return fmaf(F[0], c0, -1.0f) - F[1] * c1 + F[2] * c2;
+}
+
+// --------------------------------------------------------------------------
+// Polar factor R of F = R S (det R = +1 for det F > 0).
+//
+// 2D: closed form, R = [[c, -s], [s, c]] with (c, s) along
+// (F00 + F11, F10 - F01).
+//
+// 3D: scaled Newton iteration X <- (z X + (z X)^-T) / 2, z = |det X|^(-1/3)
+// (Higham 1986) in FP32, followed by an FP64 correction of the rotation: with
+// R0 the FP32 iterate, M = R0^T F = e^W S up to the FP32 error W (antisymmetric),
+// and the axial vector w of W solves (tr(S) I - S) w = axial(M - M^T).  The
+// axial vector of M - M^T is a difference of O(1) products that cancels to
+// O(1e-7); it is accumulated in FP64.  R = R0 (I + W + W^2/2).
+// Returns F - R directly (the fixed-corotated stress needs only that), with
+// F - R0 formed in FP32 where its entries cancel exactly (Sterbenz) and the
+// small rotation correction subtracted afterwards.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void f_minus_polar_2d(const float F[4], float out[4]) {
+  float c = F[0] + F[3], s = F[2] - F[1];
+  float inv = rsqrtf(c * c + s * s);
+  c *= inv;
+  s *= inv;
+  out[0] = F[0] - c;
+  out[1] = F[1] + s;
+  out[2] = F[2] - s;
+  out[3] = F[3] - c;
+}
+
+__device__ __forceinline__ void cofactor3(const float X[9], float C[9]) {
+  C[0] = fmaf(X[4], X[8], -X[5] * X[7]);
+  C[1] = fmaf(X[5], X[6], -X[3] * X[8]);
+  C[2] = fmaf(X[3], X[7], -X[4] * X[6]);
+  C[3] = fmaf(X[2], X[7], -X[1] * X[8]);
+  C[4] = fmaf(X[0], X[8], -X[2] * X[6]);
+  C[5] = fmaf(X[1], X[6], -X[0] * X[7]);
+  C[6] = fmaf(X[1], X[5], -X[2] * X[4]);
+  C[7] = fmaf(X[2], X[3], -X[0] * X[5]);
+  C[8] = fmaf(X[0], X[4], -X[1] * X[3]);
+}
+
+template <bool FP64_REFINE>
+__device__ __forceinline__ void f_minus_polar_3d(const float F[9], float out[9]) {
+  float X[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) X[i] = F[i];
+  // scaled Newton in FP32; converges quadratically, 10 iterations bound it
+  for (int it = 0; it < 10; ++it) {
+    float C[9];
+    cofactor3(X, C);
+    float det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    float z = rcbrtf(fabsf(det));
+    float zi = 1.0f / (z * det);
+    float diff = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      float nx = 0.5f * (z * X[i] + zi * C[i]);
+      diff = fmaxf(diff, fabsf(nx - X[i]));
+      X[i] = nx;
+    }
+    if (diff < 2e-7f) break;
+  }
+  // F - R0 (row-major); entries that cancel are exact in FP32
+#pragma unroll
+  for (int i = 0; i < 9; ++i) out[i] = F[i] - X[i];
+  if (FP64_REFINE) {
+    // axial vector of M - M^T with M = R0^T F, accumulated in FP64
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double r0 = X[3 * k + 0], r1 = X[3 * k + 1], r2 = X[3 * k + 2];
+      double f0 = F[3 * k + 0], f1 = F[3 * k + 1], f2 = F[3 * k + 2];
+      a0 = fma(r2, f1, fma(-r1, f2, a0));
+      a1 = fma(r0, f2, fma(-r2, f0, a1));
+      a2 = fma(r1, f0, fma(-r0, f1, a2));
+    }
+    // S ~ sym(R0^T F) is needed only to first order: S = R0^T F in FP32
+    float S[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        S[3 * i + j] = X[i] * F[j] + X[3 + i] * F[3 + j] + X[6 + i] * F[6 + j];
+    float s01 = 0.5f * (S[1] + S[3]), s02 = 0.5f * (S[2] + S[6]), s12 = 0.5f * (S[5] + S[7]);
+    float tr = S[0] + S[4] + S[8];
+    // A = tr(S) I - S (symmetric); w = A^-1 a
+    float A[9] = {tr - S[0], -s01, -s02, -s01, tr - S[4], -s12, -s02, -s12, tr - S[8]};
+    float Ac[9];
+    cofactor3(A, Ac);
+    float detA = A[0] * Ac[0] + A[1] * Ac[1] + A[2] * Ac[2];
+    float ia = 1.0f / detA;
+    float av0 = (float)a0, av1 = (float)a1, av2 = (float)a2;
+    float w0 = (Ac[0] * av0 + Ac[3] * av1 + Ac[6] * av2) * ia;  // A symmetric: A^-1 = cof^T / det
+    float w1 = (Ac[1] * av0 + Ac[4] * av1 + Ac[7] * av2) * ia;
+    float w2 = (Ac[2] * av0 + Ac[5] * av1 + Ac[8] * av2) * ia;
+    // W = hat(w); E = W + W^2 / 2
+    float W[9] = {0.f, -w2, w1, w2, 0.f, -w0, -w1, w0, 0.f};
+    float E[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        E[3 * i + j] = W[3 * i + j] + 0.5f * (W[3 * i] * W[j] + W[3 * i + 1] * W[3 + j] + W[3 * i + 2] * W[6 + j]);
+    // F - R = (F - R0) - R0 E
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        out[3 * i + j] -= X[3 * i] * E[j] + X[3 * i + 1] * E[3 + j] + X[3 * i + 2] * E[6 + j];
+  }
+}
+
+// Kirchhoff stress tau = P F^T.
+//   neo-Hookean:      tau = mu (F F^T - I) + lam ln(J) I
+//   fixed-corotated:  tau = 2 mu (F - R) F^T + lam (J - 1) J I
+// ln J and J - 1 come from det(F) - 1 computed without cancellation.
+template <int D, int MATERIAL, bool FP64_POLAR>
+__device__ __forceinline__ void kirchhoff(const float F[D * D], float mu, float lam, float tau[D * D]) {
+  float jm1 = det_minus_one<D>(F);
+  if (MATERIAL == 0) {
+    float l = lam * log1pf(jm1);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) s = fmaf(F[i * D + k], F[j * D + k], s);
+        tau[i * D + j] = mu * (s - (i == j ? 1.f : 0.f)) + (i == j ? l : 0.f);
+      }
+  } else {
+    float FR[D * D];
+    if (D == 2)
+      f_minus_polar_2d(F, FR);
+    else
+      f_minus_polar_3d<FP64_POLAR>(F, FR);
+    float l = lam * jm1 * (jm1 + 1.0f);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) s = fmaf(FR[i * D + k], F[j * D + k], s);
+        tau[i * D + j] = 2.f * mu * s + (i == j ? l : 0.f);
+      }
+  }
+}
+
+}  // namespace mpmrom

@@ -1,0 +1,80 @@
+"""Python surface of the implicit neural decoder (argument marshalling only).
+
+All computation runs in libmpmrom.so (csrc/decoder.cu): the square hidden
+layers as BF16 tcgen05 GEMMs with FP32 accumulation in tensor memory.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from .mpm import _ptr, _stream
+
+PRIMAL, JVP, SECANT = _abi.DECODER_PRIMAL, _abi.DECODER_JVP, _abi.DECODER_SECANT
+
+
+def dX(k):
+    """Row kind of dg/dX_k."""
+    return 1 + k
+
+
+class Decoder:
+    def __init__(self, d, r, width=128, n_hidden=5, activation=0):
+        L = _abi.lib()
+        self.desc = _abi.DecoderDesc(d, r, width, n_hidden, activation)
+        h = C.c_void_p()
+        _abi.check(L.decoder_create(C.byref(self.desc), C.byref(h)))
+        self._h = h
+        self.d, self.r = d, r
+        self.n_params = int(L.decoder_num_params(h))
+
+    def dxhat(self, j):
+        """Row kind of dg/dxhat_j."""
+        return 1 + self.d + j
+
+    @classmethod
+    def from_params(cls, p):
+        """From a synth.scenes.DecoderParams (FP64 host) -> FP32 device copy."""
+        dec = cls(p.d, p.r, p.width, p.n_hidden, p.activation)
+        dec.set_params(p.flat(), np.concatenate([p.X_min, p.X_range, p.out_shift, p.out_scale]))
+        torch.cuda.synchronize()
+        return dec
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.lib().decoder_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params, norm, stream=None):
+        f = lambda a: np.ascontiguousarray(a, np.float32) if isinstance(a, np.ndarray) else a
+        self._keep = (f(params), f(norm))
+        _abi.check(_abi.lib().decoder_set_params(self._h, _ptr(self._keep[0]), _ptr(self._keep[1]), _stream(stream)))
+
+    def get_params(self, params=None, norm=None, stream=None):
+        _abi.check(_abi.lib().decoder_get_params(self._h, _ptr(params), _ptr(norm), _stream(stream)))
+
+    def eval(self, X, latents, kinds, lat_idx=None, dirs=None, out=None, stream=None):
+        """X (n, d), latents (n_lat, r), lat_idx (n,) int32 | None, dirs (n_lat, r) | None: CUDA tensors.
+        Returns out (R, n, d)."""
+        kinds = [int(k) for k in kinds]
+        n = X.shape[0]
+        if out is None:
+            out = torch.empty((len(kinds), n, self.d), dtype=torch.float32, device=X.device)
+        karr = (C.c_int32 * len(kinds))(*kinds)
+        _abi.check(_abi.lib().decoder_eval(self._h, _ptr(X), _ptr(lat_idx), _ptr(latents), _ptr(dirs), karr,
+                                           len(kinds), n, _ptr(out), _stream(stream)))
+        return out
+
+    def status(self, clear=True, stream=None):
+        w = C.c_uint32()
+        _abi.check(_abi.lib().decoder_status_word(self._h, C.byref(w), int(clear), _stream(stream)))
+        return w.value

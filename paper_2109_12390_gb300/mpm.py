@@ -1,0 +1,128 @@
+"""Python surface of the full-order MPM step (Algorithm 1): argument marshalling only.
+
+All computation runs in libmpmrom.so (csrc/mpm.cu).  Tensors are torch
+tensors (device memory or pinned host memory) or numpy arrays (host memory);
+only their data pointers cross the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        assert a.is_contiguous() and a.dtype in (torch.float32, torch.int32), "contiguous float32/int32 expected"
+        return C.c_void_p(a.data_ptr())
+    assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class MPM:
+    """One context of the C ABI: a batch of MPM instances sharing grid and material law."""
+
+    def __init__(self, *, dim, n_grid, dx, dt, gravity, bc, bc_width, material, transfer, rho, p_vol,
+                 E, nu, inst_offsets):
+        L = _abi.lib()
+        self._E = np.ascontiguousarray(np.atleast_1d(E), np.float32)
+        self._nu = np.ascontiguousarray(np.atleast_1d(nu), np.float32)
+        self._offs = np.ascontiguousarray(inst_offsets, np.int64)
+        g = (C.c_float * 3)(*[float(v) for v in gravity])
+        self.cfg = _abi.MpmConfig(dim, n_grid, dx, dt, g, bc, bc_width, material, transfer, rho, p_vol,
+                                  len(self._E), self._E.ctypes.data_as(C.POINTER(C.c_float)),
+                                  self._nu.ctypes.data_as(C.POINTER(C.c_float)),
+                                  self._offs.ctypes.data_as(C.POINTER(C.c_int64)))
+        h = C.c_void_p()
+        _abi.check(L.mpm_init(C.byref(self.cfg), C.byref(h)))
+        self._h = h
+        self.dim = dim
+        self.n_grid = n_grid
+        self.P = int(self._offs[-1])
+        self.n_inst = len(self._E)
+
+    @classmethod
+    def from_scene(cls, sc):
+        """Context for a synth.scenes.Scene (configuration only)."""
+        return cls(dim=sc.dim, n_grid=sc.n_grid, dx=sc.dx, dt=sc.dt, gravity=sc.gravity, bc=sc.bc,
+                   bc_width=sc.bc_width, material=sc.material, transfer=sc.transfer, rho=sc.rho,
+                   p_vol=sc.p_vol, E=sc.E, nu=sc.nu, inst_offsets=sc.inst_offsets)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.lib().mpm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, x, v, F, C_=None, stream=None):
+        _abi.check(_abi.lib().mpm_set_state(self._h, _ptr(x), _ptr(v), _ptr(F), _ptr(C_), _stream(stream)))
+
+    def get_state(self, x=None, v=None, F=None, C_=None, stream=None):
+        _abi.check(_abi.lib().mpm_get_state(self._h, _ptr(x), _ptr(v), _ptr(F), _ptr(C_), _stream(stream)))
+
+    def step(self, n_steps=1, stream=None):
+        _abi.check(_abi.lib().mpm_step(self._h, int(n_steps), _stream(stream)))
+
+    def step_profiled(self, n_steps=1, stream=None):
+        """Steps with per-kernel CUDA events; returns (n_steps, 3) ms [fused, scan, permute]."""
+        out = (C.c_float * (3 * n_steps))()
+        _abi.check(_abi.lib().mpm_step_profiled(self._h, int(n_steps), out, _stream(stream)))
+        return np.frombuffer(out, np.float32).reshape(n_steps, 3).copy()
+
+    def status(self, clear=True, stream=None):
+        w = C.c_uint32()
+        _abi.check(_abi.lib().mpm_status_word(self._h, C.byref(w), int(clear), _stream(stream)))
+        return w.value
+
+    def num_block_keys(self):
+        return int(_abi.lib().mpm_num_block_keys(self._h))
+
+    def debug_bins(self, stream=None):
+        ck = np.empty(self.P, np.int32)
+        bk = np.empty(self.P, np.int32)
+        off = np.empty(self.num_block_keys() + 1, np.int32)
+        _abi.check(_abi.lib().mpm_debug_bins(self._h, _ptr(ck), _ptr(bk), _ptr(off), _stream(stream)))
+        return ck, bk, off
+
+    def debug_grid(self, stream=None):
+        N = self.n_inst * self.n_grid ** self.dim
+        m = np.empty(N, np.float32)
+        p = np.empty((N, self.dim), np.float32)
+        v = np.empty((N, self.dim), np.float32)
+        _abi.check(_abi.lib().mpm_debug_grid(self._h, _ptr(m), _ptr(p), _ptr(v), _stream(stream)))
+        shp = (self.n_inst,) + (self.n_grid,) * self.dim
+        return m.reshape(shp), p.reshape(shp + (self.dim,)), v.reshape(shp + (self.dim,))
+
+    # convenience for tests and benchmarks -------------------------------------------------
+    def load_numpy(self, x, v, F, C_=None):
+        """Loads float64/float32 numpy state (copied to float32 host arrays)."""
+        f = lambda a: None if a is None else np.ascontiguousarray(a, np.float32)
+        self._host = [f(x), f(v), f(F), f(C_)]
+        self.set_state(*self._host)
+        torch.cuda.synchronize()
+
+    def read_numpy(self):
+        d = self.dim
+        x = np.empty((self.P, d), np.float32)
+        v = np.empty((self.P, d), np.float32)
+        F = np.empty((self.P, d, d), np.float32)
+        Cm = np.empty((self.P, d, d), np.float32)
+        self.get_state(x, v, F, Cm)
+        torch.cuda.synchronize()
+        return x, v, F, Cm

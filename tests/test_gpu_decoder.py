@@ -1,0 +1,147 @@
+"""GPU parity of the decoder g(X; xhat) and its Jacobians (BF16 tensor cores) against the FP64 oracle.
+
+Tolerance: 2e-2 relative, norm-wise per quantity, for the BF16 square layers
+(FP32 accumulation); the network output is compared without the output shift
+(out_shift would otherwise hide errors of the learned part).  FP32-only paths
+(linear decoder, one hidden layer) are held to 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle.decoder as OD
+import synth.scenes as S
+
+pytestmark = pytest.mark.gpu
+TOL_BF16 = 2e-2
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _dec_params(d, r, n_hidden=5, act=OD.ELU, seed=0):
+    lo = np.full(d, 0.3)
+    return S.xavier_decoder(seed, d, r, 128, n_hidden, act, X_min=lo, X_range=np.full(d, 0.3),
+                            out_shift=np.full(d, 0.5), out_scale=np.full(d, 0.1), bias_scale=0.2)
+
+
+def _points(n, d, r, n_lat=1, seed=1):
+    rng = np.random.default_rng(seed)
+    X = 0.3 + 0.3 * rng.uniform(size=(n, d))
+    lat = rng.normal(scale=0.7, size=(n_lat, r))
+    idx = rng.integers(0, n_lat, size=n).astype(np.int32)
+    return X, lat, idx
+
+
+def _gpu(*arrays):
+    import torch
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrays]
+
+
+@pytest.mark.parametrize("d,r,n", [(2, 16, 1000), (3, 16, 777), (2, 8, 1), (3, 32, 300)])
+def test_forward_and_jacobians(d, r, n):
+    import torch
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
+    p = _dec_params(d, r)
+    dec = Decoder.from_params(p)
+    X, lat, idx = _points(n, d, r, n_lat=3)
+    Xg, latg, idxg = _gpu(X.astype(np.float32), lat.astype(np.float32), idx)
+    kinds = [PRIMAL] + [1 + k for k in range(d)] + [dec.dxhat(j) for j in range(r)]
+    out = dec.eval(Xg, latg, kinds, lat_idx=idxg).cpu().numpy()
+    torch.cuda.synchronize()
+    assert dec.status() == 0
+    Xr = X.astype(np.float32).astype(np.float64)
+    xh = lat.astype(np.float32).astype(np.float64)[idx]
+    g, JX, Jq = OD.jacobians(p, Xr, xh)
+    assert rel(out[0] - 0.5, g - 0.5) < TOL_BF16
+    assert rel(np.stack(out[1:1 + d], -1), JX) < TOL_BF16
+    assert rel(np.stack(out[1 + d:], -1), Jq) < TOL_BF16
+
+
+def test_jvp_and_secant_rows():
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL, JVP, SECANT
+    d, r, n = 2, 16, 2000
+    p = _dec_params(d, r, seed=3)
+    dec = Decoder.from_params(p)
+    X, lat, idx = _points(n, d, r, n_lat=4, seed=4)
+    rng = np.random.default_rng(5)
+    u = rng.normal(size=lat.shape)
+    Xg, latg, idxg, ug = _gpu(X.astype(np.float32), lat.astype(np.float32), idx, u.astype(np.float32))
+    out = dec.eval(Xg, latg, [PRIMAL, JVP], lat_idx=idxg, dirs=ug).cpu().numpy()
+    Xr = X.astype(np.float32).astype(np.float64)
+    xh = lat.astype(np.float32).astype(np.float64)[idx]
+    uu = u.astype(np.float32).astype(np.float64)[idx]
+    _, jv = OD.jvp_latent(p, Xr, xh, uu)
+    assert rel(out[1], jv) < TOL_BF16
+    # secant rows resolve latent increments far below BF16 resolution
+    for scale in (1e-2, 1e-4, 1e-6):
+        delta = (scale * u).astype(np.float32)
+        (dg,) = _gpu(delta)
+        sec = dec.eval(Xg, latg, [PRIMAL, SECANT], lat_idx=idxg, dirs=dg).cpu().numpy()[1]
+        ref = OD.decode(p, Xr, xh + delta.astype(np.float64)[idx]) - OD.decode(p, Xr, xh)
+        assert rel(sec, ref) < TOL_BF16, scale
+
+
+def test_linear_and_single_hidden_layer_fp32():
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
+    for n_hidden, act in [(0, OD.IDENTITY), (1, OD.ELU)]:
+        d, r, n = 3, 6, 513
+        p = _dec_params(d, r, n_hidden=n_hidden, act=act, seed=7)
+        dec = Decoder.from_params(p)
+        X, lat, idx = _points(n, d, r, n_lat=2, seed=8)
+        Xg, latg, idxg = _gpu(X.astype(np.float32), lat.astype(np.float32), idx)
+        kinds = [PRIMAL] + [1 + k for k in range(d)] + [dec.dxhat(j) for j in range(r)]
+        out = dec.eval(Xg, latg, kinds, lat_idx=idxg).cpu().numpy()
+        g, JX, Jq = OD.jacobians(p, X.astype(np.float32).astype(np.float64),
+                                 lat.astype(np.float32).astype(np.float64)[idx])
+        assert rel(out[0] - 0.5, g - 0.5) < 1e-5
+        assert rel(np.stack(out[1:1 + d], -1), JX) < 1e-5
+        assert rel(np.stack(out[1 + d:], -1), Jq) < 1e-5
+
+
+def test_identity_activation_tensor_path_is_weight_product():
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
+    d, r, n = 2, 4, 130
+    p = _dec_params(d, r, n_hidden=3, act=OD.IDENTITY, seed=9)
+    dec = Decoder.from_params(p)
+    X, lat, idx = _points(n, d, r, seed=10)
+    Xg, latg = _gpu(X.astype(np.float32), lat.astype(np.float32))
+    out = dec.eval(Xg, latg, [PRIMAL] + [dec.dxhat(j) for j in range(r)]).cpu().numpy()
+    prod = p.W[3] @ p.W[2] @ p.W[1] @ p.W[0]
+    Jq = np.stack(out[1:], -1)
+    np.testing.assert_allclose(Jq, np.broadcast_to(0.1 * prod[:, d:], Jq.shape), rtol=3e-2, atol=3e-3)
+
+
+def test_reconstruction_size_sampled():
+    """1,048,576 points (4096 latents x 256 points) forward; sampled points against the oracle."""
+    import torch
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
+    d, r, n = 2, 16, 1 << 20
+    p = _dec_params(d, r, seed=11)
+    dec = Decoder.from_params(p)
+    X, lat, idx = _points(n, d, r, n_lat=4096, seed=12)
+    Xg, latg, idxg = _gpu(X.astype(np.float32), lat.astype(np.float32), idx)
+    out = dec.eval(Xg, latg, [PRIMAL], lat_idx=idxg)
+    torch.cuda.synchronize()
+    assert dec.status() == 0
+    rng = np.random.default_rng(13)
+    sel = np.concatenate([rng.choice(n, 2000, replace=False), [0, n - 1]])
+    g = OD.decode(p, X[sel].astype(np.float32).astype(np.float64),
+                  lat.astype(np.float32).astype(np.float64)[idx[sel]])
+    assert rel(out[0].cpu().numpy()[sel] - 0.5, g - 0.5) < TOL_BF16
+
+
+def test_empty_and_bad_arguments():
+    import torch
+    from paper_2109_12390_gb300 import _abi
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
+    p = _dec_params(2, 4)
+    dec = Decoder.from_params(p)
+    X = torch.zeros((0, 2), device="cuda")
+    lat = torch.zeros((1, 4), device="cuda")
+    out = dec.eval(X, lat, [PRIMAL])
+    assert out.shape == (1, 0, 2)
+    with pytest.raises(_abi.MpmError):
+        dec.eval(torch.zeros((3, 2), device="cuda"), lat, [5, PRIMAL])   # primal must come first
+    with pytest.raises(_abi.MpmError):
+        dec.eval(torch.zeros((3, 2), device="cuda"), lat, [PRIMAL, 999])

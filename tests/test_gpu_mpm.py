@@ -1,0 +1,234 @@
+"""GPU parity of the full-order MPM step (Algorithm 1) against the FP64 oracle, through the C ABI.
+
+Tolerance: 1e-5 relative, norm-wise per quantity (|a - b|_2 / |b|_2) for the
+FP32 kernels against the FP64 oracle; cell keys, block counts and block
+offsets bit-exact (the oracle bins the GPU's own FP32 positions).
+"""
+import numpy as np
+import pytest
+
+import oracle.mpm as OM
+import synth.scenes as S
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+# C = (4 / dx^2) sum_i N_i v_i (x_i - x_p)^T amplifies the FP32 rounding of the
+# grid velocities by the inverse of its own (small) magnitude; it is held to 1e-4
+TOL_C = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _ctx(sc):
+    from paper_2109_12390_gb300.mpm import MPM
+    ctx = MPM.from_scene(sc)
+    ctx.load_numpy(sc.x, sc.v, sc.F, sc.C)
+    return ctx
+
+
+def _compare(ctx, ref, tol=TOL):
+    x, v, F, Cm = ctx.read_numpy()
+    errs = dict(x=rel(x, ref.x), v=rel(v, ref.v), F=rel(F, ref.F))
+    # C is a velocity gradient: measure it against max(|C|, |v| / dx) so that
+    # round-off-level C (rigid motion) is not divided by round-off
+    scale = max(np.linalg.norm(ref.C), np.linalg.norm(ref.v) / ref.dx)
+    errs["C"] = float(np.linalg.norm(Cm - ref.C) / scale)
+    assert all(errs[k] < tol for k in ("x", "v", "F")) and errs["C"] < TOL_C, errs
+    return errs
+
+
+def test_config1_block_200_steps():
+    """2D neo-Hookean block, 4096 particles, 128^2, dt = 1e-4, 200 steps (free flight)."""
+    sc = S.block_2d()
+    ctx = _ctx(sc)
+    ctx.step(200)
+    assert ctx.status() == 0
+    ref = sc.copy()
+    OM.step(ref, 200)
+    _compare(ctx, ref)
+
+
+@pytest.mark.parametrize("material", [OM.NEO_HOOKEAN, OM.FIXED_COROTATED])
+def test_2d_stressed_block_impact(material):
+    """2D MLS block with a random initial deformation, dropped onto the sticky floor (dt = 5e-5)."""
+    sc = S.block_2d(side=32, dt=5e-5, origin=(0.4, 0.03), v0=np.array([0.3, -0.8]))
+    sc.material = material
+    rng = np.random.default_rng(1)
+    sc.F = S.random_deformation(rng, sc.n_particles, 2, 0.03)
+    ctx = _ctx(sc)
+    ctx.step(150)
+    assert ctx.status() == 0
+    ref = sc.copy()
+    OM.step(ref, 150)
+    assert ref.x[:, 1].min() < 4.5 / 128  # the block reached the floor band
+    _compare(ctx, ref)
+
+
+@pytest.mark.parametrize("material", [OM.NEO_HOOKEAN, OM.FIXED_COROTATED])
+def test_2d_pic_impact_from_rest_shape(material):
+    """Literal PIC transfers of Algorithm 1 (exact basis gradients) through an impact, from F = I.
+
+    PIC from a rough random F is ill-conditioned (the FP64 oracle itself moves
+    v and F by ~5e-5 for a 1e-7 input perturbation), so the PIC case starts
+    from a stress-free shape and builds its stress in the impact."""
+    sc = S.block_2d(side=32, dt=5e-5, origin=(0.4, 0.03), v0=np.array([0.3, -0.8]))
+    sc.transfer, sc.material = OM.PIC, material
+    ctx = _ctx(sc)
+    ctx.step(150)
+    assert ctx.status() == 0
+    ref = sc.copy()
+    OM.step(ref, 150)
+    assert ref.x[:, 1].min() < 4.5 / 128
+    assert np.abs(ref.F - np.eye(2)).max() > 1e-3   # stress did build up
+    _compare(ctx, ref)
+
+
+def test_3d_fixed_corotated_cube_slip_floor():
+    """3D MLS fixed-corotated jittered cube (16^3), FP64-refined polar, slip floor impact."""
+    sc = S.cube_3d(side=16, bottom=0.03)
+    rng = np.random.default_rng(2)
+    sc.F = S.random_deformation(rng, sc.n_particles, 3, 0.02)
+    ctx = _ctx(sc)
+    ctx.step(80)
+    assert ctx.status() == 0
+    ref = sc.copy()
+    OM.step(ref, 80)
+    assert ref.x[:, 1].min() < 3.5 / 128
+    _compare(ctx, ref)
+
+
+def test_3d_pic_homogeneous_deformation():
+    """Literal PIC transfers in 3D (exact basis gradients) on a cube released from a homogeneous
+    deformation.  (Through an impact at this dt the FP64 oracle itself diverges under PIC, so the
+    impact case is covered by MLS only.)"""
+    sc = S.cube_3d(side=12, bottom=0.3, dt=2.5e-5)
+    sc.transfer = OM.PIC
+    A = np.random.default_rng(1).uniform(-1, 1, (3, 3))
+    sc.F[:] = np.eye(3) + 0.02 * A
+    ctx = _ctx(sc)
+    ctx.step(60)
+    assert ctx.status() == 0
+    ref = sc.copy()
+    OM.step(ref, 60)
+    _compare(ctx, ref)
+
+
+def test_batched_uneven_instances():
+    """Several instances with uneven particle counts (one empty) in one context."""
+    sc = S.batch_2d(seed=3, n_inst=4, count_range=(500, 3000), origin_y=0.03)
+    sc = sc.subset_instances([0, 1, 2, 3])
+    # make instance 2 empty
+    sizes = np.diff(sc.inst_offsets)
+    keep = np.ones(sc.n_particles, bool)
+    keep[sc.inst_offsets[2]:sc.inst_offsets[3]] = False
+    sizes[2] = 0
+    sc.x, sc.v, sc.F, sc.C = sc.x[keep], sc.v[keep], sc.F[keep], sc.C[keep]
+    sc.inst_offsets = np.concatenate([[0], np.cumsum(sizes)])
+    rng = np.random.default_rng(4)
+    for k in range(sc.n_inst):   # one homogeneous initial deformation per instance
+        s = slice(sc.inst_offsets[k], sc.inst_offsets[k + 1])
+        sc.F[s] = np.eye(2) + 0.01 * rng.uniform(-1, 1, (2, 2))
+    ctx = _ctx(sc)
+    ctx.step(60)
+    assert ctx.status() == 0
+    ref = sc.copy()
+    OM.step(ref, 60)
+    _compare(ctx, ref)
+
+
+def test_cell_keys_and_block_offsets_bit_exact():
+    sc = S.cube_3d(side=12, bottom=0.2)
+    rng = np.random.default_rng(5)
+    sc.v = rng.uniform(-1, 1, size=sc.v.shape)
+    ctx = _ctx(sc)
+    ctx.step(7)
+    x, _, _, _ = ctx.read_numpy()
+    ck, bk, off = ctx.debug_bins()
+    ref_ck = OM.cell_keys(x.astype(np.float64), sc.dx, sc.n_grid)
+    np.testing.assert_array_equal(ck, ref_ck)
+    n, B = sc.n_grid, 4
+    base = OM.stencil_base(x.astype(np.float64), sc.dx)
+    ref_bk = ((base[:, 0] // B) * (n // B) + base[:, 1] // B) * (n // B) + base[:, 2] // B
+    np.testing.assert_array_equal(bk, ref_bk)
+    _, ref_off = OM.bin_sort(ref_bk, (n // B) ** 3)
+    np.testing.assert_array_equal(off, ref_off)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_grid_transfer_and_update(dim):
+    """Algorithm 1 steps 1-2: grid mass, momentum(+dt f) and updated velocity of a stressed state."""
+    if dim == 2:
+        sc = S.block_2d(side=24, dt=5e-5, origin=(0.45, 0.01))
+    else:
+        sc = S.cube_3d(side=10, bottom=0.01)
+    rng = np.random.default_rng(6)
+    sc.F = S.random_deformation(rng, sc.n_particles, dim, 0.05)
+    sc.C = rng.uniform(-3, 3, size=sc.C.shape)
+    ctx = _ctx(sc)
+    m, p, v = ctx.debug_grid()
+    mu, lam = OM.lame(sc.E[0], sc.nu[0])
+    rm, rp = OM.p2g(sc.x.astype(np.float32).astype(np.float64), sc.v.astype(np.float32).astype(np.float64),
+                    sc.F.astype(np.float32).astype(np.float64), sc.C.astype(np.float32).astype(np.float64),
+                    sc.p_mass, sc.p_vol, mu, lam, dx=sc.dx, dt=sc.dt, n_grid=sc.n_grid,
+                    material=sc.material, transfer=sc.transfer)
+    rv = OM.grid_update(rm, rp, dt=sc.dt, gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width)
+    assert rel(m[0], rm) < TOL
+    assert rel(p[0], rp) < TOL
+    assert rel(v[0], rv) < TOL
+    # walls: the floor band holds wall nodes that received mass
+    assert (rm[(slice(None), slice(0, 3))] > 0).any()
+
+
+def test_single_particle():
+    sc = S.block_2d(side=1)
+    sc.v[:] = (0.5, 0.2)
+    ctx = _ctx(sc)
+    ctx.step(30)
+    ref = sc.copy()
+    OM.step(ref, 30)
+    _compare(ctx, ref)
+
+
+def test_out_of_grid_is_reported_not_written():
+    sc = S.block_2d(side=4)
+    sc.x[0] = (0.001, 0.5)  # stencil leaves the grid on the low side
+    ctx = _ctx(sc)
+    from paper_2109_12390_gb300 import _abi
+    word = ctx.status()
+    assert "OUT_OF_GRID" in _abi.status_names(word)
+    ctx.step(2)
+    x, _, _, _ = ctx.read_numpy()
+    assert np.isfinite(x).all()
+
+
+@pytest.mark.parametrize("n_sample", [64])
+def test_config2_full_size_sampled(n_sample):
+    """262,144-particle cube, 128^3: after 5 GPU steps, the next step of sampled particles
+    against the oracle evaluated on their neighbourhood only (exact locality of the stencils),
+    plus global mass conservation of the grid."""
+    import oracle.rom as OR
+    sc = S.cube_3d()
+    ctx = _ctx(sc)
+    ctx.step(5)
+    x0, v0, F0, C0 = [a.astype(np.float64) for a in ctx.read_numpy()]
+    m, _, _ = ctx.debug_grid()
+    assert float(m.sum(dtype=np.float64)) == pytest.approx(sc.n_particles * sc.p_mass, rel=1e-5)
+    ctx.step(1)
+    x1, v1, F1, C1 = ctx.read_numpy()
+    rng = np.random.default_rng(7)
+    samples = np.sort(rng.choice(sc.n_particles, n_sample, replace=False))
+    basis, neigh = OR.neighbourhood(x0, samples, sc.dx, sc.n_grid)
+    quad = np.concatenate([samples, neigh])
+    mu, lam = OM.lame(sc.E[0], sc.nu[0])
+    rm, rp = OM.p2g(x0[quad], v0[quad], F0[quad], C0[quad], sc.p_mass, sc.p_vol, mu, lam, dx=sc.dx, dt=sc.dt,
+                    n_grid=sc.n_grid, material=sc.material, transfer=sc.transfer)
+    rv = OM.grid_update(rm, rp, dt=sc.dt, gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width)
+    xs, vs, Fs, Cs = OM.g2p(x0[samples], F0[samples], rv, dx=sc.dx, dt=sc.dt, transfer=sc.transfer)
+    assert rel(x1[samples], xs) < TOL
+    assert rel(v1[samples], vs) < TOL
+    assert rel(F1[samples], Fs) < TOL
+    # near-rigid motion: C is at the FP32 rounding level of the grid velocities, measure it on |v|/dx
+    scale = max(np.linalg.norm(Cs), np.linalg.norm(vs) / sc.dx)
+    assert np.linalg.norm(C1[samples] - Cs) / scale < TOL_C
