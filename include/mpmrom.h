@@ -262,6 +262,195 @@ mpm_status decoder_eval(const mpm_decoder* dec, const float* X, const int32_t* l
 /* Synchronises `stream`; OR of MPM_STATUS_* bits raised by decoder kernels. */
 mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void* stream);
 
+/* ======================================================================
+ * Reduced-order step (Algorithm 2 with Lagrangian quadrature: Algorithms 3,
+ * 5 and 6 or 7) and the accumulated position error (Section 5)
+ * ====================================================================== */
+
+/*
+ * Configuration of one reduced-order instance.  Grid, time step, walls,
+ * material and transfer as in mpm_config (single instance: E, nu scalars).
+ *   latent_dim   r, 1..32.
+ *   n_samples    |P|, sample material points re-drawn every step (Sec. 3.2.1)
+ *                as the n_samples particles with the smallest 64-bit hash
+ *                h = out(out(out(seed, instance), step), particle), out(s, k)
+ *                the (k+1)-th output of SplitMix64 seeded with s; ties by id.
+ *   gn_iters     Gauss-Newton iterations of the position projection (Alg. 6);
+ *                Armijo c = 1e-4 with up to 10 step halvings, evaluated as 11
+ *                trial steps at once (the same choice as sequential
+ *                backtracking).
+ *   projection   0 = position-velocity projection (Alg. 6),
+ *                1 = velocity-only projection (Alg. 7).
+ */
+typedef struct rom_config {
+  int32_t dim;
+  int32_t n_grid;
+  float dx;
+  float dt;
+  float gravity[3];
+  int32_t bc;
+  int32_t bc_width;
+  int32_t material;
+  int32_t transfer;
+  float rho;
+  float p_vol;
+  float E;
+  float nu;
+  int32_t latent_dim;
+  int32_t n_samples;
+  uint64_t seed;
+  int32_t instance;
+  int32_t gn_iters;
+  int32_t projection;
+} rom_config;
+
+typedef struct rom_ctx rom_ctx;
+
+/*
+ * Creates a reduced-order context over n_particles material points with
+ * reference positions X (n_particles, dim) (host or device; copied).  The
+ * decoder must outlive the context and its latent dimension must equal
+ * cfg->latent_dim.  Synchronous.
+ */
+mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float* X, int64_t n_particles,
+                      rom_ctx** out);
+void rom_destroy(rom_ctx* ctx);
+
+/* Sets xhat_n, vhat_n, xhat_{n-1} (r doubles each, host or device) and the step index. Synchronous. */
+mpm_status rom_set_state(rom_ctx* ctx, const double* xhat, const double* vhat, const double* xhat_prev,
+                         int64_t step, void* stream);
+/* Reads them back (any pointer may be NULL).  Synchronous. */
+mpm_status rom_get_state(rom_ctx* ctx, double* xhat, double* vhat, double* xhat_prev, int64_t* step, void* stream);
+
+/*
+ * Initial condition by least squares (Eq. essentialSpecInt): xhat_0 by
+ * `iters` Gauss-Newton iterations of min sum_p |g(X^p; xhat) - target_p|^2
+ * from xhat = 0 over all particles, vhat_0 = argmin sum_p |(dg/dxhat) vhat - V0_p|^2;
+ * sets the state (xhat_{-1} = xhat_0 - dt vhat_0, step 0).  target and V0
+ * are (n_particles, dim), host or device.  Synchronous.
+ */
+mpm_status rom_fit_initial(rom_ctx* ctx, const float* target, const float* V0, int iters, void* stream);
+
+/*
+ * Advances the reduced state by n_steps steps of Algorithm 2: decoder at all
+ * particles, sample / basis / neighbour sets (Alg. 3), dg/dX and the velocity
+ * at the quadrature points, local particle-to-grid / grid update /
+ * grid-to-particle to the samples (Alg. 5), velocity least squares and the
+ * Gauss-Newton position projection (Alg. 6) or the velocity-only projection
+ * (Alg. 7).  All on the device: one captured CUDA graph per step, launched on
+ * `stream`.  Solver failures raise MPM_STATUS_* bits (rom_status_word).
+ */
+mpm_status rom_step(rom_ctx* ctx, int n_steps, void* stream);
+
+mpm_status rom_status_word(rom_ctx* ctx, uint32_t* out, int clear, void* stream);
+
+/*
+ * Diagnostics of the last step (any pointer may be NULL; synchronous):
+ * qlist (n_particles int32): samples ascending then neighbours ascending;
+ * counts (3 int32): |P|, |P| + |N|, basis-node list length; x_all
+ * (n_particles, dim): decoded positions g(X; xhat_n) the step used;
+ * v_trial, x_trial (|P|, dim): Algorithm 5 outputs of the samples.
+ */
+mpm_status rom_debug(rom_ctx* ctx, int32_t* qlist, int32_t* counts, float* x_all, float* v_trial,
+                     float* x_trial, void* stream);
+
+/* g(X^p; xhat_n) for every particle into device array x_out (n_particles, dim). */
+mpm_status rom_decode_all(rom_ctx* ctx, float* x_out, void* stream);
+
+/*
+ * Accumulated position error of Section 5: acc[0] += sum_i (a_i - b_i)^2,
+ * acc[1] += sum_i b_i^2 over n floats (device pointers; acc is 2 doubles on
+ * the device).  The error in percent is 100 sqrt(acc[0] / acc[1]).
+ */
+mpm_status metric_accumulate(const float* a, const float* b, int64_t n, double* acc, void* stream);
+
+/* ======================================================================
+ * Decoder training (loss of Section 4.2, optimiser and scaling of
+ * Appendix B) on snapshots of the full-order model, with the latent table
+ * the remark of Section 4.1 allows in place of the encoder
+ * ====================================================================== */
+
+/*
+ * Snapshot store.  Instance k has particles inst_offsets[k] .. inst_offsets[k+1]-1
+ * of X (reference positions).  Snapshot s belongs to instance snap_inst[s];
+ * its successor in time is snap_next[s] (-1 if none); its particle rows are
+ * stored consecutively in x, v (dim floats each) and F (dim*dim floats,
+ * row-major), snapshots back to back in index order.  Host or device pointers
+ * (copied by trainer_create).
+ */
+typedef struct snapshot_desc {
+  int32_t dim;
+  int32_t n_inst;
+  const int64_t* inst_offsets;  /* host, n_inst + 1 */
+  const float* X;
+  int32_t n_snap;
+  const int32_t* snap_inst;     /* host, n_snap */
+  const int32_t* snap_next;     /* host, n_snap */
+  const float* x;
+  const float* v;
+  const float* F;
+} snapshot_desc;
+
+/*
+ *   lambda_F, lambda_v  penalty weights of the deformation-gradient and
+ *                       velocity terms of the loss.
+ *   dt_snap             time between a snapshot and its successor (the
+ *                       latent finite difference (xhat_{n+1} - xhat_n) / dt_snap).
+ *   lr0, lr1            Adam learning rate, decaying geometrically from lr0
+ *                       to lr1 over total_steps (Appendix B: 1e-3 -> 1e-6).
+ *   batch               (snapshot, particle) pairs per step, drawn uniformly
+ *                       over all pairs by a counter-based SplitMix64 hash of
+ *                       (seed, step, i).
+ */
+typedef struct train_config {
+  float lambda_F;
+  float lambda_v;
+  float dt_snap;
+  float lr0;
+  float lr1;
+  int32_t batch;
+  int64_t total_steps;
+  uint64_t seed;
+} train_config;
+
+typedef struct trainer_ctx trainer_ctx;
+
+/*
+ * Creates a trainer for `dec` (which must have >= 2 hidden layers; its
+ * parameters are updated in place by decoder_train).  latents0: (n_snap, r)
+ * initial latent table or NULL (zeros).  Synchronous.
+ */
+mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snapshot_desc* snaps,
+                          const float* latents0, trainer_ctx** out);
+void trainer_destroy(trainer_ctx* ctx);
+
+/*
+ * n_steps optimisation steps: minibatch draw, forward with the tangent rows
+ * (dg/dX for the lambda_F term, the latent JVP for the lambda_v term) on the
+ * tensor cores, hand-written backward through the tangents (including the
+ * second-derivative terms of the activation), tensor-core weight-gradient
+ * GEMMs, latent-table gradients and Adam.  One captured graph per step.
+ */
+mpm_status decoder_train(trainer_ctx* ctx, int n_steps, void* stream);
+
+/* Loss of the last step (mean over the batch) and the step count.  Synchronous. */
+mpm_status trainer_loss(trainer_ctx* ctx, double* loss, int64_t* step, void* stream);
+
+/* Copies the latent table (n_snap, r) out (host or device pointer). */
+mpm_status trainer_get_latents(trainer_ctx* ctx, float* latents, void* stream);
+
+mpm_status trainer_status_word(trainer_ctx* ctx, uint32_t* out, int clear, void* stream);
+
+/*
+ * Gradient check: one forward/backward on the minibatch of the current step
+ * without updating.  Returns the parameter gradients (decoder_num_params
+ * floats, same layout as decoder_set_params), the latent-table gradients
+ * (n_snap, r), the batch (snapshot index and particle index within its
+ * instance, batch int32 each) and the loss.  Any output may be NULL.  Synchronous.
+ */
+mpm_status trainer_gradients(trainer_ctx* ctx, float* g_params, float* g_latents, int32_t* batch_snap,
+                             int32_t* batch_part, double* loss, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,6 +37,27 @@ class DecoderDesc(C.Structure):
 DECODER_PRIMAL, DECODER_JVP, DECODER_SECANT = 0, 1000, 1001
 
 
+class RomConfig(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("n_grid", C.c_int32), ("dx", C.c_float), ("dt", C.c_float),
+        ("gravity", C.c_float * 3), ("bc", C.c_int32), ("bc_width", C.c_int32),
+        ("material", C.c_int32), ("transfer", C.c_int32), ("rho", C.c_float), ("p_vol", C.c_float),
+        ("E", C.c_float), ("nu", C.c_float), ("latent_dim", C.c_int32), ("n_samples", C.c_int32),
+        ("seed", C.c_uint64), ("instance", C.c_int32), ("gn_iters", C.c_int32), ("projection", C.c_int32),
+    ]
+
+
+class SnapshotDesc(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_inst", C.c_int32), ("inst_offsets", C.c_void_p), ("X", C.c_void_p),
+                ("n_snap", C.c_int32), ("snap_inst", C.c_void_p), ("snap_next", C.c_void_p),
+                ("x", C.c_void_p), ("v", C.c_void_p), ("F", C.c_void_p)]
+
+
+class TrainConfig(C.Structure):
+    _fields_ = [("lambda_F", C.c_float), ("lambda_v", C.c_float), ("dt_snap", C.c_float), ("lr0", C.c_float),
+                ("lr1", C.c_float), ("batch", C.c_int32), ("total_steps", C.c_int64), ("seed", C.c_uint64)]
+
+
 class MpmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"mpmrom status {status}: {msg}")
@@ -66,6 +87,24 @@ SIGNATURES = [
     ("decoder_eval", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.POINTER(C.c_int32), C.c_int, C.c_int64, C.c_void_p, C.c_void_p]),
     ("decoder_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
+    ("rom_create", C.c_int, [C.POINTER(RomConfig), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
+    ("rom_destroy", None, [C.c_void_p]),
+    ("rom_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    ("rom_get_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rom_fit_initial", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("rom_step", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    ("rom_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
+    ("rom_debug", C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),
+    ("rom_decode_all", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("metric_accumulate", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    ("trainer_create", C.c_int, [C.c_void_p, C.POINTER(TrainConfig), C.POINTER(SnapshotDesc), C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    ("trainer_destroy", None, [C.c_void_p]),
+    ("decoder_train", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    ("trainer_loss", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_void_p]),
+    ("trainer_get_latents", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("trainer_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
+    ("trainer_gradients", C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.POINTER(C.c_double), C.c_void_p]),
 ]
 
 

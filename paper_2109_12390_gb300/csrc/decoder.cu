@@ -36,107 +36,20 @@
 #include "common.cuh"
 #include "tc.cuh"
 
+#include "decoder_common.cuh"
+
 namespace mpmrom {
-
-constexpr int kW = 128;          // hidden width of the tensor-core layers
-constexpr int kMaxTC = 4;        // square layers resident in shared memory
-constexpr int kMaxR = 64;        // row kinds per point
-constexpr int kLayerBytes = kW * kW * 2;
-
-struct DecArgs {
-  int d, r, n_tc, act;
-  const float* W0;    // (W, d + r)
-  const float* b0;    // (W)
-  const float* bh;    // (n_tc, W)
-  const float* Wout;  // (d, W)
-  const float* bout;  // (d)
-  const float* norm;  // X_min[d], X_range[d], out_shift[d], out_scale[d]
-  const uint8_t* wimg;
-  const float* X;
-  const int32_t* lat;
-  const float* latents;
-  const float* dirs;
-  int64_t n;
-  int R, Pt;
-  int kinds[kMaxR];
-  float* out;         // (R, n, d)
-  uint32_t* status;
-  // linear decoder (no hidden layer): y = W0 [Xn, xhat] + b0 with W0 (d, d + r)
-  int linear;
-};
-
-__device__ __forceinline__ float elu(float z) { return z > 0.f ? z : expm1f(z); }
-__device__ __forceinline__ float elu_d1(float z) { return z > 0.f ? 1.f : __expf(z); }
-// act(z + dz) - act(z) without cancellation on the negative branch
-__device__ __forceinline__ float elu_secant(float z, float dz) {
-  float z1 = z + dz;
-  if (z > 0.f && z1 > 0.f) return dz;
-  if (z <= 0.f && z1 <= 0.f) return __expf(z) * expm1f(dz);
-  return elu(z1) - elu(z);
-}
-
-__device__ __forceinline__ float act_f(int act, float z) { return act == 0 ? elu(z) : z; }
-__device__ __forceinline__ float act_d1(int act, float z) { return act == 0 ? elu_d1(z) : 1.f; }
-__device__ __forceinline__ float act_sec(int act, float z, float dz) { return act == 0 ? elu_secant(z, dz) : dz; }
-
-// row-kind codes (see decoder_eval in include/mpmrom.h)
-constexpr int KIND_PRIMAL = 0;
-constexpr int KIND_JVP = 1000;
-constexpr int KIND_SECANT = 1001;
-
-struct RowInfo {
-  int kind;      // code
-  int cls;       // 0 primal, 1 tangent, 2 secant, -1 padding
-  int q;         // point within tile
-  int64_t p;     // global point index
-};
-
-__device__ __forceinline__ RowInfo row_info(const DecArgs& a, int t, int64_t tile_first) {
-  RowInfo ri;
-  ri.q = t % a.Pt;
-  int k = t / a.Pt;
-  ri.p = tile_first + ri.q;
-  if (k >= a.R || ri.p >= a.n) {
-    ri.cls = -1;
-    ri.kind = -1;
-    return ri;
-  }
-  ri.kind = a.kinds[k];
-  ri.cls = ri.kind == KIND_PRIMAL ? 0 : (ri.kind == KIND_SECANT ? 2 : 1);
-  return ri;
-}
-
-// Input vector (normalised) and direction of one row.
-__device__ __forceinline__ void row_inputs(const DecArgs& a, const RowInfo& ri, float* in, float* dir) {
-  const int d = a.d, r = a.r;
-  const int li = a.lat ? a.lat[ri.p] : 0;
-  for (int i = 0; i < d; ++i) {
-    in[i] = (a.X[ri.p * d + i] - a.norm[i]) / a.norm[d + i];
-    dir[i] = 0.f;
-  }
-  for (int j = 0; j < r; ++j) {
-    in[d + j] = a.latents[(int64_t)li * r + j];
-    dir[d + j] = 0.f;
-  }
-  if (ri.cls == 1) {
-    if (ri.kind >= 1 && ri.kind <= d) dir[ri.kind - 1] = 1.f / a.norm[d + ri.kind - 1];
-    else if (ri.kind > d && ri.kind <= d + r) dir[ri.kind - 1] = 1.f;
-    else if (ri.kind == KIND_JVP)
-      for (int j = 0; j < r; ++j) dir[d + j] = a.dirs[(int64_t)li * r + j];
-  } else if (ri.cls == 2) {
-    for (int j = 0; j < r; ++j) dir[d + j] = a.dirs[(int64_t)li * r + j];
-  }
-}
 
 // --------------------------------------------------------------------------
 // Decoders without square layers (linear, or a single hidden layer): SIMT.
 // --------------------------------------------------------------------------
 __global__ void decoder_simt(DecArgs a) {
-  const int64_t rows = a.n * a.R;
+  const int64_t n = dec_count(a);
+  const int64_t rows = n * a.R;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < rows; g += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(g / a.n);
+    const int k = (int)(g / n);
     RowInfo ri;
-    ri.p = g % a.n;
+    ri.p = g % n;
     ri.q = 0;
     ri.kind = a.kinds[k];
     ri.cls = ri.kind == KIND_PRIMAL ? 0 : (ri.kind == KIND_SECANT ? 2 : 1);
@@ -163,7 +76,7 @@ __global__ void decoder_simt(DecArgs a) {
       if (ri.cls == 0)
         for (int i = 0; i < a.d; ++i) y[i] += a.bout[i];
     }
-    float* o = a.out + ((int64_t)k * a.n + ri.p) * a.d;
+    float* o = a.out + ((int64_t)k * a.n + ri.p) * a.d;   // kind stride = capacity a.n
     for (int i = 0; i < a.d; ++i) o[i] = y[i] * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
   }
 }
@@ -172,26 +85,6 @@ __global__ void decoder_simt(DecArgs a) {
 // Tensor-core decoder kernel: 128 threads, thread t owns row t of the tile
 // (tensor-memory lane t).
 // --------------------------------------------------------------------------
-struct __align__(8) DecSmemTail {
-  uint64_t bar_w;
-  uint64_t bar_mma;
-  uint32_t tmem;
-  int abort;
-};
-
-__device__ __forceinline__ void store_bf16x8(uint8_t* tile, int row, int col, const float* v) {
-  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
-  __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
-  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]);
-  __nv_bfloat162 p3 = __floats2bfloat162_rn(v[6], v[7]);
-  uint4 u;
-  u.x = *reinterpret_cast<uint32_t*>(&p0);
-  u.y = *reinterpret_cast<uint32_t*>(&p1);
-  u.z = *reinterpret_cast<uint32_t*>(&p2);
-  u.w = *reinterpret_cast<uint32_t*>(&p3);
-  *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row, col, kW)) = u;
-}
-
 __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled operand tiles
@@ -228,12 +121,13 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
 
   constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kW);
   uint32_t mma_phase = 0;
-  const int64_t n_tiles = (a.n + a.Pt - 1) / a.Pt;
+  const int64_t n_pts = dec_count(a);
+  const int64_t n_tiles = (n_pts + a.Pt - 1) / a.Pt;
   const int K0 = a.d + a.r;
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !tail->abort; tile += gridDim.x) {
     const int64_t first = tile * a.Pt;
-    const RowInfo ri = row_info(a, t, first);
+    const RowInfo ri = row_info(a, t, first, n_pts);
     float in[40], dir[40];
     if (ri.cls >= 0) row_inputs(a, ri, in, dir);
 
@@ -251,9 +145,12 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
             zd = fmaf(w, dir[i], zd);
           }
           h[j] = ri.cls == 0 ? act_f(a.act, z) : (ri.cls == 1 ? act_d1(a.act, z) * zd : act_sec(a.act, z, zd));
+          if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + t] = ri.cls == 0 ? z : zd;
         } else {
           h[j] = 0.f;
+          if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + t] = 0.f;
         }
+        if (a.astore) a.astore[(int64_t)c * a.rows_total + tile * 128 + t] = __float2bfloat16_rn(h[j]);
       }
       store_bf16x8(atile, t, c0, h);
     }
@@ -289,6 +186,13 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
         float acc[32];
         tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, acc);
         // primal rows: z = acc + b; publish z for the derivative rows of the same point
+        float* zs = a.zstore ? a.zstore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + t : nullptr;
+        if (zs) {
+          // training: keep the pre-activation (z for primal rows, zdot for tangent rows)
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            zs[(int64_t)(ch * 32 + i) * a.rows_total] = ri.cls < 0 ? 0.f : acc[i] + (ri.cls == 0 ? __ldg(&bl[ch * 32 + i]) : 0.f);
+        }
         if (ri.cls == 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
@@ -307,6 +211,11 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
         } else if (ri.cls < 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+        }
+        if (a.astore) {
+          __nv_bfloat16* as = a.astore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + t;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) as[(int64_t)(ch * 32 + i) * a.rows_total] = __float2bfloat16_rn(acc[i]);
         }
         if (last) {
           // output layer fused into the last epilogue (FP32)
@@ -357,20 +266,7 @@ __global__ void decoder_pack(const float* W, int n_layers, int64_t stride, uint8
 
 using namespace mpmrom;
 
-struct mpm_decoder {
-  int d = 0, r = 0, width = 0, n_hidden = 0, act = 0;
-  int n_tc = 0;
-  int64_t n_params = 0;
-  std::vector<int64_t> w_off, b_off;  // per linear layer offsets into params
-  float* params = nullptr;            // FP32 master copy
-  float* norm = nullptr;
-  float* wsq = nullptr;               // square-layer weights gathered contiguously (n_tc, W, W)
-  float* bsq = nullptr;               // their biases (n_tc, W)
-  uint8_t* wimg = nullptr;            // BF16 swizzled images
-  uint32_t* status = nullptr;
-  int n_sm = 0;
-  size_t smem = 0;
-};
+
 
 namespace {
 
@@ -378,7 +274,7 @@ size_t dec_smem_bytes() {
   return 1024 + kMaxTC * kLayerBytes + kLayerBytes + 64 * kW * sizeof(float) + sizeof(DecSmemTail);
 }
 
-mpm_status refresh_derived(mpm_decoder* dec, cudaStream_t s) {
+mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {
   if (dec->n_tc == 0) return MPM_OK;
   for (int l = 0; l < dec->n_tc; ++l) {
     MPM_CUDA_TRY(cudaMemcpyAsync(dec->wsq + (size_t)l * kW * kW, dec->params + dec->w_off[1 + l],
@@ -393,6 +289,14 @@ mpm_status refresh_derived(mpm_decoder* dec, cudaStream_t s) {
 }
 
 }  // namespace
+
+namespace mpmrom {
+mpm_status decoder_refresh(mpm_decoder* dec, cudaStream_t s) { return refresh_derived_impl(dec, s); }
+// Internal launcher for on-device point sets (used by the reduced-order step).
+mpm_status decoder_launch_dev(const mpm_decoder* dec, const float* X, const int32_t* idx, const int32_t* n_dev,
+                              int n_rep, int64_t capacity, const float* latents, const float* dirs,
+                              const int* kinds, int R, float* out, cudaStream_t s);
+}
 
 extern "C" {
 
@@ -465,7 +369,7 @@ mpm_status decoder_set_params(mpm_decoder* dec, const float* params, const float
   cudaStream_t s = (cudaStream_t)stream;
   MPM_CUDA_TRY(cudaMemcpyAsync(dec->params, params, sizeof(float) * dec->n_params, cudaMemcpyDefault, s));
   MPM_CUDA_TRY(cudaMemcpyAsync(dec->norm, norm, sizeof(float) * 4 * dec->d, cudaMemcpyDefault, s));
-  return refresh_derived(dec, s);
+  return refresh_derived_impl(dec, s);
 }
 
 mpm_status decoder_get_params(const mpm_decoder* dec, float* params, float* norm, void* stream) {
@@ -476,14 +380,26 @@ mpm_status decoder_get_params(const mpm_decoder* dec, float* params, float* norm
   return MPM_OK;
 }
 
+static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const int32_t* lat_idx,
+                                 const float* latents, const float* dirs, const int32_t* kinds, int R, int64_t n,
+                                 float* out, const int32_t* idx, const int32_t* n_dev, int n_rep, cudaStream_t s,
+                                 const DecArgs* extra = nullptr);
+
 mpm_status decoder_eval(const mpm_decoder* dec, const float* X, const int32_t* lat_idx, const float* latents,
                         const float* dirs, const int32_t* kinds, int R, int64_t n, float* out, void* stream) {
   MPM_CHECK_ARG(dec && kinds, "null argument");
-  MPM_CHECK_ARG(R >= 1 && R <= kMaxR && R <= 128, "R must be in [1, 64]");
   MPM_CHECK_ARG(n >= 0, "n >= 0");
   if (n == 0) return MPM_OK;
+  return decoder_launch(dec, X, lat_idx, latents, dirs, kinds, R, n, out, nullptr, nullptr, 1,
+                        (cudaStream_t)stream);
+}
+
+static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const int32_t* lat_idx,
+                                 const float* latents, const float* dirs, const int32_t* kinds, int R, int64_t n,
+                                 float* out, const int32_t* idx, const int32_t* n_dev, int n_rep, cudaStream_t s,
+                                 const DecArgs* extra) {
+  MPM_CHECK_ARG(R >= 1 && R <= kMaxR && R <= 128, "R must be in [1, 64]");
   MPM_CHECK_ARG(X && latents && out, "null argument");
-  cudaStream_t s = (cudaStream_t)stream;
   DecArgs a{};
   a.d = dec->d;
   a.r = dec->r;
@@ -517,6 +433,16 @@ mpm_status decoder_eval(const mpm_decoder* dec, const float* X, const int32_t* l
   MPM_CHECK_ARG(kinds[0] == KIND_PRIMAL || dec->n_tc == 0, "the first row kind must be the primal (0)");
   a.out = out;
   a.status = dec->status;
+  a.idx = idx;
+  a.n_dev = n_dev;
+  a.n_rep = n_rep;
+  if (extra) {
+    a.lat_per_point = extra->lat_per_point;
+    a.zstore = extra->zstore;
+    a.astore = extra->astore;
+    a.rows_total = extra->rows_total;
+    MPM_CHECK_ARG(!a.zstore || dec->n_tc > 0, "training stores need square hidden layers");
+  }
   if (dec->n_tc == 0) {
     int64_t rows = n * R;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, dec->n_sm * 8));
@@ -529,6 +455,32 @@ mpm_status decoder_eval(const mpm_decoder* dec, const float* X, const int32_t* l
   MPM_CUDA_TRY(cudaGetLastError());
   return MPM_OK;
 }
+
+}  // extern "C"
+
+namespace mpmrom {
+// Training forward: one latent and one JVP direction per point; stores the
+// per-layer pre-activations and activations of every tile row.
+mpm_status decoder_launch_train(const mpm_decoder* dec, const float* X, const float* latents, const float* dirs,
+                                const int* kinds, int R, int64_t n, float* out, float* zstore,
+                                __nv_bfloat16* astore, int64_t rows_total, cudaStream_t s) {
+  DecArgs extra{};
+  extra.lat_per_point = 1;
+  extra.zstore = zstore;
+  extra.astore = astore;
+  extra.rows_total = rows_total;
+  return decoder_launch(dec, X, nullptr, latents, dirs, kinds, R, n, out, nullptr, nullptr, 1, s, &extra);
+}
+
+mpm_status decoder_launch_dev(const mpm_decoder* dec, const float* X, const int32_t* idx, const int32_t* n_dev,
+                              int n_rep, int64_t capacity, const float* latents, const float* dirs,
+                              const int* kinds, int R, float* out, cudaStream_t s) {
+  if (capacity <= 0) return MPM_OK;
+  return decoder_launch(dec, X, nullptr, latents, dirs, kinds, R, capacity, out, idx, n_dev, n_rep, s);
+}
+}  // namespace mpmrom
+
+extern "C" {
 
 mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void* stream) {
   MPM_CHECK_ARG(dec && out, "null argument");

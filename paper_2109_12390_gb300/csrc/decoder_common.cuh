@@ -1,0 +1,174 @@
+// Device pieces shared by the decoder evaluation kernels (decoder.cu) and the
+// decoder training kernels (train.cu): argument block, activation functions,
+// row bookkeeping of the 128-row tiles, BF16 tile stores.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace mpmrom {
+
+constexpr int kW = 128;          // hidden width of the tensor-core layers
+constexpr int kMaxTC = 4;        // square layers resident in shared memory
+constexpr int kMaxR = 64;        // row kinds per point
+constexpr int kLayerBytes = kW * kW * 2;
+
+struct DecArgs {
+  int d, r, n_tc, act;
+  const float* W0;    // (W, d + r)
+  const float* b0;    // (W)
+  const float* bh;    // (n_tc, W)
+  const float* Wout;  // (d, W)
+  const float* bout;  // (d)
+  const float* norm;  // X_min[d], X_range[d], out_shift[d], out_scale[d]
+  const uint8_t* wimg;
+  const float* X;
+  const int32_t* lat;
+  const float* latents;
+  const float* dirs;
+  int64_t n;          // points (upper bound when n_dev is set)
+  int R, Pt;
+  int kinds[kMaxR];
+  float* out;         // (R, n, d)
+  // on-device point sets (reduced-order step): when n_dev is set, the point
+  // count is (*n_dev) * n_rep, point p reads X row idx[p % *n_dev] (or
+  // p % *n_dev when idx is null) and latent row p / *n_dev.
+  const int32_t* idx;
+  const int32_t* n_dev;
+  int n_rep;
+  uint32_t* status;
+  // linear decoder (no hidden layer): y = W0 [Xn, xhat] + b0 with W0 (d, d + r)
+  int linear;
+  // latent row = point index (training batches carry one latent per point)
+  int lat_per_point;
+  // training: per hidden layer l, pre-activations z (FP32) and activations a
+  // (BF16) of every tile row, stored feature-major: [l][feature][row], row =
+  // tile * 128 + t, rows_total = n_tiles * 128
+  float* zstore;
+  __nv_bfloat16* astore;
+  int64_t rows_total;
+};
+
+__device__ __forceinline__ float elu(float z) { return z > 0.f ? z : expm1f(z); }
+__device__ __forceinline__ float elu_d1(float z) { return z > 0.f ? 1.f : __expf(z); }
+// act(z + dz) - act(z) without cancellation on the negative branch
+__device__ __forceinline__ float elu_secant(float z, float dz) {
+  float z1 = z + dz;
+  if (z > 0.f && z1 > 0.f) return dz;
+  if (z <= 0.f && z1 <= 0.f) return __expf(z) * expm1f(dz);
+  return elu(z1) - elu(z);
+}
+
+__device__ __forceinline__ float act_f(int act, float z) { return act == 0 ? elu(z) : z; }
+__device__ __forceinline__ float act_d1(int act, float z) { return act == 0 ? elu_d1(z) : 1.f; }
+__device__ __forceinline__ float act_sec(int act, float z, float dz) { return act == 0 ? elu_secant(z, dz) : dz; }
+
+// row-kind codes (see decoder_eval in include/mpmrom.h)
+constexpr int KIND_PRIMAL = 0;
+constexpr int KIND_JVP = 1000;
+constexpr int KIND_SECANT = 1001;
+
+struct RowInfo {
+  int kind;      // code
+  int cls;       // 0 primal, 1 tangent, 2 secant, -1 padding
+  int q;         // point within tile
+  int64_t p;     // global point index
+};
+
+__device__ __forceinline__ int64_t dec_count(const DecArgs& a) {
+  return a.n_dev ? (int64_t)(*a.n_dev) * a.n_rep : a.n;
+}
+
+__device__ __forceinline__ RowInfo row_info(const DecArgs& a, int t, int64_t tile_first, int64_t n) {
+  RowInfo ri;
+  ri.q = t % a.Pt;
+  int k = t / a.Pt;
+  ri.p = tile_first + ri.q;
+  if (k >= a.R || ri.p >= n) {
+    ri.cls = -1;
+    ri.kind = -1;
+    return ri;
+  }
+  ri.kind = a.kinds[k];
+  ri.cls = ri.kind == KIND_PRIMAL ? 0 : (ri.kind == KIND_SECANT ? 2 : 1);
+  return ri;
+}
+
+// Input vector (normalised) and direction of one row.
+__device__ __forceinline__ void row_inputs(const DecArgs& a, const RowInfo& ri, float* in, float* dir) {
+  const int d = a.d, r = a.r;
+  int64_t xrow = ri.p;
+  int li = a.lat ? a.lat[ri.p] : (a.lat_per_point ? (int)ri.p : 0);
+  if (a.n_dev) {
+    const int cnt = max(*a.n_dev, 1);
+    xrow = ri.p % cnt;
+    li = (int)(ri.p / cnt);
+    if (a.idx) xrow = a.idx[xrow];
+  }
+  for (int i = 0; i < d; ++i) {
+    in[i] = (a.X[xrow * d + i] - a.norm[i]) / a.norm[d + i];
+    dir[i] = 0.f;
+  }
+  for (int j = 0; j < r; ++j) {
+    in[d + j] = a.latents[(int64_t)li * r + j];
+    dir[d + j] = 0.f;
+  }
+  if (ri.cls == 1) {
+    if (ri.kind >= 1 && ri.kind <= d) dir[ri.kind - 1] = 1.f / a.norm[d + ri.kind - 1];
+    else if (ri.kind > d && ri.kind <= d + r) dir[ri.kind - 1] = 1.f;
+    else if (ri.kind == KIND_JVP)
+      for (int j = 0; j < r; ++j) dir[d + j] = a.dirs[(int64_t)li * r + j];
+  } else if (ri.cls == 2) {
+    for (int j = 0; j < r; ++j) dir[d + j] = a.dirs[(int64_t)li * r + j];
+  }
+}
+
+struct __align__(8) DecSmemTail {
+  uint64_t bar_w;
+  uint64_t bar_mma;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ void store_bf16x8(uint8_t* tile, int row, int col, const float* v) {
+  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
+  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]);
+  __nv_bfloat162 p3 = __floats2bfloat162_rn(v[6], v[7]);
+  uint4 u;
+  u.x = *reinterpret_cast<uint32_t*>(&p0);
+  u.y = *reinterpret_cast<uint32_t*>(&p1);
+  u.z = *reinterpret_cast<uint32_t*>(&p2);
+  u.w = *reinterpret_cast<uint32_t*>(&p3);
+  *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row, col, kW)) = u;
+}
+
+
+}  // namespace mpmrom
+
+#include <vector>
+
+// Host-side decoder object (shared by decoder.cu and train.cu).
+struct mpm_decoder {
+  int d = 0, r = 0, width = 0, n_hidden = 0, act = 0;
+  int n_tc = 0;
+  int64_t n_params = 0;
+  std::vector<int64_t> w_off, b_off;  // per linear layer offsets into params
+  float* params = nullptr;            // FP32 master copy
+  float* norm = nullptr;
+  float* wsq = nullptr;               // square-layer weights gathered contiguously (n_tc, W, W)
+  float* bsq = nullptr;               // their biases (n_tc, W)
+  uint8_t* wimg = nullptr;            // BF16 swizzled images
+  uint32_t* status = nullptr;
+  int n_sm = 0;
+  size_t smem = 0;
+};
+
+namespace mpmrom {
+// Re-packs the BF16 shared-memory images of the square layers from the FP32 master copy.
+mpm_status decoder_refresh(mpm_decoder* dec, cudaStream_t s);
+}  // namespace mpmrom

@@ -77,34 +77,10 @@ __device__ __forceinline__ int key_of_base(const int b[D], int inst, const DevPa
   return inst * p.nblk + k;
 }
 
-// Grid update of Algorithm 1 for one node: v = p/m + dt g if m > 0, then walls.
+// Grid update of Algorithm 1 for one node (shared with the reduced-order step).
 template <int D>
 __device__ __forceinline__ void node_velocity(float4 mp, const int node[D], const DevParams& p, float v[D]) {
-  float comp[3] = {mp.y, mp.z, mp.w};
-  if (mp.x > 0.f) {
-    float im = 1.0f / mp.x;
-#pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = comp[a] * im + p.dt * p.g[a];
-  } else {
-#pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = 0.f;
-  }
-  const int lo = p.bc_width, hi = p.n - 1 - p.bc_width;
-  bool sticky = false;
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    bool l = node[a] < lo, h = node[a] > hi;
-    if (p.bc == MPM_BC_SLIP_FLOOR && a == 1) {
-      sticky |= h;
-      if (l) v[1] = fmaxf(v[1], 0.f);
-    } else {
-      sticky |= (l | h);
-    }
-  }
-  if (sticky) {
-#pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = 0.f;
-  }
+  grid_node_velocity<D>(mp, node, p.n, p.bc, p.bc_width, p.dt, p.g, v);
 }
 
 // Tile of nodes [b0 - lo_pad, b0 + B + hi_pad)^D, flattened row-major.
@@ -163,20 +139,29 @@ __device__ __forceinline__ void scatter_particle(const float x[D], const float v
     for (int i = 0; i < D * D; ++i) A[i] = p.mass * C[i] - k * tau[i];
   }
   const int NS = (D == 2) ? 9 : 27;
-#pragma unroll
+  // Stencil nodes are visited in a lane-rotated order: lanes whose particles
+  // share a cell then hit different nodes in the same iteration, which keeps
+  // the shared-memory atomics of a warp from serialising on one address.
+  const int lane = threadIdx.x & 31;
+#pragma unroll 1
   for (int s = 0; s < NS; ++s) {
+    const int q = (s + lane) % NS;
     int off[D];
     if (D == 2) {
-      off[0] = s / 3;
-      off[1] = s % 3;
+      off[0] = q / 3;
+      off[1] = q - 3 * off[0];
     } else {
-      off[0] = s / 9;
-      off[D - 2] = (s / 3) % 3;
-      off[D - 1] = s % 3;
+      off[0] = q / 9;
+      off[1] = (q / 3) % 3;
+      off[2] = q % 3;
     }
     float wt = 1.f;
+    float wsel[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) wt *= w[a][off[a]];
+    for (int a = 0; a < D; ++a) {
+      wsel[a] = off[a] == 0 ? w[a][0] : (off[a] == 1 ? w[a][1] : w[a][2]);
+      wt *= wsel[a];
+    }
     float mom[D];
     if (TRANSFER == MPM_TRANSFER_MLS) {
       float dpos[D];
@@ -193,10 +178,10 @@ __device__ __forceinline__ void scatter_particle(const float x[D], const float v
       float grad[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        float gg = dw[a][off[a]] * p.inv_dx;
+        float gg = (off[a] == 0 ? dw[a][0] : (off[a] == 1 ? dw[a][1] : dw[a][2])) * p.inv_dx;
 #pragma unroll
         for (int b = 0; b < D; ++b)
-          if (b != a) gg *= w[b][off[b]];
+          if (b != a) gg *= wsel[b];
         grad[a] = gg;
       }
       const float k = p.dt * p.vol;

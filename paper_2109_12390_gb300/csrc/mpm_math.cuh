@@ -196,4 +196,38 @@ __device__ __forceinline__ void kirchhoff(const float F[D * D], float mu, float 
   }
 }
 
+// Grid update of Algorithm 1 for one node (step 2): v = p / m + dt g when
+// m > 0 (p already holds m v + dt f), then the walls: nodes with any index
+// < bc_width or > n - 1 - bc_width are sticky (zero velocity); with the slip
+// floor (bc == 1) the low-y band instead clamps v_y >= 0.
+template <int D>
+__device__ __forceinline__ void grid_node_velocity(float4 mp, const int node[D], int n, int bc, int bc_width,
+                                                   float dt, const float g[3], float v[D]) {
+  float comp[3] = {mp.y, mp.z, mp.w};
+  if (mp.x > 0.f) {
+    float im = 1.0f / mp.x;
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = comp[a] * im + dt * g[a];
+  } else {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = 0.f;
+  }
+  const int lo = bc_width, hi = n - 1 - bc_width;
+  bool sticky = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    bool l = node[a] < lo, h = node[a] > hi;
+    if (bc == 1 && a == 1) {
+      sticky |= h;
+      if (l) v[1] = fmaxf(v[1], 0.f);
+    } else {
+      sticky |= (l | h);
+    }
+  }
+  if (sticky) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = 0.f;
+  }
+}
+
 }  // namespace mpmrom

@@ -1,0 +1,1170 @@
+// Reduced-order step (Algorithm 2 with Lagrangian quadrature) on sm_103a.
+//
+// One step, all on the device (no host round trip; replayable as a graph):
+//   decoder        x_n^p = g(X^p; xhat_n) for all particles (Alg. 3, tracking)
+//   rom_select     one CTA: clears the previous basis set on the grid, draws the
+//                  sample set P as the bottom-k of a SplitMix64 hash per
+//                  particle (8-pass radix select over the 64-bit hashes, ties
+//                  by particle id), marks the basis set I (stencil nodes of the
+//                  samples) with a per-step stamp, finds the neighbour set N
+//                  (particles outside P with a stencil node in I) and writes
+//                  the quadrature list Q = [P ascending, N ascending] (Alg. 3)
+//   decoder        dg/dX (deformation gradient, Eq. defGrad) and the JVP along
+//                  vhat_n (velocity, Eq. timederOne) at Q
+//   rom_p2g        particle-to-grid from Q onto the nodes of I only (Alg. 5,
+//                  no affine term), stress from the same device functions as
+//                  the full-order step
+//   rom_g2p        grid update + grid-to-particle to the samples: v_trial,
+//                  x_trial = x_n + dt v_trial (Alg. 5)
+//   decoder        dg/dxhat at (X^P, xhat_n)
+//   rom_normal     FP64 normal equations J^T J, J^T b (multi-CTA, FP64
+//                  atomics); the last CTA to finish factors them (parallel
+//                  Cholesky) and solves: vhat_{n+1} (Eq. nonlinear_projection:vel),
+//                  or a Gauss-Newton step delta for xhat (Eq. ...:pos)
+//   per Gauss-Newton iteration (initial guess 2 xhat_n - xhat_{n-1}):
+//     decoder      dg/dxhat and the secant g(xhat_n) - g(xhat_k) at the samples
+//     rom_normal   residual r = g(xhat_k) - x_trial = -(secant) - dt v_trial;
+//                  solve J^T J delta = -J^T r; prepare 11 trial steps 2^-m delta
+//     decoder      secants g(xhat_k + 2^-m delta) - g(xhat_n), m = 0..10, in one launch
+//     rom_linesearch  objective of every trial (FP64); the last CTA takes the
+//                  first trial that meets the Armijo condition (the same
+//                  choice as sequential backtracking) and updates xhat.
+// The Gauss-Newton residual is formed from secant rows (exact differences of
+// decoder outputs) so that BF16 GEMMs resolve latent increments of ~1e-5.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "mpm_math.cuh"
+
+struct mpm_decoder;
+namespace mpmrom {
+mpm_status decoder_launch_dev(const mpm_decoder* dec, const float* X, const int32_t* idx, const int32_t* n_dev,
+                              int n_rep, int64_t capacity, const float* latents, const float* dirs,
+                              const int* kinds, int R, float* out, cudaStream_t s);
+}
+
+namespace mpmrom {
+
+constexpr int kLS = 11;          // line-search trials 2^0 .. 2^-10
+constexpr int kMaxRl = 32;       // latent dimension bound of the solver
+constexpr int kNormBlock = 256;
+
+// ----------------------------------------------------------------- hashing
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t state, uint64_t k) {
+  uint64_t z = state + 0x9E3779B97F4A7C15ull * (k + 1ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct RomDev {
+  int d, r, P, n, k;         // dims, particles, grid nodes per axis, samples
+  float dx, inv_dx, dt;
+  float g[3];
+  int bc, bc_width;
+  float mass, vol, mu, lam;
+  uint64_t seed;
+  int inst;
+  // buffers
+  const float* X;
+  float* x_all;              // (P, d)
+  int32_t* qlist;            // (P) samples then neighbours
+  int32_t* counts;           // [0] nP, [1] nQ, [2] nI (basis-node list length)
+  int32_t* nodes;            // (k * 3^d) basis nodes of the last step (for clearing)
+  uint32_t* stamp;           // (n^d) node stamps
+  float4* grid;              // (n^d)
+  float* v_trial;            // (k, d)
+  float* x_trial;            // (k, d)
+  int64_t* step;             // device step counter
+  uint32_t* status;
+};
+
+// Block-wide exclusive scan of one int per thread (blockDim.x <= 1024).
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total, int* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nwarps ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  int excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0);
+  *total = s_warp[nwarps - 1];
+  __syncthreads();
+  return excl;
+}
+
+template <int D>
+__device__ __forceinline__ int node_linear(const int node[D], int n) {
+  int l = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) l = l * n + node[a];
+  return l;
+}
+
+// ------------------------------------------------------------ rom_select
+template <int D>
+__global__ void __launch_bounds__(1024) rom_select(RomDev R) {
+  __shared__ int s_hist[256];
+  __shared__ int s_warp[32];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_remaining;
+  const int t = threadIdx.x, T = blockDim.x;
+  const int P = R.P, k = min(R.k, P);
+  const int per = (P + T - 1) / T;
+  const int p0 = min(t * per, P), p1 = min(p0 + per, P);
+  const int64_t step = *R.step;
+  const uint32_t stamp = (uint32_t)(step + 1);
+  const uint64_t s1 = splitmix_out(splitmix_out(R.seed, (uint64_t)R.inst), (uint64_t)step);
+
+  // clear the grid nodes of the previous basis set
+  const int n_prev = R.counts[2];
+  for (int i = t; i < n_prev; i += T) R.grid[R.nodes[i]] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  // radix select of the k-th smallest hash
+  if (t == 0) {
+    s_prefix = 0ull;
+    s_remaining = k;
+  }
+  unsigned long long mask = 0ull;
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = 56 - 8 * pass;
+    for (int i = t; i < 256; i += T) s_hist[i] = 0;
+    __syncthreads();
+    const unsigned long long prefix = s_prefix;
+    for (int p = p0; p < p1; ++p) {
+      const uint64_t h = splitmix_out(s1, (uint64_t)p);
+      if ((h & mask) == prefix) atomicAdd(&s_hist[(h >> shift) & 255], 1);
+    }
+    __syncthreads();
+    if (t == 0) {
+      int rem = s_remaining, acc = 0, b = 0;
+      for (; b < 256; ++b) {
+        if (acc + s_hist[b] >= rem) break;
+        acc += s_hist[b];
+      }
+      b = min(b, 255);
+      s_remaining = rem - acc;
+      s_prefix = prefix | ((unsigned long long)b << shift);
+    }
+    mask |= 255ull << shift;
+    __syncthreads();
+  }
+  const uint64_t thr = s_prefix;
+  const int need_eq = s_remaining;  // hashes equal to thr to take, lowest ids first
+  // select: h < thr, or h == thr among the first need_eq by id
+  int n_less = 0, n_eq = 0;
+  for (int p = p0; p < p1; ++p) {
+    const uint64_t h = splitmix_out(s1, (uint64_t)p);
+    n_less += h < thr;
+    n_eq += h == thr;
+  }
+  int eq_total;
+  const int eq_before = block_exclusive_scan(n_eq, &eq_total, s_warp);
+  int sel = 0;
+  {
+    int e = eq_before;
+    for (int p = p0; p < p1; ++p) {
+      const uint64_t h = splitmix_out(s1, (uint64_t)p);
+      if (h < thr) ++sel;
+      else if (h == thr) {
+        if (e < need_eq) ++sel;
+        ++e;
+      }
+    }
+  }
+  int n_sel;
+  int pos = block_exclusive_scan(sel, &n_sel, s_warp);
+  {
+    int e = eq_before;
+    for (int p = p0; p < p1; ++p) {
+      const uint64_t h = splitmix_out(s1, (uint64_t)p);
+      bool take = h < thr;
+      if (h == thr) {
+        take = e < need_eq;
+        ++e;
+      }
+      if (take) R.qlist[pos++] = p;
+    }
+  }
+  __syncthreads();
+  // basis set I: stamp the stencil nodes of the samples (and keep them for clearing)
+  constexpr int NS = (D == 2) ? 9 : 27;
+  for (int i = t; i < k; i += T) {
+    const int p = R.qlist[i];
+    int base[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int b = stencil_base(R.x_all[(size_t)p * D + a], R.inv_dx);
+      if (b < 0 || b + 2 > R.n - 1) raise_status(R.status, STATUS_OUT_OF_GRID);
+      base[a] = min(max(b, 0), R.n - 3);
+    }
+    for (int s = 0; s < NS; ++s) {
+      int node[D];
+      node[0] = base[0] + (D == 2 ? s / 3 : s / 9);
+      node[D - 1] = base[D - 1] + s % 3;
+      if (D == 3) node[1] = base[1] + (s / 3) % 3;
+      const int l = node_linear<D>(node, R.n);
+      R.stamp[l] = stamp;
+      R.nodes[i * NS + s] = l;
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+  // neighbour set N: other particles with a stencil node in I (ascending ids)
+  int nb = 0;
+  for (int p = p0; p < p1; ++p) {
+    const uint64_t h = splitmix_out(s1, (uint64_t)p);
+    // recompute the sample decision for p
+    bool is_sample = h < thr;
+    if (h == thr) is_sample = true;  // ties resolved below
+    if (h == thr) {
+      // rank of p among equal hashes (only within this thread's range matters, plus eq_before)
+      int e = eq_before;
+      for (int q = p0; q < p; ++q) e += (splitmix_out(s1, (uint64_t)q) == thr);
+      is_sample = e < need_eq;
+    }
+    if (is_sample) continue;
+    int base[D];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int b = stencil_base(R.x_all[(size_t)p * D + a], R.inv_dx);
+      ok &= (b >= 0) & (b + 2 <= R.n - 1);
+      base[a] = min(max(b, 0), R.n - 3);
+    }
+    if (!ok) raise_status(R.status, STATUS_OUT_OF_GRID);
+    bool hit = false;
+    for (int s = 0; s < NS && !hit; ++s) {
+      int node[D];
+      node[0] = base[0] + (D == 2 ? s / 3 : s / 9);
+      node[D - 1] = base[D - 1] + s % 3;
+      if (D == 3) node[1] = base[1] + (s / 3) % 3;
+      hit = R.stamp[node_linear<D>(node, R.n)] == stamp;
+    }
+    nb += hit;
+  }
+  int n_nb;
+  int npos = block_exclusive_scan(nb, &n_nb, s_warp);
+  for (int p = p0; p < p1; ++p) {
+    const uint64_t h = splitmix_out(s1, (uint64_t)p);
+    bool is_sample = h < thr;
+    if (h == thr) {
+      int e = eq_before;
+      for (int q = p0; q < p; ++q) e += (splitmix_out(s1, (uint64_t)q) == thr);
+      is_sample = e < need_eq;
+    }
+    if (is_sample) continue;
+    int base[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      base[a] = min(max(stencil_base(R.x_all[(size_t)p * D + a], R.inv_dx), 0), R.n - 3);
+    bool hit = false;
+    for (int s = 0; s < NS && !hit; ++s) {
+      int node[D];
+      node[0] = base[0] + (D == 2 ? s / 3 : s / 9);
+      node[D - 1] = base[D - 1] + s % 3;
+      if (D == 3) node[1] = base[1] + (s / 3) % 3;
+      hit = R.stamp[node_linear<D>(node, R.n)] == stamp;
+    }
+    if (hit) R.qlist[k + npos++] = p;
+  }
+  if (t == 0) {
+    R.counts[0] = k;
+    R.counts[1] = k + n_nb;
+    R.counts[2] = k * NS;
+  }
+}
+
+// ----------------------------------------------------- local P2G (Alg. 5)
+// dec_out: (R, capQ, d) decoder output at Q with kinds [primal, dX_0..dX_{d-1}, JVP].
+template <int D, int MATERIAL, int TRANSFER>
+__global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t capQ) {
+  const int nQ = R.counts[1];
+  const uint32_t stamp = (uint32_t)(*R.step + 1);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nQ; i += gridDim.x * blockDim.x) {
+    const int pid = R.qlist[i];
+    float x[D], v[D], F[D * D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      x[a] = R.x_all[(size_t)pid * D + a];
+      v[a] = dec_out[((size_t)(1 + D) * capQ + i) * D + a];
+#pragma unroll
+      for (int b = 0; b < D; ++b) F[a * D + b] = dec_out[((size_t)(1 + b) * capQ + i) * D + a];
+    }
+    float tau[D * D];
+    kirchhoff<D, MATERIAL, true>(F, R.mu, R.lam, tau);
+    int base[D];
+    float w[D][3], dw[D][3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      base[a] = stencil_base(x[a], R.inv_dx);
+      ok &= (base[a] >= 0) & (base[a] + 2 <= R.n - 1);
+      const float fx = x[a] * R.inv_dx - (float)base[a];
+      bspline_w(fx, w[a]);
+      bspline_dw(fx, dw[a]);
+    }
+    if (!ok) continue;  // flagged by rom_select
+    constexpr int NS = (D == 2) ? 9 : 27;
+    const float kml = R.dt * R.vol * 4.0f * R.inv_dx * R.inv_dx;
+#pragma unroll 1
+    for (int s = 0; s < NS; ++s) {
+      int off[D];
+      off[0] = (D == 2 ? s / 3 : s / 9);
+      off[D - 1] = s % 3;
+      if (D == 3) off[1] = (s / 3) % 3;
+      int node[D];
+      float wt = 1.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        node[a] = base[a] + off[a];
+        wt *= w[a][off[a]];
+      }
+      const int l = node_linear<D>(node, R.n);
+      if (R.stamp[l] != stamp) continue;   // only the basis set I is assembled
+      float mom[D];
+      if (TRANSFER == MPM_TRANSFER_MLS) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float q = R.mass * v[a];
+#pragma unroll
+          for (int b = 0; b < D; ++b) q = fmaf(-kml * tau[a * D + b], (float)node[b] * R.dx - x[b], q);
+          mom[a] = wt * q;
+        }
+      } else {
+        float grad[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float gg = dw[a][off[a]] * R.inv_dx;
+#pragma unroll
+          for (int b = 0; b < D; ++b)
+            if (b != a) gg *= w[b][off[b]];
+          grad[a] = gg;
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float f = 0.f;
+#pragma unroll
+          for (int b = 0; b < D; ++b) f = fmaf(tau[a * D + b], grad[b], f);
+          mom[a] = wt * R.mass * v[a] - R.dt * R.vol * f;
+        }
+      }
+      atomicAdd(&R.grid[l], make_float4(wt * R.mass, mom[0], D > 1 ? mom[1] : 0.f, D > 2 ? mom[D - 1] : 0.f));
+    }
+  }
+}
+
+// ---------------------------------------- grid update + G2P to the samples
+template <int D>
+__global__ void rom_g2p(RomDev R) {
+  const int nP = R.counts[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nP; i += gridDim.x * blockDim.x) {
+    const int pid = R.qlist[i];
+    float x[D], w[D][3];
+    int base[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      x[a] = R.x_all[(size_t)pid * D + a];
+      base[a] = min(max(stencil_base(x[a], R.inv_dx), 0), R.n - 3);
+      bspline_w(x[a] * R.inv_dx - (float)base[a], w[a]);
+    }
+    float v[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = 0.f;
+    constexpr int NS = (D == 2) ? 9 : 27;
+    for (int s = 0; s < NS; ++s) {
+      int off[D], node[D];
+      off[0] = (D == 2 ? s / 3 : s / 9);
+      off[D - 1] = s % 3;
+      if (D == 3) off[1] = (s / 3) % 3;
+      float wt = 1.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        node[a] = base[a] + off[a];
+        wt *= w[a][off[a]];
+      }
+      float vi[D];
+      grid_node_velocity<D>(R.grid[node_linear<D>(node, R.n)], node, R.n, R.bc, R.bc_width, R.dt, R.g, vi);
+#pragma unroll
+      for (int a = 0; a < D; ++a) v[a] = fmaf(wt, vi[a], v[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      R.v_trial[(size_t)i * D + a] = v[a];
+      R.x_trial[(size_t)i * D + a] = fmaf(R.dt, v[a], x[a]);
+    }
+  }
+}
+
+// ----------------------------------------------------------- least squares
+// Solver state in FP64 (per reduced-order instance).
+struct RomSolve {
+  double* xh;        // xhat_n
+  double* xh_prev;   // xhat_{n-1}
+  double* vh;        // vhat_n
+  double* vh_new;    // vhat_{n+1}
+  double* xk;        // Gauss-Newton iterate
+  double* delta;     // Gauss-Newton step
+  double* scal;      // [0] f0, [1] slope, [2] |delta|
+  double* acc;       // normal-equation accumulators: r(r+1)/2 + r + 1
+  double* fls;       // line-search objectives (kLS)
+  uint32_t* counter; // last-CTA counters [0] normal, [1] line search
+  // FP32 copies fed to the decoder
+  float* xh32;       // xhat_n
+  float* vh32;       // vhat_n
+  float* xk32;       // iterate
+  float* dk32;       // xhat_n - iterate
+  float* ls_base32;  // kLS x r, rows = xhat_n
+  float* ls_dir32;   // kLS x r, rows = (xk - xhat_n) + 2^-m delta
+};
+
+enum { NE_VEL = 0, NE_GN = 1, NE_FIT = 2 };
+
+// Parallel Cholesky solve of the SPD system A x = b held in shared memory
+// (A: r x r, row-major).  Returns false if a pivot is not positive.
+__device__ bool chol_solve(double* A, double* b, int r) {
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    if (threadIdx.x == 0) {
+      double piv = A[j * r + j];
+      if (!(piv > 0.0)) s_bad = 1;
+      A[j * r + j] = sqrt(fmax(piv, 1e-300));
+    }
+    __syncthreads();
+    if (s_bad) return false;
+    const double ljj = A[j * r + j];
+    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * r + j] /= ljj;
+    __syncthreads();
+    for (int e = threadIdx.x; e < (r - j - 1) * (r - j - 1); e += blockDim.x) {
+      const int i = j + 1 + e / (r - j - 1), c = j + 1 + e % (r - j - 1);
+      if (c <= i) A[i * r + c] -= A[i * r + j] * A[c * r + j];
+    }
+    __syncthreads();
+  }
+  // forward / backward substitution (single thread; r <= 64)
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < r; ++i) {
+      double s = b[i];
+      for (int c = 0; c < i; ++c) s -= A[i * r + c] * b[c];
+      b[i] = s / A[i * r + i];
+    }
+    for (int i = r - 1; i >= 0; --i) {
+      double s = b[i];
+      for (int c = i + 1; c < r; ++c) s -= A[c * r + i] * b[c];
+      b[i] = s / A[i * r + i];
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Normal equations of one least-squares problem over rows (sample, component):
+//   J row = dg/dxhat (r values),  rhs row b:
+//     NE_VEL  b = v_trial                    (solve J^T J x = J^T b -> vhat_{n+1})
+//     NE_GN   b = -(g(xhat_k) - x_trial) = secant + dt v_trial   (-> delta)
+//     NE_FIT  b = target - g(xhat_k)          (initial-condition fit, -> delta)
+// dec: decoder output (R, cap, d) with kinds [primal, dxhat_0.., (secant)].
+// The last CTA factors and solves, then prepares the next stage.
+__global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, const float* __restrict__ dec,
+                                                         int64_t cap, int mode, const float* __restrict__ target,
+                                                         int projection, int n_rows_override) {
+  const int d = R.d, r = R.r;
+  const int nP = n_rows_override > 0 ? n_rows_override : R.counts[0];
+  const int rows = nP * d;
+  const int n_mat = r * (r + 1) / 2;
+  const int n_acc = n_mat + r + 1;
+  __shared__ float sJ[64][kMaxRl + 1];
+  __shared__ float sb[64];
+  __shared__ bool s_last;
+  for (int row0 = blockIdx.x * 64; row0 < rows; row0 += gridDim.x * 64) {
+    const int nr = min(64, rows - row0);
+    for (int e = threadIdx.x; e < nr * (r + 1); e += blockDim.x) {
+      const int rr = e / (r + 1), c = e % (r + 1);
+      const int row = row0 + rr, p = row / d, a = row % d;
+      if (c < r) {
+        sJ[rr][c] = dec[((size_t)(1 + c) * cap + p) * d + a];
+      } else {
+        float b;
+        if (mode == NE_VEL) b = R.v_trial[(size_t)p * d + a];
+        else if (mode == NE_GN) b = dec[((size_t)(1 + r) * cap + p) * d + a] + R.dt * R.v_trial[(size_t)p * d + a];
+        else b = target[(size_t)p * d + a] - dec[(size_t)p * d + a];
+        sb[rr] = b;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n_acc; e += blockDim.x) {
+      double s = 0.0;
+      if (e < n_mat) {
+        // upper-triangle index e -> (i, j), i <= j
+        int i = 0, rem = e;
+        while (rem >= r - i) {
+          rem -= r - i;
+          ++i;
+        }
+        const int j = i + rem;
+        for (int q = 0; q < nr; ++q) s = fma((double)sJ[q][i], (double)sJ[q][j], s);
+      } else if (e < n_mat + r) {
+        const int i = e - n_mat;
+        for (int q = 0; q < nr; ++q) s = fma((double)sJ[q][i], (double)sb[q], s);
+      } else {
+        for (int q = 0; q < nr; ++q) s = fma((double)sb[q], (double)sb[q], s);
+      }
+      atomicAdd(&S.acc[e], s);
+    }
+    __syncthreads();
+  }
+  // last CTA: factor and solve
+  __threadfence();
+  if (threadIdx.x == 0) s_last = atomicAdd(&S.counter[0], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  __shared__ double A[kMaxRl * kMaxRl];
+  __shared__ double A_keep[kMaxRl * kMaxRl];
+  __shared__ double bvec[kMaxRl];
+  __shared__ double s_rhs[kMaxRl];
+  __shared__ double s_bb, s_shift;
+  for (int e = threadIdx.x; e < n_mat; e += blockDim.x) {
+    int i = 0, rem = e;
+    while (rem >= r - i) {
+      rem -= r - i;
+      ++i;
+    }
+    const int j = i + rem;
+    const double v = atomicAdd(&S.acc[e], 0.0);
+    A[i * r + j] = v;
+    A[j * r + i] = v;
+    A_keep[i * r + j] = v;
+    A_keep[j * r + i] = v;
+  }
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    bvec[i] = atomicAdd(&S.acc[n_mat + i], 0.0);
+    s_rhs[i] = bvec[i];
+  }
+  if (threadIdx.x == 0) s_bb = atomicAdd(&S.acc[n_mat + r], 0.0);
+  __syncthreads();
+  for (int e = threadIdx.x; e < n_acc; e += blockDim.x) S.acc[e] = 0.0;
+  if (threadIdx.x == 0) S.counter[0] = 0u;
+  __syncthreads();
+  bool ok = chol_solve(A, bvec, r);
+  if (!ok) {
+    // one retry with the diagonal shifted by 1e-12 tr(A) / r
+    if (threadIdx.x == 0) {
+      double tr = 0;
+      for (int i = 0; i < r; ++i) tr += A_keep[i * r + i];
+      s_shift = 1e-12 * tr / r;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x)
+      A[e] = A_keep[e] + ((e / r) == (e % r) ? s_shift : 0.0);
+    for (int i = threadIdx.x; i < r; i += blockDim.x) bvec[i] = s_rhs[i];
+    __syncthreads();
+    ok = chol_solve(A, bvec, r);
+    if (!ok) {
+      if (threadIdx.x == 0) raise_status(R.status, STATUS_CHOLESKY);
+      for (int i = threadIdx.x; i < r; i += blockDim.x) bvec[i] = 0.0;  // no step
+      __syncthreads();
+    }
+  }
+  if (mode == NE_VEL) {
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      const double v = bvec[i];
+      S.vh_new[i] = v;
+      if (projection == 1) {
+        // velocity-only projection (Alg. 7): xhat_{n+1} = xhat_n + dt vhat_{n+1}
+        S.xk[i] = S.xh[i] + (double)R.dt * v;
+      } else {
+        // Gauss-Newton initial guess 2 xhat_n - xhat_{n-1}
+        const double g = 2.0 * S.xh[i] - S.xh_prev[i];
+        S.xk[i] = g;
+        S.xk32[i] = (float)g;
+        S.dk32[i] = (float)(S.xh[i] - g);
+      }
+    }
+  } else {
+    // GN step: J^T J delta = J^T b with b = -residual
+    __shared__ double s_slope, s_dn;
+    if (threadIdx.x == 0) {
+      double sl = 0, dn = 0;
+      for (int i = 0; i < r; ++i) {
+        sl += s_rhs[i] * bvec[i];
+        dn += bvec[i] * bvec[i];
+      }
+      s_slope = -2.0 * sl;   // d/dalpha |res + alpha J delta|^2 at 0 = 2 res^T J delta = -2 b^T J delta
+      s_dn = sqrt(dn);
+      S.scal[0] = s_bb;      // f0 = |res|^2
+      S.scal[1] = s_slope;
+      S.scal[2] = s_dn;
+    }
+    for (int i = threadIdx.x; i < r; i += blockDim.x) S.delta[i] = bvec[i];
+    __syncthreads();
+    const float* base32 = (mode == NE_FIT) ? S.xk32 : S.xh32;
+    for (int e = threadIdx.x; e < kLS * r; e += blockDim.x) {
+      const int m = e / r, i = e % r;
+      const double alpha = ldexp(1.0, -m);
+      const double basev = (mode == NE_FIT) ? S.xk[i] : S.xh[i];
+      S.ls_base32[e] = base32[i];
+      S.ls_dir32[e] = (float)((S.xk[i] - basev) + alpha * bvec[i]);
+    }
+  }
+}
+
+// Line-search objectives f(alpha_m) = |g(xhat_k + alpha_m delta) - x_trial|^2 for all
+// trials at once; dec = decoder output (2, cap, d) with kinds [primal, secant] over
+// kLS x nP points (trial m, sample p at m * nP + p).  The last CTA picks the
+// first trial meeting Armijo and updates the iterate; on the final iteration it
+// also commits the step.
+__global__ void __launch_bounds__(kNormBlock) rom_linesearch(RomDev R, RomSolve S, const float* __restrict__ dec,
+                                                             int64_t cap, int mode, const float* __restrict__ target,
+                                                             int final_iter, double armijo_c, int n_rows_override) {
+  const int d = R.d, r = R.r;
+  const int nP = n_rows_override > 0 ? n_rows_override : R.counts[0];
+  const int per = nP * d;
+  __shared__ double s_red[kNormBlock / 32];
+  __shared__ bool s_last;
+  for (int m = blockIdx.x; m < kLS; m += gridDim.x) {
+    double s = 0.0;
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int p = e / d, a = e % d;
+      const size_t pt = (size_t)m * nP + p;
+      double res;
+      if (mode == NE_FIT) {
+        // secant from the iterate: g(xk + alpha delta) = g(xk) + secant; residual vs target
+        res = (double)dec[((size_t)cap + pt) * d + a] + (double)dec[pt * d + a] - (double)target[(size_t)p * d + a];
+      } else {
+        // g(xhat_k + alpha delta) - x_trial = secant_from_xhat_n - dt v_trial
+        res = (double)dec[((size_t)cap + pt) * d + a] - (double)R.dt * R.v_trial[(size_t)p * d + a];
+      }
+      s = fma(res, res, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0;
+      for (int w = 0; w < kNormBlock / 32; ++w) tot += s_red[w];
+      S.fls[m] = tot;
+    }
+    __syncthreads();
+  }
+  __threadfence();
+  if (threadIdx.x == 0) s_last = atomicAdd(&S.counter[1], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  __shared__ int s_pick;
+  if (threadIdx.x == 0) {
+    S.counter[1] = 0u;
+    const double f0 = S.scal[0], slope = S.scal[1], dn = S.scal[2];
+    int pick = -1;
+    for (int m = 0; m < kLS; ++m) {
+      const double f = *((volatile double*)&S.fls[m]);
+      if (f <= f0 + armijo_c * ldexp(1.0, -m) * slope) {
+        pick = m;
+        break;
+      }
+    }
+    // no trial decreased the objective: a failure only if the step is not
+    // negligible and the linear model promised a decrease well above the FP32
+    // resolution of the objective (-slope / 2 = |J delta|^2 > 1e-3 f0);
+    // otherwise the iterate has converged
+    double xn = 0;
+    for (int i = 0; i < r; ++i) xn += S.xk[i] * S.xk[i];
+    if (pick < 0 && dn > 1e-8 * (1.0 + sqrt(xn)) && -0.5 * slope > 1e-3 * f0)
+      raise_status(R.status, STATUS_GN_NO_DECREASE);
+    s_pick = pick;
+  }
+  __syncthreads();
+  const int pick = s_pick;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    double xk = S.xk[i];
+    if (pick >= 0) xk += ldexp(1.0, -pick) * S.delta[i];
+    S.xk[i] = xk;
+    S.xk32[i] = (float)xk;
+    const double basev = (mode == NE_FIT) ? xk : S.xh[i];
+    S.dk32[i] = (float)(basev - xk);
+  }
+  if (final_iter && mode != NE_FIT) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      S.xh_prev[i] = S.xh[i];
+      S.xh[i] = S.xk[i];
+      S.vh[i] = S.vh_new[i];
+      S.xh32[i] = (float)S.xk[i];
+      S.vh32[i] = (float)S.vh_new[i];
+    }
+    if (threadIdx.x == 0) *R.step += 1;
+  }
+}
+
+// Commit of the velocity-only projection (Alg. 7).
+__global__ void rom_commit_velocity_only(RomDev R, RomSolve S) {
+  for (int i = threadIdx.x; i < R.r; i += blockDim.x) {
+    S.xh_prev[i] = S.xh[i];
+    S.xh[i] = S.xk[i];
+    S.vh[i] = S.vh_new[i];
+    S.xh32[i] = (float)S.xk[i];
+    S.vh32[i] = (float)S.vh_new[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *R.step += 1;
+}
+
+// Accumulated position error of Section 5: acc[0] += sum |a - b|^2, acc[1] += sum |b|^2 (FP64).
+__global__ void metric_accumulate_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
+                                         double* acc) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = a[i], y = b[i];
+    s0 = fma(x - y, x - y, s0);
+    s1 = fma(y, y, s1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&acc[0], s0);
+    atomicAdd(&acc[1], s1);
+  }
+}
+
+}  // namespace mpmrom
+
+// ============================================================================
+// Host runtime and C ABI
+// ============================================================================
+using namespace mpmrom;
+
+struct rom_ctx {
+  rom_config cfg{};
+  const mpm_decoder* dec = nullptr;
+  int d = 0, r = 0, P = 0, k = 0, n = 0;
+  int n_sm = 0;
+  RomDev dv{};
+  RomSolve sv{};
+  // device buffers
+  float* X = nullptr;
+  float* x_all = nullptr;
+  int32_t* qlist = nullptr;
+  int32_t* counts = nullptr;
+  int32_t* nodes = nullptr;
+  uint32_t* stamp = nullptr;
+  float4* grid = nullptr;
+  float* v_trial = nullptr;
+  float* x_trial = nullptr;
+  int64_t* step = nullptr;
+  uint32_t* status = nullptr;
+  int32_t* nP_all = nullptr;    // device constant P (decode-all point count)
+  float* outQ = nullptr;        // (d + 2, P, d)
+  float* outS = nullptr;        // (r + 2, k, d)
+  float* outLS = nullptr;       // (2, kLS * k, d) (capacity kLS * P for the fit)
+  double* solve_mem = nullptr;
+  float* solve32 = nullptr;
+  uint32_t* counters = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
+  const int d = c->d, r = c->r;
+  // 1. decode all particles at xhat_n
+  int k_primal[1] = {0};
+  mpm_status st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, c->P, c->sv.xh32, nullptr, k_primal, 1,
+                                     c->x_all, s);
+  if (st != MPM_OK) return st;
+  // 2. samples, basis set, neighbours
+  if (d == 2)
+    rom_select<2><<<1, 1024, 0, s>>>(c->dv);
+  else
+    rom_select<3><<<1, 1024, 0, s>>>(c->dv);
+  MPM_CUDA_TRY(cudaGetLastError());
+  // 3. F and v at the quadrature points Q
+  int kq[8];
+  kq[0] = 0;
+  for (int a = 0; a < d; ++a) kq[1 + a] = 1 + a;
+  kq[1 + d] = 1000;  // JVP along vhat_n
+  st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 1, 1, c->P, c->sv.xh32, c->sv.vh32, kq, d + 2, c->outQ,
+                          s);
+  if (st != MPM_OK) return st;
+  // 4. local P2G onto I, 5. grid update + G2P to the samples
+  const int b_q = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 4));
+  const int M = c->cfg.material, T = c->cfg.transfer;
+#define P2G_CASE(dd, mm, tt)                                                          \
+  if (d == dd && M == mm && T == tt) rom_p2g<dd, mm, tt><<<b_q, 256, 0, s>>>(c->dv, c->outQ, c->P);
+  P2G_CASE(2, 0, 0) P2G_CASE(2, 0, 1) P2G_CASE(2, 1, 0) P2G_CASE(2, 1, 1)
+  P2G_CASE(3, 0, 0) P2G_CASE(3, 0, 1) P2G_CASE(3, 1, 0) P2G_CASE(3, 1, 1)
+#undef P2G_CASE
+  MPM_CUDA_TRY(cudaGetLastError());
+  const int b_s = std::max(1, ceil_div(c->k, 128));
+  if (d == 2)
+    rom_g2p<2><<<b_s, 128, 0, s>>>(c->dv);
+  else
+    rom_g2p<3><<<b_s, 128, 0, s>>>(c->dv);
+  MPM_CUDA_TRY(cudaGetLastError());
+  // 6. velocity projection: J = dg/dxhat at (X^P, xhat_n)
+  int ks[kMaxRl + 2];
+  ks[0] = 0;
+  for (int j = 0; j < r; ++j) ks[1 + j] = 1 + d + j;
+  st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xh32, nullptr, ks, r + 1, c->outS, s);
+  if (st != MPM_OK) return st;
+  const int b_ne = std::max(1, std::min(ceil_div((int64_t)c->k * d, 64), 64));
+  rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_VEL, nullptr, c->cfg.projection, 0);
+  MPM_CUDA_TRY(cudaGetLastError());
+  if (c->cfg.projection == 1) {
+    rom_commit_velocity_only<<<1, 64, 0, s>>>(c->dv, c->sv);
+    MPM_CUDA_TRY(cudaGetLastError());
+    return MPM_OK;
+  }
+  // 7. Gauss-Newton on the positions
+  ks[1 + r] = 1001;  // secant g(xhat_n) - g(xhat_k)
+  int kls[2] = {0, 1001};
+  for (int it = 0; it < c->cfg.gn_iters; ++it) {
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xk32, c->sv.dk32, ks, r + 2,
+                            c->outS, s);
+    if (st != MPM_OK) return st;
+    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_GN, nullptr, 0, 0);
+    MPM_CUDA_TRY(cudaGetLastError());
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, kLS, (int64_t)kLS * c->k, c->sv.ls_base32,
+                            c->sv.ls_dir32, kls, 2, c->outLS, s);
+    if (st != MPM_OK) return st;
+    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, (int64_t)kLS * c->k, NE_GN, nullptr,
+                                              it == c->cfg.gn_iters - 1, 1e-4, 0);
+    MPM_CUDA_TRY(cudaGetLastError());
+  }
+  return MPM_OK;
+}
+
+template <typename T>
+mpm_status ralloc(T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return set_error(MPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  e = cudaMemset(*p, 0, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return set_error(MPM_ECUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+  return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float* X, int64_t n_particles,
+                      rom_ctx** out) {
+  MPM_CHECK_ARG(cfg && dec && X && out, "null argument");
+  *out = nullptr;
+  MPM_CHECK_ARG(cfg->dim == 2 || cfg->dim == 3, "dim must be 2 or 3");
+  MPM_CHECK_ARG(n_particles >= 1 && n_particles < (1 << 30), "particle count");
+  MPM_CHECK_ARG(cfg->n_samples >= 1, "n_samples >= 1");
+  MPM_CHECK_ARG(cfg->gn_iters >= 1 && cfg->gn_iters <= 16, "gn_iters in [1, 16]");
+  MPM_CHECK_ARG(cfg->projection == 0 || cfg->projection == 1, "projection: 0 position-velocity, 1 velocity-only");
+  MPM_CHECK_ARG(cfg->latent_dim >= 1 && cfg->latent_dim <= kMaxRl, "latent dimension in [1, 64]");
+  MPM_CHECK_ARG(cfg->n_grid >= 8, "n_grid");
+  MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
+  MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
+  auto* c = new rom_ctx();
+  c->cfg = *cfg;
+  c->dec = dec;
+  c->d = cfg->dim;
+  c->r = cfg->latent_dim;
+  c->P = (int)n_particles;
+  c->k = std::min<int>(cfg->n_samples, c->P);
+  c->n = cfg->n_grid;
+  int devn = 0;
+  cudaGetDevice(&devn);
+  cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, devn);
+  const int d = c->d, r = c->r, P = c->P, k = c->k;
+  const int NS = d == 2 ? 9 : 27;
+  const size_t gn = d == 2 ? (size_t)c->n * c->n : (size_t)c->n * c->n * c->n;
+  mpm_status st;
+  auto fail = [&](mpm_status s) {
+    rom_destroy(c);
+    return s;
+  };
+  if ((st = ralloc(&c->X, (size_t)P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->x_all, (size_t)P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->qlist, P)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->counts, 4)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->nodes, (size_t)k * NS)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->stamp, gn)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->grid, gn)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->v_trial, (size_t)P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->x_trial, (size_t)P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->step, 1)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->status, 1)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->nP_all, 1)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->outQ, (size_t)(d + 2) * P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->outS, (size_t)(r + 2) * P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->outLS, (size_t)2 * kLS * P * d)) != MPM_OK) return fail(st);
+  const int n_acc = r * (r + 1) / 2 + r + 1;
+  const size_t n64 = 6 * (size_t)r + 3 + n_acc + kLS;
+  if ((st = ralloc(&c->solve_mem, n64)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->solve32, (size_t)4 * r + 2 * kLS * r)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->counters, 2)) != MPM_OK) return fail(st);
+  MPM_CUDA_TRY(cudaMemcpy(c->X, X, sizeof(float) * P * d, cudaMemcpyDefault));
+  MPM_CUDA_TRY(cudaMemcpy(c->nP_all, &c->P, sizeof(int32_t), cudaMemcpyHostToDevice));
+  RomDev& v = c->dv;
+  v.d = d;
+  v.r = r;
+  v.P = P;
+  v.n = c->n;
+  v.k = k;
+  v.dx = cfg->dx;
+  v.inv_dx = (float)(1.0 / cfg->dx);
+  v.dt = cfg->dt;
+  for (int a = 0; a < 3; ++a) v.g[a] = cfg->gravity[a];
+  v.bc = cfg->bc;
+  v.bc_width = cfg->bc_width;
+  v.mass = cfg->rho * cfg->p_vol;
+  v.vol = cfg->p_vol;
+  const double E = cfg->E, nu = cfg->nu;
+  v.mu = (float)(E / (2 * (1 + nu)));
+  v.lam = (float)(E * nu / ((1 + nu) * (1 - 2 * nu)));
+  v.seed = cfg->seed;
+  v.inst = cfg->instance;
+  v.X = c->X;
+  v.x_all = c->x_all;
+  v.qlist = c->qlist;
+  v.counts = c->counts;
+  v.nodes = c->nodes;
+  v.stamp = c->stamp;
+  v.grid = c->grid;
+  v.v_trial = c->v_trial;
+  v.x_trial = c->x_trial;
+  v.step = c->step;
+  v.status = c->status;
+  RomSolve& S = c->sv;
+  double* m = c->solve_mem;
+  S.xh = m;
+  S.xh_prev = m + r;
+  S.vh = m + 2 * r;
+  S.vh_new = m + 3 * r;
+  S.xk = m + 4 * r;
+  S.delta = m + 5 * r;
+  S.scal = m + 6 * r;
+  S.acc = m + 6 * r + 3;
+  S.fls = S.acc + n_acc;
+  S.counter = c->counters;
+  float* f = c->solve32;
+  S.xh32 = f;
+  S.vh32 = f + r;
+  S.xk32 = f + 2 * r;
+  S.dk32 = f + 3 * r;
+  S.ls_base32 = f + 4 * r;
+  S.ls_dir32 = f + 4 * r + kLS * r;
+  MPM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  *out = c;
+  return MPM_OK;
+}
+
+void rom_destroy(rom_ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  cudaFree(c->X);
+  cudaFree(c->x_all);
+  cudaFree(c->qlist);
+  cudaFree(c->counts);
+  cudaFree(c->nodes);
+  cudaFree(c->stamp);
+  cudaFree(c->grid);
+  cudaFree(c->v_trial);
+  cudaFree(c->x_trial);
+  cudaFree(c->step);
+  cudaFree(c->status);
+  cudaFree(c->nP_all);
+  cudaFree(c->outQ);
+  cudaFree(c->outS);
+  cudaFree(c->outLS);
+  cudaFree(c->solve_mem);
+  cudaFree(c->solve32);
+  cudaFree(c->counters);
+  delete c;
+}
+
+mpm_status rom_set_state(rom_ctx* c, const double* xhat, const double* vhat, const double* xhat_prev, int64_t step,
+                         void* stream) {
+  MPM_CHECK_ARG(c && xhat && vhat && xhat_prev, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int r = c->r;
+  std::vector<double> h(3 * r);
+  MPM_CUDA_TRY(cudaMemcpyAsync(h.data(), xhat, sizeof(double) * r, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(h.data() + r, vhat, sizeof(double) * r, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(h.data() + 2 * r, xhat_prev, sizeof(double) * r, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<float> h32(2 * r);
+  for (int i = 0; i < r; ++i) {
+    h32[i] = (float)h[i];
+    h32[r + i] = (float)h[r + i];
+  }
+  MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.xh, h.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.vh, h.data() + r, sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.xh_prev, h.data() + 2 * r, sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.xh32, h32.data(), sizeof(float) * r, cudaMemcpyHostToDevice, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.vh32, h32.data() + r, sizeof(float) * r, cudaMemcpyHostToDevice, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(c->step, &step, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return MPM_OK;
+}
+
+mpm_status rom_get_state(rom_ctx* c, double* xhat, double* vhat, double* xhat_prev, int64_t* step, void* stream) {
+  MPM_CHECK_ARG(c, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int r = c->r;
+  if (xhat) MPM_CUDA_TRY(cudaMemcpyAsync(xhat, c->sv.xh, sizeof(double) * r, cudaMemcpyDefault, s));
+  if (vhat) MPM_CUDA_TRY(cudaMemcpyAsync(vhat, c->sv.vh, sizeof(double) * r, cudaMemcpyDefault, s));
+  if (xhat_prev) MPM_CUDA_TRY(cudaMemcpyAsync(xhat_prev, c->sv.xh_prev, sizeof(double) * r, cudaMemcpyDefault, s));
+  if (step) MPM_CUDA_TRY(cudaMemcpyAsync(step, c->step, sizeof(int64_t), cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return MPM_OK;
+}
+
+mpm_status rom_step(rom_ctx* c, int n_steps, void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  MPM_CHECK_ARG(n_steps >= 0, "n_steps >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!c->graph) {
+    // capture one step on a private stream; every launch reads its dynamic
+    // values (step counter, set sizes, latent state) from device memory
+    cudaGraph_t g = nullptr;
+    MPM_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    mpm_status st = rom_launch_step(c, c->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st != MPM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return set_error(MPM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_error(MPM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  for (int i = 0; i < n_steps; ++i) MPM_CUDA_TRY(cudaGraphLaunch(c->graph, s));
+  return MPM_OK;
+}
+
+mpm_status rom_status_word(rom_ctx* c, uint32_t* out, int clear, void* stream) {
+  MPM_CHECK_ARG(c && out, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t h = 0;
+  MPM_CUDA_TRY(cudaMemcpyAsync(&h, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (clear) MPM_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(uint32_t), s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = h;
+  return MPM_OK;
+}
+
+mpm_status rom_debug(rom_ctx* c, int32_t* qlist, int32_t* counts, float* x_all, float* v_trial, float* x_trial,
+                     void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (counts) MPM_CUDA_TRY(cudaMemcpyAsync(counts, c->counts, sizeof(int32_t) * 3, cudaMemcpyDefault, s));
+  if (qlist) MPM_CUDA_TRY(cudaMemcpyAsync(qlist, c->qlist, sizeof(int32_t) * c->P, cudaMemcpyDefault, s));
+  if (x_all) MPM_CUDA_TRY(cudaMemcpyAsync(x_all, c->x_all, sizeof(float) * c->P * c->d, cudaMemcpyDefault, s));
+  if (v_trial) MPM_CUDA_TRY(cudaMemcpyAsync(v_trial, c->v_trial, sizeof(float) * c->k * c->d, cudaMemcpyDefault, s));
+  if (x_trial) MPM_CUDA_TRY(cudaMemcpyAsync(x_trial, c->x_trial, sizeof(float) * c->k * c->d, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return MPM_OK;
+}
+
+mpm_status rom_decode_all(rom_ctx* c, float* x_out, void* stream) {
+  MPM_CHECK_ARG(c && x_out, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int k_primal[1] = {0};
+  mpm_status st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, c->P, c->sv.xh32, nullptr, k_primal, 1,
+                                     x_out, s);
+  return st;
+}
+
+mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int iters, void* stream) {
+  MPM_CHECK_ARG(c && target && V0, "null argument");
+  MPM_CHECK_ARG(iters >= 1 && iters <= 100, "iters in [1, 100]");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = c->d, r = c->r, P = c->P;
+  // Gauss-Newton over all particles (Eq. essentialSpecInt, first line), from xhat = 0
+  float* tgt = nullptr;
+  float* vel = nullptr;
+  MPM_CUDA_TRY(cudaMalloc((void**)&tgt, sizeof(float) * P * d));
+  MPM_CUDA_TRY(cudaMalloc((void**)&vel, sizeof(float) * P * d));
+  MPM_CUDA_TRY(cudaMemcpyAsync(tgt, target, sizeof(float) * P * d, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(vel, V0, sizeof(float) * P * d, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->sv.xk, 0, sizeof(double) * r, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->sv.xk32, 0, sizeof(float) * r, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->sv.dk32, 0, sizeof(float) * r, s));
+  int ks[kMaxRl + 2];
+  ks[0] = 0;
+  for (int j = 0; j < r; ++j) ks[1 + j] = 1 + d + j;
+  int kls[2] = {0, 1001};
+  const int b_ne = std::max(1, std::min(ceil_div((int64_t)P * d, 64), c->n_sm));
+  mpm_status st = MPM_OK;
+  for (int it = 0; it < iters && st == MPM_OK; ++it) {
+    st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, P, c->sv.xk32, nullptr, ks, r + 1, c->outS, s);
+    if (st != MPM_OK) break;
+    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, P, NE_FIT, tgt, 0, P);
+    // trials: secant from the iterate; base rows hold the iterate
+    st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, kLS, (int64_t)kLS * P, c->sv.ls_base32, c->sv.ls_dir32,
+                            kls, 2, c->outLS, s);
+    if (st != MPM_OK) break;
+    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, (int64_t)kLS * P, NE_FIT, tgt, 0, 1e-4, P);
+  }
+  // velocity fit at the fitted xhat_0 (Eq. essentialSpecInt, second line)
+  if (st == MPM_OK) {
+    st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, P, c->sv.xk32, nullptr, ks, r + 1, c->outS, s);
+  }
+  if (st == MPM_OK) {
+    // NE_VEL reads v_trial: stage V0 there; rows = all particles
+    MPM_CUDA_TRY(cudaMemcpyAsync(c->v_trial, vel, sizeof(float) * P * d, cudaMemcpyDeviceToDevice, s));
+    // solve J^T J vhat = J^T V0 (projection flag 1 keeps xk: the commit below sets the state)
+    MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.xh, c->sv.xk, sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
+    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, P, NE_VEL, nullptr, 1, P);
+  }
+  cudaFree(tgt);
+  cudaFree(vel);
+  MPM_CUDA_TRY(cudaGetLastError());
+  if (st != MPM_OK) return st;
+  // xhat_0 = fitted, vhat_0 = velocity fit, xhat_{-1} = xhat_0 - dt vhat_0
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> xh(r), vh(r), xp(r);
+  MPM_CUDA_TRY(cudaMemcpy(xh.data(), c->sv.xh, sizeof(double) * r, cudaMemcpyDeviceToHost));
+  MPM_CUDA_TRY(cudaMemcpy(vh.data(), c->sv.vh_new, sizeof(double) * r, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < r; ++i) xp[i] = xh[i] - (double)c->cfg.dt * vh[i];
+  return rom_set_state(c, xh.data(), vh.data(), xp.data(), 0, stream);
+}
+
+mpm_status metric_accumulate(const float* a, const float* b, int64_t n, double* acc, void* stream) {
+  MPM_CHECK_ARG(a && b && acc, "null argument");
+  MPM_CHECK_ARG(n >= 0, "n >= 0");
+  if (n == 0) return MPM_OK;
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 4));
+  metric_accumulate_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(a, b, n, acc);
+  MPM_CUDA_TRY(cudaGetLastError());
+  return MPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,880 @@
+// Decoder training (Section 4.2 loss, Appendix B optimiser) on sm_103a.
+//
+// Per minibatch of B (snapshot, particle) pairs, rows per point
+// [primal, dg/dX_0 .. dg/dX_{d-1}, JVP along (xhat_{n+1} - xhat_n) / dt_snap]:
+//   train_sample     counter-based draw of the pairs (SplitMix64 of
+//                    (seed, step, i), uniform over all pairs), gather of X,
+//                    latents, JVP directions and targets
+//   decoder_tc       forward (tensor cores), storing every hidden layer's
+//                    pre-activations (FP32) and activations (BF16) feature-major
+//   train_bwd_tc     loss residuals and output-layer gradients (FP32), then the
+//                    reverse sweep: z_bar = act'(z) h_bar + act''(z) sum_j zdot_j t_bar_j
+//                    for primal rows, zdot_bar = act'(z) t_bar for tangent rows
+//                    (exchanged through shared memory), next adjoint rows by a
+//                    tcgen05 GEMM with the transposed weights resident in shared
+//                    memory; layer 0 and the latent adjoints in FP32
+//   train_dw_gemm    weight gradients of the square layers, dW = Zbar^T A, as
+//                    split-K tcgen05 GEMMs over all rows (both operands stored
+//                    row-contiguous, i.e. K-major), FP32 atomics across splits
+//   train_dw0        first-layer weight gradient (K = d + r, FP32)
+//   train_lat_scatter latent-table gradient (snapshot n gets d/dxhat_n of its
+//                    own rows and -u_bar / dt; its successor gets +u_bar / dt)
+//   train_adam       Adam on the FP32 master parameters and the latent table,
+//                    learning rate decaying geometrically lr0 -> lr1
+//   + re-pack of the BF16 weight images (forward and transposed)
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "decoder_common.cuh"
+
+namespace mpmrom {
+mpm_status decoder_launch_train(const mpm_decoder* dec, const float* X, const float* latents, const float* dirs,
+                                const int* kinds, int R, int64_t n, float* out, float* zstore,
+                                __nv_bfloat16* astore, int64_t rows_total, cudaStream_t s);
+
+__device__ __forceinline__ uint64_t tr_splitmix(uint64_t state, uint64_t k) {
+  uint64_t z = state + 0x9E3779B97F4A7C15ull * (k + 1ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float act_d2(int act, float z) { return act == 0 ? (z > 0.f ? 0.f : __expf(z)) : 0.f; }
+
+struct Store {
+  int d, r;
+  int n_snap;
+  const int64_t* snap_base;   // (n_snap + 1) offsets of each snapshot's particle rows
+  const int32_t* snap_inst;
+  const int32_t* snap_next;
+  const int64_t* inst_off;    // particle offsets into X
+  const float* X;
+  const float* x;
+  const float* v;
+  const float* F;
+};
+
+struct Batch {
+  int64_t B;
+  float* X;        // (B, d)
+  float* xh;       // (B, r)
+  float* u;        // (B, r)
+  float* tx;       // (B, d)
+  float* tv;       // (B, d)
+  float* tF;       // (B, d, d)
+  float* mask;     // (B)
+  int32_t* snap;   // (B)
+  int32_t* next;   // (B)
+  int32_t* part;   // (B) particle index within its instance
+};
+
+// ------------------------------------------------------------- sampler
+__global__ void train_sample(Store st, Batch b, const float* latents, float dt_snap, uint64_t seed,
+                             const int64_t* step, double* loss) {
+  const int d = st.d, r = st.r;
+  const int64_t total = st.snap_base[st.n_snap];
+  const uint64_t s0 = tr_splitmix(seed, (uint64_t)*step);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *loss = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b.B; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t h = tr_splitmix(s0, (uint64_t)i);
+    const int64_t g = (int64_t)(h % (uint64_t)total);
+    // snapshot containing pair g: largest s with snap_base[s] <= g
+    int lo = 0, hi = st.n_snap - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (st.snap_base[mid] <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const int s = lo;
+    const int64_t local = g - st.snap_base[s];
+    const int inst = st.snap_inst[s];
+    const int64_t pidx = st.inst_off[inst] + local;
+    const int nx = st.snap_next[s];
+    b.snap[i] = s;
+    b.next[i] = nx;
+    b.part[i] = (int32_t)local;
+    for (int a = 0; a < d; ++a) {
+      b.X[i * d + a] = st.X[pidx * d + a];
+      b.tx[i * d + a] = st.x[g * d + a];
+      b.tv[i * d + a] = st.v[g * d + a];
+      for (int c = 0; c < d; ++c) b.tF[(i * d + a) * d + c] = st.F[(g * d + a) * d + c];
+    }
+    b.mask[i] = nx >= 0 ? 1.f : 0.f;
+    for (int j = 0; j < r; ++j) {
+      const float xs = latents[(int64_t)s * r + j];
+      b.xh[i * r + j] = xs;
+      b.u[i * r + j] = nx >= 0 ? (latents[(int64_t)nx * r + j] - xs) / dt_snap : 0.f;
+    }
+  }
+}
+
+// ------------------------------------------------------------- backward
+struct BwdArgs {
+  int d, r, n_hidden, n_tc, act, R, Pt;
+  int64_t n, rows_total;
+  const float* W0;      // (W, d + r)
+  const float* Wout;    // (d, W)
+  const float* norm;
+  const float* zstore;
+  const __nv_bfloat16* astore;
+  const uint8_t* wtimg;
+  const float* fwd;     // (R, n, d)
+  Batch b;
+  float lamF, lamv;
+  __nv_bfloat16* zbstore;   // (n_tc, W, rows)
+  float* zb0;               // (W, rows)
+  float* gparams;
+  int64_t gW0_off, gb0_off, gWout_off, gbout_off;
+  int64_t gb_off[kMaxTC + 1];   // bias-gradient offsets of hidden layers 0..n_hidden-1
+  float* g_lat_pt;          // (n, r)
+  float* g_u_pt;            // (n, r)
+  double* loss;
+  uint32_t* status;
+};
+
+constexpr int kExchRows = 104;
+
+__global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* wt = smem;                                 // n_tc x 32 KB (transposed square weights)
+  uint8_t* atile = smem + kMaxTC * kLayerBytes;       // 32 KB
+  float* exch = (float*)(atile + kLayerBytes);        // kExchRows x 128
+  float* sy = exch + kExchRows * kW;                  // 128 x 3
+  float* sbias = sy + 128 * 3;                        // 128
+  DecSmemTail* tail = (DecSmemTail*)(sbias + kW);
+  __shared__ double s_loss[4];
+  const int t = threadIdx.x, warp = t >> 5;
+  const int d = a.d, r = a.r, R = a.R, Pt = a.Pt;
+
+  if (t == 0) {
+    tc::mbar_init(&tail->bar_w, 1);
+    tc::mbar_init(&tail->bar_mma, 1);
+    tail->abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc<kW>(&tail->tmem);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tail->tmem;
+  if (t == 0 && a.n_tc > 0) {
+    tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(a.n_tc * kLayerBytes));
+    for (int l = 0; l < a.n_tc; ++l)
+      tc::bulk_g2s(wt + l * kLayerBytes, a.wtimg + (size_t)l * kLayerBytes, kLayerBytes, &tail->bar_w);
+  }
+  if (a.n_tc > 0 && !tc::mbar_wait(&tail->bar_w, 0)) {
+    raise_status(a.status, STATUS_TIMEOUT);
+    atomicExch(&tail->abort, 1);
+  }
+  sbias[t] = 0.f;
+  __syncthreads();
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kW);
+  uint32_t mma_phase = 0;
+  const int64_t n_tiles = (a.n + Pt - 1) / Pt;
+  const float* scale = a.norm + 3 * d;
+  double my_loss = 0.0;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !tail->abort; tile += gridDim.x) {
+    const int64_t row0 = tile * 128;
+    const int k = t / Pt, q = t % Pt;
+    const int64_t p = tile * Pt + q;
+    const bool valid = (k < R) && (p < a.n);
+    const int cls = !valid ? -1 : (k == 0 ? 0 : 1);
+    const int64_t gr = row0 + t, gp = row0 + q;
+    // ---- output layer: residual adjoints ybar (FP32)
+    float ybar[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+      const float* o = a.fwd + ((int64_t)k * a.n + p) * d;
+      for (int i = 0; i < d; ++i) {
+        float e, w;
+        if (k == 0) {
+          e = o[i] - a.b.tx[p * d + i];
+          w = 1.f;
+        } else if (k <= d) {
+          e = o[i] - a.b.tF[(p * d + i) * d + (k - 1)];
+          w = a.lamF;
+        } else {
+          e = a.b.mask[p] * (o[i] - a.b.tv[p * d + i]);
+          w = a.lamv;
+        }
+        my_loss += (double)w * e * e;
+        ybar[i] = 2.f * w * e * scale[i] / (float)a.n;
+      }
+    }
+    for (int i = 0; i < 3; ++i) sy[t * 3 + i] = ybar[i];
+    __syncthreads();
+    {
+      // dWout[i][f] = sum_rows ybar_i a_last[f];  thread t = feature f
+      const __nv_bfloat16* al = a.astore + (int64_t)(a.n_hidden - 1) * kW * a.rows_total + (int64_t)t * a.rows_total + row0;
+      float acc[3] = {0.f, 0.f, 0.f};
+      for (int c = 0; c < 128; c += 8) {
+        const uint4 u = *reinterpret_cast<const uint4*>(al + c);
+        const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float av = __bfloat162float(hv[j]);
+          for (int i = 0; i < d; ++i) acc[i] = fmaf(sy[(c + j) * 3 + i], av, acc[i]);
+        }
+      }
+      for (int i = 0; i < d; ++i) atomicAdd(&a.gparams[a.gWout_off + i * kW + t], acc[i]);
+      if (t < d) {
+        float sb = 0.f;
+        for (int q2 = 0; q2 < Pt; ++q2) sb += sy[q2 * 3 + t];
+        atomicAdd(&a.gparams[a.gbout_off + t], sb);
+      }
+    }
+    // ---- reverse sweep over the hidden layers
+    float hin[40];
+    for (int j = 0; j < r; ++j) hin[j] = 0.f;
+    for (int l = a.n_hidden - 1; l >= 0; --l) {
+      const bool from_tmem = (l < a.n_hidden - 1);
+      if (from_tmem) {
+        if (!tc::mbar_wait(&tail->bar_mma, mma_phase)) {
+          raise_status(a.status, STATUS_TIMEOUT);
+          atomicExch(&tail->abort, 1);
+        }
+        mma_phase ^= 1u;
+        tc::tc_fence_after();
+      }
+      __syncthreads();
+      if (tail->abort) break;
+      const float* zl = a.zstore + (int64_t)l * kW * a.rows_total;
+      for (int ch = 0; ch < kW / 32; ++ch) {
+        float hb[32];
+        if (from_tmem) {
+          tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, hb);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            float s = 0.f;
+            for (int o = 0; o < d; ++o) s = fmaf(__ldg(&a.Wout[o * kW + ch * 32 + i]), ybar[o], s);
+            hb[i] = s;
+          }
+        }
+        float zb[32];
+        if (cls == 1) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int f = ch * 32 + i;
+            const float zp = zl[(int64_t)f * a.rows_total + gp];
+            const float zr = zl[(int64_t)f * a.rows_total + gr];
+            zb[i] = act_d1(a.act, zp) * hb[i];
+            exch[(t - Pt) * kW + f] = act_d2(a.act, zp) * zr * hb[i];
+          }
+        }
+        __syncthreads();
+        if (cls == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int f = ch * 32 + i;
+            const float zp = zl[(int64_t)f * a.rows_total + gp];
+            float s = act_d1(a.act, zp) * hb[i];
+            for (int kk = 1; kk < R; ++kk) s += exch[((kk - 1) * Pt + q) * kW + f];
+            zb[i] = s;
+            atomicAdd(&sbias[f], s);
+          }
+        } else if (cls < 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) zb[i] = 0.f;
+        }
+        if (l >= 1) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 8) store_bf16x8(atile, t, ch * 32 + j, zb + j);
+          __nv_bfloat16* zs = a.zbstore + (int64_t)(l - 1) * kW * a.rows_total + gr;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) zs[(int64_t)(ch * 32 + i) * a.rows_total] = __float2bfloat16_rn(zb[i]);
+        } else {
+          float* zs = a.zb0 + gr;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) zs[(int64_t)(ch * 32 + i) * a.rows_total] = zb[i];
+          if (cls >= 0) {
+            for (int j = 0; j < r; ++j) {
+              float s = 0.f;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) s = fmaf(__ldg(&a.W0[(ch * 32 + i) * (d + r) + d + j]), zb[i], s);
+              hin[j] += s;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      // bias gradient of layer l
+      atomicAdd(&a.gparams[a.gb_off[l] + t], sbias[t]);
+      sbias[t] = 0.f;
+      if (l >= 1) {
+        // next adjoint rows: h_bar_{l-1} = z_bar_l W_l  (B operand = W_l^T image)
+        tc::fence_async_smem();
+        tc::tc_fence_before();
+        __syncthreads();
+        if (t == 0) {
+          tc::tc_fence_after();
+          const uint32_t a_base = tc::smem_addr(atile), b_base = tc::smem_addr(wt + (l - 1) * kLayerBytes);
+#pragma unroll
+          for (int kk = 0; kk < kW / 16; ++kk) {
+            const uint32_t koff = (uint32_t)((kk >> 2) * (kW * 128) + (kk & 3) * 32);
+            tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + koff), tc::smem_desc_sw128(b_base + koff), idesc,
+                         kk > 0 ? 1u : 0u);
+          }
+          tc::mma_commit(&tail->bar_mma);
+        }
+      }
+    }
+    if (tail->abort) break;
+    // latent adjoints of this row
+    if (cls == 0) {
+      for (int j = 0; j < r; ++j) a.g_lat_pt[p * r + j] = hin[j];
+    } else if (cls == 1 && k == d + 1) {
+      for (int j = 0; j < r; ++j) a.g_u_pt[p * r + j] = hin[j];
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+  }
+  // loss (sum over rows of w e^2; the caller divides by n)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_loss += __shfl_down_sync(0xffffffffu, my_loss, o);
+  if ((t & 31) == 0) s_loss[warp] = my_loss;
+  __syncthreads();
+  if (t == 0) atomicAdd(a.loss, s_loss[0] + s_loss[1] + s_loss[2] + s_loss[3]);
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_free<kW>(tmem);
+}
+
+// ------------------------------------------- weight gradients (split-K GEMM)
+// dW_l[out][in] = sum_rows Zbar[out][row] A[in][row]; Zbar = zbstore[l], A = astore[l]
+// (the activations entering square layer l + 1).  Grid (n_tc, splits), 128 threads.
+__global__ void __launch_bounds__(128, 1) train_dw_gemm(const __nv_bfloat16* zbstore, const __nv_bfloat16* astore,
+                                                        int64_t rows_total, int64_t k_per_split, float* gparams,
+                                                        const int64_t* w_off, uint32_t* status) {
+  __shared__ __align__(1024) uint8_t sA[kW * 128];
+  __shared__ __align__(1024) uint8_t sB[kW * 128];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int l = blockIdx.x;
+  const __nv_bfloat16* Z = zbstore + (int64_t)l * kW * rows_total;
+  const __nv_bfloat16* A = astore + (int64_t)l * kW * rows_total;
+  const int64_t k0 = (int64_t)blockIdx.y * k_per_split;
+  const int64_t k1 = min(rows_total, k0 + k_per_split);
+  if (t == 0) {
+    tc::mbar_init(&bar, 1);
+    abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc<kW>(&tslot);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tslot;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kW);
+  uint32_t phase = 0;
+  bool any = false;
+  for (int64_t kb = k0; kb < k1; kb += 64) {
+    // stage 128 x 64 blocks of both operands (K-major, 128-byte swizzle)
+    for (int e = t; e < kW * 8; e += blockDim.x) {
+      const int row = e >> 3, c = e & 7;
+      uint4 za = make_uint4(0, 0, 0, 0), zb = make_uint4(0, 0, 0, 0);
+      if (kb + c * 8 < k1) {
+        za = *reinterpret_cast<const uint4*>(Z + (int64_t)row * rows_total + kb + c * 8);
+        zb = *reinterpret_cast<const uint4*>(A + (int64_t)row * rows_total + kb + c * 8);
+      }
+      *reinterpret_cast<uint4*>(sA + tc::sw128_offset(row, c * 8, kW)) = za;
+      *reinterpret_cast<uint4*>(sB + tc::sw128_offset(row, c * 8, kW)) = zb;
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc::tc_fence_after();
+      const uint32_t a_base = tc::smem_addr(sA), b_base = tc::smem_addr(sB);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + kk * 32), tc::smem_desc_sw128(b_base + kk * 32), idesc,
+                     (any || kk > 0) ? 1u : 0u);
+      tc::mma_commit(&bar);
+    }
+    any = true;
+    if (!tc::mbar_wait(&bar, phase)) {
+      raise_status(status, STATUS_TIMEOUT);
+      atomicExch(&abort_flag, 1);
+    }
+    phase ^= 1u;
+    tc::tc_fence_after();
+    __syncthreads();
+    if (abort_flag) break;
+  }
+  if (any && !abort_flag) {
+    float* g = gparams + w_off[l + 1];
+    for (int ch = 0; ch < kW / 32; ++ch) {
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) atomicAdd(&g[t * kW + ch * 32 + i], v[i]);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_free<kW>(tmem);
+}
+
+// First-layer weight gradient: dW0[f][j] = sum_rows zb0[f][row] in_row[j].
+__global__ void train_dw0(const float* zb0, int64_t rows_total, Batch b, int d, int r, int R, int Pt,
+                          const float* norm, float* gW0) {
+  const int f = blockIdx.x;
+  const int K = d + r;
+  float acc[40];
+  for (int j = 0; j < K; ++j) acc[j] = 0.f;
+  for (int64_t gr = threadIdx.x; gr < rows_total; gr += blockDim.x) {
+    const float z = zb0[(int64_t)f * rows_total + gr];
+    if (z == 0.f) continue;
+    const int64_t tile = gr / 128;
+    const int t = (int)(gr % 128), k = t / Pt, q = t % Pt;
+    const int64_t p = tile * Pt + q;
+    if (k >= R || p >= b.B) continue;
+    if (k == 0) {
+      for (int i = 0; i < d; ++i) acc[i] = fmaf(z, (b.X[p * d + i] - norm[i]) / norm[d + i], acc[i]);
+      for (int j = 0; j < r; ++j) acc[d + j] = fmaf(z, b.xh[p * r + j], acc[d + j]);
+    } else if (k <= d) {
+      acc[k - 1] = fmaf(z, 1.f / norm[d + k - 1], acc[k - 1]);
+    } else {
+      for (int j = 0; j < r; ++j) acc[d + j] = fmaf(z, b.u[p * r + j], acc[d + j]);
+    }
+  }
+  __shared__ float red[8][40];
+  for (int j = 0; j < K; ++j) {
+    float v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+    atomicAdd(&gW0[f * K + threadIdx.x], s);
+  }
+}
+
+__global__ void train_lat_scatter(Batch b, int r, const float* g_lat_pt, const float* g_u_pt, float dt_snap,
+                                  float* g_lat) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < b.B; p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = b.snap[p], nx = b.next[p];
+    for (int j = 0; j < r; ++j) {
+      const float gu = g_u_pt[p * r + j] / dt_snap;
+      atomicAdd(&g_lat[(int64_t)s * r + j], g_lat_pt[p * r + j] - (nx >= 0 ? gu : 0.f));
+      if (nx >= 0) atomicAdd(&g_lat[(int64_t)nx * r + j], gu);
+    }
+  }
+}
+
+// Adam (Kingma and Ba 2015) on two parameter ranges; zeroes the gradients.
+__global__ void train_adam(float* p0, float* g0, float* m0, float* v0, int64_t n0, float* p1, float* g1, float* m1,
+                           float* v1, int64_t n1, const int64_t* step, int64_t total_steps, float lr0, float lr1,
+                           float beta1, float beta2, float eps, int update) {
+  const int64_t t = *step;
+  const float frac = total_steps > 1 ? (float)min(t, total_steps - 1) / (float)(total_steps - 1) : 0.f;
+  const float lr = lr0 * powf(lr1 / lr0, frac);
+  const float bc1 = 1.f - powf(beta1, (float)(t + 1)), bc2 = 1.f - powf(beta2, (float)(t + 1));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n0 + n1; i += (int64_t)gridDim.x * blockDim.x) {
+    float *p, *g, *m, *v;
+    int64_t j = i;
+    if (i < n0) {
+      p = p0; g = g0; m = m0; v = v0;
+    } else {
+      j = i - n0;
+      p = p1; g = g1; m = m1; v = v1;
+    }
+    const float gr = g[j];
+    g[j] = 0.f;
+    if (!update) continue;
+    const float mm = beta1 * m[j] + (1.f - beta1) * gr;
+    const float vv = beta2 * v[j] + (1.f - beta2) * gr * gr;
+    m[j] = mm;
+    v[j] = vv;
+    p[j] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+  }
+}
+
+__global__ void train_step_inc(int64_t* step) { *step += 1; }
+
+// Transposed BF16 images of the square layers: image row = input feature, K = output feature.
+__global__ void train_pack_transposed(const float* params, const int64_t* w_off, int n_tc, uint8_t* img) {
+  const int64_t total = (int64_t)n_tc * kW * kW;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i / (kW * kW));
+    const int rem = (int)(i % (kW * kW));
+    const int out = rem / kW, in = rem % kW;
+    const float w = params[w_off[l + 1] + rem];  // W[out][in]
+    *reinterpret_cast<__nv_bfloat16*>(img + (size_t)l * kLayerBytes + tc::sw128_offset(in, out, kW)) =
+        __float2bfloat16_rn(w);
+  }
+}
+
+}  // namespace mpmrom
+
+using namespace mpmrom;
+
+struct trainer_ctx {
+  mpm_decoder* dec = nullptr;
+  train_config cfg{};
+  int d = 0, r = 0, R = 0, Pt = 0, n_sm = 0;
+  int64_t B = 0, n_tiles = 0, rows_total = 0, n_snap = 0;
+  Store st{};
+  Batch b{};
+  // device buffers
+  int64_t* snap_base = nullptr;
+  int32_t* snap_inst = nullptr;
+  int32_t* snap_next = nullptr;
+  int64_t* inst_off = nullptr;
+  float* X = nullptr;
+  float* sx = nullptr;
+  float* sv = nullptr;
+  float* sF = nullptr;
+  float* latents = nullptr;
+  float* g_lat = nullptr;
+  float* m_lat = nullptr;
+  float* v_lat = nullptr;
+  float* gparams = nullptr;
+  float* m_par = nullptr;
+  float* v_par = nullptr;
+  float* batch_mem = nullptr;
+  int32_t* batch_idx = nullptr;
+  float* fwd = nullptr;
+  float* zstore = nullptr;
+  __nv_bfloat16* astore = nullptr;
+  __nv_bfloat16* zbstore = nullptr;
+  float* zb0 = nullptr;
+  float* g_lat_pt = nullptr;
+  float* g_u_pt = nullptr;
+  uint8_t* wtimg = nullptr;
+  int64_t* d_w_off = nullptr;
+  int64_t* step = nullptr;
+  double* loss = nullptr;
+  uint32_t* status = nullptr;
+  size_t bwd_smem = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph_noupdate = nullptr;
+};
+
+namespace {
+
+mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
+  mpm_decoder* dec = c->dec;
+  const int d = c->d, r = c->r;
+  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((c->B + 255) / 256, (int64_t)c->n_sm * 8));
+  train_sample<<<blocks, 256, 0, s>>>(c->st, c->b, c->latents, c->cfg.dt_snap, c->cfg.seed, c->step, c->loss);
+  MPM_CUDA_TRY(cudaGetLastError());
+  int kinds[8];
+  kinds[0] = 0;
+  for (int a = 0; a < d; ++a) kinds[1 + a] = 1 + a;
+  kinds[1 + d] = 1000;
+  mpm_status st = decoder_launch_train(dec, c->b.X, c->b.xh, c->b.u, kinds, c->R, c->B, c->fwd, c->zstore, c->astore,
+                                       c->rows_total, s);
+  if (st != MPM_OK) return st;
+  BwdArgs a{};
+  a.d = d;
+  a.r = r;
+  a.n_hidden = dec->n_hidden;
+  a.n_tc = dec->n_tc;
+  a.act = dec->act;
+  a.R = c->R;
+  a.Pt = c->Pt;
+  a.n = c->B;
+  a.rows_total = c->rows_total;
+  const int L = (int)dec->w_off.size();
+  a.W0 = dec->params + dec->w_off[0];
+  a.Wout = dec->params + dec->w_off[L - 1];
+  a.norm = dec->norm;
+  a.zstore = c->zstore;
+  a.astore = c->astore;
+  a.wtimg = c->wtimg;
+  a.fwd = c->fwd;
+  a.b = c->b;
+  a.lamF = c->cfg.lambda_F;
+  a.lamv = c->cfg.lambda_v;
+  a.zbstore = c->zbstore;
+  a.zb0 = c->zb0;
+  a.gparams = c->gparams;
+  a.gW0_off = dec->w_off[0];
+  a.gb0_off = dec->b_off[0];
+  a.gWout_off = dec->w_off[L - 1];
+  a.gbout_off = dec->b_off[L - 1];
+  for (int l = 0; l < dec->n_hidden; ++l) a.gb_off[l] = dec->b_off[l];
+  a.g_lat_pt = c->g_lat_pt;
+  a.g_u_pt = c->g_u_pt;
+  a.loss = c->loss;
+  a.status = c->status;
+  const int bw = (int)std::max<int64_t>(1, std::min<int64_t>(c->n_tiles, c->n_sm));
+  train_bwd_tc<<<bw, 128, c->bwd_smem, s>>>(a);
+  MPM_CUDA_TRY(cudaGetLastError());
+  if (dec->n_tc > 0) {
+    const int splits = std::max(1, c->n_sm / dec->n_tc);
+    int64_t kps = (c->rows_total + splits - 1) / splits;
+    kps = (kps + 63) / 64 * 64;
+    dim3 g(dec->n_tc, (unsigned)((c->rows_total + kps - 1) / kps));
+    train_dw_gemm<<<g, 128, 0, s>>>(c->zbstore, c->astore, c->rows_total, kps, c->gparams, c->d_w_off, c->status);
+    MPM_CUDA_TRY(cudaGetLastError());
+  }
+  train_dw0<<<kW, 256, 0, s>>>(c->zb0, c->rows_total, c->b, d, r, c->R, c->Pt, dec->norm, c->gparams + dec->w_off[0]);
+  MPM_CUDA_TRY(cudaGetLastError());
+  train_lat_scatter<<<blocks, 256, 0, s>>>(c->b, r, c->g_lat_pt, c->g_u_pt, c->cfg.dt_snap, c->g_lat);
+  MPM_CUDA_TRY(cudaGetLastError());
+  if (update) {
+    const int64_t n0 = dec->n_params, n1 = c->n_snap * r;
+    int ba = (int)std::max<int64_t>(1, std::min<int64_t>((n0 + n1 + 255) / 256, (int64_t)c->n_sm * 8));
+    train_adam<<<ba, 256, 0, s>>>(dec->params, c->gparams, c->m_par, c->v_par, n0, c->latents, c->g_lat, c->m_lat,
+                                  c->v_lat, n1, c->step, c->cfg.total_steps, c->cfg.lr0, c->cfg.lr1, 0.9f, 0.999f,
+                                  1e-8f, 1);
+    MPM_CUDA_TRY(cudaGetLastError());
+    st = decoder_refresh(dec, s);
+    if (st != MPM_OK) return st;
+    if (dec->n_tc > 0) {
+      train_pack_transposed<<<std::max(1, dec->n_tc * 64), 256, 0, s>>>(dec->params, c->d_w_off, dec->n_tc, c->wtimg);
+      MPM_CUDA_TRY(cudaGetLastError());
+    }
+    train_step_inc<<<1, 1, 0, s>>>(c->step);
+    MPM_CUDA_TRY(cudaGetLastError());
+  }
+  return MPM_OK;
+}
+
+template <typename T>
+mpm_status talloc(T** p, size_t count, bool zero = true) {
+  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return set_error(MPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  if (zero) {
+    e = cudaMemset(*p, 0, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return set_error(MPM_ECUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+  }
+  return MPM_OK;
+}
+
+mpm_status capture(trainer_ctx* c, int update, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  MPM_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  mpm_status st = train_launch_step(c, c->cap_stream, update);
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (st != MPM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return set_error(MPM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return set_error(MPM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snapshot_desc* sd, const float* latents0,
+                          trainer_ctx** out) {
+  MPM_CHECK_ARG(dec && cfg && sd && out, "null argument");
+  *out = nullptr;
+  MPM_CHECK_ARG(dec->n_tc >= 1, "training needs at least two hidden layers (square tensor-core layers)");
+  MPM_CHECK_ARG(sd->dim == dec->d, "snapshot dimension must match the decoder");
+  MPM_CHECK_ARG(sd->n_inst >= 1 && sd->inst_offsets && sd->X, "instances");
+  MPM_CHECK_ARG(sd->n_snap >= 1 && sd->snap_inst && sd->snap_next && sd->x && sd->v && sd->F, "snapshots");
+  MPM_CHECK_ARG(cfg->batch >= 1 && cfg->dt_snap > 0 && cfg->lr0 > 0 && cfg->lr1 > 0, "batch, dt_snap, lr");
+  MPM_CHECK_ARG(dec->r <= 32, "latent dimension <= 32");
+  auto* c = new trainer_ctx();
+  c->dec = dec;
+  c->cfg = *cfg;
+  c->d = dec->d;
+  c->r = dec->r;
+  c->R = c->d + 2;
+  c->Pt = 128 / c->R;
+  c->B = cfg->batch;
+  c->n_tiles = (c->B + c->Pt - 1) / c->Pt;
+  c->rows_total = c->n_tiles * 128;
+  c->n_snap = sd->n_snap;
+  int devn = 0;
+  cudaGetDevice(&devn);
+  cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, devn);
+  const int d = c->d, r = c->r;
+  mpm_status st;
+  auto fail = [&](mpm_status s) {
+    trainer_destroy(c);
+    return s;
+  };
+  // snapshot bookkeeping (host)
+  std::vector<int64_t> base(sd->n_snap + 1, 0);
+  for (int s = 0; s < sd->n_snap; ++s) {
+    const int inst = sd->snap_inst[s];
+    if (inst < 0 || inst >= sd->n_inst) return fail(set_error(MPM_EINVAL, "snap_inst out of range"));
+    if (sd->snap_next[s] >= sd->n_snap) return fail(set_error(MPM_EINVAL, "snap_next out of range"));
+    base[s + 1] = base[s] + (sd->inst_offsets[inst + 1] - sd->inst_offsets[inst]);
+  }
+  const int64_t total = base[sd->n_snap];
+  const int64_t Ptot = sd->inst_offsets[sd->n_inst];
+  if ((st = talloc(&c->snap_base, sd->n_snap + 1)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->snap_inst, sd->n_snap)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->snap_next, sd->n_snap)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->inst_off, sd->n_inst + 1)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->X, (size_t)Ptot * d, false)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->sx, (size_t)total * d, false)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->sv, (size_t)total * d, false)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->sF, (size_t)total * d * d, false)) != MPM_OK) return fail(st);
+  MPM_CUDA_TRY(cudaMemcpy(c->snap_base, base.data(), sizeof(int64_t) * (sd->n_snap + 1), cudaMemcpyHostToDevice));
+  MPM_CUDA_TRY(cudaMemcpy(c->snap_inst, sd->snap_inst, sizeof(int32_t) * sd->n_snap, cudaMemcpyDefault));
+  MPM_CUDA_TRY(cudaMemcpy(c->snap_next, sd->snap_next, sizeof(int32_t) * sd->n_snap, cudaMemcpyDefault));
+  MPM_CUDA_TRY(cudaMemcpy(c->inst_off, sd->inst_offsets, sizeof(int64_t) * (sd->n_inst + 1), cudaMemcpyDefault));
+  MPM_CUDA_TRY(cudaMemcpy(c->X, sd->X, sizeof(float) * Ptot * d, cudaMemcpyDefault));
+  MPM_CUDA_TRY(cudaMemcpy(c->sx, sd->x, sizeof(float) * total * d, cudaMemcpyDefault));
+  MPM_CUDA_TRY(cudaMemcpy(c->sv, sd->v, sizeof(float) * total * d, cudaMemcpyDefault));
+  MPM_CUDA_TRY(cudaMemcpy(c->sF, sd->F, sizeof(float) * total * d * d, cudaMemcpyDefault));
+  // latent table + optimiser state
+  const size_t nl = (size_t)sd->n_snap * r;
+  if ((st = talloc(&c->latents, nl)) != MPM_OK) return fail(st);
+  if (latents0) MPM_CUDA_TRY(cudaMemcpy(c->latents, latents0, sizeof(float) * nl, cudaMemcpyDefault));
+  if ((st = talloc(&c->g_lat, nl)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->m_lat, nl)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->v_lat, nl)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->gparams, dec->n_params)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->m_par, dec->n_params)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->v_par, dec->n_params)) != MPM_OK) return fail(st);
+  // batch
+  const int64_t B = c->B;
+  const size_t per_pt = (size_t)(d + 2 * r + d + d + d * d + 1);
+  if ((st = talloc(&c->batch_mem, per_pt * B)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->batch_idx, (size_t)3 * B)) != MPM_OK) return fail(st);
+  float* m = c->batch_mem;
+  c->b.B = B;
+  c->b.X = m;
+  m += B * d;
+  c->b.xh = m;
+  m += B * r;
+  c->b.u = m;
+  m += B * r;
+  c->b.tx = m;
+  m += B * d;
+  c->b.tv = m;
+  m += B * d;
+  c->b.tF = m;
+  m += B * d * d;
+  c->b.mask = m;
+  c->b.snap = c->batch_idx;
+  c->b.next = c->batch_idx + B;
+  c->b.part = c->batch_idx + 2 * B;
+  // activation stores
+  const size_t rows = (size_t)c->rows_total;
+  if ((st = talloc(&c->fwd, (size_t)c->R * B * d)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->zstore, (size_t)dec->n_hidden * kW * rows)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->astore, (size_t)dec->n_hidden * kW * rows)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->zbstore, (size_t)dec->n_tc * kW * rows)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->zb0, (size_t)kW * rows)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->g_lat_pt, (size_t)B * r)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->g_u_pt, (size_t)B * r)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->wtimg, (size_t)dec->n_tc * kLayerBytes)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->d_w_off, dec->w_off.size())) != MPM_OK) return fail(st);
+  MPM_CUDA_TRY(cudaMemcpy(c->d_w_off, dec->w_off.data(), sizeof(int64_t) * dec->w_off.size(), cudaMemcpyHostToDevice));
+  if ((st = talloc(&c->step, 1)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->loss, 1)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->status, 1)) != MPM_OK) return fail(st);
+  c->st.d = d;
+  c->st.r = r;
+  c->st.n_snap = sd->n_snap;
+  c->st.snap_base = c->snap_base;
+  c->st.snap_inst = c->snap_inst;
+  c->st.snap_next = c->snap_next;
+  c->st.inst_off = c->inst_off;
+  c->st.X = c->X;
+  c->st.x = c->sx;
+  c->st.v = c->sv;
+  c->st.F = c->sF;
+  c->bwd_smem = 1024 + kMaxTC * kLayerBytes + kLayerBytes + (size_t)kExchRows * kW * 4 + 128 * 3 * 4 + kW * 4 +
+                sizeof(DecSmemTail);
+  MPM_CUDA_TRY(cudaFuncSetAttribute(train_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->bwd_smem));
+  train_pack_transposed<<<std::max(1, dec->n_tc * 64), 256>>>(dec->params, c->d_w_off, dec->n_tc, c->wtimg);
+  MPM_CUDA_TRY(cudaGetLastError());
+  MPM_CUDA_TRY(cudaDeviceSynchronize());
+  MPM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  *out = c;
+  return MPM_OK;
+}
+
+void trainer_destroy(trainer_ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_noupdate) cudaGraphExecDestroy(c->graph_noupdate);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  void* bufs[] = {c->snap_base, c->snap_inst, c->snap_next, c->inst_off, c->X, c->sx, c->sv, c->sF, c->latents,
+                  c->g_lat, c->m_lat, c->v_lat, c->gparams, c->m_par, c->v_par, c->batch_mem, c->batch_idx, c->fwd,
+                  c->zstore, c->astore, c->zbstore, c->zb0, c->g_lat_pt, c->g_u_pt, c->wtimg, c->d_w_off, c->step,
+                  c->loss, c->status};
+  for (void* p : bufs) cudaFree(p);
+  delete c;
+}
+
+mpm_status decoder_train(trainer_ctx* c, int n_steps, void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  MPM_CHECK_ARG(n_steps >= 0, "n_steps >= 0");
+  if (!c->graph) {
+    mpm_status st = capture(c, 1, &c->graph);
+    if (st != MPM_OK) return st;
+  }
+  for (int i = 0; i < n_steps; ++i) MPM_CUDA_TRY(cudaGraphLaunch(c->graph, (cudaStream_t)stream));
+  return MPM_OK;
+}
+
+mpm_status trainer_loss(trainer_ctx* c, double* loss, int64_t* step, void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  cudaStream_t s = (cudaStream_t)stream;
+  double h = 0.0;
+  MPM_CUDA_TRY(cudaMemcpyAsync(&h, c->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (step) MPM_CUDA_TRY(cudaMemcpyAsync(step, c->step, sizeof(int64_t), cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (loss) *loss = h / (double)c->B;
+  return MPM_OK;
+}
+
+mpm_status trainer_get_latents(trainer_ctx* c, float* latents, void* stream) {
+  MPM_CHECK_ARG(c && latents, "null argument");
+  MPM_CUDA_TRY(cudaMemcpyAsync(latents, c->latents, sizeof(float) * c->n_snap * c->r, cudaMemcpyDefault,
+                               (cudaStream_t)stream));
+  return MPM_OK;
+}
+
+mpm_status trainer_status_word(trainer_ctx* c, uint32_t* out, int clear, void* stream) {
+  MPM_CHECK_ARG(c && out, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t h = 0;
+  MPM_CUDA_TRY(cudaMemcpyAsync(&h, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (clear) MPM_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(uint32_t), s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = h;
+  return MPM_OK;
+}
+
+mpm_status trainer_gradients(trainer_ctx* c, float* g_params, float* g_latents, int32_t* batch_snap,
+                             int32_t* batch_part, double* loss, void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  cudaStream_t s = (cudaStream_t)stream;
+  // one forward + backward on the batch of the current step, no update
+  mpm_status st = train_launch_step(c, s, 0);
+  if (st != MPM_OK) return st;
+  if (g_params) MPM_CUDA_TRY(cudaMemcpyAsync(g_params, c->gparams, sizeof(float) * c->dec->n_params, cudaMemcpyDefault, s));
+  if (g_latents) MPM_CUDA_TRY(cudaMemcpyAsync(g_latents, c->g_lat, sizeof(float) * c->n_snap * c->r, cudaMemcpyDefault, s));
+  if (batch_snap) MPM_CUDA_TRY(cudaMemcpyAsync(batch_snap, c->b.snap, sizeof(int32_t) * c->B, cudaMemcpyDefault, s));
+  if (batch_part) MPM_CUDA_TRY(cudaMemcpyAsync(batch_part, c->b.part, sizeof(int32_t) * c->B, cudaMemcpyDefault, s));
+  double h = 0.0;
+  MPM_CUDA_TRY(cudaMemcpyAsync(&h, c->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->gparams, 0, sizeof(float) * c->dec->n_params, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->g_lat, 0, sizeof(float) * c->n_snap * c->r, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (loss) *loss = h / (double)c->B;
+  return MPM_OK;
+}
+
+}  // extern "C"

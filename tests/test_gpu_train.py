@@ -1,0 +1,111 @@
+"""GPU decoder training (Section 4.2 loss, Appendix B Adam) against the FP64 oracle via the C ABI.
+
+Gradients of one minibatch (the GPU's own draw, handed to the oracle) are compared per
+parameter block at 2e-2 relative norm-wise (BF16 tensor-core GEMMs, FP32 accumulation).
+"""
+import numpy as np
+import pytest
+
+import oracle.decoder as OD
+import synth.scenes as S
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-2
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _store(d=2, n_inst=2, J=5, side=8, seed=0):
+    """Synthetic snapshot store (random smooth-ish targets) in the snapshot_desc layout."""
+    import torch
+    rng = np.random.default_rng(seed)
+    sc = S.batch_2d(seed=seed, n_inst=n_inst, fixed_side=side) if d == 2 else None
+    X = sc.x
+    P = len(X)
+    xs = X[None] + 0.01 * rng.normal(size=(J, P, d))
+    vs = rng.normal(size=(J, P, d))
+    Fs = np.eye(d)[None, None] + 0.05 * rng.normal(size=(J, P, d, d))
+    S_ = J * n_inst
+    snaps = dict(dim=d, n_inst=n_inst, inst_offsets=np.ascontiguousarray(sc.inst_offsets, np.int64),
+                 X=torch.from_numpy(X.astype(np.float32)).cuda(), n_snap=S_,
+                 snap_inst=np.array([s % n_inst for s in range(S_)], np.int32),
+                 snap_next=np.array([s + n_inst if s + n_inst < S_ else -1 for s in range(S_)], np.int32),
+                 x=torch.from_numpy(xs.reshape(-1, d).astype(np.float32)).cuda(),
+                 v=torch.from_numpy(vs.reshape(-1, d).astype(np.float32)).cuda(),
+                 F=torch.from_numpy(Fs.reshape(-1, d * d).astype(np.float32)).cuda())
+    host = dict(X=X, x=xs, v=vs, F=Fs, P=P, J=J)
+    return snaps, host
+
+
+def _oracle_batch(host, snaps, bs, bp):
+    n_inst = snaps["n_inst"]
+    offs = snaps["inst_offsets"]
+    j = bs // n_inst
+    inst = bs % n_inst
+    pidx = offs[inst] + bp
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    return {"X": f32(host["X"][pidx]), "snap": bs.astype(np.int64),
+            "next": snaps["snap_next"][bs].astype(np.int64),
+            "x": f32(host["x"][j, pidx]), "F": f32(host["F"][j, pidx]), "v": f32(host["v"][j, pidx])}
+
+
+def test_gradients_match_oracle():
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.train import Trainer
+    d, r = 2, 8
+    snaps, host = _store(d)
+    X = host["X"]
+    p = S.xavier_decoder(1, d, r, 128, 5, OD.ELU, X_min=X.min(0), X_range=X.max(0) - X.min(0),
+                         out_shift=X.mean(0), out_scale=np.full(d, 0.1), bias_scale=0.2)
+    dec = Decoder.from_params(p)
+    lat0 = 0.5 * np.random.default_rng(3).normal(size=(snaps["n_snap"], r)).astype(np.float32)
+    lamF, lamv, dts = 3.0, 0.05, 0.01
+    tr = Trainer(dec, snaps, lambda_F=lamF, lambda_v=lamv, dt_snap=dts, batch=1000, total_steps=10, latents0=lat0)
+    gp, gl, bs, bp, loss = tr.gradients()
+    batch = _oracle_batch(host, snaps, bs, bp)
+    pf = p.copy()
+    for l in range(len(pf.W)):
+        pf.W[l] = pf.W[l].astype(np.float32).astype(np.float64)
+        pf.b[l] = pf.b[l].astype(np.float32).astype(np.float64)
+    L, gW, gb, glat = OD.batch_loss_grads(pf, lat0.astype(np.float64), batch, np.float32(dts), lamF, lamv)
+    assert loss == pytest.approx(L, rel=TOL)
+    off = 0
+    for l in range(len(pf.W)):
+        nW = pf.W[l].size
+        assert rel(gp[off:off + nW].reshape(pf.W[l].shape), gW[l]) < TOL, ("W", l)
+        off += nW
+        nb = pf.b[l].size
+        assert rel(gp[off:off + nb], gb[l]) < TOL, ("b", l)
+        off += nb
+    assert rel(gl, glat) < TOL
+
+
+def test_adam_first_step_and_loss_decrease():
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.train import Trainer
+    d, r = 2, 8
+    snaps, host = _store(d, seed=4)
+    X = host["X"]
+    p = S.xavier_decoder(2, d, r, 128, 5, OD.ELU, X_min=X.min(0), X_range=X.max(0) - X.min(0),
+                         out_shift=X.mean(0), out_scale=np.full(d, 0.05))
+    dec = Decoder.from_params(p)
+    tr = Trainer(dec, snaps, lambda_F=1.0, lambda_v=0.01, dt_snap=0.01, batch=2048, total_steps=300,
+                 lr0=1e-3, lr1=1e-4, latents0=np.zeros((snaps["n_snap"], r), np.float32))
+    gp, _, _, _, loss0 = tr.gradients()
+    before = np.empty(dec.n_params, np.float32)
+    dec.get_params(before, None)
+    tr.step(1)
+    after = np.empty(dec.n_params, np.float32)
+    dec.get_params(after, None)
+    import torch
+    torch.cuda.synchronize()
+    # Adam's first step is -lr g / (|g| + eps): -lr sign(g) where |g| >> eps
+    big = np.abs(gp) > 1e-5
+    np.testing.assert_allclose((after - before)[big], -1e-3 * np.sign(gp[big]), rtol=1e-3, atol=2e-7)
+    tr.step(299)
+    loss1, step = tr.loss()
+    assert step == 300
+    assert tr.status() == 0
+    assert loss1 < 0.5 * loss0
