@@ -47,7 +47,7 @@ def generate_snapshots(scene, n_steps, every, device="cuda"):
     return dict(dim=d, n_inst=n_inst, inst_offsets=np.ascontiguousarray(scene.inst_offsets, np.int64),
                 X=torch.from_numpy(scene.x.astype(np.float32)).to(device), n_snap=S, snap_inst=snap_inst,
                 snap_next=snap_next, x=xs.reshape(-1, d), v=vs.reshape(-1, d), F=Fs.reshape(-1, d * d),
-                status=status, steps_between=every)
+                status=status, steps_between=every, dt_snap=every * float(np.float32(scene.dt)))
 
 
 class Trainer:
