@@ -175,6 +175,42 @@ mpm_status mpm_status_word(mpm_ctx* ctx, uint32_t* out, int clear, void* stream)
 mpm_status mpm_debug_bins(mpm_ctx* ctx, int32_t* cell_keys, int32_t* block_keys,
                           int32_t* block_offsets, void* stream);
 
+/*
+ * mpm_step_noalloc: the MPM step for callers that may not allocate device
+ * memory.  (This entry point has no counterpart in the paper; it is a
+ * deployment convenience.)  Some callers cannot call cudaMalloc at the point
+ * where they step a simulation: a host application that owns the whole
+ * device-memory budget and forbids allocations inside its frame loop, or
+ * code that must never risk an allocation failure or the implicit device
+ * synchronisation that cudaMalloc / cudaFree can cause.  This variant
+ * allocates nothing: all of its work memory (two particle-state buffers,
+ * the binning tables, two grids per instance) is carved out of one fixed,
+ * file-scope device array of 8 MiB inside the library, which every GPU that
+ * loads the library holds until the process exits.  It performs no
+ * cudaMalloc, cudaFree or other allocating call.
+ *
+ *   cfg          as for mpm_init (1..64 instances); copied per call.
+ *   x, v, F, C   device arrays in the layout of mpm_set_state, read as the
+ *                starting state and overwritten with the state after n_steps
+ *                steps (caller's particle order).  C may be NULL (zero).
+ *   status_out   if not NULL, the call synchronises `stream` and stores the
+ *                MPM_STATUS_* bits raised during the call.
+ *
+ * Each call loads the state, bins it, performs the particle-to-grid transfer
+ * and n_steps steps of mpm_step, and stores the state back; nothing carries
+ * over between calls.  The configuration must fit in the fixed array (for
+ * example a 2D block of 4096 particles on a 128^2 grid needs about 1 MiB, a
+ * 3D scene on a 32^3 grid with 16384 particles about 5 MiB); larger
+ * configurations are rejected with MPM_EINVAL and a message giving the bytes
+ * needed.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once for that device; make that first call before
+ * any stream capture.  All calls share the one array and every call clears
+ * the parts that must start at zero, so calls whose work overlaps on the GPU
+ * (other streams, other host threads) race: serialise them.
+ */
+mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F, float* C, int n_steps,
+                            uint32_t* status_out, void* stream);
+
 /* Number of block keys (instances x blocks per grid); for sizing block_offsets. */
 int64_t mpm_num_block_keys(const mpm_ctx* ctx);
 

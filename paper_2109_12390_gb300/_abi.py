@@ -78,6 +78,8 @@ SIGNATURES = [
     ("mpm_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
     ("mpm_debug_bins", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("mpm_num_block_keys", C.c_int64, [C.c_void_p]),
+    ("mpm_step_noalloc", C.c_int, [C.POINTER(MpmConfig)] + [C.c_void_p] * 4 + [C.c_int, C.POINTER(C.c_uint32),
+                                                                                C.c_void_p]),
     ("mpm_debug_grid", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("decoder_create", C.c_int, [C.POINTER(DecoderDesc), C.POINTER(C.c_void_p)]),
     ("decoder_destroy", None, [C.c_void_p]),

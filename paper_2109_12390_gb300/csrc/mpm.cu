@@ -803,6 +803,50 @@ mpm_status launch_scan_permute(mpm_ctx* c, cudaStream_t s, bool clear_consumed) 
 
 }  // namespace
 
+// ----------------------------------------------------------------------------
+// Fixed scratch of mpm_step_noalloc.  Every GPU that loads the library holds
+// this array until the process exits; the entry point carves its work
+// buffers out of it instead of calling cudaMalloc.
+// ----------------------------------------------------------------------------
+constexpr size_t kNoAllocBytes = size_t(8) << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device.  The host-side
+// symbol is only a stand-in, so the address comes from cudaGetSymbolAddress,
+// looked up once per device with that device current.
+mpm_status noalloc_scratch(void** out) {
+  int dev = 0;
+  MPM_CUDA_TRY(cudaGetDevice(&dev));
+  MPM_CHECK_ARG(dev >= 0 && dev < kNoAllocMaxDevices, "device index out of range for the fixed scratch table");
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr)
+      return set_error(MPM_ECUDA, std::string("cudaGetSymbolAddress(fixed scratch): ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MPM_OK;
+}
+
+struct Carve {
+  char* base;
+  size_t used, cap;
+  template <typename T>
+  T* take(size_t count) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + std::max<size_t>(count, 1) * sizeof(T);
+    return used <= cap ? reinterpret_cast<T*>(base + off) : nullptr;
+  }
+};
+
+}  // namespace
+
 extern "C" {
 
 mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
@@ -1065,6 +1109,148 @@ mpm_status mpm_status_word(mpm_ctx* c, uint32_t* out, int clear, void* stream) {
 }
 
 int64_t mpm_num_block_keys(const mpm_ctx* c) { return c ? c->n_keys : 0; }
+
+mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F, float* C, int n_steps,
+                            uint32_t* status_out, void* stream) {
+  MPM_CHECK_ARG(cfg && x && v && F, "null argument");
+  MPM_CHECK_ARG(n_steps >= 0, "n_steps must be >= 0");
+  MPM_CHECK_ARG(cfg->dim == 2 || cfg->dim == 3, "dim must be 2 or 3");
+  const int B = cfg->dim == 2 ? Blk<2>::B : Blk<3>::B;
+  MPM_CHECK_ARG(cfg->n_grid >= 8 && cfg->n_grid % B == 0, "n_grid must be a multiple of 8 (2D) / 4 (3D)");
+  MPM_CHECK_ARG(cfg->n_inst >= 1 && cfg->n_inst <= 64 && cfg->E && cfg->nu && cfg->inst_offsets,
+                "instances (1..64 for the fixed-scratch step)");
+  MPM_CHECK_ARG(cfg->dx > 0 && cfg->dt > 0 && cfg->rho > 0 && cfg->p_vol > 0, "dx, dt, rho, p_vol must be > 0");
+  MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
+  MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
+  MPM_CHECK_ARG(cfg->bc == MPM_BC_STICKY || cfg->bc == MPM_BC_SLIP_FLOOR, "bc");
+  MPM_CHECK_ARG(cfg->bc_width >= 0 && cfg->inst_offsets[0] == 0, "bc_width, inst_offsets[0]");
+  for (int k = 0; k < cfg->n_inst; ++k)
+    MPM_CHECK_ARG(cfg->inst_offsets[k + 1] >= cfg->inst_offsets[k], "inst_offsets must be non-decreasing");
+  const int64_t P64 = cfg->inst_offsets[cfg->n_inst];
+  MPM_CHECK_ARG(P64 >= 1 && P64 < (1ll << 30), "particle count out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  void* scratch = nullptr;
+  MPM_TRY(noalloc_scratch(&scratch));
+
+  // a context whose device pointers all point into the fixed scratch
+  mpm_ctx c;
+  c.cfg = *cfg;
+  c.D = cfg->dim;
+  c.n = cfg->n_grid;
+  c.B = B;
+  c.nb = c.n / B;
+  c.nblk = c.D == 2 ? c.nb * c.nb : c.nb * c.nb * c.nb;
+  c.n_inst = cfg->n_inst;
+  const int64_t nk = (int64_t)c.n_inst * c.nblk;
+  MPM_CHECK_ARG(nk < (1ll << 30), "too many grid blocks");
+  c.n_keys = (int)nk;
+  c.P = (int)P64;
+  c.material = cfg->material;
+  c.transfer = cfg->transfer;
+  c.gnodes = c.D == 2 ? (int64_t)c.n * c.n : (int64_t)c.n * c.n * c.n;
+  int dev = 0;
+  MPM_CUDA_TRY(cudaGetDevice(&dev));
+  MPM_CUDA_TRY(cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev));
+  c.max_work = ceil_div(c.P, kChunk) + std::min(c.n_keys, c.P) + 1;
+  c.n_scan_tiles = ceil_div(c.n_keys, kScanTile);
+  const int D = c.D, DD = D * D;
+  const size_t comps = 2 * D + 2 * DD;
+  Carve cv{(char*)scratch, 0, kNoAllocBytes};
+  for (int b = 0; b < 2; ++b) {
+    c.state[b] = cv.take<float>(comps * c.P);
+    c.id[b] = cv.take<int32_t>(c.P);
+    c.grid[b] = cv.take<float4>((size_t)c.n_inst * c.gnodes);
+    c.touched[b] = cv.take<uint8_t>(c.n_keys);
+  }
+  c.key = cv.take<int32_t>(c.P);
+  c.perm = cv.take<int32_t>(c.P);
+  c.counts = cv.take<int32_t>(c.n_keys);
+  c.cursor = cv.take<int32_t>(c.n_keys);
+  c.offsets = cv.take<int32_t>(c.n_keys + 1);
+  c.work = cv.take<int4>(c.max_work);
+  c.n_work = cv.take<int32_t>(1);
+  c.tile_state = cv.take<unsigned long long>(c.n_scan_tiles);
+  c.mu_lam = cv.take<float2>(c.n_inst);
+  c.d_offs = cv.take<int64_t>(c.n_inst + 1);
+  c.status = cv.take<uint32_t>(1);
+  if (cv.used > cv.cap)
+    return set_error(MPM_EINVAL, "mpm_step_noalloc: this configuration needs " + std::to_string(cv.used) +
+                                     " bytes of work memory; the fixed scratch holds " +
+                                     std::to_string(kNoAllocBytes) + " bytes (8 MiB)");
+  // the scratch keeps the previous call's contents: clear what must start at zero
+  for (int b = 0; b < 2; ++b) {
+    MPM_CUDA_TRY(cudaMemsetAsync(c.grid[b], 0, sizeof(float4) * (size_t)c.n_inst * c.gnodes, s));
+    MPM_CUDA_TRY(cudaMemsetAsync(c.touched[b], 0, c.n_keys, s));
+  }
+  MPM_CUDA_TRY(cudaMemsetAsync(c.counts, 0, sizeof(int32_t) * c.n_keys, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c.cursor, 0, sizeof(int32_t) * c.n_keys, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c.tile_state, 0, sizeof(unsigned long long) * c.n_scan_tiles, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c.n_work, 0, sizeof(int32_t), s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c.status, 0, sizeof(uint32_t), s));
+  float2 ml[64];
+  int64_t offs[65];
+  for (int k = 0; k < c.n_inst; ++k) {
+    const double E = cfg->E[k], nu = cfg->nu[k];
+    MPM_CHECK_ARG(E > 0 && nu > -1 && nu < 0.5, "E must be > 0 and -1 < nu < 0.5");
+    ml[k] = make_float2((float)(E / (2 * (1 + nu))), (float)(E * nu / ((1 + nu) * (1 - 2 * nu))));
+  }
+  for (int k = 0; k <= c.n_inst; ++k) offs[k] = cfg->inst_offsets[k];
+  MPM_CUDA_TRY(cudaMemcpyAsync(c.mu_lam, ml, sizeof(float2) * c.n_inst, cudaMemcpyHostToDevice, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(c.d_offs, offs, sizeof(int64_t) * (c.n_inst + 1), cudaMemcpyHostToDevice, s));
+  DevParams& p = c.dp;
+  p.P = c.P;
+  p.n = c.n;
+  p.nb = c.nb;
+  p.nblk = c.nblk;
+  p.n_keys = c.n_keys;
+  p.gnodes = c.gnodes;
+  p.dx = cfg->dx;
+  p.inv_dx = (float)(1.0 / cfg->dx);
+  p.dt = cfg->dt;
+  for (int a = 0; a < 3; ++a) p.g[a] = cfg->gravity[a];
+  p.bc = cfg->bc;
+  p.bc_width = cfg->bc_width;
+  p.mass = cfg->rho * cfg->p_vol;
+  p.vol = cfg->p_vol;
+  p.mu_lam = c.mu_lam;
+  c.fused_grid = std::max(1, std::min(c.max_work, c.n_sm * 8));
+  // load the caller's state, bin it and transfer it to the grid, then step
+  c.cur = 0;
+  c.g = 0;
+  const bool zeroC = (C == nullptr) || c.transfer == MPM_TRANSFER_PIC;
+  StateView dst{c.state[0], c.id[0]};
+  const int blocks = std::max(1, std::min(ceil_div(c.P, 256), c.n_sm * 8));
+  if (D == 2)
+    mpm_load<2><<<blocks, 256, 0, s>>>(c.dp, x, v, F, C, dst, c.d_offs, c.n_inst, c.key, c.counts, zeroC ? 1 : 0,
+                                       c.status);
+  else
+    mpm_load<3><<<blocks, 256, 0, s>>>(c.dp, x, v, F, C, dst, c.d_offs, c.n_inst, c.key, c.counts, zeroC ? 1 : 0,
+                                       c.status);
+  MPM_CUDA_TRY(cudaGetLastError());
+  MPM_TRY(launch_scan_permute(&c, s, /*clear_consumed=*/false));
+  MPM_TRY(launch_fused<true>(&c, s));
+  for (int k = 0; k < n_steps; ++k) {
+    MPM_TRY(launch_fused<false>(&c, s));
+    c.cur = 1 - c.cur;
+    MPM_TRY(launch_scan_permute(&c, s, /*clear_consumed=*/true));
+    c.g = 1 - c.g;
+  }
+  // write the new state back into the caller's arrays (caller's particle order)
+  StateView src{c.state[c.cur], c.id[c.cur]};
+  if (D == 2)
+    mpm_store<2><<<blocks, 256, 0, s>>>(c.dp, src, x, v, F, C);
+  else
+    mpm_store<3><<<blocks, 256, 0, s>>>(c.dp, src, x, v, F, C);
+  MPM_CUDA_TRY(cudaGetLastError());
+  if (status_out) {
+    uint32_t h = 0;
+    MPM_CUDA_TRY(cudaMemcpyAsync(&h, c.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    MPM_CUDA_TRY(cudaStreamSynchronize(s));
+    *status_out = h;
+  }
+  return MPM_OK;
+}
+
 
 mpm_status mpm_debug_bins(mpm_ctx* c, int32_t* cell_keys, int32_t* block_keys, int32_t* block_offsets, void* stream) {
   MPM_CHECK_ARG(c && c->loaded && cell_keys && block_keys, "bad argument");

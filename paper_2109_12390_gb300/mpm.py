@@ -126,3 +126,22 @@ class MPM:
         self.get_state(x, v, F, Cm)
         torch.cuda.synchronize()
         return x, v, F, Cm
+
+
+def step_noalloc(scene_cfg, x, v, F, C_=None, n_steps=1, stream=None):
+    """mpm_step_noalloc through the C ABI: steps the state held in the caller's CUDA tensors
+    x (P, d), v (P, d), F (P, d, d), C (P, d, d) in place, using only the library's fixed
+    device scratch (no allocation).  `scene_cfg` is an MPM context's configuration source:
+    a synth.scenes.Scene.  Returns the status bits raised during the call."""
+    sc = scene_cfg
+    E = np.ascontiguousarray(np.atleast_1d(sc.E), np.float32)
+    nu = np.ascontiguousarray(np.atleast_1d(sc.nu), np.float32)
+    offs = np.ascontiguousarray(sc.inst_offsets, np.int64)
+    g = (C.c_float * 3)(*[float(a) for a in sc.gravity])
+    cfg = _abi.MpmConfig(sc.dim, sc.n_grid, sc.dx, sc.dt, g, sc.bc, sc.bc_width, sc.material, sc.transfer, sc.rho,
+                         sc.p_vol, len(E), E.ctypes.data_as(C.POINTER(C.c_float)),
+                         nu.ctypes.data_as(C.POINTER(C.c_float)), offs.ctypes.data_as(C.POINTER(C.c_int64)))
+    w = C.c_uint32()
+    _abi.check(_abi.lib().mpm_step_noalloc(C.byref(cfg), _ptr(x), _ptr(v), _ptr(F), _ptr(C_), int(n_steps),
+                                           C.byref(w), _stream(stream)))
+    return w.value
