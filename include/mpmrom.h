@@ -317,6 +317,11 @@ mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void*
  *                backtracking).
  *   projection   0 = position-velocity projection (Alg. 6),
  *                1 = velocity-only projection (Alg. 7).
+ *   ridge        rho >= 0: the projections solve the regularised least-squares
+ *                problems min |J a - b|^2 + rho (tr(J^T J) / r) |a|^2 (J the
+ *                latent Jacobian at the samples).  rho = 0 is the plain least
+ *                squares of Algorithms 6 and 7 (a 1e-10 relative ridge is
+ *                always kept so that rank-deficient J^T J stays factorisable).
  */
 typedef struct rom_config {
   int32_t dim;
@@ -338,6 +343,7 @@ typedef struct rom_config {
   int32_t instance;
   int32_t gn_iters;
   int32_t projection;
+  float ridge;
 } rom_config;
 
 typedef struct rom_ctx rom_ctx;

@@ -34,6 +34,10 @@ Readings where the paper is silent (listed in the design notes):
     step halving, at most 10 halvings; if no trial decreases the objective the
     iterate is kept and the ``no_decrease`` flag is raised;
   * at the first step xhat_{-1} = xhat_0 - dt vhat_0;
+  * optional ridge rho: the projections then solve min |J a - b|^2 +
+    rho (tr(J^T J) / r) |a|^2 (Tikhonov regularisation of the least-squares
+    problems for latent Jacobians with near-null directions; rho = 0 is the
+    paper's plain least squares);
   * initial latent state by the least-squares fit of Eq. essentialSpecInt over
     all particles (Gauss-Newton from zero, then a linear least-squares fit of
     the initial velocity).
@@ -127,6 +131,7 @@ class RomScene:
     armijo_c: float = 1e-4
     max_halvings: int = 10
     projection: str = "position-velocity"   # or "velocity-only"
+    ridge: float = 0.0                       # rho of the regularised projections
 
 
 @dataclasses.dataclass
@@ -167,18 +172,25 @@ def local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_all):
     return v_trial, x_trial, basis, neigh
 
 
-def lstsq(A, b):
+def lstsq(A, b, ridge=0.0):
+    """argmin |A x - b|^2 (+ ridge * tr(A^T A) / n * |x|^2 when ridge > 0)."""
+    if ridge > 0:
+        M = A.T @ A
+        lam = ridge * np.trace(M) / M.shape[0]
+        return np.linalg.solve(M + lam * np.eye(M.shape[0]), A.T @ b)
     return np.linalg.lstsq(A, b, rcond=None)[0]
 
 
-def project_velocity(dec, Xs, xhat_n, v_trial):
-    """Eq. nonlinear_projection:vel / linear_projection: LSQ fit of v_trial by dg/dxhat at xhat_n."""
+def project_velocity(dec, Xs, xhat_n, v_trial, ridge=0.0):
+    """Eq. nonlinear_projection:vel / linear_projection: LSQ fit of v_trial by dg/dxhat at xhat_n
+    (optionally the ridge-regularised fit, a reading for ill-conditioned latent Jacobians)."""
     _, _, Jq = D.jacobians(dec, Xs, xhat_n)
-    return lstsq(Jq.reshape(-1, dec.r), v_trial.reshape(-1))
+    return lstsq(Jq.reshape(-1, dec.r), v_trial.reshape(-1), ridge)
 
 
-def gauss_newton(dec, Xs, x_trial, xhat0, iters, c=1e-4, max_halvings=10):
-    """Eq. nonlinear_projection:pos by Gauss-Newton with backtracking; returns (xhat, no_decrease)."""
+def gauss_newton(dec, Xs, x_trial, xhat0, iters, c=1e-4, max_halvings=10, ridge=0.0):
+    """Eq. nonlinear_projection:pos by Gauss-Newton with backtracking; returns (xhat, no_decrease).
+    With ridge > 0 every step solves the ridge-regularised linearised problem."""
     xh = np.array(xhat0, np.float64)
     flag = False
     target = x_trial.reshape(-1)
@@ -186,7 +198,7 @@ def gauss_newton(dec, Xs, x_trial, xhat0, iters, c=1e-4, max_halvings=10):
         g, _, Jq = D.jacobians(dec, Xs, xh)
         res = g.reshape(-1) - target
         J = Jq.reshape(-1, dec.r)
-        delta = lstsq(J, -res)
+        delta = lstsq(J, -res, ridge)
         f0 = res @ res
         slope = 2.0 * res @ (J @ delta)
         alpha = 1.0
@@ -211,12 +223,13 @@ def rom_step(dec, rs: RomScene, st: RomState, record=None):
     x_all = D.decode(dec, rs.X, st.xhat)
     v_trial, x_trial, basis, neigh = local_dynamics(dec, rs, st.xhat, st.vhat, samples, x_all)
     Xs = rs.X[samples]
-    vhat_new = project_velocity(dec, Xs, st.xhat, v_trial)
+    vhat_new = project_velocity(dec, Xs, st.xhat, v_trial, rs.ridge)
     if rs.projection == "velocity-only":
         xhat_new, flag = st.xhat + rs.dt * vhat_new, False
     else:
         guess = 2.0 * st.xhat - st.xhat_prev
-        xhat_new, flag = gauss_newton(dec, Xs, x_trial, guess, rs.gn_iters, rs.armijo_c, rs.max_halvings)
+        xhat_new, flag = gauss_newton(dec, Xs, x_trial, guess, rs.gn_iters, rs.armijo_c, rs.max_halvings,
+                                      rs.ridge)
     if record is not None:
         record.update(samples=samples, basis=basis, neigh=neigh, x_all=x_all, v_trial=v_trial,
                       x_trial=x_trial)

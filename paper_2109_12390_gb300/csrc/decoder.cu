@@ -139,10 +139,13 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
         const int c = c0 + j;
         float z = __ldg(&a.b0[c]), zd = 0.f;
         if (ri.cls >= 0) {
-          for (int i = 0; i < K0; ++i) {
-            const float w = __ldg(&a.W0[c * K0 + i]);
-            z = fmaf(w, in[i], z);
-            zd = fmaf(w, dir[i], zd);
+#pragma unroll
+          for (int i = 0; i < 40; ++i) {
+            if (i < K0) {
+              const float w = __ldg(&a.W0[c * K0 + i]);
+              z = fmaf(w, in[i], z);
+              zd = fmaf(w, dir[i], zd);
+            }
           }
           h[j] = ri.cls == 0 ? act_f(a.act, z) : (ri.cls == 1 ? act_d1(a.act, z) * zd : act_sec(a.act, z, zd));
           if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + t] = ri.cls == 0 ? z : zd;

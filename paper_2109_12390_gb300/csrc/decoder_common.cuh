@@ -109,21 +109,26 @@ __device__ __forceinline__ void row_inputs(const DecArgs& a, const RowInfo& ri, 
     li = (int)(ri.p / cnt);
     if (a.idx) xrow = a.idx[xrow];
   }
-  for (int i = 0; i < d; ++i) {
-    in[i] = (a.X[xrow * d + i] - a.norm[i]) / a.norm[d + i];
-    dir[i] = 0.f;
-  }
-  for (int j = 0; j < r; ++j) {
-    in[d + j] = a.latents[(int64_t)li * r + j];
-    dir[d + j] = 0.f;
-  }
-  if (ri.cls == 1) {
-    if (ri.kind >= 1 && ri.kind <= d) dir[ri.kind - 1] = 1.f / a.norm[d + ri.kind - 1];
-    else if (ri.kind > d && ri.kind <= d + r) dir[ri.kind - 1] = 1.f;
-    else if (ri.kind == KIND_JVP)
-      for (int j = 0; j < r; ++j) dir[d + j] = a.dirs[(int64_t)li * r + j];
-  } else if (ri.cls == 2) {
-    for (int j = 0; j < r; ++j) dir[d + j] = a.dirs[(int64_t)li * r + j];
+  // unrolled to the 40-entry bound so that in[] and dir[] stay in registers
+#pragma unroll
+  for (int i = 0; i < 40; ++i) {
+    const int K = d + r;
+    float vin = 0.f, vdir = 0.f;
+    if (i < K) {
+      if (i < d) {
+        vin = (a.X[xrow * d + i] - a.norm[i]) / a.norm[d + i];
+      } else {
+        vin = a.latents[(int64_t)li * r + (i - d)];
+      }
+      if (ri.cls == 1) {
+        if (ri.kind >= 1 && ri.kind <= d + r) vdir = (i == ri.kind - 1) ? (i < d ? 1.f / a.norm[d + i] : 1.f) : 0.f;
+        else if (ri.kind == KIND_JVP && i >= d) vdir = a.dirs[(int64_t)li * r + (i - d)];
+      } else if (ri.cls == 2 && i >= d) {
+        vdir = a.dirs[(int64_t)li * r + (i - d)];
+      }
+    }
+    in[i] = vin;
+    dir[i] = vdir;
   }
 }
 

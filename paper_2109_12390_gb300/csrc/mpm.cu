@@ -248,24 +248,34 @@ __device__ __forceinline__ void count_key_aggregated(int key, int32_t* counts) {
 // (the transfer of a freshly loaded state).
 // --------------------------------------------------------------------------
 template <int D, int MATERIAL, int TRANSFER, bool FIRST, bool FP64_POLAR>
-__global__ void __launch_bounds__(kChunk) mpm_g2p2g(DevParams p, StateView src, StateView dst,
-                                                     const int32_t* __restrict__ perm,
-                                                     const int4* __restrict__ work, const int32_t* n_work,
-                                                     const float4* __restrict__ grid_cur, float4* grid_nxt,
-                                                     uint8_t* touched_nxt, int32_t* key_out,
-                                                     int32_t* counts, uint32_t* status) {
+__global__ void __launch_bounds__(kChunk, 2) mpm_g2p2g(DevParams p, StateView src, StateView dst,
+                                                        const int32_t* __restrict__ perm,
+                                                        const int4* __restrict__ work, const int32_t* n_work,
+                                                        const float4* __restrict__ grid_cur, float4* grid_nxt,
+                                                        uint8_t* touched_nxt, int32_t* key_out,
+                                                        int32_t* counts, uint32_t* status) {
   constexpr int B = Blk<D>::B;
   constexpr int TG = B + 2;  // grid-to-particle tile: nodes [b0, b0 + B + 2)
   constexpr int TP = B + 4;  // particle-to-grid tile: nodes [b0 - 1, b0 + B + 3)
+  constexpr int TC = B + 2;  // particle-to-grid cells (stencil bases) [b0 - 1, b0 + B + 1)
   constexpr int NG = (D == 2) ? TG * TG : TG * TG * TG;
   constexpr int NT = (D == 2) ? TP * TP : TP * TP * TP;
+  constexpr int NC = (D == 2) ? TC * TC : TC * TC * TC;
   constexpr int DD = D * D;
-  __shared__ float s_v[D * NG];
+  constexpr int PD = 2 * D + DD;                 // per-particle P2G record
+  constexpr int NSLAB = (D == 2) ? 3 : 9;        // tasks per cell, 3 stencil nodes each
+  __shared__ float4 s_v4[NG];
   __shared__ float s_m[NT];
   __shared__ float s_p[D * NT];
+  __shared__ int s_cnt[NC];
+  __shared__ int s_off[NC + 1];
+  __shared__ int s_cells[NC];
+  __shared__ int s_nne;
+  __shared__ float s_rec[kChunk * PD];
 
   const int nw = *n_work;
   const int P = p.P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
     const int4 item = work[w];  // {key, start, count, -}
     const int key = item.x;
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(kChunk) mpm_g2p2g(DevParams p, StateView src, 
     int tile_lo[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) tile_lo[a] = b0[a] - 1;
-    // grid-to-particle tile with the grid update applied on load
+    // grid-to-particle tile with the grid update of Algorithm 1 applied on load
     if (!FIRST) {
       for (int t = threadIdx.x; t < NG; t += blockDim.x) {
         int node[D];
@@ -293,15 +303,9 @@ __global__ void __launch_bounds__(kChunk) mpm_g2p2g(DevParams p, StateView src, 
           r /= TG;
           inside &= node[a] < p.n;
         }
-        float v[D];
-        if (inside) {
-          node_velocity<D>(grid_cur[grid_index<D>(node, inst, p)], node, p, v);
-        } else {
-#pragma unroll
-          for (int a = 0; a < D; ++a) v[a] = 0.f;
-        }
-#pragma unroll
-        for (int a = 0; a < D; ++a) s_v[a * NG + t] = v[a];
+        float v[3] = {0.f, 0.f, 0.f};
+        if (inside) node_velocity<D>(grid_cur[grid_index<D>(node, inst, p)], node, p, v);
+        s_v4[t] = make_float4(v[0], v[1], D > 2 ? v[2] : 0.f, 0.f);
       }
     }
     for (int t = threadIdx.x; t < NT; t += blockDim.x) {
@@ -309,11 +313,14 @@ __global__ void __launch_bounds__(kChunk) mpm_g2p2g(DevParams p, StateView src, 
 #pragma unroll
       for (int a = 0; a < D; ++a) s_p[a * NT + t] = 0.f;
     }
+    for (int t = threadIdx.x; t < NC; t += blockDim.x) s_cnt[t] = 0;
     __syncthreads();
 
     const int j = item.y + threadIdx.x;
     const bool active = threadIdx.x < item.z;
     int new_key = -1;
+    int lc = -1, rank = 0;
+    float rec[PD];
     if (active) {
       const int s = perm[j];
       float x[D], v[D], F[DD], C[DD];
@@ -328,64 +335,88 @@ __global__ void __launch_bounds__(kChunk) mpm_g2p2g(DevParams p, StateView src, 
 #pragma unroll
         for (int i = 0; i < DD; ++i) C[i] = src.base[(size_t)(2 * D + DD + i) * P + s];
       } else {
-        // grid-to-particle (Algorithm 1 step 3) from the tile
-        int base[D];
-        float w[D][3], dw[D][3];
+        // grid-to-particle (Algorithm 1 step 3), separable over the stencil axes
+        int rel[D];
+        float w[D][3], g[D][3];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          base[a] = stencil_base(x[a], p.inv_dx);
-          float fx = x[a] * p.inv_dx - (float)base[a];
+          const int bse = stencil_base(x[a], p.inv_dx);
+          // in range for every particle binned to this block; the clamp only
+          // keeps clamped out-of-grid particles (already flagged) in bounds
+          rel[a] = min(max(bse - b0[a], 0), B - 1);
+          const float fx = x[a] * p.inv_dx - (float)bse;
           bspline_w(fx, w[a]);
-          if (TRANSFER == MPM_TRANSFER_PIC) bspline_dw(fx, dw[a]);
+          if (TRANSFER == MPM_TRANSFER_MLS) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) g[a][k] = w[a][k] * ((float)k - fx) * p.dx;  // w (x_i - x_p)
+          } else {
+            float dw[3];
+            bspline_dw(fx, dw);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) g[a][k] = dw[k] * p.inv_dx;  // dN/dx
+          }
         }
         float Bm[DD];
 #pragma unroll
         for (int a = 0; a < D; ++a) v[a] = 0.f;
 #pragma unroll
         for (int i = 0; i < DD; ++i) Bm[i] = 0.f;
-        const int NS = (D == 2) ? 9 : 27;
+        if (D == 2) {
 #pragma unroll
-        for (int q = 0; q < NS; ++q) {
-          int off[D];
-          if (D == 2) {
-            off[0] = q / 3;
-            off[1] = q % 3;
-          } else {
-            off[0] = q / 9;
-            off[D - 2] = (q / 3) % 3;
-            off[D - 1] = q % 3;
-          }
-          int rel[D];
-          float wt = 1.f;
+          for (int i = 0; i < 3; ++i) {
+            float S0[2] = {0.f, 0.f}, S1[2] = {0.f, 0.f};
 #pragma unroll
-          for (int a = 0; a < D; ++a) {
-            // in range for every particle binned to this block; the clamp only
-            // keeps clamped out-of-grid particles (already flagged) in bounds
-            rel[a] = min(max(base[a] - b0[a], 0), B - 1) + off[a];
-            wt *= w[a][off[a]];
-          }
-          const int t = tile_index<D, TG>(rel);
-          float vi[D];
-#pragma unroll
-          for (int a = 0; a < D; ++a) vi[a] = s_v[a * NG + t];
-#pragma unroll
-          for (int a = 0; a < D; ++a) v[a] = fmaf(wt, vi[a], v[a]);
-          if (TRANSFER == MPM_TRANSFER_MLS) {
-#pragma unroll
-            for (int b = 0; b < D; ++b) {
-              float dp = (float)(base[b] + off[b]) * p.dx - x[b];
-#pragma unroll
-              for (int a = 0; a < D; ++a) Bm[a * D + b] = fmaf(wt * vi[a], dp, Bm[a * D + b]);
+            for (int jj = 0; jj < 3; ++jj) {
+              const float4 nv = s_v4[(rel[0] + i) * TG + rel[D - 1] + jj];
+              const float wy = w[D - 1][jj], gy = g[D - 1][jj];
+              S0[0] = fmaf(wy, nv.x, S0[0]);
+              S0[1] = fmaf(wy, nv.y, S0[1]);
+              S1[0] = fmaf(gy, nv.x, S1[0]);
+              S1[1] = fmaf(gy, nv.y, S1[1]);
             }
-          } else {
+            // value weights: x-axis w (or dw for the x-gradient), y handled above
+            const float wx = w[0][i];
+            const float gx = (TRANSFER == MPM_TRANSFER_MLS) ? g[0][i] : g[0][i];
 #pragma unroll
-            for (int b = 0; b < D; ++b) {
-              float gg = dw[b][off[b]] * p.inv_dx;
+            for (int a = 0; a < 2; ++a) {
+              v[a] = fmaf(wx, S0[a], v[a]);
+              Bm[a * D + 0] = fmaf(gx, S0[a], Bm[a * D + 0]);
+              Bm[a * D + 1] = fmaf(wx, S1[a], Bm[a * D + 1]);
+            }
+          }
+        } else {
 #pragma unroll
-              for (int c = 0; c < D; ++c)
-                if (c != b) gg *= w[c][off[c]];
+          for (int i = 0; i < 3; ++i) {
+            float T0[3] = {0.f, 0.f, 0.f}, Ty[3] = {0.f, 0.f, 0.f}, Tz[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-              for (int a = 0; a < D; ++a) Bm[a * D + b] = fmaf(vi[a], gg, Bm[a * D + b]);
+            for (int jj = 0; jj < 3; ++jj) {
+              float S0[3] = {0.f, 0.f, 0.f}, S1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+              for (int kk = 0; kk < 3; ++kk) {
+                const float4 nv = s_v4[((rel[0] + i) * TG + rel[1] + jj) * TG + rel[D - 1] + kk];
+                const float wz = w[D - 1][kk], gz = g[D - 1][kk];
+                S0[0] = fmaf(wz, nv.x, S0[0]);
+                S0[1] = fmaf(wz, nv.y, S0[1]);
+                S0[2] = fmaf(wz, nv.z, S0[2]);
+                S1[0] = fmaf(gz, nv.x, S1[0]);
+                S1[1] = fmaf(gz, nv.y, S1[1]);
+                S1[2] = fmaf(gz, nv.z, S1[2]);
+              }
+              const float wy = w[1][jj], gy = g[1][jj];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                T0[a] = fmaf(wy, S0[a], T0[a]);
+                Ty[a] = fmaf(gy, S0[a], Ty[a]);
+                Tz[a] = fmaf(wy, S1[a], Tz[a]);
+              }
+            }
+            const float wx = w[0][i], gx = g[0][i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              v[a] = fmaf(wx, T0[a], v[a]);
+              Bm[a * D + 0] = fmaf(gx, T0[a], Bm[a * D + 0]);
+              Bm[a * D + 1] = fmaf(wx, Ty[a], Bm[a * D + 1]);
+              Bm[a * D + 2] = fmaf(wx, Tz[a], Bm[a * D + 2]);
             }
           }
         }
@@ -448,12 +479,206 @@ __global__ void __launch_bounds__(kChunk) mpm_g2p2g(DevParams p, StateView src, 
         new_key = key_of_base<D>(nbse, inst, p);
         key_out[j] = new_key;
       }
-      // particle-to-grid of the (new) state into the next grid
+      // particle-to-grid record of the (new) state
       float tau[DD];
       kirchhoff<D, MATERIAL, FP64_POLAR>(F, ml.x, ml.y, tau);
-      scatter_particle<D, TRANSFER, TP>(x, v, C, tau, tile_lo, inst, s_m, s_p, grid_nxt, touched_nxt, p, status);
+      int nb[D];
+      bool out_of_grid = false, in_cells = true;
+      float fx[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        nb[a] = stencil_base(x[a], p.inv_dx);
+        fx[a] = x[a] * p.inv_dx - (float)nb[a];
+        out_of_grid |= (nb[a] < 0) | (nb[a] + 2 > p.n - 1);
+        const int r = nb[a] - tile_lo[a];
+        in_cells &= (r >= 0) & (r < TC);
+      }
+      if (out_of_grid) {
+        raise_status(status, STATUS_OUT_OF_GRID);
+      } else if (!in_cells) {
+        // moved more than one cell out of the block: scatter straight to the global grid
+        scatter_particle<D, TRANSFER, TP>(x, v, C, tau, tile_lo, inst, s_m, s_p, grid_nxt, touched_nxt, p, status);
+      } else {
+        int cidx = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) cidx = cidx * TC + (nb[a] - tile_lo[a]);
+        lc = cidx;
+        rank = atomicAdd(&s_cnt[lc], 1);
+        // record: fractional position in cells, then (MLS) c = m v - A (x_p - x_base)
+        // and A = m C - dt V0 (4/dx^2) tau, or (PIC) m v and dt V0 tau
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[a] = fx[a];
+        if (TRANSFER == MPM_TRANSFER_MLS) {
+          const float k = p.dt * p.vol * 4.0f * p.inv_dx * p.inv_dx;
+          float A[DD];
+#pragma unroll
+          for (int i = 0; i < DD; ++i) A[i] = p.mass * C[i] - k * tau[i];
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            float c = p.mass * v[a];
+#pragma unroll
+            for (int b = 0; b < D; ++b) c = fmaf(-A[a * D + b], fx[b] * p.dx, c);
+            rec[D + a] = c;
+          }
+#pragma unroll
+          for (int i = 0; i < DD; ++i) rec[2 * D + i] = A[i];
+        } else {
+          const float k = p.dt * p.vol;
+#pragma unroll
+          for (int a = 0; a < D; ++a) rec[D + a] = p.mass * v[a];
+#pragma unroll
+          for (int i = 0; i < DD; ++i) rec[2 * D + i] = k * tau[i];
+        }
+      }
     }
     if (!FIRST) count_key_aggregated(new_key, counts);
+    __syncthreads();
+    // exclusive scan of the cell counts and list of non-empty cells (warp 0)
+    if (warp == 0) {
+      constexpr int PER = (NC + 31) / 32;
+      int cnt[PER], nz = 0, tot = 0;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int c = lane * PER + q;
+        cnt[q] = c < NC ? s_cnt[c] : 0;
+        tot += cnt[q];
+        nz += cnt[q] > 0;
+      }
+      int x0 = tot, z0 = nz;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, z0, o);
+        if (lane >= o) {
+          x0 += y0;
+          z0 += y1;
+        }
+      }
+      int off = x0 - tot, zoff = z0 - nz;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int c = lane * PER + q;
+        if (c < NC) {
+          s_off[c] = off;
+          if (cnt[q] > 0) s_cells[zoff++] = c;
+        }
+        off += cnt[q];
+      }
+      if (lane == 31) {
+        s_off[NC] = off;
+        s_nne = zoff;
+      }
+    }
+    __syncthreads();
+    if (lc >= 0) {
+      float* dstr = s_rec + (size_t)(s_off[lc] + rank) * PD;
+#pragma unroll
+      for (int i = 0; i < PD; ++i) dstr[i] = rec[i];
+    }
+    __syncthreads();
+    // cell-owner accumulation: one task per (non-empty cell, row of 3 stencil
+    // nodes) sums its cell's particles in registers, then adds to the tile
+    const int n_tasks = s_nne * NSLAB;
+    for (int task = threadIdx.x; task < n_tasks; task += blockDim.x) {
+      const int cell = s_cells[task / NSLAB];
+      const int slab = task % NSLAB;
+      int crel[D];
+      {
+        int r = cell;
+#pragma unroll
+        for (int a = D - 1; a >= 0; --a) {
+          crel[a] = r % TC;
+          r /= TC;
+        }
+      }
+      // stencil row: fixed offsets on the leading axes, 3 nodes along the last
+      const int o0 = (D == 2) ? slab : slab / 3;
+      const int o1 = (D == 2) ? 0 : slab % 3;
+      float am[3] = {0.f, 0.f, 0.f};
+      float ap[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      const int q1 = s_off[cell + 1];
+      for (int q = s_off[cell]; q < q1; ++q) {
+        const float* rr = s_rec + (size_t)q * PD;
+        float wl[3], wlast[3];
+        float dwl[3], dwlast[3];
+        bspline_w(rr[0], wl);
+        bspline_w(rr[D - 1], wlast);
+        float wlead = wl[0] * 0.f;
+        float wfix;  // product of the fixed-axis weights
+        float wm[3] = {0.f, 0.f, 0.f};
+        if (D == 2) {
+          wfix = (o0 == 0 ? wl[0] : (o0 == 1 ? wl[1] : wl[2]));
+        } else {
+          float wmid[3];
+          bspline_w(rr[1], wmid);
+          wfix = (o0 == 0 ? wl[0] : (o0 == 1 ? wl[1] : wl[2])) * (o1 == 0 ? wmid[0] : (o1 == 1 ? wmid[1] : wmid[2]));
+          wm[0] = wmid[0];
+          wm[1] = wmid[1];
+          wm[2] = wmid[2];
+        }
+        (void)wlead;
+        if (TRANSFER == MPM_TRANSFER_MLS) {
+          // mom = w (c + A (o dx)) with o the node offset from the cell base
+          const float* c = rr + D;
+          const float* A = rr + 2 * D;
+          float cf[3];
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            float t = c[a] + A[a * D + 0] * ((float)o0 * p.dx);
+            if (D == 3) t += A[a * D + 1] * ((float)o1 * p.dx);
+            cf[a] = t;
+          }
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            const float wt = wfix * wlast[kk];
+            am[kk] += wt * p.mass;
+#pragma unroll
+            for (int a = 0; a < D; ++a) ap[kk][a] = fmaf(wt, fmaf(A[a * D + D - 1], (float)kk * p.dx, cf[a]), ap[kk][a]);
+          }
+        } else {
+          bspline_dw(rr[0], dwl);
+          bspline_dw(rr[D - 1], dwlast);
+          const float* mv = rr + D;
+          const float* kt = rr + 2 * D;
+          const float wl0 = (o0 == 0 ? wl[0] : (o0 == 1 ? wl[1] : wl[2]));
+          const float dwl0 = (o0 == 0 ? dwl[0] : (o0 == 1 ? dwl[1] : dwl[2]));
+          float wmid1 = 1.f, dwmid1 = 0.f;
+          if (D == 3) {
+            float dwm[3];
+            bspline_dw(rr[1], dwm);
+            wmid1 = (o1 == 0 ? wm[0] : (o1 == 1 ? wm[1] : wm[2]));
+            dwmid1 = (o1 == 0 ? dwm[0] : (o1 == 1 ? dwm[1] : dwm[2]));
+          }
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            const float wt = wfix * wlast[kk];
+            float grad[3];
+            grad[0] = dwl0 * p.inv_dx * wmid1 * wlast[kk];
+            if (D == 3) grad[1] = wl0 * dwmid1 * p.inv_dx * wlast[kk];
+            grad[D - 1] = wl0 * wmid1 * dwlast[kk] * p.inv_dx;
+            am[kk] += wt * p.mass;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+              float f = 0.f;
+#pragma unroll
+              for (int b = 0; b < D; ++b) f = fmaf(kt[a * D + b], grad[b], f);
+              ap[kk][a] += wt * mv[a] - f;
+            }
+          }
+        }
+      }
+      // add the row of 3 nodes to the shared tile: tile node = cell + offset + 1 (tile starts at b0 - 1)
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) {
+        int trel[D];
+        trel[0] = crel[0] + o0;
+        if (D == 3) trel[1] = crel[1] + o1;
+        trel[D - 1] = crel[D - 1] + kk;
+        const int t = tile_index<D, TP>(trel);
+        atomicAdd(&s_m[t], am[kk]);
+#pragma unroll
+        for (int a = 0; a < D; ++a) atomicAdd(&s_p[a * NT + t], ap[kk][a]);
+      }
+    }
     __syncthreads();
     flush_tile<D, TP>(s_m, s_p, tile_lo, inst, grid_nxt, touched_nxt, p);
     __syncthreads();
@@ -514,27 +739,42 @@ __global__ void __launch_bounds__(kScanTile) mpm_scan(int n_keys, int P, int32_t
     }
     s_a[lane] = sa;
     s_b[lane] = sb;
-    if (lane == 31) {
-      // look back over the predecessor tiles
-      const unsigned long long agg = (unsigned long long)(uint32_t)sa | ((unsigned long long)(uint32_t)sb << 32);
-      st_release_u64(&tile_state[tile], agg | (1ull << 62));
-      long long pa = 0, pb = 0;
-      for (int q = tile - 1; q >= 0; --q) {
-        unsigned long long v = 0;
+    // publish this tile's aggregate, then look back 32 predecessors at a time
+    const unsigned long long agg = (unsigned long long)(uint32_t)__shfl_sync(0xffffffffu, sa, 31) |
+                                   ((unsigned long long)(uint32_t)__shfl_sync(0xffffffffu, sb, 31) << 32);
+    const int tot_a = __shfl_sync(0xffffffffu, sa, 31), tot_b = __shfl_sync(0xffffffffu, sb, 31);
+    if (lane == 0) st_release_u64(&tile_state[tile], agg | (1ull << 62));
+    long long pa = 0, pb = 0;
+    int q_hi = tile - 1;  // window [q_hi - 31, q_hi], lane i reads q_hi - i
+    bool done = q_hi < 0;
+    while (!done) {
+      const int q = q_hi - lane;
+      unsigned long long v = 0;
+      if (q >= 0) {
         uint32_t tries = 0;
         do {
           v = ld_acquire_u64(&tile_state[q]);
         } while ((v >> 62) == 0 && ++tries < (1u << 24));
-        if ((v >> 62) == 0) {
-          raise_status(status, STATUS_TIMEOUT);
-          break;
-        }
-        pa += (long long)(v & 0xffffffffull);
-        pb += (long long)((v >> 32) & 0x3fffffffull);
-        if ((v >> 62) == 2) break;
+        if ((v >> 62) == 0) raise_status(status, STATUS_TIMEOUT);
       }
-      const unsigned long long inc = (unsigned long long)(uint32_t)(pa + sa) |
-                                     ((unsigned long long)(uint32_t)(pb + sb) << 32);
+      // the nearest inclusive prefix in the window ends the look-back
+      const unsigned incl = __ballot_sync(0xffffffffu, q >= 0 && (v >> 62) == 2);
+      const int stop = incl ? (__ffs(incl) - 1) : 31;
+      long long ca = (q >= 0 && lane <= stop) ? (long long)(v & 0xffffffffull) : 0;
+      long long cb = (q >= 0 && lane <= stop) ? (long long)((v >> 32) & 0x3fffffffull) : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ca += __shfl_down_sync(0xffffffffu, ca, o);
+        cb += __shfl_down_sync(0xffffffffu, cb, o);
+      }
+      pa += __shfl_sync(0xffffffffu, ca, 0);
+      pb += __shfl_sync(0xffffffffu, cb, 0);
+      done = incl != 0 || q_hi - 31 < 0;
+      q_hi -= 32;
+    }
+    if (lane == 0) {
+      const unsigned long long inc = (unsigned long long)(uint32_t)(pa + tot_a) |
+                                     ((unsigned long long)(uint32_t)(pb + tot_b) << 32);
       st_release_u64(&tile_state[tile], inc | (2ull << 62));
       s_prefix[0] = pa;
       s_prefix[1] = pb;

@@ -487,7 +487,7 @@ __device__ bool chol_solve(double* A, double* b, int r) {
 // The last CTA factors and solves, then prepares the next stage.
 __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, const float* __restrict__ dec,
                                                          int64_t cap, int mode, const float* __restrict__ target,
-                                                         int projection, int n_rows_override) {
+                                                         int projection, int n_rows_override, float ridge) {
   const int d = R.d, r = R.r;
   const int nP = n_rows_override > 0 ? n_rows_override : R.counts[0];
   const int rows = nP * d;
@@ -566,25 +566,31 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
   for (int e = threadIdx.x; e < n_acc; e += blockDim.x) S.acc[e] = 0.0;
   if (threadIdx.x == 0) S.counter[0] = 0u;
   __syncthreads();
-  bool ok = chol_solve(A, bvec, r);
-  if (!ok) {
-    // one retry with the diagonal shifted by 1e-12 tr(A) / r
-    if (threadIdx.x == 0) {
-      double tr = 0;
-      for (int i = 0; i < r; ++i) tr += A_keep[i * r + i];
-      s_shift = 1e-12 * tr / r;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x)
-      A[e] = A_keep[e] + ((e / r) == (e % r) ? s_shift : 0.0);
+  // Ridge rho tr(A) / r (rho = max(ridge, 1e-10)): the regularised least
+  // squares of the ridge option, and with the 1e-10 floor it keeps the
+  // factorisation defined when latent directions do not move the samples
+  // (rank-deficient J^T J; the solution then tends to the minimum-norm one).
+  // One retry with a larger ridge; after that the step is skipped and
+  // CHOLESKY raised.
+  if (threadIdx.x == 0) {
+    double tr = 0;
+    for (int i = 0; i < r; ++i) tr += A_keep[i * r + i];
+    s_shift = (tr > 0 ? tr : 1.0) / r;
+  }
+  __syncthreads();
+  bool ok = false;
+  for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+    const double rr = attempt == 0 ? fmax(1e-10, (double)ridge) : fmax(1e-6, 100.0 * (double)ridge);
+    const double ridge_abs = rr * s_shift;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) A[e] = A_keep[e] + ((e / r) == (e % r) ? ridge_abs : 0.0);
     for (int i = threadIdx.x; i < r; i += blockDim.x) bvec[i] = s_rhs[i];
     __syncthreads();
     ok = chol_solve(A, bvec, r);
-    if (!ok) {
-      if (threadIdx.x == 0) raise_status(R.status, STATUS_CHOLESKY);
-      for (int i = threadIdx.x; i < r; i += blockDim.x) bvec[i] = 0.0;  // no step
-      __syncthreads();
-    }
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) raise_status(R.status, STATUS_CHOLESKY);
+    for (int i = threadIdx.x; i < r; i += blockDim.x) bvec[i] = 0.0;  // no step
+    __syncthreads();
   }
   if (mode == NE_VEL) {
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
@@ -833,7 +839,8 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
   st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xh32, nullptr, ks, r + 1, c->outS, s);
   if (st != MPM_OK) return st;
   const int b_ne = std::max(1, std::min(ceil_div((int64_t)c->k * d, 64), 64));
-  rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_VEL, nullptr, c->cfg.projection, 0);
+  rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_VEL, nullptr, c->cfg.projection, 0,
+                                         c->cfg.ridge);
   MPM_CUDA_TRY(cudaGetLastError());
   if (c->cfg.projection == 1) {
     rom_commit_velocity_only<<<1, 64, 0, s>>>(c->dv, c->sv);
@@ -847,7 +854,7 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
     st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xk32, c->sv.dk32, ks, r + 2,
                             c->outS, s);
     if (st != MPM_OK) return st;
-    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_GN, nullptr, 0, 0);
+    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_GN, nullptr, 0, 0, c->cfg.ridge);
     MPM_CUDA_TRY(cudaGetLastError());
     st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, kLS, (int64_t)kLS * c->k, c->sv.ls_base32,
                             c->sv.ls_dir32, kls, 2, c->outLS, s);
@@ -885,6 +892,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   MPM_CHECK_ARG(cfg->n_grid >= 8, "n_grid");
   MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
   MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
+  MPM_CHECK_ARG(cfg->ridge >= 0.f, "ridge >= 0");
   auto* c = new rom_ctx();
   c->cfg = *cfg;
   c->dec = dec;
@@ -1123,7 +1131,7 @@ mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int
   for (int it = 0; it < iters && st == MPM_OK; ++it) {
     st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, P, c->sv.xk32, nullptr, ks, r + 1, c->outS, s);
     if (st != MPM_OK) break;
-    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, P, NE_FIT, tgt, 0, P);
+    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, P, NE_FIT, tgt, 0, P, 0.f);
     // trials: secant from the iterate; base rows hold the iterate
     st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, kLS, (int64_t)kLS * P, c->sv.ls_base32, c->sv.ls_dir32,
                             kls, 2, c->outLS, s);
@@ -1139,7 +1147,7 @@ mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int
     MPM_CUDA_TRY(cudaMemcpyAsync(c->v_trial, vel, sizeof(float) * P * d, cudaMemcpyDeviceToDevice, s));
     // solve J^T J vhat = J^T V0 (projection flag 1 keeps xk: the commit below sets the state)
     MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.xh, c->sv.xk, sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
-    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, P, NE_VEL, nullptr, 1, P);
+    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, P, NE_VEL, nullptr, 1, P, 0.f);
   }
   cudaFree(tgt);
   cudaFree(vel);

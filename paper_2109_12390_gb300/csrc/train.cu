@@ -139,6 +139,7 @@ struct BwdArgs {
 };
 
 constexpr int kExchRows = 104;
+constexpr int kExchStride = kW + 1;   // padded row stride: lanes of a warp hit distinct banks
 
 __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -146,11 +147,11 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
   uint8_t* wt = smem;                                 // n_tc x 32 KB (transposed square weights)
   uint8_t* atile = smem + kMaxTC * kLayerBytes;       // 32 KB
   float* exch = (float*)(atile + kLayerBytes);        // kExchRows x 128
-  float* sy = exch + kExchRows * kW;                  // 128 x 3
+  float* sy = exch + kExchRows * kExchStride;         // 128 x 3
   float* sbias = sy + 128 * 3;                        // 128
   DecSmemTail* tail = (DecSmemTail*)(sbias + kW);
   __shared__ double s_loss[4];
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int d = a.d, r = a.r, R = a.R, Pt = a.Pt;
 
   if (t == 0) {
@@ -231,8 +232,9 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
       }
     }
     // ---- reverse sweep over the hidden layers
-    float hin[40];
-    for (int j = 0; j < r; ++j) hin[j] = 0.f;
+    float hin[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) hin[j] = 0.f;
     for (int l = a.n_hidden - 1; l >= 0; --l) {
       const bool from_tmem = (l < a.n_hidden - 1);
       if (from_tmem) {
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
             const float zp = zl[(int64_t)f * a.rows_total + gp];
             const float zr = zl[(int64_t)f * a.rows_total + gr];
             zb[i] = act_d1(a.act, zp) * hb[i];
-            exch[(t - Pt) * kW + f] = act_d2(a.act, zp) * zr * hb[i];
+            exch[(t - Pt) * kExchStride + f] = act_d2(a.act, zp) * zr * hb[i];
           }
         }
         __syncthreads();
@@ -276,13 +278,31 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
             const int f = ch * 32 + i;
             const float zp = zl[(int64_t)f * a.rows_total + gp];
             float s = act_d1(a.act, zp) * hb[i];
-            for (int kk = 1; kk < R; ++kk) s += exch[((kk - 1) * Pt + q) * kW + f];
+            for (int kk = 1; kk < R; ++kk) s += exch[((kk - 1) * Pt + q) * kExchStride + f];
             zb[i] = s;
-            atomicAdd(&sbias[f], s);
           }
         } else if (cls < 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) zb[i] = 0.f;
+        }
+        // bias gradient: sum of the primal rows' z_bar (primal rows all sit in warp 0);
+        // transpose-reduce the 32 columns across the warp so lane i ends with column i
+        if (warp == 0) {
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = (cls == 0) ? zb[i] : 0.f;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < o; ++i) {
+              // lanes with bit o set keep the upper half of the columns, the others the lower half
+              const float send = up ? v[i] : v[i + o];
+              const float keep = up ? v[i + o] : v[i];
+              v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+          }
+          sbias[ch * 32 + lane] += v[0];
         }
         if (l >= 1) {
 #pragma unroll
@@ -295,17 +315,20 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) zs[(int64_t)(ch * 32 + i) * a.rows_total] = zb[i];
           if (cls >= 0) {
-            for (int j = 0; j < r; ++j) {
-              float s = 0.f;
 #pragma unroll
-              for (int i = 0; i < 32; ++i) s = fmaf(__ldg(&a.W0[(ch * 32 + i) * (d + r) + d + j]), zb[i], s);
-              hin[j] += s;
+            for (int j = 0; j < 32; ++j) {
+              if (j < r) {
+                float s = 0.f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) s = fmaf(__ldg(&a.W0[(ch * 32 + i) * (d + r) + d + j]), zb[i], s);
+                hin[j] += s;
+              }
             }
           }
         }
         __syncthreads();
       }
-      // bias gradient of layer l
+      // bias gradient of layer l (sbias was filled by warp 0 before the last barrier)
       atomicAdd(&a.gparams[a.gb_off[l] + t], sbias[t]);
       sbias[t] = 0.f;
       if (l >= 1) {
@@ -329,9 +352,13 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
     if (tail->abort) break;
     // latent adjoints of this row
     if (cls == 0) {
-      for (int j = 0; j < r; ++j) a.g_lat_pt[p * r + j] = hin[j];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < r) a.g_lat_pt[p * r + j] = hin[j];
     } else if (cls == 1 && k == d + 1) {
-      for (int j = 0; j < r; ++j) a.g_u_pt[p * r + j] = hin[j];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < r) a.g_u_pt[p * r + j] = hin[j];
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -425,13 +452,16 @@ __global__ void __launch_bounds__(128, 1) train_dw_gemm(const __nv_bfloat16* zbs
   if (warp == 0) tc::tmem_free<kW>(tmem);
 }
 
-// First-layer weight gradient: dW0[f][j] = sum_rows zb0[f][row] in_row[j].
+// First-layer weight gradient: dW0[f][j] = sum_rows zb0[f][row] in_row[j]
+// (in_row: normalised input for primal rows, the input direction for tangent rows).
+constexpr int kMaxIn = 40;
 __global__ void train_dw0(const float* zb0, int64_t rows_total, Batch b, int d, int r, int R, int Pt,
                           const float* norm, float* gW0) {
   const int f = blockIdx.x;
   const int K = d + r;
-  float acc[40];
-  for (int j = 0; j < K; ++j) acc[j] = 0.f;
+  float acc[kMaxIn];
+#pragma unroll
+  for (int j = 0; j < kMaxIn; ++j) acc[j] = 0.f;
   for (int64_t gr = threadIdx.x; gr < rows_total; gr += blockDim.x) {
     const float z = zb0[(int64_t)f * rows_total + gr];
     if (z == 0.f) continue;
@@ -439,17 +469,19 @@ __global__ void train_dw0(const float* zb0, int64_t rows_total, Batch b, int d, 
     const int t = (int)(gr % 128), k = t / Pt, q = t % Pt;
     const int64_t p = tile * Pt + q;
     if (k >= R || p >= b.B) continue;
-    if (k == 0) {
-      for (int i = 0; i < d; ++i) acc[i] = fmaf(z, (b.X[p * d + i] - norm[i]) / norm[d + i], acc[i]);
-      for (int j = 0; j < r; ++j) acc[d + j] = fmaf(z, b.xh[p * r + j], acc[d + j]);
-    } else if (k <= d) {
-      acc[k - 1] = fmaf(z, 1.f / norm[d + k - 1], acc[k - 1]);
-    } else {
-      for (int j = 0; j < r; ++j) acc[d + j] = fmaf(z, b.u[p * r + j], acc[d + j]);
+#pragma unroll
+    for (int j = 0; j < kMaxIn; ++j) {
+      if (j >= K) break;
+      float in;
+      if (k == 0) in = j < d ? (b.X[p * d + j] - norm[j]) / norm[d + j] : b.xh[p * r + (j - d)];
+      else if (k <= d) in = (j == k - 1) ? 1.f / norm[d + k - 1] : 0.f;
+      else in = j < d ? 0.f : b.u[p * r + (j - d)];
+      acc[j] = fmaf(z, in, acc[j]);
     }
   }
-  __shared__ float red[8][40];
-  for (int j = 0; j < K; ++j) {
+  __shared__ float red[8][kMaxIn];
+#pragma unroll
+  for (int j = 0; j < kMaxIn; ++j) {
     float v = acc[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -793,7 +825,7 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   c->st.x = c->sx;
   c->st.v = c->sv;
   c->st.F = c->sF;
-  c->bwd_smem = 1024 + kMaxTC * kLayerBytes + kLayerBytes + (size_t)kExchRows * kW * 4 + 128 * 3 * 4 + kW * 4 +
+  c->bwd_smem = 1024 + kMaxTC * kLayerBytes + kLayerBytes + (size_t)kExchRows * kExchStride * 4 + 128 * 3 * 4 + kW * 4 +
                 sizeof(DecSmemTail);
   MPM_CUDA_TRY(cudaFuncSetAttribute(train_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->bwd_smem));
   train_pack_transposed<<<std::max(1, dec->n_tc * 64), 256>>>(dec->params, c->d_w_off, dec->n_tc, c->wtimg);

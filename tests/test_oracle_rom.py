@@ -126,3 +126,17 @@ def test_position_error_toy():
     err.add(np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 0.0]]), np.array([[0.0, 1.0], [3.0, 0.0], [0.0, 0.0]]))
     # numerator: 1 + 1 = 2; denominator: 1 + 4 + 1 + 1 + 9 = 16 -> 100 * sqrt(2) / 4
     assert err.percent() == pytest.approx(100 * np.sqrt(2) / 4, rel=1e-15)
+
+
+def test_ridge_projection_equals_augmented_least_squares():
+    """The ridge option: argmin |J a - b|^2 + rho tr(J^T J)/r |a|^2 equals the plain
+    least-squares solution of the stacked system [J; sqrt(lam) I] a = [b; 0]."""
+    rng = np.random.default_rng(12)
+    J = rng.normal(size=(40, 6)) @ np.diag([1, 1, 1, 1e-2, 1e-3, 1e-3])
+    b = rng.normal(size=40)
+    rho = 1e-3
+    lam = rho * np.trace(J.T @ J) / 6
+    aug = np.linalg.lstsq(np.vstack([J, np.sqrt(lam) * np.eye(6)]), np.concatenate([b, np.zeros(6)]), rcond=None)[0]
+    np.testing.assert_allclose(R.lstsq(J, b, rho), aug, rtol=1e-10, atol=1e-12)
+    # rho -> 0 recovers the least-squares fit on the well-determined directions
+    np.testing.assert_allclose(J @ R.lstsq(J, b, 1e-14), J @ R.lstsq(J, b), rtol=1e-6, atol=1e-8)
