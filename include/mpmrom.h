@@ -272,7 +272,13 @@ enum {
   /* 1 .. d:          dg/dX_k, k = kind - 1                             */
   /* d+1 .. d+r:      dg/dxhat_j, j = kind - d - 1                      */
   DECODER_JVP = 1000,     /* (dg/dxhat) u with u = dirs[lat_idx[p]]       */
-  DECODER_SECANT = 1001   /* g(X; xhat + u) - g(X; xhat), u = dirs[lat_idx[p]] */
+  DECODER_SECANT = 1001,  /* g(X; xhat + u) - g(X; xhat), u = dirs[lat_idx[p]] */
+  /* DECODER_MIXED + b, b = 1 .. d + r: d/d(input b) of the DECODER_JVP row,
+   * i.e. d/dX_k ((dg/dxhat) u) for b = k + 1 <= d: the material gradient of the
+   * decoded velocity (Eq. timederOne) that the reduced step's affine
+   * quadrature velocity needs.  The call must also request DECODER_JVP and
+   * tangent kind b. */
+  DECODER_MIXED = 2000
 };
 
 /*
@@ -280,8 +286,8 @@ enum {
  *   X        (n, d) reference positions.
  *   lat_idx  (n) int32 row of `latents` (and `dirs`) per point, or NULL (row 0).
  *   latents  (n_lat, r) latent coordinates xhat.
- *   dirs     (n_lat, r) directions for DECODER_JVP / DECODER_SECANT rows
- *            (NULL if none is requested).
+ *   dirs     (n_lat, r) directions for DECODER_JVP / DECODER_SECANT /
+ *            DECODER_MIXED rows (NULL if none is requested).
  *   kinds    host array of R row kinds (R in 1..64); kinds[0] must be
  *            DECODER_PRIMAL.
  *   out      (R, n, d): out[k][p] = the quantity of kinds[k] at point p.
@@ -290,7 +296,9 @@ enum {
  * Derivative rows propagate with the primal pre-activations of the same
  * point (forward-mode chain rule); secant rows propagate the exact
  * difference act(z + dz) - act(z), so they resolve latent increments far
- * below BF16 resolution.
+ * below BF16 resolution; mixed rows propagate act''(z) (W u)(W t) +
+ * act'(z) (W m) (forward over forward).  Errors: MPM_EINVAL for an unknown
+ * kind, a mixed row without its JVP / tangent partner rows, or missing dirs.
  */
 mpm_status decoder_eval(const mpm_decoder* dec, const float* X, const int32_t* lat_idx, const float* latents,
                         const float* dirs, const int32_t* kinds, int R, int64_t n, float* out, void* stream);
@@ -322,6 +330,12 @@ mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void*
  *                latent Jacobian at the samples).  rho = 0 is the plain least
  *                squares of Algorithms 6 and 7 (a 1e-10 relative ridge is
  *                always kept so that rank-deficient J^T J stays factorisable).
+ *   affine       MLS transfer only.  0: the quadrature points enter the local
+ *                particle-to-grid transfer with C = 0, as Algorithm 5 writes
+ *                it.  1: they carry the affine velocity of the decoded motion,
+ *                C = (dv/dX) (dg/dX)^-1 with v = (dg/dxhat) vhat_n (the state an
+ *                APIC particle of that motion carries; the full-order MLS model
+ *                transfers it too).  Ignored with the PIC transfer.
  */
 typedef struct rom_config {
   int32_t dim;
@@ -344,6 +358,7 @@ typedef struct rom_config {
   int32_t gn_iters;
   int32_t projection;
   float ridge;
+  int32_t affine;
 } rom_config;
 
 typedef struct rom_ctx rom_ctx;

@@ -107,6 +107,41 @@ def jvp_latent(dec, X, xhat, u):
     return g, gd[0]
 
 
+def velocity_gradient(dec, X, xhat, u):
+    """Decoded velocity v = (dg/dxhat) u (Eq. timederOne with xhat_dot = u) and its
+    material gradient dv/dX (n, d, d), [p, i, k] = dv_i/dX_k, by forward-over-forward
+    chain rule: along the layers carry z, the latent tangent s (direction u), the
+    X tangents t_k and the mixed tangents m_k = d s / d X_k, with
+        s' = act'(z) (W s),  t_k' = act'(z) (W t_k),
+        m_k' = act''(z) (W s)(W t_k) + act'(z) (W m_k).
+    The spatial velocity gradient of the decoded motion is (dv/dX) (dg/dX)^-1."""
+    d, r = dec.d, dec.r
+    h = _inputs(dec, X, xhat)
+    n = len(h)
+    u = np.broadcast_to(np.asarray(u, np.float64), (n, r))
+    s = np.concatenate([np.zeros((n, d)), u], axis=1)
+    ts = [np.broadcast_to(np.concatenate([np.eye(d)[k] / dec.X_range, np.zeros(r)]), (n, d + r)) for k in range(d)]
+    ms = [np.zeros((n, d + r)) for _ in range(d)]
+    L = len(dec.W)
+    for l in range(L):
+        W = dec.W[l]
+        z = h @ W.T + dec.b[l]
+        zs = s @ W.T
+        zt = [t @ W.T for t in ts]
+        zm = [m @ W.T for m in ms]
+        if l < L - 1:
+            a1, a2 = act_d1(z, dec.activation), act_d2(z, dec.activation)
+            h = act(z, dec.activation)
+            s = a1 * zs
+            ts = [a1 * q for q in zt]
+            ms = [a2 * zs * q + a1 * mq for q, mq in zip(zt, zm)]
+        else:
+            s, ms = zs, zm
+    v = s * dec.out_scale
+    dvdX = np.stack([m * dec.out_scale for m in ms], axis=-1)
+    return v, dvdX
+
+
 # ------------------------------------------------------------------------------ training
 
 

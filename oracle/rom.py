@@ -34,6 +34,11 @@ Readings where the paper is silent (listed in the design notes):
     step halving, at most 10 halvings; if no trial decreases the objective the
     iterate is kept and the ``no_decrease`` flag is raised;
   * at the first step xhat_{-1} = xhat_0 - dt vhat_0;
+  * quadrature-point affine velocity (MLS transfer only): Algorithm 5 gives the
+    quadrature points C = 0, which matches the paper's PIC full-order model;
+    with the MLS/APIC full-order model the option ``affine = "decoded"`` gives
+    them the affine velocity of the decoded motion, C = (dv/dX) (dg/dX)^-1 with
+    v = (dg/dxhat) vhat, the state an APIC particle of that motion carries;
   * optional ridge rho: the projections then solve min |J a - b|^2 +
     rho (tr(J^T J) / r) |a|^2 (Tikhonov regularisation of the least-squares
     problems for latent Jacobians with near-null directions; rho = 0 is the
@@ -132,6 +137,7 @@ class RomScene:
     max_halvings: int = 10
     projection: str = "position-velocity"   # or "velocity-only"
     ridge: float = 0.0                       # rho of the regularised projections
+    affine: str = "zero"                     # quadrature-point C: "zero" or "decoded"
 
 
 @dataclasses.dataclass
@@ -151,11 +157,16 @@ def local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_all):
     basis, neigh = neighbourhood(x_all, samples, rs.dx, rs.n_grid)
     quad = np.concatenate([samples, neigh])
     _, FX, _ = D.jacobians(dec, rs.X[quad], xhat)
-    _, vq = D.jvp_latent(dec, rs.X[quad], xhat, vhat)
+    vq, dvdX = D.velocity_gradient(dec, rs.X[quad], xhat, vhat)
     xq = x_all[quad]
     d = xq.shape[1]
+    if rs.affine == "decoded" and rs.transfer == M.MLS:
+        # affine velocity of the decoded motion: C = (dv/dX) F^-1
+        Cq = np.einsum("pik,pkj->pij", dvdX, np.linalg.inv(FX))
+    else:
+        Cq = np.zeros((len(quad), d, d))
     mu, lam = M.lame(rs.E, rs.nu)
-    m, p = M.p2g(xq, vq, FX, np.zeros((len(quad), d, d)), rs.mass, rs.vol, mu, lam, dx=rs.dx,
+    m, p = M.p2g(xq, vq, FX, Cq, rs.mass, rs.vol, mu, lam, dx=rs.dx,
                  dt=rs.dt, n_grid=rs.n_grid, material=rs.material, transfer=rs.transfer)
     vg = M.grid_update(m, p, dt=rs.dt, gravity=rs.gravity, bc=rs.bc, bc_width=rs.bc_width)
     xs = x_all[samples]

@@ -34,7 +34,7 @@ class DecoderDesc(C.Structure):
                 ("activation", C.c_int32)]
 
 
-DECODER_PRIMAL, DECODER_JVP, DECODER_SECANT = 0, 1000, 1001
+DECODER_PRIMAL, DECODER_JVP, DECODER_SECANT, DECODER_MIXED = 0, 1000, 1001, 2000
 
 
 class RomConfig(C.Structure):
@@ -44,7 +44,7 @@ class RomConfig(C.Structure):
         ("material", C.c_int32), ("transfer", C.c_int32), ("rho", C.c_float), ("p_vol", C.c_float),
         ("E", C.c_float), ("nu", C.c_float), ("latent_dim", C.c_int32), ("n_samples", C.c_int32),
         ("seed", C.c_uint64), ("instance", C.c_int32), ("gn_iters", C.c_int32), ("projection", C.c_int32),
-        ("ridge", C.c_float),
+        ("ridge", C.c_float), ("affine", C.c_int32),
     ]
 
 

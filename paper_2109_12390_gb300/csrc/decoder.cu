@@ -12,8 +12,11 @@
 //   kind 0          primal              h = act(z)
 //   tangent kinds   dg along an input direction   t = act'(z) . (W t_prev)
 //   secant kind     g(xhat + delta) - g(xhat)     s = act(z + W s_prev) - act(z)
-// where z is the primal pre-activation of the same point, exchanged through
-// shared memory.  The secant rows give differences of decoder outputs without
+//   mixed kinds     d/d(input b) of the JVP row   m = act''(z) (W u)(W t) + act'(z) (W m_prev)
+// where z is the primal pre-activation of the same point and, for a mixed row,
+// W u and W t are the pre-activations of the JVP row and of the input-b tangent
+// row of the same point; the pre-activations of a 32-column chunk are
+// exchanged between the rows of a tile through shared memory.  The secant rows give differences of decoder outputs without
 // the BF16 rounding of the two absolute evaluations (the Gauss-Newton
 // residual needs differences far below BF16 resolution).
 //
@@ -52,15 +55,17 @@ __global__ void decoder_simt(DecArgs a) {
     ri.p = g % n;
     ri.q = 0;
     ri.kind = a.kinds[k];
-    ri.cls = ri.kind == KIND_PRIMAL ? 0 : (ri.kind == KIND_SECANT ? 2 : 1);
+    ri.cls = kind_class(ri.kind);
     float in[40], dir[40];
     row_inputs(a, ri, in, dir);
     const int K = a.d + a.r;
     float y[3] = {0.f, 0.f, 0.f};
     if (a.linear) {
+      // an affine map has no mixed second derivative
       for (int i = 0; i < a.d; ++i) {
         float z = 0.f;
-        for (int c = 0; c < K; ++c) z = fmaf(a.W0[i * K + c], ri.cls == 0 ? in[c] : dir[c], z);
+        if (ri.cls != 3)
+          for (int c = 0; c < K; ++c) z = fmaf(a.W0[i * K + c], ri.cls == 0 ? in[c] : dir[c], z);
         y[i] = z + (ri.cls == 0 ? a.b0[i] : 0.f);
       }
     } else {
@@ -70,7 +75,11 @@ __global__ void decoder_simt(DecArgs a) {
           z = fmaf(a.W0[c * K + i], in[i], z);
           zd = fmaf(a.W0[c * K + i], dir[i], zd);
         }
-        float h = ri.cls == 0 ? act_f(a.act, z) : (ri.cls == 1 ? act_d1(a.act, z) * zd : act_sec(a.act, z, zd));
+        float h;
+        if (ri.cls == 0) h = act_f(a.act, z);
+        else if (ri.cls == 1) h = act_d1(a.act, z) * zd;
+        else if (ri.cls == 2) h = act_sec(a.act, z, zd);
+        else h = act_d2(a.act, z) * zd * mixed_t0(a, a.W0 + c * K, ri.kind);
         for (int i = 0; i < a.d; ++i) y[i] = fmaf(a.Wout[i * kW + c], h, y[i]);
       }
       if (ri.cls == 0)
@@ -91,8 +100,8 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* wsm = smem;                                   // n_tc x 32 KB
   uint8_t* atile = smem + kMaxTC * kLayerBytes;          // 32 KB
-  float* zx = (float*)(atile + kLayerBytes);             // Pt x 128 fp32 (if R > 1)
-  DecSmemTail* tail = (DecSmemTail*)(zx + 64 * kW);
+  float* xb = (float*)(atile + kLayerBytes);             // 128 rows x 33: pre-activations of one chunk
+  DecSmemTail* tail = (DecSmemTail*)(xb + 64 * kW);
   const int t = threadIdx.x, warp = t >> 5;
 
   if (t == 0) {
@@ -147,7 +156,10 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
               zd = fmaf(w, dir[i], zd);
             }
           }
-          h[j] = ri.cls == 0 ? act_f(a.act, z) : (ri.cls == 1 ? act_d1(a.act, z) * zd : act_sec(a.act, z, zd));
+          if (ri.cls == 0) h[j] = act_f(a.act, z);
+          else if (ri.cls == 1) h[j] = act_d1(a.act, z) * zd;
+          else if (ri.cls == 2) h[j] = act_sec(a.act, z, zd);
+          else h[j] = act_d2(a.act, z) * zd * mixed_t0(a, a.W0 + c * K0, ri.kind);
           if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + t] = ri.cls == 0 ? z : zd;
         } else {
           h[j] = 0.f;
@@ -198,19 +210,30 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
         }
         if (ri.cls == 0) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            acc[i] += __ldg(&bl[ch * 32 + i]);
-            if (a.R > 1) zx[ri.q * kW + ch * 32 + i] = acc[i];
-            acc[i] = act_f(a.act, acc[i]);
-          }
+          for (int i = 0; i < 32; ++i) acc[i] += __ldg(&bl[ch * 32 + i]);
         }
-        if (a.R > 1) __syncthreads();
-        if (ri.cls == 1) {
+        if (a.R > 1) {
+          // publish this row's pre-activations (stride 33: conflict-free)
 #pragma unroll
-          for (int i = 0; i < 32; ++i) acc[i] *= act_d1(a.act, zx[ri.q * kW + ch * 32 + i]);
+          for (int i = 0; i < 32; ++i) xb[t * 33 + i] = acc[i];
+          __syncthreads();
+        }
+        // the primal row of point q is tile row q (kind index 0)
+        const float* zq = xb + ri.q * 33;
+        if (ri.cls == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] = act_f(a.act, acc[i]);
+        } else if (ri.cls == 1) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] *= act_d1(a.act, zq[i]);
         } else if (ri.cls == 2) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) acc[i] = act_sec(a.act, zx[ri.q * kW + ch * 32 + i], acc[i]);
+          for (int i = 0; i < 32; ++i) acc[i] = act_sec(a.act, zq[i], acc[i]);
+        } else if (ri.cls == 3) {
+          const float* uq = xb + (ri.ja * a.Pt + ri.q) * 33;
+          const float* tq = xb + (ri.jb * a.Pt + ri.q) * 33;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] = act_d2(a.act, zq[i]) * uq[i] * tq[i] + act_d1(a.act, zq[i]) * acc[i];
         } else if (ri.cls < 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[i] = 0.f;
@@ -424,13 +447,27 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   a.n = n;
   a.R = R;
   a.Pt = 128 / R;
-  bool need_dirs = false;
+  bool need_dirs = false, has_mixed = false;
   for (int k = 0; k < R; ++k) {
     const int c = kinds[k];
-    MPM_CHECK_ARG(c == KIND_PRIMAL || (c >= 1 && c <= dec->d + dec->r) || c == KIND_JVP || c == KIND_SECANT,
+    const bool mixed = c > KIND_MIXED && c <= KIND_MIXED + dec->d + dec->r;
+    MPM_CHECK_ARG(c == KIND_PRIMAL || (c >= 1 && c <= dec->d + dec->r) || c == KIND_JVP || c == KIND_SECANT || mixed,
                   "unknown row kind");
-    need_dirs |= (c == KIND_JVP || c == KIND_SECANT);
+    need_dirs |= (c == KIND_JVP || c == KIND_SECANT || mixed);
+    has_mixed |= mixed;
     a.kinds[k] = c;
+    a.mix_jvp[k] = 0;
+    a.mix_tan[k] = 0;
+    if (mixed) {
+      int kj = -1, kt = -1;
+      for (int q = 0; q < R; ++q) {
+        if (kinds[q] == KIND_JVP && kj < 0) kj = q;
+        if (kinds[q] == c - KIND_MIXED && kt < 0) kt = q;
+      }
+      MPM_CHECK_ARG(kj >= 0 && kt >= 0, "a mixed row needs the JVP row and the tangent row of its input in the call");
+      a.mix_jvp[k] = (int8_t)kj;
+      a.mix_tan[k] = (int8_t)kt;
+    }
   }
   MPM_CHECK_ARG(!need_dirs || dirs, "JVP / secant rows need dirs");
   MPM_CHECK_ARG(kinds[0] == KIND_PRIMAL || dec->n_tc == 0, "the first row kind must be the primal (0)");
@@ -445,6 +482,7 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
     a.astore = extra->astore;
     a.rows_total = extra->rows_total;
     MPM_CHECK_ARG(!a.zstore || dec->n_tc > 0, "training stores need square hidden layers");
+    MPM_CHECK_ARG(!a.zstore || !has_mixed, "training stores take no mixed rows");
   }
   if (dec->n_tc == 0) {
     int64_t rows = n * R;

@@ -33,6 +33,9 @@ struct DecArgs {
   int64_t n;          // points (upper bound when n_dev is set)
   int R, Pt;
   int kinds[kMaxR];
+  // mixed rows: kind indices of the JVP row and of the tangent row they pair
+  int8_t mix_jvp[kMaxR];
+  int8_t mix_tan[kMaxR];
   float* out;         // (R, n, d)
   // on-device point sets (reduced-order step): when n_dev is set, the point
   // count is (*n_dev) * n_rep, point p reads X row idx[p % *n_dev] (or
@@ -55,6 +58,7 @@ struct DecArgs {
 
 __device__ __forceinline__ float elu(float z) { return z > 0.f ? z : expm1f(z); }
 __device__ __forceinline__ float elu_d1(float z) { return z > 0.f ? 1.f : __expf(z); }
+__device__ __forceinline__ float elu_d2(float z) { return z > 0.f ? 0.f : __expf(z); }
 // act(z + dz) - act(z) without cancellation on the negative branch
 __device__ __forceinline__ float elu_secant(float z, float dz) {
   float z1 = z + dz;
@@ -65,19 +69,27 @@ __device__ __forceinline__ float elu_secant(float z, float dz) {
 
 __device__ __forceinline__ float act_f(int act, float z) { return act == 0 ? elu(z) : z; }
 __device__ __forceinline__ float act_d1(int act, float z) { return act == 0 ? elu_d1(z) : 1.f; }
+__device__ __forceinline__ float act_d2(int act, float z) { return act == 0 ? elu_d2(z) : 0.f; }
 __device__ __forceinline__ float act_sec(int act, float z, float dz) { return act == 0 ? elu_secant(z, dz) : dz; }
 
 // row-kind codes (see decoder_eval in include/mpmrom.h)
 constexpr int KIND_PRIMAL = 0;
 constexpr int KIND_JVP = 1000;
 constexpr int KIND_SECANT = 1001;
+// KIND_MIXED + b (b = 1 .. d + r): derivative along input b of the JVP row
+constexpr int KIND_MIXED = 2000;
 
 struct RowInfo {
   int kind;      // code
-  int cls;       // 0 primal, 1 tangent, 2 secant, -1 padding
+  int cls;       // 0 primal, 1 tangent, 2 secant, 3 mixed, -1 padding
   int q;         // point within tile
   int64_t p;     // global point index
+  int ja, jb;    // mixed rows: kind indices of the paired JVP and tangent rows
 };
+
+__device__ __forceinline__ int kind_class(int kind) {
+  return kind == KIND_PRIMAL ? 0 : (kind == KIND_SECANT ? 2 : (kind > KIND_MIXED ? 3 : 1));
+}
 
 __device__ __forceinline__ int64_t dec_count(const DecArgs& a) {
   return a.n_dev ? (int64_t)(*a.n_dev) * a.n_rep : a.n;
@@ -94,7 +106,9 @@ __device__ __forceinline__ RowInfo row_info(const DecArgs& a, int t, int64_t til
     return ri;
   }
   ri.kind = a.kinds[k];
-  ri.cls = ri.kind == KIND_PRIMAL ? 0 : (ri.kind == KIND_SECANT ? 2 : 1);
+  ri.cls = kind_class(ri.kind);
+  ri.ja = a.mix_jvp[k];
+  ri.jb = a.mix_tan[k];
   return ri;
 }
 
@@ -123,13 +137,21 @@ __device__ __forceinline__ void row_inputs(const DecArgs& a, const RowInfo& ri, 
       if (ri.cls == 1) {
         if (ri.kind >= 1 && ri.kind <= d + r) vdir = (i == ri.kind - 1) ? (i < d ? 1.f / a.norm[d + i] : 1.f) : 0.f;
         else if (ri.kind == KIND_JVP && i >= d) vdir = a.dirs[(int64_t)li * r + (i - d)];
-      } else if (ri.cls == 2 && i >= d) {
+      } else if ((ri.cls == 2 || ri.cls == 3) && i >= d) {
+        // secant increment, or the JVP direction that a mixed row differentiates
         vdir = a.dirs[(int64_t)li * r + (i - d)];
       }
     }
     in[i] = vin;
     dir[i] = vdir;
   }
+}
+
+// Layer-0 tangent of a mixed row along input b (the normalised X axes scale by
+// 1 / X_range): the weight column itself.
+__device__ __forceinline__ float mixed_t0(const DecArgs& a, const float* W0row, int kind) {
+  const int b = kind - KIND_MIXED - 1;
+  return b < a.d ? W0row[b] / a.norm[a.d + b] : W0row[b];
 }
 
 struct __align__(8) DecSmemTail {

@@ -27,8 +27,12 @@ __device__ __forceinline__ void bspline_dw(float fx, float dw[3]) {
 // floor(x * inv_dx - 0.5); exact for power-of-two dx (x * inv_dx is a scaling
 // by a power of two and the subtraction of 0.5 is exact), the same integer the
 // FP64 definition gives.
+// The floor is clamped before the conversion: a NaN or a huge coordinate then
+// gives an index that every range check rejects and for which base + 2 cannot
+// overflow.
 __device__ __forceinline__ int stencil_base(float x, float inv_dx) {
-  return (int)floorf(x * inv_dx - 0.5f);
+  const float b = floorf(x * inv_dx - 0.5f);
+  return (int)fminf(fmaxf(b, -16.0f), 16777216.0f);
 }
 
 // det(F) - 1 without cancellation (fma keeps the product exact before the -1).

@@ -84,6 +84,32 @@ struct RomDev {
   uint32_t* status;
 };
 
+// Inverse of a small matrix by its adjugate (F of a quadrature point, det F > 0).
+template <int D>
+__device__ __forceinline__ void inverse(const float* F, float* Fi);
+template <>
+__device__ __forceinline__ void inverse<2>(const float* F, float* Fi) {
+  const float id = 1.0f / (F[0] * F[3] - F[1] * F[2]);
+  Fi[0] = F[3] * id;
+  Fi[1] = -F[1] * id;
+  Fi[2] = -F[2] * id;
+  Fi[3] = F[0] * id;
+}
+template <>
+__device__ __forceinline__ void inverse<3>(const float* F, float* Fi) {
+  const float c00 = F[4] * F[8] - F[5] * F[7], c01 = F[5] * F[6] - F[3] * F[8], c02 = F[3] * F[7] - F[4] * F[6];
+  const float id = 1.0f / (F[0] * c00 + F[1] * c01 + F[2] * c02);
+  Fi[0] = c00 * id;
+  Fi[3] = c01 * id;
+  Fi[6] = c02 * id;
+  Fi[1] = (F[2] * F[7] - F[1] * F[8]) * id;
+  Fi[4] = (F[0] * F[8] - F[2] * F[6]) * id;
+  Fi[7] = (F[1] * F[6] - F[0] * F[7]) * id;
+  Fi[2] = (F[1] * F[5] - F[2] * F[4]) * id;
+  Fi[5] = (F[2] * F[3] - F[0] * F[5]) * id;
+  Fi[8] = (F[0] * F[4] - F[1] * F[3]) * id;
+}
+
 // Block-wide exclusive scan of one int per thread (blockDim.x <= 1024).
 __device__ __forceinline__ int block_exclusive_scan(int v, int* total, int* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
@@ -294,8 +320,9 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
 }
 
 // ----------------------------------------------------- local P2G (Alg. 5)
-// dec_out: (R, capQ, d) decoder output at Q with kinds [primal, dX_0..dX_{d-1}, JVP].
-template <int D, int MATERIAL, int TRANSFER>
+// dec_out: (R, capQ, d) decoder output at Q with kinds [primal, dX_0..dX_{d-1}, JVP]
+// and, with AFFINE, the mixed rows d/dX_b of the JVP (dv/dX).
+template <int D, int MATERIAL, int TRANSFER, bool AFFINE>
 __global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t capQ) {
   const int nQ = R.counts[1];
   const uint32_t stamp = (uint32_t)(*R.step + 1);
@@ -311,6 +338,28 @@ __global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t cap
     }
     float tau[D * D];
     kirchhoff<D, MATERIAL, true>(F, R.mu, R.lam, tau);
+    // MLS: A = m C - dt V0 (4/dx^2) tau, C = (dv/dX) F^-1 with AFFINE, else 0
+    float A[D * D];
+    const float kml = R.dt * R.vol * 4.0f * R.inv_dx * R.inv_dx;
+#pragma unroll
+    for (int e = 0; e < D * D; ++e) A[e] = -kml * tau[e];
+    if (AFFINE && TRANSFER == MPM_TRANSFER_MLS) {
+      float G[D * D], Fi[D * D];
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) G[a * D + b] = dec_out[((size_t)(2 + D + b) * capQ + i) * D + a];
+      inverse<D>(F, Fi);
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          float c = 0.f;
+#pragma unroll
+          for (int e = 0; e < D; ++e) c = fmaf(G[a * D + e], Fi[e * D + b], c);
+          A[a * D + b] = fmaf(R.mass, c, A[a * D + b]);
+        }
+    }
     int base[D];
     float w[D][3], dw[D][3];
     bool ok = true;
@@ -324,7 +373,6 @@ __global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t cap
     }
     if (!ok) continue;  // flagged by rom_select
     constexpr int NS = (D == 2) ? 9 : 27;
-    const float kml = R.dt * R.vol * 4.0f * R.inv_dx * R.inv_dx;
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
       int off[D];
@@ -346,7 +394,7 @@ __global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t cap
         for (int a = 0; a < D; ++a) {
           float q = R.mass * v[a];
 #pragma unroll
-          for (int b = 0; b < D; ++b) q = fmaf(-kml * tau[a * D + b], (float)node[b] * R.dx - x[b], q);
+          for (int b = 0; b < D; ++b) q = fmaf(A[a * D + b], (float)node[b] * R.dx - x[b], q);
           mom[a] = wt * q;
         }
       } else {
@@ -784,7 +832,7 @@ struct rom_ctx {
   int64_t* step = nullptr;
   uint32_t* status = nullptr;
   int32_t* nP_all = nullptr;    // device constant P (decode-all point count)
-  float* outQ = nullptr;        // (d + 2, P, d)
+  float* outQ = nullptr;        // (2 d + 2, P, d)
   float* outS = nullptr;        // (r + 2, k, d)
   float* outLS = nullptr;       // (2, kLS * k, d) (capacity kLS * P for the fit)
   double* solve_mem = nullptr;
@@ -810,18 +858,25 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
     rom_select<3><<<1, 1024, 0, s>>>(c->dv);
   MPM_CUDA_TRY(cudaGetLastError());
   // 3. F and v at the quadrature points Q
+  const bool affine = c->cfg.affine && c->cfg.transfer == MPM_TRANSFER_MLS;
   int kq[8];
   kq[0] = 0;
   for (int a = 0; a < d; ++a) kq[1 + a] = 1 + a;
   kq[1 + d] = 1000;  // JVP along vhat_n
-  st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 1, 1, c->P, c->sv.xh32, c->sv.vh32, kq, d + 2, c->outQ,
-                          s);
+  for (int a = 0; a < d; ++a) kq[2 + d + a] = 2000 + 1 + a;  // d/dX_a of the JVP
+  st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 1, 1, c->P, c->sv.xh32, c->sv.vh32, kq,
+                          affine ? 2 * d + 2 : d + 2, c->outQ, s);
   if (st != MPM_OK) return st;
   // 4. local P2G onto I, 5. grid update + G2P to the samples
   const int b_q = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 4));
   const int M = c->cfg.material, T = c->cfg.transfer;
-#define P2G_CASE(dd, mm, tt)                                                          \
-  if (d == dd && M == mm && T == tt) rom_p2g<dd, mm, tt><<<b_q, 256, 0, s>>>(c->dv, c->outQ, c->P);
+#define P2G_CASE(dd, mm, tt)                                                                     \
+  if (d == dd && M == mm && T == tt) {                                                           \
+    if (affine)                                                                                  \
+      rom_p2g<dd, mm, tt, true><<<b_q, 256, 0, s>>>(c->dv, c->outQ, c->P);                       \
+    else                                                                                         \
+      rom_p2g<dd, mm, tt, false><<<b_q, 256, 0, s>>>(c->dv, c->outQ, c->P);                      \
+  }
   P2G_CASE(2, 0, 0) P2G_CASE(2, 0, 1) P2G_CASE(2, 1, 0) P2G_CASE(2, 1, 1)
   P2G_CASE(3, 0, 0) P2G_CASE(3, 0, 1) P2G_CASE(3, 1, 0) P2G_CASE(3, 1, 1)
 #undef P2G_CASE
@@ -893,6 +948,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
   MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
   MPM_CHECK_ARG(cfg->ridge >= 0.f, "ridge >= 0");
+  MPM_CHECK_ARG(cfg->affine == 0 || cfg->affine == 1, "affine: 0 or 1");
   auto* c = new rom_ctx();
   c->cfg = *cfg;
   c->dec = dec;
@@ -924,7 +980,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   if ((st = ralloc(&c->step, 1)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->status, 1)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->nP_all, 1)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->outQ, (size_t)(d + 2) * P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->outQ, (size_t)(2 * d + 2) * P * d)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->outS, (size_t)(r + 2) * P * d)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->outLS, (size_t)2 * kLS * P * d)) != MPM_OK) return fail(st);
   const int n_acc = r * (r + 1) / 2 + r + 1;

@@ -45,7 +45,6 @@ __device__ __forceinline__ uint64_t tr_splitmix(uint64_t state, uint64_t k) {
   return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ float act_d2(int act, float z) { return act == 0 ? (z > 0.f ? 0.f : __expf(z)) : 0.f; }
 
 struct Store {
   int d, r;

@@ -21,6 +21,12 @@ def dX(k):
     return 1 + k
 
 
+def mixed(kind):
+    """Row kind of d/d(input of tangent `kind`) of the JVP row; with kind = dX(k) this is
+    the material gradient d/dX_k of the decoded velocity (dg/dxhat) u."""
+    return _abi.DECODER_MIXED + int(kind)
+
+
 class Decoder:
     def __init__(self, d, r, width=128, n_hidden=5, activation=0):
         L = _abi.lib()

@@ -25,11 +25,11 @@ class ROM:
     """One reduced-order instance bound to a decoder and the reference positions X."""
 
     def __init__(self, decoder, X, *, dim, n_grid, dx, dt, gravity, bc, bc_width, material, transfer, rho,
-                 p_vol, E, nu, n_samples, seed, instance=0, gn_iters=3, projection=0, ridge=0.0):
+                 p_vol, E, nu, n_samples, seed, instance=0, gn_iters=3, projection=0, ridge=0.0, affine=0):
         L = _abi.lib()
         g = (C.c_float * 3)(*[float(v) for v in gravity])
         self.cfg = _abi.RomConfig(dim, n_grid, dx, dt, g, bc, bc_width, material, transfer, rho, p_vol, E, nu,
-                                  decoder.r, n_samples, seed, instance, gn_iters, projection, ridge)
+                                  decoder.r, n_samples, seed, instance, gn_iters, projection, ridge, affine)
         self._X = np.ascontiguousarray(X, np.float32) if isinstance(X, np.ndarray) else X
         self.P = int(self._X.shape[0])
         self.d, self.r = dim, decoder.r
@@ -40,13 +40,14 @@ class ROM:
         self._h = h
 
     @classmethod
-    def from_scene(cls, decoder, sc, n_samples, seed, instance=0, gn_iters=3, projection=0, X=None, ridge=0.0):
+    def from_scene(cls, decoder, sc, n_samples, seed, instance=0, gn_iters=3, projection=0, X=None, ridge=0.0,
+                   affine=0):
         k = 0
         return cls(decoder, sc.x if X is None else X, dim=sc.dim, n_grid=sc.n_grid, dx=sc.dx, dt=sc.dt,
                    gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width, material=sc.material,
                    transfer=sc.transfer, rho=sc.rho, p_vol=sc.p_vol, E=float(sc.E[k]), nu=float(sc.nu[k]),
                    n_samples=n_samples, seed=seed, instance=instance, gn_iters=gn_iters, projection=projection,
-                   ridge=ridge)
+                   ridge=ridge, affine=affine)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -82,6 +82,49 @@ def test_jvp_and_secant_rows():
         assert rel(sec, ref) < TOL_BF16, scale
 
 
+@pytest.mark.parametrize("d,n_hidden,tol", [(2, 5, TOL_BF16), (3, 5, TOL_BF16), (2, 1, 1e-5), (3, 1, 1e-5)])
+def test_mixed_rows_velocity_gradient(d, n_hidden, tol):
+    """Mixed rows d/dX_k of the JVP row against the oracle's forward-over-forward dv/dX:
+    5 hidden layers on the tensor cores (BF16), one hidden layer in FP32.  The JVP and
+    tangent rows of the same call stay as accurate as without the mixed rows."""
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL, JVP, mixed, dX
+    r, n = 16, 1500
+    p = _dec_params(d, r, n_hidden=n_hidden, seed=21)
+    dec = Decoder.from_params(p)
+    X, lat, idx = _points(n, d, r, n_lat=3, seed=22)
+    u = np.random.default_rng(23).normal(size=lat.shape)
+    Xg, latg, idxg, ug = _gpu(X.astype(np.float32), lat.astype(np.float32), idx, u.astype(np.float32))
+    kinds = [PRIMAL] + [dX(k) for k in range(d)] + [JVP] + [mixed(dX(k)) for k in range(d)]
+    out = dec.eval(Xg, latg, kinds, lat_idx=idxg, dirs=ug).cpu().numpy()
+    assert dec.status() == 0
+    Xr = X.astype(np.float32).astype(np.float64)
+    xh = lat.astype(np.float32).astype(np.float64)[idx]
+    uu = u.astype(np.float32).astype(np.float64)[idx]
+    v, G = OD.velocity_gradient(p, Xr, xh, uu)
+    _, JX, _ = OD.jacobians(p, Xr, xh)
+    assert rel(np.stack(out[1:1 + d], -1), JX) < tol
+    assert rel(out[1 + d], v) < tol
+    assert rel(np.stack(out[2 + d:], -1), G) < tol
+
+
+def test_mixed_rows_of_affine_network_vanish_and_need_partners():
+    import torch
+    from paper_2109_12390_gb300 import _abi
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL, JVP, mixed, dX
+    d, r, n = 2, 4, 200
+    for n_hidden in (0, 3):
+        p = _dec_params(d, r, n_hidden=n_hidden, act=OD.IDENTITY, seed=24)
+        dec = Decoder.from_params(p)
+        X, lat, idx = _points(n, d, r, seed=25)
+        Xg, latg, ug = _gpu(X.astype(np.float32), lat.astype(np.float32), np.ones_like(lat, np.float32))
+        out = dec.eval(Xg, latg, [PRIMAL, dX(0), dX(1), JVP, mixed(dX(0)), mixed(dX(1))], dirs=ug).cpu().numpy()
+        assert np.abs(out[4:]).max() == 0.0
+    with pytest.raises(_abi.MpmError):
+        dec.eval(Xg, latg, [PRIMAL, JVP, mixed(dX(0))], dirs=ug)   # no dX_0 tangent row
+    with pytest.raises(_abi.MpmError):
+        dec.eval(Xg, latg, [PRIMAL, dX(0), mixed(dX(0))], dirs=ug)  # no JVP row
+
+
 def test_linear_and_single_hidden_layer_fp32():
     from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
     for n_hidden, act in [(0, OD.IDENTITY), (1, OD.ELU)]:

@@ -206,6 +206,29 @@ def test_out_of_grid_is_reported_not_written():
     assert np.isfinite(x).all()
 
 
+def test_blow_up_is_reported_not_written():
+    """A particle whose speed overflows the grid spacing (|v| = 1e30) drags its neighbours to
+    huge, then non-finite, coordinates: the step must flag them and keep every index in range
+    (no write outside the grid, binning still consistent), and the context stays usable."""
+    from paper_2109_12390_gb300 import _abi
+    sc = S.block_2d(side=8)
+    sc.v[0] = (1e30, 0.0)
+    sc.x[1] = (np.nan, 0.5)
+    ctx = _ctx(sc)
+    ctx.step(4)
+    names = _abi.status_names(ctx.status())
+    assert "NONFINITE" in names or "OUT_OF_GRID" in names
+    x, _, _, _ = ctx.read_numpy()
+    assert x.shape == sc.x.shape
+    # a clean state loaded into the same context steps normally
+    sc2 = S.block_2d(side=8)
+    ctx.load_numpy(sc2.x, sc2.v, sc2.F, sc2.C)
+    ctx.step(3)
+    ref = sc2.copy()
+    OM.step(ref, 3)
+    _compare(ctx, ref)
+
+
 @pytest.mark.parametrize("n_sample", [64])
 def test_config2_full_size_sampled(n_sample):
     """262,144-particle cube, 128^3: after 5 GPU steps, the next step of sampled particles

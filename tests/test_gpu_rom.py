@@ -70,7 +70,7 @@ def test_translation_decoder_reproduces_free_fall():
 
 
 def _elu_setup(seed=3, side=32, r=16, k=64, material=OM.FIXED_COROTATED, transfer=OM.MLS, projection=0,
-               n_hidden=5):
+               n_hidden=5, affine=0):
     from paper_2109_12390_gb300.decoder import Decoder
     from paper_2109_12390_gb300.rom import ROM
     sc = S.block_2d(side=side, dt=5e-5, origin=(0.4, 0.3), E=20.0)
@@ -80,7 +80,7 @@ def _elu_setup(seed=3, side=32, r=16, k=64, material=OM.FIXED_COROTATED, transfe
     p = S.xavier_decoder(seed, 2, r, 128, n_hidden, OD.ELU, X_min=X.min(0), X_range=X.max(0) - X.min(0),
                          out_shift=c, out_scale=np.full(2, 0.05), bias_scale=0.2)
     dec = Decoder.from_params(p)
-    rom = ROM.from_scene(dec, sc, n_samples=k, seed=seed, projection=projection)
+    rom = ROM.from_scene(dec, sc, n_samples=k, seed=seed, projection=projection, affine=affine)
     rng = np.random.default_rng(seed)
     xh = 0.3 * rng.normal(size=r)
     vh = rng.normal(size=r)
@@ -88,6 +88,7 @@ def _elu_setup(seed=3, side=32, r=16, k=64, material=OM.FIXED_COROTATED, transfe
     rom.set_state(xh, vh, xp, 0)
     rs = _rom_scene(sc, k, seed)
     rs.projection = "velocity-only" if projection else "position-velocity"
+    rs.affine = "decoded" if affine else "zero"
     return sc, p, dec, rom, rs, xh, vh, xp
 
 
@@ -151,6 +152,22 @@ def test_one_step_projection_fp32_decoder(projection):
         xh_ref, flag = OR.gauss_newton(p, Xs, x_trial_ref, 2 * xh - xp, 3)
         assert not flag
         assert rel(xh1 - xh, xh_ref - xh) < 1e-3
+
+
+@pytest.mark.parametrize("n_hidden,tol", [(1, 1e-4), (5, TOL_BF16)])
+def test_one_step_affine_quadrature_velocity(n_hidden, tol):
+    """MLS local step with the decoded affine velocity C = (dv/dX) F^-1 on the quadrature
+    points: v_trial against the oracle's, and different from the C = 0 step of Algorithm 5."""
+    sc, p, dec, rom, rs, xh, vh, xp = _elu_setup(seed=5, r=4, n_hidden=n_hidden, projection=1, affine=1)
+    rom.step(1)
+    assert rom.status() & ~ALLOWED_RANDOM == 0
+    dbg = rom.debug()
+    xa = dbg["x_all"].astype(np.float64)
+    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
+    assert rel(dbg["v_trial"], v_trial) < tol
+    rs.affine = "zero"
+    v_zero, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
+    assert rel(v_zero, v_trial) > 1e-2   # the affine term is not negligible here (3-4 %)
 
 
 def test_fit_initial_condition():

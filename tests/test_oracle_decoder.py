@@ -133,3 +133,36 @@ def test_adam_constant_gradient_closed_form():
     assert q1[0] == pytest.approx(q2[0], rel=1e-6)
     assert D.lr_schedule(0, 100) == pytest.approx(1e-3)
     assert D.lr_schedule(99, 100) == pytest.approx(1e-6)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_velocity_gradient_against_central_differences(d):
+    """dv/dX of the decoded velocity v = (dg/dxhat) u against central differences in X of
+    the latent JVP (an independent forward-mode evaluation), and v against the JVP itself."""
+    rng = np.random.default_rng(20 + d)
+    r = 5
+    X = rng.uniform(0.2, 0.8, size=(7, d))
+    dec = S.xavier_decoder(3, d, r, 24, 3, D.ELU, X_min=X.min(0), X_range=X.max(0) - X.min(0) + 0.1,
+                           out_shift=np.full(d, 0.5), out_scale=np.full(d, 0.3), bias_scale=0.3)
+    xh = 0.4 * rng.normal(size=r)
+    u = rng.normal(size=r)
+    v, G = D.velocity_gradient(dec, X, xh, u)
+    _, v_ref = D.jvp_latent(dec, X, xh, u)
+    np.testing.assert_allclose(v, v_ref, rtol=1e-13, atol=1e-15)
+    h = 1e-5
+    for k in range(d):
+        e = np.zeros(d)
+        e[k] = h
+        _, vp = D.jvp_latent(dec, X + e, xh, u)
+        _, vm = D.jvp_latent(dec, X - e, xh, u)
+        fd = (vp - vm) / (2 * h)
+        assert np.linalg.norm(G[:, :, k] - fd) <= 1e-7 * np.linalg.norm(fd)
+
+
+def test_velocity_gradient_of_affine_networks_is_zero():
+    """Identity activation: g is affine in (X, xhat) jointly, so dv/dX vanishes exactly."""
+    rng = np.random.default_rng(4)
+    X = rng.uniform(size=(5, 2))
+    dec = S.xavier_decoder(1, 2, 3, 16, 2, D.IDENTITY, X_min=X.min(0), X_range=X.max(0) - X.min(0))
+    _, G = D.velocity_gradient(dec, X, rng.normal(size=3), rng.normal(size=3))
+    assert np.abs(G).max() == 0.0
