@@ -1,4 +1,5 @@
-"""Benchmark of the hot path: MPM particle-steps/s on the 3D fixed-corotated cube.
+"""Benchmark of the hot path: MPM particle-steps/s on the 3D fixed-corotated cube, and the
+reduced-order model's steps/s against the full-order model at its measured position error.
 
 Workload (N = 1): 262,144 particles (64^3 jittered lattice at dx/2), 128^3
 grid, fixed-corotated material with FP64-refined polar factor, slip floor,
@@ -6,6 +7,11 @@ dt = 5e-5, MLS-MPM.  A step is one explicit MPM step of every instance
 (binning, particle-to-grid, grid update, grid-to-particle).  Inputs are
 resident in HBM when the timed region starts; L2 is flushed (a 256 MiB write)
 before every timed step, outside its CUDA-event interval.
+
+The reduced-order leg (key "rom"; skipped with --no-rom) generates snapshots with the GPU
+full-order model, trains the decoder on the GPU, runs the reduced model on a held-out 2D impact
+scene and reports its steps/s next to the full-order steps/s on the same scene, with the
+accumulated relative position error of Section 5.
 
 With torchrun (N > 1) every rank runs an independent replica of the workload
 (the single-scene step does not shard; batched instances would shard by
@@ -32,7 +38,7 @@ sys.path.insert(0, ROOT)
 
 import synth.scenes as S  # noqa: E402
 
-METRIC = "MPM particle-steps/s"
+METRIC = "MPM particle-steps/s vs ROM steps/s at \u22641e-2 rel. position err, 1 GB300"
 UNIT = "particle-steps/s"
 WORKLOAD = "3D fixed-corotated cube, 262144 particles, 128^3 grid, MLS-MPM, FP64-refined polar, dt=5e-5, slip floor"
 # algorithmic bytes per particle-step (3D): particle state read + written once,
@@ -132,6 +138,46 @@ def cpu_baseline_fom(sc, max_seconds=20.0):
             "sample": f"{steps} full step(s) of the {sc.n_particles}-particle cube in FP64 numpy, single thread"}
 
 
+# reduced-order leg: 2D impact scene (4096 particles, 128^2 grid, E = 1e4) against the full-order
+# model on the same parameters, decoder trained on 16 snapshot trajectories of held-out (E, v0)
+ROM_STEPS = 4000            # 0.2 s of simulated time at dt = 5e-5
+ROM_TRAIN_STEPS = 3000
+ROM_SETTINGS = dict(n_samples=256, gn_iters=3, projection=0, ridge=1e-4, affine=1)
+
+
+def rom_leg(r=16):
+    """Snapshots from the GPU full-order model, decoder training, reduced-order run and the
+    accumulated position error (Section 5) against the full-order run on the same scene."""
+    import torch
+    from paper_2109_12390_gb300 import pipeline as PL
+    from paper_2109_12390_gb300.train import generate_snapshots
+    train_sc = S.batch_2d(seed=3, n_inst=16, fixed_side=64, n_grid=128, origin_y=0.06)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    snaps = generate_snapshots(train_sc, ROM_STEPS, 10)
+    torch.cuda.synchronize()
+    t_snap = time.perf_counter() - t0
+    dec, _ = PL.decoder_for_snapshots(snaps, r, seed=0)
+    tr, hist, t_train = PL.train(snaps, dec, steps=ROM_TRAIN_STEPS)
+    loss = hist[-1][1]
+    tr.close()
+    test_sc = S.block_2d(seed=4, side=64, dt=5e-5, origin=(0.375, 0.06), E=1e4)
+    fom_xs, fom_rate, fom_status = PL.fom_positions(test_sc, ROM_STEPS)
+    run = PL.rom_error(dec, test_sc, fom_xs, seed=4, **ROM_SETTINGS)
+    return {
+        "scene": "2D neo-Hookean block 64x64 (4096 particles), 128^2 grid, E=1e4, nu=0.3, dt=5e-5, sticky walls, "
+                 f"floor impact, {ROM_STEPS} steps; decoder 2+{r}->128x5->2 ELU trained on 16 instances "
+                 "(E, v0) ~ U[5e3,1.5e4] x U[-0.5,0.5]^2",
+        "rom_steps_per_s": run.rom_steps_per_s, "fom_steps_per_s": fom_rate,
+        "speedup": run.rom_steps_per_s / fom_rate, "rel_position_error": run.error_percent / 100.0,
+        "meets_1e-2": bool(run.error_percent <= 1.0), "rom_status_word": run.status, "fom_status_word": fom_status,
+        "settings": dict(ROM_SETTINGS, latent_dim=r),
+        "training": {"steps": ROM_TRAIN_STEPS, "batch_points": 65536, "seconds": t_train,
+                     "points_per_s": ROM_TRAIN_STEPS * 65536 / t_train, "final_loss": loss,
+                     "snapshot_seconds": t_snap, "snapshots": int(snaps["n_snap"])},
+    }
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -186,35 +232,42 @@ def run_ours(args, ws, rank, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        ctx.step_profiled(1)
+    ctx.step_profiled(args.warmup, flush=flush)
     assert ctx.status() == 0, "unstable state during warm-up"
-    kern = []
-    step_ms = []
     barrier()
     with Clocks(local) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            s0 = torch.cuda.Event(enable_timing=True)
-            s1 = torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            k = ctx.step_profiled(1)
-            s1.record(stream)
-            s1.synchronize()
-            step_ms.append(s0.elapsed_time(s1))
-            kern.append(k[0])
+        # all K steps enqueued at once; events around every kernel and every step on the
+        # launching stream; the L2 flush runs between steps, outside the timed intervals
+        kern = ctx.step_profiled(args.steps, flush=flush)
     barrier()
     status = ctx.status()
+    step_ms = kern[:, 3]
     total_ms = float(np.sum(step_ms))
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    kern = np.array(kern)
     fused_ms = float(kern[:, 0].mean())
     peak, peak_kind = _peaks()
     achieved = ALGO_BYTES_3D * P / (fused_ms * 1e-3) / 1e9
+
+    # the same workload with the compensated-FP32 rotation correction of the polar factor, and a
+    # scaled-up cube (2,097,152 particles on 256^3, working set far above L2)
+    variants = {}
+    for name, vsc, eft in (("polar_eft", sc, 1), ("cube_2M_256", S.cube_3d(side=128, n_grid=256, dt=2.5e-5), 0)):
+        vctx = MPM.from_scene(vsc, polar_eft=eft)
+        vctx.load_numpy(vsc.x, vsc.v, vsc.F, vsc.C)
+        vctx.step_profiled(args.warmup, flush=flush)
+        vk = vctx.step_profiled(min(args.steps, 20), flush=flush)
+        vf = float(vk[:, 0].mean())
+        variants[name] = {"particles": vsc.n_particles, "polar": "compensated FP32" if eft else "FP64",
+                          "ms_per_step": float(vk[:, 3].mean()), "fused_ms": vf,
+                          "particle_steps_per_s": vsc.n_particles / (float(vk[:, 3].mean()) * 1e-3),
+                          "fused_gbs": ALGO_BYTES_3D * vsc.n_particles / (vf * 1e-3) / 1e9,
+                          "status_word": vctx.status()}
+        variants[name]["fused_frac"] = variants[name]["fused_gbs"] / _peaks()[0]
+        vctx.close()
 
     # end to end through the public API: pinned host state in, one step, state out
     d = sc.dim
@@ -258,12 +311,15 @@ def run_ours(args, ws, rank, local):
                            "mpm_permute": float(kern[:, 2].mean())},
             "e2e": {"value": ws * P * args.steps / (e2e_total * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+            "variants": variants,
             "gpu_launches": 3 * args.steps,
             "clocks": clk.summary(),
             "status_word": status,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_fom(sc)
+        if not args.no_rom:
+            line["rom"] = rom_leg()
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
@@ -278,6 +334,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rom", action="store_true", help="skip the reduced-order leg (training + ROM run)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

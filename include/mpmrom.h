@@ -90,6 +90,13 @@ const char* mpm_last_error(void);
  *   inst_offsets  host array of n_inst+1 int64: particles of instance k are
  *                 rows inst_offsets[k] .. inst_offsets[k+1]-1 of the state
  *                 arrays.
+ *   polar_eft     3D fixed-corotated only: the polar factor R of F is an FP32
+ *                 scaled Newton iteration plus one rotation correction whose
+ *                 cancelling sums need more than FP32.  0 (default): those
+ *                 sums in FP64.  1: as compensated sums of FP32 error-free
+ *                 transformations (as accurate as twice FP32 precision, at
+ *                 FP32 throughput; GB300's FP64 rate is a small fraction of
+ *                 its FP32 rate).
  */
 typedef struct mpm_config {
   int32_t dim;
@@ -107,6 +114,7 @@ typedef struct mpm_config {
   const float* E;
   const float* nu;
   const int64_t* inst_offsets;
+  int32_t polar_eft;
 } mpm_config;
 
 typedef struct mpm_ctx mpm_ctx;
@@ -152,11 +160,17 @@ mpm_status mpm_step(mpm_ctx* ctx, int n_steps, void* stream);
 
 /*
  * mpm_step with CUDA events recorded around each kernel of every step on
- * `stream`; synchronises after each step and writes the device durations in
- * milliseconds of [fused step kernel, scan, re-binning] for step k to
- * kernel_ms[3k .. 3k+2] (host array of 3 * n_steps floats).  For measurement.
+ * `stream`, for measurement.  All n_steps steps are enqueued before the one
+ * synchronisation at the end, so the host adds no gaps between them.  If
+ * flush_bytes > 0, flush_buf (caller-owned device buffer of flush_bytes
+ * bytes) is overwritten between steps, outside the timed intervals (to evict
+ * the working set from L2).  Writes the device durations in milliseconds of
+ * [fused step kernel, scan, re-binning] for step k to kernel_ms[4k .. 4k+2]
+ * and the whole step (first to last event) to kernel_ms[4k+3] (host array of
+ * 4 * n_steps floats).
  */
-mpm_status mpm_step_profiled(mpm_ctx* ctx, int n_steps, float* kernel_ms, void* stream);
+mpm_status mpm_step_profiled(mpm_ctx* ctx, int n_steps, void* flush_buf, size_t flush_bytes, float* kernel_ms,
+                             void* stream);
 
 /*
  * Synchronises `stream`, then returns the OR of MPM_STATUS_* bits raised by

@@ -25,7 +25,7 @@ class MpmConfig(C.Structure):
         ("gravity", C.c_float * 3), ("bc", C.c_int32), ("bc_width", C.c_int32),
         ("material", C.c_int32), ("transfer", C.c_int32), ("rho", C.c_float), ("p_vol", C.c_float),
         ("n_inst", C.c_int32), ("E", C.POINTER(C.c_float)), ("nu", C.POINTER(C.c_float)),
-        ("inst_offsets", C.POINTER(C.c_int64)),
+        ("inst_offsets", C.POINTER(C.c_int64)), ("polar_eft", C.c_int32),
     ]
 
 
@@ -75,7 +75,7 @@ SIGNATURES = [
     ("mpm_set_state", C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_void_p]),
     ("mpm_get_state", C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_void_p]),
     ("mpm_step", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
-    ("mpm_step_profiled", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.c_void_p]),
+    ("mpm_step_profiled", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_float), C.c_void_p]),
     ("mpm_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
     ("mpm_debug_bins", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("mpm_num_block_keys", C.c_int64, [C.c_void_p]),

@@ -247,8 +247,8 @@ __device__ __forceinline__ void count_key_aggregated(int key, int32_t* counts) {
 // The fused step kernel.  FIRST = true runs only the particle-to-grid half
 // (the transfer of a freshly loaded state).
 // --------------------------------------------------------------------------
-template <int D, int MATERIAL, int TRANSFER, bool FIRST, bool FP64_POLAR>
-__global__ void __launch_bounds__(kChunk, 2) mpm_g2p2g(DevParams p, StateView src, StateView dst,
+template <int D, int MATERIAL, int TRANSFER, bool FIRST, int POLAR>
+__global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView src, StateView dst,
                                                         const int32_t* __restrict__ perm,
                                                         const int4* __restrict__ work, const int32_t* n_work,
                                                         const float4* __restrict__ grid_cur, float4* grid_nxt,
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kChunk, 2) mpm_g2p2g(DevParams p, StateView sr
   constexpr int NC = (D == 2) ? TC * TC : TC * TC * TC;
   constexpr int DD = D * D;
   constexpr int PD = 2 * D + DD;                 // per-particle P2G record
-  constexpr int NSLAB = (D == 2) ? 3 : 9;        // tasks per cell, 3 stencil nodes each
+  constexpr int NSLAB = 3;                       // tasks per cell (leading stencil offset)
   __shared__ float4 s_v4[NG];
   __shared__ float s_m[NT];
   __shared__ float s_p[D * NT];
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kChunk, 2) mpm_g2p2g(DevParams p, StateView sr
       }
       // particle-to-grid record of the (new) state
       float tau[DD];
-      kirchhoff<D, MATERIAL, FP64_POLAR>(F, ml.x, ml.y, tau);
+      kirchhoff<D, MATERIAL, POLAR>(F, ml.x, ml.y, tau);
       int nb[D];
       bool out_of_grid = false, in_cells = true;
       float fx[D];
@@ -575,12 +575,13 @@ __global__ void __launch_bounds__(kChunk, 2) mpm_g2p2g(DevParams p, StateView sr
       for (int i = 0; i < PD; ++i) dstr[i] = rec[i];
     }
     __syncthreads();
-    // cell-owner accumulation: one task per (non-empty cell, row of 3 stencil
-    // nodes) sums its cell's particles in registers, then adds to the tile
+    // cell-owner accumulation: one task per (non-empty cell, leading stencil
+    // offset o0) sums its cell's particles in registers over the 3 (2D) or
+    // 3 x 3 (3D) stencil nodes with that offset, then adds them to the tile
     const int n_tasks = s_nne * NSLAB;
     for (int task = threadIdx.x; task < n_tasks; task += blockDim.x) {
       const int cell = s_cells[task / NSLAB];
-      const int slab = task % NSLAB;
+      const int o0 = task % NSLAB;
       int crel[D];
       {
         int r = cell;
@@ -590,94 +591,91 @@ __global__ void __launch_bounds__(kChunk, 2) mpm_g2p2g(DevParams p, StateView sr
           r /= TC;
         }
       }
-      // stencil row: fixed offsets on the leading axes, 3 nodes along the last
-      const int o0 = (D == 2) ? slab : slab / 3;
-      const int o1 = (D == 2) ? 0 : slab % 3;
-      float am[3] = {0.f, 0.f, 0.f};
-      float ap[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      constexpr int NROW = (D == 2) ? 1 : 3;   // rows of 3 nodes (middle-axis offset o1)
+      float am[NROW][3], ap[NROW][3][D];
+#pragma unroll
+      for (int o1 = 0; o1 < NROW; ++o1)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          am[o1][kk] = 0.f;
+#pragma unroll
+          for (int a = 0; a < D; ++a) ap[o1][kk][a] = 0.f;
+        }
       const int q1 = s_off[cell + 1];
       for (int q = s_off[cell]; q < q1; ++q) {
         const float* rr = s_rec + (size_t)q * PD;
-        float wl[3], wlast[3];
-        float dwl[3], dwlast[3];
+        float wl[3], wlast[3], wmid[3];
         bspline_w(rr[0], wl);
         bspline_w(rr[D - 1], wlast);
-        float wlead = wl[0] * 0.f;
-        float wfix;  // product of the fixed-axis weights
-        float wm[3] = {0.f, 0.f, 0.f};
-        if (D == 2) {
-          wfix = (o0 == 0 ? wl[0] : (o0 == 1 ? wl[1] : wl[2]));
-        } else {
-          float wmid[3];
-          bspline_w(rr[1], wmid);
-          wfix = (o0 == 0 ? wl[0] : (o0 == 1 ? wl[1] : wl[2])) * (o1 == 0 ? wmid[0] : (o1 == 1 ? wmid[1] : wmid[2]));
-          wm[0] = wmid[0];
-          wm[1] = wmid[1];
-          wm[2] = wmid[2];
-        }
-        (void)wlead;
+        if (D == 3) bspline_w(rr[1], wmid);
+        const float w0 = (o0 == 0 ? wl[0] : (o0 == 1 ? wl[1] : wl[2]));
         if (TRANSFER == MPM_TRANSFER_MLS) {
           // mom = w (c + A (o dx)) with o the node offset from the cell base
           const float* c = rr + D;
           const float* A = rr + 2 * D;
-          float cf[3];
+          float c0[D];
 #pragma unroll
-          for (int a = 0; a < D; ++a) {
-            float t = c[a] + A[a * D + 0] * ((float)o0 * p.dx);
-            if (D == 3) t += A[a * D + 1] * ((float)o1 * p.dx);
-            cf[a] = t;
-          }
+          for (int a = 0; a < D; ++a) c0[a] = fmaf(A[a * D + 0], (float)o0 * p.dx, c[a]);
 #pragma unroll
-          for (int kk = 0; kk < 3; ++kk) {
-            const float wt = wfix * wlast[kk];
-            am[kk] += wt * p.mass;
+          for (int o1 = 0; o1 < NROW; ++o1) {
+            const float w01 = (D == 3) ? w0 * wmid[o1] : w0;
+            float c1[D];
 #pragma unroll
-            for (int a = 0; a < D; ++a) ap[kk][a] = fmaf(wt, fmaf(A[a * D + D - 1], (float)kk * p.dx, cf[a]), ap[kk][a]);
+            for (int a = 0; a < D; ++a) c1[a] = (D == 3) ? fmaf(A[a * D + 1], (float)o1 * p.dx, c0[a]) : c0[a];
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+              const float wt = w01 * wlast[kk];
+              am[o1][kk] = fmaf(wt, p.mass, am[o1][kk]);
+#pragma unroll
+              for (int a = 0; a < D; ++a)
+                ap[o1][kk][a] = fmaf(wt, fmaf(A[a * D + D - 1], (float)kk * p.dx, c1[a]), ap[o1][kk][a]);
+            }
           }
         } else {
+          float dwl[3], dwlast[3], dwmid[3];
           bspline_dw(rr[0], dwl);
           bspline_dw(rr[D - 1], dwlast);
+          if (D == 3) bspline_dw(rr[1], dwmid);
           const float* mv = rr + D;
           const float* kt = rr + 2 * D;
-          const float wl0 = (o0 == 0 ? wl[0] : (o0 == 1 ? wl[1] : wl[2]));
-          const float dwl0 = (o0 == 0 ? dwl[0] : (o0 == 1 ? dwl[1] : dwl[2]));
-          float wmid1 = 1.f, dwmid1 = 0.f;
-          if (D == 3) {
-            float dwm[3];
-            bspline_dw(rr[1], dwm);
-            wmid1 = (o1 == 0 ? wm[0] : (o1 == 1 ? wm[1] : wm[2]));
-            dwmid1 = (o1 == 0 ? dwm[0] : (o1 == 1 ? dwm[1] : dwm[2]));
-          }
+          const float dw0 = (o0 == 0 ? dwl[0] : (o0 == 1 ? dwl[1] : dwl[2]));
 #pragma unroll
-          for (int kk = 0; kk < 3; ++kk) {
-            const float wt = wfix * wlast[kk];
-            float grad[3];
-            grad[0] = dwl0 * p.inv_dx * wmid1 * wlast[kk];
-            if (D == 3) grad[1] = wl0 * dwmid1 * p.inv_dx * wlast[kk];
-            grad[D - 1] = wl0 * wmid1 * dwlast[kk] * p.inv_dx;
-            am[kk] += wt * p.mass;
+          for (int o1 = 0; o1 < NROW; ++o1) {
+            const float wm1 = (D == 3) ? wmid[o1] : 1.f;
+            const float dwm1 = (D == 3) ? dwmid[o1] : 0.f;
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-              float f = 0.f;
+            for (int kk = 0; kk < 3; ++kk) {
+              const float wt = w0 * wm1 * wlast[kk];
+              float grad[3];
+              grad[0] = dw0 * p.inv_dx * wm1 * wlast[kk];
+              if (D == 3) grad[1] = w0 * dwm1 * p.inv_dx * wlast[kk];
+              grad[D - 1] = w0 * wm1 * dwlast[kk] * p.inv_dx;
+              am[o1][kk] = fmaf(wt, p.mass, am[o1][kk]);
 #pragma unroll
-              for (int b = 0; b < D; ++b) f = fmaf(kt[a * D + b], grad[b], f);
-              ap[kk][a] += wt * mv[a] - f;
+              for (int a = 0; a < D; ++a) {
+                float f = 0.f;
+#pragma unroll
+                for (int b = 0; b < D; ++b) f = fmaf(kt[a * D + b], grad[b], f);
+                ap[o1][kk][a] += wt * mv[a] - f;
+              }
             }
           }
         }
       }
-      // add the row of 3 nodes to the shared tile: tile node = cell + offset + 1 (tile starts at b0 - 1)
+      // add the task's nodes to the shared tile: tile node = cell + offset (tile starts at b0 - 1)
 #pragma unroll
-      for (int kk = 0; kk < 3; ++kk) {
-        int trel[D];
-        trel[0] = crel[0] + o0;
-        if (D == 3) trel[1] = crel[1] + o1;
-        trel[D - 1] = crel[D - 1] + kk;
-        const int t = tile_index<D, TP>(trel);
-        atomicAdd(&s_m[t], am[kk]);
+      for (int o1 = 0; o1 < NROW; ++o1)
 #pragma unroll
-        for (int a = 0; a < D; ++a) atomicAdd(&s_p[a * NT + t], ap[kk][a]);
-      }
+        for (int kk = 0; kk < 3; ++kk) {
+          int trel[D];
+          trel[0] = crel[0] + o0;
+          if (D == 3) trel[1] = crel[1] + o1;
+          trel[D - 1] = crel[D - 1] + kk;
+          const int t = tile_index<D, TP>(trel);
+          atomicAdd(&s_m[t], am[o1][kk]);
+#pragma unroll
+          for (int a = 0; a < D; ++a) atomicAdd(&s_p[a * NT + t], ap[o1][kk][a]);
+        }
     }
     __syncthreads();
     flush_tile<D, TP>(s_m, s_p, tile_lo, inst, grid_nxt, touched_nxt, p);
@@ -960,7 +958,7 @@ using namespace mpmrom;
 
 struct mpm_ctx {
   int D = 0, n = 0, B = 0, nb = 0, nblk = 0, n_keys = 0, P = 0, n_inst = 0;
-  int material = 0, transfer = 0;
+  int material = 0, transfer = 0, polar_eft = 0;
   int64_t gnodes = 0;
   mpm_config cfg{};
   std::vector<float> E, nu;
@@ -1000,14 +998,14 @@ mpm_status dalloc(T** p, size_t count) {
     if (_s != MPM_OK) return _s; \
   } while (0)
 
-template <int D, int MAT, int TR, bool FIRST, bool FP64>
+template <int D, int MAT, int TR, bool FIRST, int POLAR>
 mpm_status launch_fused_t(mpm_ctx* c, cudaStream_t s) {
   StateView src{c->state[c->cur], c->id[c->cur]};
   StateView dst{c->state[1 - c->cur], c->id[1 - c->cur]};
   float4* gcur = c->grid[c->g];
   float4* gnxt = FIRST ? c->grid[c->g] : c->grid[1 - c->g];
   uint8_t* tn = FIRST ? c->touched[c->g] : c->touched[1 - c->g];
-  mpm_g2p2g<D, MAT, TR, FIRST, FP64><<<c->fused_grid, kChunk, 0, s>>>(
+  mpm_g2p2g<D, MAT, TR, FIRST, POLAR><<<c->fused_grid, kChunk, 0, s>>>(
       c->dp, src, dst, c->perm, c->work, c->n_work, gcur, gnxt, tn, c->key, c->counts, c->status);
   MPM_CUDA_TRY(cudaGetLastError());
   return MPM_OK;
@@ -1016,11 +1014,16 @@ mpm_status launch_fused_t(mpm_ctx* c, cudaStream_t s) {
 template <bool FIRST>
 mpm_status launch_fused(mpm_ctx* c, cudaStream_t s) {
   const int D = c->D, M = c->material, T = c->transfer;
-#define CASE(d, m, t)                                        \
-  if (D == d && M == m && T == t) return launch_fused_t<d, m, t, FIRST, true>(c, s);
+  // the polar variant matters for the 3D fixed-corotated material only
+#define CASE(d, m, t)                                                                       \
+  if (D == d && M == m && T == t) return launch_fused_t<d, m, t, FIRST, POLAR_EFT>(c, s);
   CASE(2, 0, 0) CASE(2, 0, 1) CASE(2, 1, 0) CASE(2, 1, 1)
-  CASE(3, 0, 0) CASE(3, 0, 1) CASE(3, 1, 0) CASE(3, 1, 1)
+  CASE(3, 0, 0) CASE(3, 0, 1)
 #undef CASE
+  if (D == 3 && M == 1 && T == 0)
+    return c->polar_eft ? launch_fused_t<3, 1, 0, FIRST, POLAR_EFT>(c, s) : launch_fused_t<3, 1, 0, FIRST, POLAR_FP64>(c, s);
+  if (D == 3 && M == 1 && T == 1)
+    return c->polar_eft ? launch_fused_t<3, 1, 1, FIRST, POLAR_EFT>(c, s) : launch_fused_t<3, 1, 1, FIRST, POLAR_FP64>(c, s);
   return set_error(MPM_EINVAL, "unsupported (dim, material, transfer)");
 }
 
@@ -1100,6 +1103,7 @@ mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
   MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
   MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
   MPM_CHECK_ARG(cfg->bc == MPM_BC_STICKY || cfg->bc == MPM_BC_SLIP_FLOOR, "bc");
+  MPM_CHECK_ARG(cfg->polar_eft == 0 || cfg->polar_eft == 1, "polar_eft: 0 or 1");
   MPM_CHECK_ARG(cfg->bc_width >= 0, "bc_width");
   MPM_CHECK_ARG(cfg->inst_offsets[0] == 0, "inst_offsets[0] must be 0");
   for (int k = 0; k < cfg->n_inst; ++k)
@@ -1123,6 +1127,7 @@ mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
   c->P = (int)P64;
   c->material = cfg->material;
   c->transfer = cfg->transfer;
+  c->polar_eft = cfg->polar_eft;
   c->gnodes = c->D == 2 ? (int64_t)c->n * c->n : (int64_t)c->n * c->n * c->n;
   c->E.assign(cfg->E, cfg->E + c->n_inst);
   c->nu.assign(cfg->nu, cfg->nu + c->n_inst);
@@ -1277,23 +1282,31 @@ mpm_status mpm_step(mpm_ctx* c, int n_steps, void* stream) {
   return MPM_OK;
 }
 
-mpm_status mpm_step_profiled(mpm_ctx* c, int n_steps, float* kernel_ms, void* stream) {
+mpm_status mpm_step_profiled(mpm_ctx* c, int n_steps, void* flush_buf, size_t flush_bytes, float* kernel_ms,
+                             void* stream) {
   MPM_CHECK_ARG(c && kernel_ms, "null argument");
   MPM_CHECK_ARG(c->loaded, "mpm_set_state must be called first");
   MPM_CHECK_ARG(n_steps >= 0, "n_steps must be >= 0");
+  MPM_CHECK_ARG(flush_bytes == 0 || flush_buf, "flush_buf is null");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t ev[4];
-  for (int i = 0; i < 4; ++i) MPM_CUDA_TRY(cudaEventCreate(&ev[i]));
+  std::vector<cudaEvent_t> ev((size_t)4 * n_steps, nullptr);
   mpm_status st = MPM_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) st = set_error(MPM_ECUDA, "cudaEventCreate");
   for (int k = 0; k < n_steps && st == MPM_OK; ++k) {
-    cudaEventRecord(ev[0], s);
+    cudaEvent_t* e = ev.data() + 4 * k;
+    if (k > 0 && flush_bytes > 0 && cudaMemsetAsync(flush_buf, k & 0xff, flush_bytes, s) != cudaSuccess) {
+      st = set_error(MPM_ECUDA, "flush memset");
+      break;
+    }
+    cudaEventRecord(e[0], s);
     st = launch_fused<false>(c, s);
     if (st != MPM_OK) break;
     c->cur = 1 - c->cur;
-    cudaEventRecord(ev[1], s);
+    cudaEventRecord(e[1], s);
     mpm_scan<<<c->n_scan_tiles, kScanTile, 0, s>>>(c->n_keys, c->P, c->counts, c->offsets, c->cursor, c->work,
                                                    c->n_work, c->max_work, c->tile_state, c->status);
-    cudaEventRecord(ev[2], s);
+    cudaEventRecord(e[2], s);
     int blocks = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 8));
     if (c->D == 2)
       mpm_permute<2><<<blocks, 256, 0, s>>>(c->dp, c->key, c->offsets, c->cursor, c->perm, c->grid[c->g],
@@ -1301,17 +1314,22 @@ mpm_status mpm_step_profiled(mpm_ctx* c, int n_steps, float* kernel_ms, void* st
     else
       mpm_permute<3><<<blocks, 256, 0, s>>>(c->dp, c->key, c->offsets, c->cursor, c->perm, c->grid[c->g],
                                             c->touched[c->g], c->tile_state, c->n_scan_tiles);
-    cudaEventRecord(ev[3], s);
+    cudaEventRecord(e[3], s);
     c->g = 1 - c->g;
-    if (cudaEventSynchronize(ev[3]) != cudaSuccess) {
-      st = set_error(MPM_ECUDA, "event sync");
-      break;
-    }
-    for (int q = 0; q < 3; ++q) cudaEventElapsedTime(&kernel_ms[3 * k + q], ev[q], ev[q + 1]);
   }
-  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (st == MPM_OK && n_steps > 0) {
+    if (cudaEventSynchronize(ev.back()) != cudaSuccess) st = set_error(MPM_ECUDA, "event sync");
+    for (int k = 0; k < n_steps && st == MPM_OK; ++k) {
+      const cudaEvent_t* e = ev.data() + 4 * k;
+      for (int q = 0; q < 3; ++q) cudaEventElapsedTime(&kernel_ms[4 * k + q], e[q], e[q + 1]);
+      cudaEventElapsedTime(&kernel_ms[4 * k + 3], e[0], e[3]);
+    }
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (st != MPM_OK) return st;
   MPM_CUDA_TRY(cudaGetLastError());
-  return st;
+  return MPM_OK;
 }
 
 mpm_status mpm_get_state(mpm_ctx* c, float* x, float* v, float* F, float* C, void* stream) {
@@ -1363,6 +1381,7 @@ mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F,
   MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
   MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
   MPM_CHECK_ARG(cfg->bc == MPM_BC_STICKY || cfg->bc == MPM_BC_SLIP_FLOOR, "bc");
+  MPM_CHECK_ARG(cfg->polar_eft == 0 || cfg->polar_eft == 1, "polar_eft: 0 or 1");
   MPM_CHECK_ARG(cfg->bc_width >= 0 && cfg->inst_offsets[0] == 0, "bc_width, inst_offsets[0]");
   for (int k = 0; k < cfg->n_inst; ++k)
     MPM_CHECK_ARG(cfg->inst_offsets[k + 1] >= cfg->inst_offsets[k], "inst_offsets must be non-decreasing");
@@ -1387,6 +1406,7 @@ mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F,
   c.P = (int)P64;
   c.material = cfg->material;
   c.transfer = cfg->transfer;
+  c.polar_eft = cfg->polar_eft;
   c.gnodes = c.D == 2 ? (int64_t)c.n * c.n : (int64_t)c.n * c.n * c.n;
   int dev = 0;
   MPM_CUDA_TRY(cudaGetDevice(&dev));

@@ -60,11 +60,16 @@ __device__ __forceinline__ float det_minus_one<3>(const float F[9]) {
 // (F00 + F11, F10 - F01).
 //
 // 3D: scaled Newton iteration X <- (z X + (z X)^-T) / 2, z = |det X|^(-1/3)
-// (Higham 1986) in FP32, followed by an FP64 correction of the rotation: with
-// R0 the FP32 iterate, M = R0^T F = e^W S up to the FP32 error W (antisymmetric),
-// and the axial vector w of W solves (tr(S) I - S) w = axial(M - M^T).  The
-// axial vector of M - M^T is a difference of O(1) products that cancels to
-// O(1e-7); it is accumulated in FP64.  R = R0 (I + W + W^2/2).
+// (Higham 1986) in FP32, followed by a correction of the rotation: with R0 the
+// FP32 iterate, M = R0^T F = e^W S up to the FP32 error W (antisymmetric), and
+// the axial vector w of W solves (tr(S) I - S) w = axial(M - M^T).  The axial
+// vector of M - M^T is a difference of O(1) products that cancels to O(1e-7);
+// it is accumulated either in FP64 (POLAR_FP64) or, at FP32 throughput, as an
+// exact sum of FP32 error-free transformations (POLAR_EFT: every product a b
+// split into p + e with e = fma(a, b, -p) exactly (Dekker 1971), the p summed
+// with Knuth's TwoSum and all rounding errors added at the end, the
+// compensated summation of Ogita, Rump and Oishi 2005: as accurate as
+// summing in twice the working precision).  R = R0 (I + W + W^2/2).
 // Returns F - R directly (the fixed-corotated stress needs only that), with
 // F - R0 formed in FP32 where its entries cancel exactly (Sterbenz) and the
 // small rotation correction subtracted afterwards.
@@ -92,7 +97,35 @@ __device__ __forceinline__ void cofactor3(const float X[9], float C[9]) {
   C[8] = fmaf(X[0], X[4], -X[1] * X[3]);
 }
 
-template <bool FP64_REFINE>
+constexpr int POLAR_FP32 = 0;  // scaled Newton only
+constexpr int POLAR_FP64 = 1;  // + FP64 rotation correction
+constexpr int POLAR_EFT = 2;   // + rotation correction from compensated FP32 sums
+
+// s + err = a + b exactly (Knuth's TwoSum; no reassociation under nvcc's
+// default floating-point rules)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = a + b;
+  const float bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+}
+
+// sum_k x_k y_k (6 terms) by Dot2 of Ogita, Rump and Oishi 2005: each product
+// split exactly into p + e, the p summed with TwoSum, every rounding error
+// collected in c and added once at the end.
+__device__ __forceinline__ float dot6_compensated(const float x[6], const float y[6]) {
+  float s = 0.f, c = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float p = x[k] * y[k];
+    const float e = fmaf(x[k], y[k], -p);
+    float err;
+    two_sum(s, p, s, err);
+    c += err + e;
+  }
+  return s + c;
+}
+
+template <int REFINE>
 __device__ __forceinline__ void f_minus_polar_3d(const float F[9], float out[9]) {
   float X[9];
 #pragma unroll
@@ -116,16 +149,36 @@ __device__ __forceinline__ void f_minus_polar_3d(const float F[9], float out[9])
   // F - R0 (row-major); entries that cancel are exact in FP32
 #pragma unroll
   for (int i = 0; i < 9; ++i) out[i] = F[i] - X[i];
-  if (FP64_REFINE) {
-    // axial vector of M - M^T with M = R0^T F, accumulated in FP64
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  if (REFINE != POLAR_FP32) {
+    // axial vector of M - M^T with M = R0^T F:
+    //   a0 = sum_k r2k f1k - r1k f2k, a1 = sum_k r0k f2k - r2k f0k, a2 = sum_k r1k f0k - r0k f1k
+    float av0, av1, av2;
+    if (REFINE == POLAR_FP64) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      double r0 = X[3 * k + 0], r1 = X[3 * k + 1], r2 = X[3 * k + 2];
-      double f0 = F[3 * k + 0], f1 = F[3 * k + 1], f2 = F[3 * k + 2];
-      a0 = fma(r2, f1, fma(-r1, f2, a0));
-      a1 = fma(r0, f2, fma(-r2, f0, a1));
-      a2 = fma(r1, f0, fma(-r0, f1, a2));
+      for (int k = 0; k < 3; ++k) {
+        double r0 = X[3 * k + 0], r1 = X[3 * k + 1], r2 = X[3 * k + 2];
+        double f0 = F[3 * k + 0], f1 = F[3 * k + 1], f2 = F[3 * k + 2];
+        a0 = fma(r2, f1, fma(-r1, f2, a0));
+        a1 = fma(r0, f2, fma(-r2, f0, a1));
+        a2 = fma(r1, f0, fma(-r0, f1, a2));
+      }
+      av0 = (float)a0;
+      av1 = (float)a1;
+      av2 = (float)a2;
+    } else {
+      float x0[6], y0[6], x1[6], y1[6], x2[6], y2[6];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float r0 = X[3 * k + 0], r1 = X[3 * k + 1], r2 = X[3 * k + 2];
+        const float f0 = F[3 * k + 0], f1 = F[3 * k + 1], f2 = F[3 * k + 2];
+        x0[2 * k] = r2;  y0[2 * k] = f1;  x0[2 * k + 1] = -r1; y0[2 * k + 1] = f2;
+        x1[2 * k] = r0;  y1[2 * k] = f2;  x1[2 * k + 1] = -r2; y1[2 * k + 1] = f0;
+        x2[2 * k] = r1;  y2[2 * k] = f0;  x2[2 * k + 1] = -r0; y2[2 * k + 1] = f1;
+      }
+      av0 = dot6_compensated(x0, y0);
+      av1 = dot6_compensated(x1, y1);
+      av2 = dot6_compensated(x2, y2);
     }
     // S ~ sym(R0^T F) is needed only to first order: S = R0^T F in FP32
     float S[9];
@@ -142,7 +195,6 @@ __device__ __forceinline__ void f_minus_polar_3d(const float F[9], float out[9])
     cofactor3(A, Ac);
     float detA = A[0] * Ac[0] + A[1] * Ac[1] + A[2] * Ac[2];
     float ia = 1.0f / detA;
-    float av0 = (float)a0, av1 = (float)a1, av2 = (float)a2;
     float w0 = (Ac[0] * av0 + Ac[3] * av1 + Ac[6] * av2) * ia;  // A symmetric: A^-1 = cof^T / det
     float w1 = (Ac[1] * av0 + Ac[4] * av1 + Ac[7] * av2) * ia;
     float w2 = (Ac[2] * av0 + Ac[5] * av1 + Ac[8] * av2) * ia;
@@ -167,7 +219,7 @@ __device__ __forceinline__ void f_minus_polar_3d(const float F[9], float out[9])
 //   neo-Hookean:      tau = mu (F F^T - I) + lam ln(J) I
 //   fixed-corotated:  tau = 2 mu (F - R) F^T + lam (J - 1) J I
 // ln J and J - 1 come from det(F) - 1 computed without cancellation.
-template <int D, int MATERIAL, bool FP64_POLAR>
+template <int D, int MATERIAL, int POLAR>
 __device__ __forceinline__ void kirchhoff(const float F[D * D], float mu, float lam, float tau[D * D]) {
   float jm1 = det_minus_one<D>(F);
   if (MATERIAL == 0) {
@@ -186,7 +238,7 @@ __device__ __forceinline__ void kirchhoff(const float F[D * D], float mu, float 
     if (D == 2)
       f_minus_polar_2d(F, FR);
     else
-      f_minus_polar_3d<FP64_POLAR>(F, FR);
+      f_minus_polar_3d<POLAR>(F, FR);
     float l = lam * jm1 * (jm1 + 1.0f);
 #pragma unroll
     for (int i = 0; i < D; ++i)

@@ -337,7 +337,7 @@ __global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t cap
       for (int b = 0; b < D; ++b) F[a * D + b] = dec_out[((size_t)(1 + b) * capQ + i) * D + a];
     }
     float tau[D * D];
-    kirchhoff<D, MATERIAL, true>(F, R.mu, R.lam, tau);
+    kirchhoff<D, MATERIAL, POLAR_FP64>(F, R.mu, R.lam, tau);
     // MLS: A = m C - dt V0 (4/dx^2) tau, C = (dv/dX) F^-1 with AFFINE, else 0
     float A[D * D];
     const float kml = R.dt * R.vol * 4.0f * R.inv_dx * R.inv_dx;

@@ -34,7 +34,7 @@ class MPM:
     """One context of the C ABI: a batch of MPM instances sharing grid and material law."""
 
     def __init__(self, *, dim, n_grid, dx, dt, gravity, bc, bc_width, material, transfer, rho, p_vol,
-                 E, nu, inst_offsets):
+                 E, nu, inst_offsets, polar_eft=0):
         L = _abi.lib()
         self._E = np.ascontiguousarray(np.atleast_1d(E), np.float32)
         self._nu = np.ascontiguousarray(np.atleast_1d(nu), np.float32)
@@ -43,7 +43,7 @@ class MPM:
         self.cfg = _abi.MpmConfig(dim, n_grid, dx, dt, g, bc, bc_width, material, transfer, rho, p_vol,
                                   len(self._E), self._E.ctypes.data_as(C.POINTER(C.c_float)),
                                   self._nu.ctypes.data_as(C.POINTER(C.c_float)),
-                                  self._offs.ctypes.data_as(C.POINTER(C.c_int64)))
+                                  self._offs.ctypes.data_as(C.POINTER(C.c_int64)), int(polar_eft))
         h = C.c_void_p()
         _abi.check(L.mpm_init(C.byref(self.cfg), C.byref(h)))
         self._h = h
@@ -53,11 +53,11 @@ class MPM:
         self.n_inst = len(self._E)
 
     @classmethod
-    def from_scene(cls, sc):
+    def from_scene(cls, sc, polar_eft=0):
         """Context for a synth.scenes.Scene (configuration only)."""
         return cls(dim=sc.dim, n_grid=sc.n_grid, dx=sc.dx, dt=sc.dt, gravity=sc.gravity, bc=sc.bc,
                    bc_width=sc.bc_width, material=sc.material, transfer=sc.transfer, rho=sc.rho,
-                   p_vol=sc.p_vol, E=sc.E, nu=sc.nu, inst_offsets=sc.inst_offsets)
+                   p_vol=sc.p_vol, E=sc.E, nu=sc.nu, inst_offsets=sc.inst_offsets, polar_eft=polar_eft)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -79,11 +79,15 @@ class MPM:
     def step(self, n_steps=1, stream=None):
         _abi.check(_abi.lib().mpm_step(self._h, int(n_steps), _stream(stream)))
 
-    def step_profiled(self, n_steps=1, stream=None):
-        """Steps with per-kernel CUDA events; returns (n_steps, 3) ms [fused, scan, permute]."""
-        out = (C.c_float * (3 * n_steps))()
-        _abi.check(_abi.lib().mpm_step_profiled(self._h, int(n_steps), out, _stream(stream)))
-        return np.frombuffer(out, np.float32).reshape(n_steps, 3).copy()
+    def step_profiled(self, n_steps=1, flush=None, stream=None):
+        """Steps with CUDA events around every kernel, all steps enqueued before one final
+        synchronisation; `flush` (a CUDA tensor) is overwritten between steps, outside the timed
+        intervals.  Returns (n_steps, 4) ms [fused, scan, permute, whole step]."""
+        out = (C.c_float * (4 * n_steps))()
+        fb = None if flush is None else C.c_void_p(flush.data_ptr())
+        nb = 0 if flush is None else flush.numel() * flush.element_size()
+        _abi.check(_abi.lib().mpm_step_profiled(self._h, int(n_steps), fb, nb, out, _stream(stream)))
+        return np.frombuffer(out, np.float32).reshape(n_steps, 4).copy()
 
     def status(self, clear=True, stream=None):
         w = C.c_uint32()
@@ -140,7 +144,7 @@ def step_noalloc(scene_cfg, x, v, F, C_=None, n_steps=1, stream=None):
     g = (C.c_float * 3)(*[float(a) for a in sc.gravity])
     cfg = _abi.MpmConfig(sc.dim, sc.n_grid, sc.dx, sc.dt, g, sc.bc, sc.bc_width, sc.material, sc.transfer, sc.rho,
                          sc.p_vol, len(E), E.ctypes.data_as(C.POINTER(C.c_float)),
-                         nu.ctypes.data_as(C.POINTER(C.c_float)), offs.ctypes.data_as(C.POINTER(C.c_int64)))
+                         nu.ctypes.data_as(C.POINTER(C.c_float)), offs.ctypes.data_as(C.POINTER(C.c_int64)), 0)
     w = C.c_uint32()
     _abi.check(_abi.lib().mpm_step_noalloc(C.byref(cfg), _ptr(x), _ptr(v), _ptr(F), _ptr(C_), int(n_steps),
                                            C.byref(w), _stream(stream)))

@@ -82,11 +82,19 @@ def test_jvp_and_secant_rows():
         assert rel(sec, ref) < TOL_BF16, scale
 
 
-@pytest.mark.parametrize("d,n_hidden,tol", [(2, 5, TOL_BF16), (3, 5, TOL_BF16), (2, 1, 1e-5), (3, 1, 1e-5)])
+# A second derivative through four BF16 layers: its terms act''(z)(W u)(W t) and act'(z)(W m)
+# partly cancel, so the BF16 rounding of the layer inputs costs more than for first
+# derivatives.  Rounding the same network's square-layer inputs and weights to BF16 in an FP64
+# evaluation gives 6.0e-2 norm-wise for the d = 2 case below; the bound leaves margin for that.
+TOL_MIXED_BF16 = 1e-1
+
+
+@pytest.mark.parametrize("d,n_hidden,tol", [(2, 5, TOL_MIXED_BF16), (3, 5, TOL_MIXED_BF16), (2, 1, 1e-5),
+                                            (3, 1, 1e-5)])
 def test_mixed_rows_velocity_gradient(d, n_hidden, tol):
     """Mixed rows d/dX_k of the JVP row against the oracle's forward-over-forward dv/dX:
     5 hidden layers on the tensor cores (BF16), one hidden layer in FP32.  The JVP and
-    tangent rows of the same call stay as accurate as without the mixed rows."""
+    tangent rows of the same call keep the first-derivative tolerance."""
     from paper_2109_12390_gb300.decoder import Decoder, PRIMAL, JVP, mixed, dX
     r, n = 16, 1500
     p = _dec_params(d, r, n_hidden=n_hidden, seed=21)
@@ -102,8 +110,9 @@ def test_mixed_rows_velocity_gradient(d, n_hidden, tol):
     uu = u.astype(np.float32).astype(np.float64)[idx]
     v, G = OD.velocity_gradient(p, Xr, xh, uu)
     _, JX, _ = OD.jacobians(p, Xr, xh)
-    assert rel(np.stack(out[1:1 + d], -1), JX) < tol
-    assert rel(out[1 + d], v) < tol
+    tol1 = min(tol, TOL_BF16)
+    assert rel(np.stack(out[1:1 + d], -1), JX) < tol1
+    assert rel(out[1 + d], v) < tol1
     assert rel(np.stack(out[2 + d:], -1), G) < tol
 
 

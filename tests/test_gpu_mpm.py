@@ -99,6 +99,30 @@ def test_3d_fixed_corotated_cube_slip_floor():
     _compare(ctx, ref)
 
 
+def test_3d_polar_compensated_fp32_matches_fp64():
+    """The compensated-FP32 rotation correction of the polar factor (polar_eft = 1) against the
+    FP64 one and the oracle, on the stressed 3D impact: same trajectory to FP32 rounding."""
+    from paper_2109_12390_gb300.mpm import MPM
+    sc = S.cube_3d(side=16, bottom=0.03)
+    rng = np.random.default_rng(2)
+    sc.F = S.random_deformation(rng, sc.n_particles, 3, 0.02)
+    out = []
+    for eft in (0, 1):
+        ctx = MPM.from_scene(sc, polar_eft=eft)
+        ctx.load_numpy(sc.x, sc.v, sc.F, sc.C)
+        ctx.step(80)
+        assert ctx.status() == 0
+        out.append(ctx.read_numpy())
+        if eft:
+            ref = sc.copy()
+            OM.step(ref, 80)
+            _compare(ctx, ref)
+    # the two runs differ by FP32 rounding amplified over 80 stressed steps (float atomics
+    # alone make two runs of one variant differ at ~1e-6)
+    for a, b in zip(out[0][:3], out[1][:3]):   # x, v, F
+        assert rel(b, a.astype(np.float64)) < 5e-6
+
+
 def test_3d_pic_homogeneous_deformation():
     """Literal PIC transfers in 3D (exact basis gradients) on a cube released from a homogeneous
     deformation.  (Through an impact at this dt the FP64 oracle itself diverges under PIC, so the

@@ -149,8 +149,9 @@ def test_one_step_projection_fp32_decoder(projection):
         np.testing.assert_allclose(xh1, xh + float(np.float32(sc.dt)) * vh1, rtol=1e-12, atol=1e-14)
     else:
         x_trial_ref = OD.decode(p, Xs, xh) + float(np.float32(sc.dt)) * vt
-        xh_ref, flag = OR.gauss_newton(p, Xs, x_trial_ref, 2 * xh - xp, 3)
-        assert not flag
+        # (the oracle's no-decrease flag is not compared: on this FP32-derived target the last
+        # iteration sits at the residual's rounding floor, where either outcome is correct)
+        xh_ref, _ = OR.gauss_newton(p, Xs, x_trial_ref, 2 * xh - xp, 3)
         assert rel(xh1 - xh, xh_ref - xh) < 1e-3
 
 
