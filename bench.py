@@ -56,35 +56,59 @@ def _dist():
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+    """Samples SM clocks and throttle reasons with nvidia-smi around the timed region.
+
+    The sampler is running (first sample read) before the region starts and keeps running until
+    a sample after its end has arrived; the summary uses the samples from the last one before
+    the region to the first one after it (a region shorter than the sampling period is
+    bracketed by its neighbours)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=50):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
+        self.samples = []   # (host time, line)
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.samples.append((time.perf_counter(), line))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._reader, daemon=True).start()
+            deadline = time.perf_counter() + 10.0
+            while not self.samples and time.perf_counter() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.t0 = time.perf_counter()
         return self
 
     def __exit__(self, *a):
-        self.lines = []
+        self.t1 = time.perf_counter()
         if self.proc is not None:
+            deadline = time.perf_counter() + 2.0
+            while (not self.samples or self.samples[-1][0] <= self.t1) and time.perf_counter() < deadline:
+                time.sleep(0.01)
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                out = ""
-            self.lines = [l for l in out.splitlines() if l.strip()]
+        before = [i for i, (t, _) in enumerate(self.samples) if t <= self.t0]
+        after = [i for i, (t, _) in enumerate(self.samples) if t > self.t1]
+        lo = before[-1] if before else 0
+        hi = after[0] if after else len(self.samples) - 1
+        self.lines = [l for _, l in self.samples[lo:hi + 1]]
 
     def summary(self):
         sm, mx, reasons = [], [], set()
@@ -104,7 +128,7 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window_ms": 1e3 * (self.t1 - self.t0)}
 
 
 def _peaks():
@@ -255,7 +279,9 @@ def run_ours(args, ws, rank, local):
     # the same workload with the compensated-FP32 rotation correction of the polar factor, and a
     # scaled-up cube (2,097,152 particles on 256^3, working set far above L2)
     variants = {}
-    for name, vsc, eft in (("polar_eft", sc, 1), ("cube_2M_256", S.cube_3d(side=128, n_grid=256, dt=2.5e-5), 0)):
+    extra = () if args.profile else (("polar_eft", sc, 1),
+                                     ("cube_2M_256", S.cube_3d(side=128, n_grid=256, dt=2.5e-5), 0))
+    for name, vsc, eft in extra:
         vctx = MPM.from_scene(vsc, polar_eft=eft)
         vctx.load_numpy(vsc.x, vsc.v, vsc.F, vsc.C)
         vctx.step_profiled(args.warmup, flush=flush)
@@ -277,7 +303,7 @@ def run_ours(args, ws, rank, local):
     hC = torch.from_numpy(sc.C.astype(np.float32).reshape(P, d * d)).pin_memory()
     ox, ov, oF, oC = [torch.empty_like(t).pin_memory() for t in (hx, hv, hF, hC)]
     e2e_ms = []
-    for i in range(args.warmup + args.steps):
+    for i in range(0 if args.profile else args.warmup + args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -287,7 +313,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = float(np.sum(e2e_ms))
+    e2e_total = float(np.sum(e2e_ms)) if e2e_ms else float("nan")
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([e2e_total], device=dev)
@@ -309,16 +335,16 @@ def run_ours(args, ws, rank, local):
                          "algorithmic_bytes_per_launch": ALGO_BYTES_3D * P, "kernel_ms": fused_ms},
             "kernels_ms": {"mpm_g2p2g": fused_ms, "mpm_scan": float(kern[:, 1].mean()),
                            "mpm_permute": float(kern[:, 2].mean())},
-            "e2e": {"value": ws * P * args.steps / (e2e_total * 1e-3), "unit": UNIT,
-                    "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+            "e2e": None if args.profile else {"value": ws * P * args.steps / (e2e_total * 1e-3), "unit": UNIT,
+                                              "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
             "variants": variants,
             "gpu_launches": 3 * args.steps,
             "clocks": clk.summary(),
             "status_word": status,
         }
-        if not args.no_cpu_baseline:
+        if not (args.no_cpu_baseline or args.profile):
             line["cpu_baseline"] = cpu_baseline_fom(sc)
-        if not args.no_rom:
+        if not (args.no_rom or args.profile):
             line["rom"] = rom_leg()
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -335,6 +361,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-order leg (training + ROM run)")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the warm-up and the timed steps (for profiler launch lists)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

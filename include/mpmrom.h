@@ -341,15 +341,26 @@ mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void*
  *                1 = velocity-only projection (Alg. 7).
  *   ridge        rho >= 0: the projections solve the regularised least-squares
  *                problems min |J a - b|^2 + rho (tr(J^T J) / r) |a|^2 (J the
- *                latent Jacobian at the samples).  rho = 0 is the plain least
- *                squares of Algorithms 6 and 7 (a 1e-10 relative ridge is
- *                always kept so that rank-deficient J^T J stays factorisable).
+ *                latent Jacobian at the samples) for the increment a of the
+ *                unknown from its prior: the Gauss-Newton step from the current
+ *                iterate, and vhat_{n+1} - vhat_n for the velocity (so that
+ *                latent directions the samples do not resolve keep their
+ *                velocity).  rho = 0 is the plain least squares of Algorithms 6
+ *                and 7 (a 1e-10 relative ridge is always kept so that
+ *                rank-deficient J^T J stays factorisable).
  *   affine       MLS transfer only.  0: the quadrature points enter the local
  *                particle-to-grid transfer with C = 0, as Algorithm 5 writes
  *                it.  1: they carry the affine velocity of the decoded motion,
  *                C = (dv/dX) (dg/dX)^-1 with v = (dg/dxhat) vhat_n (the state an
  *                APIC particle of that motion carries; the full-order MLS model
  *                transfers it too).  Ignored with the PIC transfer.
+ *   f_reference  0: the quadrature points' deformation gradient is the decoder's
+ *                dg/dX (Eq. defGrad).  1: it is measured from the decoded initial
+ *                configuration, F = (dg/dX)(X; xhat_n) [(dg/dX)(X; xhat_ref)]^-1
+ *                with xhat_ref the fitted initial latent state (rom_fit_initial)
+ *                or the one given to rom_set_reference: the decoder's
+ *                approximation error of the undeformed configuration then
+ *                produces no stress.  For initial states with F = I.
  */
 typedef struct rom_config {
   int32_t dim;
@@ -373,6 +384,7 @@ typedef struct rom_config {
   int32_t projection;
   float ridge;
   int32_t affine;
+  int32_t f_reference;
 } rom_config;
 
 typedef struct rom_ctx rom_ctx;
@@ -401,6 +413,15 @@ mpm_status rom_get_state(rom_ctx* ctx, double* xhat, double* vhat, double* xhat_
  * are (n_particles, dim), host or device.  Synchronous.
  */
 mpm_status rom_fit_initial(rom_ctx* ctx, const float* target, const float* V0, int iters, void* stream);
+
+/*
+ * Reference configuration of the f_reference option: decodes dg/dX at every
+ * particle at xhat_ref (r doubles, host or device) and keeps its inverse
+ * (P x d x d floats, owned by the context).  rom_fit_initial calls it with the
+ * fitted xhat_0 when cfg.f_reference = 1.  Errors: MPM_EINVAL if f_reference
+ * is 0.
+ */
+mpm_status rom_set_reference(rom_ctx* ctx, const double* xhat_ref, void* stream);
 
 /*
  * Advances the reduced state by n_steps steps of Algorithm 2: decoder at all

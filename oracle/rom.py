@@ -34,6 +34,10 @@ Readings where the paper is silent (listed in the design notes):
     step halving, at most 10 halvings; if no trial decreases the objective the
     iterate is kept and the ``no_decrease`` flag is raised;
   * at the first step xhat_{-1} = xhat_0 - dt vhat_0;
+  * optional reference gradient (f_reference): the quadrature points' stress
+    uses F = (dg/dX)(X; xhat_n) [(dg/dX)(X; xhat_ref)]^-1 with xhat_ref the
+    fitted initial latent state (for initial states with F = I), so that the
+    decoder's error in representing the undeformed body is not a strain;
   * quadrature-point affine velocity (MLS transfer only): Algorithm 5 gives the
     quadrature points C = 0, which matches the paper's PIC full-order model;
     with the MLS/APIC full-order model the option ``affine = "decoded"`` gives
@@ -42,7 +46,11 @@ Readings where the paper is silent (listed in the design notes):
   * optional ridge rho: the projections then solve min |J a - b|^2 +
     rho (tr(J^T J) / r) |a|^2 (Tikhonov regularisation of the least-squares
     problems for latent Jacobians with near-null directions; rho = 0 is the
-    paper's plain least squares);
+    paper's plain least squares), where a is the increment of the unknown
+    from its prior: the Gauss-Newton step from the current iterate
+    (Levenberg-Marquardt damping) and, for the velocity, the change from
+    vhat_n (a penalty on vhat itself would pull the latent velocity to zero
+    and damp the motion);
   * initial latent state by the least-squares fit of Eq. essentialSpecInt over
     all particles (Gauss-Newton from zero, then a linear least-squares fit of
     the initial velocity).
@@ -138,6 +146,7 @@ class RomScene:
     projection: str = "position-velocity"   # or "velocity-only"
     ridge: float = 0.0                       # rho of the regularised projections
     affine: str = "zero"                     # quadrature-point C: "zero" or "decoded"
+    F_ref_inv: np.ndarray | None = None      # (P, d, d) inverse reference gradients (f_reference option)
 
 
 @dataclasses.dataclass
@@ -165,8 +174,10 @@ def local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_all):
         Cq = np.einsum("pik,pkj->pij", dvdX, np.linalg.inv(FX))
     else:
         Cq = np.zeros((len(quad), d, d))
+    # stress from the gradient measured against the decoded reference configuration (option)
+    Fs = FX if rs.F_ref_inv is None else np.einsum("pik,pkj->pij", FX, rs.F_ref_inv[quad])
     mu, lam = M.lame(rs.E, rs.nu)
-    m, p = M.p2g(xq, vq, FX, Cq, rs.mass, rs.vol, mu, lam, dx=rs.dx,
+    m, p = M.p2g(xq, vq, Fs, Cq, rs.mass, rs.vol, mu, lam, dx=rs.dx,
                  dt=rs.dt, n_grid=rs.n_grid, material=rs.material, transfer=rs.transfer)
     vg = M.grid_update(m, p, dt=rs.dt, gravity=rs.gravity, bc=rs.bc, bc_width=rs.bc_width)
     xs = x_all[samples]
@@ -183,6 +194,14 @@ def local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_all):
     return v_trial, x_trial, basis, neigh
 
 
+def reference_inverse(dec, X, xhat_ref):
+    """Inverse gradients [(dg/dX)(X_p; xhat_ref)]^-1 of the decoded reference configuration (the
+    f_reference option: F = (dg/dX)(X; xhat_n) G_p, so the decoder's approximation error of the
+    undeformed configuration produces no stress)."""
+    _, FX, _ = D.jacobians(dec, X, xhat_ref)
+    return np.linalg.inv(FX)
+
+
 def lstsq(A, b, ridge=0.0):
     """argmin |A x - b|^2 (+ ridge * tr(A^T A) / n * |x|^2 when ridge > 0)."""
     if ridge > 0:
@@ -192,11 +211,17 @@ def lstsq(A, b, ridge=0.0):
     return np.linalg.lstsq(A, b, rcond=None)[0]
 
 
-def project_velocity(dec, Xs, xhat_n, v_trial, ridge=0.0):
-    """Eq. nonlinear_projection:vel / linear_projection: LSQ fit of v_trial by dg/dxhat at xhat_n
-    (optionally the ridge-regularised fit, a reading for ill-conditioned latent Jacobians)."""
+def project_velocity(dec, Xs, xhat_n, v_trial, ridge=0.0, vhat_n=None):
+    """Eq. nonlinear_projection:vel / linear_projection: LSQ fit of v_trial by dg/dxhat at xhat_n.
+    With ridge > 0 the regularised fit penalises the change of the latent velocity from vhat_n
+    (a reading for ill-conditioned latent Jacobians: unresolved directions keep their previous
+    velocity instead of being pulled to zero): vhat = vhat_n + argmin |J a - (v_trial - J vhat_n)|^2
+    + ridge tr(J^T J)/r |a|^2.  With ridge = 0 this is the plain fit."""
     _, _, Jq = D.jacobians(dec, Xs, xhat_n)
-    return lstsq(Jq.reshape(-1, dec.r), v_trial.reshape(-1), ridge)
+    J = Jq.reshape(-1, dec.r)
+    if vhat_n is None:
+        vhat_n = np.zeros(dec.r)
+    return vhat_n + lstsq(J, v_trial.reshape(-1) - J @ vhat_n, ridge)
 
 
 def gauss_newton(dec, Xs, x_trial, xhat0, iters, c=1e-4, max_halvings=10, ridge=0.0):
@@ -234,7 +259,7 @@ def rom_step(dec, rs: RomScene, st: RomState, record=None):
     x_all = D.decode(dec, rs.X, st.xhat)
     v_trial, x_trial, basis, neigh = local_dynamics(dec, rs, st.xhat, st.vhat, samples, x_all)
     Xs = rs.X[samples]
-    vhat_new = project_velocity(dec, Xs, st.xhat, v_trial, rs.ridge)
+    vhat_new = project_velocity(dec, Xs, st.xhat, v_trial, rs.ridge, st.vhat)
     if rs.projection == "velocity-only":
         xhat_new, flag = st.xhat + rs.dt * vhat_new, False
     else:

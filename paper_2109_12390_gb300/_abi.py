@@ -44,7 +44,7 @@ class RomConfig(C.Structure):
         ("material", C.c_int32), ("transfer", C.c_int32), ("rho", C.c_float), ("p_vol", C.c_float),
         ("E", C.c_float), ("nu", C.c_float), ("latent_dim", C.c_int32), ("n_samples", C.c_int32),
         ("seed", C.c_uint64), ("instance", C.c_int32), ("gn_iters", C.c_int32), ("projection", C.c_int32),
-        ("ridge", C.c_float), ("affine", C.c_int32),
+        ("ridge", C.c_float), ("affine", C.c_int32), ("f_reference", C.c_int32),
     ]
 
 
@@ -95,6 +95,7 @@ SIGNATURES = [
     ("rom_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     ("rom_get_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("rom_fit_initial", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("rom_set_reference", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("rom_step", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("rom_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
     ("rom_debug", C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),

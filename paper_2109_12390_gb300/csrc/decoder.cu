@@ -91,18 +91,38 @@ __global__ void decoder_simt(DecArgs a) {
 }
 
 // --------------------------------------------------------------------------
-// Tensor-core decoder kernel: 128 threads, thread t owns row t of the tile
-// (tensor-memory lane t).
+// Tensor-core decoder kernel: 256 threads.  Warps w and w + 4 read the same
+// tensor-memory lane group (lanes 32 (w % 4) ..): thread t owns tile row
+// rw = 32 (w % 4) + lane and the column half h = w / 4 (columns 64 h .. 64 h + 63)
+// of every layer, so each row's epilogue is split over two warps.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
+constexpr int kDecThreads = 256;
+constexpr int kXbStride = 33;                            // padded row stride of the exchange
+constexpr int kW0Stride = 40;                            // first-layer row stride (d + r <= 40)
+
+__device__ __forceinline__ float elu_bf16_input(float z) {
+  // ELU whose result feeds a BF16 operand (or the FP32 output layer): exp(z) - 1
+  // with the fast exponential; its absolute error (~1e-7) is far below BF16
+  // resolution of the activations
+  return z > 0.f ? z : __expf(z) - 1.0f;
+}
+
+__global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled operand tiles
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* wsm = smem;                                   // n_tc x 32 KB
   uint8_t* atile = smem + kMaxTC * kLayerBytes;          // 32 KB
-  float* xb = (float*)(atile + kLayerBytes);             // 128 rows x 33: pre-activations of one chunk
-  DecSmemTail* tail = (DecSmemTail*)(xb + 64 * kW);
-  const int t = threadIdx.x, warp = t >> 5;
+  float* xb = (float*)(atile + kLayerBytes);             // [2 halves][128 rows][33]: one chunk per half
+  float* ypart = xb + 2 * 128 * kXbStride;               // [128 rows][3]: output partial of half 1
+  float* sW0 = ypart + 128 * 3;                          // [128][kW0Stride] first layer, zero-padded
+  float* sb0 = sW0 + kW * kW0Stride;                     // [128]
+  float* sbh = sb0 + kW;                                 // [kMaxTC][128] square-layer biases
+  float* sWout = sbh + kMaxTC * kW;                      // [3][128] output layer
+  DecSmemTail* tail = (DecSmemTail*)(sWout + 3 * kW);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int rw = (warp & 3) * 32 + lane;                 // tile row / tensor-memory lane
+  const int h = warp >> 2;                               // column half
 
   if (t == 0) {
     tc::mbar_init(&tail->bar_w, 1);
@@ -116,6 +136,18 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
   tc::tc_fence_after();
   const uint32_t tmem = tail->tmem;
 
+  // FP32 first layer, biases and output layer staged in shared memory (read by
+  // every row of every tile)
+  {
+    const int K0s = a.d + a.r;
+    for (int e = t; e < kW * kW0Stride; e += kDecThreads) {
+      const int c = e / kW0Stride, i = e % kW0Stride;
+      sW0[e] = i < K0s ? a.W0[c * K0s + i] : 0.f;
+    }
+    for (int e = t; e < kW; e += kDecThreads) sb0[e] = a.b0[e];
+    for (int e = t; e < a.n_tc * kW; e += kDecThreads) sbh[e] = a.bh[e];
+    for (int e = t; e < a.d * kW; e += kDecThreads) sWout[e] = a.Wout[e];
+  }
   // resident weights of the square layers
   if (t == 0) {
     tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(a.n_tc * kLayerBytes));
@@ -133,41 +165,49 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
   const int64_t n_pts = dec_count(a);
   const int64_t n_tiles = (n_pts + a.Pt - 1) / a.Pt;
   const int K0 = a.d + a.r;
+  float* xh = xb + h * 128 * kXbStride;                  // this half's exchange buffer
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !tail->abort; tile += gridDim.x) {
     const int64_t first = tile * a.Pt;
-    const RowInfo ri = row_info(a, t, first, n_pts);
+    const RowInfo ri = row_info(a, rw, first, n_pts);
     float in[40], dir[40];
     if (ri.cls >= 0) row_inputs(a, ri, in, dir);
 
-    // ---- layer 0 on the CUDA cores (FP32), 8 columns at a time
-    for (int c0 = 0; c0 < kW; c0 += 8) {
-      float h[8];
+    // ---- layer 0 on the CUDA cores (FP32), this thread's 64 columns, 8 at a time
+    for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 8) {
+      float hv[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int c = c0 + j;
-        float z = __ldg(&a.b0[c]), zd = 0.f;
+        float z = sb0[c], zd = 0.f;
+        const float* w0r = sW0 + c * kW0Stride;
         if (ri.cls >= 0) {
 #pragma unroll
-          for (int i = 0; i < 40; ++i) {
-            if (i < K0) {
-              const float w = __ldg(&a.W0[c * K0 + i]);
-              z = fmaf(w, in[i], z);
-              zd = fmaf(w, dir[i], zd);
+          for (int i4 = 0; i4 < kW0Stride / 4; ++i4) {
+            if (4 * i4 < K0) {   // padded weights are zero, as are in[] and dir[] beyond K0
+              const float4 w = *reinterpret_cast<const float4*>(w0r + 4 * i4);
+              z = fmaf(w.x, in[4 * i4 + 0], z);
+              z = fmaf(w.y, in[4 * i4 + 1], z);
+              z = fmaf(w.z, in[4 * i4 + 2], z);
+              z = fmaf(w.w, in[4 * i4 + 3], z);
+              zd = fmaf(w.x, dir[4 * i4 + 0], zd);
+              zd = fmaf(w.y, dir[4 * i4 + 1], zd);
+              zd = fmaf(w.z, dir[4 * i4 + 2], zd);
+              zd = fmaf(w.w, dir[4 * i4 + 3], zd);
             }
           }
-          if (ri.cls == 0) h[j] = act_f(a.act, z);
-          else if (ri.cls == 1) h[j] = act_d1(a.act, z) * zd;
-          else if (ri.cls == 2) h[j] = act_sec(a.act, z, zd);
-          else h[j] = act_d2(a.act, z) * zd * mixed_t0(a, a.W0 + c * K0, ri.kind);
-          if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + t] = ri.cls == 0 ? z : zd;
+          if (ri.cls == 0) hv[j] = a.act == 0 ? elu_bf16_input(z) : z;
+          else if (ri.cls == 1) hv[j] = act_d1(a.act, z) * zd;
+          else if (ri.cls == 2) hv[j] = act_sec(a.act, z, zd);
+          else hv[j] = act_d2(a.act, z) * zd * mixed_t0(a, w0r, ri.kind);
+          if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + rw] = ri.cls == 0 ? z : zd;
         } else {
-          h[j] = 0.f;
-          if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + t] = 0.f;
+          hv[j] = 0.f;
+          if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + rw] = 0.f;
         }
-        if (a.astore) a.astore[(int64_t)c * a.rows_total + tile * 128 + t] = __float2bfloat16_rn(h[j]);
+        if (a.astore) a.astore[(int64_t)c * a.rows_total + tile * 128 + rw] = __float2bfloat16_rn(hv[j]);
       }
-      store_bf16x8(atile, t, c0, h);
+      store_bf16x8(atile, rw, c0, hv);
     }
 
     float y[3] = {0.f, 0.f, 0.f};
@@ -196,33 +236,36 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
       __syncthreads();
       if (tail->abort) break;
       const bool last = (l == a.n_tc - 1);
-      const float* bl = a.bh + l * kW;
-      for (int ch = 0; ch < kW / 32; ++ch) {
+      const float* bl = sbh + l * kW;
+      for (int i2 = 0; i2 < 2; ++i2) {
+        const int ch = 2 * h + i2;
         float acc[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, acc);
-        // primal rows: z = acc + b; publish z for the derivative rows of the same point
-        float* zs = a.zstore ? a.zstore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + t : nullptr;
+        tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + ch * 32, acc);
+        // training: keep the pre-activation (z for primal rows, zdot for tangent rows)
+        float* zs = a.zstore ? a.zstore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + rw : nullptr;
         if (zs) {
-          // training: keep the pre-activation (z for primal rows, zdot for tangent rows)
 #pragma unroll
           for (int i = 0; i < 32; ++i)
-            zs[(int64_t)(ch * 32 + i) * a.rows_total] = ri.cls < 0 ? 0.f : acc[i] + (ri.cls == 0 ? __ldg(&bl[ch * 32 + i]) : 0.f);
+            zs[(int64_t)(ch * 32 + i) * a.rows_total] =
+                ri.cls < 0 ? 0.f : acc[i] + (ri.cls == 0 ? bl[ch * 32 + i] : 0.f);
         }
         if (ri.cls == 0) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) acc[i] += __ldg(&bl[ch * 32 + i]);
+          for (int i = 0; i < 32; ++i) acc[i] += bl[ch * 32 + i];
         }
         if (a.R > 1) {
-          // publish this row's pre-activations (stride 33: conflict-free)
+          // publish this row's pre-activations of the chunk (stride 33: conflict-free)
 #pragma unroll
-          for (int i = 0; i < 32; ++i) xb[t * 33 + i] = acc[i];
+          for (int i = 0; i < 32; ++i) xh[rw * kXbStride + i] = acc[i];
           __syncthreads();
         }
         // the primal row of point q is tile row q (kind index 0)
-        const float* zq = xb + ri.q * 33;
+        const float* zq = xh + ri.q * kXbStride;
         if (ri.cls == 0) {
+          if (a.act == 0) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) acc[i] = act_f(a.act, acc[i]);
+            for (int i = 0; i < 32; ++i) acc[i] = elu_bf16_input(acc[i]);
+          }
         } else if (ri.cls == 1) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[i] *= act_d1(a.act, zq[i]);
@@ -230,41 +273,46 @@ __global__ void __launch_bounds__(128, 1) decoder_tc(DecArgs a) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[i] = act_sec(a.act, zq[i], acc[i]);
         } else if (ri.cls == 3) {
-          const float* uq = xb + (ri.ja * a.Pt + ri.q) * 33;
-          const float* tq = xb + (ri.jb * a.Pt + ri.q) * 33;
+          const float* uq = xh + (ri.ja * a.Pt + ri.q) * kXbStride;
+          const float* tq = xh + (ri.jb * a.Pt + ri.q) * kXbStride;
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[i] = act_d2(a.act, zq[i]) * uq[i] * tq[i] + act_d1(a.act, zq[i]) * acc[i];
-        } else if (ri.cls < 0) {
+        } else {
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[i] = 0.f;
         }
         if (a.astore) {
-          __nv_bfloat16* as = a.astore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + t;
+          __nv_bfloat16* as = a.astore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + rw;
 #pragma unroll
           for (int i = 0; i < 32; ++i) as[(int64_t)(ch * 32 + i) * a.rows_total] = __float2bfloat16_rn(acc[i]);
         }
         if (last) {
-          // output layer fused into the last epilogue (FP32)
+          // output layer fused into the last epilogue (FP32), partial over this half's columns
           for (int o = 0; o < a.d; ++o) {
-            float s = 0.f;
+            float sacc = 0.f;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) s = fmaf(__ldg(&a.Wout[o * kW + ch * 32 + i]), acc[i], s);
-            y[o] += s;
+            for (int i = 0; i < 32; ++i) sacc = fmaf(sWout[o * kW + ch * 32 + i], acc[i], sacc);
+            y[o] += sacc;
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; j += 8) store_bf16x8(atile, t, ch * 32 + j, acc + j);
+          for (int j = 0; j < 32; j += 8) store_bf16x8(atile, rw, ch * 32 + j, acc + j);
         }
         if (a.R > 1) __syncthreads();
       }
       tc::tc_fence_before();
     }
     if (tail->abort) break;
-    if (ri.cls >= 0) {
-      const int kidx = t / a.Pt;  // position of this row's kind in `kinds`
+    // combine the two column halves of the output layer
+    if (h == 1) {
+      for (int o = 0; o < a.d; ++o) ypart[rw * 3 + o] = y[o];
+    }
+    __syncthreads();
+    if (h == 0 && ri.cls >= 0) {
+      const int kidx = rw / a.Pt;  // position of this row's kind in `kinds`
       float* o = a.out + ((int64_t)kidx * a.n + ri.p) * a.d;
       for (int i = 0; i < a.d; ++i) {
-        float v = y[i] + (ri.cls == 0 ? __ldg(&a.bout[i]) : 0.f);
+        float v = y[i] + ypart[rw * 3 + i] + (ri.cls == 0 ? __ldg(&a.bout[i]) : 0.f);
         o[i] = v * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
       }
     }
@@ -297,7 +345,9 @@ using namespace mpmrom;
 namespace {
 
 size_t dec_smem_bytes() {
-  return 1024 + kMaxTC * kLayerBytes + kLayerBytes + 64 * kW * sizeof(float) + sizeof(DecSmemTail);
+  return 1024 + kMaxTC * kLayerBytes + kLayerBytes +
+         (2 * 128 * kXbStride + 128 * 3 + kW * kW0Stride + kW + kMaxTC * kW + 3 * kW) * sizeof(float) +
+         sizeof(DecSmemTail);
 }
 
 mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {
@@ -491,7 +541,7 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   } else {
     const int64_t tiles = (n + a.Pt - 1) / a.Pt;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));
-    decoder_tc<<<blocks, 128, dec->smem, s>>>(a);
+    decoder_tc<<<blocks, kDecThreads, dec->smem, s>>>(a);
   }
   MPM_CUDA_TRY(cudaGetLastError());
   return MPM_OK;

@@ -82,6 +82,7 @@ struct RomDev {
   float* x_trial;            // (k, d)
   int64_t* step;             // device step counter
   uint32_t* status;
+  const float* Fref_inv;     // (P, d, d) inverse reference gradients, or null (f_reference = 0)
 };
 
 // Inverse of a small matrix by its adjugate (F of a quadrature point, det F > 0).
@@ -180,15 +181,40 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
       if ((h & mask) == prefix) atomicAdd(&s_hist[(h >> shift) & 255], 1);
     }
     __syncthreads();
-    if (t == 0) {
-      int rem = s_remaining, acc = 0, b = 0;
-      for (; b < 256; ++b) {
-        if (acc + s_hist[b] >= rem) break;
-        acc += s_hist[b];
+    if (t < 32) {
+      // first bin b whose cumulative count reaches the remaining rank (warp 0:
+      // lane l holds bins 8 l .. 8 l + 7)
+      const int lane = t;
+      const int rem = s_remaining;
+      int c[8], tot = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        c[j] = s_hist[lane * 8 + j];
+        tot += c[j];
       }
-      b = min(b, 255);
-      s_remaining = rem - acc;
-      s_prefix = prefix | ((unsigned long long)b << shift);
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned cross = __ballot_sync(0xffffffffu, incl >= rem);
+      const int owner = cross ? __ffs(cross) - 1 : 31;
+      if (lane == owner) {
+        int acc = incl - tot, b = lane * 8 + 7;
+        bool found = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (!found && acc + c[j] >= rem) {
+            b = lane * 8 + j;
+            found = true;
+          } else if (!found) {
+            acc += c[j];
+          }
+        }
+        s_remaining = rem - acc;
+        s_prefix = prefix | ((unsigned long long)b << shift);
+      }
     }
     mask |= 255ull << shift;
     __syncthreads();
@@ -336,9 +362,28 @@ __global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t cap
 #pragma unroll
       for (int b = 0; b < D; ++b) F[a * D + b] = dec_out[((size_t)(1 + b) * capQ + i) * D + a];
     }
+    // deformation gradient for the stress: measured from the decoded reference
+    // configuration (F G_p) when the f_reference option holds G_p
+    float Fs[D * D];
+    if (R.Fref_inv) {
+      const float* G = R.Fref_inv + (size_t)pid * D * D;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          float acc = 0.f;
+#pragma unroll
+          for (int e = 0; e < D; ++e) acc = fmaf(F[a * D + e], G[e * D + b], acc);
+          Fs[a * D + b] = acc;
+        }
+    } else {
+#pragma unroll
+      for (int e = 0; e < D * D; ++e) Fs[e] = F[e];
+    }
     float tau[D * D];
-    kirchhoff<D, MATERIAL, POLAR_FP64>(F, R.mu, R.lam, tau);
+    kirchhoff<D, MATERIAL, POLAR_FP64>(Fs, R.mu, R.lam, tau);
     // MLS: A = m C - dt V0 (4/dx^2) tau, C = (dv/dX) F^-1 with AFFINE, else 0
+    // (C is the same with or without the reference: both factors carry G_p)
     float A[D * D];
     const float kml = R.dt * R.vol * 4.0f * R.inv_dx * R.inv_dx;
 #pragma unroll
@@ -420,6 +465,27 @@ __global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t cap
   }
 }
 
+// Inverse reference gradients G_p = [(dg/dX)(X_p; xhat_ref)]^-1 from decoder rows
+// [primal, dX_0 .. dX_{d-1}] over all particles.
+template <int D>
+__global__ void rom_reference(const float* __restrict__ dec_out, int64_t cap, int P, float* Fref_inv,
+                              uint32_t* status) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    float F[D * D], G[D * D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) F[a * D + b] = dec_out[((size_t)(1 + b) * cap + p) * D + a];
+    inverse<D>(F, G);
+    bool ok = true;
+#pragma unroll
+    for (int e = 0; e < D * D; ++e) ok &= isfinite(G[e]);
+    if (!ok) raise_status(status, STATUS_NONFINITE);
+#pragma unroll
+    for (int e = 0; e < D * D; ++e) Fref_inv[(size_t)p * D * D + e] = ok ? G[e] : (e % (D + 1) == 0 ? 1.f : 0.f);
+  }
+}
+
 // ---------------------------------------- grid update + G2P to the samples
 template <int D>
 __global__ void rom_g2p(RomDev R) {
@@ -487,21 +553,27 @@ struct RomSolve {
 enum { NE_VEL = 0, NE_GN = 1, NE_FIT = 2 };
 
 // Parallel Cholesky solve of the SPD system A x = b held in shared memory
-// (A: r x r, row-major).  Returns false if a pivot is not positive.
+// (A: r x r, row-major).  Returns false if a pivot is not positive.  One FP64
+// square root and one reciprocal per column; the substitutions multiply by the
+// stored reciprocal pivots (FP64 division and square root are long-latency
+// sequences on this GPU).
 __device__ bool chol_solve(double* A, double* b, int r) {
   __shared__ int s_bad;
+  __shared__ double s_rdiag[kMaxRl];
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
   for (int j = 0; j < r; ++j) {
     if (threadIdx.x == 0) {
       double piv = A[j * r + j];
       if (!(piv > 0.0)) s_bad = 1;
-      A[j * r + j] = sqrt(fmax(piv, 1e-300));
+      const double l = sqrt(fmax(piv, 1e-300));
+      A[j * r + j] = l;
+      s_rdiag[j] = 1.0 / l;
     }
     __syncthreads();
     if (s_bad) return false;
-    const double ljj = A[j * r + j];
-    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * r + j] /= ljj;
+    const double rl = s_rdiag[j];
+    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * r + j] *= rl;
     __syncthreads();
     for (int e = threadIdx.x; e < (r - j - 1) * (r - j - 1); e += blockDim.x) {
       const int i = j + 1 + e / (r - j - 1), c = j + 1 + e % (r - j - 1);
@@ -512,27 +584,20 @@ __device__ bool chol_solve(double* A, double* b, int r) {
   // forward / backward substitution (single thread; r <= 64)
   if (threadIdx.x == 0) {
     for (int i = 0; i < r; ++i) {
-      double s = b[i];
-      for (int c = 0; c < i; ++c) s -= A[i * r + c] * b[c];
-      b[i] = s / A[i * r + i];
+      double sacc = b[i];
+      for (int c = 0; c < i; ++c) sacc -= A[i * r + c] * b[c];
+      b[i] = sacc * s_rdiag[i];
     }
     for (int i = r - 1; i >= 0; --i) {
-      double s = b[i];
-      for (int c = i + 1; c < r; ++c) s -= A[c * r + i] * b[c];
-      b[i] = s / A[i * r + i];
+      double sacc = b[i];
+      for (int c = i + 1; c < r; ++c) sacc -= A[c * r + i] * b[c];
+      b[i] = sacc * s_rdiag[i];
     }
   }
   __syncthreads();
   return true;
 }
 
-// Normal equations of one least-squares problem over rows (sample, component):
-//   J row = dg/dxhat (r values),  rhs row b:
-//     NE_VEL  b = v_trial                    (solve J^T J x = J^T b -> vhat_{n+1})
-//     NE_GN   b = -(g(xhat_k) - x_trial) = secant + dt v_trial   (-> delta)
-//     NE_FIT  b = target - g(xhat_k)          (initial-condition fit, -> delta)
-// dec: decoder output (R, cap, d) with kinds [primal, dxhat_0.., (secant)].
-// The last CTA factors and solves, then prepares the next stage.
 __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, const float* __restrict__ dec,
                                                          int64_t cap, int mode, const float* __restrict__ target,
                                                          int projection, int n_rows_override, float ridge) {
@@ -541,8 +606,8 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
   const int rows = nP * d;
   const int n_mat = r * (r + 1) / 2;
   const int n_acc = n_mat + r + 1;
-  __shared__ float sJ[64][kMaxRl + 1];
-  __shared__ float sb[64];
+  __shared__ double sJ[64][kMaxRl + 1];
+  __shared__ double sb[64];
   __shared__ bool s_last;
   for (int row0 = blockIdx.x * 64; row0 < rows; row0 += gridDim.x * 64) {
     const int nr = min(64, rows - row0);
@@ -552,8 +617,13 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
       if (c < r) {
         sJ[rr][c] = dec[((size_t)(1 + c) * cap + p) * d + a];
       } else {
-        float b;
-        if (mode == NE_VEL) b = R.v_trial[(size_t)p * d + a];
+        double b;
+        if (mode == NE_VEL) {
+          // right-hand side of the velocity increment: v_trial - J vhat_n
+          double jv = 0.0;
+          for (int c2 = 0; c2 < r; ++c2) jv = fma((double)dec[((size_t)(1 + c2) * cap + p) * d + a], S.vh[c2], jv);
+          b = (double)R.v_trial[(size_t)p * d + a] - jv;
+        }
         else if (mode == NE_GN) b = dec[((size_t)(1 + r) * cap + p) * d + a] + R.dt * R.v_trial[(size_t)p * d + a];
         else b = target[(size_t)p * d + a] - dec[(size_t)p * d + a];
         sb[rr] = b;
@@ -570,12 +640,12 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
           ++i;
         }
         const int j = i + rem;
-        for (int q = 0; q < nr; ++q) s = fma((double)sJ[q][i], (double)sJ[q][j], s);
+        for (int q = 0; q < nr; ++q) s = fma(sJ[q][i], sJ[q][j], s);
       } else if (e < n_mat + r) {
         const int i = e - n_mat;
-        for (int q = 0; q < nr; ++q) s = fma((double)sJ[q][i], (double)sb[q], s);
+        for (int q = 0; q < nr; ++q) s = fma(sJ[q][i], sb[q], s);
       } else {
-        for (int q = 0; q < nr; ++q) s = fma((double)sb[q], (double)sb[q], s);
+        for (int q = 0; q < nr; ++q) s = fma(sb[q], sb[q], s);
       }
       atomicAdd(&S.acc[e], s);
     }
@@ -642,7 +712,8 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
   }
   if (mode == NE_VEL) {
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
-      const double v = bvec[i];
+      // the solve gave the increment from vhat_n (zero if the factorisation failed)
+      const double v = S.vh[i] + bvec[i];
       S.vh_new[i] = v;
       if (projection == 1) {
         // velocity-only projection (Alg. 7): xhat_{n+1} = xhat_n + dt vhat_{n+1}
@@ -833,6 +904,8 @@ struct rom_ctx {
   uint32_t* status = nullptr;
   int32_t* nP_all = nullptr;    // device constant P (decode-all point count)
   float* outQ = nullptr;        // (2 d + 2, P, d)
+  float* Fref_inv = nullptr;    // (P, d, d) with f_reference
+  float* xref32 = nullptr;      // (r) reference latent
   float* outS = nullptr;        // (r + 2, k, d)
   float* outLS = nullptr;       // (2, kLS * k, d) (capacity kLS * P for the fit)
   double* solve_mem = nullptr;
@@ -949,6 +1022,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
   MPM_CHECK_ARG(cfg->ridge >= 0.f, "ridge >= 0");
   MPM_CHECK_ARG(cfg->affine == 0 || cfg->affine == 1, "affine: 0 or 1");
+  MPM_CHECK_ARG(cfg->f_reference == 0 || cfg->f_reference == 1, "f_reference: 0 or 1");
   auto* c = new rom_ctx();
   c->cfg = *cfg;
   c->dec = dec;
@@ -981,6 +1055,10 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   if ((st = ralloc(&c->status, 1)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->nP_all, 1)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->outQ, (size_t)(2 * d + 2) * P * d)) != MPM_OK) return fail(st);
+  if (cfg->f_reference) {
+    if ((st = ralloc(&c->Fref_inv, (size_t)P * d * d)) != MPM_OK) return fail(st);
+    if ((st = ralloc(&c->xref32, (size_t)r)) != MPM_OK) return fail(st);
+  }
   if ((st = ralloc(&c->outS, (size_t)(r + 2) * P * d)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->outLS, (size_t)2 * kLS * P * d)) != MPM_OK) return fail(st);
   const int n_acc = r * (r + 1) / 2 + r + 1;
@@ -1061,6 +1139,8 @@ void rom_destroy(rom_ctx* c) {
   cudaFree(c->status);
   cudaFree(c->nP_all);
   cudaFree(c->outQ);
+  cudaFree(c->Fref_inv);
+  cudaFree(c->xref32);
   cudaFree(c->outS);
   cudaFree(c->outLS);
   cudaFree(c->solve_mem);
@@ -1163,6 +1243,35 @@ mpm_status rom_decode_all(rom_ctx* c, float* x_out, void* stream) {
   return st;
 }
 
+mpm_status rom_set_reference(rom_ctx* c, const double* xhat_ref, void* stream) {
+  MPM_CHECK_ARG(c && xhat_ref, "null argument");
+  MPM_CHECK_ARG(c->cfg.f_reference == 1, "rom_set_reference needs cfg.f_reference = 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = c->d, r = c->r, P = c->P;
+  std::vector<double> h(r);
+  MPM_CUDA_TRY(cudaMemcpyAsync(h.data(), xhat_ref, sizeof(double) * r, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<float> h32(h.begin(), h.end());
+  MPM_CUDA_TRY(cudaMemcpyAsync(c->xref32, h32.data(), sizeof(float) * r, cudaMemcpyHostToDevice, s));
+  int kr[4] = {0, 1, 2, 3};
+  mpm_status st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, P, c->xref32, nullptr, kr, d + 1, c->outQ, s);
+  if (st != MPM_OK) return st;
+  const int b = std::max(1, std::min(ceil_div(P, 256), c->n_sm * 4));
+  if (d == 2)
+    rom_reference<2><<<b, 256, 0, s>>>(c->outQ, P, P, c->Fref_inv, c->status);
+  else
+    rom_reference<3><<<b, 256, 0, s>>>(c->outQ, P, P, c->Fref_inv, c->status);
+  MPM_CUDA_TRY(cudaGetLastError());
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  // the captured step graph holds the kernel arguments: recapture on the next step
+  c->dv.Fref_inv = c->Fref_inv;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return MPM_OK;
+}
+
 mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int iters, void* stream) {
   MPM_CHECK_ARG(c && target && V0, "null argument");
   MPM_CHECK_ARG(iters >= 1 && iters <= 100, "iters in [1, 100]");
@@ -1199,8 +1308,9 @@ mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int
     st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, P, c->sv.xk32, nullptr, ks, r + 1, c->outS, s);
   }
   if (st == MPM_OK) {
-    // NE_VEL reads v_trial: stage V0 there; rows = all particles
+    // NE_VEL reads v_trial: stage V0 there; rows = all particles; the prior vhat is zero
     MPM_CUDA_TRY(cudaMemcpyAsync(c->v_trial, vel, sizeof(float) * P * d, cudaMemcpyDeviceToDevice, s));
+    MPM_CUDA_TRY(cudaMemsetAsync(c->sv.vh, 0, sizeof(double) * r, s));
     // solve J^T J vhat = J^T V0 (projection flag 1 keeps xk: the commit below sets the state)
     MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.xh, c->sv.xk, sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
     rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, P, NE_VEL, nullptr, 1, P, 0.f);
@@ -1215,6 +1325,10 @@ mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int
   MPM_CUDA_TRY(cudaMemcpy(xh.data(), c->sv.xh, sizeof(double) * r, cudaMemcpyDeviceToHost));
   MPM_CUDA_TRY(cudaMemcpy(vh.data(), c->sv.vh_new, sizeof(double) * r, cudaMemcpyDeviceToHost));
   for (int i = 0; i < r; ++i) xp[i] = xh[i] - (double)c->cfg.dt * vh[i];
+  if (c->cfg.f_reference) {
+    const mpm_status sr = rom_set_reference(c, xh.data(), stream);
+    if (sr != MPM_OK) return sr;
+  }
   return rom_set_state(c, xh.data(), vh.data(), xp.data(), 0, stream);
 }
 

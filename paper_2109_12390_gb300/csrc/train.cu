@@ -140,17 +140,24 @@ struct BwdArgs {
 constexpr int kExchRows = 104;
 constexpr int kExchStride = kW + 1;   // padded row stride: lanes of a warp hit distinct banks
 
-__global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
+// 256 threads: warps w and w + 4 read the same tensor-memory lane group; thread
+// t owns tile row rw = 32 (w % 4) + lane and the feature half h = w / 4
+// (features 64 h .. 64 h + 63) of every layer.
+constexpr int kBwdThreads = 256;
+
+__global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* wt = smem;                                 // n_tc x 32 KB (transposed square weights)
   uint8_t* atile = smem + kMaxTC * kLayerBytes;       // 32 KB
-  float* exch = (float*)(atile + kLayerBytes);        // kExchRows x 128
+  float* exch = (float*)(atile + kLayerBytes);        // kExchRows x 129
   float* sy = exch + kExchRows * kExchStride;         // 128 x 3
   float* sbias = sy + 128 * 3;                        // 128
   DecSmemTail* tail = (DecSmemTail*)(sbias + kW);
-  __shared__ double s_loss[4];
+  __shared__ double s_loss[8];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int rw = (warp & 3) * 32 + lane;              // tile row / tensor-memory lane
+  const int h = warp >> 2;                            // feature half
   const int d = a.d, r = a.r, R = a.R, Pt = a.Pt;
 
   if (t == 0) {
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
     raise_status(a.status, STATUS_TIMEOUT);
     atomicExch(&tail->abort, 1);
   }
-  sbias[t] = 0.f;
+  if (t < kW) sbias[t] = 0.f;
   __syncthreads();
   constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kW);
   uint32_t mma_phase = 0;
@@ -183,11 +190,11 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !tail->abort; tile += gridDim.x) {
     const int64_t row0 = tile * 128;
-    const int k = t / Pt, q = t % Pt;
+    const int k = rw / Pt, q = rw % Pt;
     const int64_t p = tile * Pt + q;
     const bool valid = (k < R) && (p < a.n);
     const int cls = !valid ? -1 : (k == 0 ? 0 : 1);
-    const int64_t gr = row0 + t, gp = row0 + q;
+    const int64_t gr = row0 + rw, gp = row0 + q;
     // ---- output layer: residual adjoints ybar (FP32)
     float ybar[3] = {0.f, 0.f, 0.f};
     if (valid) {
@@ -204,26 +211,29 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
           e = a.b.mask[p] * (o[i] - a.b.tv[p * d + i]);
           w = a.lamv;
         }
-        my_loss += (double)w * e * e;
+        if (h == 0) my_loss += (double)w * e * e;
         ybar[i] = 2.f * w * e * scale[i] / (float)a.n;
       }
     }
-    for (int i = 0; i < 3; ++i) sy[t * 3 + i] = ybar[i];
+    if (h == 0)
+      for (int i = 0; i < 3; ++i) sy[rw * 3 + i] = ybar[i];
     __syncthreads();
     {
-      // dWout[i][f] = sum_rows ybar_i a_last[f];  thread t = feature f
-      const __nv_bfloat16* al = a.astore + (int64_t)(a.n_hidden - 1) * kW * a.rows_total + (int64_t)t * a.rows_total + row0;
+      // dWout[i][f] = sum_rows ybar_i a_last[f]: thread = feature f = t % 128, rows 64 (t / 128) ..
+      const int f = t & 127, rh = t >> 7;
+      const __nv_bfloat16* al = a.astore + (int64_t)(a.n_hidden - 1) * kW * a.rows_total + (int64_t)f * a.rows_total +
+                                row0 + 64 * rh;
       float acc[3] = {0.f, 0.f, 0.f};
-      for (int c = 0; c < 128; c += 8) {
+      for (int c = 0; c < 64; c += 8) {
         const uint4 u = *reinterpret_cast<const uint4*>(al + c);
         const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&u);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float av = __bfloat162float(hv[j]);
-          for (int i = 0; i < d; ++i) acc[i] = fmaf(sy[(c + j) * 3 + i], av, acc[i]);
+          for (int i = 0; i < d; ++i) acc[i] = fmaf(sy[(64 * rh + c + j) * 3 + i], av, acc[i]);
         }
       }
-      for (int i = 0; i < d; ++i) atomicAdd(&a.gparams[a.gWout_off + i * kW + t], acc[i]);
+      for (int i = 0; i < d; ++i) atomicAdd(&a.gparams[a.gWout_off + i * kW + f], acc[i]);
       if (t < d) {
         float sb = 0.f;
         for (int q2 = 0; q2 < Pt; ++q2) sb += sy[q2 * 3 + t];
@@ -231,9 +241,6 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
       }
     }
     // ---- reverse sweep over the hidden layers
-    float hin[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) hin[j] = 0.f;
     for (int l = a.n_hidden - 1; l >= 0; --l) {
       const bool from_tmem = (l < a.n_hidden - 1);
       if (from_tmem) {
@@ -247,16 +254,17 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
       __syncthreads();
       if (tail->abort) break;
       const float* zl = a.zstore + (int64_t)l * kW * a.rows_total;
-      for (int ch = 0; ch < kW / 32; ++ch) {
+      for (int i2 = 0; i2 < 2; ++i2) {
+        const int ch = 2 * h + i2;
         float hb[32];
         if (from_tmem) {
-          tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, hb);
+          tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + ch * 32, hb);
         } else {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            float s = 0.f;
-            for (int o = 0; o < d; ++o) s = fmaf(__ldg(&a.Wout[o * kW + ch * 32 + i]), ybar[o], s);
-            hb[i] = s;
+            float sacc = 0.f;
+            for (int o = 0; o < d; ++o) sacc = fmaf(__ldg(&a.Wout[o * kW + ch * 32 + i]), ybar[o], sacc);
+            hb[i] = sacc;
           }
         }
         float zb[32];
@@ -267,7 +275,7 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
             const float zp = zl[(int64_t)f * a.rows_total + gp];
             const float zr = zl[(int64_t)f * a.rows_total + gr];
             zb[i] = act_d1(a.act, zp) * hb[i];
-            exch[(t - Pt) * kExchStride + f] = act_d2(a.act, zp) * zr * hb[i];
+            exch[(rw - Pt) * kExchStride + f] = act_d2(a.act, zp) * zr * hb[i];
           }
         }
         __syncthreads();
@@ -276,17 +284,17 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
           for (int i = 0; i < 32; ++i) {
             const int f = ch * 32 + i;
             const float zp = zl[(int64_t)f * a.rows_total + gp];
-            float s = act_d1(a.act, zp) * hb[i];
-            for (int kk = 1; kk < R; ++kk) s += exch[((kk - 1) * Pt + q) * kExchStride + f];
-            zb[i] = s;
+            float sacc = act_d1(a.act, zp) * hb[i];
+            for (int kk = 1; kk < R; ++kk) sacc += exch[((kk - 1) * Pt + q) * kExchStride + f];
+            zb[i] = sacc;
           }
         } else if (cls < 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) zb[i] = 0.f;
         }
-        // bias gradient: sum of the primal rows' z_bar (primal rows all sit in warp 0);
+        // bias gradient: sum of the primal rows' z_bar (primal rows all sit in lane group 0);
         // transpose-reduce the 32 columns across the warp so lane i ends with column i
-        if (warp == 0) {
+        if ((warp & 3) == 0) {
           float v[32];
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = (cls == 0) ? zb[i] : 0.f;
@@ -305,31 +313,24 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
         }
         if (l >= 1) {
 #pragma unroll
-          for (int j = 0; j < 32; j += 8) store_bf16x8(atile, t, ch * 32 + j, zb + j);
+          for (int j = 0; j < 32; j += 8) store_bf16x8(atile, rw, ch * 32 + j, zb + j);
           __nv_bfloat16* zs = a.zbstore + (int64_t)(l - 1) * kW * a.rows_total + gr;
 #pragma unroll
           for (int i = 0; i < 32; ++i) zs[(int64_t)(ch * 32 + i) * a.rows_total] = __float2bfloat16_rn(zb[i]);
         } else {
+          // first-layer adjoints (FP32); the first-layer weight gradient and the latent
+          // adjoints are formed from them by train_dw0_lat
           float* zs = a.zb0 + gr;
 #pragma unroll
           for (int i = 0; i < 32; ++i) zs[(int64_t)(ch * 32 + i) * a.rows_total] = zb[i];
-          if (cls >= 0) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (j < r) {
-                float s = 0.f;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) s = fmaf(__ldg(&a.W0[(ch * 32 + i) * (d + r) + d + j]), zb[i], s);
-                hin[j] += s;
-              }
-            }
-          }
         }
         __syncthreads();
       }
-      // bias gradient of layer l (sbias was filled by warp 0 before the last barrier)
-      atomicAdd(&a.gparams[a.gb_off[l] + t], sbias[t]);
-      sbias[t] = 0.f;
+      // bias gradient of layer l (sbias was filled before the last barrier)
+      if (t < kW) {
+        atomicAdd(&a.gparams[a.gb_off[l] + t], sbias[t]);
+        sbias[t] = 0.f;
+      }
       if (l >= 1) {
         // next adjoint rows: h_bar_{l-1} = z_bar_l W_l  (B operand = W_l^T image)
         tc::fence_async_smem();
@@ -349,16 +350,6 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
       }
     }
     if (tail->abort) break;
-    // latent adjoints of this row
-    if (cls == 0) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < r) a.g_lat_pt[p * r + j] = hin[j];
-    } else if (cls == 1 && k == d + 1) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < r) a.g_u_pt[p * r + j] = hin[j];
-    }
     tc::tc_fence_before();
     __syncthreads();
   }
@@ -367,7 +358,11 @@ __global__ void __launch_bounds__(128, 1) train_bwd_tc(BwdArgs a) {
   for (int o = 16; o > 0; o >>= 1) my_loss += __shfl_down_sync(0xffffffffu, my_loss, o);
   if ((t & 31) == 0) s_loss[warp] = my_loss;
   __syncthreads();
-  if (t == 0) atomicAdd(a.loss, s_loss[0] + s_loss[1] + s_loss[2] + s_loss[3]);
+  if (t == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < kBwdThreads / 32; ++w) tot += s_loss[w];
+    atomicAdd(a.loss, tot);
+  }
   tc::tc_fence_after();
   if (warp == 0) tc::tmem_free<kW>(tmem);
 }
@@ -454,43 +449,88 @@ __global__ void __launch_bounds__(128, 1) train_dw_gemm(const __nv_bfloat16* zbs
 // First-layer weight gradient: dW0[f][j] = sum_rows zb0[f][row] in_row[j]
 // (in_row: normalised input for primal rows, the input direction for tangent rows).
 constexpr int kMaxIn = 40;
-__global__ void train_dw0(const float* zb0, int64_t rows_total, Batch b, int d, int r, int R, int Pt,
-                          const float* norm, float* gW0) {
-  const int f = blockIdx.x;
+// First-layer weight gradient dW0[f][j] = sum_rows zbar0[f][row] in[row][j] and the
+// latent adjoints of the primal rows (d loss / d xhat) and of the JVP rows
+// (d loss / d u), sum_f zbar0[f][row] W0[f][d + j], from one pass over zbar0 in
+// chunks of 32 rows staged in shared memory.  in[row] is the layer-0 input of
+// the row: [Xn, xhat] (primal), e_k / X_range_k (X tangent), [0, u] (JVP).
+constexpr int kDw0Rows = 32;
+__global__ void __launch_bounds__(256) train_dw0_lat(const float* zb0, int64_t rows_total, Batch b, int d, int r,
+                                                     int R, int Pt, const float* norm, const float* W0, float* gW0,
+                                                     float* g_lat_pt, float* g_u_pt) {
+  __shared__ float sz[kW][kDw0Rows + 1];
+  __shared__ float sin_[kDw0Rows][kMaxIn + 1];
+  __shared__ float sWl[kW][33];
+  const int t = threadIdx.x;
   const int K = d + r;
+  for (int e = t; e < kW * r; e += blockDim.x) sWl[e / r][e % r] = W0[(e / r) * K + d + (e % r)];
+  const int f = t & (kW - 1), half = t >> 7;
   float acc[kMaxIn];
 #pragma unroll
   for (int j = 0; j < kMaxIn; ++j) acc[j] = 0.f;
-  for (int64_t gr = threadIdx.x; gr < rows_total; gr += blockDim.x) {
-    const float z = zb0[(int64_t)f * rows_total + gr];
-    if (z == 0.f) continue;
-    const int64_t tile = gr / 128;
-    const int t = (int)(gr % 128), k = t / Pt, q = t % Pt;
-    const int64_t p = tile * Pt + q;
-    if (k >= R || p >= b.B) continue;
+  const int64_t n_chunks = (rows_total + kDw0Rows - 1) / kDw0Rows;
+  for (int64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+    const int64_t row0 = chunk * kDw0Rows;
+    __syncthreads();
+    for (int e = t; e < kW * kDw0Rows; e += blockDim.x) {
+      const int ff = e / kDw0Rows, rr = e % kDw0Rows;
+      sz[ff][rr] = row0 + rr < rows_total ? zb0[(int64_t)ff * rows_total + row0 + rr] : 0.f;
+    }
+    for (int e = t; e < kDw0Rows * K; e += blockDim.x) {
+      const int rr = e / K, j = e % K;
+      const int64_t gr = row0 + rr;
+      const int64_t tile = gr / 128;
+      const int tr = (int)(gr % 128), k = tr / Pt, q = tr % Pt;
+      const int64_t p = tile * Pt + q;
+      float in = 0.f;
+      if (gr < rows_total && k < R && p < b.B) {
+        if (k == 0) in = j < d ? (b.X[p * d + j] - norm[j]) / norm[d + j] : b.xh[p * r + (j - d)];
+        else if (k <= d) in = (j == k - 1) ? 1.f / norm[d + k - 1] : 0.f;
+        else in = j < d ? 0.f : b.u[p * r + (j - d)];
+      }
+      sin_[rr][j] = in;
+    }
+    __syncthreads();
+    // (a) weight gradient: this thread's feature over its half of the rows
+#pragma unroll 4
+    for (int rr = 16 * half; rr < 16 * half + 16; ++rr) {
+      const float z = sz[f][rr];
 #pragma unroll
-    for (int j = 0; j < kMaxIn; ++j) {
-      if (j >= K) break;
-      float in;
-      if (k == 0) in = j < d ? (b.X[p * d + j] - norm[j]) / norm[d + j] : b.xh[p * r + (j - d)];
-      else if (k <= d) in = (j == k - 1) ? 1.f / norm[d + k - 1] : 0.f;
-      else in = j < d ? 0.f : b.u[p * r + (j - d)];
-      acc[j] = fmaf(z, in, acc[j]);
+      for (int j = 0; j < kMaxIn; ++j)
+        if (j < K) acc[j] = fmaf(z, sin_[rr][j], acc[j]);
+    }
+    // (b) latent adjoints of primal and JVP rows
+    for (int o = t; o < kDw0Rows * r; o += blockDim.x) {
+      const int rr = o / r, j = o % r;
+      const int64_t gr = row0 + rr;
+      const int64_t tile = gr / 128;
+      const int tr = (int)(gr % 128), k = tr / Pt, q = tr % Pt;
+      const int64_t p = tile * Pt + q;
+      if (gr >= rows_total || p >= b.B || !(k == 0 || k == d + 1)) continue;
+      float v = 0.f;
+#pragma unroll 8
+      for (int ff = 0; ff < kW; ++ff) v = fmaf(sz[ff][rr], sWl[ff][j], v);
+      if (k == 0) g_lat_pt[p * r + j] = v;
+      else g_u_pt[p * r + j] = v;
     }
   }
-  __shared__ float red[8][kMaxIn];
-#pragma unroll
-  for (int j = 0; j < kMaxIn; ++j) {
-    float v = acc[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][j] = v;
-  }
+  // combine the two row halves of each feature, then one atomic per weight
   __syncthreads();
-  if (threadIdx.x < K) {
-    float s = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-    atomicAdd(&gW0[f * K + threadIdx.x], s);
+  float* red = &sz[0][0];   // reused as [128][33]: two passes of 32 inputs
+#pragma unroll
+  for (int j0 = 0; j0 < kMaxIn; j0 += 32) {
+    if (half == 1) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j0 + j < kMaxIn) red[f * 33 + j] = acc[j0 + j];
+    }
+    __syncthreads();
+    if (half == 0) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j0 + j < K) atomicAdd(&gW0[f * K + j0 + j], acc[j0 + j] + red[f * 33 + j]);
+    }
+    __syncthreads();
   }
 }
 
@@ -645,7 +685,7 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
   a.loss = c->loss;
   a.status = c->status;
   const int bw = (int)std::max<int64_t>(1, std::min<int64_t>(c->n_tiles, c->n_sm));
-  train_bwd_tc<<<bw, 128, c->bwd_smem, s>>>(a);
+  train_bwd_tc<<<bw, kBwdThreads, c->bwd_smem, s>>>(a);
   MPM_CUDA_TRY(cudaGetLastError());
   if (dec->n_tc > 0) {
     const int splits = std::max(1, c->n_sm / dec->n_tc);
@@ -655,7 +695,9 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
     train_dw_gemm<<<g, 128, 0, s>>>(c->zbstore, c->astore, c->rows_total, kps, c->gparams, c->d_w_off, c->status);
     MPM_CUDA_TRY(cudaGetLastError());
   }
-  train_dw0<<<kW, 256, 0, s>>>(c->zb0, c->rows_total, c->b, d, r, c->R, c->Pt, dec->norm, c->gparams + dec->w_off[0]);
+  train_dw0_lat<<<c->n_sm * 4, 256, 0, s>>>(c->zb0, c->rows_total, c->b, d, r, c->R, c->Pt, dec->norm,
+                                           dec->params + dec->w_off[0], c->gparams + dec->w_off[0], c->g_lat_pt,
+                                           c->g_u_pt);
   MPM_CUDA_TRY(cudaGetLastError());
   train_lat_scatter<<<blocks, 256, 0, s>>>(c->b, r, c->g_lat_pt, c->g_u_pt, c->cfg.dt_snap, c->g_lat);
   MPM_CUDA_TRY(cudaGetLastError());

@@ -25,11 +25,13 @@ class ROM:
     """One reduced-order instance bound to a decoder and the reference positions X."""
 
     def __init__(self, decoder, X, *, dim, n_grid, dx, dt, gravity, bc, bc_width, material, transfer, rho,
-                 p_vol, E, nu, n_samples, seed, instance=0, gn_iters=3, projection=0, ridge=0.0, affine=0):
+                 p_vol, E, nu, n_samples, seed, instance=0, gn_iters=3, projection=0, ridge=0.0, affine=0,
+                 f_reference=0):
         L = _abi.lib()
         g = (C.c_float * 3)(*[float(v) for v in gravity])
         self.cfg = _abi.RomConfig(dim, n_grid, dx, dt, g, bc, bc_width, material, transfer, rho, p_vol, E, nu,
-                                  decoder.r, n_samples, seed, instance, gn_iters, projection, ridge, affine)
+                                  decoder.r, n_samples, seed, instance, gn_iters, projection, ridge, affine,
+                                  f_reference)
         self._X = np.ascontiguousarray(X, np.float32) if isinstance(X, np.ndarray) else X
         self.P = int(self._X.shape[0])
         self.d, self.r = dim, decoder.r
@@ -41,13 +43,13 @@ class ROM:
 
     @classmethod
     def from_scene(cls, decoder, sc, n_samples, seed, instance=0, gn_iters=3, projection=0, X=None, ridge=0.0,
-                   affine=0):
+                   affine=0, f_reference=0):
         k = 0
         return cls(decoder, sc.x if X is None else X, dim=sc.dim, n_grid=sc.n_grid, dx=sc.dx, dt=sc.dt,
                    gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width, material=sc.material,
                    transfer=sc.transfer, rho=sc.rho, p_vol=sc.p_vol, E=float(sc.E[k]), nu=float(sc.nu[k]),
                    n_samples=n_samples, seed=seed, instance=instance, gn_iters=gn_iters, projection=projection,
-                   ridge=ridge, affine=affine)
+                   ridge=ridge, affine=affine, f_reference=f_reference)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -78,6 +80,10 @@ class ROM:
         t = np.ascontiguousarray(target, np.float32)
         v = np.ascontiguousarray(np.broadcast_to(V0, (self.P, self.d)), np.float32)
         _abi.check(_abi.lib().rom_fit_initial(self._h, _ptr(t), _ptr(v), int(iters), _stream(stream)))
+
+    def set_reference(self, xhat_ref, stream=None):
+        a = np.ascontiguousarray(xhat_ref, np.float64)
+        _abi.check(_abi.lib().rom_set_reference(self._h, _p64(a), _stream(stream)))
 
     def step(self, n_steps=1, stream=None):
         _abi.check(_abi.lib().rom_step(self._h, int(n_steps), _stream(stream)))

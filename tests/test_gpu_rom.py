@@ -70,7 +70,7 @@ def test_translation_decoder_reproduces_free_fall():
 
 
 def _elu_setup(seed=3, side=32, r=16, k=64, material=OM.FIXED_COROTATED, transfer=OM.MLS, projection=0,
-               n_hidden=5, affine=0):
+               n_hidden=5, affine=0, f_reference=0):
     from paper_2109_12390_gb300.decoder import Decoder
     from paper_2109_12390_gb300.rom import ROM
     sc = S.block_2d(side=side, dt=5e-5, origin=(0.4, 0.3), E=20.0)
@@ -80,7 +80,8 @@ def _elu_setup(seed=3, side=32, r=16, k=64, material=OM.FIXED_COROTATED, transfe
     p = S.xavier_decoder(seed, 2, r, 128, n_hidden, OD.ELU, X_min=X.min(0), X_range=X.max(0) - X.min(0),
                          out_shift=c, out_scale=np.full(2, 0.05), bias_scale=0.2)
     dec = Decoder.from_params(p)
-    rom = ROM.from_scene(dec, sc, n_samples=k, seed=seed, projection=projection, affine=affine)
+    rom = ROM.from_scene(dec, sc, n_samples=k, seed=seed, projection=projection, affine=affine,
+                         f_reference=f_reference)
     rng = np.random.default_rng(seed)
     xh = 0.3 * rng.normal(size=r)
     vh = rng.normal(size=r)
@@ -169,6 +170,25 @@ def test_one_step_affine_quadrature_velocity(n_hidden, tol):
     rs.affine = "zero"
     v_zero, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
     assert rel(v_zero, v_trial) > 1e-2   # the affine term is not negligible here (3-4 %)
+
+
+@pytest.mark.parametrize("n_hidden,tol", [(1, 1e-4), (5, TOL_BF16)])
+def test_one_step_reference_gradient(n_hidden, tol):
+    """f_reference: the stress uses (dg/dX)(xhat_n) [(dg/dX)(xhat_ref)]^-1; v_trial against the
+    oracle with the same reference, and different from the uncorrected step."""
+    sc, p, dec, rom, rs, xh, vh, xp = _elu_setup(seed=6, r=4, n_hidden=n_hidden, projection=1, f_reference=1)
+    xref = xh + 0.05 * np.random.default_rng(9).normal(size=len(xh))
+    rom.set_reference(xref)
+    rom.step(1)
+    assert rom.status() & ~ALLOWED_RANDOM == 0
+    dbg = rom.debug()
+    xa = dbg["x_all"].astype(np.float64)
+    rs.F_ref_inv = OR.reference_inverse(p, sc.x, xref)
+    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
+    assert rel(dbg["v_trial"], v_trial) < tol
+    rs.F_ref_inv = None
+    v_plain, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
+    assert rel(v_plain, v_trial) > 10 * min(tol, 1e-3)
 
 
 def test_fit_initial_condition():

@@ -140,3 +140,60 @@ def test_ridge_projection_equals_augmented_least_squares():
     np.testing.assert_allclose(R.lstsq(J, b, rho), aug, rtol=1e-10, atol=1e-12)
     # rho -> 0 recovers the least-squares fit on the well-determined directions
     np.testing.assert_allclose(J @ R.lstsq(J, b, 1e-14), J @ R.lstsq(J, b), rtol=1e-6, atol=1e-8)
+
+
+def test_ridge_velocity_projection_penalises_the_change_from_vhat_n():
+    """With the ridge, the velocity projection equals the stacked least-squares problem
+    [J; sqrt(lam) I] v = [v_trial; sqrt(lam) vhat_n]: near-null latent directions keep vhat_n
+    (a constant latent velocity that J reproduces exactly is a fixed point for any ridge), and
+    ridge = 0 is the plain fit."""
+    rng = np.random.default_rng(13)
+    d, r = 2, 4
+    X = rng.uniform(0.3, 0.6, size=(30, d))
+    dec = S.xavier_decoder(2, d, r, 16, 2, D.ELU, X_min=X.min(0), X_range=X.max(0) - X.min(0),
+                           out_scale=np.full(d, 0.1), bias_scale=0.2)
+    xh = 0.2 * rng.normal(size=r)
+    vh_n = rng.normal(size=r)
+    _, _, Jq = D.jacobians(dec, X, xh)
+    J = Jq.reshape(-1, r)
+    vt = (J @ vh_n).reshape(-1, d)
+    for rho in (0.0, 1e-4, 1e-1):
+        np.testing.assert_allclose(R.project_velocity(dec, X, xh, vt, rho, vh_n), vh_n, rtol=1e-9, atol=1e-11)
+    vt2 = vt + 0.3 * rng.normal(size=vt.shape)
+    rho = 1e-2
+    lam = rho * np.trace(J.T @ J) / r
+    aug = np.linalg.lstsq(np.vstack([J, np.sqrt(lam) * np.eye(r)]),
+                          np.concatenate([vt2.reshape(-1), np.sqrt(lam) * vh_n]), rcond=None)[0]
+    np.testing.assert_allclose(R.project_velocity(dec, X, xh, vt2, rho, vh_n), aug, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(R.project_velocity(dec, X, xh, vt2, 0.0, vh_n),
+                               np.linalg.lstsq(J, vt2.reshape(-1), rcond=None)[0], rtol=1e-9, atol=1e-11)
+
+
+def test_reference_gradient_makes_the_decoded_initial_state_stress_free():
+    """f_reference: with G_p the inverse decoded gradient at xhat_ref, the stress-carrying gradient
+    at xhat_ref is the identity exactly, so a body at rest (vhat = 0, g = 0) in the decoded
+    reference configuration gets zero trial velocity; without the correction the decoder's
+    gradient error at rest produces stress and motion."""
+    from oracle import mpm as OM
+    sc = S.block_2d(side=8, dt=5e-5, origin=(0.4, 0.4), E=1e4)
+    rng = np.random.default_rng(5)
+    # a linear decoder g = A X + E xhat whose gradient A at rest is 1 % off the identity
+    lo, rng_ = sc.x.min(0), sc.x.max(0) - sc.x.min(0)
+    dec = S.xavier_decoder(0, 2, 3, 128, 0, D.IDENTITY, X_min=lo, X_range=rng_)
+    A = np.eye(2) + 0.01 * rng.uniform(-1, 1, (2, 2))
+    dec.W[0] = np.concatenate([A @ np.diag(rng_), 0.01 * rng.normal(size=(2, 3))], axis=1)
+    dec.b[0] = A @ lo
+    xh = 0.1 * rng.normal(size=3)
+    rs = R.RomScene(X=sc.x.copy(), mass=sc.p_mass, vol=sc.p_vol, E=1e4, nu=0.3, dx=sc.dx, dt=sc.dt,
+                    n_grid=sc.n_grid, gravity=np.zeros(3), bc=sc.bc, bc_width=sc.bc_width,
+                    material=OM.NEO_HOOKEAN, transfer=OM.MLS, n_samples=16, seed=1)
+    x_all = D.decode(dec, sc.x, xh)
+    samples = R.sample_set(1, 0, 0, len(sc.x), 16)
+    v0, _, _, _ = R.local_dynamics(dec, rs, xh, np.zeros(3), samples, x_all)
+    assert np.abs(v0).max() > 1e-6           # stress from the decoder's gradient error
+    rs.F_ref_inv = R.reference_inverse(dec, sc.x, xh)
+    _, FX, _ = D.jacobians(dec, sc.x, xh)
+    np.testing.assert_allclose(np.einsum("pik,pkj->pij", FX, rs.F_ref_inv), np.broadcast_to(np.eye(2), FX.shape),
+                               atol=1e-12)
+    v1, _, _, _ = R.local_dynamics(dec, rs, xh, np.zeros(3), samples, x_all)
+    assert np.abs(v1).max() < 1e-9 * np.abs(v0).max()
