@@ -268,14 +268,21 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
           }
         }
         float zb[32];
+        // pre-activations of this chunk: the point's primal z (every row) and the row's own
+        // tangent zdot (tangent rows), all loads issued before the exchange barrier
+        float zpv[32], zrv[32];
+        if (cls >= 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) zpv[i] = zl[(int64_t)(ch * 32 + i) * a.rows_total + gp];
+        }
         if (cls == 1) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) zrv[i] = zl[(int64_t)(ch * 32 + i) * a.rows_total + gr];
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int f = ch * 32 + i;
-            const float zp = zl[(int64_t)f * a.rows_total + gp];
-            const float zr = zl[(int64_t)f * a.rows_total + gr];
-            zb[i] = act_d1(a.act, zp) * hb[i];
-            exch[(rw - Pt) * kExchStride + f] = act_d2(a.act, zp) * zr * hb[i];
+            zb[i] = act_d1(a.act, zpv[i]) * hb[i];
+            exch[(rw - Pt) * kExchStride + f] = act_d2(a.act, zpv[i]) * zrv[i] * hb[i];
           }
         }
         __syncthreads();
@@ -283,8 +290,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int f = ch * 32 + i;
-            const float zp = zl[(int64_t)f * a.rows_total + gp];
-            float sacc = act_d1(a.act, zp) * hb[i];
+            float sacc = act_d1(a.act, zpv[i]) * hb[i];
             for (int kk = 1; kk < R; ++kk) sacc += exch[((kk - 1) * Pt + q) * kExchStride + f];
             zb[i] = sacc;
           }

@@ -58,6 +58,7 @@ class RomRun:
     fom_steps_per_s: float
     status: int
     steps: int
+    error_percent_at: dict = dataclasses.field(default_factory=dict)   # step -> accumulated error so far
 
 
 def fom_positions(scene, steps, device="cuda"):
@@ -87,7 +88,7 @@ def fom_positions(scene, steps, device="cuda"):
 
 
 def rom_error(decoder, scene, fom_xs, *, n_samples=256, seed=4, gn_iters=3, projection=0, fit_iters=20, ridge=0.0,
-              affine=0, f_reference=0):
+              affine=0, f_reference=0, checkpoints=()):
     """Runs the reduced model from the least-squares initial condition (Eq. essentialSpecInt) for as
     many steps as fom_xs has, accumulating the Section 5 error on the device."""
     steps = fom_xs.shape[0] - 1
@@ -104,13 +105,20 @@ def rom_error(decoder, scene, fom_xs, *, n_samples=256, seed=4, gn_iters=3, proj
     rom.fit_initial(scene.x, scene.v, iters=fit_iters)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    marks = {}
     for n in range(1, steps + 1):
         rom.step(1)
         rom.decode_all(xr)
         metric_accumulate(xr, fom_xs[n], acc)
+        if n in checkpoints:
+            marks[n] = acc.clone()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     num, den = acc.cpu().numpy()
+    at = {}
+    for n, a in marks.items():
+        nn, dd = a.cpu().numpy()
+        at[n] = 100.0 * float(np.sqrt(nn / dd))
     # pure stepping rate
     rom.fit_initial(scene.x, scene.v, iters=fit_iters)
     torch.cuda.synchronize()
@@ -121,4 +129,4 @@ def rom_error(decoder, scene, fom_xs, *, n_samples=256, seed=4, gn_iters=3, proj
     status = rom.status()
     rom.close()
     return RomRun(error_percent=100.0 * float(np.sqrt(num / den)), rom_steps_per_s=rate, fom_steps_per_s=float("nan"),
-                  status=status, steps=steps)
+                  status=status, steps=steps, error_percent_at=at)
