@@ -320,6 +320,17 @@ mpm_status decoder_eval(const mpm_decoder* dec, const float* X, const int32_t* l
 /* Synchronises `stream`; OR of MPM_STATUS_* bits raised by decoder kernels. */
 mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void* stream);
 
+/*
+ * Arithmetic of the square hidden layers in decoder_eval and in the reduced
+ * step's decoder calls (training always uses the tensor cores).  fp32 = 0
+ * (default): BF16 x BF16 -> FP32 tcgen05 GEMMs.  fp32 = 1: FP32 GEMMs on the
+ * CUDA cores from the FP32 master weights; for the reduced step's small calls,
+ * whose time is set by per-tile latency rather than throughput, this costs
+ * little and removes the BF16 rounding of positions and gradients.  Takes
+ * effect for reduced-order contexts created afterwards.  Errors: MPM_EINVAL.
+ */
+mpm_status decoder_set_precision(mpm_decoder* dec, int fp32);
+
 /* ======================================================================
  * Reduced-order step (Algorithm 2 with Lagrangian quadrature: Algorithms 3,
  * 5 and 6 or 7) and the accumulated position error (Section 5)

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("decoder_eval", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.POINTER(C.c_int32), C.c_int, C.c_int64, C.c_void_p, C.c_void_p]),
     ("decoder_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
+    ("decoder_set_precision", C.c_int, [C.c_void_p, C.c_int]),
     ("rom_create", C.c_int, [C.POINTER(RomConfig), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
     ("rom_destroy", None, [C.c_void_p]),
     ("rom_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),

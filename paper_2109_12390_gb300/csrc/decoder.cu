@@ -323,6 +323,157 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
   if (warp == 0) tc::tmem_free<kW>(tmem);
 }
 
+// --------------------------------------------------------------------------
+// FP32 decoder on the CUDA cores, for calls whose rows are too few to keep the
+// tensor cores busy and whose results need FP32 accuracy (the reduced step's
+// positions and gradients).  Same 128-row tiles and row kinds as decoder_tc;
+// each square layer is a 128 x 128 x 128 FP32 GEMM from shared memory (thread
+// (ty, tx) computes rows 8 ty .. 8 ty + 7 x features 8 tx .. 8 tx + 7), the
+// layer's weights streamed into shared memory transposed.  Pre-activations are
+// exchanged through shared memory for the derivative rows exactly as in the
+// tensor-core kernel, all in FP32.
+// --------------------------------------------------------------------------
+constexpr int kF32Threads = 256;
+constexpr int kZStride = kW + 1;
+
+__global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
+  extern __shared__ __align__(16) float fsm[];
+  float* AT = fsm;                        // [128 k][128 rows] activations, transposed
+  float* Wt = AT + kW * 128;              // [128 in][128 out] current square layer, transposed
+  float* Z = Wt + kW * kW;                // [128 rows][kZStride] pre-activations of the layer
+  float* sW0 = Z + 128 * kZStride;        // [128][kW0Stride]
+  float* sb0 = sW0 + kW * kW0Stride;      // [128]
+  float* sbh = sb0 + kW;                  // [kMaxTC][128]
+  float* sWout = sbh + kMaxTC * kW;       // [3][128]
+  const int t = threadIdx.x;
+  const int K0 = a.d + a.r;
+  for (int e = t; e < kW * kW0Stride; e += kF32Threads) {
+    const int c = e / kW0Stride, i = e % kW0Stride;
+    sW0[e] = i < K0 ? a.W0[c * K0 + i] : 0.f;
+  }
+  for (int e = t; e < kW; e += kF32Threads) sb0[e] = a.b0[e];
+  for (int e = t; e < a.n_tc * kW; e += kF32Threads) sbh[e] = a.bh[e];
+  for (int e = t; e < a.d * kW; e += kF32Threads) sWout[e] = a.Wout[e];
+  __syncthreads();
+
+  const int64_t n_pts = dec_count(a);
+  const int64_t n_tiles = (n_pts + a.Pt - 1) / a.Pt;
+  const int rw = t & 127, h = t >> 7;     // layer 0: row and column half
+  const int ty = t >> 4, tx = t & 15;     // square layers: 8 x 8 output block
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t first = tile * a.Pt;
+    // ---- layer 0 (FP32), this thread's row and 64 columns
+    {
+      const RowInfo ri = row_info(a, rw, first, n_pts);
+      float in[40], dir[40];
+      if (ri.cls >= 0) row_inputs(a, ri, in, dir);
+      for (int c = 64 * h; c < 64 * h + 64; ++c) {
+        float hv = 0.f;
+        if (ri.cls >= 0) {
+          const float* w0r = sW0 + c * kW0Stride;
+          float z = sb0[c], zd = 0.f;
+#pragma unroll
+          for (int i4 = 0; i4 < kW0Stride / 4; ++i4) {
+            if (4 * i4 < K0) {
+              const float4 w = *reinterpret_cast<const float4*>(w0r + 4 * i4);
+              z = fmaf(w.x, in[4 * i4 + 0], z);
+              z = fmaf(w.y, in[4 * i4 + 1], z);
+              z = fmaf(w.z, in[4 * i4 + 2], z);
+              z = fmaf(w.w, in[4 * i4 + 3], z);
+              zd = fmaf(w.x, dir[4 * i4 + 0], zd);
+              zd = fmaf(w.y, dir[4 * i4 + 1], zd);
+              zd = fmaf(w.z, dir[4 * i4 + 2], zd);
+              zd = fmaf(w.w, dir[4 * i4 + 3], zd);
+            }
+          }
+          if (ri.cls == 0) hv = act_f(a.act, z);
+          else if (ri.cls == 1) hv = act_d1(a.act, z) * zd;
+          else if (ri.cls == 2) hv = act_sec(a.act, z, zd);
+          else hv = act_d2(a.act, z) * zd * mixed_t0(a, w0r, ri.kind);
+        }
+        AT[c * 128 + rw] = hv;
+      }
+    }
+    // row bookkeeping of this thread's 8 GEMM rows
+    RowInfo rows[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) rows[j] = row_info(a, 8 * ty + j, first, n_pts);
+    for (int l = 0; l < a.n_tc; ++l) {
+      // this layer's weights, transposed: Wt[k][f] = W_l[f][k]
+      const float* Wl = a.wsq + (size_t)l * kW * kW;
+      for (int e = t; e < kW * kW; e += kF32Threads) {
+        const int f = e / kW, k = e % kW;
+        Wt[k * kW + f] = Wl[e];
+      }
+      __syncthreads();
+      float acc[8][8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[j][i] = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < kW; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(AT + k * 128 + 8 * ty);
+        const float4 a1 = *reinterpret_cast<const float4*>(AT + k * 128 + 8 * ty + 4);
+        const float4 w0 = *reinterpret_cast<const float4*>(Wt + k * kW + 8 * tx);
+        const float4 w1 = *reinterpret_cast<const float4*>(Wt + k * kW + 8 * tx + 4);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[j][i] = fmaf(av[j], wv[i], acc[j][i]);
+      }
+      // pre-activations (with the bias on primal rows) for the exchange
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          Z[(8 * ty + j) * kZStride + 8 * tx + i] =
+              acc[j][i] + (rows[j].cls == 0 ? sbh[l * kW + 8 * tx + i] : 0.f);
+      __syncthreads();
+      // activations of the next layer (transposed), from the row's own and exchanged pre-activations
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const RowInfo& ri = rows[j];
+        const int row = 8 * ty + j;
+        const float* zq = Z + ri.q * kZStride;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int f = 8 * tx + i;
+          const float zo = Z[row * kZStride + f];
+          float hv;
+          if (ri.cls == 0) hv = act_f(a.act, zo);
+          else if (ri.cls == 1) hv = act_d1(a.act, zq[f]) * zo;
+          else if (ri.cls == 2) hv = act_sec(a.act, zq[f], zo);
+          else if (ri.cls == 3)
+            hv = act_d2(a.act, zq[f]) * Z[(ri.ja * a.Pt + ri.q) * kZStride + f] *
+                     Z[(ri.jb * a.Pt + ri.q) * kZStride + f] +
+                 act_d1(a.act, zq[f]) * zo;
+          else hv = 0.f;
+          AT[f * 128 + row] = hv;
+        }
+      }
+      __syncthreads();
+    }
+    // ---- output layer (FP32): thread t < 128 owns row t
+    if (t < 128) {
+      const RowInfo ri = row_info(a, t, first, n_pts);
+      if (ri.cls >= 0) {
+        const int kidx = t / a.Pt;
+        float* o = a.out + ((int64_t)kidx * a.n + ri.p) * a.d;
+        for (int i = 0; i < a.d; ++i) {
+          float y = 0.f;
+          for (int k = 0; k < kW; ++k) y = fmaf(sWout[i * kW + k], AT[k * 128 + t], y);
+          y += (ri.cls == 0 ? a.bout[i] : 0.f);
+          o[i] = y * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Packs the square-layer weights (FP32, (out, in) row-major) into BF16 images
 // in the 128-byte swizzled K-major layout the MMA reads.
 __global__ void decoder_pack(const float* W, int n_layers, int64_t stride, uint8_t* img) {
@@ -348,6 +499,10 @@ size_t dec_smem_bytes() {
   return 1024 + kMaxTC * kLayerBytes + kLayerBytes +
          (2 * 128 * kXbStride + 128 * 3 + kW * kW0Stride + kW + kMaxTC * kW + 3 * kW) * sizeof(float) +
          sizeof(DecSmemTail);
+}
+
+size_t dec_f32_smem_bytes() {
+  return (size_t)(kW * 128 + kW * kW + 128 * kZStride + kW * kW0Stride + kW + kMaxTC * kW + 3 * kW) * sizeof(float);
 }
 
 mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {
@@ -419,6 +574,8 @@ mpm_status decoder_create(const decoder_desc* desc, mpm_decoder** out) {
   if (e == cudaSuccess) e = cudaMemset(dec->params, 0, sizeof(float) * dec->n_params);
   if (e == cudaSuccess) e = cudaMemset(dec->status, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(decoder_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec->smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(decoder_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec_f32_smem_bytes());
   if (e != cudaSuccess) {
     decoder_destroy(dec);
     return set_error(MPM_ENOMEM, std::string("decoder_create: ") + cudaGetErrorString(e));
@@ -439,6 +596,13 @@ void decoder_destroy(mpm_decoder* dec) {
 }
 
 int64_t decoder_num_params(const mpm_decoder* dec) { return dec ? dec->n_params : 0; }
+
+mpm_status decoder_set_precision(mpm_decoder* dec, int fp32) {
+  MPM_CHECK_ARG(dec, "null decoder");
+  MPM_CHECK_ARG(fp32 == 0 || fp32 == 1, "fp32: 0 or 1");
+  dec->fp32 = fp32;
+  return MPM_OK;
+}
 
 mpm_status decoder_set_params(mpm_decoder* dec, const float* params, const float* norm, void* stream) {
   MPM_CHECK_ARG(dec && params && norm, "null argument");
@@ -490,6 +654,7 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   a.bout = dec->params + dec->b_off[L - 1];
   a.norm = dec->norm;
   a.wimg = dec->wimg;
+  a.wsq = dec->wsq;
   a.X = X;
   a.lat = lat_idx;
   a.latents = latents;
@@ -538,6 +703,10 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
     int64_t rows = n * R;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, dec->n_sm * 8));
     decoder_simt<<<blocks, 128, 0, s>>>(a);
+  } else if (dec->fp32 && !a.zstore) {
+    const int64_t tiles = (n + a.Pt - 1) / a.Pt;
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));
+    decoder_f32<<<blocks, kF32Threads, dec_f32_smem_bytes(), s>>>(a);
   } else {
     const int64_t tiles = (n + a.Pt - 1) / a.Pt;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));

@@ -26,6 +26,7 @@ struct DecArgs {
   const float* bout;  // (d)
   const float* norm;  // X_min[d], X_range[d], out_shift[d], out_scale[d]
   const uint8_t* wimg;
+  const float* wsq;   // (n_tc, W, W) FP32 square-layer weights, (out, in) row-major
   const float* X;
   const int32_t* lat;
   const float* latents;
@@ -193,6 +194,7 @@ struct mpm_decoder {
   uint32_t* status = nullptr;
   int n_sm = 0;
   size_t smem = 0;
+  int fp32 = 0;                       // evaluate square layers in FP32 on the CUDA cores
 };
 
 namespace mpmrom {

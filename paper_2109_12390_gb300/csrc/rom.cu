@@ -552,50 +552,71 @@ struct RomSolve {
 
 enum { NE_VEL = 0, NE_GN = 1, NE_FIT = 2 };
 
-// Parallel Cholesky solve of the SPD system A x = b held in shared memory
-// (A: r x r, row-major).  Returns false if a pivot is not positive.  One FP64
-// square root and one reciprocal per column; the substitutions multiply by the
-// stored reciprocal pivots (FP64 division and square root are long-latency
-// sequences on this GPU).
+// Cholesky solve of the SPD system A x = b held in shared memory (A: r x r,
+// row-major, r <= 32) by the block's first warp, synchronised with __syncwarp
+// only; the other warps wait at the final barrier.  One FP64 square root and one
+// reciprocal per column (computed by lane 0 and broadcast); the substitutions
+// multiply by the stored reciprocal pivots (FP64 division and square root are
+// long-latency sequences on this GPU).  Returns false, for the whole block, if a
+// pivot is not positive.
 __device__ bool chol_solve(double* A, double* b, int r) {
   __shared__ int s_bad;
   __shared__ double s_rdiag[kMaxRl];
-  if (threadIdx.x == 0) s_bad = 0;
-  __syncthreads();
-  for (int j = 0; j < r; ++j) {
-    if (threadIdx.x == 0) {
-      double piv = A[j * r + j];
-      if (!(piv > 0.0)) s_bad = 1;
-      const double l = sqrt(fmax(piv, 1e-300));
-      A[j * r + j] = l;
-      s_rdiag[j] = 1.0 / l;
+  if (threadIdx.x < 32) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;
+    int bad = 0;
+    for (int j = 0; j < r; ++j) {
+      const double piv = A[j * r + j];
+      if (!(piv > 0.0)) {
+        bad = 1;
+        break;
+      }
+      double l = 0.0, rl = 0.0;
+      if (lane == 0) {
+        l = sqrt(piv);
+        rl = 1.0 / l;
+      }
+      l = __shfl_sync(full, l, 0);
+      rl = __shfl_sync(full, rl, 0);
+      __syncwarp();
+      if (lane == 0) {
+        A[j * r + j] = l;
+        s_rdiag[j] = rl;
+      }
+      for (int i = j + 1 + lane; i < r; i += 32) A[i * r + j] *= rl;
+      __syncwarp();
+      const int m = r - j - 1;
+      for (int e = lane; e < m * m; e += 32) {
+        const int i = j + 1 + e / m, c = j + 1 + e % m;
+        if (c <= i) A[i * r + c] -= A[i * r + j] * A[c * r + j];
+      }
+      __syncwarp();
     }
-    __syncthreads();
-    if (s_bad) return false;
-    const double rl = s_rdiag[j];
-    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * r + j] *= rl;
-    __syncthreads();
-    for (int e = threadIdx.x; e < (r - j - 1) * (r - j - 1); e += blockDim.x) {
-      const int i = j + 1 + e / (r - j - 1), c = j + 1 + e % (r - j - 1);
-      if (c <= i) A[i * r + c] -= A[i * r + j] * A[c * r + j];
+    if (!bad) {
+      // L y = b
+      for (int i = 0; i < r; ++i) {
+        double yi = 0.0;
+        if (lane == 0) yi = b[i] * s_rdiag[i];
+        yi = __shfl_sync(full, yi, 0);
+        if (lane == 0) b[i] = yi;
+        for (int k = i + 1 + lane; k < r; k += 32) b[k] -= A[k * r + i] * yi;
+        __syncwarp();
+      }
+      // L^T x = y
+      for (int i = r - 1; i >= 0; --i) {
+        double xi = 0.0;
+        if (lane == 0) xi = b[i] * s_rdiag[i];
+        xi = __shfl_sync(full, xi, 0);
+        if (lane == 0) b[i] = xi;
+        for (int k = lane; k < i; k += 32) b[k] -= A[i * r + k] * xi;
+        __syncwarp();
+      }
     }
-    __syncthreads();
+    if (lane == 0) s_bad = bad;
   }
-  // forward / backward substitution (single thread; r <= 64)
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < r; ++i) {
-      double sacc = b[i];
-      for (int c = 0; c < i; ++c) sacc -= A[i * r + c] * b[c];
-      b[i] = sacc * s_rdiag[i];
-    }
-    for (int i = r - 1; i >= 0; --i) {
-      double sacc = b[i];
-      for (int c = i + 1; c < r; ++c) sacc -= A[c * r + i] * b[c];
-      b[i] = sacc * s_rdiag[i];
-    }
-  }
   __syncthreads();
-  return true;
+  return !s_bad;
 }
 
 __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, const float* __restrict__ dec,

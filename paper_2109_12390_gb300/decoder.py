@@ -80,6 +80,11 @@ class Decoder:
                                            len(kinds), n, _ptr(out), _stream(stream)))
         return out
 
+    def set_precision(self, fp32):
+        """fp32=True: square layers in FP32 on the CUDA cores (decoder_eval and reduced-order
+        contexts created afterwards); False: BF16 tensor cores."""
+        _abi.check(_abi.lib().decoder_set_precision(self._h, int(bool(fp32))))
+
     def status(self, clear=True, stream=None):
         w = C.c_uint32()
         _abi.check(_abi.lib().decoder_status_word(self._h, C.byref(w), int(clear), _stream(stream)))

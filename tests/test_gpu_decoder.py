@@ -134,6 +134,40 @@ def test_mixed_rows_of_affine_network_vanish_and_need_partners():
         dec.eval(Xg, latg, [PRIMAL, dX(0), mixed(dX(0))], dirs=ug)  # no JVP row
 
 
+@pytest.mark.parametrize("d,r,n", [(2, 16, 1000), (3, 8, 333)])
+def test_fp32_cuda_core_path_deep_decoder(d, r, n):
+    """decoder_set_precision(fp32): the 5-hidden-layer decoder evaluated in FP32 on the CUDA cores
+    matches the FP64 oracle to FP32 accuracy for every row kind (primal, tangents, JVP, secant,
+    mixed), and the BF16 tensor-core path stays available on the same object."""
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL, JVP, SECANT, dX, mixed
+    p = _dec_params(d, r, seed=31)
+    dec = Decoder.from_params(p)
+    X, lat, idx = _points(n, d, r, n_lat=3, seed=32)
+    u = 0.3 * np.random.default_rng(33).normal(size=lat.shape)
+    Xg, latg, idxg, ug = _gpu(X.astype(np.float32), lat.astype(np.float32), idx, u.astype(np.float32))
+    Xr = X.astype(np.float32).astype(np.float64)
+    xh = lat.astype(np.float32).astype(np.float64)[idx]
+    uu = u.astype(np.float32).astype(np.float64)[idx]
+    g, JX, Jq = OD.jacobians(p, Xr, xh)
+    v, G = OD.velocity_gradient(p, Xr, xh, uu)
+    dec.set_precision(True)
+    kinds = [PRIMAL] + [dX(k) for k in range(d)] + [JVP] + [mixed(dX(k)) for k in range(d)]
+    out = dec.eval(Xg, latg, kinds, lat_idx=idxg, dirs=ug).cpu().numpy()
+    assert dec.status() == 0
+    assert rel(out[0] - 0.5, g - 0.5) < 1e-5
+    assert rel(np.stack(out[1:1 + d], -1), JX) < 1e-5
+    assert rel(out[1 + d], v) < 1e-5
+    assert rel(np.stack(out[2 + d:], -1), G) < 1e-4
+    out2 = dec.eval(Xg, latg, [PRIMAL] + [dec.dxhat(j) for j in range(r)], lat_idx=idxg).cpu().numpy()
+    assert rel(np.stack(out2[1:], -1), Jq) < 1e-5
+    sec = dec.eval(Xg, latg, [PRIMAL, SECANT], lat_idx=idxg, dirs=ug).cpu().numpy()[1]
+    ref = OD.decode(p, Xr, xh + uu) - OD.decode(p, Xr, xh)
+    assert rel(sec, ref) < 1e-5
+    dec.set_precision(False)
+    out3 = dec.eval(Xg, latg, [PRIMAL], lat_idx=idxg).cpu().numpy()
+    assert 1e-6 < rel(out3[0] - 0.5, g - 0.5) < TOL_BF16
+
+
 def test_linear_and_single_hidden_layer_fp32():
     from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
     for n_hidden, act in [(0, OD.IDENTITY), (1, OD.ELU)]:

@@ -194,6 +194,32 @@ def test_one_step_reference_gradient(n_hidden, tol):
     assert rel(v_plain, v_trial) > 10 * min(tol, 1e-3)
 
 
+@pytest.mark.parametrize("projection", [0, 1])
+def test_one_step_fp32_deep_decoder(projection):
+    """The 5-hidden-layer decoder on the FP32 CUDA-core path: the reduced step (Algorithms 2, 3,
+    5 and 6 or 7) against the FP64 oracle end to end at FP32 tolerances."""
+    from paper_2109_12390_gb300.rom import ROM
+    sc, p, dec, rom, rs, xh, vh, xp = _elu_setup(seed=8, r=4, n_hidden=5, projection=projection)
+    rom.close()
+    dec.set_precision(True)
+    rom = ROM.from_scene(dec, sc, n_samples=64, seed=8, projection=projection)
+    rom.set_state(xh, vh, xp, 0)
+    rom.step(1)
+    assert rom.status() & ~ALLOWED_RANDOM == 0
+    dbg = rom.debug()
+    xa = dbg["x_all"].astype(np.float64)
+    assert rel(xa - p.out_shift, OD.decode(p, sc.x, xh) - p.out_shift) < 1e-5
+    basis, neigh = OR.neighbourhood(xa, dbg["samples"], sc.dx, sc.n_grid)
+    np.testing.assert_array_equal(dbg["neigh"], neigh)
+    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
+    assert rel(dbg["v_trial"], v_trial) < 1e-4
+    Xs = sc.x[dbg["samples"]]
+    vt = dbg["v_trial"].astype(np.float64)
+    vh_ref = OR.project_velocity(p, Xs, xh, vt)
+    xh1, vh1, _, _ = rom.get_state()
+    assert rel(vh1, vh_ref) < 1e-3
+
+
 def test_fit_initial_condition():
     """Eq. essentialSpecInt least-squares fit of xhat_0, vhat_0 over all particles."""
     from paper_2109_12390_gb300.rom import ROM
