@@ -177,7 +177,8 @@ ROM_CHECKPOINT = 2000
 ROM_TRAIN_STEPS = 12000
 ROM_TRAIN_INSTANCES = 32
 ROM_TESTS = 4
-ROM_SETTINGS = dict(n_samples=256, gn_iters=3, projection=0, ridge=1e-1, affine=0, f_reference=0)
+ROM_SETTINGS = dict(n_samples=256, gn_iters=3, projection=0, ridge=1e-1, affine=0, f_reference=1)
+ROM_DECODER_FP32 = True     # reduced-step decoder calls in FP32 on the CUDA cores (training stays BF16)
 
 
 def _rom_tests(steps, n_tests=ROM_TESTS):
@@ -191,6 +192,53 @@ def _rom_tests(steps, n_tests=ROM_TESTS):
         fx, rate, status = PL.fom_positions(sc, steps)
         tests.append(dict(scene=sc, fom=fx, fom_rate=rate, fom_status=status, E=E, v0=v0.tolist()))
     return tests
+
+
+def cpu_baseline_rom(dec, sc, r, max_seconds=20.0):
+    """The FP64 oracle's reduced step (Algorithms 2, 3, 5, 6), as it stands, with the trained
+    decoder's parameters, on the first held-out scene: whole steps until ~max_seconds, one thread."""
+    import torch
+    import oracle.decoder as OD
+    import oracle.rom as OR
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter = threadpool_limits(1)
+    except Exception:  # pragma: no cover
+        limiter = None
+    p = S.xavier_decoder(0, sc.dim, r, 128, 5, OD.ELU)
+    params = torch.empty(dec.n_params, dtype=torch.float32, device="cuda")
+    norm = torch.empty(4 * sc.dim, dtype=torch.float32, device="cuda")
+    dec.get_params(params, norm)
+    torch.cuda.synchronize()
+    flat = params.cpu().numpy().astype(np.float64)
+    off = 0
+    for l in range(len(p.W)):
+        n = p.W[l].size
+        p.W[l] = flat[off:off + n].reshape(p.W[l].shape)
+        off += n
+        n = p.b[l].size
+        p.b[l] = flat[off:off + n]
+        off += n
+    nm = norm.cpu().numpy().astype(np.float64)
+    d = sc.dim
+    p.X_min, p.X_range, p.out_shift, p.out_scale = nm[:d], nm[d:2 * d], nm[2 * d:3 * d], nm[3 * d:]
+    rs = OR.RomScene(X=sc.x.copy(), mass=sc.p_mass, vol=sc.p_vol, E=float(sc.E[0]), nu=float(sc.nu[0]), dx=sc.dx,
+                     dt=sc.dt, n_grid=sc.n_grid, gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width,
+                     material=sc.material, transfer=sc.transfer, n_samples=ROM_SETTINGS["n_samples"], seed=4,
+                     gn_iters=ROM_SETTINGS["gn_iters"], ridge=ROM_SETTINGS["ridge"])
+    st = OR.RomState(xhat=np.zeros(r), vhat=np.zeros(r), xhat_prev=np.zeros(r))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        st = OR.rom_step(p, rs, st)
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds or steps >= 5:
+            break
+    dt = time.perf_counter() - t0
+    if limiter is not None and hasattr(limiter, "unregister"):
+        limiter.unregister()
+    return {"value": steps / dt, "unit": "ROM steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle reduced step(s) of the first held-out scene, single thread"}
 
 
 def rom_leg(r=16, train_steps=None, steps=None):
@@ -214,6 +262,7 @@ def rom_leg(r=16, train_steps=None, steps=None):
     tr, hist, t_train = PL.train(snaps, dec, steps=train_steps)
     loss = hist[-1][1]
     tr.close()
+    dec.set_precision(ROM_DECODER_FP32)
     tests = _rom_tests(steps)
     per_test = []
     for t in tests:
@@ -230,19 +279,23 @@ def rom_leg(r=16, train_steps=None, steps=None):
     t0s = tests[0]
     fx_ck = t0s["fom"][:ck + 1]
     untrained, _ = PL.decoder_for_snapshots(snaps, r, seed=0)
+    untrained.set_precision(ROM_DECODER_FP32)
     e_untrained = PL.rom_error(untrained, t0s["scene"], fx_ck, seed=4, **ROM_SETTINGS).error_percent / 100.0
     lin, _ = PL.decoder_for_snapshots(snaps, r, seed=0, activation=1)
     trl, histl, t_lin = PL.train(snaps, lin, steps=max(1, train_steps // 4))
     trl.close()
+    lin.set_precision(ROM_DECODER_FP32)
     e_linear = PL.rom_error(lin, t0s["scene"], fx_ck, seed=4, **ROM_SETTINGS).error_percent / 100.0
+    cpu = cpu_baseline_rom(dec, tests[0]["scene"], r)
     return {
+        "cpu_baseline": cpu,
         "scene": "2D neo-Hookean block 64x64 (4096 particles), 128^2 grid, nu=0.3, dt=5e-5, sticky walls, floor "
                  f"impact; decoder 2+{r}->128x5->2 ELU trained on {ROM_TRAIN_INSTANCES} trajectories, "
                  f"(E, v0) ~ U[5e3,1.5e4] x U[-0.5,0.5]^2; {len(tests)} held-out test draws",
         "rom_steps_per_s": rom_rate, "fom_steps_per_s": fom_rate, "speedup": rom_rate / fom_rate,
         "rel_position_error": err_ck, "error_steps": ck, "rel_position_error_full": err_full, "full_steps": steps,
         "meets_1e-2": bool(err_ck <= 1e-2), "per_test": per_test,
-        "settings": dict(ROM_SETTINGS, latent_dim=r),
+        "settings": dict(ROM_SETTINGS, latent_dim=r, decoder="FP32 CUDA cores" if ROM_DECODER_FP32 else "BF16 tcgen05"),
         "gain": {"trained": per_test[0]["rel_error_at_checkpoint"], "untrained_xavier": e_untrained,
                  "trained_linear_manifold": e_linear, "linear_training_steps": max(1, train_steps // 4),
                  "steps": ck},

@@ -335,11 +335,12 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 // --------------------------------------------------------------------------
 constexpr int kF32Threads = 256;
 constexpr int kZStride = kW + 1;
+constexpr int kATStride = 132;            // AT row stride: float4-aligned, 2-way conflicts on transposed stores
 
 __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   extern __shared__ __align__(16) float fsm[];
-  float* AT = fsm;                        // [128 k][128 rows] activations, transposed
-  float* Wt = AT + kW * 128;              // [128 in][128 out] current square layer, transposed
+  float* AT = fsm;                        // [128 k][kATStride] activations, transposed
+  float* Wt = AT + kW * kATStride;        // [128 in][128 out] current square layer, transposed
   float* Z = Wt + kW * kW;                // [128 rows][kZStride] pre-activations of the layer
   float* sW0 = Z + 128 * kZStride;        // [128][kW0Stride]
   float* sb0 = sW0 + kW * kW0Stride;      // [128]
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   const int64_t n_pts = dec_count(a);
   const int64_t n_tiles = (n_pts + a.Pt - 1) / a.Pt;
   const int rw = t & 127, h = t >> 7;     // layer 0: row and column half
-  const int ty = t >> 4, tx = t & 15;     // square layers: 8 x 8 output block
+  const int ty = t >> 4, tx = t & 15;     // square layers: rows 8 ty .. 8 ty + 7, features tx + 16 i
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t first = tile * a.Pt;
     // ---- layer 0 (FP32), this thread's row and 64 columns
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
           else if (ri.cls == 2) hv = act_sec(a.act, z, zd);
           else hv = act_d2(a.act, z) * zd * mixed_t0(a, w0r, ri.kind);
         }
-        AT[c * 128 + rw] = hv;
+        AT[c * kATStride + rw] = hv;
       }
     }
     // row bookkeeping of this thread's 8 GEMM rows
@@ -399,11 +400,11 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) rows[j] = row_info(a, 8 * ty + j, first, n_pts);
     for (int l = 0; l < a.n_tc; ++l) {
-      // this layer's weights, transposed: Wt[k][f] = W_l[f][k]
-      const float* Wl = a.wsq + (size_t)l * kW * kW;
-      for (int e = t; e < kW * kW; e += kF32Threads) {
-        const int f = e / kW, k = e % kW;
-        Wt[k * kW + f] = Wl[e];
+      // this layer's weights, already transposed in global memory: Wt[k][f] = W_l[f][k]
+      {
+        const float4* src = reinterpret_cast<const float4*>(a.wsqT + (size_t)l * kW * kW);
+        float4* dst = reinterpret_cast<float4*>(Wt);
+        for (int e = t; e < kW * kW / 4; e += kF32Threads) dst[e] = src[e];
       }
       __syncthreads();
       float acc[8][8];
@@ -413,12 +414,12 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
         for (int i = 0; i < 8; ++i) acc[j][i] = 0.f;
 #pragma unroll 4
       for (int k = 0; k < kW; ++k) {
-        const float4 a0 = *reinterpret_cast<const float4*>(AT + k * 128 + 8 * ty);
-        const float4 a1 = *reinterpret_cast<const float4*>(AT + k * 128 + 8 * ty + 4);
-        const float4 w0 = *reinterpret_cast<const float4*>(Wt + k * kW + 8 * tx);
-        const float4 w1 = *reinterpret_cast<const float4*>(Wt + k * kW + 8 * tx + 4);
+        const float4 a0 = *reinterpret_cast<const float4*>(AT + k * kATStride + 8 * ty);
+        const float4 a1 = *reinterpret_cast<const float4*>(AT + k * kATStride + 8 * ty + 4);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        float wv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wv[i] = Wt[k * kW + tx + 16 * i];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
 #pragma unroll
@@ -429,30 +430,29 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
       for (int j = 0; j < 8; ++j)
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-          Z[(8 * ty + j) * kZStride + 8 * tx + i] =
-              acc[j][i] + (rows[j].cls == 0 ? sbh[l * kW + 8 * tx + i] : 0.f);
+          Z[(8 * ty + j) * kZStride + tx + 16 * i] = acc[j][i] + (rows[j].cls == 0 ? sbh[l * kW + tx + 16 * i] : 0.f);
       __syncthreads();
       // activations of the next layer (transposed), from the row's own and exchanged pre-activations
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const RowInfo& ri = rows[j];
-        const int row = 8 * ty + j;
-        const float* zq = Z + ri.q * kZStride;
+      for (int i = 0; i < 8; ++i) {
+        const int f = tx + 16 * i;
+        float hv[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int f = 8 * tx + i;
-          const float zo = Z[row * kZStride + f];
-          float hv;
-          if (ri.cls == 0) hv = act_f(a.act, zo);
-          else if (ri.cls == 1) hv = act_d1(a.act, zq[f]) * zo;
-          else if (ri.cls == 2) hv = act_sec(a.act, zq[f], zo);
+        for (int j = 0; j < 8; ++j) {
+          const RowInfo& ri = rows[j];
+          const float zo = Z[(8 * ty + j) * kZStride + f];
+          const float zq = Z[ri.q * kZStride + f];
+          if (ri.cls == 0) hv[j] = act_f(a.act, zo);
+          else if (ri.cls == 1) hv[j] = act_d1(a.act, zq) * zo;
+          else if (ri.cls == 2) hv[j] = act_sec(a.act, zq, zo);
           else if (ri.cls == 3)
-            hv = act_d2(a.act, zq[f]) * Z[(ri.ja * a.Pt + ri.q) * kZStride + f] *
-                     Z[(ri.jb * a.Pt + ri.q) * kZStride + f] +
-                 act_d1(a.act, zq[f]) * zo;
-          else hv = 0.f;
-          AT[f * 128 + row] = hv;
+            hv[j] = act_d2(a.act, zq) * Z[(ri.ja * a.Pt + ri.q) * kZStride + f] *
+                        Z[(ri.jb * a.Pt + ri.q) * kZStride + f] +
+                    act_d1(a.act, zq) * zo;
+          else hv[j] = 0.f;
         }
+        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty + 4) = make_float4(hv[4], hv[5], hv[6], hv[7]);
       }
       __syncthreads();
     }
@@ -464,13 +464,29 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
         float* o = a.out + ((int64_t)kidx * a.n + ri.p) * a.d;
         for (int i = 0; i < a.d; ++i) {
           float y = 0.f;
-          for (int k = 0; k < kW; ++k) y = fmaf(sWout[i * kW + k], AT[k * 128 + t], y);
+          for (int k = 0; k < kW; ++k) y = fmaf(sWout[i * kW + k], AT[k * kATStride + t], y);
           y += (ri.cls == 0 ? a.bout[i] : 0.f);
           o[i] = y * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
         }
       }
     }
     __syncthreads();
+  }
+}
+
+// Transposed FP32 copies of the square layers for the CUDA-core path:
+// WT[l][k][f] = W[l][f][k].
+__global__ void decoder_transpose(const float* W, int n_layers, float* WT) {
+  __shared__ float tileT[32][33];
+  for (int l = 0; l < n_layers; ++l) {
+    for (int b = blockIdx.x; b < 16; b += gridDim.x) {
+      const int f0 = (b / 4) * 32, k0 = (b % 4) * 32;
+      const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
+      for (int y = tyy; y < 32; y += blockDim.x / 32) tileT[y][tx] = W[(size_t)l * kW * kW + (f0 + y) * kW + k0 + tx];
+      __syncthreads();
+      for (int y = tyy; y < 32; y += blockDim.x / 32) WT[(size_t)l * kW * kW + (k0 + y) * kW + f0 + tx] = tileT[tx][y];
+      __syncthreads();
+    }
   }
 }
 
@@ -502,7 +518,8 @@ size_t dec_smem_bytes() {
 }
 
 size_t dec_f32_smem_bytes() {
-  return (size_t)(kW * 128 + kW * kW + 128 * kZStride + kW * kW0Stride + kW + kMaxTC * kW + 3 * kW) * sizeof(float);
+  return (size_t)(kW * kATStride + kW * kW + 128 * kZStride + kW * kW0Stride + kW + kMaxTC * kW + 3 * kW) *
+         sizeof(float);
 }
 
 mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {
@@ -515,6 +532,8 @@ mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {
   }
   decoder_pack<<<std::max(1, std::min(dec->n_sm * 4, dec->n_tc * 64)), 256, 0, s>>>(dec->wsq, dec->n_tc,
                                                                                     (int64_t)kW * kW, dec->wimg);
+  MPM_CUDA_TRY(cudaGetLastError());
+  decoder_transpose<<<16, 256, 0, s>>>(dec->wsq, dec->n_tc, dec->wsqT);
   MPM_CUDA_TRY(cudaGetLastError());
   return MPM_OK;
 }
@@ -570,6 +589,7 @@ mpm_status decoder_create(const decoder_desc* desc, mpm_decoder** out) {
     e = cudaMalloc((void**)&dec->wsq, sizeof(float) * dec->n_tc * kW * kW);
     if (e == cudaSuccess) e = cudaMalloc((void**)&dec->bsq, sizeof(float) * dec->n_tc * kW);
     if (e == cudaSuccess) e = cudaMalloc((void**)&dec->wimg, (size_t)dec->n_tc * kLayerBytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dec->wsqT, sizeof(float) * dec->n_tc * kW * kW);
   }
   if (e == cudaSuccess) e = cudaMemset(dec->params, 0, sizeof(float) * dec->n_params);
   if (e == cudaSuccess) e = cudaMemset(dec->status, 0, sizeof(uint32_t));
@@ -591,6 +611,7 @@ void decoder_destroy(mpm_decoder* dec) {
   cudaFree(dec->wsq);
   cudaFree(dec->bsq);
   cudaFree(dec->wimg);
+  cudaFree(dec->wsqT);
   cudaFree(dec->status);
   delete dec;
 }
@@ -655,6 +676,7 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   a.norm = dec->norm;
   a.wimg = dec->wimg;
   a.wsq = dec->wsq;
+  a.wsqT = dec->wsqT;
   a.X = X;
   a.lat = lat_idx;
   a.latents = latents;

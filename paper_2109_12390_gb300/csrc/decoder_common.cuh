@@ -27,6 +27,7 @@ struct DecArgs {
   const float* norm;  // X_min[d], X_range[d], out_shift[d], out_scale[d]
   const uint8_t* wimg;
   const float* wsq;   // (n_tc, W, W) FP32 square-layer weights, (out, in) row-major
+  const float* wsqT;  // (n_tc, W, W) the same transposed, (in, out) row-major
   const float* X;
   const int32_t* lat;
   const float* latents;
@@ -190,6 +191,7 @@ struct mpm_decoder {
   float* norm = nullptr;
   float* wsq = nullptr;               // square-layer weights gathered contiguously (n_tc, W, W)
   float* bsq = nullptr;               // their biases (n_tc, W)
+  float* wsqT = nullptr;              // transposed FP32 copies (n_tc, W, W) for the CUDA-core path
   uint8_t* wimg = nullptr;            // BF16 swizzled images
   uint32_t* status = nullptr;
   int n_sm = 0;

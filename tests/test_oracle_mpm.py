@@ -228,3 +228,42 @@ def test_walls():
     assert np.abs(v2[:3]).max() == 0 and np.abs(v2[-3:]).max() == 0
     assert np.abs(v2[:, :3]).max() == 0 and np.abs(v2[:, -3:]).max() == 0
     np.testing.assert_array_equal(v2[3:-3, 3:-3], np.broadcast_to([0.5, -2.0], (n - 6, n - 6, 2)))
+
+
+def _momenta(s, d):
+    """Total linear momentum and APIC angular momentum sum_p m (x_p x v_p + (dx^2/4) eps:C_p)."""
+    p = (s.p_mass * s.v).sum(0)
+    x, v, C = s.x, s.v, s.C
+    if d == 2:
+        L = s.p_mass * ((x[:, 0] * v[:, 1] - x[:, 1] * v[:, 0]).sum() + s.dx ** 2 / 4 * (C[:, 1, 0] - C[:, 0, 1]).sum())
+        return p, np.atleast_1d(L)
+    L = s.p_mass * (np.cross(x, v).sum(0) + s.dx ** 2 / 4 * np.stack(
+        [C[:, 2, 1] - C[:, 1, 2], C[:, 0, 2] - C[:, 2, 0], C[:, 1, 0] - C[:, 0, 1]], 1).sum(0))
+    return p, L
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_free_stressed_steps_conserve_momenta(d):
+    """No gravity, no wall contact, random velocities and deformation: 20 full MLS steps keep the
+    total linear momentum and the APIC angular momentum to round-off (symmetric Kirchhoff stress,
+    mass-weighted affine transfer); PIC keeps the linear momentum but not the angular one."""
+    for transfer in (M.MLS, M.PIC):
+        if d == 2:
+            sc = S.block_2d(side=16, dt=5e-5, origin=(0.45, 0.45), E=5e3)
+        else:
+            sc = S.cube_3d(side=8, n_grid=64, dt=5e-5, bottom=0.45)
+        rng = np.random.default_rng(1)
+        sc.transfer = transfer
+        sc.gravity = np.zeros(3)
+        sc.v = 0.3 * rng.normal(size=sc.v.shape)
+        sc.F = S.random_deformation(rng, sc.n_particles, d, 0.02)
+        sc.C[:] = 0.0
+        M.step(sc, 1)   # C becomes the grid-consistent affine velocity
+        p0, L0 = _momenta(sc, d)
+        M.step(sc, 20)
+        p1, L1 = _momenta(sc, d)
+        assert np.abs(p1 - p0).max() <= 1e-12 * np.abs(p0).max()
+        if transfer == M.MLS:
+            assert np.abs(L1 - L0).max() <= 1e-12 * np.abs(L0).max()
+        else:
+            assert np.abs(L1 - L0).max() > 1e-4 * np.abs(L0).max()
