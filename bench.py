@@ -370,11 +370,8 @@ def run_ours(args, ws, rank, local):
     status = ctx.status()
     step_ms = kern[:, 3]
     total_ms = float(np.sum(step_ms))
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2109_12390_gb300.dist import max_over_ranks
+    total_ms = max_over_ranks(total_ms, device=dev)
     fused_ms = float(kern[:, 0].mean())
     peak, peak_kind = _peaks()
     achieved = ALGO_BYTES_3D * P / (fused_ms * 1e-3) / 1e9
@@ -417,11 +414,7 @@ def run_ours(args, ws, rank, local):
         if i >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = float(np.sum(e2e_ms)) if e2e_ms else float("nan")
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, device=dev)
     bytes_io = 4 * P * (2 * d + 2 * d * d)
 
     if rank == 0:

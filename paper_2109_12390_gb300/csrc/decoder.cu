@@ -334,15 +334,27 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 // tensor-core kernel, all in FP32.
 // --------------------------------------------------------------------------
 constexpr int kF32Threads = 256;
-constexpr int kZStride = kW + 1;
 constexpr int kATStride = 132;            // AT row stride: float4-aligned, 2-way conflicts on transposed stores
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// ELU for the FP32 path: exp(z) - 1 with the fast exponential (absolute error at the FP32 ulp of
+// values near 1, far below the parity tolerance)
+__device__ __forceinline__ float act_f32path(int act, float z) {
+  return act == 0 ? (z > 0.f ? z : __expf(z) - 1.0f) : z;
+}
 
 __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   extern __shared__ __align__(16) float fsm[];
-  float* AT = fsm;                        // [128 k][kATStride] activations, transposed
-  float* Wt = AT + kW * kATStride;        // [128 in][128 out] current square layer, transposed
-  float* Z = Wt + kW * kW;                // [128 rows][kZStride] pre-activations of the layer
-  float* sW0 = Z + 128 * kZStride;        // [128][kW0Stride]
+  float* AT = fsm;                        // [128 k][kATStride] activations / pre-activations, transposed
+  float* Wt0 = AT + kW * kATStride;       // two [128 in][128 out] weight buffers, transposed
+  float* sW0 = Wt0 + 2 * kW * kW;         // [128][kW0Stride]
   float* sb0 = sW0 + kW * kW0Stride;      // [128]
   float* sbh = sb0 + kW;                  // [kMaxTC][128]
   float* sWout = sbh + kMaxTC * kW;       // [3][128]
@@ -355,6 +367,13 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   for (int e = t; e < kW; e += kF32Threads) sb0[e] = a.b0[e];
   for (int e = t; e < a.n_tc * kW; e += kF32Threads) sbh[e] = a.bh[e];
   for (int e = t; e < a.d * kW; e += kF32Threads) sWout[e] = a.Wout[e];
+  // weights of square layer l into buffer l % 2 (asynchronous copy, waited before its GEMM)
+  auto prefetch = [&](int l) {
+    const float* src = a.wsqT + (size_t)l * kW * kW;
+    float* dst = Wt0 + (l & 1) * kW * kW;
+    for (int e = t; e < kW * kW / 4; e += kF32Threads) cp_async16(dst + 4 * e, src + 4 * e);
+    cp_async_commit();
+  };
   __syncthreads();
 
   const int64_t n_pts = dec_count(a);
@@ -363,6 +382,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   const int ty = t >> 4, tx = t & 15;     // square layers: rows 8 ty .. 8 ty + 7, features tx + 16 i
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t first = tile * a.Pt;
+    if (a.n_tc > 0) prefetch(0);
     // ---- layer 0 (FP32), this thread's row and 64 columns
     {
       const RowInfo ri = row_info(a, rw, first, n_pts);
@@ -387,7 +407,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
               zd = fmaf(w.w, dir[4 * i4 + 3], zd);
             }
           }
-          if (ri.cls == 0) hv = act_f(a.act, z);
+          if (ri.cls == 0) hv = act_f32path(a.act, z);
           else if (ri.cls == 1) hv = act_d1(a.act, z) * zd;
           else if (ri.cls == 2) hv = act_sec(a.act, z, zd);
           else hv = act_d2(a.act, z) * zd * mixed_t0(a, w0r, ri.kind);
@@ -400,13 +420,10 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) rows[j] = row_info(a, 8 * ty + j, first, n_pts);
     for (int l = 0; l < a.n_tc; ++l) {
-      // this layer's weights, already transposed in global memory: Wt[k][f] = W_l[f][k]
-      {
-        const float4* src = reinterpret_cast<const float4*>(a.wsqT + (size_t)l * kW * kW);
-        float4* dst = reinterpret_cast<float4*>(Wt);
-        for (int e = t; e < kW * kW / 4; e += kF32Threads) dst[e] = src[e];
-      }
-      __syncthreads();
+      cp_async_wait_all();
+      __syncthreads();                                  // AT complete, weights of layer l landed
+      if (l + 1 < a.n_tc) prefetch(l + 1);              // overlaps the GEMM below
+      const float* Wt = Wt0 + (l & 1) * kW * kW;
       float acc[8][8];
 #pragma unroll
       for (int j = 0; j < 8; ++j)
@@ -425,37 +442,47 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) acc[j][i] = fmaf(av[j], wv[i], acc[j][i]);
       }
-      // pre-activations (with the bias on primal rows) for the exchange
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          Z[(8 * ty + j) * kZStride + tx + 16 * i] = acc[j][i] + (rows[j].cls == 0 ? sbh[l * kW + tx + 16 * i] : 0.f);
-      __syncthreads();
-      // activations of the next layer (transposed), from the row's own and exchanged pre-activations
+      __syncthreads();                                  // every GEMM has read AT
+      // pre-activations (bias on primal rows) replace the activations in AT
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int f = tx + 16 * i;
-        float hv[8];
+        float z[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) z[j] = acc[j][i] + (rows[j].cls == 0 ? sbh[l * kW + f] : 0.f);
+        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty) = make_float4(z[0], z[1], z[2], z[3]);
+        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty + 4) = make_float4(z[4], z[5], z[6], z[7]);
+      }
+      __syncthreads();
+      // activations of the next layer from the row's own and exchanged pre-activations (registers)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float* col = AT + (tx + 16 * i) * kATStride;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const RowInfo& ri = rows[j];
-          const float zo = Z[(8 * ty + j) * kZStride + f];
-          const float zq = Z[ri.q * kZStride + f];
-          if (ri.cls == 0) hv[j] = act_f(a.act, zo);
-          else if (ri.cls == 1) hv[j] = act_d1(a.act, zq) * zo;
-          else if (ri.cls == 2) hv[j] = act_sec(a.act, zq, zo);
+          const float zo = col[8 * ty + j];
+          const float zq = col[ri.q];
+          float hv;
+          if (ri.cls == 0) hv = act_f32path(a.act, zo);
+          else if (ri.cls == 1) hv = act_d1(a.act, zq) * zo;
+          else if (ri.cls == 2) hv = act_sec(a.act, zq, zo);
           else if (ri.cls == 3)
-            hv[j] = act_d2(a.act, zq) * Z[(ri.ja * a.Pt + ri.q) * kZStride + f] *
-                        Z[(ri.jb * a.Pt + ri.q) * kZStride + f] +
-                    act_d1(a.act, zq) * zo;
-          else hv[j] = 0.f;
+            hv = act_d2(a.act, zq) * col[ri.ja * a.Pt + ri.q] * col[ri.jb * a.Pt + ri.q] + act_d1(a.act, zq) * zo;
+          else hv = 0.f;
+          acc[j][i] = hv;
         }
-        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty + 4) = make_float4(hv[4], hv[5], hv[6], hv[7]);
       }
-      __syncthreads();
+      __syncthreads();                                  // every pre-activation read
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int f = tx + 16 * i;
+        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty) = make_float4(acc[0][i], acc[1][i], acc[2][i], acc[3][i]);
+        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty + 4) =
+            make_float4(acc[4][i], acc[5][i], acc[6][i], acc[7][i]);
+      }
     }
+    __syncthreads();
     // ---- output layer (FP32): thread t < 128 owns row t
     if (t < 128) {
       const RowInfo ri = row_info(a, t, first, n_pts);
@@ -472,6 +499,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
     }
     __syncthreads();
   }
+  cp_async_wait_all();
 }
 
 // Transposed FP32 copies of the square layers for the CUDA-core path:
@@ -518,8 +546,7 @@ size_t dec_smem_bytes() {
 }
 
 size_t dec_f32_smem_bytes() {
-  return (size_t)(kW * kATStride + kW * kW + 128 * kZStride + kW * kW0Stride + kW + kMaxTC * kW + 3 * kW) *
-         sizeof(float);
+  return (size_t)(kW * kATStride + 2 * kW * kW + kW * kW0Stride + kW + kMaxTC * kW + 3 * kW) * sizeof(float);
 }
 
 mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {

@@ -83,6 +83,7 @@ struct RomDev {
   int64_t* step;             // device step counter
   uint32_t* status;
   const float* Fref_inv;     // (P, d, d) inverse reference gradients, or null (f_reference = 0)
+  int q_by_pid;              // quadrature decoder rows indexed by particle id (one decode of all particles)
 };
 
 // Inverse of a small matrix by its adjugate (F of a quadrature point, det F > 0).
@@ -354,13 +355,14 @@ __global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t cap
   const uint32_t stamp = (uint32_t)(*R.step + 1);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nQ; i += gridDim.x * blockDim.x) {
     const int pid = R.qlist[i];
+    const int qi = R.q_by_pid ? pid : i;   // row of this point in dec_out
     float x[D], v[D], F[D * D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       x[a] = R.x_all[(size_t)pid * D + a];
-      v[a] = dec_out[((size_t)(1 + D) * capQ + i) * D + a];
+      v[a] = dec_out[((size_t)(1 + D) * capQ + qi) * D + a];
 #pragma unroll
-      for (int b = 0; b < D; ++b) F[a * D + b] = dec_out[((size_t)(1 + b) * capQ + i) * D + a];
+      for (int b = 0; b < D; ++b) F[a * D + b] = dec_out[((size_t)(1 + b) * capQ + qi) * D + a];
     }
     // deformation gradient for the stress: measured from the decoded reference
     // configuration (F G_p) when the f_reference option holds G_p
@@ -393,7 +395,7 @@ __global__ void rom_p2g(RomDev R, const float* __restrict__ dec_out, int64_t cap
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int b = 0; b < D; ++b) G[a * D + b] = dec_out[((size_t)(2 + D + b) * capQ + i) * D + a];
+        for (int b = 0; b < D; ++b) G[a * D + b] = dec_out[((size_t)(2 + D + b) * capQ + qi) * D + a];
       inverse<D>(F, Fi);
 #pragma unroll
       for (int a = 0; a < D; ++a)
@@ -913,7 +915,9 @@ struct rom_ctx {
   RomSolve sv{};
   // device buffers
   float* X = nullptr;
-  float* x_all = nullptr;
+  float* x_all = nullptr;       // decoded positions (the primal block of outQ when merged)
+  float* x_all_buf = nullptr;
+  bool merged = false;          // one decode of all particles serves positions and quadrature rows
   int32_t* qlist = nullptr;
   int32_t* counts = nullptr;
   int32_t* nodes = nullptr;
@@ -940,27 +944,37 @@ namespace {
 
 mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
   const int d = c->d, r = c->r;
-  // 1. decode all particles at xhat_n
-  int k_primal[1] = {0};
-  mpm_status st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, c->P, c->sv.xh32, nullptr, k_primal, 1,
-                                     c->x_all, s);
-  if (st != MPM_OK) return st;
-  // 2. samples, basis set, neighbours
-  if (d == 2)
-    rom_select<2><<<1, 1024, 0, s>>>(c->dv);
-  else
-    rom_select<3><<<1, 1024, 0, s>>>(c->dv);
-  MPM_CUDA_TRY(cudaGetLastError());
-  // 3. F and v at the quadrature points Q
   const bool affine = c->cfg.affine && c->cfg.transfer == MPM_TRANSFER_MLS;
   int kq[8];
   kq[0] = 0;
   for (int a = 0; a < d; ++a) kq[1 + a] = 1 + a;
   kq[1 + d] = 1000;  // JVP along vhat_n
   for (int a = 0; a < d; ++a) kq[2 + d + a] = 2000 + 1 + a;  // d/dX_a of the JVP
-  st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 1, 1, c->P, c->sv.xh32, c->sv.vh32, kq,
-                          affine ? 2 * d + 2 : d + 2, c->outQ, s);
-  if (st != MPM_OK) return st;
+  const int Rq = affine ? 2 * d + 2 : d + 2;
+  mpm_status st = MPM_OK;
+  if (c->merged) {
+    // 1 + 3. one decode of every particle with the quadrature rows: positions (x_all is its
+    // primal block) and F, v for whichever particles the neighbourhood selects
+    st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, c->P, c->sv.xh32, c->sv.vh32, kq, Rq, c->outQ, s);
+    if (st != MPM_OK) return st;
+  } else {
+    // 1. decode all particles at xhat_n
+    int k_primal[1] = {0};
+    st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, c->P, c->sv.xh32, nullptr, k_primal, 1, c->x_all, s);
+    if (st != MPM_OK) return st;
+  }
+  // 2. samples, basis set, neighbours
+  if (d == 2)
+    rom_select<2><<<1, 1024, 0, s>>>(c->dv);
+  else
+    rom_select<3><<<1, 1024, 0, s>>>(c->dv);
+  MPM_CUDA_TRY(cudaGetLastError());
+  if (!c->merged) {
+    // 3. F and v at the quadrature points Q
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 1, 1, c->P, c->sv.xh32, c->sv.vh32, kq, Rq, c->outQ,
+                            s);
+    if (st != MPM_OK) return st;
+  }
   // 4. local P2G onto I, 5. grid update + G2P to the samples
   const int b_q = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 4));
   const int M = c->cfg.material, T = c->cfg.transfer;
@@ -1064,7 +1078,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
     return s;
   };
   if ((st = ralloc(&c->X, (size_t)P * d)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->x_all, (size_t)P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->x_all_buf, (size_t)P * d)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->qlist, P)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->counts, 4)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->nodes, (size_t)k * NS)) != MPM_OK) return fail(st);
@@ -1080,6 +1094,10 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
     if ((st = ralloc(&c->Fref_inv, (size_t)P * d * d)) != MPM_OK) return fail(st);
     if ((st = ralloc(&c->xref32, (size_t)r)) != MPM_OK) return fail(st);
   }
+  // one decode of all particles per step when the neighbourhood of the samples covers most of
+  // the body anyway (2D: a sample's neighbourhood spans 5 x 5 cells, ~100 particles at 4 per cell)
+  c->merged = (int64_t)P <= 32 * (int64_t)c->k;
+  c->x_all = c->merged ? c->outQ : c->x_all_buf;
   if ((st = ralloc(&c->outS, (size_t)(r + 2) * P * d)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->outLS, (size_t)2 * kLS * P * d)) != MPM_OK) return fail(st);
   const int n_acc = r * (r + 1) / 2 + r + 1;
@@ -1110,6 +1128,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   v.inst = cfg->instance;
   v.X = c->X;
   v.x_all = c->x_all;
+  v.q_by_pid = c->merged ? 1 : 0;
   v.qlist = c->qlist;
   v.counts = c->counts;
   v.nodes = c->nodes;
@@ -1148,7 +1167,7 @@ void rom_destroy(rom_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->X);
-  cudaFree(c->x_all);
+  cudaFree(c->x_all_buf);
   cudaFree(c->qlist);
   cudaFree(c->counts);
   cudaFree(c->nodes);
