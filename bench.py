@@ -241,6 +241,50 @@ def cpu_baseline_rom(dec, sc, r, max_seconds=20.0):
             "sample": f"{steps} FP64 oracle reduced step(s) of the first held-out scene, single thread"}
 
 
+def rom_serving(dec, n_inst=8, steps=200):
+    """Many independent reduced-order instances served concurrently, one CUDA stream and one
+    captured step graph each (held-out (E, v0) draws of the same scene).  Returns the aggregate
+    reduced steps/s over all instances and the per-step latency distribution."""
+    import torch
+    from paper_2109_12390_gb300.rom import ROM
+    rng = np.random.default_rng(55)
+    roms, streams = [], []
+    for _ in range(n_inst):
+        E = float(rng.uniform(5e3, 1.5e4))
+        v0 = rng.uniform(-0.5, 0.5, size=2)
+        sc = S.block_2d(seed=4, side=64, dt=5e-5, origin=(0.375, 0.06), E=E, v0=v0)
+        rom = ROM.from_scene(dec, sc, seed=4, **{k: v for k, v in ROM_SETTINGS.items()})
+        rom.fit_initial(sc.x, sc.v, iters=20)
+        roms.append(rom)
+        streams.append(torch.cuda.Stream())
+    for rom, st in zip(roms, streams):
+        rom.step(2, stream=st)            # graph capture outside the timed region
+    torch.cuda.synchronize()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+          for _ in range(n_inst)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for st in streams:
+        st.wait_event(t_start)
+    for k in range(steps):
+        for i, (rom, st) in enumerate(zip(roms, streams)):
+            ev[i][k][0].record(st)
+            rom.step(1, stream=st)
+            ev[i][k][1].record(st)
+    for st in streams:
+        torch.cuda.current_stream().wait_stream(st)
+    t_end.record()
+    torch.cuda.synchronize()
+    wall_ms = t_start.elapsed_time(t_end)
+    lat = np.array([[a.elapsed_time(b) for a, b in ev[i]] for i in range(n_inst)]).ravel()
+    status = [rom.status() for rom in roms]
+    for rom in roms:
+        rom.close()
+    return {"instances": n_inst, "steps_each": steps, "aggregate_rom_steps_per_s": n_inst * steps / (wall_ms * 1e-3),
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "status_words": status, "how": "one CUDA stream and one captured step graph per instance"}
+
+
 def rom_leg(r=16, train_steps=None, steps=None):
     """Snapshots from the GPU full-order model, decoder training on the GPU, reduced-order runs on
     held-out scenes and their accumulated position error (Section 5) against the full-order runs;
@@ -287,8 +331,10 @@ def rom_leg(r=16, train_steps=None, steps=None):
     lin.set_precision(ROM_DECODER_FP32)
     e_linear = PL.rom_error(lin, t0s["scene"], fx_ck, seed=4, **ROM_SETTINGS).error_percent / 100.0
     cpu = cpu_baseline_rom(dec, tests[0]["scene"], r)
+    serving = rom_serving(dec, n_inst=8, steps=min(200, steps))
     return {
         "cpu_baseline": cpu,
+        "serving": serving,
         "scene": "2D neo-Hookean block 64x64 (4096 particles), 128^2 grid, nu=0.3, dt=5e-5, sticky walls, floor "
                  f"impact; decoder 2+{r}->128x5->2 ELU trained on {ROM_TRAIN_INSTANCES} trajectories, "
                  f"(E, v0) ~ U[5e3,1.5e4] x U[-0.5,0.5]^2; {len(tests)} held-out test draws",
