@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 // tensor-core kernel, all in FP32.
 // --------------------------------------------------------------------------
 constexpr int kF32Threads = 256;
-constexpr int kATStride = 132;            // AT row stride: float4-aligned, 2-way conflicts on transposed stores
+constexpr int kF32Rows = 64;              // rows per tile of the FP32 path
+constexpr int kATStride = kF32Rows + 4;   // AT row stride: float4-aligned
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
@@ -350,6 +351,10 @@ __device__ __forceinline__ float act_f32path(int act, float z) {
   return act == 0 ? (z > 0.f ? z : __expf(z) - 1.0f) : z;
 }
 
+// Tiles of kF32Rows = 64 rows (Pt = 64 / R points): twice as many CTAs as the
+// tensor-core tiling for a given call, which is what the small calls of the
+// reduced step need.  Thread (ty, tx) owns rows 8 ty .. 8 ty + 7 and features
+// tx + 32 i (i < 4) of each square layer.
 __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   extern __shared__ __align__(16) float fsm[];
   float* AT = fsm;                        // [128 k][kATStride] activations / pre-activations, transposed
@@ -378,17 +383,17 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
 
   const int64_t n_pts = dec_count(a);
   const int64_t n_tiles = (n_pts + a.Pt - 1) / a.Pt;
-  const int rw = t & 127, h = t >> 7;     // layer 0: row and column half
-  const int ty = t >> 4, tx = t & 15;     // square layers: rows 8 ty .. 8 ty + 7, features tx + 16 i
+  const int rw = t & (kF32Rows - 1), hq = t / kF32Rows;   // layer 0: row and column quarter
+  const int ty = t >> 5, tx = t & 31;                     // square layers
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t first = tile * a.Pt;
     if (a.n_tc > 0) prefetch(0);
-    // ---- layer 0 (FP32), this thread's row and 64 columns
+    // ---- layer 0 (FP32), this thread's row and 32 columns
     {
       const RowInfo ri = row_info(a, rw, first, n_pts);
       float in[40], dir[40];
       if (ri.cls >= 0) row_inputs(a, ri, in, dir);
-      for (int c = 64 * h; c < 64 * h + 64; ++c) {
+      for (int c = 32 * hq; c < 32 * hq + 32; ++c) {
         float hv = 0.f;
         if (ri.cls >= 0) {
           const float* w0r = sW0 + c * kW0Stride;
@@ -424,29 +429,29 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
       __syncthreads();                                  // AT complete, weights of layer l landed
       if (l + 1 < a.n_tc) prefetch(l + 1);              // overlaps the GEMM below
       const float* Wt = Wt0 + (l & 1) * kW * kW;
-      float acc[8][8];
+      float acc[8][4];
 #pragma unroll
       for (int j = 0; j < 8; ++j)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[j][i] = 0.f;
+        for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
 #pragma unroll 4
       for (int k = 0; k < kW; ++k) {
         const float4 a0 = *reinterpret_cast<const float4*>(AT + k * kATStride + 8 * ty);
         const float4 a1 = *reinterpret_cast<const float4*>(AT + k * kATStride + 8 * ty + 4);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        float wv[8];
+        float wv[4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) wv[i] = Wt[k * kW + tx + 16 * i];
+        for (int i = 0; i < 4; ++i) wv[i] = Wt[k * kW + tx + 32 * i];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
 #pragma unroll
-          for (int i = 0; i < 8; ++i) acc[j][i] = fmaf(av[j], wv[i], acc[j][i]);
+          for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(av[j], wv[i], acc[j][i]);
       }
       __syncthreads();                                  // every GEMM has read AT
       // pre-activations (bias on primal rows) replace the activations in AT
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int f = tx + 16 * i;
+      for (int i = 0; i < 4; ++i) {
+        const int f = tx + 32 * i;
         float z[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) z[j] = acc[j][i] + (rows[j].cls == 0 ? sbh[l * kW + f] : 0.f);
@@ -456,8 +461,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
       __syncthreads();
       // activations of the next layer from the row's own and exchanged pre-activations (registers)
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float* col = AT + (tx + 16 * i) * kATStride;
+      for (int i = 0; i < 4; ++i) {
+        const float* col = AT + (tx + 32 * i) * kATStride;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const RowInfo& ri = rows[j];
@@ -475,25 +480,32 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
       }
       __syncthreads();                                  // every pre-activation read
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int f = tx + 16 * i;
+      for (int i = 0; i < 4; ++i) {
+        const int f = tx + 32 * i;
         *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty) = make_float4(acc[0][i], acc[1][i], acc[2][i], acc[3][i]);
         *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty + 4) =
             make_float4(acc[4][i], acc[5][i], acc[6][i], acc[7][i]);
       }
     }
     __syncthreads();
-    // ---- output layer (FP32): thread t < 128 owns row t
-    if (t < 128) {
-      const RowInfo ri = row_info(a, t, first, n_pts);
-      if (ri.cls >= 0) {
-        const int kidx = t / a.Pt;
+    // ---- output layer (FP32): 4 threads per row, k split in quarters and combined by shuffles
+    {
+      const int row = t >> 2, kq = t & 3;
+      const RowInfo ri = row_info(a, row, first, n_pts);
+      float y[3] = {0.f, 0.f, 0.f};
+      for (int i = 0; i < a.d; ++i)
+        for (int k = 32 * kq; k < 32 * kq + 32; ++k) y[i] = fmaf(sWout[i * kW + k], AT[k * kATStride + row], y[i]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        y[i] += __shfl_xor_sync(0xffffffffu, y[i], 1);
+        y[i] += __shfl_xor_sync(0xffffffffu, y[i], 2);
+      }
+      if (kq == 0 && ri.cls >= 0) {
+        const int kidx = row / a.Pt;
         float* o = a.out + ((int64_t)kidx * a.n + ri.p) * a.d;
         for (int i = 0; i < a.d; ++i) {
-          float y = 0.f;
-          for (int k = 0; k < kW; ++k) y = fmaf(sWout[i * kW + k], AT[k * kATStride + t], y);
-          y += (ri.cls == 0 ? a.bout[i] : 0.f);
-          o[i] = y * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
+          const float v = y[i] + (ri.cls == 0 ? a.bout[i] : 0.f);
+          o[i] = v * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
         }
       }
     }
@@ -753,6 +765,8 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, dec->n_sm * 8));
     decoder_simt<<<blocks, 128, 0, s>>>(a);
   } else if (dec->fp32 && !a.zstore) {
+    MPM_CHECK_ARG(R <= kF32Rows, "the FP32 path takes at most 64 row kinds");
+    a.Pt = kF32Rows / R;
     const int64_t tiles = (n + a.Pt - 1) / a.Pt;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));
     decoder_f32<<<blocks, kF32Threads, dec_f32_smem_bytes(), s>>>(a);
