@@ -136,7 +136,7 @@ __device__ __forceinline__ void f_minus_polar_3d(const float F[9], float out[9])
     cofactor3(X, C);
     float det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
     float z = rcbrtf(fabsf(det));
-    float zi = 1.0f / (z * det);
+    float zi = __frcp_rn(z * det);   // correctly rounded 1 / x, the value 1.0f / x gives
     float diff = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -194,7 +194,7 @@ __device__ __forceinline__ void f_minus_polar_3d(const float F[9], float out[9])
     float Ac[9];
     cofactor3(A, Ac);
     float detA = A[0] * Ac[0] + A[1] * Ac[1] + A[2] * Ac[2];
-    float ia = 1.0f / detA;
+    float ia = __frcp_rn(detA);
     float w0 = (Ac[0] * av0 + Ac[3] * av1 + Ac[6] * av2) * ia;  // A symmetric: A^-1 = cof^T / det
     float w1 = (Ac[1] * av0 + Ac[4] * av1 + Ac[7] * av2) * ia;
     float w2 = (Ac[2] * av0 + Ac[5] * av1 + Ac[8] * av2) * ia;
@@ -261,7 +261,7 @@ __device__ __forceinline__ void grid_node_velocity(float4 mp, const int node[D],
                                                    float dt, const float g[3], float v[D]) {
   float comp[3] = {mp.y, mp.z, mp.w};
   if (mp.x > 0.f) {
-    float im = 1.0f / mp.x;
+    float im = __frcp_rn(mp.x);
 #pragma unroll
     for (int a = 0; a < D; ++a) v[a] = comp[a] * im + dt * g[a];
   } else {

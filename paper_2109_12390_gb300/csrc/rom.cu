@@ -556,10 +556,11 @@ enum { NE_VEL = 0, NE_GN = 1, NE_FIT = 2 };
 
 // Cholesky solve of the SPD system A x = b held in shared memory (A: r x r,
 // row-major, r <= 32) by the block's first warp, synchronised with __syncwarp
-// only; the other warps wait at the final barrier.  One FP64 square root and one
-// reciprocal per column (computed by lane 0 and broadcast); the substitutions
-// multiply by the stored reciprocal pivots (FP64 division and square root are
-// long-latency sequences on this GPU).  Returns false, for the whole block, if a
+// only; the other warps wait at the final barrier.  Per column one reciprocal
+// square root of the pivot, by Newton-Raphson in FP64 from an FP32 seed
+// (computed by lane 0 and broadcast); the substitutions multiply by the stored
+// reciprocal pivots, so the solve has no FP64 division or square root (long-
+// latency sequences on this GPU).  Returns false, for the whole block, if a
 // pivot is not positive.
 __device__ bool chol_solve(double* A, double* b, int r) {
   __shared__ int s_bad;
@@ -576,8 +577,13 @@ __device__ bool chol_solve(double* A, double* b, int r) {
       }
       double l = 0.0, rl = 0.0;
       if (lane == 0) {
-        l = sqrt(piv);
-        rl = 1.0 / l;
+        // 1 / sqrt(piv) by Newton-Raphson on f(y) = 1/y^2 - piv from an FP32 seed:
+        // y <- y (3 - piv y^2) / 2, quadratic convergence, two steps reach FP64 precision
+        double y = (double)rsqrtf((float)piv);
+        y = y * (1.5 - 0.5 * piv * y * y);
+        y = y * (1.5 - 0.5 * piv * y * y);
+        rl = y;
+        l = piv * y;
       }
       l = __shfl_sync(full, l, 0);
       rl = __shfl_sync(full, rl, 0);
