@@ -161,8 +161,11 @@ def p2g(x, v, F, C, mass, vol, mu, lam, *, dx, dt, n_grid, material, transfer):
     shape = (n_grid,) * d
     m = np.zeros(shape)
     p = np.zeros(shape + (d,))
+    # mass and reference volume: one value for all particles, or one per particle
+    mass = np.broadcast_to(np.asarray(mass, np.float64), (P,))
+    vol = np.broadcast_to(np.asarray(vol, np.float64), (P,))
     if transfer == MLS:
-        affine = mass * C - (dt * vol * 4.0 / dx ** 2) * tau
+        affine = mass[:, None, None] * C - (dt * 4.0 / dx ** 2) * vol[:, None, None] * tau
     for off in stencil_offsets(d):
         node = base + np.array(off)
         weight = np.ones(P)
@@ -170,7 +173,7 @@ def p2g(x, v, F, C, mass, vol, mu, lam, *, dx, dt, n_grid, material, transfer):
             weight = weight * w[:, k, off[k]]
         dpos = node * dx - x
         if transfer == MLS:
-            mom = weight[:, None] * (mass * v + np.einsum("pij,pj->pi", affine, dpos))
+            mom = weight[:, None] * (mass[:, None] * v + np.einsum("pij,pj->pi", affine, dpos))
         else:
             grad = np.empty((P, d))
             for a in range(d):
@@ -179,7 +182,7 @@ def p2g(x, v, F, C, mass, vol, mu, lam, *, dx, dt, n_grid, material, transfer):
                     if k != a:
                         g = g * w[:, k, off[k]]
                 grad[:, a] = g
-            mom = weight[:, None] * mass * v - dt * vol * np.einsum("pij,pj->pi", tau, grad)
+            mom = weight[:, None] * mass[:, None] * v - dt * vol[:, None] * np.einsum("pij,pj->pi", tau, grad)
         idx = tuple(node[:, k] for k in range(d))
         np.add.at(m, idx, weight * mass)
         np.add.at(p, idx, mom)

@@ -65,6 +65,7 @@ error metric on a hand-computed toy.
 from __future__ import annotations
 
 import dataclasses
+import itertools
 
 import numpy as np
 
@@ -121,6 +122,64 @@ def neighbourhood(x_all, samples, dx, n_grid):
     return basis, np.nonzero(hit)[0]
 
 
+# ----------------------------------------------------------- Eulerian quadrature (Algorithm 4)
+
+
+def eulerian_cells(basis, d, n_grid):
+    """Grid cells whose quadrature points can reach a node of the basis set I: a point in cell c
+    has stencil base c - 1 or c, so its stencil covers nodes c - 1 .. c + 2; node i is reached from
+    cells i - 2 .. i + 1 along every axis.  Sorted linear cell ids (cell c = lower corner node c),
+    clipped to cells whose stencils stay in the grid."""
+    nodes = np.array(basis, np.int64)
+    coords = np.stack(np.unravel_index(nodes, (n_grid,) * d), axis=1)
+    cells = set()
+    for off in itertools.product(range(-2, 2), repeat=d):
+        c = coords + np.array(off)
+        ok = np.all((c >= 1) & (c <= n_grid - 3), axis=1)
+        cells.update(np.ravel_multi_index(tuple(c[ok].T), (n_grid,) * d).tolist())
+    return np.array(sorted(cells), np.int64)
+
+
+def eulerian_points(cells, d, n_grid, dx, ell):
+    """ell^d evenly spaced quadrature points per cell, (c + (q + 1/2) / ell) dx, each with volume
+    (dx / ell)^d (Section 3.2.2); ordered by cell, then q lexicographically."""
+    coords = np.stack(np.unravel_index(cells, (n_grid,) * d), axis=1).astype(np.float64)
+    offs = (np.array(list(itertools.product(range(ell), repeat=d)), np.float64) + 0.5) / ell
+    pts = (coords[:, None, :] + offs[None, :, :]) * dx
+    return pts.reshape(-1, d), (dx / ell) ** d
+
+
+def invert_decoder(dec, x, xhat, X0, iters):
+    """Newton's method on g(X; xhat) = x (Section 3.2.2): X <- X - (dg/dX)^-1 (g(X) - x).
+    Returns X and the final residual norms."""
+    X = np.array(X0, np.float64)
+    for _ in range(iters):
+        g, FX, _ = D.jacobians(dec, X, xhat)
+        X = X - np.linalg.solve(FX, (g - x)[..., None])[..., 0]
+    g = D.decode(dec, X, xhat)
+    return X, np.linalg.norm(g - x, axis=1)
+
+
+def reference_occupancy(X, h):
+    """The reference domain as the union of the particles' volume boxes (side h = V0^(1/d), centred
+    on the reference positions): returns (origin, shape, occupied flags) of a box grid of spacing
+    h whose cell k holds particle positions in [origin + k h, origin + (k + 1) h)."""
+    origin = X.min(0) - 0.5 * h
+    idx = np.floor((X - origin) / h).astype(np.int64)
+    shape = tuple(idx.max(0) + 1)
+    occ = np.zeros(shape, bool)
+    occ[tuple(idx.T)] = True
+    return origin, shape, occ
+
+
+def inside_reference(Xq, origin, h, shape, occ):
+    idx = np.floor((Xq - origin) / h).astype(np.int64)
+    ok = np.all((idx >= 0) & (idx < np.array(shape)), axis=1)
+    out = np.zeros(len(Xq), bool)
+    out[ok] = occ[tuple(idx[ok].T)]
+    return out
+
+
 @dataclasses.dataclass
 class RomScene:
     """Static data of one reduced-order instance."""
@@ -147,6 +206,9 @@ class RomScene:
     ridge: float = 0.0                       # rho of the regularised projections
     affine: str = "zero"                     # quadrature-point C: "zero" or "decoded"
     F_ref_inv: np.ndarray | None = None      # (P, d, d) inverse reference gradients (f_reference option)
+    quadrature: str = "lagrangian"           # or "eulerian" (Algorithm 4)
+    ell: int = 2                             # Eulerian quadrature points per cell per dimension
+    newton_iters: int = 4                    # decoder inversion iterations
 
 
 @dataclasses.dataclass
@@ -200,6 +262,56 @@ def reference_inverse(dec, X, xhat_ref):
     undeformed configuration produces no stress)."""
     _, FX, _ = D.jacobians(dec, X, xhat_ref)
     return np.linalg.inv(FX)
+
+
+def eulerian_quadrature(dec, rs: RomScene, xhat, vhat, samples, x_samples, X_guess=None):
+    """Algorithm 4: quadrature points on the cells around the basis set of the samples, their
+    reference positions by inverting the decoder, kinematics there by Eqs. defGrad and timederOne,
+    mass rho0 V_q / J.  Points whose reference position is outside the reference domain (or whose
+    inversion does not converge) carry no mass.  Returns (basis, cells, points x_q, reference X_q,
+    F_q, v_q, mass_q, reference volume V_q / J_q, inside flags)."""
+    d = rs.X.shape[1]
+    nodes = stencil_nodes(x_samples, rs.dx, rs.n_grid)
+    basis = np.unique(nodes)
+    cells = eulerian_cells(basis, d, rs.n_grid)
+    xq, Vq = eulerian_points(cells, d, rs.n_grid, rs.dx, rs.ell)
+    if X_guess is None:
+        X_guess = xq - (x_samples - rs.X[samples]).mean(0)
+    Xq, resid = invert_decoder(dec, xq, xhat, X_guess, rs.newton_iters)
+    h = rs.vol ** (1.0 / d)
+    origin, shape, occ = reference_occupancy(rs.X, h)
+    inside = inside_reference(Xq, origin, h, shape, occ) & (resid < 1e-6 * rs.dx)
+    _, FX, _ = D.jacobians(dec, Xq, xhat)
+    _, vq = D.jvp_latent(dec, Xq, xhat, vhat)
+    J = np.linalg.det(FX)
+    rho0 = rs.mass / rs.vol
+    V0 = np.where(inside, Vq / np.where(J > 0, J, 1.0), 0.0)
+    return basis, cells, xq, Xq, FX, vq, rho0 * V0, V0, inside
+
+
+def eulerian_local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_samples, X_guess=None):
+    """Algorithm 5 with the Eulerian quadrature points of Algorithm 4: P2G from the points inside
+    the body onto the basis set, grid update, G2P to the samples.  Returns (v_trial, x_trial, and
+    the quadrature data of eulerian_quadrature)."""
+    q = eulerian_quadrature(dec, rs, xhat, vhat, samples, x_samples, X_guess)
+    basis, cells, xq, Xq, FX, vq, mq, V0, inside = q
+    d = xq.shape[1]
+    mu, lam = M.lame(rs.E, rs.nu)
+    sel = inside
+    m, p = M.p2g(xq[sel], vq[sel], FX[sel], np.zeros((int(sel.sum()), d, d)), mq[sel], V0[sel], mu, lam,
+                 dx=rs.dx, dt=rs.dt, n_grid=rs.n_grid, material=rs.material, transfer=rs.transfer)
+    vg = M.grid_update(m, p, dt=rs.dt, gravity=rs.gravity, bc=rs.bc, bc_width=rs.bc_width)
+    xs = x_samples
+    base = M.stencil_base(xs, rs.dx)
+    w, _ = M.bspline(xs / rs.dx - base)
+    v_trial = np.zeros((len(samples), d))
+    for off in M.stencil_offsets(d):
+        node = base + np.array(off)
+        weight = np.ones(len(samples))
+        for k in range(d):
+            weight = weight * w[:, k, off[k]]
+        v_trial += weight[:, None] * vg[tuple(node[:, k] for k in range(d))]
+    return v_trial, xs + rs.dt * v_trial, q
 
 
 def lstsq(A, b, ridge=0.0):
@@ -256,8 +368,14 @@ def rom_step(dec, rs: RomScene, st: RomState, record=None):
     """Algorithm 2 with Lagrangian quadrature; returns the new RomState."""
     P = len(rs.X)
     samples = sample_set(rs.seed, rs.inst, st.step, P, rs.n_samples)
-    x_all = D.decode(dec, rs.X, st.xhat)
-    v_trial, x_trial, basis, neigh = local_dynamics(dec, rs, st.xhat, st.vhat, samples, x_all)
+    if rs.quadrature == "eulerian":
+        x_all = None
+        x_s = D.decode(dec, rs.X[samples], st.xhat)
+        v_trial, x_trial, q = eulerian_local_dynamics(dec, rs, st.xhat, st.vhat, samples, x_s)
+        basis, neigh = q[0], np.zeros(0, np.int64)
+    else:
+        x_all = D.decode(dec, rs.X, st.xhat)
+        v_trial, x_trial, basis, neigh = local_dynamics(dec, rs, st.xhat, st.vhat, samples, x_all)
     Xs = rs.X[samples]
     vhat_new = project_velocity(dec, Xs, st.xhat, v_trial, rs.ridge, st.vhat)
     if rs.projection == "velocity-only":

@@ -197,3 +197,72 @@ def test_reference_gradient_makes_the_decoded_initial_state_stress_free():
                                atol=1e-12)
     v1, _, _, _ = R.local_dynamics(dec, rs, xh, np.zeros(3), samples, x_all)
     assert np.abs(v1).max() < 1e-9 * np.abs(v0).max()
+
+
+# ---------------------------------------------------------------- Eulerian quadrature (Alg. 4)
+
+
+def test_eulerian_cells_brute_force():
+    """Cells whose ell = 2 quadrature points reach a basis node: enumerate every cell's points and
+    their stencils directly."""
+    n, d, dx = 16, 2, 1.0 / 16
+    basis = np.array([5 * n + 7, 9 * n + 9])
+    cells = R.eulerian_cells(basis, d, n)
+    want = []
+    for c in range(n * n):
+        ci = np.array(np.unravel_index(c, (n, n)))
+        if ci.min() < 1 or ci.max() > n - 3:
+            continue
+        pts, _ = R.eulerian_points(np.array([c]), d, n, dx, 2)
+        nodes = R.stencil_nodes(pts, dx, n)
+        if np.isin(nodes, basis).any():
+            want.append(c)
+    np.testing.assert_array_equal(cells, want)
+
+
+def test_decoder_inversion():
+    """Newton inversion of g(X; xhat) = x: exact in one iteration for a decoder affine in X, and to
+    round-off for an ELU decoder started from a perturbed reference position."""
+    rng = np.random.default_rng(21)
+    X = rng.uniform(0.3, 0.6, size=(40, 2))
+    lin = _translation_decoder(2, X.min(0), X.max(0) - X.min(0))
+    lin.W[0][:, :2] = lin.W[0][:, :2] @ np.array([[1.1, 0.2], [-0.1, 0.9]])
+    xh = np.array([0.01, -0.02])
+    x = D.decode(lin, X, xh)
+    Xi, res = R.invert_decoder(lin, x, xh, X + 0.01, 1)
+    np.testing.assert_allclose(Xi, X, atol=1e-13)
+    dec = S.xavier_decoder(4, 2, 3, 32, 2, D.ELU, X_min=X.min(0), X_range=X.max(0) - X.min(0),
+                           out_shift=X.mean(0), out_scale=np.full(2, 0.1), bias_scale=0.1)
+    dec.W[0][:, :2] *= 0.3
+    xh = 0.1 * rng.normal(size=3)
+    x = D.decode(dec, X, xh)
+    _, FX, _ = D.jacobians(dec, X, xh)
+    assert np.abs(np.linalg.det(FX)).min() > 0
+    Xi, res = R.invert_decoder(dec, x, xh, X + 1e-3 * rng.normal(size=X.shape), 6)
+    assert res.max() < 1e-13
+    np.testing.assert_allclose(Xi, X, atol=1e-11)
+
+
+def test_eulerian_quadrature_mass_and_free_fall():
+    """Translation decoder g = X + xhat with the body aligned to the quadrature grid: when the
+    samples' cells cover the whole block, the inside quadrature points carry exactly the
+    particles' total mass; and the Eulerian reduced step reproduces the full-order free fall."""
+    sc = S.block_2d(side=16, dt=5e-5, origin=(0.375, 0.375), v0=np.array([0.2, 0.3]))
+    X = sc.x.copy()
+    dec = _translation_decoder(2, X.min(0), X.max(0) - X.min(0))
+    rs = R.RomScene(X=X, mass=sc.p_mass, vol=sc.p_vol, E=1e4, nu=0.3, dx=sc.dx, dt=sc.dt, n_grid=sc.n_grid,
+                    gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width, material=sc.material,
+                    transfer=sc.transfer, n_samples=len(X), seed=4, quadrature="eulerian")
+    xh = np.array([2, -1]) * sc.dx / 2          # a shift by whole quadrature spacings keeps the alignment
+    samples = np.arange(len(X))
+    q = R.eulerian_quadrature(dec, rs, xh, np.zeros(2), samples, D.decode(dec, X, xh))
+    mq, inside = q[6], q[8]
+    assert inside.sum() == len(X)              # ell = 2 on a block at dx / 2 spacing: one point per particle
+    np.testing.assert_allclose(mq.sum(), sc.p_mass * len(X), rtol=1e-14)
+    rs.n_samples = 12
+    st = R.rom_init(dec, X, sc.v[0], sc.dt)
+    fom = sc.copy()
+    for _ in range(5):
+        st = R.rom_step(dec, rs, st)
+        M.step(fom, 1)
+        np.testing.assert_allclose(D.decode(dec, X, st.xhat), fom.x, atol=1e-13)
