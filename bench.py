@@ -330,6 +330,18 @@ def rom_leg(r=16, train_steps=None, steps=None):
     trl.close()
     lin.set_precision(ROM_DECODER_FP32)
     e_linear = PL.rom_error(lin, t0s["scene"], fx_ck, seed=4, **ROM_SETTINGS).error_percent / 100.0
+    # Eulerian quadrature (Algorithm 4) on the first test: it has no particle ids at its points, so
+    # no reference-gradient correction; the Lagrangian quadrature without it is the like-for-like
+    eul_settings = dict(ROM_SETTINGS, f_reference=0)
+    e_eul = PL.rom_error(dec, t0s["scene"], t0s["fom"], seed=4, checkpoints=(ck,), quadrature=1, **eul_settings)
+    e_lag = PL.rom_error(dec, t0s["scene"], t0s["fom"], seed=4, checkpoints=(ck,), **eul_settings)
+    eulerian = {"rel_error_at_checkpoint": e_eul.error_percent_at[ck] / 100.0,
+                "rel_error_full": e_eul.error_percent / 100.0, "rom_steps_per_s": e_eul.rom_steps_per_s,
+                "status_word": e_eul.status, "ell": 2, "newton_iters": 4,
+                "lagrangian_same_settings": {"rel_error_at_checkpoint": e_lag.error_percent_at[ck] / 100.0,
+                                             "rel_error_full": e_lag.error_percent / 100.0,
+                                             "rom_steps_per_s": e_lag.rom_steps_per_s},
+                "settings": eul_settings, "steps": ck}
     cpu = cpu_baseline_rom(dec, tests[0]["scene"], r)
     serving = rom_serving(dec, n_inst=8, steps=min(200, steps))
     return {
@@ -345,6 +357,7 @@ def rom_leg(r=16, train_steps=None, steps=None):
         "gain": {"trained": per_test[0]["rel_error_at_checkpoint"], "untrained_xavier": e_untrained,
                  "trained_linear_manifold": e_linear, "linear_training_steps": max(1, train_steps // 4),
                  "steps": ck},
+        "eulerian_quadrature": eulerian,
         "training": {"steps": train_steps, "batch_points": 65536, "seconds": t_train,
                      "points_per_s": train_steps * 65536 / t_train, "ms_per_step": 1e3 * t_train / train_steps,
                      "final_loss": loss, "snapshot_seconds": t_snap, "snapshots": int(snaps["n_snap"])},

@@ -372,6 +372,22 @@ mpm_status decoder_set_precision(mpm_decoder* dec, int fp32);
  *                or the one given to rom_set_reference: the decoder's
  *                approximation error of the undeformed configuration then
  *                produces no stress.  For initial states with F = I.
+ *   quadrature   0: Lagrangian quadrature (Alg. 3): the samples and the
+ *                particles whose stencils reach their basis set.  1: Eulerian
+ *                quadrature (Alg. 4): ell^d points per grid cell at
+ *                (c + (j + 1/2) / ell) dx on every cell whose points reach a
+ *                node of the basis set (cells i - 2 .. i + 1 around node i,
+ *                restricted to cells 1 .. n_grid - 3); each point's reference
+ *                position X_q solves g(X_q; xhat_n) = x_q by newton_iters Newton
+ *                steps from x_q minus the samples' mean displacement; the point
+ *                carries mass rho V_q / J and reference volume V_q / J
+ *                (V_q = (dx / ell)^d, J = det dg/dX) when X_q lies in the
+ *                reference domain (the union of the particles' boxes of side
+ *                p_vol^(1/d) centred on X) and |g(X_q) - x_q| < newton_tol dx,
+ *                none otherwise.  Excludes affine and f_reference.
+ *   ell          points per cell per axis, 1..4 (0: 2).
+ *   newton_iters decoder inversion steps, 1..16 (0: 4).
+ *   newton_tol   convergence threshold in units of dx (0: 1e-3).
  */
 typedef struct rom_config {
   int32_t dim;
@@ -396,6 +412,10 @@ typedef struct rom_config {
   float ridge;
   int32_t affine;
   int32_t f_reference;
+  int32_t quadrature;
+  int32_t ell;
+  int32_t newton_iters;
+  float newton_tol;
 } rom_config;
 
 typedef struct rom_ctx rom_ctx;
@@ -440,8 +460,11 @@ mpm_status rom_set_reference(rom_ctx* ctx, const double* xhat_ref, void* stream)
  * at the quadrature points, local particle-to-grid / grid update /
  * grid-to-particle to the samples (Alg. 5), velocity least squares and the
  * Gauss-Newton position projection (Alg. 6) or the velocity-only projection
- * (Alg. 7).  All on the device: one captured CUDA graph per step, launched on
- * `stream`.  Solver failures raise MPM_STATUS_* bits (rom_status_word).
+ * (Alg. 7).  With the Eulerian quadrature (cfg.quadrature = 1) the samples are
+ * decoded alone and the quadrature points come from Algorithm 4 instead of the
+ * neighbour set.  All on the device: one captured CUDA graph per step,
+ * launched on `stream`.  Solver failures raise MPM_STATUS_* bits
+ * (rom_status_word; MPM_STATUS_CAPACITY if the cells exceed the capacity).
  */
 mpm_status rom_step(rom_ctx* ctx, int n_steps, void* stream);
 
@@ -450,12 +473,26 @@ mpm_status rom_status_word(rom_ctx* ctx, uint32_t* out, int clear, void* stream)
 /*
  * Diagnostics of the last step (any pointer may be NULL; synchronous):
  * qlist (n_particles int32): samples ascending then neighbours ascending;
- * counts (3 int32): |P|, |P| + |N|, basis-node list length; x_all
+ * counts (3 int32): |P|, |P| + |N| (the number of Eulerian quadrature points
+ * with cfg.quadrature = 1), basis-node list length; x_all
  * (n_particles, dim): decoded positions g(X; xhat_n) the step used;
  * v_trial, x_trial (|P|, dim): Algorithm 5 outputs of the samples.
  */
 mpm_status rom_debug(rom_ctx* ctx, int32_t* qlist, int32_t* counts, float* x_all, float* v_trial,
                      float* x_trial, void* stream);
+
+/*
+ * Eulerian quadrature of the last step (cfg.quadrature = 1; synchronous; any
+ * output pointer may be NULL): the number of points n_points, their positions
+ * x_points and reference positions X_points (n_points, dim), mass and
+ * reference volume (n_points; zero for points outside the body).  Points are
+ * ordered by cell in the order the cells were collected, then by sub-point
+ * (last axis fastest).  Output buffers (host or device) must hold the point
+ * capacity: min((n_grid - 3)^dim, 6^dim n_samples) ell^dim points.  Errors:
+ * MPM_EINVAL with the Lagrangian quadrature.
+ */
+mpm_status rom_debug_quadrature(rom_ctx* ctx, int32_t* n_points, float* x_points, float* X_points, float* mass,
+                                float* V0, void* stream);
 
 /* g(X^p; xhat_n) for every particle into device array x_out (n_particles, dim). */
 mpm_status rom_decode_all(rom_ctx* ctx, float* x_out, void* stream);

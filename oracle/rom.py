@@ -209,6 +209,7 @@ class RomScene:
     quadrature: str = "lagrangian"           # or "eulerian" (Algorithm 4)
     ell: int = 2                             # Eulerian quadrature points per cell per dimension
     newton_iters: int = 4                    # decoder inversion iterations
+    newton_tol: float = 1e-3                 # converged: final residual below newton_tol * dx
 
 
 @dataclasses.dataclass
@@ -264,12 +265,14 @@ def reference_inverse(dec, X, xhat_ref):
     return np.linalg.inv(FX)
 
 
-def eulerian_quadrature(dec, rs: RomScene, xhat, vhat, samples, x_samples, X_guess=None):
+def eulerian_quadrature(dec, rs: RomScene, xhat, vhat, samples, x_samples, X_guess=None, inside_override=None):
     """Algorithm 4: quadrature points on the cells around the basis set of the samples, their
     reference positions by inverting the decoder, kinematics there by Eqs. defGrad and timederOne,
     mass rho0 V_q / J.  Points whose reference position is outside the reference domain (or whose
     inversion does not converge) carry no mass.  Returns (basis, cells, points x_q, reference X_q,
-    F_q, v_q, mass_q, reference volume V_q / J_q, inside flags)."""
+    F_q, v_q, mass_q, reference volume V_q / J_q, inside flags).  ``inside_override`` (index array,
+    flag array) replaces the inside decision of the listed points (a decision taken elsewhere in
+    another precision)."""
     d = rs.X.shape[1]
     nodes = stencil_nodes(x_samples, rs.dx, rs.n_grid)
     basis = np.unique(nodes)
@@ -280,7 +283,9 @@ def eulerian_quadrature(dec, rs: RomScene, xhat, vhat, samples, x_samples, X_gue
     Xq, resid = invert_decoder(dec, xq, xhat, X_guess, rs.newton_iters)
     h = rs.vol ** (1.0 / d)
     origin, shape, occ = reference_occupancy(rs.X, h)
-    inside = inside_reference(Xq, origin, h, shape, occ) & (resid < 1e-6 * rs.dx)
+    inside = inside_reference(Xq, origin, h, shape, occ) & (resid < rs.newton_tol * rs.dx)
+    if inside_override is not None:
+        inside[inside_override[0]] = inside_override[1]
     _, FX, _ = D.jacobians(dec, Xq, xhat)
     _, vq = D.jvp_latent(dec, Xq, xhat, vhat)
     J = np.linalg.det(FX)
@@ -289,11 +294,11 @@ def eulerian_quadrature(dec, rs: RomScene, xhat, vhat, samples, x_samples, X_gue
     return basis, cells, xq, Xq, FX, vq, rho0 * V0, V0, inside
 
 
-def eulerian_local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_samples, X_guess=None):
+def eulerian_local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_samples, X_guess=None, inside_override=None):
     """Algorithm 5 with the Eulerian quadrature points of Algorithm 4: P2G from the points inside
     the body onto the basis set, grid update, G2P to the samples.  Returns (v_trial, x_trial, and
     the quadrature data of eulerian_quadrature)."""
-    q = eulerian_quadrature(dec, rs, xhat, vhat, samples, x_samples, X_guess)
+    q = eulerian_quadrature(dec, rs, xhat, vhat, samples, x_samples, X_guess, inside_override)
     basis, cells, xq, Xq, FX, vq, mq, V0, inside = q
     d = xq.shape[1]
     mu, lam = M.lame(rs.E, rs.nu)

@@ -45,6 +45,7 @@ class RomConfig(C.Structure):
         ("E", C.c_float), ("nu", C.c_float), ("latent_dim", C.c_int32), ("n_samples", C.c_int32),
         ("seed", C.c_uint64), ("instance", C.c_int32), ("gn_iters", C.c_int32), ("projection", C.c_int32),
         ("ridge", C.c_float), ("affine", C.c_int32), ("f_reference", C.c_int32),
+        ("quadrature", C.c_int32), ("ell", C.c_int32), ("newton_iters", C.c_int32), ("newton_tol", C.c_float),
     ]
 
 
@@ -100,6 +101,7 @@ SIGNATURES = [
     ("rom_step", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("rom_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
     ("rom_debug", C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),
+    ("rom_debug_quadrature", C.c_int, [C.c_void_p, C.POINTER(C.c_int32)] + [C.c_void_p] * 4 + [C.c_void_p]),
     ("rom_decode_all", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("metric_accumulate", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("trainer_create", C.c_int, [C.c_void_p, C.POINTER(TrainConfig), C.POINTER(SnapshotDesc), C.c_void_p,

@@ -35,6 +35,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -84,6 +85,20 @@ struct RomDev {
   uint32_t* status;
   const float* Fref_inv;     // (P, d, d) inverse reference gradients, or null (f_reference = 0)
   int q_by_pid;              // quadrature decoder rows indexed by particle id (one decode of all particles)
+  // Eulerian quadrature (Algorithm 4)
+  int eulerian;              // 1: samples only in rom_select; quadrature points on cells
+  int ell;                   // points per cell per dimension
+  const float* x_samp;       // (k, d) decoded sample positions (Eulerian mode), or null
+  uint32_t* cstamp;          // (n^d) cell stamps
+  int32_t* clist;            // (cap_cells) cells of the quadrature set
+  int cap_cells;
+  float* qX;                 // (cap_cells ell^d, d) reference positions of the quadrature points
+  float* qm;                 // (cap_cells ell^d) mass (0 outside the body)
+  float* qV0;                // (cap_cells ell^d) reference volume V_q / J
+  const uint8_t* occ;        // reference-domain occupancy of boxes of side occ_h
+  float occ_origin[3];
+  float occ_h;
+  int occ_shape[3];
 };
 
 // Inverse of a small matrix by its adjugate (F of a quadrature point, det F > 0).
@@ -258,6 +273,12 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
     }
   }
   __syncthreads();
+  if (R.eulerian) {
+    // Algorithm 4: only the samples; their basis set and the quadrature cells come after the
+    // samples are decoded (rom_eul_cells)
+    if (t == 0) R.counts[0] = k;
+    return;
+  }
   // basis set I: stamp the stencil nodes of the samples (and keep them for clearing)
   constexpr int NS = (D == 2) ? 9 : 27;
   for (int i = t; i < k; i += T) {
@@ -488,6 +509,255 @@ __global__ void rom_reference(const float* __restrict__ dec_out, int64_t cap, in
   }
 }
 
+// ------------------------------------------- Eulerian quadrature (Alg. 4)
+// Basis set I from the decoded sample positions (stamps, node list for the next
+// clear) and the quadrature cells: every cell whose points reach a node of I,
+// cells i - 2 .. i + 1 per axis around node i, kept when their stencils stay in
+// the grid.  A cell is appended once per step (atomic exchange of its stamp).
+// One CTA.  counts[1] = number of quadrature points (cells x ell^d).
+template <int D>
+__global__ void __launch_bounds__(1024) rom_eul_cells(RomDev R) {
+  __shared__ int s_nc;
+  const int t = threadIdx.x, T = blockDim.x;
+  const int k = R.counts[0];
+  const uint32_t stamp = (uint32_t)(*R.step + 1);
+  constexpr int NS = (D == 2) ? 9 : 27;
+  constexpr int NC = (D == 2) ? 16 : 64;     // cells -2 .. 1 around a node, per axis 4
+  if (t == 0) s_nc = 0;
+  __syncthreads();
+  for (int i = t; i < k; i += T) {
+    int base[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int b = stencil_base(R.x_samp[(size_t)i * D + a], R.inv_dx);
+      if (b < 0 || b + 2 > R.n - 1) raise_status(R.status, STATUS_OUT_OF_GRID);
+      base[a] = min(max(b, 0), R.n - 3);
+    }
+    for (int s = 0; s < NS; ++s) {
+      int node[D];
+      node[0] = base[0] + (D == 2 ? s / 3 : s / 9);
+      node[D - 1] = base[D - 1] + s % 3;
+      if (D == 3) node[1] = base[1] + (s / 3) % 3;
+      const int l = node_linear<D>(node, R.n);
+      R.stamp[l] = stamp;
+      R.nodes[i * NS + s] = l;
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < k * NS * NC; e += T) {
+    const int l = R.nodes[e / NC];
+    const int o = e % NC;
+    int c[D];
+    int rem = l;
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      c[a] = rem % R.n;
+      rem /= R.n;
+    }
+    bool ok = true;
+    int oo = o;
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      c[a] += (oo % 4) - 2;
+      oo /= 4;
+      ok &= (c[a] >= 1) & (c[a] <= R.n - 3);
+    }
+    if (!ok) continue;
+    const int cl = node_linear<D>(c, R.n);
+    if (atomicExch(&R.cstamp[cl], stamp) != stamp) {
+      const int slot = atomicAdd(&s_nc, 1);
+      if (slot < R.cap_cells) R.clist[slot] = cl;
+      else raise_status(R.status, STATUS_CAPACITY);
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    int pts = 1;
+    for (int a = 0; a < D; ++a) pts *= R.ell;
+    R.counts[1] = min(s_nc, R.cap_cells) * pts;
+    R.counts[2] = k * NS;
+  }
+}
+
+// Position of quadrature point q: cell clist[q / ell^d], sub-point q % ell^d
+// (lexicographic, last axis fastest), at (c + (j + 1/2) / ell) dx.
+template <int D>
+__device__ __forceinline__ void eul_point(const RomDev& R, int q, float x[D]) {
+  int pts = 1;
+#pragma unroll
+  for (int a = 0; a < D; ++a) pts *= R.ell;
+  int rem = R.clist[q / pts];
+  int sub = q % pts;
+  int c[D], j[D];
+#pragma unroll
+  for (int a = D - 1; a >= 0; --a) {
+    c[a] = rem % R.n;
+    rem /= R.n;
+    j[a] = sub % R.ell;
+    sub /= R.ell;
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) x[a] = ((float)c[a] + ((float)j[a] + 0.5f) / (float)R.ell) * R.dx;
+}
+
+// Initial reference positions: the point minus the samples' mean displacement.
+template <int D>
+__global__ void __launch_bounds__(1024) rom_eul_guess(RomDev R) {
+  __shared__ float s_sum[32][3];
+  __shared__ float s_mean[3];
+  const int t = threadIdx.x, T = blockDim.x, lane = t & 31, warp = t >> 5;
+  const int k = R.counts[0];
+  float acc[3] = {0.f, 0.f, 0.f};
+  for (int i = t; i < k; i += T) {
+    const int pid = R.qlist[i];
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] += R.x_samp[(size_t)i * D + a] - R.X[(size_t)pid * D + a];
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+    if (lane == 0) s_sum[warp][a] = acc[a];
+  }
+  __syncthreads();
+  if (t < D) {
+    float sm = 0.f;
+    for (int w = 0; w < T / 32; ++w) sm += s_sum[w][t];
+    s_mean[t] = sm / (float)max(k, 1);
+  }
+  __syncthreads();
+  const int nq = R.counts[1];
+  for (int q = t; q < nq; q += T) {
+    float x[D];
+    eul_point<D>(R, q, x);
+#pragma unroll
+    for (int a = 0; a < D; ++a) R.qX[(size_t)q * D + a] = x[a] - s_mean[a];
+  }
+}
+
+// One Newton step of the decoder inversion, X <- X - (dg/dX)^-1 (g(X) - x_q), from
+// decoder rows [primal, dX_0 .. dX_{d-1}] at X.
+template <int D>
+__global__ void rom_eul_newton(RomDev R, const float* __restrict__ dec, int64_t cap) {
+  const int nq = R.counts[1];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    float x[D], F[D * D], Fi[D * D], r[D];
+    eul_point<D>(R, q, x);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      r[a] = dec[(size_t)q * D + a] - x[a];
+#pragma unroll
+      for (int b = 0; b < D; ++b) F[a * D + b] = dec[((size_t)(1 + b) * cap + q) * D + a];
+    }
+    inverse<D>(F, Fi);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      float dX = 0.f;
+#pragma unroll
+      for (int b = 0; b < D; ++b) dX = fmaf(Fi[a * D + b], r[b], dX);
+      if (isfinite(dX)) R.qX[(size_t)q * D + a] -= dX;
+    }
+  }
+}
+
+// Mass, reference volume and local P2G of the Eulerian quadrature points (Algorithms 4 and 5).
+// dec rows [primal, dX_0 .. dX_{d-1}, JVP] at the points' final reference positions X.  A point
+// carries mass rho0 V_q / J and reference volume V_q / J when X lies in the reference domain (the
+// occupancy boxes) and the inversion converged (|g(X) - x_q| < tol); otherwise none.  Stress from
+// F = dg/dX, C = 0, assembled onto the nodes of the basis set only.
+template <int D, int MATERIAL, int TRANSFER>
+__global__ void rom_eul_p2g(RomDev R, const float* __restrict__ dec, int64_t cap, float tol) {
+  const int nq = R.counts[1];
+  const uint32_t stamp = (uint32_t)(*R.step + 1);
+  float Vq = 1.f;
+#pragma unroll
+  for (int a = 0; a < D; ++a) Vq *= R.dx / (float)R.ell;
+  const float rho0 = R.mass / R.vol;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    float x[D], v[D], F[D * D];
+    eul_point<D>(R, q, x);
+    float res2 = 0.f;
+    bool inside = true;
+    int lin = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const float r = dec[(size_t)q * D + a] - x[a];
+      res2 = fmaf(r, r, res2);
+      v[a] = dec[((size_t)(1 + D) * cap + q) * D + a];
+#pragma unroll
+      for (int b = 0; b < D; ++b) F[a * D + b] = dec[((size_t)(1 + b) * cap + q) * D + a];
+      const float ib = floorf((R.qX[(size_t)q * D + a] - R.occ_origin[a]) / R.occ_h);
+      inside &= (ib >= 0.f) & (ib < (float)R.occ_shape[a]);
+      lin = lin * R.occ_shape[a] + (inside ? (int)ib : 0);
+    }
+    inside = inside && R.occ[lin] != 0;
+    const float J = det_minus_one<D>(F) + 1.0f;
+    const bool ok = inside && (res2 < tol * tol) && (J > 0.f) && isfinite(J);
+    const float V0 = ok ? Vq / J : 0.f;
+    const float mq = ok ? rho0 * V0 : 0.f;
+    R.qV0[q] = V0;
+    R.qm[q] = mq;
+    if (!ok) continue;
+    float tau[D * D];
+    kirchhoff<D, MATERIAL, POLAR_FP64>(F, R.mu, R.lam, tau);
+    int base[D];
+    float w[D][3], dw[D][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      base[a] = stencil_base(x[a], R.inv_dx);
+      const float fx = x[a] * R.inv_dx - (float)base[a];
+      bspline_w(fx, w[a]);
+      bspline_dw(fx, dw[a]);
+    }
+    constexpr int NS = (D == 2) ? 9 : 27;
+    const float kml = R.dt * V0 * 4.0f * R.inv_dx * R.inv_dx;
+#pragma unroll 1
+    for (int s = 0; s < NS; ++s) {
+      int off[D];
+      off[0] = (D == 2 ? s / 3 : s / 9);
+      off[D - 1] = s % 3;
+      if (D == 3) off[1] = (s / 3) % 3;
+      int node[D];
+      float wt = 1.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        node[a] = base[a] + off[a];
+        wt *= w[a][off[a]];
+      }
+      const int l = node_linear<D>(node, R.n);
+      if (R.stamp[l] != stamp) continue;   // only the basis set I is assembled
+      float mom[D];
+      if (TRANSFER == MPM_TRANSFER_MLS) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float qq = mq * v[a];
+#pragma unroll
+          for (int b = 0; b < D; ++b) qq = fmaf(-kml * tau[a * D + b], (float)node[b] * R.dx - x[b], qq);
+          mom[a] = wt * qq;
+        }
+      } else {
+        float grad[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float gg = dw[a][off[a]] * R.inv_dx;
+#pragma unroll
+          for (int b = 0; b < D; ++b)
+            if (b != a) gg *= w[b][off[b]];
+          grad[a] = gg;
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float f = 0.f;
+#pragma unroll
+          for (int b = 0; b < D; ++b) f = fmaf(tau[a * D + b], grad[b], f);
+          mom[a] = wt * mq * v[a] - R.dt * V0 * f;
+        }
+      }
+      atomicAdd(&R.grid[l], make_float4(wt * mq, mom[0], D > 1 ? mom[1] : 0.f, D > 2 ? mom[D - 1] : 0.f));
+    }
+  }
+}
+
 // ---------------------------------------- grid update + G2P to the samples
 template <int D>
 __global__ void rom_g2p(RomDev R) {
@@ -498,7 +768,7 @@ __global__ void rom_g2p(RomDev R) {
     int base[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      x[a] = R.x_all[(size_t)pid * D + a];
+      x[a] = R.x_samp ? R.x_samp[(size_t)i * D + a] : R.x_all[(size_t)pid * D + a];
       base[a] = min(max(stencil_base(x[a], R.inv_dx), 0), R.n - 3);
       bspline_w(x[a] * R.inv_dx - (float)base[a], w[a]);
     }
@@ -942,21 +1212,29 @@ struct rom_ctx {
   double* solve_mem = nullptr;
   float* solve32 = nullptr;
   uint32_t* counters = nullptr;
+  // Eulerian quadrature (Algorithm 4)
+  bool eulerian = false;
+  int ell = 0, newton_iters = 0;
+  float newton_tol = 0.f;
+  int64_t cap_q = 0;            // quadrature-point capacity (cells x ell^d)
+  uint32_t* cstamp = nullptr;
+  int32_t* clist = nullptr;
+  float* qX = nullptr;
+  float* qm = nullptr;
+  float* qV0 = nullptr;
+  uint8_t* occ = nullptr;
+  float* outE = nullptr;        // (d + 2, cap_q, d) decoder rows at the quadrature points
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
 };
 
 namespace {
 
-mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
-  const int d = c->d, r = c->r;
-  const bool affine = c->cfg.affine && c->cfg.transfer == MPM_TRANSFER_MLS;
-  int kq[8];
-  kq[0] = 0;
-  for (int a = 0; a < d; ++a) kq[1 + a] = 1 + a;
-  kq[1 + d] = 1000;  // JVP along vhat_n
-  for (int a = 0; a < d; ++a) kq[2 + d + a] = 2000 + 1 + a;  // d/dX_a of the JVP
-  const int Rq = affine ? 2 * d + 2 : d + 2;
+// Lagrangian quadrature (Algorithm 3): decoded positions, samples, basis and neighbour sets, F
+// and v at the quadrature points, local P2G onto the basis set.
+mpm_status rom_launch_lagrangian(rom_ctx* c, const int* kq, int Rq, bool affine, cudaStream_t s) {
+  const int d = c->d;
+  const int M = c->cfg.material, T = c->cfg.transfer;
   mpm_status st = MPM_OK;
   if (c->merged) {
     // 1 + 3. one decode of every particle with the quadrature rows: positions (x_all is its
@@ -981,9 +1259,8 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
                             s);
     if (st != MPM_OK) return st;
   }
-  // 4. local P2G onto I, 5. grid update + G2P to the samples
+  // 4. local P2G onto I
   const int b_q = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 4));
-  const int M = c->cfg.material, T = c->cfg.transfer;
 #define P2G_CASE(dd, mm, tt)                                                                     \
   if (d == dd && M == mm && T == tt) {                                                           \
     if (affine)                                                                                  \
@@ -995,19 +1272,84 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
   P2G_CASE(3, 0, 0) P2G_CASE(3, 0, 1) P2G_CASE(3, 1, 0) P2G_CASE(3, 1, 1)
 #undef P2G_CASE
   MPM_CUDA_TRY(cudaGetLastError());
+  return MPM_OK;
+}
+
+mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
+  const int d = c->d, r = c->r;
+  const bool affine = c->cfg.affine && c->cfg.transfer == MPM_TRANSFER_MLS;
+  int kq[8];
+  kq[0] = 0;
+  for (int a = 0; a < d; ++a) kq[1 + a] = 1 + a;
+  kq[1 + d] = 1000;  // JVP along vhat_n
+  for (int a = 0; a < d; ++a) kq[2 + d + a] = 2000 + 1 + a;  // d/dX_a of the JVP
+  const int Rq = affine ? 2 * d + 2 : d + 2;
+  mpm_status st = MPM_OK;
+  int ks[kMaxRl + 2];
+  ks[0] = 0;
+  for (int j = 0; j < r; ++j) ks[1 + j] = 1 + d + j;
   const int b_s = std::max(1, ceil_div(c->k, 128));
+  const int b_ne = std::max(1, std::min(ceil_div((int64_t)c->k * d, 64), 64));
+  const int M = c->cfg.material, T = c->cfg.transfer;
+  if (c->eulerian) {
+    // Algorithm 4.  1. samples
+    if (d == 2)
+      rom_select<2><<<1, 1024, 0, s>>>(c->dv);
+    else
+      rom_select<3><<<1, 1024, 0, s>>>(c->dv);
+    MPM_CUDA_TRY(cudaGetLastError());
+    // 2. positions and latent Jacobian at the samples (the rows of the velocity projection)
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xh32, nullptr, ks, r + 1, c->outS,
+                            s);
+    if (st != MPM_OK) return st;
+    // 3. basis set, quadrature cells and points, initial reference positions
+    if (d == 2) {
+      rom_eul_cells<2><<<1, 1024, 0, s>>>(c->dv);
+      rom_eul_guess<2><<<1, 1024, 0, s>>>(c->dv);
+    } else {
+      rom_eul_cells<3><<<1, 1024, 0, s>>>(c->dv);
+      rom_eul_guess<3><<<1, 1024, 0, s>>>(c->dv);
+    }
+    MPM_CUDA_TRY(cudaGetLastError());
+    // 4. Newton inversion of the decoder at the points
+    const int b_e = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c->cap_q, (int64_t)256), c->n_sm * 4));
+    int kn[4] = {0, 1, 2, 3};
+    for (int it = 0; it < c->newton_iters; ++it) {
+      st = decoder_launch_dev(c->dec, c->qX, nullptr, c->counts + 1, 1, c->cap_q, c->sv.xh32, nullptr, kn, 1 + d,
+                              c->outE, s);
+      if (st != MPM_OK) return st;
+      if (d == 2)
+        rom_eul_newton<2><<<b_e, 256, 0, s>>>(c->dv, c->outE, c->cap_q);
+      else
+        rom_eul_newton<3><<<b_e, 256, 0, s>>>(c->dv, c->outE, c->cap_q);
+      MPM_CUDA_TRY(cudaGetLastError());
+    }
+    // 5. F, v at the final reference positions; mass; local P2G onto I
+    st = decoder_launch_dev(c->dec, c->qX, nullptr, c->counts + 1, 1, c->cap_q, c->sv.xh32, c->sv.vh32, kq, d + 2,
+                            c->outE, s);
+    if (st != MPM_OK) return st;
+    const float tol = c->newton_tol * c->cfg.dx;
+#define EUL_CASE(dd, mm, tt) \
+    if (d == dd && M == mm && T == tt) rom_eul_p2g<dd, mm, tt><<<b_e, 256, 0, s>>>(c->dv, c->outE, c->cap_q, tol);
+    EUL_CASE(2, 0, 0) EUL_CASE(2, 0, 1) EUL_CASE(2, 1, 0) EUL_CASE(2, 1, 1)
+    EUL_CASE(3, 0, 0) EUL_CASE(3, 0, 1) EUL_CASE(3, 1, 0) EUL_CASE(3, 1, 1)
+#undef EUL_CASE
+    MPM_CUDA_TRY(cudaGetLastError());
+  } else {
+    st = rom_launch_lagrangian(c, kq, Rq, affine, s);
+    if (st != MPM_OK) return st;
+  }
   if (d == 2)
     rom_g2p<2><<<b_s, 128, 0, s>>>(c->dv);
   else
     rom_g2p<3><<<b_s, 128, 0, s>>>(c->dv);
   MPM_CUDA_TRY(cudaGetLastError());
-  // 6. velocity projection: J = dg/dxhat at (X^P, xhat_n)
-  int ks[kMaxRl + 2];
-  ks[0] = 0;
-  for (int j = 0; j < r; ++j) ks[1 + j] = 1 + d + j;
-  st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xh32, nullptr, ks, r + 1, c->outS, s);
-  if (st != MPM_OK) return st;
-  const int b_ne = std::max(1, std::min(ceil_div((int64_t)c->k * d, 64), 64));
+  // 6. velocity projection: J = dg/dxhat at (X^P, xhat_n) (decoded in step 2 with the Eulerian quadrature)
+  if (!c->eulerian) {
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xh32, nullptr, ks, r + 1, c->outS,
+                            s);
+    if (st != MPM_OK) return st;
+  }
   rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_VEL, nullptr, c->cfg.projection, 0,
                                          c->cfg.ridge);
   MPM_CUDA_TRY(cudaGetLastError());
@@ -1064,6 +1406,12 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   MPM_CHECK_ARG(cfg->ridge >= 0.f, "ridge >= 0");
   MPM_CHECK_ARG(cfg->affine == 0 || cfg->affine == 1, "affine: 0 or 1");
   MPM_CHECK_ARG(cfg->f_reference == 0 || cfg->f_reference == 1, "f_reference: 0 or 1");
+  MPM_CHECK_ARG(cfg->quadrature == 0 || cfg->quadrature == 1, "quadrature: 0 Lagrangian, 1 Eulerian");
+  MPM_CHECK_ARG(cfg->ell >= 0 && cfg->ell <= 4, "ell in [1, 4] (0: default 2)");
+  MPM_CHECK_ARG(cfg->newton_iters >= 0 && cfg->newton_iters <= 16, "newton_iters in [1, 16] (0: default 4)");
+  MPM_CHECK_ARG(cfg->newton_tol >= 0.f, "newton_tol >= 0 (0: default 1e-3)");
+  MPM_CHECK_ARG(!(cfg->quadrature == 1 && cfg->f_reference == 1), "f_reference needs the Lagrangian quadrature");
+  MPM_CHECK_ARG(!(cfg->quadrature == 1 && cfg->affine == 1), "affine needs the Lagrangian quadrature");
   auto* c = new rom_ctx();
   c->cfg = *cfg;
   c->dec = dec;
@@ -1102,7 +1450,8 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   }
   // one decode of all particles per step when the neighbourhood of the samples covers most of
   // the body anyway (2D: a sample's neighbourhood spans 5 x 5 cells, ~100 particles at 4 per cell)
-  c->merged = (int64_t)P <= 32 * (int64_t)c->k;
+  c->eulerian = cfg->quadrature == 1;
+  c->merged = !c->eulerian && (int64_t)P <= 32 * (int64_t)c->k;
   c->x_all = c->merged ? c->outQ : c->x_all_buf;
   if ((st = ralloc(&c->outS, (size_t)(r + 2) * P * d)) != MPM_OK) return fail(st);
   if ((st = ralloc(&c->outLS, (size_t)2 * kLS * P * d)) != MPM_OK) return fail(st);
@@ -1114,6 +1463,68 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   MPM_CUDA_TRY(cudaMemcpy(c->X, X, sizeof(float) * P * d, cudaMemcpyDefault));
   MPM_CUDA_TRY(cudaMemcpy(c->nP_all, &c->P, sizeof(int32_t), cudaMemcpyHostToDevice));
   RomDev& v = c->dv;
+  if (c->eulerian) {
+    c->ell = cfg->ell ? cfg->ell : 2;
+    c->newton_iters = cfg->newton_iters ? cfg->newton_iters : 4;
+    c->newton_tol = cfg->newton_tol > 0.f ? cfg->newton_tol : 1e-3f;
+    // quadrature cells: the union over samples of the 6^d cells around their 3^d stencil nodes
+    int64_t cells_grid = 1, cells_samp = k, pts = 1;
+    for (int a = 0; a < d; ++a) {
+      cells_grid *= c->n - 3;
+      cells_samp *= 6;
+      pts *= c->ell;
+    }
+    const int64_t cap_cells = std::min(cells_grid, cells_samp);
+    c->cap_q = cap_cells * pts;
+    MPM_CHECK_ARG(c->cap_q < (int64_t)1 << 30, "quadrature-point capacity");
+    if ((st = ralloc(&c->cstamp, gn)) != MPM_OK) return fail(st);
+    if ((st = ralloc(&c->clist, (size_t)cap_cells)) != MPM_OK) return fail(st);
+    if ((st = ralloc(&c->qX, (size_t)c->cap_q * d)) != MPM_OK) return fail(st);
+    if ((st = ralloc(&c->qm, (size_t)c->cap_q)) != MPM_OK) return fail(st);
+    if ((st = ralloc(&c->qV0, (size_t)c->cap_q)) != MPM_OK) return fail(st);
+    if ((st = ralloc(&c->outE, (size_t)(d + 2) * c->cap_q * d)) != MPM_OK) return fail(st);
+    // reference domain: union of the particles' volume boxes of side h = V0^(1/d) centred on X,
+    // as occupancy flags of a box grid of spacing h from origin = min X - h / 2
+    std::vector<float> hX((size_t)P * d);
+    MPM_CUDA_TRY(cudaMemcpy(hX.data(), c->X, sizeof(float) * P * d, cudaMemcpyDeviceToHost));
+    const double h = std::pow((double)cfg->p_vol, 1.0 / d);
+    double lo[3] = {0, 0, 0};
+    int64_t shape[3] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) {
+      lo[a] = hX[a];
+      for (int p = 0; p < P; ++p) lo[a] = std::min(lo[a], (double)hX[(size_t)p * d + a]);
+      lo[a] -= 0.5 * h;
+      int64_t mx = 0;
+      for (int p = 0; p < P; ++p) mx = std::max<int64_t>(mx, (int64_t)std::floor(((double)hX[(size_t)p * d + a] - lo[a]) / h));
+      shape[a] = mx + 1;
+    }
+    const int64_t n_occ = shape[0] * shape[1] * shape[2];
+    MPM_CHECK_ARG(n_occ <= ((int64_t)1 << 28), "reference occupancy grid too large (particle volume vs extent)");
+    std::vector<uint8_t> occ((size_t)n_occ, 0);
+    for (int p = 0; p < P; ++p) {
+      int64_t lin = 0;
+      for (int a = 0; a < d; ++a)
+        lin = lin * shape[a] + (int64_t)std::floor(((double)hX[(size_t)p * d + a] - lo[a]) / h);
+      occ[(size_t)lin] = 1;
+    }
+    if ((st = ralloc(&c->occ, (size_t)n_occ)) != MPM_OK) return fail(st);
+    MPM_CUDA_TRY(cudaMemcpy(c->occ, occ.data(), (size_t)n_occ, cudaMemcpyHostToDevice));
+    v.eulerian = 1;
+    v.ell = c->ell;
+    v.x_samp = c->outS;   // primal block of the sample decode
+    v.cstamp = c->cstamp;
+    v.clist = c->clist;
+    v.cap_cells = (int)cap_cells;
+    v.qX = c->qX;
+    v.qm = c->qm;
+    v.qV0 = c->qV0;
+    v.occ = c->occ;
+    for (int a = 0; a < 3; ++a) {
+      v.occ_origin[a] = (float)lo[a];
+      v.occ_shape[a] = (int)shape[a];
+    }
+    v.occ_h = (float)h;
+  }
   v.d = d;
   v.r = r;
   v.P = P;
@@ -1174,6 +1585,13 @@ void rom_destroy(rom_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->X);
   cudaFree(c->x_all_buf);
+  cudaFree(c->cstamp);
+  cudaFree(c->clist);
+  cudaFree(c->qX);
+  cudaFree(c->qm);
+  cudaFree(c->qV0);
+  cudaFree(c->occ);
+  cudaFree(c->outE);
   cudaFree(c->qlist);
   cudaFree(c->counts);
   cudaFree(c->nodes);
@@ -1216,6 +1634,12 @@ mpm_status rom_set_state(rom_ctx* c, const double* xhat, const double* vhat, con
   MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.xh32, h32.data(), sizeof(float) * r, cudaMemcpyHostToDevice, s));
   MPM_CUDA_TRY(cudaMemcpyAsync(c->sv.vh32, h32.data() + r, sizeof(float) * r, cudaMemcpyHostToDevice, s));
   MPM_CUDA_TRY(cudaMemcpyAsync(c->step, &step, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  // a new step index may repeat stamps of an earlier run: start from an empty grid
+  const size_t gn = c->d == 2 ? (size_t)c->n * c->n : (size_t)c->n * c->n * c->n;
+  MPM_CUDA_TRY(cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * gn, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->grid, 0, sizeof(float4) * gn, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4, s));
+  if (c->cstamp) MPM_CUDA_TRY(cudaMemsetAsync(c->cstamp, 0, sizeof(uint32_t) * gn, s));
   MPM_CUDA_TRY(cudaStreamSynchronize(s));
   return MPM_OK;
 }
@@ -1276,6 +1700,46 @@ mpm_status rom_debug(rom_ctx* c, int32_t* qlist, int32_t* counts, float* x_all, 
   if (x_all) MPM_CUDA_TRY(cudaMemcpyAsync(x_all, c->x_all, sizeof(float) * c->P * c->d, cudaMemcpyDefault, s));
   if (v_trial) MPM_CUDA_TRY(cudaMemcpyAsync(v_trial, c->v_trial, sizeof(float) * c->k * c->d, cudaMemcpyDefault, s));
   if (x_trial) MPM_CUDA_TRY(cudaMemcpyAsync(x_trial, c->x_trial, sizeof(float) * c->k * c->d, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return MPM_OK;
+}
+
+mpm_status rom_debug_quadrature(rom_ctx* c, int32_t* n_points, float* x_points, float* X_points, float* mass,
+                                float* V0, void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  MPM_CHECK_ARG(c->eulerian, "rom_debug_quadrature needs the Eulerian quadrature");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t cnt[2] = {0, 0};
+  MPM_CUDA_TRY(cudaMemcpyAsync(cnt, c->counts, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  const int64_t nq = cnt[1];
+  if (n_points) *n_points = (int32_t)nq;
+  if (X_points) MPM_CUDA_TRY(cudaMemcpyAsync(X_points, c->qX, sizeof(float) * nq * c->d, cudaMemcpyDefault, s));
+  if (mass) MPM_CUDA_TRY(cudaMemcpyAsync(mass, c->qm, sizeof(float) * nq, cudaMemcpyDefault, s));
+  if (V0) MPM_CUDA_TRY(cudaMemcpyAsync(V0, c->qV0, sizeof(float) * nq, cudaMemcpyDefault, s));
+  if (x_points) {
+    // cell ids, expanded on the host into the points' positions (c + (j + 1/2) / ell) dx
+    const int d = c->d, ell = c->ell;
+    int pts = 1;
+    for (int a = 0; a < d; ++a) pts *= ell;
+    std::vector<int32_t> cells((size_t)(nq / pts));
+    MPM_CUDA_TRY(cudaMemcpyAsync(cells.data(), c->clist, sizeof(int32_t) * cells.size(), cudaMemcpyDeviceToHost, s));
+    MPM_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<float> xp((size_t)nq * d);
+    for (int64_t q = 0; q < nq; ++q) {
+      int rem = cells[(size_t)(q / pts)], sub = (int)(q % pts);
+      int cc[3], jj[3];
+      for (int a = d - 1; a >= 0; --a) {
+        cc[a] = rem % c->n;
+        rem /= c->n;
+        jj[a] = sub % ell;
+        sub /= ell;
+      }
+      for (int a = 0; a < d; ++a)
+        xp[(size_t)q * d + a] = ((float)cc[a] + ((float)jj[a] + 0.5f) / (float)ell) * c->cfg.dx;
+    }
+    MPM_CUDA_TRY(cudaMemcpyAsync(x_points, xp.data(), sizeof(float) * nq * d, cudaMemcpyDefault, s));
+  }
   MPM_CUDA_TRY(cudaStreamSynchronize(s));
   return MPM_OK;
 }

@@ -88,12 +88,13 @@ def fom_positions(scene, steps, device="cuda"):
 
 
 def rom_error(decoder, scene, fom_xs, *, n_samples=256, seed=4, gn_iters=3, projection=0, fit_iters=20, ridge=0.0,
-              affine=0, f_reference=0, checkpoints=()):
+              affine=0, f_reference=0, quadrature=0, ell=0, newton_iters=0, checkpoints=()):
     """Runs the reduced model from the least-squares initial condition (Eq. essentialSpecInt) for as
     many steps as fom_xs has, accumulating the Section 5 error on the device."""
     steps = fom_xs.shape[0] - 1
     rom = ROM.from_scene(decoder, scene, n_samples=n_samples, seed=seed, gn_iters=gn_iters, projection=projection,
-                         ridge=ridge, affine=affine, f_reference=f_reference)
+                         ridge=ridge, affine=affine, f_reference=f_reference, quadrature=quadrature, ell=ell,
+                         newton_iters=newton_iters)
     rom.fit_initial(scene.x, scene.v, iters=fit_iters)
     acc = torch.zeros(2, dtype=torch.float64, device="cuda")
     xr = torch.empty_like(fom_xs[0])

@@ -26,12 +26,14 @@ class ROM:
 
     def __init__(self, decoder, X, *, dim, n_grid, dx, dt, gravity, bc, bc_width, material, transfer, rho,
                  p_vol, E, nu, n_samples, seed, instance=0, gn_iters=3, projection=0, ridge=0.0, affine=0,
-                 f_reference=0):
+                 f_reference=0, quadrature=0, ell=0, newton_iters=0, newton_tol=0.0):
         L = _abi.lib()
         g = (C.c_float * 3)(*[float(v) for v in gravity])
         self.cfg = _abi.RomConfig(dim, n_grid, dx, dt, g, bc, bc_width, material, transfer, rho, p_vol, E, nu,
                                   decoder.r, n_samples, seed, instance, gn_iters, projection, ridge, affine,
-                                  f_reference)
+                                  f_reference, quadrature, ell, newton_iters, newton_tol)
+        self.eulerian = bool(quadrature)
+        self.ell = int(ell or 2)
         self._X = np.ascontiguousarray(X, np.float32) if isinstance(X, np.ndarray) else X
         self.P = int(self._X.shape[0])
         self.d, self.r = dim, decoder.r
@@ -43,13 +45,14 @@ class ROM:
 
     @classmethod
     def from_scene(cls, decoder, sc, n_samples, seed, instance=0, gn_iters=3, projection=0, X=None, ridge=0.0,
-                   affine=0, f_reference=0):
+                   affine=0, f_reference=0, quadrature=0, ell=0, newton_iters=0, newton_tol=0.0):
         k = 0
         return cls(decoder, sc.x if X is None else X, dim=sc.dim, n_grid=sc.n_grid, dx=sc.dx, dt=sc.dt,
                    gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width, material=sc.material,
                    transfer=sc.transfer, rho=sc.rho, p_vol=sc.p_vol, E=float(sc.E[k]), nu=float(sc.nu[k]),
                    n_samples=n_samples, seed=seed, instance=instance, gn_iters=gn_iters, projection=projection,
-                   ridge=ridge, affine=affine, f_reference=f_reference)
+                   ridge=ridge, affine=affine, f_reference=f_reference, quadrature=quadrature, ell=ell,
+                   newton_iters=newton_iters, newton_tol=newton_tol)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -101,7 +104,23 @@ class ROM:
         xt = np.empty((self.n_samples, self.d), np.float32)
         _abi.check(_abi.lib().rom_debug(self._h, _ptr(q), _ptr(cnt), _ptr(xa), _ptr(vt), _ptr(xt), _stream(stream)))
         nP, nQ = int(cnt[0]), int(cnt[1])
+        if self.eulerian:
+            return dict(samples=q[:nP].copy(), neigh=q[:0].copy(), n_points=nQ, v_trial=vt, x_trial=xt)
         return dict(samples=q[:nP].copy(), neigh=q[nP:nQ].copy(), x_all=xa, v_trial=vt, x_trial=xt)
+
+    def quadrature_points(self, stream=None):
+        """Eulerian quadrature of the last step: dict of x (points), X (reference positions), mass, V0."""
+        d, n = self.d, self.cfg.n_grid
+        cap = min((n - 3) ** d, 6 ** d * self.n_samples) * self.ell ** d
+        x = np.empty((cap, d), np.float32)
+        X = np.empty((cap, d), np.float32)
+        m = np.empty(cap, np.float32)
+        v0 = np.empty(cap, np.float32)
+        nq = C.c_int32()
+        _abi.check(_abi.lib().rom_debug_quadrature(self._h, C.byref(nq), _ptr(x), _ptr(X), _ptr(m), _ptr(v0),
+                                                   _stream(stream)))
+        k = nq.value
+        return dict(x=x[:k].copy(), X=X[:k].copy(), mass=m[:k].copy(), V0=v0[:k].copy())
 
     def decode_all(self, out=None, stream=None):
         if out is None:

@@ -235,3 +235,26 @@ def xavier_decoder(seed: int, d: int, r: int, width: int = 128, n_hidden: int = 
         X_range=np.ones(d) if X_range is None else np.asarray(X_range, np.float64),
         out_shift=np.zeros(d) if out_shift is None else np.asarray(out_shift, np.float64),
         out_scale=np.ones(d) if out_scale is None else np.asarray(out_scale, np.float64))
+
+
+def near_identity_decoder(seed: int, d: int, r: int, n_hidden: int = 1, X_min=None, X_range=None,
+                          eps: float = 1e-3, width: int = 128) -> DecoderParams:
+    """ELU network whose output is X plus a small nonlinear function of (X, xhat).
+
+    The first d hidden units of every layer carry the normalised inputs X_n + 1 (positive, so the
+    ELU passes them through); the output layer maps them back to X.  The remaining units are
+    Xavier-initialised and enter the output with weights of size eps, so dg/dX = I + O(eps / X_range)
+    and the decoded motion stays invertible (a configuration the inversion of the decoder and the
+    reference-domain test see in a deformed body)."""
+    p = xavier_decoder(seed, d, r, width, n_hidden, 0, X_min=X_min, X_range=X_range, bias_scale=0.2)
+    rng = np.random.default_rng(seed + 1)
+    for l in range(n_hidden):
+        W, b = p.W[l], p.b[l]
+        W[:d, :] = 0.0
+        W[:d, :d] = np.eye(d)
+        b[:d] = 1.0 if l == 0 else 0.0
+    Wo = p.W[-1]
+    Wo[:, :] = eps * rng.uniform(-1, 1, size=Wo.shape)
+    Wo[:, :d] = np.diag(p.X_range)
+    p.b[-1][:] = p.X_min - p.X_range
+    return p
