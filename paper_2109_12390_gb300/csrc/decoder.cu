@@ -326,16 +326,24 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 // --------------------------------------------------------------------------
 // FP32 decoder on the CUDA cores, for calls whose rows are too few to keep the
 // tensor cores busy and whose results need FP32 accuracy (the reduced step's
-// positions and gradients).  Same 128-row tiles and row kinds as decoder_tc;
-// each square layer is a 128 x 128 x 128 FP32 GEMM from shared memory (thread
-// (ty, tx) computes rows 8 ty .. 8 ty + 7 x features 8 tx .. 8 tx + 7), the
-// layer's weights streamed into shared memory transposed.  Pre-activations are
-// exchanged through shared memory for the derivative rows exactly as in the
-// tensor-core kernel, all in FP32.
+// positions and gradients).  Same row kinds as decoder_tc, in tiles of 64 rows
+// (Pt = 64 / R points), one persistent CTA of 512 threads (16 warps) per SM.
+//   layer 0       thread = one row x 16 columns; inputs staged in shared memory
+//   square layer  128 x 64 x 128 FP32 GEMM from shared memory, thread = 4 rows
+//                 (one group per warp) x 4 consecutive features; weights
+//                 double-buffered from a transposed copy by asynchronous copies
+//   exchange      pre-activations to a second buffer (row-major), derivative rows
+//                 read the primal (and, for mixed rows, JVP and tangent) rows'
+//                 values as float4 of the thread's own 4 features
+//   output layer  8 threads per row, interleaved k, shuffle reduction
+// Activations (the GEMM's input) are stored feature-major, [f][64 rows], the
+// rows in float4 groups permuted per feature (group g of feature f at slot
+// g ^ (f & 15)) so that the feature-strided stores of a warp spread over the
+// banks.  Two barriers per square layer.
 // --------------------------------------------------------------------------
-constexpr int kF32Threads = 256;
+constexpr int kF32Threads = 512;
 constexpr int kF32Rows = 64;              // rows per tile of the FP32 path
-constexpr int kATStride = kF32Rows + 4;   // AT row stride: float4-aligned
+constexpr int kF32In = 41;                // staged input row stride (d + r <= 40)
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
@@ -351,156 +359,194 @@ __device__ __forceinline__ float act_f32path(int act, float z) {
   return act == 0 ? (z > 0.f ? z : __expf(z) - 1.0f) : z;
 }
 
-// Tiles of kF32Rows = 64 rows (Pt = 64 / R points): twice as many CTAs as the
-// tensor-core tiling for a given call, which is what the small calls of the
-// reduced step need.  Thread (ty, tx) owns rows 8 ty .. 8 ty + 7 and features
-// tx + 32 i (i < 4) of each square layer.
+// Offset of (feature f, tile row) in an activation buffer.
+__device__ __forceinline__ int f32_slot(int f, int row) { return f * kF32Rows + 4 * ((row >> 2) ^ (f & 15)) + (row & 3); }
+
+// Activation of a derivative row from its own pre-activation zo, the primal row's zq and, for a
+// mixed row, the JVP row's za and the tangent row's zb (same point, same feature).
+__device__ __forceinline__ float f32_deriv_act(int act, int cls, float zo, float zq, float za, float zb) {
+  if (cls == 1) return act_d1(act, zq) * zo;
+  if (cls == 2) return act_sec(act, zq, zo);
+  return act_d2(act, zq) * za * zb + act_d1(act, zq) * zo;
+}
+
 __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   extern __shared__ __align__(16) float fsm[];
-  float* AT = fsm;                        // [128 k][kATStride] activations / pre-activations, transposed
-  float* Wt0 = AT + kW * kATStride;       // two [128 in][128 out] weight buffers, transposed
-  float* sW0 = Wt0 + 2 * kW * kW;         // [128][kW0Stride]
-  float* sb0 = sW0 + kW * kW0Stride;      // [128]
+  float* A0 = fsm;                        // [128 f][64 rows] activations (GEMM input)
+  float* A1 = A0 + kW * kF32Rows;         // [64 rows][128 f] pre-activations; staged inputs at layer 0
+  float* Wt0 = A1 + kW * kF32Rows;        // two [128 in][128 out] weight buffers, transposed
+  float* W0T = Wt0 + 2 * kW * kW;         // [40 in][128 out] first layer, transposed
+  float* sb0 = W0T + kW0Stride * kW;      // [128]
   float* sbh = sb0 + kW;                  // [kMaxTC][128]
   float* sWout = sbh + kMaxTC * kW;       // [3][128]
+  float* IN = A1;                         // [64 rows][kF32In] normalised inputs (layer 0 only)
+  float* DIR = A1 + kF32Rows * kF32In;    // [64 rows][kF32In] input directions
   const int t = threadIdx.x;
   const int K0 = a.d + a.r;
-  for (int e = t; e < kW * kW0Stride; e += kF32Threads) {
-    const int c = e / kW0Stride, i = e % kW0Stride;
-    sW0[e] = i < K0 ? a.W0[c * K0 + i] : 0.f;
+  // constant operands: all loads issued before any is used
+#pragma unroll
+  for (int j = 0; j < (kW0Stride * kW) / kF32Threads; ++j) {
+    const int e = t + j * kF32Threads;   // e = i * 128 + c
+    const int i = e >> 7, c = e & (kW - 1);
+    if (i < K0) W0T[e] = a.W0[c * K0 + i];
   }
-  for (int e = t; e < kW; e += kF32Threads) sb0[e] = a.b0[e];
-  for (int e = t; e < a.n_tc * kW; e += kF32Threads) sbh[e] = a.bh[e];
-  for (int e = t; e < a.d * kW; e += kF32Threads) sWout[e] = a.Wout[e];
+  if (t < kW) sb0[t] = a.b0[t];
+  if (t < a.n_tc * kW) sbh[t] = a.bh[t];
+  if (t < a.d * kW) sWout[t] = a.Wout[t];
   // weights of square layer l into buffer l % 2 (asynchronous copy, waited before its GEMM)
   auto prefetch = [&](int l) {
     const float* src = a.wsqT + (size_t)l * kW * kW;
     float* dst = Wt0 + (l & 1) * kW * kW;
-    for (int e = t; e < kW * kW / 4; e += kF32Threads) cp_async16(dst + 4 * e, src + 4 * e);
+#pragma unroll
+    for (int j = 0; j < kW * kW / 4 / kF32Threads; ++j) {
+      const int e = t + j * kF32Threads;
+      cp_async16(dst + 4 * e, src + 4 * e);
+    }
     cp_async_commit();
   };
-  __syncthreads();
 
   const int64_t n_pts = dec_count(a);
   const int64_t n_tiles = (n_pts + a.Pt - 1) / a.Pt;
-  const int rw = t & (kF32Rows - 1), hq = t / kF32Rows;   // layer 0: row and column quarter
-  const int ty = t >> 5, tx = t & 31;                     // square layers
+  const int warp = t >> 5, lane = t & 31;
+  const int f0 = 4 * lane;                 // square layers: features f0 .. f0 + 3, rows 4 warp .. 4 warp + 3
+  const int rw = t & (kF32Rows - 1), cg = t >> 6;   // layer 0: row rw, columns 16 cg .. 16 cg + 15
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t first = tile * a.Pt;
     if (a.n_tc > 0) prefetch(0);
-    // ---- layer 0 (FP32), this thread's row and 32 columns
-    {
-      const RowInfo ri = row_info(a, rw, first, n_pts);
-      float in[40], dir[40];
-      if (ri.cls >= 0) row_inputs(a, ri, in, dir);
-      for (int c = 32 * hq; c < 32 * hq + 32; ++c) {
-        float hv = 0.f;
-        if (ri.cls >= 0) {
-          const float* w0r = sW0 + c * kW0Stride;
-          float z = sb0[c], zd = 0.f;
-#pragma unroll
-          for (int i4 = 0; i4 < kW0Stride / 4; ++i4) {
-            if (4 * i4 < K0) {
-              const float4 w = *reinterpret_cast<const float4*>(w0r + 4 * i4);
-              z = fmaf(w.x, in[4 * i4 + 0], z);
-              z = fmaf(w.y, in[4 * i4 + 1], z);
-              z = fmaf(w.z, in[4 * i4 + 2], z);
-              z = fmaf(w.w, in[4 * i4 + 3], z);
-              zd = fmaf(w.x, dir[4 * i4 + 0], zd);
-              zd = fmaf(w.y, dir[4 * i4 + 1], zd);
-              zd = fmaf(w.z, dir[4 * i4 + 2], zd);
-              zd = fmaf(w.w, dir[4 * i4 + 3], zd);
-            }
-          }
-          if (ri.cls == 0) hv = act_f32path(a.act, z);
-          else if (ri.cls == 1) hv = act_d1(a.act, z) * zd;
-          else if (ri.cls == 2) hv = act_sec(a.act, z, zd);
-          else hv = act_d2(a.act, z) * zd * mixed_t0(a, w0r, ri.kind);
-        }
-        AT[c * kATStride + rw] = hv;
-      }
-    }
-    // row bookkeeping of this thread's 8 GEMM rows
-    RowInfo rows[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) rows[j] = row_info(a, 8 * ty + j, first, n_pts);
-    for (int l = 0; l < a.n_tc; ++l) {
-      cp_async_wait_all();
-      __syncthreads();                                  // AT complete, weights of layer l landed
-      if (l + 1 < a.n_tc) prefetch(l + 1);              // overlaps the GEMM below
-      const float* Wt = Wt0 + (l & 1) * kW * kW;
-      float acc[8][4];
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
-#pragma unroll 4
-      for (int k = 0; k < kW; ++k) {
-        const float4 a0 = *reinterpret_cast<const float4*>(AT + k * kATStride + 8 * ty);
-        const float4 a1 = *reinterpret_cast<const float4*>(AT + k * kATStride + 8 * ty + 4);
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        float wv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) wv[i] = Wt[k * kW + tx + 32 * i];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(av[j], wv[i], acc[j][i]);
-      }
-      __syncthreads();                                  // every GEMM has read AT
-      // pre-activations (bias on primal rows) replace the activations in AT
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int f = tx + 32 * i;
-        float z[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) z[j] = acc[j][i] + (rows[j].cls == 0 ? sbh[l * kW + f] : 0.f);
-        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty) = make_float4(z[0], z[1], z[2], z[3]);
-        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty + 4) = make_float4(z[4], z[5], z[6], z[7]);
-      }
-      __syncthreads();
-      // activations of the next layer from the row's own and exchanged pre-activations (registers)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float* col = AT + (tx + 32 * i) * kATStride;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const RowInfo& ri = rows[j];
-          const float zo = col[8 * ty + j];
-          const float zq = col[ri.q];
-          float hv;
-          if (ri.cls == 0) hv = act_f32path(a.act, zo);
-          else if (ri.cls == 1) hv = act_d1(a.act, zq) * zo;
-          else if (ri.cls == 2) hv = act_sec(a.act, zq, zo);
-          else if (ri.cls == 3)
-            hv = act_d2(a.act, zq) * col[ri.ja * a.Pt + ri.q] * col[ri.jb * a.Pt + ri.q] + act_d1(a.act, zq) * zo;
-          else hv = 0.f;
-          acc[j][i] = hv;
-        }
-      }
-      __syncthreads();                                  // every pre-activation read
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int f = tx + 32 * i;
-        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty) = make_float4(acc[0][i], acc[1][i], acc[2][i], acc[3][i]);
-        *reinterpret_cast<float4*>(AT + f * kATStride + 8 * ty + 4) =
-            make_float4(acc[4][i], acc[5][i], acc[6][i], acc[7][i]);
-      }
+    // ---- inputs of the tile's rows
+    for (int e = t; e < kF32Rows * K0; e += kF32Threads) {
+      const int row = e / K0, i = e - row * K0;
+      const RowInfo ri = row_info(a, row, first, n_pts);
+      float vin = 0.f, vdir = 0.f;
+      if (ri.cls >= 0) row_input_elem(a, ri, i, vin, vdir);
+      IN[row * kF32In + i] = vin;
+      DIR[row * kF32In + i] = vdir;
     }
     __syncthreads();
-    // ---- output layer (FP32): 4 threads per row, k split in quarters and combined by shuffles
+    // ---- layer 0 (FP32)
     {
-      const int row = t >> 2, kq = t & 3;
+      const RowInfo ri = row_info(a, rw, first, n_pts);
+      float z[16], zd[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        z[c] = sb0[16 * cg + c];
+        zd[c] = 0.f;
+      }
+      for (int i = 0; i < K0; ++i) {
+        const float vin = IN[rw * kF32In + i], vdir = DIR[rw * kF32In + i];
+        const float4* w4 = reinterpret_cast<const float4*>(W0T + i * kW + 16 * cg);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 w = w4[q];
+          z[4 * q + 0] = fmaf(w.x, vin, z[4 * q + 0]);
+          z[4 * q + 1] = fmaf(w.y, vin, z[4 * q + 1]);
+          z[4 * q + 2] = fmaf(w.z, vin, z[4 * q + 2]);
+          z[4 * q + 3] = fmaf(w.w, vin, z[4 * q + 3]);
+          zd[4 * q + 0] = fmaf(w.x, vdir, zd[4 * q + 0]);
+          zd[4 * q + 1] = fmaf(w.y, vdir, zd[4 * q + 1]);
+          zd[4 * q + 2] = fmaf(w.z, vdir, zd[4 * q + 2]);
+          zd[4 * q + 3] = fmaf(w.w, vdir, zd[4 * q + 3]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int col = 16 * cg + c;
+        float hv = 0.f;
+        if (ri.cls == 0) hv = act_f32path(a.act, z[c]);
+        else if (ri.cls == 1) hv = act_d1(a.act, z[c]) * zd[c];
+        else if (ri.cls == 2) hv = act_sec(a.act, z[c], zd[c]);
+        else if (ri.cls == 3) {
+          const int b = ri.kind - KIND_MIXED - 1;
+          const float t0 = b < a.d ? W0T[b * kW + col] / a.norm[a.d + b] : W0T[b * kW + col];
+          hv = act_d2(a.act, z[c]) * zd[c] * t0;
+        }
+        A0[f32_slot(col, rw)] = hv;
+      }
+    }
+    // row bookkeeping of this warp's 4 GEMM rows
+    RowInfo rows[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) rows[j] = row_info(a, 4 * warp + j, first, n_pts);
+    for (int l = 0; l < a.n_tc; ++l) {
+      cp_async_wait_all();
+      __syncthreads();                                  // A0 complete, weights of layer l landed, A1 free
+      if (l + 1 < a.n_tc) prefetch(l + 1);              // overlaps the GEMM below
+      const float* Wt = Wt0 + (l & 1) * kW * kW;
+      float acc[4][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < kW; ++k) {
+        const float4 av = *reinterpret_cast<const float4*>(A0 + k * kF32Rows + 4 * (warp ^ (k & 15)));
+        const float4 wv = *reinterpret_cast<const float4*>(Wt + k * kW + f0);
+        const float ar[4] = {av.x, av.y, av.z, av.w};
+        const float wr[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(ar[j], wr[i], acc[j][i]);
+      }
+      // pre-activations (bias on primal rows) to A1, row-major [64 rows][128 f]
+      const float4 b4 = *reinterpret_cast<const float4*>(sbh + l * kW + f0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (rows[j].cls == 0) {
+          acc[j][0] += b4.x;
+          acc[j][1] += b4.y;
+          acc[j][2] += b4.z;
+          acc[j][3] += b4.w;
+        }
+        *reinterpret_cast<float4*>(A1 + (4 * warp + j) * kW + f0) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+      }
+      __syncthreads();                                  // A1 complete, every GEMM has read A0
+      // activations of the next layer into A0; derivative rows read their partners' values
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const RowInfo& ri = rows[j];
+        if (ri.cls == 0) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[j][i] = act_f32path(a.act, acc[j][i]);
+        } else if (ri.cls < 0) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+        } else {
+          const float4 q4 = *reinterpret_cast<const float4*>(A1 + ri.q * kW + f0);
+          float4 a4 = q4, c4 = q4;
+          if (ri.cls == 3) {
+            a4 = *reinterpret_cast<const float4*>(A1 + (ri.ja * a.Pt + ri.q) * kW + f0);
+            c4 = *reinterpret_cast<const float4*>(A1 + (ri.jb * a.Pt + ri.q) * kW + f0);
+          }
+          acc[j][0] = f32_deriv_act(a.act, ri.cls, acc[j][0], q4.x, a4.x, c4.x);
+          acc[j][1] = f32_deriv_act(a.act, ri.cls, acc[j][1], q4.y, a4.y, c4.y);
+          acc[j][2] = f32_deriv_act(a.act, ri.cls, acc[j][2], q4.z, a4.z, c4.z);
+          acc[j][3] = f32_deriv_act(a.act, ri.cls, acc[j][3], q4.w, a4.w, c4.w);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(A0 + f32_slot(f0 + i, 4 * warp)) = make_float4(acc[0][i], acc[1][i], acc[2][i], acc[3][i]);
+    }
+    __syncthreads();                                    // A0 complete
+    // ---- output layer (FP32): 8 threads per row, k interleaved, combined by shuffles
+    {
+      const int row = t >> 3, part = t & 7;
       const RowInfo ri = row_info(a, row, first, n_pts);
       float y[3] = {0.f, 0.f, 0.f};
-      for (int i = 0; i < a.d; ++i)
-        for (int k = 32 * kq; k < 32 * kq + 32; ++k) y[i] = fmaf(sWout[i * kW + k], AT[k * kATStride + row], y[i]);
+#pragma unroll 4
+      for (int kk = 0; kk < kW / 8; ++kk) {
+        const int k = part + 8 * kk;
+        const float h = A0[f32_slot(k, row)];
+        for (int i = 0; i < a.d; ++i) y[i] = fmaf(sWout[i * kW + k], h, y[i]);
+      }
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         y[i] += __shfl_xor_sync(0xffffffffu, y[i], 1);
         y[i] += __shfl_xor_sync(0xffffffffu, y[i], 2);
+        y[i] += __shfl_xor_sync(0xffffffffu, y[i], 4);
       }
-      if (kq == 0 && ri.cls >= 0) {
+      if (part == 0 && ri.cls >= 0) {
         const int kidx = row / a.Pt;
         float* o = a.out + ((int64_t)kidx * a.n + ri.p) * a.d;
         for (int i = 0; i < a.d; ++i) {
@@ -509,7 +555,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
         }
       }
     }
-    __syncthreads();
+    __syncthreads();                                    // A0 / A1 / weight buffer 0 free for the next tile
   }
   cp_async_wait_all();
 }
@@ -558,7 +604,7 @@ size_t dec_smem_bytes() {
 }
 
 size_t dec_f32_smem_bytes() {
-  return (size_t)(kW * kATStride + 2 * kW * kW + kW * kW0Stride + kW + kMaxTC * kW + 3 * kW) * sizeof(float);
+  return (size_t)(2 * kW * kF32Rows + 2 * kW * kW + kW0Stride * kW + kW + kMaxTC * kW + 3 * kW) * sizeof(float);
 }
 
 mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {

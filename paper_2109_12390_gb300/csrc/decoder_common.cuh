@@ -149,6 +149,27 @@ __device__ __forceinline__ void row_inputs(const DecArgs& a, const RowInfo& ri, 
   }
 }
 
+// Entry i (< d + r) of row_inputs: normalised input and direction of one row.
+__device__ __forceinline__ void row_input_elem(const DecArgs& a, const RowInfo& ri, int i, float& vin, float& vdir) {
+  const int d = a.d, r = a.r;
+  int64_t xrow = ri.p;
+  int li = a.lat ? a.lat[ri.p] : (a.lat_per_point ? (int)ri.p : 0);
+  if (a.n_dev) {
+    const int cnt = max(*a.n_dev, 1);
+    xrow = ri.p % cnt;
+    li = (int)(ri.p / cnt);
+    if (a.idx) xrow = a.idx[xrow];
+  }
+  vin = i < d ? (a.X[xrow * d + i] - a.norm[i]) / a.norm[d + i] : a.latents[(int64_t)li * r + (i - d)];
+  vdir = 0.f;
+  if (ri.cls == 1) {
+    if (ri.kind >= 1 && ri.kind <= d + r) vdir = (i == ri.kind - 1) ? (i < d ? 1.f / a.norm[d + i] : 1.f) : 0.f;
+    else if (ri.kind == KIND_JVP && i >= d) vdir = a.dirs[(int64_t)li * r + (i - d)];
+  } else if ((ri.cls == 2 || ri.cls == 3) && i >= d) {
+    vdir = a.dirs[(int64_t)li * r + (i - d)];
+  }
+}
+
 // Layer-0 tangent of a mixed row along input b (the normalised X axes scale by
 // 1 / X_range): the weight column itself.
 __device__ __forceinline__ float mixed_t0(const DecArgs& a, const float* W0row, int kind) {
