@@ -541,6 +541,18 @@ typedef struct snapshot_desc {
  *   batch               (snapshot, particle) pairs per step, drawn uniformly
  *                       over all pairs by a counter-based SplitMix64 hash of
  *                       (seed, step, i).
+ *   encoder_subset      0: one trainable latent per snapshot (the latent
+ *                       table the Remark of Section 4.1 allows).  n > 0: the
+ *                       latents come from the encoder network of Section 4.1
+ *                       / Table 1, trained with the decoder, whose input is the
+ *                       positions of n particles of each snapshot (ids
+ *                       floor(j P / n), j < n, P the instance's particle
+ *                       count), standardised per coordinate (mean and standard
+ *                       deviation over all snapshots) and concatenated
+ *                       particle-major; single-channel convolutions of kernel
+ *                       6 and stride 2 (ELU) down to the last length >= 32, a
+ *                       32-wide ELU layer and a linear layer to r.  dim x n in
+ *                       [32, 8192].  Weights Xavier-uniform from `seed`.
  */
 typedef struct train_config {
   float lambda_F;
@@ -551,6 +563,7 @@ typedef struct train_config {
   int32_t batch;
   int64_t total_steps;
   uint64_t seed;
+  int32_t encoder_subset;
 } train_config;
 
 typedef struct trainer_ctx trainer_ctx;
@@ -558,7 +571,7 @@ typedef struct trainer_ctx trainer_ctx;
 /*
  * Creates a trainer for `dec` (which must have >= 2 hidden layers; its
  * parameters are updated in place by decoder_train).  latents0: (n_snap, r)
- * initial latent table or NULL (zeros).  Synchronous.
+ * initial latent table or NULL (zeros); ignored with an encoder.  Synchronous.
  */
 mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snapshot_desc* snaps,
                           const float* latents0, trainer_ctx** out);
@@ -576,7 +589,8 @@ mpm_status decoder_train(trainer_ctx* ctx, int n_steps, void* stream);
 /* Loss of the last step (mean over the batch) and the step count.  Synchronous. */
 mpm_status trainer_loss(trainer_ctx* ctx, double* loss, int64_t* step, void* stream);
 
-/* Copies the latent table (n_snap, r) out (host or device pointer). */
+/* Copies the latents (n_snap, r) out (host or device pointer): the table, or the
+ * encoder's output at the start of the last step. */
 mpm_status trainer_get_latents(trainer_ctx* ctx, float* latents, void* stream);
 
 mpm_status trainer_status_word(trainer_ctx* ctx, uint32_t* out, int clear, void* stream);
@@ -584,12 +598,35 @@ mpm_status trainer_status_word(trainer_ctx* ctx, uint32_t* out, int clear, void*
 /*
  * Gradient check: one forward/backward on the minibatch of the current step
  * without updating.  Returns the parameter gradients (decoder_num_params
- * floats, same layout as decoder_set_params), the latent-table gradients
- * (n_snap, r), the batch (snapshot index and particle index within its
- * instance, batch int32 each) and the loss.  Any output may be NULL.  Synchronous.
+ * floats, same layout as decoder_set_params), the per-snapshot latent
+ * gradients (n_snap, r), with an encoder its parameter gradients
+ * (trainer_encoder_params layout), the batch (snapshot index and particle
+ * index within its instance, batch int32 each) and the loss.  Any output may
+ * be NULL.  Synchronous.
  */
-mpm_status trainer_gradients(trainer_ctx* ctx, float* g_params, float* g_latents, int32_t* batch_snap,
-                             int32_t* batch_part, double* loss, void* stream);
+mpm_status trainer_gradients(trainer_ctx* ctx, float* g_params, float* g_latents, float* g_encoder,
+                             int32_t* batch_snap, int32_t* batch_part, double* loss, void* stream);
+
+/*
+ * Encoder parameters (trainer created with encoder_subset > 0): *n_params
+ * floats, per convolution l its taps w_l[0..5] then its bias, then W1 (32 x
+ * d_conv, row-major), b1 (32), W2 (r x 32, row-major), b2 (r); and the input
+ * standardisation shift_scale = [shift (dim), scale (dim)].  Any output may be
+ * NULL.  Errors: MPM_EINVAL without an encoder.  Synchronous.
+ */
+mpm_status trainer_encoder_params(trainer_ctx* ctx, float* params, float* shift_scale, int64_t* n_params,
+                                  void* stream);
+/* Replaces the encoder parameters and/or the standardisation (NULL keeps it) and
+ * resets the encoder's Adam moments.  Synchronous. */
+mpm_status trainer_set_encoder_params(trainer_ctx* ctx, const float* params, const float* shift_scale,
+                                      void* stream);
+/*
+ * Generalized coordinates of n full-order states: x (n, n_particles, dim), host
+ * or device, particle order of the training instances; latents (n, r), host or
+ * device.  Uses the trainer's subset rule and standardisation.  Synchronous.
+ */
+mpm_status trainer_encode(trainer_ctx* ctx, const float* x, int64_t n, int64_t n_particles, float* latents,
+                          void* stream);
 
 #ifdef __cplusplus
 }

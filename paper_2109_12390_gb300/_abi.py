@@ -57,7 +57,8 @@ class SnapshotDesc(C.Structure):
 
 class TrainConfig(C.Structure):
     _fields_ = [("lambda_F", C.c_float), ("lambda_v", C.c_float), ("dt_snap", C.c_float), ("lr0", C.c_float),
-                ("lr1", C.c_float), ("batch", C.c_int32), ("total_steps", C.c_int64), ("seed", C.c_uint64)]
+                ("lr1", C.c_float), ("batch", C.c_int32), ("total_steps", C.c_int64), ("seed", C.c_uint64),
+                ("encoder_subset", C.c_int32)]
 
 
 class MpmError(RuntimeError):
@@ -111,7 +112,10 @@ SIGNATURES = [
     ("trainer_loss", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_void_p]),
     ("trainer_get_latents", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("trainer_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
-    ("trainer_gradients", C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.POINTER(C.c_double), C.c_void_p]),
+    ("trainer_gradients", C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.POINTER(C.c_double), C.c_void_p]),
+    ("trainer_encoder_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
+    ("trainer_set_encoder_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("trainer_encode", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),
 ]
 
 

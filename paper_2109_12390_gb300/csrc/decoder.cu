@@ -326,23 +326,34 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 // --------------------------------------------------------------------------
 // FP32 decoder on the CUDA cores, for calls whose rows are too few to keep the
 // tensor cores busy and whose results need FP32 accuracy (the reduced step's
-// positions and gradients).  Same row kinds as decoder_tc, in tiles of 64 rows
-// (Pt = 64 / R points), one persistent CTA of 512 threads (16 warps) per SM.
-//   layer 0       thread = one row x 16 columns; inputs staged in shared memory
-//   square layer  128 x 64 x 128 FP32 GEMM from shared memory, thread = 4 rows
-//                 (one group per warp) x 4 consecutive features; weights
+// positions and gradients).  Same row kinds as decoder_tc; one persistent CTA
+// of 512 threads (16 warps) per SM; tiles of TR = 32 or 64 row slots.
+// Rows reach the tiles in one of two ways:
+//   aligned  (mixed rows present) slot k Pt + q = kind k of point q, Pt = TR / R
+//            points per tile, as in decoder_tc;
+//   packed   the call's rows in (point, kind) order, U <= TR - 1 per tile,
+//            chosen so that the tiles spread over all SMs; slot 0 recomputes
+//            the primal row of the tile's first point (its derivative rows may
+//            start mid-point) and is not written out.
+// Per tile:
+//   layer 0       512 / TR threads per row, each 128 TR / 512 columns; inputs
+//                 staged in shared memory first
+//   square layer  128 x TR x 128 FP32 GEMM from shared memory: warp w < TR / 4
+//                 owns slots 4 w .. 4 w + 3, lane l features 4 l .. 4 l + 3
+//                 (one float4 of activations, one of weights per k); weights
 //                 double-buffered from a transposed copy by asynchronous copies
-//   exchange      pre-activations to a second buffer (row-major), derivative rows
-//                 read the primal (and, for mixed rows, JVP and tangent) rows'
-//                 values as float4 of the thread's own 4 features
-//   output layer  8 threads per row, interleaved k, shuffle reduction
-// Activations (the GEMM's input) are stored feature-major, [f][64 rows], the
-// rows in float4 groups permuted per feature (group g of feature f at slot
-// g ^ (f & 15)) so that the feature-strided stores of a warp spread over the
-// banks.  Two barriers per square layer.
+//   exchange      pre-activations to a second buffer (row-major, float4 quads
+//                 permuted per row group); derivative rows read the primal
+//                 (and, for mixed rows, JVP and tangent) rows' values as float4
+//                 of the thread's own 4 features
+//   output layer  512 / TR threads per row, interleaved k, shuffle reduction
+// Activations (the GEMM's input) are stored feature-major, [f][TR slots], the
+// slots in float4 groups permuted per feature (group g of feature f at
+// g ^ (f mod TR / 4)) so that the feature-strided stores of a warp spread over
+// the banks.  Two barriers per square layer.
 // --------------------------------------------------------------------------
 constexpr int kF32Threads = 512;
-constexpr int kF32Rows = 64;              // rows per tile of the FP32 path
+constexpr int kF32Rows = 64;              // largest tile (row slots)
 constexpr int kF32In = 41;                // staged input row stride (d + r <= 40)
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
@@ -359,8 +370,15 @@ __device__ __forceinline__ float act_f32path(int act, float z) {
   return act == 0 ? (z > 0.f ? z : __expf(z) - 1.0f) : z;
 }
 
-// Offset of (feature f, tile row) in an activation buffer.
-__device__ __forceinline__ int f32_slot(int f, int row) { return f * kF32Rows + 4 * ((row >> 2) ^ (f & 15)) + (row & 3); }
+// Offset of (feature f, slot) in an activation buffer of TR slots.
+template <int TR>
+__device__ __forceinline__ int f32_slot(int f, int slot) {
+  return f * TR + 4 * ((slot >> 2) ^ (f & (TR / 4 - 1))) + (slot & 3);
+}
+
+// Offset of the float4 of features f .. f + 3 (f a multiple of 4) of a slot in the row-major
+// pre-activation buffer.
+__device__ __forceinline__ int f32_zslot(int slot, int f) { return slot * kW + 4 * ((f >> 2) ^ ((slot >> 2) & 7)); }
 
 // Activation of a derivative row from its own pre-activation zo, the primal row's zq and, for a
 // mixed row, the JVP row's za and the tangent row's zb (same point, same feature).
@@ -370,17 +388,62 @@ __device__ __forceinline__ float f32_deriv_act(int act, int cls, float zo, float
   return act_d2(act, zq) * za * zb + act_d1(act, zq) * zo;
 }
 
+// One slot of an FP32-path tile: the row (kind, class, point), the slots of its partner rows and
+// the output block it is written to (-1: not written).
+struct F32Row {
+  RowInfo ri;
+  int qs, as, bs;
+  int kidx;
+};
+
+__device__ __forceinline__ F32Row f32_row(const DecArgs& a, int slot, int64_t tile, int64_t n_pts) {
+  F32Row fr;
+  if (a.f32_U == 0) {
+    fr.ri = row_info(a, slot, tile * a.Pt, n_pts);
+    fr.qs = fr.ri.q;
+    fr.as = fr.ri.ja * a.Pt + fr.ri.q;
+    fr.bs = fr.ri.jb * a.Pt + fr.ri.q;
+    fr.kidx = fr.ri.cls >= 0 ? slot / a.Pt : -1;
+    return fr;
+  }
+  const int U = a.f32_U;
+  const int64_t g0 = tile * U;
+  const int64_t g = slot == 0 ? (g0 / a.R) * a.R : g0 + slot - 1;
+  fr.ri.q = fr.ri.ja = fr.ri.jb = 0;
+  fr.qs = fr.as = fr.bs = 0;
+  if (slot > U || g >= n_pts * a.R) {
+    fr.ri.cls = -1;
+    fr.ri.kind = -1;
+    fr.ri.p = 0;
+    fr.kidx = -1;
+    return fr;
+  }
+  const int64_t p = g / a.R;
+  const int k = (int)(g - p * a.R);
+  fr.ri.p = p;
+  fr.ri.kind = a.kinds[k];
+  fr.ri.cls = kind_class(fr.ri.kind);
+  const int64_t gp = p * a.R;   // the point's primal row: in this tile, or recomputed in slot 0
+  fr.qs = gp >= g0 ? (int)(gp - g0 + 1) : 0;
+  fr.kidx = slot == 0 ? -1 : k;
+  return fr;
+}
+
+template <int TR>
 __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
+  constexpr int G = TR / 4;                   // row groups = GEMM warps
+  constexpr int TPR = kF32Threads / TR;       // threads per row in layer 0 and the output layer
+  constexpr int CPT = kW / TPR;               // layer-0 columns per thread
   extern __shared__ __align__(16) float fsm[];
-  float* A0 = fsm;                        // [128 f][64 rows] activations (GEMM input)
-  float* A1 = A0 + kW * kF32Rows;         // [64 rows][128 f] pre-activations; staged inputs at layer 0
-  float* Wt0 = A1 + kW * kF32Rows;        // two [128 in][128 out] weight buffers, transposed
-  float* W0T = Wt0 + 2 * kW * kW;         // [40 in][128 out] first layer, transposed
-  float* sb0 = W0T + kW0Stride * kW;      // [128]
-  float* sbh = sb0 + kW;                  // [kMaxTC][128]
-  float* sWout = sbh + kMaxTC * kW;       // [3][128]
-  float* IN = A1;                         // [64 rows][kF32In] normalised inputs (layer 0 only)
-  float* DIR = A1 + kF32Rows * kF32In;    // [64 rows][kF32In] input directions
+  float* A0 = fsm;                            // [128 f][TR slots] activations (GEMM input)
+  float* A1 = A0 + kW * kF32Rows;             // [TR slots][128 f] pre-activations; staged inputs at layer 0
+  float* Wt0 = A1 + kW * kF32Rows;            // two [128 in][128 out] weight buffers, transposed
+  float* W0T = Wt0 + 2 * kW * kW;             // [40 in][128 out] first layer, transposed
+  float* sb0 = W0T + kW0Stride * kW;          // [128]
+  float* sbh = sb0 + kW;                      // [kMaxTC][128]
+  float* sWout = sbh + kMaxTC * kW;           // [3][128]
+  float* IN = A1;                             // [TR][kF32In] normalised inputs (layer 0 only)
+  float* DIR = A1 + kF32Rows * kF32In;        // [TR][kF32In] input directions
   const int t = threadIdx.x;
   const int K0 = a.d + a.r;
   // constant operands: all loads issued before any is used
@@ -406,37 +469,37 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   };
 
   const int64_t n_pts = dec_count(a);
-  const int64_t n_tiles = (n_pts + a.Pt - 1) / a.Pt;
+  const int64_t n_tiles = a.f32_U ? (n_pts * a.R + a.f32_U - 1) / a.f32_U : (n_pts + a.Pt - 1) / a.Pt;
   const int warp = t >> 5, lane = t & 31;
-  const int f0 = 4 * lane;                 // square layers: features f0 .. f0 + 3, rows 4 warp .. 4 warp + 3
-  const int rw = t & (kF32Rows - 1), cg = t >> 6;   // layer 0: row rw, columns 16 cg .. 16 cg + 15
+  const int f0 = 4 * lane;                    // square layers: features f0 .. f0 + 3, slots 4 warp .. 4 warp + 3
+  const int rw = t % TR, cg = t / TR;         // layer 0: slot rw, columns CPT cg .. CPT cg + CPT - 1
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int64_t first = tile * a.Pt;
     if (a.n_tc > 0) prefetch(0);
     // ---- inputs of the tile's rows
-    for (int e = t; e < kF32Rows * K0; e += kF32Threads) {
-      const int row = e / K0, i = e - row * K0;
-      const RowInfo ri = row_info(a, row, first, n_pts);
+    for (int e = t; e < TR * K0; e += kF32Threads) {
+      const int slot = e / K0, i = e - slot * K0;
+      const F32Row fr = f32_row(a, slot, tile, n_pts);
       float vin = 0.f, vdir = 0.f;
-      if (ri.cls >= 0) row_input_elem(a, ri, i, vin, vdir);
-      IN[row * kF32In + i] = vin;
-      DIR[row * kF32In + i] = vdir;
+      if (fr.ri.cls >= 0) row_input_elem(a, fr.ri, i, vin, vdir);
+      IN[slot * kF32In + i] = vin;
+      DIR[slot * kF32In + i] = vdir;
     }
     __syncthreads();
     // ---- layer 0 (FP32)
     {
-      const RowInfo ri = row_info(a, rw, first, n_pts);
-      float z[16], zd[16];
+      const F32Row fr = f32_row(a, rw, tile, n_pts);
+      const RowInfo& ri = fr.ri;
+      float z[CPT], zd[CPT];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        z[c] = sb0[16 * cg + c];
+      for (int c = 0; c < CPT; ++c) {
+        z[c] = sb0[CPT * cg + c];
         zd[c] = 0.f;
       }
       for (int i = 0; i < K0; ++i) {
         const float vin = IN[rw * kF32In + i], vdir = DIR[rw * kF32In + i];
-        const float4* w4 = reinterpret_cast<const float4*>(W0T + i * kW + 16 * cg);
+        const float4* w4 = reinterpret_cast<const float4*>(W0T + i * kW + CPT * cg);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < CPT / 4; ++q) {
           const float4 w = w4[q];
           z[4 * q + 0] = fmaf(w.x, vin, z[4 * q + 0]);
           z[4 * q + 1] = fmaf(w.y, vin, z[4 * q + 1]);
@@ -449,8 +512,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
         }
       }
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int col = 16 * cg + c;
+      for (int c = 0; c < CPT; ++c) {
+        const int col = CPT * cg + c;
         float hv = 0.f;
         if (ri.cls == 0) hv = act_f32path(a.act, z[c]);
         else if (ri.cls == 1) hv = act_d1(a.act, z[c]) * zd[c];
@@ -460,95 +523,99 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
           const float t0 = b < a.d ? W0T[b * kW + col] / a.norm[a.d + b] : W0T[b * kW + col];
           hv = act_d2(a.act, z[c]) * zd[c] * t0;
         }
-        A0[f32_slot(col, rw)] = hv;
+        A0[f32_slot<TR>(col, rw)] = hv;
       }
     }
-    // row bookkeeping of this warp's 4 GEMM rows
-    RowInfo rows[4];
+    // slot bookkeeping of this warp's 4 GEMM slots
+    F32Row rows[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) rows[j] = row_info(a, 4 * warp + j, first, n_pts);
+    for (int j = 0; j < 4; ++j) rows[j] = f32_row(a, (4 * warp + j) % TR, tile, n_pts);
     for (int l = 0; l < a.n_tc; ++l) {
       cp_async_wait_all();
       __syncthreads();                                  // A0 complete, weights of layer l landed, A1 free
       if (l + 1 < a.n_tc) prefetch(l + 1);              // overlaps the GEMM below
-      const float* Wt = Wt0 + (l & 1) * kW * kW;
       float acc[4][4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
-#pragma unroll 8
-      for (int k = 0; k < kW; ++k) {
-        const float4 av = *reinterpret_cast<const float4*>(A0 + k * kF32Rows + 4 * (warp ^ (k & 15)));
-        const float4 wv = *reinterpret_cast<const float4*>(Wt + k * kW + f0);
-        const float ar[4] = {av.x, av.y, av.z, av.w};
-        const float wr[4] = {wv.x, wv.y, wv.z, wv.w};
+      if (warp < G) {
+        const float* Wt = Wt0 + (l & 1) * kW * kW;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(ar[j], wr[i], acc[j][i]);
-      }
-      // pre-activations (bias on primal rows) to A1, row-major [64 rows][128 f]
-      const float4 b4 = *reinterpret_cast<const float4*>(sbh + l * kW + f0);
+          for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < kW; ++k) {
+          const float4 av = *reinterpret_cast<const float4*>(A0 + k * TR + 4 * (warp ^ (k & (G - 1))));
+          const float4 wv = *reinterpret_cast<const float4*>(Wt + k * kW + f0);
+          const float ar[4] = {av.x, av.y, av.z, av.w};
+          const float wr[4] = {wv.x, wv.y, wv.z, wv.w};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (rows[j].cls == 0) {
-          acc[j][0] += b4.x;
-          acc[j][1] += b4.y;
-          acc[j][2] += b4.z;
-          acc[j][3] += b4.w;
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(ar[j], wr[i], acc[j][i]);
         }
-        *reinterpret_cast<float4*>(A1 + (4 * warp + j) * kW + f0) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+        // pre-activations (bias on primal rows) to A1
+        const float4 b4 = *reinterpret_cast<const float4*>(sbh + l * kW + f0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (rows[j].ri.cls == 0) {
+            acc[j][0] += b4.x;
+            acc[j][1] += b4.y;
+            acc[j][2] += b4.z;
+            acc[j][3] += b4.w;
+          }
+          *reinterpret_cast<float4*>(A1 + f32_zslot(4 * warp + j, f0)) =
+              make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+        }
       }
       __syncthreads();                                  // A1 complete, every GEMM has read A0
-      // activations of the next layer into A0; derivative rows read their partners' values
+      if (warp < G) {
+        // activations of the next layer into A0; derivative rows read their partners' values
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const RowInfo& ri = rows[j];
-        if (ri.cls == 0) {
+        for (int j = 0; j < 4; ++j) {
+          const F32Row& fr = rows[j];
+          if (fr.ri.cls == 0) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) acc[j][i] = act_f32path(a.act, acc[j][i]);
-        } else if (ri.cls < 0) {
+            for (int i = 0; i < 4; ++i) acc[j][i] = act_f32path(a.act, acc[j][i]);
+          } else if (fr.ri.cls < 0) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
-        } else {
-          const float4 q4 = *reinterpret_cast<const float4*>(A1 + ri.q * kW + f0);
-          float4 a4 = q4, c4 = q4;
-          if (ri.cls == 3) {
-            a4 = *reinterpret_cast<const float4*>(A1 + (ri.ja * a.Pt + ri.q) * kW + f0);
-            c4 = *reinterpret_cast<const float4*>(A1 + (ri.jb * a.Pt + ri.q) * kW + f0);
+            for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+          } else {
+            const float4 q4 = *reinterpret_cast<const float4*>(A1 + f32_zslot(fr.qs, f0));
+            float4 a4 = q4, c4 = q4;
+            if (fr.ri.cls == 3) {
+              a4 = *reinterpret_cast<const float4*>(A1 + f32_zslot(fr.as, f0));
+              c4 = *reinterpret_cast<const float4*>(A1 + f32_zslot(fr.bs, f0));
+            }
+            acc[j][0] = f32_deriv_act(a.act, fr.ri.cls, acc[j][0], q4.x, a4.x, c4.x);
+            acc[j][1] = f32_deriv_act(a.act, fr.ri.cls, acc[j][1], q4.y, a4.y, c4.y);
+            acc[j][2] = f32_deriv_act(a.act, fr.ri.cls, acc[j][2], q4.z, a4.z, c4.z);
+            acc[j][3] = f32_deriv_act(a.act, fr.ri.cls, acc[j][3], q4.w, a4.w, c4.w);
           }
-          acc[j][0] = f32_deriv_act(a.act, ri.cls, acc[j][0], q4.x, a4.x, c4.x);
-          acc[j][1] = f32_deriv_act(a.act, ri.cls, acc[j][1], q4.y, a4.y, c4.y);
-          acc[j][2] = f32_deriv_act(a.act, ri.cls, acc[j][2], q4.z, a4.z, c4.z);
-          acc[j][3] = f32_deriv_act(a.act, ri.cls, acc[j][3], q4.w, a4.w, c4.w);
         }
-      }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(A0 + f32_slot(f0 + i, 4 * warp)) = make_float4(acc[0][i], acc[1][i], acc[2][i], acc[3][i]);
+        for (int i = 0; i < 4; ++i)
+          *reinterpret_cast<float4*>(A0 + f32_slot<TR>(f0 + i, 4 * warp)) =
+              make_float4(acc[0][i], acc[1][i], acc[2][i], acc[3][i]);
+      }
     }
     __syncthreads();                                    // A0 complete
-    // ---- output layer (FP32): 8 threads per row, k interleaved, combined by shuffles
+    // ---- output layer (FP32): TPR threads per row, k interleaved, combined by shuffles
     {
-      const int row = t >> 3, part = t & 7;
-      const RowInfo ri = row_info(a, row, first, n_pts);
+      const int slot = t / TPR, part = t % TPR;
+      const F32Row fr = f32_row(a, slot, tile, n_pts);
       float y[3] = {0.f, 0.f, 0.f};
 #pragma unroll 4
-      for (int kk = 0; kk < kW / 8; ++kk) {
-        const int k = part + 8 * kk;
-        const float h = A0[f32_slot(k, row)];
+      for (int kk = 0; kk < kW / TPR; ++kk) {
+        const int k = part + TPR * kk;
+        const float h = A0[f32_slot<TR>(k, slot)];
         for (int i = 0; i < a.d; ++i) y[i] = fmaf(sWout[i * kW + k], h, y[i]);
       }
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        y[i] += __shfl_xor_sync(0xffffffffu, y[i], 1);
-        y[i] += __shfl_xor_sync(0xffffffffu, y[i], 2);
-        y[i] += __shfl_xor_sync(0xffffffffu, y[i], 4);
-      }
-      if (part == 0 && ri.cls >= 0) {
-        const int kidx = row / a.Pt;
-        float* o = a.out + ((int64_t)kidx * a.n + ri.p) * a.d;
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int o = 1; o < TPR; o <<= 1) y[i] += __shfl_xor_sync(0xffffffffu, y[i], o);
+      if (part == 0 && fr.kidx >= 0) {
+        const RowInfo& ri = fr.ri;
+        float* o = a.out + ((int64_t)fr.kidx * a.n + ri.p) * a.d;
         for (int i = 0; i < a.d; ++i) {
           const float v = y[i] + (ri.cls == 0 ? a.bout[i] : 0.f);
           o[i] = v * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
@@ -680,7 +747,9 @@ mpm_status decoder_create(const decoder_desc* desc, mpm_decoder** out) {
   if (e == cudaSuccess) e = cudaMemset(dec->status, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(decoder_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec->smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(decoder_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec_f32_smem_bytes());
+    e = cudaFuncSetAttribute(decoder_f32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec_f32_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(decoder_f32<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec_f32_smem_bytes());
   if (e != cudaSuccess) {
     decoder_destroy(dec);
     return set_error(MPM_ENOMEM, std::string("decoder_create: ") + cudaGetErrorString(e));
@@ -812,10 +881,27 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
     decoder_simt<<<blocks, 128, 0, s>>>(a);
   } else if (dec->fp32 && !a.zstore) {
     MPM_CHECK_ARG(R <= kF32Rows, "the FP32 path takes at most 64 row kinds");
-    a.Pt = kF32Rows / R;
-    const int64_t tiles = (n + a.Pt - 1) / a.Pt;
+    int64_t tiles;
+    bool small = false;
+    if (has_mixed) {
+      // mixed rows read their JVP and tangent partners: point-aligned tiles
+      a.f32_U = 0;
+      a.Pt = kF32Rows / R;
+      tiles = (n + a.Pt - 1) / a.Pt;
+    } else {
+      // packed tiles: about one per SM, 32 or 64 slots
+      const int64_t rows = n * R;
+      const int64_t U = std::max<int64_t>(1, std::min<int64_t>((rows + dec->n_sm - 1) / dec->n_sm, kF32Rows - 1));
+      a.f32_U = (int)U;
+      a.Pt = 1;
+      small = U + 1 <= 32;
+      tiles = (rows + U - 1) / U;
+    }
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));
-    decoder_f32<<<blocks, kF32Threads, dec_f32_smem_bytes(), s>>>(a);
+    if (small)
+      decoder_f32<32><<<blocks, kF32Threads, dec_f32_smem_bytes(), s>>>(a);
+    else
+      decoder_f32<64><<<blocks, kF32Threads, dec_f32_smem_bytes(), s>>>(a);
   } else {
     const int64_t tiles = (n + a.Pt - 1) / a.Pt;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));

@@ -50,6 +50,8 @@ struct DecArgs {
   int linear;
   // latent row = point index (training batches carry one latent per point)
   int lat_per_point;
+  // FP32 path: useful rows per packed tile (0: point-aligned tiles of Pt points)
+  int f32_U;
   // training: per hidden layer l, pre-activations z (FP32) and activations a
   // (BF16) of every tile row, stored feature-major: [l][feature][row], row =
   // tile * 128 + t, rows_total = n_tiles * 128

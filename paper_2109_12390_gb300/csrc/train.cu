@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "decoder_common.cuh"
+#include "encoder.cuh"
 
 namespace mpmrom {
 mpm_status decoder_launch_train(const mpm_decoder* dec, const float* X, const float* latents, const float* dirs,
@@ -637,6 +638,16 @@ struct trainer_ctx {
   double* loss = nullptr;
   uint32_t* status = nullptr;
   size_t bwd_smem = 0;
+  // encoder (Section 4.1) in place of the latent table
+  bool enc = false;
+  EncDesc E{};
+  float* U = nullptr;           // (n_snap, L0) standardised subset positions
+  float* enc_p = nullptr;       // parameters, gradients, Adam moments
+  float* enc_g = nullptr;
+  float* enc_m = nullptr;
+  float* enc_v = nullptr;
+  float* enc_ss = nullptr;      // shift (d), scale (d)
+  double* enc_work = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaGraphExec_t graph_noupdate = nullptr;
@@ -648,6 +659,11 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
   mpm_decoder* dec = c->dec;
   const int d = c->d, r = c->r;
   int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((c->B + 255) / 256, (int64_t)c->n_sm * 8));
+  if (c->enc) {
+    // latents of every snapshot from the encoder
+    mpm_status se = enc_forward(c->E, c->enc_p, c->U, c->n_snap, c->latents, c->n_sm, s);
+    if (se != MPM_OK) return se;
+  }
   train_sample<<<blocks, 256, 0, s>>>(c->st, c->b, c->latents, c->cfg.dt_snap, c->cfg.seed, c->step, c->loss);
   MPM_CUDA_TRY(cudaGetLastError());
   int kinds[8];
@@ -707,12 +723,22 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
   MPM_CUDA_TRY(cudaGetLastError());
   train_lat_scatter<<<blocks, 256, 0, s>>>(c->b, r, c->g_lat_pt, c->g_u_pt, c->cfg.dt_snap, c->g_lat);
   MPM_CUDA_TRY(cudaGetLastError());
+  if (c->enc) {
+    // pull the per-snapshot latent gradients back through the encoder
+    st = enc_backward(c->E, c->enc_p, c->U, c->n_snap, c->g_lat, c->enc_g, c->n_sm, s);
+    if (st != MPM_OK) return st;
+  }
   if (update) {
-    const int64_t n0 = dec->n_params, n1 = c->n_snap * r;
+    // Adam on the decoder and on the latent table or the encoder
+    const int64_t n0 = dec->n_params, n1 = c->enc ? (int64_t)c->E.n_params : c->n_snap * r;
+    float* p1 = c->enc ? c->enc_p : c->latents;
+    float* g1 = c->enc ? c->enc_g : c->g_lat;
+    float* m1 = c->enc ? c->enc_m : c->m_lat;
+    float* v1 = c->enc ? c->enc_v : c->v_lat;
+    if (c->enc) MPM_CUDA_TRY(cudaMemsetAsync(c->g_lat, 0, sizeof(float) * c->n_snap * r, s));
     int ba = (int)std::max<int64_t>(1, std::min<int64_t>((n0 + n1 + 255) / 256, (int64_t)c->n_sm * 8));
-    train_adam<<<ba, 256, 0, s>>>(dec->params, c->gparams, c->m_par, c->v_par, n0, c->latents, c->g_lat, c->m_lat,
-                                  c->v_lat, n1, c->step, c->cfg.total_steps, c->cfg.lr0, c->cfg.lr1, 0.9f, 0.999f,
-                                  1e-8f, 1);
+    train_adam<<<ba, 256, 0, s>>>(dec->params, c->gparams, c->m_par, c->v_par, n0, p1, g1, m1, v1, n1, c->step,
+                                  c->cfg.total_steps, c->cfg.lr0, c->cfg.lr1, 0.9f, 0.999f, 1e-8f, 1);
     MPM_CUDA_TRY(cudaGetLastError());
     st = decoder_refresh(dec, s);
     if (st != MPM_OK) return st;
@@ -820,6 +846,45 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   if ((st = talloc(&c->g_lat, nl)) != MPM_OK) return fail(st);
   if ((st = talloc(&c->m_lat, nl)) != MPM_OK) return fail(st);
   if ((st = talloc(&c->v_lat, nl)) != MPM_OK) return fail(st);
+  if (cfg->encoder_subset > 0) {
+    c->enc = true;
+    if (!enc_describe(d, r, cfg->encoder_subset, 0, &c->E))
+      return fail(set_error(MPM_EINVAL, "encoder_subset: d x subset must be in [32, 8192]"));
+    for (int i = 0; i < sd->n_inst; ++i)
+      if (sd->inst_offsets[i + 1] - sd->inst_offsets[i] < cfg->encoder_subset)
+        return fail(set_error(MPM_EINVAL, "encoder_subset larger than an instance"));
+    const int np = c->E.n_params;
+    if ((st = talloc(&c->U, (size_t)sd->n_snap * c->E.L[0], false)) != MPM_OK) return fail(st);
+    if ((st = talloc(&c->enc_p, np)) != MPM_OK) return fail(st);
+    if ((st = talloc(&c->enc_g, np)) != MPM_OK) return fail(st);
+    if ((st = talloc(&c->enc_m, np)) != MPM_OK) return fail(st);
+    if ((st = talloc(&c->enc_v, np)) != MPM_OK) return fail(st);
+    if ((st = talloc(&c->enc_ss, 2 * d)) != MPM_OK) return fail(st);
+    if ((st = talloc(&c->enc_work, 2 * d)) != MPM_OK) return fail(st);
+    if ((st = enc_prepare(c->E)) != MPM_OK) return fail(st);
+    if ((st = enc_moments(c->E, c->sx, c->snap_base, sd->n_snap, c->enc_work, c->enc_ss, 0)) != MPM_OK) return fail(st);
+    if ((st = enc_gather(c->E, c->sx, c->snap_base, sd->n_snap, c->enc_ss, c->U, 0)) != MPM_OK) return fail(st);
+    // Xavier-uniform initial weights (fan-in / fan-out of each layer's linear map), zero biases,
+    // uniform numbers from SplitMix64 seeded with the training seed
+    std::vector<float> h(np, 0.f);
+    uint64_t state = cfg->seed ^ 0x656e636f646572ull;
+    auto uni = [&](float lim) {
+      state += 0x9E3779B97F4A7C15ull;
+      uint64_t z = state;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      return lim * (2.f * (float)((z >> 40) * (1.0 / 16777216.0)) - 1.f);
+    };
+    const float lc = std::sqrt(6.f / (kEncKernel + 1));
+    for (int l = 0; l < c->E.n_conv; ++l)
+      for (int k = 0; k < kEncKernel; ++k) h[7 * l + k] = uni(lc);
+    const int dc = c->E.L[c->E.n_conv];
+    const float l1 = std::sqrt(6.f / (dc + kEncFC)), l2 = std::sqrt(6.f / (kEncFC + r));
+    for (int i = 0; i < kEncFC * dc; ++i) h[c->E.oW1 + i] = uni(l1);
+    for (int i = 0; i < r * kEncFC; ++i) h[c->E.oW2 + i] = uni(l2);
+    MPM_CUDA_TRY(cudaMemcpy(c->enc_p, h.data(), sizeof(float) * np, cudaMemcpyHostToDevice));
+  }
   if ((st = talloc(&c->gparams, dec->n_params)) != MPM_OK) return fail(st);
   if ((st = talloc(&c->m_par, dec->n_params)) != MPM_OK) return fail(st);
   if ((st = talloc(&c->v_par, dec->n_params)) != MPM_OK) return fail(st);
@@ -891,7 +956,7 @@ void trainer_destroy(trainer_ctx* c) {
   void* bufs[] = {c->snap_base, c->snap_inst, c->snap_next, c->inst_off, c->X, c->sx, c->sv, c->sF, c->latents,
                   c->g_lat, c->m_lat, c->v_lat, c->gparams, c->m_par, c->v_par, c->batch_mem, c->batch_idx, c->fwd,
                   c->zstore, c->astore, c->zbstore, c->zb0, c->g_lat_pt, c->g_u_pt, c->wtimg, c->d_w_off, c->step,
-                  c->loss, c->status};
+                  c->loss, c->status, c->U, c->enc_p, c->enc_g, c->enc_m, c->enc_v, c->enc_ss, c->enc_work};
   for (void* p : bufs) cudaFree(p);
   delete c;
 }
@@ -936,7 +1001,7 @@ mpm_status trainer_status_word(trainer_ctx* c, uint32_t* out, int clear, void* s
   return MPM_OK;
 }
 
-mpm_status trainer_gradients(trainer_ctx* c, float* g_params, float* g_latents, int32_t* batch_snap,
+mpm_status trainer_gradients(trainer_ctx* c, float* g_params, float* g_latents, float* g_encoder, int32_t* batch_snap,
                              int32_t* batch_part, double* loss, void* stream) {
   MPM_CHECK_ARG(c, "null context");
   cudaStream_t s = (cudaStream_t)stream;
@@ -945,15 +1010,78 @@ mpm_status trainer_gradients(trainer_ctx* c, float* g_params, float* g_latents, 
   if (st != MPM_OK) return st;
   if (g_params) MPM_CUDA_TRY(cudaMemcpyAsync(g_params, c->gparams, sizeof(float) * c->dec->n_params, cudaMemcpyDefault, s));
   if (g_latents) MPM_CUDA_TRY(cudaMemcpyAsync(g_latents, c->g_lat, sizeof(float) * c->n_snap * c->r, cudaMemcpyDefault, s));
+  if (g_encoder && c->enc)
+    MPM_CUDA_TRY(cudaMemcpyAsync(g_encoder, c->enc_g, sizeof(float) * c->E.n_params, cudaMemcpyDefault, s));
   if (batch_snap) MPM_CUDA_TRY(cudaMemcpyAsync(batch_snap, c->b.snap, sizeof(int32_t) * c->B, cudaMemcpyDefault, s));
   if (batch_part) MPM_CUDA_TRY(cudaMemcpyAsync(batch_part, c->b.part, sizeof(int32_t) * c->B, cudaMemcpyDefault, s));
   double h = 0.0;
   MPM_CUDA_TRY(cudaMemcpyAsync(&h, c->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   MPM_CUDA_TRY(cudaMemsetAsync(c->gparams, 0, sizeof(float) * c->dec->n_params, s));
   MPM_CUDA_TRY(cudaMemsetAsync(c->g_lat, 0, sizeof(float) * c->n_snap * c->r, s));
+  if (c->enc) MPM_CUDA_TRY(cudaMemsetAsync(c->enc_g, 0, sizeof(float) * c->E.n_params, s));
   MPM_CUDA_TRY(cudaStreamSynchronize(s));
   if (loss) *loss = h / (double)c->B;
   return MPM_OK;
+}
+
+mpm_status trainer_encoder_params(trainer_ctx* c, float* params, float* shift_scale, int64_t* n_params, void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  MPM_CHECK_ARG(c->enc, "the trainer has no encoder (train_config.encoder_subset = 0)");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_params) *n_params = c->E.n_params;
+  if (params) MPM_CUDA_TRY(cudaMemcpyAsync(params, c->enc_p, sizeof(float) * c->E.n_params, cudaMemcpyDefault, s));
+  if (shift_scale) MPM_CUDA_TRY(cudaMemcpyAsync(shift_scale, c->enc_ss, sizeof(float) * 2 * c->d, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return MPM_OK;
+}
+
+mpm_status trainer_set_encoder_params(trainer_ctx* c, const float* params, const float* shift_scale, void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  MPM_CHECK_ARG(c->enc, "the trainer has no encoder (train_config.encoder_subset = 0)");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (params) MPM_CUDA_TRY(cudaMemcpyAsync(c->enc_p, params, sizeof(float) * c->E.n_params, cudaMemcpyDefault, s));
+  if (shift_scale) {
+    MPM_CUDA_TRY(cudaMemcpyAsync(c->enc_ss, shift_scale, sizeof(float) * 2 * c->d, cudaMemcpyDefault, s));
+    mpm_status st = enc_gather(c->E, c->sx, c->snap_base, c->n_snap, c->enc_ss, c->U, s);
+    if (st != MPM_OK) return st;
+  }
+  MPM_CUDA_TRY(cudaMemsetAsync(c->enc_m, 0, sizeof(float) * c->E.n_params, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->enc_v, 0, sizeof(float) * c->E.n_params, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return MPM_OK;
+}
+
+mpm_status trainer_encode(trainer_ctx* c, const float* x, int64_t n, int64_t n_particles, float* latents,
+                          void* stream) {
+  MPM_CHECK_ARG(c && x && latents, "null argument");
+  MPM_CHECK_ARG(c->enc, "the trainer has no encoder (train_config.encoder_subset = 0)");
+  MPM_CHECK_ARG(n >= 0 && n_particles >= c->E.n_sub, "n >= 0 and n_particles >= the encoder subset");
+  if (n == 0) return MPM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = c->d;
+  float *xd = nullptr, *Ud = nullptr, *ld = nullptr;
+  int64_t* base = nullptr;
+  std::vector<int64_t> hb(n + 1);
+  for (int64_t i = 0; i <= n; ++i) hb[i] = i * n_particles;
+  mpm_status st = MPM_OK;
+  cudaError_t e = cudaMalloc((void**)&xd, sizeof(float) * n * n_particles * d);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&Ud, sizeof(float) * n * c->E.L[0]);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ld, sizeof(float) * n * c->r);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&base, sizeof(int64_t) * (n + 1));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(xd, x, sizeof(float) * n * n_particles * d, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(base, hb.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    st = enc_gather(c->E, xd, base, n, c->enc_ss, Ud, s);
+    if (st == MPM_OK) st = enc_forward(c->E, c->enc_p, Ud, n, ld, c->n_sm, s);
+    if (st == MPM_OK) e = cudaMemcpyAsync(latents, ld, sizeof(float) * n * c->r, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  cudaFree(xd);
+  cudaFree(Ud);
+  cudaFree(ld);
+  cudaFree(base);
+  if (e != cudaSuccess) return set_error(MPM_ECUDA, std::string("trainer_encode: ") + cudaGetErrorString(e));
+  return st;
 }
 
 }  // extern "C"

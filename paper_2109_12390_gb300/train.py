@@ -52,7 +52,7 @@ def generate_snapshots(scene, n_steps, every, device="cuda"):
 
 class Trainer:
     def __init__(self, decoder, snaps, *, lambda_F=100.0, lambda_v=0.01, dt_snap, lr0=1e-3, lr1=1e-6,
-                 batch=65536, total_steps=10000, seed=0, latents0=None):
+                 batch=65536, total_steps=10000, seed=0, latents0=None, encoder_subset=0):
         L = _abi.lib()
         self.decoder = decoder
         self.snaps = snaps
@@ -60,13 +60,15 @@ class Trainer:
         sd = _abi.SnapshotDesc(snaps["dim"], snaps["n_inst"], _vp(snaps["inst_offsets"]), _vp(snaps["X"]),
                                snaps["n_snap"], _vp(snaps["snap_inst"]), _vp(snaps["snap_next"]),
                                _vp(snaps["x"]), _vp(snaps["v"]), _vp(snaps["F"]))
-        cfg = _abi.TrainConfig(lambda_F, lambda_v, dt_snap, lr0, lr1, batch, total_steps, seed)
+        cfg = _abi.TrainConfig(lambda_F, lambda_v, dt_snap, lr0, lr1, batch, total_steps, seed, encoder_subset)
         self.cfg = cfg
         lat = None if latents0 is None else np.ascontiguousarray(latents0, np.float32)
         h = C.c_void_p()
         _abi.check(L.trainer_create(decoder._h, C.byref(cfg), C.byref(sd), _vp(lat), C.byref(h)))
         self._h = h
         self.n_snap, self.r, self.batch = snaps["n_snap"], decoder.r, batch
+        self.encoder_subset = int(encoder_subset)
+        self.d = snaps["dim"]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -100,11 +102,46 @@ class Trainer:
         return w.value
 
     def gradients(self, stream=None):
+        """(decoder parameter gradients, per-snapshot latent gradients, batch snapshot ids, batch
+        particle ids, loss) of one forward/backward without update; with an encoder, the encoder's
+        parameter gradients are in self.last_encoder_gradients."""
         gp = np.empty(self.decoder.n_params, np.float32)
         gl = np.empty((self.n_snap, self.r), np.float32)
+        ge = np.empty(self.encoder_n_params(), np.float32) if self.encoder_subset else None
         bs = np.empty(self.batch, np.int32)
         bp = np.empty(self.batch, np.int32)
         loss = C.c_double()
-        _abi.check(_abi.lib().trainer_gradients(self._h, _vp(gp), _vp(gl), _vp(bs), _vp(bp), C.byref(loss),
-                                                _stream(stream)))
+        _abi.check(_abi.lib().trainer_gradients(self._h, _vp(gp), _vp(gl), _vp(ge), _vp(bs), _vp(bp),
+                                                C.byref(loss), _stream(stream)))
+        self.last_encoder_gradients = ge
         return gp, gl, bs, bp, loss.value
+
+    # ---- encoder (train_config.encoder_subset > 0)
+    def encoder_n_params(self):
+        n = C.c_int64()
+        _abi.check(_abi.lib().trainer_encoder_params(self._h, None, None, C.byref(n), None))
+        return n.value
+
+    def encoder_params(self, stream=None):
+        """(parameter vector, shift_scale (2 d))"""
+        p = np.empty(self.encoder_n_params(), np.float32)
+        ss = np.empty(2 * self.d, np.float32)
+        _abi.check(_abi.lib().trainer_encoder_params(self._h, _vp(p), _vp(ss), None, _stream(stream)))
+        return p, ss
+
+    def set_encoder_params(self, params=None, shift_scale=None, stream=None):
+        p = None if params is None else np.ascontiguousarray(params, np.float32)
+        ss = None if shift_scale is None else np.ascontiguousarray(shift_scale, np.float32)
+        _abi.check(_abi.lib().trainer_set_encoder_params(self._h, _vp(p), _vp(ss), _stream(stream)))
+
+    def encode(self, x, stream=None):
+        """x (n, P, d) full-order positions -> (n, r) generalized coordinates."""
+        if isinstance(x, torch.Tensor):
+            x = x.detach().float().contiguous()
+            n, P = x.shape[0], x.shape[1]
+        else:
+            x = np.ascontiguousarray(x, np.float32)
+            n, P = x.shape[0], x.shape[1]
+        out = np.empty((n, self.r), np.float32)
+        _abi.check(_abi.lib().trainer_encode(self._h, _vp(x), int(n), int(P), _vp(out), _stream(stream)))
+        return out

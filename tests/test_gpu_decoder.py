@@ -134,11 +134,12 @@ def test_mixed_rows_of_affine_network_vanish_and_need_partners():
         dec.eval(Xg, latg, [PRIMAL, dX(0), mixed(dX(0))], dirs=ug)  # no JVP row
 
 
-@pytest.mark.parametrize("d,r,n", [(2, 16, 1000), (3, 8, 333)])
+@pytest.mark.parametrize("d,r,n", [(2, 16, 1000), (3, 8, 333), (2, 16, 37), (3, 8, 5)])
 def test_fp32_cuda_core_path_deep_decoder(d, r, n):
     """decoder_set_precision(fp32): the 5-hidden-layer decoder evaluated in FP32 on the CUDA cores
     matches the FP64 oracle to FP32 accuracy for every row kind (primal, tangents, JVP, secant,
-    mixed), and the BF16 tensor-core path stays available on the same object."""
+    mixed), and the BF16 tensor-core path stays available on the same object.  The small sizes
+    pack a few rows per tile, so tiles start in the middle of a point's rows."""
     from paper_2109_12390_gb300.decoder import Decoder, PRIMAL, JVP, SECANT, dX, mixed
     p = _dec_params(d, r, seed=31)
     dec = Decoder.from_params(p)
