@@ -823,20 +823,35 @@ struct RomSolve {
 };
 
 enum { NE_VEL = 0, NE_GN = 1, NE_FIT = 2 };
+constexpr int kNERows = 32;      // normal-equation rows per CTA tile
+
+// One term of a compensated dot product (Ogita, Rump and Oishi, "Accurate sum and dot product",
+// 2005, Dot2): the product x y is split exactly into p + pe by an FMA, p is added to the running
+// sum sh by an error-free two-sum, and both rounding errors are collected in sc.  sh + sc carries
+// the dot product to about twice the working precision.
+// The _rn intrinsics keep the compiler from contracting the product into the sums.
+__device__ __forceinline__ void dot2_term(float x, float y, float& sh, float& sc) {
+  const float p = __fmul_rn(x, y);
+  const float pe = fmaf(x, y, -p);
+  const float t = __fadd_rn(sh, p);
+  const float z = __fsub_rn(t, sh);
+  sc += __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z)) + pe;
+  sh = t;
+}
 
 // Cholesky solve of the SPD system A x = b held in shared memory (A: r x r,
 // row-major, r <= 32) by the block's first warp, synchronised with __syncwarp
-// only; the other warps wait at the final barrier.  Per column one reciprocal
-// square root of the pivot, by Newton-Raphson in FP64 from an FP32 seed
-// (computed by lane 0 and broadcast); the substitutions multiply by the stored
-// reciprocal pivots, so the solve has no FP64 division or square root (long-
-// latency sequences on this GPU).  Returns false, for the whole block, if a
-// pivot is not positive.
+// only; the other warps wait at the final barrier.  Column j: every lane reads
+// the pivot and forms its reciprocal square root itself (Newton-Raphson in FP64
+// from an FP32 seed: no broadcast, no FP64 division or square root, which are
+// long-latency sequences on this GPU); lane q owns row j + 1 + q of the
+// column and of the trailing update.  The substitutions multiply by the stored
+// reciprocal pivots.  Returns false, for the whole block, if a pivot is not
+// positive.
 __device__ bool chol_solve(double* A, double* b, int r) {
   __shared__ int s_bad;
   __shared__ double s_rdiag[kMaxRl];
   if (threadIdx.x < 32) {
-    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x;
     int bad = 0;
     for (int j = 0; j < r; ++j) {
@@ -845,49 +860,42 @@ __device__ bool chol_solve(double* A, double* b, int r) {
         bad = 1;
         break;
       }
-      double l = 0.0, rl = 0.0;
+      // 1 / sqrt(piv) by Newton-Raphson on f(y) = 1/y^2 - piv: y <- y (3 - piv y^2) / 2,
+      // quadratic convergence, two steps from the FP32 seed reach FP64 precision
+      double y = (double)rsqrtf((float)piv);
+      y = y * (1.5 - 0.5 * piv * y * y);
+      y = y * (1.5 - 0.5 * piv * y * y);
+      const int i = j + 1 + lane;
+      double l = 0.0;
+      if (i < r) {
+        l = A[i * r + j] * y;
+        A[i * r + j] = l;
+      }
       if (lane == 0) {
-        // 1 / sqrt(piv) by Newton-Raphson on f(y) = 1/y^2 - piv from an FP32 seed:
-        // y <- y (3 - piv y^2) / 2, quadratic convergence, two steps reach FP64 precision
-        double y = (double)rsqrtf((float)piv);
-        y = y * (1.5 - 0.5 * piv * y * y);
-        y = y * (1.5 - 0.5 * piv * y * y);
-        rl = y;
-        l = piv * y;
+        A[j * r + j] = piv * y;
+        s_rdiag[j] = y;
       }
-      l = __shfl_sync(full, l, 0);
-      rl = __shfl_sync(full, rl, 0);
       __syncwarp();
-      if (lane == 0) {
-        A[j * r + j] = l;
-        s_rdiag[j] = rl;
-      }
-      for (int i = j + 1 + lane; i < r; i += 32) A[i * r + j] *= rl;
-      __syncwarp();
-      const int m = r - j - 1;
-      for (int e = lane; e < m * m; e += 32) {
-        const int i = j + 1 + e / m, c = j + 1 + e % m;
-        if (c <= i) A[i * r + c] -= A[i * r + j] * A[c * r + j];
-      }
+      if (i < r)
+        for (int k = j + 1; k <= i; ++k) A[i * r + k] -= l * A[k * r + j];
       __syncwarp();
     }
     if (!bad) {
-      // L y = b
-      for (int i = 0; i < r; ++i) {
-        double yi = 0.0;
-        if (lane == 0) yi = b[i] * s_rdiag[i];
-        yi = __shfl_sync(full, yi, 0);
-        if (lane == 0) b[i] = yi;
-        for (int k = i + 1 + lane; k < r; k += 32) b[k] -= A[k * r + i] * yi;
+      // L y = b, by columns
+      for (int k = 0; k < r; ++k) {
+        const double yk = b[k] * s_rdiag[k];
+        __syncwarp();
+        if (lane == 0) b[k] = yk;
+        const int i = k + 1 + lane;
+        if (i < r) b[i] -= A[i * r + k] * yk;
         __syncwarp();
       }
-      // L^T x = y
+      // L^T x = y, by rows of L
       for (int i = r - 1; i >= 0; --i) {
-        double xi = 0.0;
-        if (lane == 0) xi = b[i] * s_rdiag[i];
-        xi = __shfl_sync(full, xi, 0);
+        const double xi = b[i] * s_rdiag[i];
+        __syncwarp();
         if (lane == 0) b[i] = xi;
-        for (int k = lane; k < i; k += 32) b[k] -= A[i * r + k] * xi;
+        if (lane < i) b[lane] -= A[i * r + lane] * xi;
         __syncwarp();
       }
     }
@@ -895,6 +903,108 @@ __device__ bool chol_solve(double* A, double* b, int r) {
   }
   __syncthreads();
   return !s_bad;
+}
+
+// Solve of the same SPD system by an FP32 Cholesky factor with iterative refinement in FP64
+// (the first warp; FP64 arithmetic has a ~65-cycle dependent latency on this GPU, FP32 ~5): the
+// correction of each sweep solves L L^T d = b - A x with the FP32 factor, the residual is formed in
+// FP64 from the unmodified A, and the sweeps stop once the correction is below 2^-40 of x (the
+// entries of A and b, assembled by compensated FP32 sums, carry about that relative accuracy).
+// Converges when cond(A) is well below 1 / FP32 epsilon; returns false (A and b untouched) if the
+// FP32 factorisation breaks down or 8 sweeps do not converge, and the caller falls back to
+// chol_solve.  On success b holds the solution.
+__device__ bool chol_solve_refined(const double* A, double* b, int r) {
+  __shared__ float L[kMaxRl * kMaxRl];
+  __shared__ float s_rd[kMaxRl];
+  __shared__ float s_v[kMaxRl];
+  __shared__ double s_x[kMaxRl];
+  __shared__ int s_ok;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int e = lane; e < r * r; e += 32) L[e] = (float)A[e];
+    __syncwarp();
+    int ok = 1;
+    for (int j = 0; j < r; ++j) {
+      const float piv = L[j * r + j];
+      if (!(piv > 0.f) || !(piv < 3.0e38f)) {
+        ok = 0;
+        break;
+      }
+      const float y = rsqrtf(piv);
+      const int i = j + 1 + lane;
+      float l = 0.f;
+      if (i < r) {
+        l = L[i * r + j] * y;
+        L[i * r + j] = l;
+      }
+      if (lane == 0) {
+        L[j * r + j] = piv * y;
+        s_rd[j] = y;
+      }
+      __syncwarp();
+      if (i < r)
+        for (int k = j + 1; k <= i; ++k) L[i * r + k] -= l * L[k * r + j];
+      __syncwarp();
+    }
+    int conv = 0;
+    if (ok) {
+      if (lane < r) {
+        s_x[lane] = 0.0;
+        s_v[lane] = (float)b[lane];
+      }
+      __syncwarp();
+      for (int sweep = 0; sweep < 8 && !conv; ++sweep) {
+        // L L^T d = v (FP32), d overwrites v
+        for (int k = 0; k < r; ++k) {
+          const float yk = s_v[k] * s_rd[k];
+          __syncwarp();
+          if (lane == 0) s_v[k] = yk;
+          const int i = k + 1 + lane;
+          if (i < r) s_v[i] -= L[i * r + k] * yk;
+          __syncwarp();
+        }
+        for (int i = r - 1; i >= 0; --i) {
+          const float xi = s_v[i] * s_rd[i];
+          __syncwarp();
+          if (lane == 0) s_v[i] = xi;
+          if (lane < i) s_v[lane] -= L[i * r + lane] * xi;
+          __syncwarp();
+        }
+        // x += d; residual b - A x in FP64 (four independent partial sums per row)
+        float dmax = 0.f, xmax = 0.f;
+        if (lane < r) {
+          const double xn = s_x[lane] + (double)s_v[lane];
+          s_x[lane] = xn;
+          dmax = fabsf(s_v[lane]);
+          xmax = fabsf((float)xn);
+        }
+        __syncwarp();
+        if (lane < r) {
+          double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+          int jj = 0;
+          for (; jj + 3 < r; jj += 4) {
+            p0 = fma(A[lane * r + jj], s_x[jj], p0);
+            p1 = fma(A[lane * r + jj + 1], s_x[jj + 1], p1);
+            p2 = fma(A[lane * r + jj + 2], s_x[jj + 2], p2);
+            p3 = fma(A[lane * r + jj + 3], s_x[jj + 3], p3);
+          }
+          for (; jj < r; ++jj) p0 = fma(A[lane * r + jj], s_x[jj], p0);
+          s_v[lane] = (float)(b[lane] - ((p0 + p1) + (p2 + p3)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+          xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        }
+        conv = dmax <= 9.1e-13f * xmax;   // 2^-40 of x: below the accuracy of the assembled system
+        __syncwarp();
+      }
+    }
+    if (conv && lane < r) b[lane] = s_x[lane];
+    if (lane == 0) s_ok = conv;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, const float* __restrict__ dec,
@@ -905,32 +1015,51 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
   const int rows = nP * d;
   const int n_mat = r * (r + 1) / 2;
   const int n_acc = n_mat + r + 1;
-  __shared__ double sJ[64][kMaxRl + 1];
-  __shared__ double sb[64];
+  __shared__ float sJ[kNERows][kMaxRl + 1];
+  __shared__ float sb[kNERows];
   __shared__ bool s_last;
-  for (int row0 = blockIdx.x * 64; row0 < rows; row0 += gridDim.x * 64) {
-    const int nr = min(64, rows - row0);
-    for (int e = threadIdx.x; e < nr * (r + 1); e += blockDim.x) {
-      const int rr = e / (r + 1), c = e % (r + 1);
+  // hi / lo FP32 split of vhat_n (FP64) for the velocity right-hand side
+  __shared__ float s_vh_hi[kMaxRl], s_vh_lo[kMaxRl];
+  if (mode == NE_VEL && threadIdx.x < r) {
+    const double v = S.vh[threadIdx.x];
+    const float hi = (float)v;
+    s_vh_hi[threadIdx.x] = hi;
+    s_vh_lo[threadIdx.x] = (float)(v - (double)hi);
+  }
+  __syncthreads();
+  for (int row0 = blockIdx.x * kNERows; row0 < rows; row0 += gridDim.x * kNERows) {
+    const int nr = min(kNERows, rows - row0);
+    for (int e = threadIdx.x; e < nr * r; e += blockDim.x) {
+      const int rr = e / r, c = e % r;
       const int row = row0 + rr, p = row / d, a = row % d;
-      if (c < r) {
-        sJ[rr][c] = dec[((size_t)(1 + c) * cap + p) * d + a];
-      } else {
-        double b;
-        if (mode == NE_VEL) {
-          // right-hand side of the velocity increment: v_trial - J vhat_n
-          double jv = 0.0;
-          for (int c2 = 0; c2 < r; ++c2) jv = fma((double)dec[((size_t)(1 + c2) * cap + p) * d + a], S.vh[c2], jv);
-          b = (double)R.v_trial[(size_t)p * d + a] - jv;
+      sJ[rr][c] = dec[((size_t)(1 + c) * cap + p) * d + a];
+    }
+    if (threadIdx.x < nr) {
+      const int rr = threadIdx.x;
+      const int row = row0 + rr, p = row / d, a = row % d;
+      float b;
+      if (mode == NE_VEL) {
+        // right-hand side of the velocity increment: v_trial - J vhat_n, J vhat_n by a compensated
+        // dot product of the FP32 row with the hi / lo parts of vhat_n
+        float sh = 0.f, sc = 0.f;
+        for (int c = 0; c < r; ++c) {
+          const float x = dec[((size_t)(1 + c) * cap + p) * d + a];
+          dot2_term(x, s_vh_hi[c], sh, sc);
+          dot2_term(x, s_vh_lo[c], sh, sc);
         }
-        else if (mode == NE_GN) b = dec[((size_t)(1 + r) * cap + p) * d + a] + R.dt * R.v_trial[(size_t)p * d + a];
-        else b = target[(size_t)p * d + a] - dec[(size_t)p * d + a];
-        sb[rr] = b;
+        b = (R.v_trial[(size_t)p * d + a] - sh) - sc;
+      } else if (mode == NE_GN) {
+        b = dec[((size_t)(1 + r) * cap + p) * d + a] + R.dt * R.v_trial[(size_t)p * d + a];
+      } else {
+        b = target[(size_t)p * d + a] - dec[(size_t)p * d + a];
       }
+      sb[rr] = b;
     }
     __syncthreads();
+    // entries of J^T J (upper triangle), J^T b and b^T b over this tile's rows: compensated FP32
+    // dot products (Dot2: exact products by FMA, error-free sums), added in FP64
     for (int e = threadIdx.x; e < n_acc; e += blockDim.x) {
-      double s = 0.0;
+      float sh = 0.f, sc = 0.f;
       if (e < n_mat) {
         // upper-triangle index e -> (i, j), i <= j
         int i = 0, rem = e;
@@ -939,14 +1068,14 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
           ++i;
         }
         const int j = i + rem;
-        for (int q = 0; q < nr; ++q) s = fma(sJ[q][i], sJ[q][j], s);
+        for (int q = 0; q < nr; ++q) dot2_term(sJ[q][i], sJ[q][j], sh, sc);
       } else if (e < n_mat + r) {
         const int i = e - n_mat;
-        for (int q = 0; q < nr; ++q) s = fma(sJ[q][i], sb[q], s);
+        for (int q = 0; q < nr; ++q) dot2_term(sJ[q][i], sb[q], sh, sc);
       } else {
-        for (int q = 0; q < nr; ++q) s = fma(sb[q], sb[q], s);
+        for (int q = 0; q < nr; ++q) dot2_term(sb[q], sb[q], sh, sc);
       }
-      atomicAdd(&S.acc[e], s);
+      atomicAdd(&S.acc[e], (double)sh + (double)sc);
     }
     __syncthreads();
   }
@@ -1002,7 +1131,7 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) A[e] = A_keep[e] + ((e / r) == (e % r) ? ridge_abs : 0.0);
     for (int i = threadIdx.x; i < r; i += blockDim.x) bvec[i] = s_rhs[i];
     __syncthreads();
-    ok = chol_solve(A, bvec, r);
+    ok = chol_solve_refined(A, bvec, r) || chol_solve(A, bvec, r);
   }
   if (!ok) {
     if (threadIdx.x == 0) raise_status(R.status, STATUS_CHOLESKY);
@@ -1289,7 +1418,7 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
   ks[0] = 0;
   for (int j = 0; j < r; ++j) ks[1 + j] = 1 + d + j;
   const int b_s = std::max(1, ceil_div(c->k, 128));
-  const int b_ne = std::max(1, std::min(ceil_div((int64_t)c->k * d, 64), 64));
+  const int b_ne = std::max(1, std::min(ceil_div((int64_t)c->k * d, kNERows), 64));
   const int M = c->cfg.material, T = c->cfg.transfer;
   if (c->eulerian) {
     // Algorithm 4.  1. samples
@@ -1801,7 +1930,7 @@ mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int
   ks[0] = 0;
   for (int j = 0; j < r; ++j) ks[1 + j] = 1 + d + j;
   int kls[2] = {0, 1001};
-  const int b_ne = std::max(1, std::min(ceil_div((int64_t)P * d, 64), c->n_sm));
+  const int b_ne = std::max(1, std::min(ceil_div((int64_t)P * d, kNERows), c->n_sm));
   mpm_status st = MPM_OK;
   for (int it = 0; it < iters && st == MPM_OK; ++it) {
     st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, P, c->sv.xk32, nullptr, ks, r + 1, c->outS, s);
