@@ -16,7 +16,11 @@ Readings where the paper is silent (each listed in the design notes):
     in MLS mode the basis gradient is replaced by its moving-least-squares
     counterpart (4 / dx^2) N_i (x_i - x_p) and F is updated with C_p;
   * constitutive laws: neo-Hookean and fixed-corotated (Stomakhin et al. 2012,
-    the paper's material), Lame parameters from (E, nu);
+    the paper's material), Lame parameters from (E, nu); a plastic variant of
+    the fixed-corotated material (material 2: after the F update the singular
+    values are clamped to [1 - theta_c, 1 + theta_s], Stomakhin et al. 2013
+    without hardening) for plastic bodies, which the reduced model does not
+    cover;
   * the internal force enters the grid momentum as dt f_i (same arithmetic as
     the grid update of Algorithm 1, summed before the division by m_i);
   * boundaries: nodes with any index < w or > n - 1 - w are wall nodes; sticky
@@ -37,7 +41,7 @@ import itertools
 import numpy as np
 
 MLS, PIC = 0, 1
-NEO_HOOKEAN, FIXED_COROTATED = 0, 1
+NEO_HOOKEAN, FIXED_COROTATED, FIXED_COROTATED_PLASTIC = 0, 1, 2
 BC_STICKY, BC_SLIP_FLOOR = 0, 1
 
 
@@ -107,6 +111,34 @@ def polar_rotation(F: np.ndarray) -> np.ndarray:
     U[..., :, -1] *= np.where(detU < 0, -1.0, 1.0)[..., None]
     Vt[..., -1, :] *= np.where(detV < 0, -1.0, 1.0)[..., None]
     return U @ Vt
+
+
+def signed_svd(F):
+    """F = U diag(s) V^T with U, V proper rotations (det +1): when det U or det V is negative the
+    last column is negated and the sign moves to the smallest singular value."""
+    U, s, Vt = np.linalg.svd(F)
+    detU = np.linalg.det(U)
+    detV = np.linalg.det(Vt)
+    U, s, Vt = U.copy(), s.copy(), Vt.copy()
+    flipU = detU < 0
+    flipV = detV < 0
+    U[..., :, -1] *= np.where(flipU, -1.0, 1.0)[..., None]
+    Vt[..., -1, :] *= np.where(flipV, -1.0, 1.0)[..., None]
+    s[..., -1] *= np.where(flipU ^ flipV, -1.0, 1.0)
+    return U, s, Vt
+
+
+def plastic_return(F, lo, hi):
+    """Return mapping of the plastic material (material 2): the elastic deformation gradient keeps
+    its rotations, its singular values are clamped to [lo, hi] (lo = 1 - theta_c, hi = 1 +
+    theta_s), the excess is plastic flow (Stomakhin et al. 2013, without hardening).  Particles
+    whose singular values are all inside the bounds keep F unchanged."""
+    U, s, Vt = signed_svd(F)
+    c = np.clip(s, lo, hi)
+    out = np.array(F, np.float64, copy=True)
+    moved = np.any(c != s, axis=-1)
+    out[moved] = np.einsum("pij,pj,pjk->pik", U[moved], c[moved], Vt[moved])
+    return out
 
 
 def energy(F, material, mu, lam):
@@ -283,6 +315,8 @@ def step(scene, n_steps: int = 1, return_grid: bool = False):
                              bc_width=scene.bc_width)
             xn, vn, Fn, Cn = g2p(scene.x[s], scene.F[s], vg, dx=scene.dx, dt=scene.dt,
                                  transfer=scene.transfer)
+            if scene.material == FIXED_COROTATED_PLASTIC:
+                Fn = plastic_return(Fn, 1.0 - scene.theta_c, 1.0 + scene.theta_s)
             scene.x[s], scene.v[s], scene.F[s], scene.C[s] = xn, vn, Fn, Cn
             if return_grid:
                 grids.append((m, p, vg))

@@ -54,6 +54,9 @@ class Scene:
     v: np.ndarray                # (P, d)
     F: np.ndarray                # (P, d, d)
     C: np.ndarray                # (P, d, d)
+    # plastic material (material 2): singular values of F kept in [1 - theta_c, 1 + theta_s]
+    theta_c: float = 2.5e-2
+    theta_s: float = 7.5e-3
 
     @property
     def n_inst(self) -> int:
@@ -258,3 +261,20 @@ def near_identity_decoder(seed: int, d: int, r: int, n_hidden: int = 1, X_min=No
     Wo[:, :d] = np.diag(p.X_range)
     p.b[-1][:] = p.X_min - p.X_range
     return p
+
+
+def refine_block_2d(sc: Scene, factor: int = 2) -> Scene:
+    """The same single 2D block (a dx/2 lattice) discretised `factor` times finer: particles at
+    (dx / factor) / 2 spacing over the same extent, a grid of factor x n_grid nodes, the same
+    material and initial velocity (super-resolution scenes of Section 5)."""
+    assert sc.dim == 2 and sc.n_inst == 1
+    h = sc.dx / 2
+    lo = sc.x.min(0) - 0.5 * h
+    counts = np.round((sc.x.max(0) + 0.5 * h - lo) / h).astype(int)
+    dxf = sc.dx / factor
+    x = _lattice(tuple(counts * factor), dxf / 2, lo)
+    v = np.broadcast_to(sc.v[0], x.shape).copy()
+    F, C = _identity_state(x)
+    return dataclasses.replace(sc, n_grid=sc.n_grid * factor, dx=dxf, p_vol=(dxf / 2) ** 2,
+                               inst_offsets=np.array([0, len(x)], np.int64), x=x, v=v, F=F, C=C,
+                               gravity=sc.gravity.copy(), E=sc.E.copy(), nu=sc.nu.copy())

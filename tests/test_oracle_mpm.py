@@ -267,3 +267,62 @@ def test_free_stressed_steps_conserve_momenta(d):
             assert np.abs(L1 - L0).max() <= 1e-12 * np.abs(L0).max()
         else:
             assert np.abs(L1 - L0).max() > 1e-4 * np.abs(L0).max()
+
+
+def _rot2(a):
+    return np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+
+
+def _rot3(rng):
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    return q * np.sign(np.linalg.det(q))
+
+
+def test_plastic_return_closed_forms():
+    """Material 2: singular values clamped to [1 - theta_c, 1 + theta_s], rotations kept."""
+    lo, hi = 1 - 2.5e-2, 1 + 7.5e-3
+    R1, R2 = _rot2(0.3), _rot2(-1.1)
+    F = R1 @ np.diag([1.2, 0.9]) @ R2.T
+    out = M.plastic_return(F[None], lo, hi)[0]
+    np.testing.assert_allclose(out, R1 @ np.diag([hi, lo]) @ R2.T, rtol=0, atol=1e-14)
+    rng = np.random.default_rng(0)
+    Q1, Q2 = _rot3(rng), _rot3(rng)
+    F3 = Q1 @ np.diag([1.02, 0.99, 0.95]) @ Q2.T
+    out3 = M.plastic_return(F3[None], lo, hi)[0]
+    np.testing.assert_allclose(out3, Q1 @ np.diag([hi, 0.99, lo]) @ Q2.T, rtol=0, atol=1e-14)
+    # inside the bounds: unchanged, bit for bit
+    Fe = Q1 @ np.diag([1.005, 0.99, 0.98]) @ Q2.T
+    assert np.array_equal(M.plastic_return(Fe[None], lo, hi)[0], Fe)
+
+
+def test_plastic_return_invariants():
+    rng = np.random.default_rng(1)
+    lo, hi = 0.9, 1.05
+    F = np.eye(3)[None] + 0.2 * rng.normal(size=(200, 3, 3))
+    F = F[np.linalg.det(F) > 0.2]
+    out = M.plastic_return(F, lo, hi)
+    s = np.linalg.svd(out, compute_uv=False)
+    assert s.min() >= lo - 1e-12 and s.max() <= hi + 1e-12
+    np.testing.assert_allclose(M.polar_rotation(out), M.polar_rotation(F), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(M.plastic_return(out, lo, hi), out, rtol=0, atol=1e-13)
+
+
+def test_plastic_material_with_wide_bounds_is_the_elastic_material():
+    sc = S.block_2d(side=8, dt=5e-5)
+    rng = np.random.default_rng(2)
+    sc.F = S.random_deformation(rng, sc.n_particles, 2, 0.05)
+    sc.material = M.FIXED_COROTATED
+    a = sc.copy()
+    b = sc.copy()
+    b.material = M.FIXED_COROTATED_PLASTIC
+    b.theta_c, b.theta_s = 0.9, 10.0
+    M.step(a, 5)
+    M.step(b, 5)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.F, b.F)
+    # with the snow bounds the same motion yields plastically: the singular values stay inside
+    c = sc.copy()
+    c.material = M.FIXED_COROTATED_PLASTIC
+    M.step(c, 5)
+    s = np.linalg.svd(c.F, compute_uv=False)
+    assert s.max() <= 1 + c.theta_s + 1e-12 and s.min() >= 1 - c.theta_c - 1e-12
+    assert not np.allclose(c.F, a.F)
