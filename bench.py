@@ -177,6 +177,7 @@ ROM_CHECKPOINT = 2000
 ROM_TRAIN_STEPS = 12000
 ROM_TRAIN_INSTANCES = 32
 ROM_TESTS = 4
+ENCODER_SUBSET = 1024
 ROM_SETTINGS = dict(n_samples=256, gn_iters=3, projection=0, ridge=1e-1, affine=0, f_reference=1)
 ROM_DECODER_FP32 = True     # reduced-step decoder calls in FP32 on the CUDA cores (training stays BF16)
 
@@ -248,6 +249,7 @@ def rom_serving(dec, n_inst=8, steps=200):
     import torch
     from paper_2109_12390_gb300.rom import ROM
     rng = np.random.default_rng(55)
+    dec.set_concurrency(n_inst)   # fewer, fuller FP32 tiles per call: the instances share the SMs
     roms, streams = [], []
     for _ in range(n_inst):
         E = float(rng.uniform(5e3, 1.5e4))
@@ -280,6 +282,7 @@ def rom_serving(dec, n_inst=8, steps=200):
     status = [rom.status() for rom in roms]
     for rom in roms:
         rom.close()
+    dec.set_concurrency(1)
     return {"instances": n_inst, "steps_each": steps, "aggregate_rom_steps_per_s": n_inst * steps / (wall_ms * 1e-3),
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "status_words": status, "how": "one CUDA stream and one captured step graph per instance"}
@@ -342,6 +345,18 @@ def rom_leg(r=16, train_steps=None, steps=None):
                                              "rel_error_full": e_lag.error_percent / 100.0,
                                              "rom_steps_per_s": e_lag.rom_steps_per_s},
                 "settings": eul_settings, "steps": ck}
+    # decoder trained with the encoder of Section 4.1 (1024 of the 4096 particles per snapshot) in
+    # place of the latent table, same steps and settings; first test
+    enc_dec, _ = PL.decoder_for_snapshots(snaps, r, seed=0)
+    tre, histe, t_enc = PL.train(snaps, enc_dec, steps=train_steps, encoder_subset=ENCODER_SUBSET)
+    tre.close()
+    enc_dec.set_precision(ROM_DECODER_FP32)
+    e_enc = PL.rom_error(enc_dec, t0s["scene"], t0s["fom"], seed=4, checkpoints=(ck,), **ROM_SETTINGS)
+    encoder = {"subset": ENCODER_SUBSET, "training_steps": train_steps, "training_seconds": t_enc,
+               "ms_per_step": 1e3 * t_enc / train_steps, "final_loss": histe[-1][1],
+               "rel_error_at_checkpoint": e_enc.error_percent_at[ck] / 100.0,
+               "rel_error_full": e_enc.error_percent / 100.0, "status_word": e_enc.status, "steps": ck,
+               "latent_table_same_test": per_test[0]["rel_error_at_checkpoint"]}
     cpu = cpu_baseline_rom(dec, tests[0]["scene"], r)
     serving = rom_serving(dec, n_inst=8, steps=min(200, steps))
     return {
@@ -358,6 +373,7 @@ def rom_leg(r=16, train_steps=None, steps=None):
                  "trained_linear_manifold": e_linear, "linear_training_steps": max(1, train_steps // 4),
                  "steps": ck},
         "eulerian_quadrature": eulerian,
+        "encoder": encoder,
         "training": {"steps": train_steps, "batch_points": 65536, "seconds": t_train,
                      "points_per_s": train_steps * 65536 / t_train, "ms_per_step": 1e3 * t_train / train_steps,
                      "final_loss": loss, "snapshot_seconds": t_snap, "snapshots": int(snaps["n_snap"])},

@@ -55,7 +55,7 @@ enum {
 };
 
 enum { MPM_TRANSFER_MLS = 0, MPM_TRANSFER_PIC = 1 };
-enum { MPM_NEO_HOOKEAN = 0, MPM_FIXED_COROTATED = 1 };
+enum { MPM_NEO_HOOKEAN = 0, MPM_FIXED_COROTATED = 1, MPM_FIXED_COROTATED_PLASTIC = 2 };
 enum { MPM_BC_STICKY = 0, MPM_BC_SLIP_FLOOR = 1 };
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
@@ -79,7 +79,12 @@ const char* mpm_last_error(void);
  *                 the low-y band clamps v_y >= 0; the other walls are sticky.
  *   material      MPM_NEO_HOOKEAN or MPM_FIXED_COROTATED (Stomakhin et al.
  *                 2012, the material of Section 5); Lame parameters from
- *                 (E, nu) per instance.
+ *                 (E, nu) per instance.  MPM_FIXED_COROTATED_PLASTIC: the
+ *                 fixed-corotated law on an elastic F whose singular values
+ *                 are clamped, after every F update, to
+ *                 [1 - plastic_compression, 1 + plastic_stretch] (a
+ *                 snow-like plastic body, Stomakhin et al. 2013 without
+ *                 hardening; the reduced-order model does not cover it).
  *   transfer      MPM_TRANSFER_MLS (MLS-MPM with APIC affine velocity, the
  *                 default) or MPM_TRANSFER_PIC (the literal transfers of
  *                 Algorithm 1 with exact basis gradients).
@@ -97,6 +102,8 @@ const char* mpm_last_error(void);
  *                 transformations (as accurate as twice FP32 precision, at
  *                 FP32 throughput; GB300's FP64 rate is a small fraction of
  *                 its FP32 rate).
+ *   plastic_compression, plastic_stretch   theta_c, theta_s of the plastic
+ *                 material (e.g. 2.5e-2, 7.5e-3); ignored otherwise.
  */
 typedef struct mpm_config {
   int32_t dim;
@@ -115,6 +122,8 @@ typedef struct mpm_config {
   const float* nu;
   const int64_t* inst_offsets;
   int32_t polar_eft;
+  float plastic_compression;
+  float plastic_stretch;
 } mpm_config;
 
 typedef struct mpm_ctx mpm_ctx;
@@ -331,6 +340,16 @@ mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void*
  */
 mpm_status decoder_set_precision(mpm_decoder* dec, int fp32);
 
+/*
+ * Expected number of decoder calls running at the same time on different
+ * streams (k >= 1, default 1).  The FP32 path spreads a call's rows over about
+ * (SM count / k) tiles: one tile per SM gives the lowest latency to a single
+ * caller, fewer and fuller tiles leave SMs to concurrent callers (many
+ * reduced-order instances served at once).  Affects launches made, and step
+ * graphs captured, afterwards.  Errors: MPM_EINVAL.
+ */
+mpm_status decoder_set_concurrency(mpm_decoder* dec, int k);
+
 /* ======================================================================
  * Reduced-order step (Algorithm 2 with Lagrangian quadrature: Algorithms 3,
  * 5 and 6 or 7) and the accumulated position error (Section 5)
@@ -496,6 +515,15 @@ mpm_status rom_debug_quadrature(rom_ctx* ctx, int32_t* n_points, float* x_points
 
 /* g(X^p; xhat_n) for every particle into device array x_out (n_particles, dim). */
 mpm_status rom_decode_all(rom_ctx* ctx, float* x_out, void* stream);
+
+/*
+ * g(X; xhat_n) at n reference positions X (n, dim) that need not be particles of
+ * the context: the decoder is defined on the whole reference domain, so the
+ * reduced state can be rendered at any resolution (the zero-shot
+ * super-resolution of Section 5).  X and x_out are device arrays.  Asynchronous
+ * on `stream`.
+ */
+mpm_status rom_decode_points(rom_ctx* ctx, const float* X, int64_t n, float* x_out, void* stream);
 
 /*
  * Accumulated position error of Section 5: acc[0] += sum_i (a_i - b_i)^2,

@@ -26,6 +26,7 @@ class MpmConfig(C.Structure):
         ("material", C.c_int32), ("transfer", C.c_int32), ("rho", C.c_float), ("p_vol", C.c_float),
         ("n_inst", C.c_int32), ("E", C.POINTER(C.c_float)), ("nu", C.POINTER(C.c_float)),
         ("inst_offsets", C.POINTER(C.c_int64)), ("polar_eft", C.c_int32),
+        ("plastic_compression", C.c_float), ("plastic_stretch", C.c_float),
     ]
 
 
@@ -93,6 +94,7 @@ SIGNATURES = [
                                C.POINTER(C.c_int32), C.c_int, C.c_int64, C.c_void_p, C.c_void_p]),
     ("decoder_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
     ("decoder_set_precision", C.c_int, [C.c_void_p, C.c_int]),
+    ("decoder_set_concurrency", C.c_int, [C.c_void_p, C.c_int]),
     ("rom_create", C.c_int, [C.POINTER(RomConfig), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
     ("rom_destroy", None, [C.c_void_p]),
     ("rom_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
@@ -104,6 +106,7 @@ SIGNATURES = [
     ("rom_debug", C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),
     ("rom_debug_quadrature", C.c_int, [C.c_void_p, C.POINTER(C.c_int32)] + [C.c_void_p] * 4 + [C.c_void_p]),
     ("rom_decode_all", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rom_decode_points", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("metric_accumulate", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("trainer_create", C.c_int, [C.c_void_p, C.POINTER(TrainConfig), C.POINTER(SnapshotDesc), C.c_void_p,
                                  C.POINTER(C.c_void_p)]),

@@ -772,6 +772,13 @@ void decoder_destroy(mpm_decoder* dec) {
 
 int64_t decoder_num_params(const mpm_decoder* dec) { return dec ? dec->n_params : 0; }
 
+mpm_status decoder_set_concurrency(mpm_decoder* dec, int k) {
+  MPM_CHECK_ARG(dec, "null decoder");
+  MPM_CHECK_ARG(k >= 1, "k >= 1");
+  dec->concurrency = k;
+  return MPM_OK;
+}
+
 mpm_status decoder_set_precision(mpm_decoder* dec, int fp32) {
   MPM_CHECK_ARG(dec, "null decoder");
   MPM_CHECK_ARG(fp32 == 0 || fp32 == 1, "fp32: 0 or 1");
@@ -889,9 +896,10 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
       a.Pt = kF32Rows / R;
       tiles = (n + a.Pt - 1) / a.Pt;
     } else {
-      // packed tiles: about one per SM, 32 or 64 slots
+      // packed tiles: about one per SM (per SM share of the concurrent callers), 32 or 64 slots
       const int64_t rows = n * R;
-      const int64_t U = std::max<int64_t>(1, std::min<int64_t>((rows + dec->n_sm - 1) / dec->n_sm, kF32Rows - 1));
+      const int64_t target = std::max(1, dec->n_sm / std::max(1, dec->concurrency));
+      const int64_t U = std::max<int64_t>(1, std::min<int64_t>((rows + target - 1) / target, kF32Rows - 1));
       a.f32_U = (int)U;
       a.Pt = 1;
       small = U + 1 <= 32;

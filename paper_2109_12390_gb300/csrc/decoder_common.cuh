@@ -220,6 +220,7 @@ struct mpm_decoder {
   int n_sm = 0;
   size_t smem = 0;
   int fp32 = 0;                       // evaluate square layers in FP32 on the CUDA cores
+  int concurrency = 1;                // expected concurrent calls (FP32 tiling)
 };
 
 namespace mpmrom {

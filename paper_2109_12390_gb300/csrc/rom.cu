@@ -1882,6 +1882,15 @@ mpm_status rom_decode_all(rom_ctx* c, float* x_out, void* stream) {
   return st;
 }
 
+mpm_status rom_decode_points(rom_ctx* c, const float* X, int64_t n, float* x_out, void* stream) {
+  MPM_CHECK_ARG(c && (X || n == 0) && (x_out || n == 0), "null argument");
+  MPM_CHECK_ARG(n >= 0, "n >= 0");
+  if (n == 0) return MPM_OK;
+  int k_primal[1] = {0};
+  return decoder_launch_dev(c->dec, X, nullptr, nullptr, 1, n, c->sv.xh32, nullptr, k_primal, 1, x_out,
+                            (cudaStream_t)stream);
+}
+
 mpm_status rom_set_reference(rom_ctx* c, const double* xhat_ref, void* stream) {
   MPM_CHECK_ARG(c && xhat_ref, "null argument");
   MPM_CHECK_ARG(c->cfg.f_reference == 1, "rom_set_reference needs cfg.f_reference = 1");

@@ -85,6 +85,11 @@ class Decoder:
         contexts created afterwards); False: BF16 tensor cores."""
         _abi.check(_abi.lib().decoder_set_precision(self._h, int(bool(fp32))))
 
+    def set_concurrency(self, k):
+        """Expected number of concurrent calls on different streams (FP32 tiling; see
+        decoder_set_concurrency)."""
+        _abi.check(_abi.lib().decoder_set_concurrency(self._h, int(k)))
+
     def status(self, clear=True, stream=None):
         w = C.c_uint32()
         _abi.check(_abi.lib().decoder_status_word(self._h, C.byref(w), int(clear), _stream(stream)))

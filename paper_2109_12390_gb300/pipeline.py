@@ -32,10 +32,12 @@ def decoder_for_snapshots(snaps, r, seed=0, width=128, n_hidden=5, activation=0)
 
 
 def train(snaps, decoder, *, steps, batch=65536, lambda_F=100.0, lambda_v=0.01, lr0=1e-3, lr1=1e-6, seed=0,
-          report_every=0):
+          report_every=0, encoder_subset=0):
+    """Trains the decoder with a latent table (encoder_subset = 0) or with the encoder of Section 4.1 on
+    encoder_subset particles per snapshot."""
     dt_snap = float(snaps["dt_snap"])
     tr = Trainer(decoder, snaps, lambda_F=lambda_F, lambda_v=lambda_v, dt_snap=dt_snap, lr0=lr0, lr1=lr1,
-                 batch=batch, total_steps=steps, seed=seed)
+                 batch=batch, total_steps=steps, seed=seed, encoder_subset=encoder_subset)
     history = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()

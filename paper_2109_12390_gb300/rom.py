@@ -129,6 +129,15 @@ class ROM:
         return out
 
 
+    def decode_points(self, X, out=None, stream=None):
+        """g(X; xhat_n) at arbitrary reference positions X (n, d) CUDA tensor (super-resolution)."""
+        X = X.contiguous()
+        if out is None:
+            out = torch.empty((X.shape[0], self.d), dtype=torch.float32, device=X.device)
+        _abi.check(_abi.lib().rom_decode_points(self._h, _ptr(X), int(X.shape[0]), _ptr(out), _stream(stream)))
+        return out
+
+
 def metric_accumulate(a, b, acc, stream=None):
     """acc (2,) float64 CUDA tensor += [sum (a - b)^2, sum b^2] (Section 5 error metric)."""
     _abi.check(_abi.lib().metric_accumulate(_ptr(a), _ptr(b), a.numel(), _p64(acc), _stream(stream)))
