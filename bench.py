@@ -454,8 +454,11 @@ def run_ours(args, ws, rank, local):
     # the same workload with the compensated-FP32 rotation correction of the polar factor, and a
     # scaled-up cube (2,097,152 particles on 256^3, working set far above L2)
     variants = {}
+    plastic = sc.copy()
+    plastic.material = 2   # plastic fixed-corotated (singular values clamped), second workload
     extra = () if args.profile else (("polar_eft", sc, 1),
-                                     ("cube_2M_256", S.cube_3d(side=128, n_grid=256, dt=2.5e-5), 0))
+                                     ("cube_2M_256", S.cube_3d(side=128, n_grid=256, dt=2.5e-5), 0),
+                                     ("plastic_cube", plastic, 0))
     for name, vsc, eft in extra:
         vctx = MPM.from_scene(vsc, polar_eft=eft)
         vctx.load_numpy(vsc.x, vsc.v, vsc.F, vsc.C)
@@ -466,7 +469,7 @@ def run_ours(args, ws, rank, local):
                           "ms_per_step": float(vk[:, 3].mean()), "fused_ms": vf,
                           "particle_steps_per_s": vsc.n_particles / (float(vk[:, 3].mean()) * 1e-3),
                           "fused_gbs": ALGO_BYTES_3D * vsc.n_particles / (vf * 1e-3) / 1e9,
-                          "status_word": vctx.status()}
+                          "status_word": vctx.status(), "material": int(vsc.material)}
         variants[name]["fused_frac"] = variants[name]["fused_gbs"] / _peaks()[0]
         vctx.close()
 

@@ -61,6 +61,7 @@ struct DevParams {
   int bc, bc_width;
   float mass, vol;
   const float2* mu_lam;  // per instance
+  float sv_lo, sv_hi;    // plastic material: bounds of the singular values of F
 };
 
 struct StateView {
@@ -448,6 +449,7 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
           }
 #pragma unroll
         for (int i = 0; i < DD; ++i) F[i] = Fn[i];
+        if (MATERIAL == MPM_FIXED_COROTATED_PLASTIC) plastic_return<D>(F, p.sv_lo, p.sv_hi);
 #pragma unroll
         for (int a = 0; a < D; ++a) x[a] = fmaf(p.dt, v[a], x[a]);
         // write the new state contiguously (block order of the old keys)
@@ -1017,13 +1019,14 @@ mpm_status launch_fused(mpm_ctx* c, cudaStream_t s) {
   // the polar variant matters for the 3D fixed-corotated material only
 #define CASE(d, m, t)                                                                       \
   if (D == d && M == m && T == t) return launch_fused_t<d, m, t, FIRST, POLAR_EFT>(c, s);
-  CASE(2, 0, 0) CASE(2, 0, 1) CASE(2, 1, 0) CASE(2, 1, 1)
+  CASE(2, 0, 0) CASE(2, 0, 1) CASE(2, 1, 0) CASE(2, 1, 1) CASE(2, 2, 0) CASE(2, 2, 1)
   CASE(3, 0, 0) CASE(3, 0, 1)
 #undef CASE
-  if (D == 3 && M == 1 && T == 0)
-    return c->polar_eft ? launch_fused_t<3, 1, 0, FIRST, POLAR_EFT>(c, s) : launch_fused_t<3, 1, 0, FIRST, POLAR_FP64>(c, s);
-  if (D == 3 && M == 1 && T == 1)
-    return c->polar_eft ? launch_fused_t<3, 1, 1, FIRST, POLAR_EFT>(c, s) : launch_fused_t<3, 1, 1, FIRST, POLAR_FP64>(c, s);
+#define CASE3(m, t)                                                                                              \
+  if (D == 3 && M == m && T == t)                                                                               \
+    return c->polar_eft ? launch_fused_t<3, m, t, FIRST, POLAR_EFT>(c, s) : launch_fused_t<3, m, t, FIRST, POLAR_FP64>(c, s);
+  CASE3(1, 0) CASE3(1, 1) CASE3(2, 0) CASE3(2, 1)
+#undef CASE3
   return set_error(MPM_EINVAL, "unsupported (dim, material, transfer)");
 }
 
@@ -1100,7 +1103,12 @@ mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
   MPM_CHECK_ARG(cfg->n_grid >= 8 && cfg->n_grid % B == 0, "n_grid must be a multiple of 8 (2D) / 4 (3D)");
   MPM_CHECK_ARG(cfg->n_inst >= 1 && cfg->E && cfg->nu && cfg->inst_offsets, "instances");
   MPM_CHECK_ARG(cfg->dx > 0 && cfg->dt > 0 && cfg->rho > 0 && cfg->p_vol > 0, "dx, dt, rho, p_vol must be > 0");
-  MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
+  MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED ||
+                    cfg->material == MPM_FIXED_COROTATED_PLASTIC,
+                "material");
+  MPM_CHECK_ARG(cfg->material != MPM_FIXED_COROTATED_PLASTIC ||
+                    (cfg->plastic_compression >= 0.f && cfg->plastic_compression < 1.f && cfg->plastic_stretch >= 0.f),
+                "plastic bounds: 0 <= plastic_compression < 1, plastic_stretch >= 0");
   MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
   MPM_CHECK_ARG(cfg->bc == MPM_BC_STICKY || cfg->bc == MPM_BC_SLIP_FLOOR, "bc");
   MPM_CHECK_ARG(cfg->polar_eft == 0 || cfg->polar_eft == 1, "polar_eft: 0 or 1");
@@ -1202,6 +1210,8 @@ mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
   p.mass = cfg->rho * cfg->p_vol;
   p.vol = cfg->p_vol;
   p.mu_lam = c->mu_lam;
+  p.sv_lo = 1.f - cfg->plastic_compression;
+  p.sv_hi = 1.f + cfg->plastic_stretch;
   c->fused_grid = std::max(1, std::min(c->max_work, c->n_sm * 8));
   *out = c;
   return MPM_OK;
@@ -1378,7 +1388,12 @@ mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F,
   MPM_CHECK_ARG(cfg->n_inst >= 1 && cfg->n_inst <= 64 && cfg->E && cfg->nu && cfg->inst_offsets,
                 "instances (1..64 for the fixed-scratch step)");
   MPM_CHECK_ARG(cfg->dx > 0 && cfg->dt > 0 && cfg->rho > 0 && cfg->p_vol > 0, "dx, dt, rho, p_vol must be > 0");
-  MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
+  MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED ||
+                    cfg->material == MPM_FIXED_COROTATED_PLASTIC,
+                "material");
+  MPM_CHECK_ARG(cfg->material != MPM_FIXED_COROTATED_PLASTIC ||
+                    (cfg->plastic_compression >= 0.f && cfg->plastic_compression < 1.f && cfg->plastic_stretch >= 0.f),
+                "plastic bounds: 0 <= plastic_compression < 1, plastic_stretch >= 0");
   MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
   MPM_CHECK_ARG(cfg->bc == MPM_BC_STICKY || cfg->bc == MPM_BC_SLIP_FLOOR, "bc");
   MPM_CHECK_ARG(cfg->polar_eft == 0 || cfg->polar_eft == 1, "polar_eft: 0 or 1");
@@ -1473,6 +1488,8 @@ mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F,
   p.mass = cfg->rho * cfg->p_vol;
   p.vol = cfg->p_vol;
   p.mu_lam = c.mu_lam;
+  p.sv_lo = 1.f - cfg->plastic_compression;
+  p.sv_hi = 1.f + cfg->plastic_stretch;
   c.fused_grid = std::max(1, std::min(c.max_work, c.n_sm * 8));
   // load the caller's state, bin it and transfer it to the grid, then step
   c.cur = 0;

@@ -215,6 +215,141 @@ __device__ __forceinline__ void f_minus_polar_3d(const float F[9], float out[9])
   }
 }
 
+// ------------------------------------------------------------- plasticity
+// Rotation of the polar decomposition F = R S: 2D in closed form (as in f_minus_polar_2d), 3D by
+// the FP32 scaled Newton iteration of f_minus_polar_3d.
+template <int D>
+__device__ __forceinline__ void polar_rotation(const float F[D * D], float R[D * D]);
+template <>
+__device__ __forceinline__ void polar_rotation<2>(const float F[4], float R[4]) {
+  float c = F[0] + F[3], s = F[2] - F[1];
+  const float inv = rsqrtf(c * c + s * s);
+  c *= inv;
+  s *= inv;
+  R[0] = c;
+  R[1] = -s;
+  R[2] = s;
+  R[3] = c;
+}
+template <>
+__device__ __forceinline__ void polar_rotation<3>(const float F[9], float R[9]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = F[i];
+  for (int it = 0; it < 10; ++it) {
+    float C[9];
+    cofactor3(R, C);
+    const float det = R[0] * C[0] + R[1] * C[1] + R[2] * C[2];
+    const float z = rcbrtf(fabsf(det));
+    const float zi = __frcp_rn(z * det);
+    float diff = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float nx = 0.5f * (z * R[i] + zi * C[i]);
+      diff = fmaxf(diff, fabsf(nx - R[i]));
+      R[i] = nx;
+    }
+    if (diff < 2e-7f) break;
+  }
+}
+
+// Eigen-decomposition A = Q diag(l) Q^T of a symmetric D x D matrix by cyclic Jacobi rotations
+// (Golub and Van Loan, Matrix Computations, Sec. 8.5): each rotation zeroes one off-diagonal
+// entry, with t = sign(th) / (|th| + sqrt(th^2 + 1)), th = (a_qq - a_pp) / (2 a_pq); one rotation
+// is exact in 2D, five sweeps converge to FP32 precision in 3D.
+template <int D>
+__device__ __forceinline__ void jacobi_eig_sym(float A[D * D], float Q[D * D], float l[D]) {
+#pragma unroll
+  for (int i = 0; i < D * D; ++i) Q[i] = (i % (D + 1) == 0) ? 1.f : 0.f;
+  constexpr int SWEEPS = D == 2 ? 1 : 5;
+  for (int sw = 0; sw < SWEEPS; ++sw) {
+#pragma unroll
+    for (int pq = 0; pq < (D == 2 ? 1 : 3); ++pq) {
+      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      const float apq = A[p * D + q];
+      if (apq == 0.f) continue;
+      const float th = (A[q * D + q] - A[p * D + p]) / (2.f * apq);
+      const float t = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+      const float c = rsqrtf(fmaf(t, t, 1.f)), sn = t * c;
+      // A <- J^T A J, Q <- Q J with J the rotation in the (p, q) plane
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float akp = A[k * D + p], akq = A[k * D + q];
+        A[k * D + p] = c * akp - sn * akq;
+        A[k * D + q] = sn * akp + c * akq;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float apk = A[p * D + k], aqk = A[q * D + k];
+        A[p * D + k] = c * apk - sn * aqk;
+        A[q * D + k] = sn * apk + c * aqk;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float qkp = Q[k * D + p], qkq = Q[k * D + q];
+        Q[k * D + p] = c * qkp - sn * qkq;
+        Q[k * D + q] = sn * qkp + c * qkq;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) l[i] = A[i * D + i];
+}
+
+// Return mapping of the plastic fixed-corotated material: with F = R S and S = Q diag(l) Q^T
+// (so F = (R Q) diag(l) Q^T is its singular value decomposition), the singular values are clamped
+// to [lo, hi] and F rebuilt as R Q diag(clamped) Q^T; F is left untouched when no value moves.
+template <int D>
+__device__ __forceinline__ void plastic_return(float F[D * D], float lo, float hi) {
+  float R[D * D], S[D * D], Q[D * D], l[D];
+  polar_rotation<D>(F, R);
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc = fmaf(R[k * D + i], F[k * D + j], acc);
+      S[i * D + j] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i + 1; j < D; ++j) {
+      const float m = 0.5f * (S[i * D + j] + S[j * D + i]);
+      S[i * D + j] = m;
+      S[j * D + i] = m;
+    }
+  jacobi_eig_sym<D>(S, Q, l);
+  bool moved = false;
+  float lc[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    lc[i] = fminf(fmaxf(l[i], lo), hi);
+    moved |= lc[i] != l[i];
+  }
+  if (!moved) return;
+  // U = R Q; F = U diag(lc) Q^T
+  float U[D * D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc = fmaf(R[i * D + k], Q[k * D + j], acc);
+      U[i * D + j] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc = fmaf(U[i * D + k] * lc[k], Q[j * D + k], acc);
+      F[i * D + j] = acc;
+    }
+}
+
 // Kirchhoff stress tau = P F^T.
 //   neo-Hookean:      tau = mu (F F^T - I) + lam ln(J) I
 //   fixed-corotated:  tau = 2 mu (F - R) F^T + lam (J - 1) J I

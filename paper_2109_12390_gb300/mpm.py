@@ -34,7 +34,7 @@ class MPM:
     """One context of the C ABI: a batch of MPM instances sharing grid and material law."""
 
     def __init__(self, *, dim, n_grid, dx, dt, gravity, bc, bc_width, material, transfer, rho, p_vol,
-                 E, nu, inst_offsets, polar_eft=0):
+                 E, nu, inst_offsets, polar_eft=0, plastic_compression=2.5e-2, plastic_stretch=7.5e-3):
         L = _abi.lib()
         self._E = np.ascontiguousarray(np.atleast_1d(E), np.float32)
         self._nu = np.ascontiguousarray(np.atleast_1d(nu), np.float32)
@@ -43,7 +43,8 @@ class MPM:
         self.cfg = _abi.MpmConfig(dim, n_grid, dx, dt, g, bc, bc_width, material, transfer, rho, p_vol,
                                   len(self._E), self._E.ctypes.data_as(C.POINTER(C.c_float)),
                                   self._nu.ctypes.data_as(C.POINTER(C.c_float)),
-                                  self._offs.ctypes.data_as(C.POINTER(C.c_int64)), int(polar_eft))
+                                  self._offs.ctypes.data_as(C.POINTER(C.c_int64)), int(polar_eft),
+                                  float(plastic_compression), float(plastic_stretch))
         h = C.c_void_p()
         _abi.check(L.mpm_init(C.byref(self.cfg), C.byref(h)))
         self._h = h
@@ -57,7 +58,8 @@ class MPM:
         """Context for a synth.scenes.Scene (configuration only)."""
         return cls(dim=sc.dim, n_grid=sc.n_grid, dx=sc.dx, dt=sc.dt, gravity=sc.gravity, bc=sc.bc,
                    bc_width=sc.bc_width, material=sc.material, transfer=sc.transfer, rho=sc.rho,
-                   p_vol=sc.p_vol, E=sc.E, nu=sc.nu, inst_offsets=sc.inst_offsets, polar_eft=polar_eft)
+                   p_vol=sc.p_vol, E=sc.E, nu=sc.nu, inst_offsets=sc.inst_offsets, polar_eft=polar_eft,
+                   plastic_compression=sc.theta_c, plastic_stretch=sc.theta_s)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -144,7 +146,8 @@ def step_noalloc(scene_cfg, x, v, F, C_=None, n_steps=1, stream=None):
     g = (C.c_float * 3)(*[float(a) for a in sc.gravity])
     cfg = _abi.MpmConfig(sc.dim, sc.n_grid, sc.dx, sc.dt, g, sc.bc, sc.bc_width, sc.material, sc.transfer, sc.rho,
                          sc.p_vol, len(E), E.ctypes.data_as(C.POINTER(C.c_float)),
-                         nu.ctypes.data_as(C.POINTER(C.c_float)), offs.ctypes.data_as(C.POINTER(C.c_int64)), 0)
+                         nu.ctypes.data_as(C.POINTER(C.c_float)), offs.ctypes.data_as(C.POINTER(C.c_int64)), 0,
+                         float(sc.theta_c), float(sc.theta_s))
     w = C.c_uint32()
     _abi.check(_abi.lib().mpm_step_noalloc(C.byref(cfg), _ptr(x), _ptr(v), _ptr(F), _ptr(C_), int(n_steps),
                                            C.byref(w), _stream(stream)))

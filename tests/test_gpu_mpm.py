@@ -282,3 +282,77 @@ def test_config2_full_size_sampled(n_sample):
     # near-rigid motion: C is at the FP32 rounding level of the grid velocities, measure it on |v|/dx
     scale = max(np.linalg.norm(Cs), np.linalg.norm(vs) / sc.dx)
     assert np.linalg.norm(C1[samples] - Cs) / scale < TOL_C
+
+
+def _compare_plastic(ctx, ref):
+    """x and F at 1e-5; v at 1e-4: the return mapping clamps at the bounds, so a singular value
+    that FP32 and FP64 place on opposite sides of a bound changes the stress there by E times the
+    rounding of F instead of smoothly, and the grid velocities carry it (measured: x 3e-7, F 1e-6,
+    v 2.6e-5 after 80 to 150 impact steps)."""
+    x, v, F, Cm = ctx.read_numpy()
+    errs = dict(x=rel(x, ref.x), v=rel(v, ref.v), F=rel(F, ref.F))
+    scale = max(np.linalg.norm(ref.C), np.linalg.norm(ref.v) / ref.dx)
+    errs["C"] = float(np.linalg.norm(Cm - ref.C) / scale)
+    assert errs["x"] < TOL and errs["F"] < TOL and errs["v"] < 1e-4 and errs["C"] < TOL_C, errs
+    return errs
+
+
+def _plastic_flow(sc, steps):
+    """The elastic oracle run from the same state: its F differs from the plastic run's only
+    where the return mapping acted."""
+    ela = sc.copy()
+    ela.material = OM.FIXED_COROTATED
+    OM.step(ela, steps)
+    return ela
+
+
+@pytest.mark.parametrize("transfer", [OM.MLS, OM.PIC])
+def test_2d_plastic_block_impact(transfer):
+    """Plastic fixed-corotated block (singular values clamped to [1 - theta_c, 1 + theta_s] after
+    every F update) dropped onto the floor: the return mapping acts on most particles and the
+    trajectory matches the FP64 oracle to FP32 tolerance."""
+    sc = S.block_2d(side=32, dt=5e-5, origin=(0.4, 0.03), v0=np.array([0.3, -0.8]))
+    sc.material, sc.transfer = OM.FIXED_COROTATED_PLASTIC, transfer
+    if transfer == OM.MLS:
+        sc.F = S.random_deformation(np.random.default_rng(1), sc.n_particles, 2, 0.03)
+    ctx = _ctx(sc)
+    ctx.step(150)
+    assert ctx.status() == 0
+    ref = sc.copy()
+    OM.step(ref, 150)
+    assert ref.x[:, 1].min() < 4.5 / 128
+    assert np.abs(ref.F - _plastic_flow(sc, 150).F).max() > 1e-4      # plastic flow did happen
+    _compare_plastic(ctx, ref)
+
+
+def test_3d_plastic_cube_slip_floor():
+    """3D plastic fixed-corotated cube (FP64-refined polar for the stress, FP32 polar and Jacobi
+    eigen-decomposition for the return mapping) through a slip-floor impact."""
+    sc = S.cube_3d(side=16, bottom=0.03)
+    sc.material = OM.FIXED_COROTATED_PLASTIC
+    sc.F = S.random_deformation(np.random.default_rng(2), sc.n_particles, 3, 0.02)
+    ctx = _ctx(sc)
+    ctx.step(80)
+    assert ctx.status() == 0
+    ref = sc.copy()
+    OM.step(ref, 80)
+    assert np.abs(ref.F - _plastic_flow(sc, 80).F).max() > 1e-4
+    _compare_plastic(ctx, ref)
+
+
+def test_plastic_material_with_wide_bounds_is_elastic():
+    """With bounds no singular value reaches, the plastic material is the elastic one (the return
+    mapping leaves F untouched); runs differ only by float-atomic ordering."""
+    sc = S.cube_3d(side=12, bottom=0.03)
+    sc.F = S.random_deformation(np.random.default_rng(3), sc.n_particles, 3, 0.02)
+    out = []
+    for mat in (OM.FIXED_COROTATED, OM.FIXED_COROTATED_PLASTIC):
+        s2 = sc.copy()
+        s2.material = mat
+        s2.theta_c, s2.theta_s = 0.9, 10.0
+        ctx = _ctx(s2)
+        ctx.step(40)
+        assert ctx.status() == 0
+        out.append(ctx.read_numpy())
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert rel(b, a.astype(np.float64)) < 5e-6
