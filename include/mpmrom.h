@@ -301,7 +301,12 @@ enum {
    * decoded velocity (Eq. timederOne) that the reduced step's affine
    * quadrature velocity needs.  The call must also request DECODER_JVP and
    * tangent kind b. */
-  DECODER_MIXED = 2000
+  DECODER_MIXED = 2000,
+  /* DECODER_SECANT_DIR + m, m = 0 .. 63: g(X; xhat + u_m) - g(X; xhat) with u_m the
+   * m-th direction of the point's latent row: dirs then holds (n_lat, n_dirs, r),
+   * n_dirs = 1 + the largest m requested (the JVP, secant and mixed rows use
+   * direction 0).  Several secants of one point share its primal row. */
+  DECODER_SECANT_DIR = 3000
 };
 
 /*

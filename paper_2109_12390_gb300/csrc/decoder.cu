@@ -845,13 +845,17 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   a.n = n;
   a.R = R;
   a.Pt = 128 / R;
+  a.n_dirs = 1;
   bool need_dirs = false, has_mixed = false;
   for (int k = 0; k < R; ++k) {
     const int c = kinds[k];
     const bool mixed = c > KIND_MIXED && c <= KIND_MIXED + dec->d + dec->r;
-    MPM_CHECK_ARG(c == KIND_PRIMAL || (c >= 1 && c <= dec->d + dec->r) || c == KIND_JVP || c == KIND_SECANT || mixed,
+    const bool secant_dir = c >= KIND_SECANT_DIR && c < KIND_SECANT_DIR + kMaxR;
+    MPM_CHECK_ARG(c == KIND_PRIMAL || (c >= 1 && c <= dec->d + dec->r) || c == KIND_JVP || c == KIND_SECANT ||
+                      mixed || secant_dir,
                   "unknown row kind");
-    need_dirs |= (c == KIND_JVP || c == KIND_SECANT || mixed);
+    need_dirs |= (c == KIND_JVP || c == KIND_SECANT || mixed || secant_dir);
+    if (secant_dir) a.n_dirs = std::max(a.n_dirs, c - KIND_SECANT_DIR + 1);
     has_mixed |= mixed;
     a.kinds[k] = c;
     a.mix_jvp[k] = 0;

@@ -52,6 +52,8 @@ struct DecArgs {
   int lat_per_point;
   // FP32 path: useful rows per packed tile (0: point-aligned tiles of Pt points)
   int f32_U;
+  // direction blocks per latent row in `dirs` (KIND_SECANT_DIR rows; 1 otherwise)
+  int n_dirs;
   // training: per hidden layer l, pre-activations z (FP32) and activations a
   // (BF16) of every tile row, stored feature-major: [l][feature][row], row =
   // tile * 128 + t, rows_total = n_tiles * 128
@@ -63,11 +65,21 @@ struct DecArgs {
 __device__ __forceinline__ float elu(float z) { return z > 0.f ? z : expm1f(z); }
 __device__ __forceinline__ float elu_d1(float z) { return z > 0.f ? 1.f : __expf(z); }
 __device__ __forceinline__ float elu_d2(float z) { return z > 0.f ? 0.f : __expf(z); }
+// exp(x) - 1 for the small increments of secant rows: below |x| = 1/32 the Taylor polynomial
+// x + x^2/2 + ... + x^6/720 in Horner form (truncation below 1e-12 relative there), else expm1f
+__device__ __forceinline__ float expm1_small(float x) {
+  if (fabsf(x) < 0.03125f)
+    return x * fmaf(0.5f * x,
+                    fmaf(x * (1.f / 3.f), fmaf(0.25f * x, fmaf(0.2f * x, fmaf(x, 1.f / 6.f, 1.f), 1.f), 1.f), 1.f),
+                    1.f);
+  return expm1f(x);
+}
+
 // act(z + dz) - act(z) without cancellation on the negative branch
 __device__ __forceinline__ float elu_secant(float z, float dz) {
   float z1 = z + dz;
   if (z > 0.f && z1 > 0.f) return dz;
-  if (z <= 0.f && z1 <= 0.f) return __expf(z) * expm1f(dz);
+  if (z <= 0.f && z1 <= 0.f) return __expf(z) * expm1_small(dz);
   return elu(z1) - elu(z);
 }
 
@@ -82,6 +94,8 @@ constexpr int KIND_JVP = 1000;
 constexpr int KIND_SECANT = 1001;
 // KIND_MIXED + b (b = 1 .. d + r): derivative along input b of the JVP row
 constexpr int KIND_MIXED = 2000;
+// KIND_SECANT_DIR + m (m < 64): secant along the m-th direction block of the point's latent row
+constexpr int KIND_SECANT_DIR = 3000;
 
 struct RowInfo {
   int kind;      // code
@@ -92,7 +106,16 @@ struct RowInfo {
 };
 
 __device__ __forceinline__ int kind_class(int kind) {
-  return kind == KIND_PRIMAL ? 0 : (kind == KIND_SECANT ? 2 : (kind > KIND_MIXED ? 3 : 1));
+  if (kind == KIND_PRIMAL) return 0;
+  if (kind == KIND_SECANT || kind >= KIND_SECANT_DIR) return 2;
+  return kind > KIND_MIXED ? 3 : 1;
+}
+
+// Offset of the direction of a row (JVP, secant, mixed: block 0; KIND_SECANT_DIR + m: block m) of
+// latent row li in `dirs`, laid out (n_lat, n_dirs, r).
+__device__ __forceinline__ int64_t dir_offset(const DecArgs& a, int kind, int li) {
+  const int m = kind >= KIND_SECANT_DIR ? kind - KIND_SECANT_DIR : 0;
+  return ((int64_t)li * a.n_dirs + m) * a.r;
 }
 
 __device__ __forceinline__ int64_t dec_count(const DecArgs& a) {
@@ -140,10 +163,10 @@ __device__ __forceinline__ void row_inputs(const DecArgs& a, const RowInfo& ri, 
       }
       if (ri.cls == 1) {
         if (ri.kind >= 1 && ri.kind <= d + r) vdir = (i == ri.kind - 1) ? (i < d ? 1.f / a.norm[d + i] : 1.f) : 0.f;
-        else if (ri.kind == KIND_JVP && i >= d) vdir = a.dirs[(int64_t)li * r + (i - d)];
+        else if (ri.kind == KIND_JVP && i >= d) vdir = a.dirs[dir_offset(a, ri.kind, li) + (i - d)];
       } else if ((ri.cls == 2 || ri.cls == 3) && i >= d) {
         // secant increment, or the JVP direction that a mixed row differentiates
-        vdir = a.dirs[(int64_t)li * r + (i - d)];
+        vdir = a.dirs[dir_offset(a, ri.kind, li) + (i - d)];
       }
     }
     in[i] = vin;
@@ -166,9 +189,9 @@ __device__ __forceinline__ void row_input_elem(const DecArgs& a, const RowInfo& 
   vdir = 0.f;
   if (ri.cls == 1) {
     if (ri.kind >= 1 && ri.kind <= d + r) vdir = (i == ri.kind - 1) ? (i < d ? 1.f / a.norm[d + i] : 1.f) : 0.f;
-    else if (ri.kind == KIND_JVP && i >= d) vdir = a.dirs[(int64_t)li * r + (i - d)];
+    else if (ri.kind == KIND_JVP && i >= d) vdir = a.dirs[dir_offset(a, ri.kind, li) + (i - d)];
   } else if ((ri.cls == 2 || ri.cls == 3) && i >= d) {
-    vdir = a.dirs[(int64_t)li * r + (i - d)];
+    vdir = a.dirs[dir_offset(a, ri.kind, li) + (i - d)];
   }
 }
 

@@ -26,6 +26,7 @@
 //     rom_normal   residual r = g(xhat_k) - x_trial = -(secant) - dt v_trial;
 //                  solve J^T J delta = -J^T r; prepare 11 trial steps 2^-m delta
 //     decoder      secants g(xhat_k + 2^-m delta) - g(xhat_n), m = 0..10, in one launch
+//                  (one primal row and 11 secant rows along direction blocks per sample)
 //     rom_linesearch  objective of every trial (FP64); the last CTA takes the
 //                  first trial that meets the Armijo condition (the same
 //                  choice as sequential backtracking) and updates xhat.
@@ -1183,8 +1184,8 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
 }
 
 // Line-search objectives f(alpha_m) = |g(xhat_k + alpha_m delta) - x_trial|^2 for all
-// trials at once; dec = decoder output (2, cap, d) with kinds [primal, secant] over
-// kLS x nP points (trial m, sample p at m * nP + p).  The last CTA picks the
+// trials at once; dec = decoder output (1 + kLS, cap, d) at the nP samples with kinds
+// [primal, secant along trial direction 0, ..., kLS - 1] (one primal row per sample).  The last CTA picks the
 // first trial meeting Armijo and updates the iterate; on the final iteration it
 // also commits the step.
 __global__ void __launch_bounds__(kNormBlock) rom_linesearch(RomDev R, RomSolve S, const float* __restrict__ dec,
@@ -1199,14 +1200,15 @@ __global__ void __launch_bounds__(kNormBlock) rom_linesearch(RomDev R, RomSolve 
     double s = 0.0;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int p = e / d, a = e % d;
-      const size_t pt = (size_t)m * nP + p;
+      // rows: kind 0 the primal at the base latent, kind 1 + m the secant of trial m
+      const double sec = (double)dec[((size_t)(1 + m) * cap + p) * d + a];
       double res;
       if (mode == NE_FIT) {
         // secant from the iterate: g(xk + alpha delta) = g(xk) + secant; residual vs target
-        res = (double)dec[((size_t)cap + pt) * d + a] + (double)dec[pt * d + a] - (double)target[(size_t)p * d + a];
+        res = sec + (double)dec[(size_t)p * d + a] - (double)target[(size_t)p * d + a];
       } else {
         // g(xhat_k + alpha delta) - x_trial = secant_from_xhat_n - dt v_trial
-        res = (double)dec[((size_t)cap + pt) * d + a] - (double)R.dt * R.v_trial[(size_t)p * d + a];
+        res = sec - (double)R.dt * R.v_trial[(size_t)p * d + a];
       }
       s = fma(res, res, s);
     }
@@ -1337,7 +1339,7 @@ struct rom_ctx {
   float* Fref_inv = nullptr;    // (P, d, d) with f_reference
   float* xref32 = nullptr;      // (r) reference latent
   float* outS = nullptr;        // (r + 2, k, d)
-  float* outLS = nullptr;       // (2, kLS * k, d) (capacity kLS * P for the fit)
+  float* outLS = nullptr;       // (1 + kLS, k, d) (capacity P for the fit)
   double* solve_mem = nullptr;
   float* solve32 = nullptr;
   uint32_t* counters = nullptr;
@@ -1489,17 +1491,19 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
   }
   // 7. Gauss-Newton on the positions
   ks[1 + r] = 1001;  // secant g(xhat_n) - g(xhat_k)
-  int kls[2] = {0, 1001};
+  int kls[1 + kLS];
+  kls[0] = 0;
+  for (int m = 0; m < kLS; ++m) kls[1 + m] = 3000 + m;   // secant along trial direction m
   for (int it = 0; it < c->cfg.gn_iters; ++it) {
     st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xk32, c->sv.dk32, ks, r + 2,
                             c->outS, s);
     if (st != MPM_OK) return st;
     rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_GN, nullptr, 0, 0, c->cfg.ridge);
     MPM_CUDA_TRY(cudaGetLastError());
-    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, kLS, (int64_t)kLS * c->k, c->sv.ls_base32,
-                            c->sv.ls_dir32, kls, 2, c->outLS, s);
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.ls_base32, c->sv.ls_dir32, kls,
+                            1 + kLS, c->outLS, s);
     if (st != MPM_OK) return st;
-    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, (int64_t)kLS * c->k, NE_GN, nullptr,
+    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, c->k, NE_GN, nullptr,
                                               it == c->cfg.gn_iters - 1, 1e-4, 0);
     MPM_CUDA_TRY(cudaGetLastError());
   }
@@ -1583,7 +1587,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   c->merged = !c->eulerian && (int64_t)P <= 32 * (int64_t)c->k;
   c->x_all = c->merged ? c->outQ : c->x_all_buf;
   if ((st = ralloc(&c->outS, (size_t)(r + 2) * P * d)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->outLS, (size_t)2 * kLS * P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->outLS, (size_t)(1 + kLS) * P * d)) != MPM_OK) return fail(st);
   const int n_acc = r * (r + 1) / 2 + r + 1;
   const size_t n64 = 6 * (size_t)r + 3 + n_acc + kLS;
   if ((st = ralloc(&c->solve_mem, n64)) != MPM_OK) return fail(st);
@@ -1938,7 +1942,9 @@ mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int
   int ks[kMaxRl + 2];
   ks[0] = 0;
   for (int j = 0; j < r; ++j) ks[1 + j] = 1 + d + j;
-  int kls[2] = {0, 1001};
+  int kls[1 + kLS];
+  kls[0] = 0;
+  for (int m = 0; m < kLS; ++m) kls[1 + m] = 3000 + m;
   const int b_ne = std::max(1, std::min(ceil_div((int64_t)P * d, kNERows), c->n_sm));
   mpm_status st = MPM_OK;
   for (int it = 0; it < iters && st == MPM_OK; ++it) {
@@ -1946,10 +1952,10 @@ mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int
     if (st != MPM_OK) break;
     rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, P, NE_FIT, tgt, 0, P, 0.f);
     // trials: secant from the iterate; base rows hold the iterate
-    st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, kLS, (int64_t)kLS * P, c->sv.ls_base32, c->sv.ls_dir32,
-                            kls, 2, c->outLS, s);
+    st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, P, c->sv.ls_base32, c->sv.ls_dir32, kls, 1 + kLS,
+                            c->outLS, s);
     if (st != MPM_OK) break;
-    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, (int64_t)kLS * P, NE_FIT, tgt, 0, 1e-4, P);
+    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, P, NE_FIT, tgt, 0, 1e-4, P);
   }
   // velocity fit at the fitted xhat_0 (Eq. essentialSpecInt, second line)
   if (st == MPM_OK) {

@@ -21,6 +21,11 @@ def dX(k):
     return 1 + k
 
 
+def secant_dir(m):
+    """Kind of the secant row along the m-th direction of the point's latent row."""
+    return 3000 + int(m)
+
+
 def mixed(kind):
     """Row kind of d/d(input of tangent `kind`) of the JVP row; with kind = dX(k) this is
     the material gradient d/dX_k of the decoded velocity (dg/dxhat) u."""

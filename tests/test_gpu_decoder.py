@@ -234,3 +234,26 @@ def test_empty_and_bad_arguments():
         dec.eval(torch.zeros((3, 2), device="cuda"), lat, [5, PRIMAL])   # primal must come first
     with pytest.raises(_abi.MpmError):
         dec.eval(torch.zeros((3, 2), device="cuda"), lat, [PRIMAL, 999])
+
+
+@pytest.mark.parametrize("fp32,tol", [(True, 1e-5), (False, TOL_BF16)])
+def test_secant_rows_along_direction_blocks(fp32, tol):
+    """DECODER_SECANT_DIR + m: several secants of one point, each along its own direction block of
+    the point's latent row (dirs laid out (n_lat, n_dirs, r)), sharing the point's primal row; the
+    reduced step's line search evaluates its 11 trial steps this way."""
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL, secant_dir
+    d, r, n, nd = 2, 8, 300, 3
+    p = _dec_params(d, r, seed=41)
+    dec = Decoder.from_params(p)
+    dec.set_precision(fp32)
+    X, lat, idx = _points(n, d, r, n_lat=2, seed=42)
+    u = (1e-3 * np.random.default_rng(43).normal(size=(len(lat), nd, r))).astype(np.float32)
+    Xg, latg, idxg, ug = _gpu(X.astype(np.float32), lat.astype(np.float32), idx, u)
+    out = dec.eval(Xg, latg, [PRIMAL] + [secant_dir(m) for m in range(nd)], lat_idx=idxg, dirs=ug).cpu().numpy()
+    assert dec.status() == 0
+    Xr = X.astype(np.float32).astype(np.float64)
+    xh = lat.astype(np.float32).astype(np.float64)[idx]
+    g0 = OD.decode(p, Xr, xh)
+    for m in range(nd):
+        ref = OD.decode(p, Xr, xh + u.astype(np.float64)[idx, m]) - g0
+        assert rel(out[1 + m], ref) < tol, (m, rel(out[1 + m], ref))
