@@ -164,8 +164,11 @@ __device__ __forceinline__ int node_linear(const int node[D], int n) {
 }
 
 // ------------------------------------------------------------ rom_select
+constexpr int kSelMaxBits = 65536;   // particles whose neighbour decisions rom_select keeps in shared memory
+
 template <int D>
 __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
+  __shared__ uint32_t s_nbits[kSelMaxBits / 32];
   __shared__ int s_hist[256];
   __shared__ int s_warp[32];
   __shared__ unsigned long long s_prefix;
@@ -303,61 +306,62 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
   }
   __threadfence_block();
   __syncthreads();
-  // neighbour set N: other particles with a stencil node in I (ascending ids)
-  int nb = 0;
-  for (int p = p0; p < p1; ++p) {
-    const uint64_t h = splitmix_out(s1, (uint64_t)p);
-    // recompute the sample decision for p
-    bool is_sample = h < thr;
-    if (h == thr) is_sample = true;  // ties resolved below
+  // neighbour set N: other particles with a stencil node in I (ascending ids).  The stencil's
+  // stamps are loaded together (independent loads), and for P <= kSelMaxBits the first pass
+  // keeps its decisions in a shared bit mask for the second.
+  auto is_sample_of = [&](int p, uint64_t h) {
+    bool smp = h < thr;
     if (h == thr) {
       // rank of p among equal hashes (only within this thread's range matters, plus eq_before)
       int e = eq_before;
       for (int q = p0; q < p; ++q) e += (splitmix_out(s1, (uint64_t)q) == thr);
-      is_sample = e < need_eq;
+      smp = e < need_eq;
     }
-    if (is_sample) continue;
+    return smp;
+  };
+  auto neighbour_hit = [&](int p, bool flag_out_of_grid) {
     int base[D];
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      int b = stencil_base(R.x_all[(size_t)p * D + a], R.inv_dx);
+      const int b = stencil_base(R.x_all[(size_t)p * D + a], R.inv_dx);
       ok &= (b >= 0) & (b + 2 <= R.n - 1);
       base[a] = min(max(b, 0), R.n - 3);
     }
-    if (!ok) raise_status(R.status, STATUS_OUT_OF_GRID);
-    bool hit = false;
-    for (int s = 0; s < NS && !hit; ++s) {
+    if (!ok && flag_out_of_grid) raise_status(R.status, STATUS_OUT_OF_GRID);
+    uint32_t st[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
       int node[D];
       node[0] = base[0] + (D == 2 ? s / 3 : s / 9);
       node[D - 1] = base[D - 1] + s % 3;
       if (D == 3) node[1] = base[1] + (s / 3) % 3;
-      hit = R.stamp[node_linear<D>(node, R.n)] == stamp;
+      st[s] = R.stamp[node_linear<D>(node, R.n)];
     }
+    bool hit = false;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) hit |= st[s] == stamp;
+    return hit;
+  };
+  const bool keep_bits = P <= kSelMaxBits;
+  for (int w = t; w < (P + 31) / 32 && keep_bits; w += T) s_nbits[w] = 0u;
+  __syncthreads();
+  int nb = 0;
+  for (int p = p0; p < p1; ++p) {
+    if (is_sample_of(p, splitmix_out(s1, (uint64_t)p))) continue;
+    const bool hit = neighbour_hit(p, true);
     nb += hit;
+    if (hit && keep_bits) atomicOr(&s_nbits[p >> 5], 1u << (p & 31));
   }
   int n_nb;
   int npos = block_exclusive_scan(nb, &n_nb, s_warp);
   for (int p = p0; p < p1; ++p) {
-    const uint64_t h = splitmix_out(s1, (uint64_t)p);
-    bool is_sample = h < thr;
-    if (h == thr) {
-      int e = eq_before;
-      for (int q = p0; q < p; ++q) e += (splitmix_out(s1, (uint64_t)q) == thr);
-      is_sample = e < need_eq;
-    }
-    if (is_sample) continue;
-    int base[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-      base[a] = min(max(stencil_base(R.x_all[(size_t)p * D + a], R.inv_dx), 0), R.n - 3);
-    bool hit = false;
-    for (int s = 0; s < NS && !hit; ++s) {
-      int node[D];
-      node[0] = base[0] + (D == 2 ? s / 3 : s / 9);
-      node[D - 1] = base[D - 1] + s % 3;
-      if (D == 3) node[1] = base[1] + (s / 3) % 3;
-      hit = R.stamp[node_linear<D>(node, R.n)] == stamp;
+    bool hit;
+    if (keep_bits) {
+      hit = (s_nbits[p >> 5] >> (p & 31)) & 1u;
+    } else {
+      if (is_sample_of(p, splitmix_out(s1, (uint64_t)p))) continue;
+      hit = neighbour_hit(p, false);
     }
     if (hit) R.qlist[k + npos++] = p;
   }

@@ -1053,10 +1053,11 @@ mpm_status trainer_set_encoder_params(trainer_ctx* c, const float* params, const
 
 mpm_status trainer_encode(trainer_ctx* c, const float* x, int64_t n, int64_t n_particles, float* latents,
                           void* stream) {
-  MPM_CHECK_ARG(c && x && latents, "null argument");
+  MPM_CHECK_ARG(c, "null context");
   MPM_CHECK_ARG(c->enc, "the trainer has no encoder (train_config.encoder_subset = 0)");
   MPM_CHECK_ARG(n >= 0 && n_particles >= c->E.n_sub, "n >= 0 and n_particles >= the encoder subset");
   if (n == 0) return MPM_OK;
+  MPM_CHECK_ARG(x && latents, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int d = c->d;
   float *xd = nullptr, *Ud = nullptr, *ld = nullptr;

@@ -121,3 +121,18 @@ def test_training_with_encoder_reduces_loss():
     assert step == 50 and tr.status() == 0
     assert np.isfinite(l1) and l1 < l0
     assert np.abs(vec1 - vec0).max() > 0      # Adam moves the encoder, not a table
+
+
+def test_encoder_arguments():
+    from paper_2109_12390_gb300 import _abi
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.train import Trainer
+    snaps, host, p, dec, tr = _setup(seed=3)
+    assert tr.encode(np.zeros((0, 256, 2), np.float32)).shape == (0, dec.r)
+    with pytest.raises(_abi.MpmError):
+        Trainer(dec, snaps, dt_snap=0.01, batch=100, total_steps=1, encoder_subset=257)   # larger than an instance
+    with pytest.raises(_abi.MpmError):
+        Trainer(dec, snaps, dt_snap=0.01, batch=100, total_steps=1, encoder_subset=8)     # 2 x 8 < 32 inputs
+    table = Trainer(dec, snaps, dt_snap=0.01, batch=100, total_steps=1)
+    with pytest.raises(_abi.MpmError):
+        table.encoder_params()                                                            # no encoder

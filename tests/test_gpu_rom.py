@@ -334,3 +334,26 @@ def test_super_resolution_decoding_and_finer_reduced_model():
     OM.step(fom, 10)
     assert rel(romf.decode_all().cpu().numpy(), fom.x) < 1e-6
     romf.close()
+
+
+def test_samples_cover_every_particle_and_empty_calls():
+    """n_samples >= P: every particle is a sample, the neighbour set is empty, and the step is the
+    oracle's; zero-point decode calls are valid no-ops."""
+    import torch
+    from paper_2109_12390_gb300.rom import ROM
+    sc, p, dec, rom, rs, xh, vh, xp = _elu_setup(seed=6, side=8, r=4, n_hidden=1, k=64)
+    rom.close()
+    rom = ROM.from_scene(dec, sc, n_samples=1000, seed=6)
+    assert rom.n_samples == sc.n_particles
+    rom.set_state(xh, vh, xp, 0)
+    rom.step(1)
+    assert rom.status() & ~ALLOWED_RANDOM == 0
+    dbg = rom.debug()
+    np.testing.assert_array_equal(dbg["samples"], np.arange(sc.n_particles))
+    assert len(dbg["neigh"]) == 0
+    rs.n_samples = sc.n_particles
+    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], dbg["x_all"].astype(np.float64))
+    assert rel(dbg["v_trial"], v_trial) < 1e-4
+    out = rom.decode_points(torch.empty((0, 2), dtype=torch.float32, device="cuda"))
+    assert out.shape == (0, 2)
+    rom.close()
