@@ -1123,10 +1123,12 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
   // (rank-deficient J^T J; the solution then tends to the minimum-norm one).
   // One retry with a larger ridge; after that the step is skipped and
   // CHOLESKY raised.
-  if (threadIdx.x == 0) {
-    double tr = 0;
-    for (int i = 0; i < r; ++i) tr += A_keep[i * r + i];
-    s_shift = (tr > 0 ? tr : 1.0) / r;
+  if (threadIdx.x < 32) {
+    // trace by a warp reduction (serial FP64 sums are long dependency chains on this GPU)
+    double tr = threadIdx.x < r ? A_keep[threadIdx.x * r + threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (threadIdx.x == 0) s_shift = (tr > 0 ? tr : 1.0) / r;
   }
   __syncthreads();
   bool ok = false;
@@ -1162,17 +1164,21 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
   } else {
     // GN step: J^T J delta = J^T b with b = -residual
     __shared__ double s_slope, s_dn;
-    if (threadIdx.x == 0) {
-      double sl = 0, dn = 0;
-      for (int i = 0; i < r; ++i) {
-        sl += s_rhs[i] * bvec[i];
-        dn += bvec[i] * bvec[i];
+    if (threadIdx.x < 32) {
+      double sl = threadIdx.x < r ? s_rhs[threadIdx.x] * bvec[threadIdx.x] : 0.0;
+      double dn = threadIdx.x < r ? bvec[threadIdx.x] * bvec[threadIdx.x] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sl += __shfl_xor_sync(0xffffffffu, sl, o);
+        dn += __shfl_xor_sync(0xffffffffu, dn, o);
       }
-      s_slope = -2.0 * sl;   // d/dalpha |res + alpha J delta|^2 at 0 = 2 res^T J delta = -2 b^T J delta
-      s_dn = sqrt(dn);
-      S.scal[0] = s_bb;      // f0 = |res|^2
-      S.scal[1] = s_slope;
-      S.scal[2] = s_dn;
+      if (threadIdx.x == 0) {
+        s_slope = -2.0 * sl;   // d/dalpha |res + alpha J delta|^2 at 0 = 2 res^T J delta = -2 b^T J delta
+        s_dn = sqrt(dn);
+        S.scal[0] = s_bb;      // f0 = |res|^2
+        S.scal[1] = s_slope;
+        S.scal[2] = s_dn;
+      }
     }
     for (int i = threadIdx.x; i < r; i += blockDim.x) S.delta[i] = bvec[i];
     __syncthreads();
