@@ -49,7 +49,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the fused step kernel on this workload, from one ncu
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); the state written
 # by a step stays in L2 under ncu's cache control, so this is below the algorithmic traffic
-FUSED_DRAM_BYTES_NCU = 16_782_336
+FUSED_DRAM_BYTES_NCU = 16_779_776
 
 
 def _dist():
