@@ -26,7 +26,9 @@ Readings where the paper is silent (each listed in the design notes):
   * boundaries: nodes with any index < w or > n - 1 - w are wall nodes; sticky
     walls zero the velocity; the slip floor clamps v_y >= 0 on the low-y band
     and leaves the other walls sticky;
-  * nodes with m_i == 0 get zero velocity.
+  * nodes with m_i == 0 get zero velocity;
+  * kinematic (Dirichlet) particles of group g take the prescribed velocity v_g after the grid
+    to particle transfer, move with it and carry C = 0 (their F follows the grid).
 
 Pins (tests/test_oracle_mpm.py): partition of unity and linear reproduction of
 the weights, brute-force piecewise basis, exact mass and linear-momentum
@@ -139,6 +141,21 @@ def plastic_return(F, lo, hi):
     moved = np.any(c != s, axis=-1)
     out[moved] = np.einsum("pij,pj,pjk->pik", U[moved], c[moved], Vt[moved])
     return out
+
+
+def kinematic_override(x, xn, vn, Cn, group, kin_vel, dt):
+    """Essential (Dirichlet) boundary of Section 2: particles of kinematic group g (group >= 0) take
+    the prescribed velocity kin_vel[g] and move with it, x_{n+1} = x_n + dt v_g, carrying no affine
+    velocity (C = 0); F follows the grid like every particle.  Other particles are unchanged."""
+    m = np.asarray(group) >= 0
+    if not np.any(m):
+        return xn, vn, Cn
+    xn, vn, Cn = xn.copy(), vn.copy(), Cn.copy()
+    vg = np.asarray(kin_vel, np.float64)[np.asarray(group)[m]]
+    vn[m] = vg
+    xn[m] = x[m] + dt * vg
+    Cn[m] = 0.0
+    return xn, vn, Cn
 
 
 def energy(F, material, mu, lam):
@@ -317,6 +334,9 @@ def step(scene, n_steps: int = 1, return_grid: bool = False):
                                  transfer=scene.transfer)
             if scene.material == FIXED_COROTATED_PLASTIC:
                 Fn = plastic_return(Fn, 1.0 - scene.theta_c, 1.0 + scene.theta_s)
+            if scene.kin_group is not None:
+                xn, vn, Cn = kinematic_override(scene.x[s], xn, vn, Cn, scene.kin_group[s], scene.kin_vel,
+                                                scene.dt)
             scene.x[s], scene.v[s], scene.F[s], scene.C[s] = xn, vn, Fn, Cn
             if return_grid:
                 grids.append((m, p, vg))

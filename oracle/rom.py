@@ -113,6 +113,38 @@ def stencil_nodes(x, dx, n_grid):
     return np.stack(out, axis=1)
 
 
+def kinematic_sample_set(seed, inst, step, n_particles, k, groups, m_kin):
+    """Sample set with kinematic boundaries (Section 3.2.1: their material points are included;
+    Section 5: at least 5 per boundary).  The k particles with the smallest hash (ascending), then,
+    for each kinematic group g in order, those of its min(m_kin, |g|) particles of smallest (hash,
+    id) that are not already drawn (ascending)."""
+    base = sample_set(seed, inst, step, n_particles, k)
+    h = sample_hash(seed, inst, step, np.arange(n_particles, dtype=np.uint64))
+    taken = np.zeros(n_particles, bool)
+    taken[base] = True
+    parts = [base]
+    groups = np.asarray(groups)
+    for g in range(int(groups.max()) + 1 if groups.size else 0):
+        ids = np.nonzero(groups == g)[0]
+        first = ids[np.lexsort((ids, h[ids]))][:m_kin]
+        extra = np.sort(first[~taken[first]])
+        taken[extra] = True
+        parts.append(extra)
+    return np.concatenate(parts).astype(np.int64)
+
+
+def prescribe_kinematic(rs, samples, x_samples, v_trial):
+    """Trial state of kinematic samples: their prescribed velocity (the Dirichlet condition enforced
+    in the full-space update, Section 3.2.1)."""
+    if rs.kin_group is None:
+        return v_trial, x_samples + rs.dt * v_trial
+    g = np.asarray(rs.kin_group)[samples]
+    m = g >= 0
+    v = v_trial.copy()
+    v[m] = np.asarray(rs.kin_vel, np.float64)[g[m]]
+    return v, x_samples + rs.dt * v
+
+
 def neighbourhood(x_all, samples, dx, n_grid):
     """Algorithm 3 sets: basis set I (sorted node ids) and neighbour set N (sorted particle ids)."""
     nodes = stencil_nodes(x_all, dx, n_grid)
@@ -210,6 +242,9 @@ class RomScene:
     ell: int = 2                             # Eulerian quadrature points per cell per dimension
     newton_iters: int = 4                    # decoder inversion iterations
     newton_tol: float = 1e-3                 # converged: final residual below newton_tol * dx
+    kin_group: np.ndarray | None = None      # kinematic group per particle (-1: free)
+    kin_vel: np.ndarray | None = None        # prescribed velocity per group (n_groups, d)
+    kin_min_samples: int = 5                 # samples forced from each kinematic group
 
 
 @dataclasses.dataclass
@@ -253,7 +288,7 @@ def local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_all):
         for k in range(d):
             weight = weight * w[:, k, off[k]]
         v_trial += weight[:, None] * vg[tuple(node[:, k] for k in range(d))]
-    x_trial = xs + rs.dt * v_trial
+    v_trial, x_trial = prescribe_kinematic(rs, samples, xs, v_trial)
     return v_trial, x_trial, basis, neigh
 
 
@@ -316,7 +351,8 @@ def eulerian_local_dynamics(dec, rs: RomScene, xhat, vhat, samples, x_samples, X
         for k in range(d):
             weight = weight * w[:, k, off[k]]
         v_trial += weight[:, None] * vg[tuple(node[:, k] for k in range(d))]
-    return v_trial, xs + rs.dt * v_trial, q
+    v_trial, x_trial = prescribe_kinematic(rs, samples, xs, v_trial)
+    return v_trial, x_trial, q
 
 
 def lstsq(A, b, ridge=0.0):
@@ -372,7 +408,11 @@ def gauss_newton(dec, Xs, x_trial, xhat0, iters, c=1e-4, max_halvings=10, ridge=
 def rom_step(dec, rs: RomScene, st: RomState, record=None):
     """Algorithm 2 with Lagrangian quadrature; returns the new RomState."""
     P = len(rs.X)
-    samples = sample_set(rs.seed, rs.inst, st.step, P, rs.n_samples)
+    if rs.kin_group is None:
+        samples = sample_set(rs.seed, rs.inst, st.step, P, rs.n_samples)
+    else:
+        samples = kinematic_sample_set(rs.seed, rs.inst, st.step, P, min(rs.n_samples, P), rs.kin_group,
+                                       rs.kin_min_samples)
     if rs.quadrature == "eulerian":
         x_all = None
         x_s = D.decode(dec, rs.X[samples], st.xhat)

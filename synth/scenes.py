@@ -57,6 +57,10 @@ class Scene:
     # plastic material (material 2): singular values of F kept in [1 - theta_c, 1 + theta_s]
     theta_c: float = 2.5e-2
     theta_s: float = 7.5e-3
+    # kinematic boundaries: group id per particle (-1: free) and the prescribed velocity of each
+    # group (n_groups, d); None: no kinematic particles
+    kin_group: np.ndarray | None = None
+    kin_vel: np.ndarray | None = None
 
     @property
     def n_inst(self) -> int:
@@ -74,7 +78,9 @@ class Scene:
         return dataclasses.replace(
             self, gravity=self.gravity.copy(), E=self.E.copy(), nu=self.nu.copy(),
             inst_offsets=self.inst_offsets.copy(), x=self.x.copy(), v=self.v.copy(),
-            F=self.F.copy(), C=self.C.copy())
+            F=self.F.copy(), C=self.C.copy(),
+            kin_group=None if self.kin_group is None else self.kin_group.copy(),
+            kin_vel=None if self.kin_vel is None else self.kin_vel.copy())
 
     def subset_instances(self, ids) -> "Scene":
         ids = list(ids)
@@ -278,3 +284,21 @@ def refine_block_2d(sc: Scene, factor: int = 2) -> Scene:
     return dataclasses.replace(sc, n_grid=sc.n_grid * factor, dx=dxf, p_vol=(dxf / 2) ** 2,
                                inst_offsets=np.array([0, len(x)], np.int64), x=x, v=v, F=F, C=C,
                                gravity=sc.gravity.copy(), E=sc.E.copy(), nu=sc.nu.copy())
+
+
+def clamped_bar_2d(seed: int = 5, side: int = 32, top_velocity=(0.4, -0.3), layers: int = 2,
+                   dt: float = 5e-5) -> Scene:
+    """Square block whose bottom `layers` particle rows are held still and whose top rows move at a
+    fixed velocity (two kinematic boundaries, as in the tension / torsion scenes of Section 5);
+    gravity off, neo-Hookean."""
+    sc = block_2d(seed=seed, side=side, dt=dt, origin=(0.375, 0.375), E=5e3, v0=np.zeros(2))
+    sc.gravity = np.zeros(3)
+    y = sc.x[:, 1]
+    ys = np.unique(np.round(y, 12))
+    g = np.full(sc.n_particles, -1, np.int32)
+    g[y <= ys[layers - 1] + 1e-12] = 0
+    g[y >= ys[-layers] - 1e-12] = 1
+    sc.kin_group = g
+    sc.kin_vel = np.array([[0.0, 0.0], list(top_velocity)], np.float64)
+    sc.v = np.where((g == 1)[:, None], sc.kin_vel[1], 0.0)
+    return sc

@@ -326,3 +326,25 @@ def test_plastic_material_with_wide_bounds_is_the_elastic_material():
     s = np.linalg.svd(c.F, compute_uv=False)
     assert s.max() <= 1 + c.theta_s + 1e-12 and s.min() >= 1 - c.theta_c - 1e-12
     assert not np.allclose(c.F, a.F)
+
+
+def test_kinematic_particles_follow_their_prescribed_motion():
+    """Dirichlet particles: the held group stays in place, the moving group translates at its
+    velocity exactly, the free particles are pulled along; with every group id -1 the step is the
+    plain one."""
+    sc = S.clamped_bar_2d(side=16)
+    a = sc.copy()
+    n = 30
+    M.step(a, n)
+    g = sc.kin_group
+    assert np.array_equal(a.x[g == 0], sc.x[g == 0])
+    np.testing.assert_allclose(a.x[g == 1], sc.x[g == 1] + n * sc.dt * sc.kin_vel[1], rtol=0, atol=1e-14)
+    assert np.all(a.C[g >= 0] == 0) and np.all(a.v[g == 1] == sc.kin_vel[1])
+    assert np.abs(a.v[g == -1]).max() > 0.05          # the free particles are dragged
+    b = sc.copy()
+    b.kin_group = np.full(sc.n_particles, -1, np.int32)
+    c = sc.copy()
+    c.kin_group, c.kin_vel = None, None
+    M.step(b, 5)
+    M.step(c, 5)
+    assert np.array_equal(b.x, c.x) and np.array_equal(b.F, c.F)

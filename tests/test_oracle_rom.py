@@ -266,3 +266,58 @@ def test_eulerian_quadrature_mass_and_free_fall():
         st = R.rom_step(dec, rs, st)
         M.step(fom, 1)
         np.testing.assert_allclose(D.decode(dec, X, st.xhat), fom.x, atol=1e-13)
+
+
+def test_kinematic_sample_set_brute_force():
+    """Every kinematic group contributes its min(m, |g|) smallest-(hash, id) particles to the sample
+    set; the bottom-k draw comes first, the group extras (not already drawn) after it."""
+    rng = np.random.default_rng(0)
+    P, k, m = 500, 40, 5
+    groups = np.full(P, -1, np.int32)
+    groups[rng.choice(P, 30, replace=False)] = 0
+    groups[rng.choice(np.nonzero(groups < 0)[0], 3, replace=False)] = 1     # smaller than m
+    for step in range(4):
+        smp = R.kinematic_sample_set(9, 2, step, P, k, groups, m)
+        h = R.sample_hash(9, 2, step, np.arange(P, dtype=np.uint64))
+        order = sorted(range(P), key=lambda p: (int(h[p]), p))
+        base = sorted(order[:k])
+        assert list(smp[:k]) == base
+        assert len(set(smp.tolist())) == len(smp)
+        want = set(base)
+        for g in (0, 1):
+            members = [p for p in order if groups[p] == g]
+            want |= set(members[:m])
+            assert sum(groups[smp] == g) >= min(m, len(members))
+        assert set(smp.tolist()) == want
+
+
+def test_kinematic_trial_velocities_and_translation():
+    """Kinematic samples take their prescribed velocity; with a translation decoder and every group
+    moving at the body's velocity the reduced step follows the translation exactly."""
+    sc = S.clamped_bar_2d(side=16, top_velocity=(0.0, 0.0))
+    v0 = np.array([0.2, -0.1])
+    sc.kin_vel = np.array([v0, v0])
+    sc.v = np.broadcast_to(v0, sc.x.shape).copy()
+    X = sc.x.copy()
+    dec = _translation_decoder(2, X.min(0), X.max(0) - X.min(0))
+    rs = R.RomScene(X=X, mass=sc.p_mass, vol=sc.p_vol, E=float(sc.E[0]), nu=float(sc.nu[0]), dx=sc.dx,
+                    dt=sc.dt, n_grid=sc.n_grid, gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width,
+                    material=sc.material, transfer=sc.transfer, n_samples=12, seed=4,
+                    kin_group=sc.kin_group, kin_vel=sc.kin_vel)
+    st = R.RomState(xhat=np.zeros(2), vhat=v0.copy(), xhat_prev=-sc.dt * v0)
+    for n in range(5):
+        rec = {}
+        st = R.rom_step(dec, rs, st, rec)
+        g = sc.kin_group[rec["samples"]]
+        assert (g == 0).sum() >= 5 and (g == 1).sum() >= 5
+        np.testing.assert_allclose(rec["v_trial"][g >= 0], np.broadcast_to(v0, ((g >= 0).sum(), 2)), rtol=0,
+                                   atol=0)
+    np.testing.assert_allclose(st.xhat, 5 * sc.dt * v0, rtol=1e-12, atol=1e-15)
+    # a moving group with another velocity: its samples report it, the rest keep the grid velocity
+    vt = np.zeros((3, 2))
+    rs.kin_vel = np.array([[0.0, 0.0], [1.0, 2.0]])
+    smp = np.array([np.nonzero(sc.kin_group == 1)[0][0], np.nonzero(sc.kin_group == -1)[0][0],
+                    np.nonzero(sc.kin_group == 0)[0][0]])
+    v, xt = R.prescribe_kinematic(rs, smp, X[smp], vt + 0.5)
+    np.testing.assert_array_equal(v, [[1.0, 2.0], [0.5, 0.5], [0.0, 0.0]])
+    np.testing.assert_allclose(xt, X[smp] + sc.dt * v, rtol=0, atol=1e-16)
