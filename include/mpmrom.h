@@ -182,6 +182,17 @@ mpm_status mpm_step_profiled(mpm_ctx* ctx, int n_steps, void* flush_buf, size_t 
                              void* stream);
 
 /*
+ * Kinematic (essential, Dirichlet) boundaries: group[p] (n_particles int32, host or device, the
+ * caller's particle order; -1 = free) assigns particles to n_groups groups with prescribed
+ * velocities (n_groups, dim floats).  After every grid-to-particle transfer a particle of group g
+ * takes velocity[g], moves with it and carries no affine velocity (its F follows the grid like
+ * every particle's).  n_groups = 0 or group = NULL removes them.  Synchronous.  Errors:
+ * MPM_EINVAL for group ids outside [-1, n_groups).
+ */
+mpm_status mpm_set_kinematic(mpm_ctx* ctx, const int32_t* group, int32_t n_groups, const float* velocities,
+                             void* stream);
+
+/*
  * Synchronises `stream`, then returns the OR of MPM_STATUS_* bits raised by
  * the device since the last clear in *out (clears it when `clear` != 0).
  */
@@ -497,7 +508,8 @@ mpm_status rom_status_word(rom_ctx* ctx, uint32_t* out, int clear, void* stream)
 /*
  * Diagnostics of the last step (any pointer may be NULL; synchronous):
  * qlist (n_particles int32): samples ascending then neighbours ascending;
- * counts (3 int32): |P|, |P| + |N| (the number of Eulerian quadrature points
+ * counts (3 int32): |P| (with kinematic groups up to n_samples + min_samples x
+ * n_groups; v_trial, x_trial then hold that many rows), |P| + |N| (the number of Eulerian quadrature points
  * with cfg.quadrature = 1), basis-node list length; x_all
  * (n_particles, dim): decoded positions g(X; xhat_n) the step used;
  * v_trial, x_trial (|P|, dim): Algorithm 5 outputs of the samples.
@@ -517,6 +529,19 @@ mpm_status rom_debug(rom_ctx* ctx, int32_t* qlist, int32_t* counts, float* x_all
  */
 mpm_status rom_debug_quadrature(rom_ctx* ctx, int32_t* n_points, float* x_points, float* X_points, float* mass,
                                 float* V0, void* stream);
+
+/*
+ * Kinematic (Dirichlet) boundaries of the reduced model (Lagrangian quadrature only): group[p]
+ * (n_particles int32, host or device; -1 = free), n_groups prescribed velocities (n_groups, dim
+ * floats).  Every step's sample set is the n_samples-particle draw plus, for each group, those of
+ * its min(min_samples, |group|) particles of smallest hash (the same SplitMix64 hash, ties by id)
+ * that the draw missed, appended group by group in ascending id (min_samples in [1, 32]; the
+ * paper finds 5 enough); kinematic samples take their prescribed velocity as trial velocity.
+ * n_groups = 0 removes them.  Resets the grid and the step graph (call before stepping, then
+ * set the state).  Synchronous.  Errors: MPM_EINVAL.
+ */
+mpm_status rom_set_kinematic(rom_ctx* ctx, const int32_t* group, int32_t n_groups, const float* velocities,
+                             int32_t min_samples, void* stream);
 
 /* g(X^p; xhat_n) for every particle into device array x_out (n_particles, dim). */
 mpm_status rom_decode_all(rom_ctx* ctx, float* x_out, void* stream);

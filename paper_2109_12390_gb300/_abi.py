@@ -78,6 +78,7 @@ SIGNATURES = [
     ("mpm_set_state", C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_void_p]),
     ("mpm_get_state", C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_void_p]),
     ("mpm_step", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    ("mpm_set_kinematic", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("mpm_step_profiled", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_float), C.c_void_p]),
     ("mpm_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
     ("mpm_debug_bins", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -106,6 +107,7 @@ SIGNATURES = [
     ("rom_debug", C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),
     ("rom_debug_quadrature", C.c_int, [C.c_void_p, C.POINTER(C.c_int32)] + [C.c_void_p] * 4 + [C.c_void_p]),
     ("rom_decode_all", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rom_set_kinematic", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     ("rom_decode_points", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("metric_accumulate", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("trainer_create", C.c_int, [C.c_void_p, C.POINTER(TrainConfig), C.POINTER(SnapshotDesc), C.c_void_p,

@@ -62,6 +62,8 @@ struct DevParams {
   float mass, vol;
   const float2* mu_lam;  // per instance
   float sv_lo, sv_hi;    // plastic material: bounds of the singular values of F
+  const int32_t* kin_group;  // kinematic group per particle id (-1 free), or null
+  const float* kin_vel;      // prescribed velocity per group (3 floats each)
 };
 
 struct StateView {
@@ -450,6 +452,16 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
 #pragma unroll
         for (int i = 0; i < DD; ++i) F[i] = Fn[i];
         if (MATERIAL == MPM_FIXED_COROTATED_PLASTIC) plastic_return<D>(F, p.sv_lo, p.sv_hi);
+        if (p.kin_group) {
+          // kinematic (Dirichlet) particle: prescribed velocity, no affine velocity; F follows the grid
+          const int kg = p.kin_group[pid];
+          if (kg >= 0) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) v[a] = p.kin_vel[3 * kg + a];
+#pragma unroll
+            for (int i = 0; i < DD; ++i) C[i] = 0.f;
+          }
+        }
 #pragma unroll
         for (int a = 0; a < D; ++a) x[a] = fmaf(p.dt, v[a], x[a]);
         // write the new state contiguously (block order of the old keys)
@@ -980,6 +992,8 @@ struct mpm_ctx {
   int64_t* d_offs = nullptr;
   uint32_t* status = nullptr;
   float* staging = nullptr;  // AoS x, v, F, C
+  int32_t* kin_group = nullptr;  // kinematic group per particle (caller's order = particle id)
+  float* kin_vel = nullptr;      // prescribed velocity per group (3 floats each)
   int cur = 0, g = 0;
   bool loaded = false;
   DevParams dp{};
@@ -1237,7 +1251,44 @@ void mpm_destroy(mpm_ctx* c) {
   cudaFree(c->d_offs);
   cudaFree(c->status);
   cudaFree(c->staging);
+  cudaFree(c->kin_group);
+  cudaFree(c->kin_vel);
   delete c;
+}
+
+mpm_status mpm_set_kinematic(mpm_ctx* c, const int32_t* group, int32_t n_groups, const float* velocities,
+                             void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  MPM_CHECK_ARG(n_groups >= 0, "n_groups >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_groups == 0 || !group) {
+    c->dp.kin_group = nullptr;
+    c->dp.kin_vel = nullptr;
+    return MPM_OK;
+  }
+  MPM_CHECK_ARG(velocities, "velocities of the kinematic groups");
+  std::vector<int32_t> h((size_t)c->P);
+  std::vector<float> hv((size_t)n_groups * c->D);
+  MPM_CUDA_TRY(cudaMemcpyAsync(h.data(), group, sizeof(int32_t) * c->P, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(hv.data(), velocities, sizeof(float) * hv.size(), cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < c->P; ++i) MPM_CHECK_ARG(h[i] >= -1 && h[i] < n_groups, "group ids in [-1, n_groups)");
+  std::vector<float> v3((size_t)n_groups * 3, 0.f);
+  for (int g = 0; g < n_groups; ++g)
+    for (int a = 0; a < c->D; ++a) v3[(size_t)3 * g + a] = hv[(size_t)c->D * g + a];
+  cudaFree(c->kin_group);
+  cudaFree(c->kin_vel);
+  c->kin_group = nullptr;
+  c->kin_vel = nullptr;
+  c->dp.kin_group = nullptr;
+  c->dp.kin_vel = nullptr;
+  MPM_CUDA_TRY(cudaMalloc((void**)&c->kin_group, sizeof(int32_t) * c->P));
+  MPM_CUDA_TRY(cudaMalloc((void**)&c->kin_vel, sizeof(float) * v3.size()));
+  MPM_CUDA_TRY(cudaMemcpy(c->kin_group, h.data(), sizeof(int32_t) * c->P, cudaMemcpyHostToDevice));
+  MPM_CUDA_TRY(cudaMemcpy(c->kin_vel, v3.data(), sizeof(float) * v3.size(), cudaMemcpyHostToDevice));
+  c->dp.kin_group = c->kin_group;
+  c->dp.kin_vel = c->kin_vel;
+  return MPM_OK;
 }
 
 mpm_status mpm_set_state(mpm_ctx* c, const float* x, const float* v, const float* F, const float* C, void* stream) {

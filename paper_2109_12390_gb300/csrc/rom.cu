@@ -100,6 +100,13 @@ struct RomDev {
   float occ_origin[3];
   float occ_h;
   int occ_shape[3];
+  // kinematic (Dirichlet) boundaries
+  const int32_t* kin_group;  // group per particle (-1 free), or null
+  const float* kin_vel;      // prescribed velocity per group (3 floats each)
+  const int32_t* kg_off;     // (n_groups + 1) offsets into kg_ids
+  const int32_t* kg_ids;     // particles of each group, ascending
+  int n_groups, m_kin;
+  uint32_t* sel_bits;        // ((P + 31) / 32) sample membership of the current step
 };
 
 // Inverse of a small matrix by its adjugate (F of a quadrature point, det F > 0).
@@ -164,6 +171,7 @@ __device__ __forceinline__ int node_linear(const int node[D], int n) {
 }
 
 // ------------------------------------------------------------ rom_select
+constexpr int kMaxKin = 32;          // samples forced from one kinematic group, at most
 constexpr int kSelMaxBits = 65536;   // particles whose neighbour decisions rom_select keeps in shared memory
 
 template <int D>
@@ -173,6 +181,7 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
   __shared__ int s_warp[32];
   __shared__ unsigned long long s_prefix;
   __shared__ int s_remaining;
+  __shared__ int s_nP;
   const int t = threadIdx.x, T = blockDim.x;
   const int P = R.P, k = min(R.k, P);
   const int per = (P + T - 1) / T;
@@ -277,15 +286,84 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
     }
   }
   __syncthreads();
+  int nP = k;
+  if (R.n_groups > 0) {
+    // kinematic boundaries: each group's min(m_kin, |g|) particles of smallest (hash, id) join
+    // the draw; those not already drawn are appended, group by group, in ascending id
+    for (int w = t; w < (P + 31) / 32; w += T) R.sel_bits[w] = 0u;
+    __syncthreads();
+    for (int i = t; i < k; i += T) {
+      const int q = R.qlist[i];
+      atomicOr(&R.sel_bits[q >> 5], 1u << (q & 31));
+    }
+    __syncthreads();
+    if (t < 32) {
+      const unsigned full = 0xffffffffu;
+      int cnt = k;
+      for (int g = 0; g < R.n_groups; ++g) {
+        const int a0 = R.kg_off[g], a1 = R.kg_off[g + 1];
+        const int rounds = min(R.m_kin, a1 - a0);
+        unsigned long long ph = 0ull;
+        int pid_prev = -1;
+        int picked[kMaxKin];
+        int np = 0;
+        for (int round = 0; round < rounds; ++round) {
+          unsigned long long bh = ~0ull;
+          int bid = 0x7fffffff;
+          for (int e = a0 + t; e < a1; e += 32) {
+            const int q = R.kg_ids[e];
+            const unsigned long long h = splitmix_out(s1, (uint64_t)q);
+            const bool after = round == 0 || h > ph || (h == ph && q > pid_prev);
+            if (after && (h < bh || (h == bh && q < bid))) {
+              bh = h;
+              bid = q;
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long oh = __shfl_xor_sync(full, bh, o);
+            const int oid = __shfl_xor_sync(full, bid, o);
+            if (oh < bh || (oh == bh && oid < bid)) {
+              bh = oh;
+              bid = oid;
+            }
+          }
+          ph = bh;
+          pid_prev = bid;
+          if (t == 0 && !((R.sel_bits[bid >> 5] >> (bid & 31)) & 1u)) picked[np++] = bid;
+        }
+        if (t == 0) {
+          for (int i = 1; i < np; ++i) {   // ascending ids
+            const int v = picked[i];
+            int j = i - 1;
+            while (j >= 0 && picked[j] > v) {
+              picked[j + 1] = picked[j];
+              --j;
+            }
+            picked[j + 1] = v;
+          }
+          for (int i = 0; i < np; ++i) {
+            R.qlist[cnt++] = picked[i];
+            R.sel_bits[picked[i] >> 5] |= 1u << (picked[i] & 31);
+          }
+        }
+        cnt = __shfl_sync(full, cnt, 0);
+        __syncwarp();
+      }
+      if (t == 0) s_nP = cnt;
+    }
+    __syncthreads();
+    nP = s_nP;
+  }
   if (R.eulerian) {
     // Algorithm 4: only the samples; their basis set and the quadrature cells come after the
     // samples are decoded (rom_eul_cells)
-    if (t == 0) R.counts[0] = k;
+    if (t == 0) R.counts[0] = nP;
     return;
   }
   // basis set I: stamp the stencil nodes of the samples (and keep them for clearing)
   constexpr int NS = (D == 2) ? 9 : 27;
-  for (int i = t; i < k; i += T) {
+  for (int i = t; i < nP; i += T) {
     const int p = R.qlist[i];
     int base[D];
 #pragma unroll
@@ -310,6 +388,7 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
   // stamps are loaded together (independent loads), and for P <= kSelMaxBits the first pass
   // keeps its decisions in a shared bit mask for the second.
   auto is_sample_of = [&](int p, uint64_t h) {
+    if (R.n_groups > 0) return ((R.sel_bits[p >> 5] >> (p & 31)) & 1u) != 0u;
     bool smp = h < thr;
     if (h == thr) {
       // rank of p among equal hashes (only within this thread's range matters, plus eq_before)
@@ -363,12 +442,12 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
       if (is_sample_of(p, splitmix_out(s1, (uint64_t)p))) continue;
       hit = neighbour_hit(p, false);
     }
-    if (hit) R.qlist[k + npos++] = p;
+    if (hit) R.qlist[nP + npos++] = p;
   }
   if (t == 0) {
-    R.counts[0] = k;
-    R.counts[1] = k + n_nb;
-    R.counts[2] = k * NS;
+    R.counts[0] = nP;
+    R.counts[1] = nP + n_nb;
+    R.counts[2] = nP * NS;
   }
 }
 
@@ -796,6 +875,14 @@ __global__ void rom_g2p(RomDev R) {
       grid_node_velocity<D>(R.grid[node_linear<D>(node, R.n)], node, R.n, R.bc, R.bc_width, R.dt, R.g, vi);
 #pragma unroll
       for (int a = 0; a < D; ++a) v[a] = fmaf(wt, vi[a], v[a]);
+    }
+    if (R.kin_group) {
+      // kinematic sample: its prescribed velocity (the Dirichlet condition of the full-space update)
+      const int kg = R.kin_group[pid];
+      if (kg >= 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) v[a] = R.kin_vel[3 * kg + a];
+      }
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -1353,6 +1440,13 @@ struct rom_ctx {
   double* solve_mem = nullptr;
   float* solve32 = nullptr;
   uint32_t* counters = nullptr;
+  // kinematic boundaries: sample capacity k_cap = k + m_kin x n_groups
+  int k_cap = 0;
+  int32_t* kin_group = nullptr;
+  float* kin_vel = nullptr;
+  int32_t* kg_off = nullptr;
+  int32_t* kg_ids = nullptr;
+  uint32_t* sel_bits = nullptr;
   // Eulerian quadrature (Algorithm 4)
   bool eulerian = false;
   int ell = 0, newton_iters = 0;
@@ -1429,8 +1523,8 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
   int ks[kMaxRl + 2];
   ks[0] = 0;
   for (int j = 0; j < r; ++j) ks[1 + j] = 1 + d + j;
-  const int b_s = std::max(1, ceil_div(c->k, 128));
-  const int b_ne = std::max(1, std::min(ceil_div((int64_t)c->k * d, kNERows), 64));
+  const int b_s = std::max(1, ceil_div(c->k_cap, 128));
+  const int b_ne = std::max(1, std::min(ceil_div((int64_t)c->k_cap * d, kNERows), 64));
   const int M = c->cfg.material, T = c->cfg.transfer;
   if (c->eulerian) {
     // Algorithm 4.  1. samples
@@ -1440,7 +1534,7 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
       rom_select<3><<<1, 1024, 0, s>>>(c->dv);
     MPM_CUDA_TRY(cudaGetLastError());
     // 2. positions and latent Jacobian at the samples (the rows of the velocity projection)
-    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xh32, nullptr, ks, r + 1, c->outS,
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k_cap, c->sv.xh32, nullptr, ks, r + 1, c->outS,
                             s);
     if (st != MPM_OK) return st;
     // 3. basis set, quadrature cells and points, initial reference positions
@@ -1487,11 +1581,11 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
   MPM_CUDA_TRY(cudaGetLastError());
   // 6. velocity projection: J = dg/dxhat at (X^P, xhat_n) (decoded in step 2 with the Eulerian quadrature)
   if (!c->eulerian) {
-    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xh32, nullptr, ks, r + 1, c->outS,
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k_cap, c->sv.xh32, nullptr, ks, r + 1, c->outS,
                             s);
     if (st != MPM_OK) return st;
   }
-  rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_VEL, nullptr, c->cfg.projection, 0,
+  rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k_cap, NE_VEL, nullptr, c->cfg.projection, 0,
                                          c->cfg.ridge);
   MPM_CUDA_TRY(cudaGetLastError());
   if (c->cfg.projection == 1) {
@@ -1505,15 +1599,15 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
   kls[0] = 0;
   for (int m = 0; m < kLS; ++m) kls[1 + m] = 3000 + m;   // secant along trial direction m
   for (int it = 0; it < c->cfg.gn_iters; ++it) {
-    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.xk32, c->sv.dk32, ks, r + 2,
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k_cap, c->sv.xk32, c->sv.dk32, ks, r + 2,
                             c->outS, s);
     if (st != MPM_OK) return st;
-    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k, NE_GN, nullptr, 0, 0, c->cfg.ridge);
+    rom_normal<<<b_ne, kNormBlock, 0, s>>>(c->dv, c->sv, c->outS, c->k_cap, NE_GN, nullptr, 0, 0, c->cfg.ridge);
     MPM_CUDA_TRY(cudaGetLastError());
-    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k, c->sv.ls_base32, c->sv.ls_dir32, kls,
+    st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 0, 1, c->k_cap, c->sv.ls_base32, c->sv.ls_dir32, kls,
                             1 + kLS, c->outLS, s);
     if (st != MPM_OK) return st;
-    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, c->k, NE_GN, nullptr,
+    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, c->k_cap, NE_GN, nullptr,
                                               it == c->cfg.gn_iters - 1, 1e-4, 0);
     MPM_CUDA_TRY(cudaGetLastError());
   }
@@ -1562,6 +1656,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   c->r = cfg->latent_dim;
   c->P = (int)n_particles;
   c->k = std::min<int>(cfg->n_samples, c->P);
+  c->k_cap = c->k;
   c->n = cfg->n_grid;
   int devn = 0;
   cudaGetDevice(&devn);
@@ -1728,6 +1823,11 @@ void rom_destroy(rom_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->X);
   cudaFree(c->x_all_buf);
+  cudaFree(c->kin_group);
+  cudaFree(c->kin_vel);
+  cudaFree(c->kg_off);
+  cudaFree(c->kg_ids);
+  cudaFree(c->sel_bits);
   cudaFree(c->cstamp);
   cudaFree(c->clist);
   cudaFree(c->qX);
@@ -1841,8 +1941,8 @@ mpm_status rom_debug(rom_ctx* c, int32_t* qlist, int32_t* counts, float* x_all, 
   if (counts) MPM_CUDA_TRY(cudaMemcpyAsync(counts, c->counts, sizeof(int32_t) * 3, cudaMemcpyDefault, s));
   if (qlist) MPM_CUDA_TRY(cudaMemcpyAsync(qlist, c->qlist, sizeof(int32_t) * c->P, cudaMemcpyDefault, s));
   if (x_all) MPM_CUDA_TRY(cudaMemcpyAsync(x_all, c->x_all, sizeof(float) * c->P * c->d, cudaMemcpyDefault, s));
-  if (v_trial) MPM_CUDA_TRY(cudaMemcpyAsync(v_trial, c->v_trial, sizeof(float) * c->k * c->d, cudaMemcpyDefault, s));
-  if (x_trial) MPM_CUDA_TRY(cudaMemcpyAsync(x_trial, c->x_trial, sizeof(float) * c->k * c->d, cudaMemcpyDefault, s));
+  if (v_trial) MPM_CUDA_TRY(cudaMemcpyAsync(v_trial, c->v_trial, sizeof(float) * c->k_cap * c->d, cudaMemcpyDefault, s));
+  if (x_trial) MPM_CUDA_TRY(cudaMemcpyAsync(x_trial, c->x_trial, sizeof(float) * c->k_cap * c->d, cudaMemcpyDefault, s));
   MPM_CUDA_TRY(cudaStreamSynchronize(s));
   return MPM_OK;
 }
@@ -1894,6 +1994,93 @@ mpm_status rom_decode_all(rom_ctx* c, float* x_out, void* stream) {
   mpm_status st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, c->P, c->sv.xh32, nullptr, k_primal, 1,
                                      x_out, s);
   return st;
+}
+
+mpm_status rom_set_kinematic(rom_ctx* c, const int32_t* group, int32_t n_groups, const float* velocities,
+                             int32_t min_samples, void* stream) {
+  MPM_CHECK_ARG(c, "null context");
+  MPM_CHECK_ARG(n_groups >= 0, "n_groups >= 0");
+  MPM_CHECK_ARG(!c->eulerian || n_groups == 0, "kinematic boundaries need the Lagrangian quadrature");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int P = c->P, NS = c->d == 2 ? 9 : 27;
+  cudaFree(c->kin_group);
+  cudaFree(c->kin_vel);
+  cudaFree(c->kg_off);
+  cudaFree(c->kg_ids);
+  cudaFree(c->sel_bits);
+  c->kin_group = nullptr;
+  c->kin_vel = nullptr;
+  c->kg_off = nullptr;
+  c->kg_ids = nullptr;
+  c->sel_bits = nullptr;
+  c->dv.kin_group = nullptr;
+  c->dv.kin_vel = nullptr;
+  c->dv.kg_off = nullptr;
+  c->dv.kg_ids = nullptr;
+  c->dv.sel_bits = nullptr;
+  c->dv.n_groups = 0;
+  c->dv.m_kin = 0;
+  int k_cap = c->k;
+  if (n_groups > 0 && group) {
+    MPM_CHECK_ARG(velocities, "velocities of the kinematic groups");
+    MPM_CHECK_ARG(min_samples >= 1 && min_samples <= kMaxKin, "min_samples in [1, 32]");
+    std::vector<int32_t> h(P);
+    std::vector<float> hv((size_t)n_groups * c->d);
+    MPM_CUDA_TRY(cudaMemcpyAsync(h.data(), group, sizeof(int32_t) * P, cudaMemcpyDefault, s));
+    MPM_CUDA_TRY(cudaMemcpyAsync(hv.data(), velocities, sizeof(float) * hv.size(), cudaMemcpyDefault, s));
+    MPM_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<int32_t> off(n_groups + 1, 0), ids;
+    for (int p = 0; p < P; ++p) {
+      MPM_CHECK_ARG(h[p] >= -1 && h[p] < n_groups, "group ids in [-1, n_groups)");
+      if (h[p] >= 0) ++off[h[p] + 1];
+    }
+    for (int g = 0; g < n_groups; ++g) off[g + 1] += off[g];
+    ids.resize(off[n_groups]);
+    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    for (int p = 0; p < P; ++p)
+      if (h[p] >= 0) ids[fill[h[p]]++] = p;   // ascending within each group
+    std::vector<float> v3((size_t)n_groups * 3, 0.f);
+    for (int g = 0; g < n_groups; ++g)
+      for (int a = 0; a < c->d; ++a) v3[(size_t)3 * g + a] = hv[(size_t)c->d * g + a];
+    mpm_status st;
+    if ((st = ralloc(&c->kin_group, P)) != MPM_OK) return st;
+    if ((st = ralloc(&c->kin_vel, v3.size())) != MPM_OK) return st;
+    if ((st = ralloc(&c->kg_off, off.size())) != MPM_OK) return st;
+    if ((st = ralloc(&c->kg_ids, ids.size())) != MPM_OK) return st;
+    if ((st = ralloc(&c->sel_bits, (size_t)(P + 31) / 32)) != MPM_OK) return st;
+    MPM_CUDA_TRY(cudaMemcpy(c->kin_group, h.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice));
+    MPM_CUDA_TRY(cudaMemcpy(c->kin_vel, v3.data(), sizeof(float) * v3.size(), cudaMemcpyHostToDevice));
+    MPM_CUDA_TRY(cudaMemcpy(c->kg_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice));
+    if (!ids.empty())
+      MPM_CUDA_TRY(cudaMemcpy(c->kg_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice));
+    c->dv.kin_group = c->kin_group;
+    c->dv.kin_vel = c->kin_vel;
+    c->dv.kg_off = c->kg_off;
+    c->dv.kg_ids = c->kg_ids;
+    c->dv.sel_bits = c->sel_bits;
+    c->dv.n_groups = n_groups;
+    c->dv.m_kin = min_samples;
+    k_cap = std::min(P, c->k + min_samples * n_groups);
+  }
+  // the basis-node list and the step graph depend on the sample capacity
+  if (k_cap != c->k_cap) {
+    cudaFree(c->nodes);
+    c->nodes = nullptr;
+    mpm_status st = ralloc(&c->nodes, (size_t)k_cap * NS);
+    if (st != MPM_OK) return st;
+    c->dv.nodes = c->nodes;
+    // the old node list is gone: start from an empty grid, as rom_set_state does
+    const size_t gn = c->d == 2 ? (size_t)c->n * c->n : (size_t)c->n * c->n * c->n;
+    MPM_CUDA_TRY(cudaMemset(c->counts, 0, sizeof(int32_t) * 4));
+    MPM_CUDA_TRY(cudaMemset(c->grid, 0, sizeof(float4) * gn));
+    MPM_CUDA_TRY(cudaMemset(c->stamp, 0, sizeof(uint32_t) * gn));
+    c->k_cap = k_cap;
+  }
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return MPM_OK;
 }
 
 mpm_status rom_decode_points(rom_ctx* c, const float* X, int64_t n, float* x_out, void* stream) {

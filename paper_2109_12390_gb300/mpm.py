@@ -55,11 +55,25 @@ class MPM:
 
     @classmethod
     def from_scene(cls, sc, polar_eft=0):
-        """Context for a synth.scenes.Scene (configuration only)."""
-        return cls(dim=sc.dim, n_grid=sc.n_grid, dx=sc.dx, dt=sc.dt, gravity=sc.gravity, bc=sc.bc,
-                   bc_width=sc.bc_width, material=sc.material, transfer=sc.transfer, rho=sc.rho,
-                   p_vol=sc.p_vol, E=sc.E, nu=sc.nu, inst_offsets=sc.inst_offsets, polar_eft=polar_eft,
-                   plastic_compression=sc.theta_c, plastic_stretch=sc.theta_s)
+        """Context for a synth.scenes.Scene (configuration and kinematic groups; no state)."""
+        ctx = cls(dim=sc.dim, n_grid=sc.n_grid, dx=sc.dx, dt=sc.dt, gravity=sc.gravity, bc=sc.bc,
+                  bc_width=sc.bc_width, material=sc.material, transfer=sc.transfer, rho=sc.rho,
+                  p_vol=sc.p_vol, E=sc.E, nu=sc.nu, inst_offsets=sc.inst_offsets, polar_eft=polar_eft,
+                  plastic_compression=sc.theta_c, plastic_stretch=sc.theta_s)
+        if getattr(sc, "kin_group", None) is not None:
+            ctx.set_kinematic(sc.kin_group, sc.kin_vel)
+        return ctx
+
+    def set_kinematic(self, group, velocities, stream=None):
+        """Kinematic (Dirichlet) groups: group id per particle (-1 free), prescribed velocity per
+        group (n_groups, dim).  group=None removes them."""
+        if group is None:
+            _abi.check(_abi.lib().mpm_set_kinematic(self._h, None, 0, None, _stream(stream)))
+            return
+        g = np.ascontiguousarray(group, np.int32)
+        v = np.ascontiguousarray(velocities, np.float32).reshape(-1, self.dim)
+        _abi.check(_abi.lib().mpm_set_kinematic(self._h, g.ctypes.data_as(C.c_void_p), int(len(v)),
+                                                v.ctypes.data_as(C.c_void_p), _stream(stream)))
 
     def close(self):
         if getattr(self, "_h", None):

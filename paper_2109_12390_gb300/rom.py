@@ -96,14 +96,26 @@ class ROM:
         _abi.check(_abi.lib().rom_status_word(self._h, C.byref(w), int(clear), _stream(stream)))
         return w.value
 
+    def set_kinematic(self, group, velocities, min_samples=5, stream=None):
+        """Kinematic (Dirichlet) boundaries: group id per particle (-1 free), prescribed velocity per
+        group; at least min_samples samples per group each step.  group=None removes them."""
+        if group is None:
+            _abi.check(_abi.lib().rom_set_kinematic(self._h, None, 0, None, 1, _stream(stream)))
+            return
+        g = np.ascontiguousarray(group, np.int32)
+        v = np.ascontiguousarray(velocities, np.float32).reshape(-1, self.d)
+        _abi.check(_abi.lib().rom_set_kinematic(self._h, _ptr(g), int(len(v)), _ptr(v), int(min_samples),
+                                                _stream(stream)))
+
     def debug(self, stream=None):
         q = np.empty(self.P, np.int32)
         cnt = np.empty(3, np.int32)
         xa = np.empty((self.P, self.d), np.float32)
-        vt = np.empty((self.n_samples, self.d), np.float32)
-        xt = np.empty((self.n_samples, self.d), np.float32)
+        vt = np.empty((self.P, self.d), np.float32)    # at least the sample capacity
+        xt = np.empty((self.P, self.d), np.float32)
         _abi.check(_abi.lib().rom_debug(self._h, _ptr(q), _ptr(cnt), _ptr(xa), _ptr(vt), _ptr(xt), _stream(stream)))
         nP, nQ = int(cnt[0]), int(cnt[1])
+        vt, xt = vt[:nP].copy(), xt[:nP].copy()
         if self.eulerian:
             return dict(samples=q[:nP].copy(), neigh=q[:0].copy(), n_points=nQ, v_trial=vt, x_trial=xt)
         return dict(samples=q[:nP].copy(), neigh=q[nP:nQ].copy(), x_all=xa, v_trial=vt, x_trial=xt)

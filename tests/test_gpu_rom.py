@@ -357,3 +357,40 @@ def test_samples_cover_every_particle_and_empty_calls():
     out = rom.decode_points(torch.empty((0, 2), dtype=torch.float32, device="cuda"))
     assert out.shape == (0, 2)
     rom.close()
+
+
+def test_kinematic_samples_and_trial_velocities():
+    """Kinematic boundaries in the reduced step: each step's sample set is the oracle's (bottom-k
+    draw plus each group's smallest-hash particles), bit-exact, and kinematic samples take their
+    prescribed trial velocity; the other trial velocities match the oracle's local step."""
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.rom import ROM
+    sc = S.clamped_bar_2d(side=32)
+    X = sc.x
+    p = S.near_identity_decoder(21, 2, 4, 1, X_min=X.min(0), X_range=X.max(0) - X.min(0), eps=3e-3)
+    dec = Decoder.from_params(p)
+    dec.set_precision(True)
+    rom = ROM.from_scene(dec, sc, n_samples=48, seed=6, projection=1)
+    rom.set_kinematic(sc.kin_group, sc.kin_vel, min_samples=5)
+    rng = np.random.default_rng(6)
+    xh = 0.3 * rng.normal(size=4)
+    vh = rng.normal(size=4)
+    rom.set_state(xh, vh, xh - sc.dt * vh, 0)
+    rs = _rom_scene(sc, 48, 6)
+    rs.kin_group, rs.kin_vel, rs.projection = sc.kin_group, sc.kin_vel, "velocity-only"
+    for step in range(3):
+        xh_n, vh_n, _, _ = rom.get_state()
+        rom.step(1)
+        assert rom.status() == 0
+        dbg = rom.debug()
+        want = OR.kinematic_sample_set(6, 0, step, len(X), 48, sc.kin_group, 5)
+        np.testing.assert_array_equal(dbg["samples"], want)
+        g = sc.kin_group[dbg["samples"]]
+        assert (g == 0).sum() >= 5 and (g == 1).sum() >= 5
+        assert np.array_equal(dbg["v_trial"][g >= 0], sc.kin_vel[g[g >= 0]].astype(np.float32))
+        xa = dbg["x_all"].astype(np.float64)
+        basis, neigh = OR.neighbourhood(xa, dbg["samples"], sc.dx, sc.n_grid)
+        np.testing.assert_array_equal(dbg["neigh"], neigh)
+        v_trial, _, _, _ = OR.local_dynamics(p, rs, xh_n, vh_n, dbg["samples"], xa)
+        assert rel(dbg["v_trial"], v_trial) < 1e-4
+    rom.close()
