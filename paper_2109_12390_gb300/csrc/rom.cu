@@ -1,26 +1,32 @@
-// Reduced-order step (Algorithm 2 with Lagrangian quadrature) on sm_103a.
+// Reduced-order step (Algorithm 2) on sm_103a.
 //
-// One step, all on the device (no host round trip; replayable as a graph):
-//   decoder        x_n^p = g(X^p; xhat_n) for all particles (Alg. 3, tracking)
+// One step, all on the device (no host round trip; replayable as a graph), with the Lagrangian
+// quadrature of Algorithm 3 (default):
+//   decoder        x_n^p = g(X^p; xhat_n) for all particles (Alg. 3, tracking); when the
+//                  neighbourhood covers most of the body this one decode also produces the
+//                  quadrature rows below for every particle
 //   rom_select     one CTA: clears the previous basis set on the grid, draws the
 //                  sample set P as the bottom-k of a SplitMix64 hash per
 //                  particle (8-pass radix select over the 64-bit hashes, ties
-//                  by particle id), marks the basis set I (stencil nodes of the
-//                  samples) with a per-step stamp, finds the neighbour set N
-//                  (particles outside P with a stencil node in I) and writes
-//                  the quadrature list Q = [P ascending, N ascending] (Alg. 3)
+//                  by particle id) plus, with kinematic boundaries, each
+//                  group's smallest-hash particles, marks the basis set I
+//                  (stencil nodes of the samples) with a per-step stamp, finds
+//                  the neighbour set N (particles outside P with a stencil
+//                  node in I) and writes the quadrature list Q = [P, N] (Alg. 3)
 //   decoder        dg/dX (deformation gradient, Eq. defGrad) and the JVP along
 //                  vhat_n (velocity, Eq. timederOne) at Q
 //   rom_p2g        particle-to-grid from Q onto the nodes of I only (Alg. 5,
-//                  no affine term), stress from the same device functions as
-//                  the full-order step
-//   rom_g2p        grid update + grid-to-particle to the samples: v_trial,
-//                  x_trial = x_n + dt v_trial (Alg. 5)
+//                  no affine term unless asked), stress from the same device
+//                  functions as the full-order step
+//   rom_g2p        grid update + grid-to-particle to the samples: v_trial (the
+//                  prescribed velocity for kinematic samples), x_trial = x_n +
+//                  dt v_trial (Alg. 5)
 //   decoder        dg/dxhat at (X^P, xhat_n)
-//   rom_normal     FP64 normal equations J^T J, J^T b (multi-CTA, FP64
-//                  atomics); the last CTA to finish factors them (parallel
-//                  Cholesky) and solves: vhat_{n+1} (Eq. nonlinear_projection:vel),
-//                  or a Gauss-Newton step delta for xhat (Eq. ...:pos)
+//   rom_normal     normal equations J^T J, J^T b (multi-CTA, compensated FP32
+//                  sums added in FP64); the last CTA to finish solves them (FP32
+//                  Cholesky with FP64 refinement, FP64 Cholesky fallback):
+//                  vhat_{n+1} (Eq. nonlinear_projection:vel), or a Gauss-Newton
+//                  step delta for xhat (Eq. ...:pos)
 //   per Gauss-Newton iteration (initial guess 2 xhat_n - xhat_{n-1}):
 //     decoder      dg/dxhat and the secant g(xhat_n) - g(xhat_k) at the samples
 //     rom_normal   residual r = g(xhat_k) - x_trial = -(secant) - dt v_trial;
@@ -30,6 +36,9 @@
 //     rom_linesearch  objective of every trial (FP64); the last CTA takes the
 //                  first trial that meets the Armijo condition (the same
 //                  choice as sequential backtracking) and updates xhat.
+// With the Eulerian quadrature of Algorithm 4 the samples are decoded alone and
+// the quadrature points are cell points whose reference positions come from a
+// Newton inversion of the decoder (rom_eul_* kernels).
 // The Gauss-Newton residual is formed from secant rows (exact differences of
 // decoder outputs) so that BF16 GEMMs resolve latent increments of ~1e-5.
 #include <cuda_runtime.h>
