@@ -694,6 +694,11 @@ mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {
 
 namespace mpmrom {
 mpm_status decoder_refresh(mpm_decoder* dec, cudaStream_t s) { return refresh_derived_impl(dec, s); }
+// Coordinate and latent widths of a decoder, for code that holds it as an opaque handle.
+void decoder_shape(const mpm_decoder* dec, int* d, int* r) {
+  *d = dec->d;
+  *r = dec->r;
+}
 // Internal launcher for on-device point sets (used by the reduced-order step).
 mpm_status decoder_launch_dev(const mpm_decoder* dec, const float* X, const int32_t* idx, const int32_t* n_dev,
                               int n_rep, int64_t capacity, const float* latents, const float* dirs,

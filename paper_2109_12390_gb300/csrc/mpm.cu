@@ -1132,6 +1132,8 @@ mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
     MPM_CHECK_ARG(cfg->inst_offsets[k + 1] >= cfg->inst_offsets[k], "inst_offsets must be non-decreasing");
   const int64_t P64 = cfg->inst_offsets[cfg->n_inst];
   MPM_CHECK_ARG(P64 >= 1 && P64 < (1ll << 30), "particle count out of range");
+  for (int k = 0; k < cfg->n_inst; ++k)
+    MPM_CHECK_ARG(cfg->E[k] > 0 && cfg->nu[k] > -1 && cfg->nu[k] < 0.5f, "E must be > 0 and -1 < nu < 0.5");
   auto* c = new mpm_ctx();
   c->cfg = *cfg;
   c->D = cfg->dim;
@@ -1191,7 +1193,6 @@ mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
   std::vector<float2> ml(c->n_inst);
   for (int k = 0; k < c->n_inst; ++k) {
     double E = c->E[k], nu = c->nu[k];
-    if (!(E > 0) || !(nu > -1 && nu < 0.5)) return fail(set_error(MPM_EINVAL, "E must be > 0 and -1 < nu < 0.5"));
     ml[k] = make_float2((float)(E / (2 * (1 + nu))), (float)(E * nu / ((1 + nu) * (1 - 2 * nu))));
   }
   cudaError_t e = cudaSuccess;

@@ -57,6 +57,7 @@ namespace mpmrom {
 mpm_status decoder_launch_dev(const mpm_decoder* dec, const float* X, const int32_t* idx, const int32_t* n_dev,
                               int n_rep, int64_t capacity, const float* latents, const float* dirs,
                               const int* kinds, int R, float* out, cudaStream_t s);
+void decoder_shape(const mpm_decoder* dec, int* d, int* r);
 }
 
 namespace mpmrom {
@@ -1645,8 +1646,15 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   MPM_CHECK_ARG(cfg->n_samples >= 1, "n_samples >= 1");
   MPM_CHECK_ARG(cfg->gn_iters >= 1 && cfg->gn_iters <= 16, "gn_iters in [1, 16]");
   MPM_CHECK_ARG(cfg->projection == 0 || cfg->projection == 1, "projection: 0 position-velocity, 1 velocity-only");
-  MPM_CHECK_ARG(cfg->latent_dim >= 1 && cfg->latent_dim <= kMaxRl, "latent dimension in [1, 64]");
+  MPM_CHECK_ARG(cfg->latent_dim >= 1 && cfg->latent_dim <= kMaxRl, "latent dimension in [1, 32]");
+  int dec_d = 0, dec_r = 0;
+  decoder_shape(dec, &dec_d, &dec_r);
+  MPM_CHECK_ARG(dec_d == cfg->dim && dec_r == cfg->latent_dim, "the decoder's d and r must equal dim and latent_dim");
   MPM_CHECK_ARG(cfg->n_grid >= 8, "n_grid");
+  MPM_CHECK_ARG(cfg->dx > 0 && cfg->dt > 0 && cfg->rho > 0 && cfg->p_vol > 0, "dx, dt, rho, p_vol must be > 0");
+  MPM_CHECK_ARG(cfg->E > 0 && cfg->nu > -1 && cfg->nu < 0.5f, "E must be > 0 and -1 < nu < 0.5");
+  MPM_CHECK_ARG(cfg->bc == MPM_BC_STICKY || cfg->bc == MPM_BC_SLIP_FLOOR, "bc");
+  MPM_CHECK_ARG(cfg->bc_width >= 0, "bc_width");
   MPM_CHECK_ARG(cfg->material == MPM_NEO_HOOKEAN || cfg->material == MPM_FIXED_COROTATED, "material");
   MPM_CHECK_ARG(cfg->transfer == MPM_TRANSFER_MLS || cfg->transfer == MPM_TRANSFER_PIC, "transfer");
   MPM_CHECK_ARG(cfg->ridge >= 0.f, "ridge >= 0");
@@ -1674,39 +1682,39 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   const int NS = d == 2 ? 9 : 27;
   const size_t gn = d == 2 ? (size_t)c->n * c->n : (size_t)c->n * c->n * c->n;
   mpm_status st;
-  auto fail = [&](mpm_status s) {
-    rom_destroy(c);
-    return s;
-  };
-  if ((st = ralloc(&c->X, (size_t)P * d)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->x_all_buf, (size_t)P * d)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->qlist, P)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->counts, 4)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->nodes, (size_t)k * NS)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->stamp, gn)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->grid, gn)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->v_trial, (size_t)P * d)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->x_trial, (size_t)P * d)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->step, 1)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->status, 1)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->nP_all, 1)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->outQ, (size_t)(2 * d + 2) * P * d)) != MPM_OK) return fail(st);
+  struct Owner {  // destroys the partly built context on every early return
+    rom_ctx* c;
+    ~Owner() { rom_destroy(c); }
+  } owner{c};
+  if ((st = ralloc(&c->X, (size_t)P * d)) != MPM_OK) return st;
+  if ((st = ralloc(&c->x_all_buf, (size_t)P * d)) != MPM_OK) return st;
+  if ((st = ralloc(&c->qlist, P)) != MPM_OK) return st;
+  if ((st = ralloc(&c->counts, 4)) != MPM_OK) return st;
+  if ((st = ralloc(&c->nodes, (size_t)k * NS)) != MPM_OK) return st;
+  if ((st = ralloc(&c->stamp, gn)) != MPM_OK) return st;
+  if ((st = ralloc(&c->grid, gn)) != MPM_OK) return st;
+  if ((st = ralloc(&c->v_trial, (size_t)P * d)) != MPM_OK) return st;
+  if ((st = ralloc(&c->x_trial, (size_t)P * d)) != MPM_OK) return st;
+  if ((st = ralloc(&c->step, 1)) != MPM_OK) return st;
+  if ((st = ralloc(&c->status, 1)) != MPM_OK) return st;
+  if ((st = ralloc(&c->nP_all, 1)) != MPM_OK) return st;
+  if ((st = ralloc(&c->outQ, (size_t)(2 * d + 2) * P * d)) != MPM_OK) return st;
   if (cfg->f_reference) {
-    if ((st = ralloc(&c->Fref_inv, (size_t)P * d * d)) != MPM_OK) return fail(st);
-    if ((st = ralloc(&c->xref32, (size_t)r)) != MPM_OK) return fail(st);
+    if ((st = ralloc(&c->Fref_inv, (size_t)P * d * d)) != MPM_OK) return st;
+    if ((st = ralloc(&c->xref32, (size_t)r)) != MPM_OK) return st;
   }
   // one decode of all particles per step when the neighbourhood of the samples covers most of
   // the body anyway (2D: a sample's neighbourhood spans 5 x 5 cells, ~100 particles at 4 per cell)
   c->eulerian = cfg->quadrature == 1;
   c->merged = !c->eulerian && (int64_t)P <= 32 * (int64_t)c->k;
   c->x_all = c->merged ? c->outQ : c->x_all_buf;
-  if ((st = ralloc(&c->outS, (size_t)(r + 2) * P * d)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->outLS, (size_t)(1 + kLS) * P * d)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->outS, (size_t)(r + 2) * P * d)) != MPM_OK) return st;
+  if ((st = ralloc(&c->outLS, (size_t)(1 + kLS) * P * d)) != MPM_OK) return st;
   const int n_acc = r * (r + 1) / 2 + r + 1;
   const size_t n64 = 6 * (size_t)r + 3 + n_acc + kLS;
-  if ((st = ralloc(&c->solve_mem, n64)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->solve32, (size_t)4 * r + 2 * kLS * r)) != MPM_OK) return fail(st);
-  if ((st = ralloc(&c->counters, 2)) != MPM_OK) return fail(st);
+  if ((st = ralloc(&c->solve_mem, n64)) != MPM_OK) return st;
+  if ((st = ralloc(&c->solve32, (size_t)4 * r + 2 * kLS * r)) != MPM_OK) return st;
+  if ((st = ralloc(&c->counters, 2)) != MPM_OK) return st;
   MPM_CUDA_TRY(cudaMemcpy(c->X, X, sizeof(float) * P * d, cudaMemcpyDefault));
   MPM_CUDA_TRY(cudaMemcpy(c->nP_all, &c->P, sizeof(int32_t), cudaMemcpyHostToDevice));
   RomDev& v = c->dv;
@@ -1724,12 +1732,12 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
     const int64_t cap_cells = std::min(cells_grid, cells_samp);
     c->cap_q = cap_cells * pts;
     MPM_CHECK_ARG(c->cap_q < (int64_t)1 << 30, "quadrature-point capacity");
-    if ((st = ralloc(&c->cstamp, gn)) != MPM_OK) return fail(st);
-    if ((st = ralloc(&c->clist, (size_t)cap_cells)) != MPM_OK) return fail(st);
-    if ((st = ralloc(&c->qX, (size_t)c->cap_q * d)) != MPM_OK) return fail(st);
-    if ((st = ralloc(&c->qm, (size_t)c->cap_q)) != MPM_OK) return fail(st);
-    if ((st = ralloc(&c->qV0, (size_t)c->cap_q)) != MPM_OK) return fail(st);
-    if ((st = ralloc(&c->outE, (size_t)(d + 2) * c->cap_q * d)) != MPM_OK) return fail(st);
+    if ((st = ralloc(&c->cstamp, gn)) != MPM_OK) return st;
+    if ((st = ralloc(&c->clist, (size_t)cap_cells)) != MPM_OK) return st;
+    if ((st = ralloc(&c->qX, (size_t)c->cap_q * d)) != MPM_OK) return st;
+    if ((st = ralloc(&c->qm, (size_t)c->cap_q)) != MPM_OK) return st;
+    if ((st = ralloc(&c->qV0, (size_t)c->cap_q)) != MPM_OK) return st;
+    if ((st = ralloc(&c->outE, (size_t)(d + 2) * c->cap_q * d)) != MPM_OK) return st;
     // reference domain: union of the particles' volume boxes of side h = V0^(1/d) centred on X,
     // as occupancy flags of a box grid of spacing h from origin = min X - h / 2
     std::vector<float> hX((size_t)P * d);
@@ -1754,7 +1762,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
         lin = lin * shape[a] + (int64_t)std::floor(((double)hX[(size_t)p * d + a] - lo[a]) / h);
       occ[(size_t)lin] = 1;
     }
-    if ((st = ralloc(&c->occ, (size_t)n_occ)) != MPM_OK) return fail(st);
+    if ((st = ralloc(&c->occ, (size_t)n_occ)) != MPM_OK) return st;
     MPM_CUDA_TRY(cudaMemcpy(c->occ, occ.data(), (size_t)n_occ, cudaMemcpyHostToDevice));
     v.eulerian = 1;
     v.ell = c->ell;
@@ -1822,6 +1830,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   S.ls_base32 = f + 4 * r;
   S.ls_dir32 = f + 4 * r + kLS * r;
   MPM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  owner.c = nullptr;
   *out = c;
   return MPM_OK;
 }

@@ -809,28 +809,28 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, devn);
   const int d = c->d, r = c->r;
   mpm_status st;
-  auto fail = [&](mpm_status s) {
-    trainer_destroy(c);
-    return s;
-  };
+  struct Owner {  // destroys the partly built context on every early return
+    trainer_ctx* c;
+    ~Owner() { trainer_destroy(c); }
+  } owner{c};
   // snapshot bookkeeping (host)
   std::vector<int64_t> base(sd->n_snap + 1, 0);
   for (int s = 0; s < sd->n_snap; ++s) {
     const int inst = sd->snap_inst[s];
-    if (inst < 0 || inst >= sd->n_inst) return fail(set_error(MPM_EINVAL, "snap_inst out of range"));
-    if (sd->snap_next[s] >= sd->n_snap) return fail(set_error(MPM_EINVAL, "snap_next out of range"));
+    if (inst < 0 || inst >= sd->n_inst) return set_error(MPM_EINVAL, "snap_inst out of range");
+    if (sd->snap_next[s] >= sd->n_snap) return set_error(MPM_EINVAL, "snap_next out of range");
     base[s + 1] = base[s] + (sd->inst_offsets[inst + 1] - sd->inst_offsets[inst]);
   }
   const int64_t total = base[sd->n_snap];
   const int64_t Ptot = sd->inst_offsets[sd->n_inst];
-  if ((st = talloc(&c->snap_base, sd->n_snap + 1)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->snap_inst, sd->n_snap)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->snap_next, sd->n_snap)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->inst_off, sd->n_inst + 1)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->X, (size_t)Ptot * d, false)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->sx, (size_t)total * d, false)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->sv, (size_t)total * d, false)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->sF, (size_t)total * d * d, false)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->snap_base, sd->n_snap + 1)) != MPM_OK) return st;
+  if ((st = talloc(&c->snap_inst, sd->n_snap)) != MPM_OK) return st;
+  if ((st = talloc(&c->snap_next, sd->n_snap)) != MPM_OK) return st;
+  if ((st = talloc(&c->inst_off, sd->n_inst + 1)) != MPM_OK) return st;
+  if ((st = talloc(&c->X, (size_t)Ptot * d, false)) != MPM_OK) return st;
+  if ((st = talloc(&c->sx, (size_t)total * d, false)) != MPM_OK) return st;
+  if ((st = talloc(&c->sv, (size_t)total * d, false)) != MPM_OK) return st;
+  if ((st = talloc(&c->sF, (size_t)total * d * d, false)) != MPM_OK) return st;
   MPM_CUDA_TRY(cudaMemcpy(c->snap_base, base.data(), sizeof(int64_t) * (sd->n_snap + 1), cudaMemcpyHostToDevice));
   MPM_CUDA_TRY(cudaMemcpy(c->snap_inst, sd->snap_inst, sizeof(int32_t) * sd->n_snap, cudaMemcpyDefault));
   MPM_CUDA_TRY(cudaMemcpy(c->snap_next, sd->snap_next, sizeof(int32_t) * sd->n_snap, cudaMemcpyDefault));
@@ -841,29 +841,29 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   MPM_CUDA_TRY(cudaMemcpy(c->sF, sd->F, sizeof(float) * total * d * d, cudaMemcpyDefault));
   // latent table + optimiser state
   const size_t nl = (size_t)sd->n_snap * r;
-  if ((st = talloc(&c->latents, nl)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->latents, nl)) != MPM_OK) return st;
   if (latents0) MPM_CUDA_TRY(cudaMemcpy(c->latents, latents0, sizeof(float) * nl, cudaMemcpyDefault));
-  if ((st = talloc(&c->g_lat, nl)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->m_lat, nl)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->v_lat, nl)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->g_lat, nl)) != MPM_OK) return st;
+  if ((st = talloc(&c->m_lat, nl)) != MPM_OK) return st;
+  if ((st = talloc(&c->v_lat, nl)) != MPM_OK) return st;
   if (cfg->encoder_subset > 0) {
     c->enc = true;
     if (!enc_describe(d, r, cfg->encoder_subset, 0, &c->E))
-      return fail(set_error(MPM_EINVAL, "encoder_subset: d x subset must be in [32, 8192]"));
+      return set_error(MPM_EINVAL, "encoder_subset: d x subset must be in [32, 8192]");
     for (int i = 0; i < sd->n_inst; ++i)
       if (sd->inst_offsets[i + 1] - sd->inst_offsets[i] < cfg->encoder_subset)
-        return fail(set_error(MPM_EINVAL, "encoder_subset larger than an instance"));
+        return set_error(MPM_EINVAL, "encoder_subset larger than an instance");
     const int np = c->E.n_params;
-    if ((st = talloc(&c->U, (size_t)sd->n_snap * c->E.L[0], false)) != MPM_OK) return fail(st);
-    if ((st = talloc(&c->enc_p, np)) != MPM_OK) return fail(st);
-    if ((st = talloc(&c->enc_g, np)) != MPM_OK) return fail(st);
-    if ((st = talloc(&c->enc_m, np)) != MPM_OK) return fail(st);
-    if ((st = talloc(&c->enc_v, np)) != MPM_OK) return fail(st);
-    if ((st = talloc(&c->enc_ss, 2 * d)) != MPM_OK) return fail(st);
-    if ((st = talloc(&c->enc_work, 2 * d)) != MPM_OK) return fail(st);
-    if ((st = enc_prepare(c->E)) != MPM_OK) return fail(st);
-    if ((st = enc_moments(c->E, c->sx, c->snap_base, sd->n_snap, c->enc_work, c->enc_ss, 0)) != MPM_OK) return fail(st);
-    if ((st = enc_gather(c->E, c->sx, c->snap_base, sd->n_snap, c->enc_ss, c->U, 0)) != MPM_OK) return fail(st);
+    if ((st = talloc(&c->U, (size_t)sd->n_snap * c->E.L[0], false)) != MPM_OK) return st;
+    if ((st = talloc(&c->enc_p, np)) != MPM_OK) return st;
+    if ((st = talloc(&c->enc_g, np)) != MPM_OK) return st;
+    if ((st = talloc(&c->enc_m, np)) != MPM_OK) return st;
+    if ((st = talloc(&c->enc_v, np)) != MPM_OK) return st;
+    if ((st = talloc(&c->enc_ss, 2 * d)) != MPM_OK) return st;
+    if ((st = talloc(&c->enc_work, 2 * d)) != MPM_OK) return st;
+    if ((st = enc_prepare(c->E)) != MPM_OK) return st;
+    if ((st = enc_moments(c->E, c->sx, c->snap_base, sd->n_snap, c->enc_work, c->enc_ss, 0)) != MPM_OK) return st;
+    if ((st = enc_gather(c->E, c->sx, c->snap_base, sd->n_snap, c->enc_ss, c->U, 0)) != MPM_OK) return st;
     // Xavier-uniform initial weights (fan-in / fan-out of each layer's linear map), zero biases,
     // uniform numbers from SplitMix64 seeded with the training seed
     std::vector<float> h(np, 0.f);
@@ -885,14 +885,14 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
     for (int i = 0; i < r * kEncFC; ++i) h[c->E.oW2 + i] = uni(l2);
     MPM_CUDA_TRY(cudaMemcpy(c->enc_p, h.data(), sizeof(float) * np, cudaMemcpyHostToDevice));
   }
-  if ((st = talloc(&c->gparams, dec->n_params)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->m_par, dec->n_params)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->v_par, dec->n_params)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->gparams, dec->n_params)) != MPM_OK) return st;
+  if ((st = talloc(&c->m_par, dec->n_params)) != MPM_OK) return st;
+  if ((st = talloc(&c->v_par, dec->n_params)) != MPM_OK) return st;
   // batch
   const int64_t B = c->B;
   const size_t per_pt = (size_t)(d + 2 * r + d + d + d * d + 1);
-  if ((st = talloc(&c->batch_mem, per_pt * B)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->batch_idx, (size_t)3 * B)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->batch_mem, per_pt * B)) != MPM_OK) return st;
+  if ((st = talloc(&c->batch_idx, (size_t)3 * B)) != MPM_OK) return st;
   float* m = c->batch_mem;
   c->b.B = B;
   c->b.X = m;
@@ -913,19 +913,19 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   c->b.part = c->batch_idx + 2 * B;
   // activation stores
   const size_t rows = (size_t)c->rows_total;
-  if ((st = talloc(&c->fwd, (size_t)c->R * B * d)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->zstore, (size_t)dec->n_hidden * kW * rows)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->astore, (size_t)dec->n_hidden * kW * rows)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->zbstore, (size_t)dec->n_tc * kW * rows)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->zb0, (size_t)kW * rows)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->g_lat_pt, (size_t)B * r)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->g_u_pt, (size_t)B * r)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->wtimg, (size_t)dec->n_tc * kLayerBytes)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->d_w_off, dec->w_off.size())) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->fwd, (size_t)c->R * B * d)) != MPM_OK) return st;
+  if ((st = talloc(&c->zstore, (size_t)dec->n_hidden * kW * rows)) != MPM_OK) return st;
+  if ((st = talloc(&c->astore, (size_t)dec->n_hidden * kW * rows)) != MPM_OK) return st;
+  if ((st = talloc(&c->zbstore, (size_t)dec->n_tc * kW * rows)) != MPM_OK) return st;
+  if ((st = talloc(&c->zb0, (size_t)kW * rows)) != MPM_OK) return st;
+  if ((st = talloc(&c->g_lat_pt, (size_t)B * r)) != MPM_OK) return st;
+  if ((st = talloc(&c->g_u_pt, (size_t)B * r)) != MPM_OK) return st;
+  if ((st = talloc(&c->wtimg, (size_t)dec->n_tc * kLayerBytes)) != MPM_OK) return st;
+  if ((st = talloc(&c->d_w_off, dec->w_off.size())) != MPM_OK) return st;
   MPM_CUDA_TRY(cudaMemcpy(c->d_w_off, dec->w_off.data(), sizeof(int64_t) * dec->w_off.size(), cudaMemcpyHostToDevice));
-  if ((st = talloc(&c->step, 1)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->loss, 1)) != MPM_OK) return fail(st);
-  if ((st = talloc(&c->status, 1)) != MPM_OK) return fail(st);
+  if ((st = talloc(&c->step, 1)) != MPM_OK) return st;
+  if ((st = talloc(&c->loss, 1)) != MPM_OK) return st;
+  if ((st = talloc(&c->status, 1)) != MPM_OK) return st;
   c->st.d = d;
   c->st.r = r;
   c->st.n_snap = sd->n_snap;
@@ -944,6 +944,7 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   MPM_CUDA_TRY(cudaGetLastError());
   MPM_CUDA_TRY(cudaDeviceSynchronize());
   MPM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  owner.c = nullptr;
   *out = c;
   return MPM_OK;
 }

@@ -102,6 +102,16 @@ def test_mpm_init_rejects_decreasing_offsets_and_plastic_bounds(lib):
     assert "plastic" in lib.mpm_last_error().decode()
 
 
+
+@pytest.mark.parametrize("E,nu", [(0.0, 0.3), (1e4, 0.5), (1e4, -1.0), (float("nan"), 0.3)])
+def test_mpm_init_rejects_invalid_material_before_allocating(lib, E, nu):
+    cfg, keep = _mpm_cfg()
+    keep[0][0], keep[1][0] = E, nu
+    out = C.c_void_p()
+    assert lib.mpm_init(C.byref(cfg), C.byref(out)) == _abi.MPM_EINVAL and not out.value
+    assert "E must be" in lib.mpm_last_error().decode()
+
+
 @pytest.mark.parametrize("desc,needle", [
     (dict(d=4, r=8, width=128, n_hidden=3, activation=0), "d must be"),
     (dict(d=2, r=40, width=128, n_hidden=3, activation=0), "d + r"),

@@ -394,3 +394,24 @@ def test_kinematic_samples_and_trial_velocities():
         v_trial, _, _, _ = OR.local_dynamics(p, rs, xh_n, vh_n, dbg["samples"], xa)
         assert rel(dbg["v_trial"], v_trial) < 1e-4
     rom.close()
+
+
+def test_rom_create_rejects_a_decoder_of_other_widths():
+    """The reduced model refuses a decoder whose coordinate or latent width differs from its
+    configuration (the step would read latents past the decoder's input)."""
+    import ctypes as C
+    from paper_2109_12390_gb300 import _abi
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.rom import ROM
+    sc = S.block_2d(side=8)
+    dec = Decoder.from_params(S.xavier_decoder(0, 2, 4, 128, 2, OD.ELU))
+    rom = ROM.from_scene(dec, sc, n_samples=8, seed=1)
+    lib = _abi.lib()
+    X = np.ascontiguousarray(sc.x, np.float32)
+    for field, value in (("latent_dim", 5), ("dim", 3)):
+        cfg = _abi.RomConfig.from_buffer_copy(rom.cfg)
+        setattr(cfg, field, value)
+        out = C.c_void_p()
+        st = lib.rom_create(C.byref(cfg), dec._h, X.ctypes.data, X.shape[0], C.byref(out))
+        assert st == _abi.MPM_EINVAL and not out.value, field
+        assert "decoder's d and r" in lib.mpm_last_error().decode()
