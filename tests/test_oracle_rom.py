@@ -102,6 +102,41 @@ def test_gauss_newton_equals_qr_least_squares_for_linear_decoder():
     np.testing.assert_allclose(xh, sol, rtol=1e-12, atol=1e-12)
 
 
+def test_gauss_newton_reaches_the_nonlinear_least_squares_minimiser():
+    """Alg. 6 on a nonlinear (ELU) decoder: with a consistent target it recovers the latent that
+    produced it to round-off within 5 iterations (Gauss-Newton converges quadratically at zero
+    residual); with a noisy target it reaches the minimiser that scipy's Levenberg-Marquardt finds
+    from the same start; from a far start the backtracking keeps every iteration's objective at
+    or below the previous one."""
+    so = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(31)
+    d, r = 2, 3
+    X = rng.uniform(0.3, 0.6, size=(20, d))
+    dec = S.xavier_decoder(7, d, r, 16, 2, D.ELU, X_min=X.min(0), X_range=X.max(0) - X.min(0),
+                           out_scale=np.full(d, 0.2), bias_scale=0.2)
+    xt = rng.normal(size=r)
+    exact = D.decode(dec, X, xt)
+    for pert in (0.3, 1.0):
+        x0 = xt + pert * np.random.default_rng(1).normal(size=r)
+        xh, flag = R.gauss_newton(dec, X, exact, x0, iters=5)
+        np.testing.assert_allclose(xh, xt, rtol=0, atol=1e-13)
+    noisy = exact + 0.002 * rng.normal(size=exact.shape)
+
+    def f(z):
+        return (D.decode(dec, X, z) - noisy).reshape(-1)
+
+    x0 = xt + 1.0 * rng.normal(size=r)
+    ref = so.least_squares(f, x0, xtol=1e-15, ftol=1e-15, gtol=1e-15, method="lm").x
+    xh, _ = R.gauss_newton(dec, X, noisy, x0, iters=40)
+    np.testing.assert_allclose(xh, ref, rtol=0, atol=1e-7)
+    z = xt + 3.0 * rng.normal(size=r)
+    obj = [f(z) @ f(z)]
+    for _ in range(8):
+        z, _ = R.gauss_newton(dec, X, noisy, z, iters=1)
+        obj.append(f(z) @ f(z))
+    assert np.all(np.diff(obj) <= 0) and obj[-1] < 1e-2 * obj[0]
+
+
 def test_velocity_only_matches_position_velocity_to_second_order():
     rng = np.random.default_rng(1)
     d, r = 2, 3
@@ -218,6 +253,48 @@ def test_eulerian_cells_brute_force():
         if np.isin(nodes, basis).any():
             want.append(c)
     np.testing.assert_array_equal(cells, want)
+
+
+def test_eulerian_points_tile_their_cells():
+    """ell^d points per cell at the centres of the ell^d equal sub-cells (Section 3.2.2): each
+    point lies inside its own cell, the sub-cell volumes add up to the cells' volume, and in 3D the
+    points of one cell are the sub-cell centres written out by hand."""
+    n, dx = 16, 1.0 / 16
+    for d in (2, 3):
+        cells = np.array([3, 5 * n + 7, 2 * n + 9] if d == 2 else [3, (5 * n + 7) * n + 2])
+        for ell in (1, 2, 3):
+            pts, vol = R.eulerian_points(cells, d, n, dx, ell)
+            assert pts.shape == (len(cells) * ell ** d, d)
+            owner = np.ravel_multi_index(tuple(np.floor(pts / dx).astype(np.int64).T), (n,) * d)
+            np.testing.assert_array_equal(owner, np.repeat(cells, ell ** d))
+            assert vol * len(pts) == pytest.approx(len(cells) * dx ** d, rel=1e-14)
+            assert len(np.unique(pts, axis=0)) == len(pts)
+    pts, _ = R.eulerian_points(np.array([(1 * n + 2) * n + 3]), 3, n, dx, 2)
+    want = [[(1 + a / 2 + 0.25) * dx, (2 + b / 2 + 0.25) * dx, (3 + c / 2 + 0.25) * dx]
+            for a in range(2) for b in range(2) for c in range(2)]
+    np.testing.assert_allclose(pts, want, rtol=0, atol=1e-15)
+
+
+def test_reference_domain_is_the_union_of_particle_boxes():
+    """Inside test of the reference domain (Section 3.2.2: a point belongs to the body when it lies
+    in the reference configuration): an L-shaped body with a hole on a lattice of spacing h,
+    against the union of the particles' boxes [X_p - h/2, X_p + h/2)^d tested point by point.
+    h is a power of two, so box faces are exact and points on them are tested too."""
+    h = 0.25
+    for d in (2, 3):
+        ks = np.array(list(np.ndindex(*(6,) * d)))
+        keep = ~((ks[:, 0] >= 3) & (ks[:, 1] >= 3))          # L shape
+        keep &= ~np.all(ks[:, :2] == [1, 1], axis=1)           # a hole
+        X = 1.0 + (ks[keep] + 0.5) * h
+        origin, shape, occ = R.reference_occupancy(X, h)
+        rng = np.random.default_rng(5 + d)
+        Xq = np.concatenate([rng.uniform(0.5, 3.0, size=(4000, d)),
+                             1.0 + rng.integers(-2, 9, size=(2000, d)) * (h / 2)])
+        got = R.inside_reference(Xq, origin, h, shape, occ)
+        lo, hi = X - h / 2, X + h / 2
+        want = np.array([np.any(np.all((lo <= q) & (q < hi), axis=1)) for q in Xq])
+        np.testing.assert_array_equal(got, want)
+        assert want.any() and not want.all()
 
 
 def test_decoder_inversion():
