@@ -47,8 +47,9 @@ WORKLOAD = "3D fixed-corotated cube, 262144 particles, 128^3 grid, MLS-MPM, FP64
 ALGO_BYTES_3D = 2 * 96 + 7
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the fused step kernel on this workload, from one ncu
-# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); the state written
-# by a step stays in L2 under ncu's cache control, so this is below the algorithmic traffic
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum).  It is below the
+# algorithmic traffic: the written state is still in L2 when the kernel ends, and in that capture
+# part of the state reads were served by L2 as well
 FUSED_DRAM_BYTES_NCU = 16_779_776
 
 
