@@ -287,6 +287,32 @@ def test_config4_scale_step_runs():
     assert step == 20 and np.isfinite(xh1).all()
 
 
+def test_config4_scale_one_step_parity():
+    """The reduced step at the benchmark's size and launch configuration (4096 particles, 256
+    samples, r = 16, 5 hidden layers on the FP32 decoder path, 3 Gauss-Newton iterations):
+    sample and neighbour sets bit-exact, the decoded positions, the trial velocities of the local
+    step and the velocity projection against the FP64 oracle."""
+    from paper_2109_12390_gb300.rom import ROM
+    sc, p, dec, rom, rs, xh, vh, xp = _elu_setup(seed=11, side=64, r=16, k=256)
+    rom.close()
+    dec.set_precision(True)
+    rom = ROM.from_scene(dec, sc, n_samples=256, seed=11)
+    rom.set_state(xh, vh, xp, 0)
+    rom.step(1)
+    assert rom.status() & ~ALLOWED_RANDOM == 0
+    dbg = rom.debug()
+    np.testing.assert_array_equal(dbg["samples"], OR.sample_set(11, 0, 0, len(sc.x), 256))
+    xa = dbg["x_all"].astype(np.float64)
+    assert rel(xa - p.out_shift, OD.decode(p, sc.x, xh) - p.out_shift) < 1e-5
+    basis, neigh = OR.neighbourhood(xa, dbg["samples"], sc.dx, sc.n_grid)
+    np.testing.assert_array_equal(dbg["neigh"], neigh)
+    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
+    assert rel(dbg["v_trial"], v_trial) < 1e-4
+    vh_ref = OR.project_velocity(p, sc.x[dbg["samples"]], xh, dbg["v_trial"].astype(np.float64))
+    _, vh1, _, _ = rom.get_state()
+    assert rel(vh1, vh_ref) < 1e-3
+
+
 def test_metric_accumulate():
     import torch
     from paper_2109_12390_gb300.rom import metric_accumulate
