@@ -130,6 +130,32 @@ def test_eulerian_step_2d_deep_decoder_position_projection():
     _check_step(sc, p, 64, 5, projection=0)
 
 
+def test_eulerian_step_benchmark_size():
+    """The Eulerian step at the benchmark's size and launch configuration (4096 particles, 256
+    samples, r = 16, 5 hidden layers on the FP32 decoder path, 3 Gauss-Newton iterations, about
+    5,000 quadrature points): one step against the oracle, then 20 steps run clean."""
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.rom import ROM
+    sc = S.block_2d(side=64, dt=5e-5, origin=(0.375, 0.3), E=1e3)
+    X = sc.x
+    p = S.near_identity_decoder(9, 2, 16, 5, X_min=X.min(0), X_range=X.max(0) - X.min(0), eps=3e-3)
+    nb, nq, ni = _check_step(sc, p, 256, 5, projection=0)
+    assert nq > 4000 and ni > 3000
+    dec = Decoder.from_params(p)
+    dec.set_precision(True)
+    rom = ROM.from_scene(dec, sc, n_samples=256, seed=5, quadrature=1)
+    rng = np.random.default_rng(5)
+    xh = 0.3 * rng.normal(size=16)
+    vh = rng.normal(size=16)
+    rom.set_state(xh, vh, xh - sc.dt * vh, 0)
+    rom.step(20)
+    assert rom.status() == 0
+    xh1, vh1, _, step = rom.get_state()
+    assert step == 20 and np.isfinite(xh1).all() and np.isfinite(vh1).all()
+    rom.close()
+    dec.close()
+
+
 def test_eulerian_step_3d():
     sc = S.cube_3d(seed=2, side=12, n_grid=64, dt=5e-5, bottom=0.3)
     X = sc.x
