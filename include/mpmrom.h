@@ -531,7 +531,7 @@ mpm_status rom_debug_quadrature(rom_ctx* ctx, int32_t* n_points, float* x_points
                                 float* V0, void* stream);
 
 /*
- * Kinematic (Dirichlet) boundaries of the reduced model (Lagrangian quadrature only): group[p]
+ * Kinematic (Dirichlet) boundaries of the reduced model (either quadrature): group[p]
  * (n_particles int32, host or device; -1 = free), n_groups prescribed velocities (n_groups, dim
  * floats).  Every step's sample set is the n_samples-particle draw plus, for each group, those of
  * its min(min_samples, |group|) particles of smallest hash (the same SplitMix64 hash, ties by id)

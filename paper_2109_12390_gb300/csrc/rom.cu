@@ -1633,6 +1633,48 @@ mpm_status ralloc(T** p, size_t count) {
   return MPM_OK;
 }
 
+// Cell and point buffers of the Eulerian quadrature for up to n_samp samples: the union over the
+// samples of the 6^d cells around their 3^d stencil nodes (clipped to the grid), ell^d points per
+// cell.  While the buffers are replaced the capacity reads 0, so a failed allocation leaves a
+// context whose step has no quadrature points and raises STATUS_CAPACITY instead of touching freed
+// memory.
+mpm_status rom_alloc_quadrature(rom_ctx* c, int n_samp) {
+  const int d = c->d;
+  int64_t cells_grid = 1, cells_samp = n_samp, pts = 1;
+  for (int a = 0; a < d; ++a) {
+    cells_grid *= c->n - 3;
+    cells_samp *= 6;
+    pts *= c->ell;
+  }
+  const int64_t cap_cells = std::min(cells_grid, cells_samp);
+  MPM_CHECK_ARG(cap_cells * pts < (int64_t)1 << 30, "quadrature-point capacity");
+  c->cap_q = 0;
+  c->dv.cap_cells = 0;
+  cudaFree(c->clist);
+  cudaFree(c->qX);
+  cudaFree(c->qm);
+  cudaFree(c->qV0);
+  cudaFree(c->outE);
+  c->clist = nullptr;
+  c->qX = c->qm = c->qV0 = c->outE = nullptr;
+  c->dv.clist = nullptr;
+  c->dv.qX = c->dv.qm = c->dv.qV0 = nullptr;
+  const int64_t cap_q = cap_cells * pts;
+  mpm_status st;
+  if ((st = ralloc(&c->clist, (size_t)cap_cells)) != MPM_OK) return st;
+  if ((st = ralloc(&c->qX, (size_t)cap_q * d)) != MPM_OK) return st;
+  if ((st = ralloc(&c->qm, (size_t)cap_q)) != MPM_OK) return st;
+  if ((st = ralloc(&c->qV0, (size_t)cap_q)) != MPM_OK) return st;
+  if ((st = ralloc(&c->outE, (size_t)(d + 2) * cap_q * d)) != MPM_OK) return st;
+  c->dv.clist = c->clist;
+  c->dv.qX = c->qX;
+  c->dv.qm = c->qm;
+  c->dv.qV0 = c->qV0;
+  c->dv.cap_cells = (int)cap_cells;
+  c->cap_q = cap_q;
+  return MPM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1722,22 +1764,8 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
     c->ell = cfg->ell ? cfg->ell : 2;
     c->newton_iters = cfg->newton_iters ? cfg->newton_iters : 4;
     c->newton_tol = cfg->newton_tol > 0.f ? cfg->newton_tol : 1e-3f;
-    // quadrature cells: the union over samples of the 6^d cells around their 3^d stencil nodes
-    int64_t cells_grid = 1, cells_samp = k, pts = 1;
-    for (int a = 0; a < d; ++a) {
-      cells_grid *= c->n - 3;
-      cells_samp *= 6;
-      pts *= c->ell;
-    }
-    const int64_t cap_cells = std::min(cells_grid, cells_samp);
-    c->cap_q = cap_cells * pts;
-    MPM_CHECK_ARG(c->cap_q < (int64_t)1 << 30, "quadrature-point capacity");
     if ((st = ralloc(&c->cstamp, gn)) != MPM_OK) return st;
-    if ((st = ralloc(&c->clist, (size_t)cap_cells)) != MPM_OK) return st;
-    if ((st = ralloc(&c->qX, (size_t)c->cap_q * d)) != MPM_OK) return st;
-    if ((st = ralloc(&c->qm, (size_t)c->cap_q)) != MPM_OK) return st;
-    if ((st = ralloc(&c->qV0, (size_t)c->cap_q)) != MPM_OK) return st;
-    if ((st = ralloc(&c->outE, (size_t)(d + 2) * c->cap_q * d)) != MPM_OK) return st;
+    if ((st = rom_alloc_quadrature(c, k)) != MPM_OK) return st;
     // reference domain: union of the particles' volume boxes of side h = V0^(1/d) centred on X,
     // as occupancy flags of a box grid of spacing h from origin = min X - h / 2
     std::vector<float> hX((size_t)P * d);
@@ -1768,11 +1796,6 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
     v.ell = c->ell;
     v.x_samp = c->outS;   // primal block of the sample decode
     v.cstamp = c->cstamp;
-    v.clist = c->clist;
-    v.cap_cells = (int)cap_cells;
-    v.qX = c->qX;
-    v.qm = c->qm;
-    v.qV0 = c->qV0;
     v.occ = c->occ;
     for (int a = 0; a < 3; ++a) {
       v.occ_origin[a] = (float)lo[a];
@@ -2018,7 +2041,6 @@ mpm_status rom_set_kinematic(rom_ctx* c, const int32_t* group, int32_t n_groups,
                              int32_t min_samples, void* stream) {
   MPM_CHECK_ARG(c, "null context");
   MPM_CHECK_ARG(n_groups >= 0, "n_groups >= 0");
-  MPM_CHECK_ARG(!c->eulerian || n_groups == 0, "kinematic boundaries need the Lagrangian quadrature");
   cudaStream_t s = (cudaStream_t)stream;
   const int P = c->P, NS = c->d == 2 ? 9 : 27;
   cudaFree(c->kin_group);
@@ -2093,6 +2115,8 @@ mpm_status rom_set_kinematic(rom_ctx* c, const int32_t* group, int32_t n_groups,
     MPM_CUDA_TRY(cudaMemset(c->grid, 0, sizeof(float4) * gn));
     MPM_CUDA_TRY(cudaMemset(c->stamp, 0, sizeof(uint32_t) * gn));
     c->k_cap = k_cap;
+    // the Eulerian quadrature cells around the larger sample set
+    if (c->eulerian && (st = rom_alloc_quadrature(c, k_cap)) != MPM_OK) return st;
   }
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);

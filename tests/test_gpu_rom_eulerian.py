@@ -44,7 +44,7 @@ def _order_key(x, dx, ell, n, d):
     return cl * ell ** d + jl, cl
 
 
-def _check_step(sc, p, k, seed, projection=1, transfer=None):
+def _check_step(sc, p, k, seed, projection=1, transfer=None, m_kin=0):
     import torch
     from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
     from paper_2109_12390_gb300.rom import ROM
@@ -54,6 +54,8 @@ def _check_step(sc, p, k, seed, projection=1, transfer=None):
     dec = Decoder.from_params(p)
     dec.set_precision(True)
     rom = ROM.from_scene(dec, sc, n_samples=k, seed=seed, projection=projection, quadrature=1)
+    if m_kin:
+        rom.set_kinematic(sc.kin_group, sc.kin_vel, min_samples=m_kin)
     rng = np.random.default_rng(seed)
     xh = 0.3 * rng.normal(size=r)
     vh = rng.normal(size=r)
@@ -62,7 +64,11 @@ def _check_step(sc, p, k, seed, projection=1, transfer=None):
     assert rom.status() == 0
     dbg = rom.debug()
     samples = dbg["samples"]
-    np.testing.assert_array_equal(samples, OR.sample_set(seed, 0, 0, len(sc.x), k))
+    if m_kin:
+        want = OR.kinematic_sample_set(seed, 0, 0, len(sc.x), k, sc.kin_group, m_kin)
+    else:
+        want = OR.sample_set(seed, 0, 0, len(sc.x), k)
+    np.testing.assert_array_equal(samples, want)
     # the GPU's own decoded sample positions (same kernel and rows as the step's sample decode)
     Xs = np.ascontiguousarray(sc.x[samples], np.float32)
     out = dec.eval(torch.from_numpy(Xs).cuda(), torch.from_numpy(xh.astype(np.float32)[None]).cuda(),
@@ -71,6 +77,10 @@ def _check_step(sc, p, k, seed, projection=1, transfer=None):
     assert rel(xs, OD.decode(p, sc.x[samples], xh)) < 1e-6
     qg = rom.quadrature_points()
     rs = _rom_scene(sc, k, seed)
+    if m_kin:
+        rs.kin_group, rs.kin_vel, rs.kin_min_samples = sc.kin_group, sc.kin_vel, m_kin
+        g = sc.kin_group[samples]
+        assert np.array_equal(dbg["v_trial"][g >= 0], sc.kin_vel[g[g >= 0]].astype(np.float32))
     quad = OR.eulerian_quadrature(p, rs, xh, vh, samples, xs)
     basis, cells, xq, Xq, FX, vq, mq, V0, inside = quad
     # point sets: same cells, same points
@@ -154,6 +164,17 @@ def test_eulerian_step_benchmark_size():
     assert step == 20 and np.isfinite(xh1).all() and np.isfinite(vh1).all()
     rom.close()
     dec.close()
+
+
+def test_eulerian_step_kinematic_boundaries():
+    """Kinematic (Dirichlet) groups with the Eulerian quadrature: the sample set adds each group's
+    smallest-hash particles (bit-exact), kinematic samples take their prescribed trial velocity,
+    and the quadrature cells, points and the other trial velocities match the oracle around the
+    enlarged sample set."""
+    sc = S.clamped_bar_2d(side=32)
+    X = sc.x
+    p = S.near_identity_decoder(21, 2, 4, 1, X_min=X.min(0), X_range=X.max(0) - X.min(0), eps=3e-3)
+    _check_step(sc, p, 48, 6, projection=0, m_kin=5)
 
 
 def test_eulerian_step_3d():
