@@ -368,9 +368,11 @@ def test_kinematic_sample_set_brute_force():
         assert set(smp.tolist()) == want
 
 
-def test_kinematic_trial_velocities_and_translation():
+@pytest.mark.parametrize("quadrature", ["lagrangian", "eulerian"])
+def test_kinematic_trial_velocities_and_translation(quadrature):
     """Kinematic samples take their prescribed velocity; with a translation decoder and every group
-    moving at the body's velocity the reduced step follows the translation exactly."""
+    moving at the body's velocity the reduced step follows the translation exactly, with either
+    quadrature."""
     sc = S.clamped_bar_2d(side=16, top_velocity=(0.0, 0.0))
     v0 = np.array([0.2, -0.1])
     sc.kin_vel = np.array([v0, v0])
@@ -380,7 +382,7 @@ def test_kinematic_trial_velocities_and_translation():
     rs = R.RomScene(X=X, mass=sc.p_mass, vol=sc.p_vol, E=float(sc.E[0]), nu=float(sc.nu[0]), dx=sc.dx,
                     dt=sc.dt, n_grid=sc.n_grid, gravity=sc.gravity, bc=sc.bc, bc_width=sc.bc_width,
                     material=sc.material, transfer=sc.transfer, n_samples=12, seed=4,
-                    kin_group=sc.kin_group, kin_vel=sc.kin_vel)
+                    kin_group=sc.kin_group, kin_vel=sc.kin_vel, quadrature=quadrature)
     st = R.RomState(xhat=np.zeros(2), vhat=v0.copy(), xhat_prev=-sc.dt * v0)
     for n in range(5):
         rec = {}
