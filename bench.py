@@ -385,18 +385,15 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     sc = S.cube_3d()
-    for _ in range(args.warmup if args.warmup < 1 else 0):
-        pass
     times = []
     import oracle.mpm as OM
-    ref = sc.copy()
     # each timed step: one oracle step of a 1/8 sub-block of the workload (bounded CPU time)
     sub = sc.copy()
     side_mask = (sc.x[:, 0] < 0.5) & (sc.x[:, 2] < 0.5) & (sc.x[:, 1] < 0.05 + 0.125)
     sub.x, sub.v, sub.F, sub.C = sc.x[side_mask], sc.v[side_mask], sc.F[side_mask], sc.C[side_mask]
     sub.inst_offsets = np.array([0, int(side_mask.sum())])
-    for _ in range(max(0, min(args.warmup, 1))):
-        OM.step(sub.copy(), 1)
+    for _ in range(args.warmup):
+        OM.step(sub, 1)
     for _ in range(args.steps):
         t0 = time.perf_counter()
         OM.step(sub, 1)
