@@ -348,3 +348,39 @@ def test_kinematic_particles_follow_their_prescribed_motion():
     M.step(b, 5)
     M.step(c, 5)
     assert np.array_equal(b.x, c.x) and np.array_equal(b.F, c.F)
+
+
+def test_p2g_conservation_over_random_clouds():
+    """The mass, linear-momentum and (MLS) angular-momentum identities of the transfer, over
+    randomly drawn clouds, dimensions, transfers and materials (property-based)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=30, deadline=None)
+    @hyp.given(seed=st.integers(0, 2 ** 31 - 1), d=st.sampled_from([2, 3]),
+               transfer=st.sampled_from([M.MLS, M.PIC]), material=st.sampled_from([M.NEO_HOOKEAN, M.FIXED_COROTATED]),
+               P=st.integers(1, 60), spread=st.floats(0.0, 0.3))
+    def check(seed, d, transfer, material, P, spread):
+        rng = np.random.default_rng(seed)
+        n, dx, dt = 32, 1.0 / 32, 1e-4
+        x, v, F, C = _random_state(rng, P, d, spread)
+        mass, vol = float(rng.uniform(0.1, 2.0)), 1e-3
+        mu, lam = M.lame(float(rng.uniform(1e3, 5e4)), 0.3)
+        m, p = M.p2g(x, v, F, C, mass, vol, mu, lam, dx=dx, dt=dt, n_grid=n, material=material, transfer=transfer)
+        assert m.sum() == pytest.approx(P * mass, rel=1e-12)
+        np.testing.assert_allclose(p.reshape(-1, d).sum(0), mass * v.sum(0), rtol=1e-10, atol=1e-10)
+        if transfer == M.MLS:
+            xi = np.stack(np.indices(m.shape), -1).reshape(-1, d) * dx
+            pi = p.reshape(-1, d)
+            if d == 2:
+                Lg = np.sum(xi[:, 0] * pi[:, 1] - xi[:, 1] * pi[:, 0])
+                Lp = mass * np.sum(x[:, 0] * v[:, 1] - x[:, 1] * v[:, 0] + dx * dx / 4 * (C[:, 1, 0] - C[:, 0, 1]))
+                assert Lg == pytest.approx(Lp, rel=1e-10, abs=1e-11)
+            else:
+                eps = np.zeros((3, 3, 3))
+                for a, b, c in itertools.permutations(range(3)):
+                    eps[a, b, c] = np.linalg.det(np.eye(3)[[a, b, c]])
+                Lp = mass * (np.cross(x, v).sum(0) + dx * dx / 4 * np.einsum("abc,pcb->a", eps, C))
+                np.testing.assert_allclose(np.cross(xi, pi).sum(0), Lp, rtol=1e-10, atol=1e-11)
+
+    check()
