@@ -166,3 +166,37 @@ def test_velocity_gradient_of_affine_networks_is_zero():
     dec = S.xavier_decoder(1, 2, 3, 16, 2, D.IDENTITY, X_min=X.min(0), X_range=X.max(0) - X.min(0))
     _, G = D.velocity_gradient(dec, X, rng.normal(size=3), rng.normal(size=3))
     assert np.abs(G).max() == 0.0
+
+
+def test_jacobians_over_random_architectures():
+    """Forward-mode Jacobians dg/dX and dg/dxhat and the latent JVP against central differences,
+    over randomly drawn dimensions, latent sizes, depths, activations and inputs (property-based)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=25, deadline=None, derandomize=True)
+    @hyp.given(seed=st.integers(0, 2 ** 31 - 1), d=st.sampled_from([2, 3]), r=st.integers(1, 6),
+               n_hidden=st.integers(0, 4), act=st.sampled_from([D.ELU, D.IDENTITY]))
+    def check(seed, d, r, n_hidden, act):
+        rng = np.random.default_rng(seed)
+        dec = S.xavier_decoder(seed % 1000, d, r, 16, n_hidden, act, bias_scale=0.3)
+        X = rng.uniform(size=(5, d))
+        xh = rng.normal(size=r)
+        g, JX, Jq = D.jacobians(dec, X, xh)
+        np.testing.assert_allclose(g, D.decode(dec, X, xh), rtol=0, atol=1e-14)
+        h = 1e-6
+        for k in range(d):
+            e = np.zeros(d)
+            e[k] = h
+            fd = (D.decode(dec, X + e, xh) - D.decode(dec, X - e, xh)) / (2 * h)
+            np.testing.assert_allclose(JX[:, :, k], fd, rtol=1e-6, atol=1e-8)
+        for j in range(r):
+            e = np.zeros(r)
+            e[j] = h
+            fd = (D.decode(dec, X, xh + e) - D.decode(dec, X, xh - e)) / (2 * h)
+            np.testing.assert_allclose(Jq[:, :, j], fd, rtol=1e-6, atol=1e-8)
+        u = rng.normal(size=r)
+        _, jv = D.jvp_latent(dec, X, xh, u)
+        np.testing.assert_allclose(jv, np.einsum("pij,j->pi", Jq, u), rtol=1e-12, atol=1e-13)
+
+    check()

@@ -356,7 +356,7 @@ def test_p2g_conservation_over_random_clouds():
     hyp = pytest.importorskip("hypothesis")
     st = pytest.importorskip("hypothesis.strategies")
 
-    @hyp.settings(max_examples=30, deadline=None)
+    @hyp.settings(max_examples=30, deadline=None, derandomize=True)
     @hyp.given(seed=st.integers(0, 2 ** 31 - 1), d=st.sampled_from([2, 3]),
                transfer=st.sampled_from([M.MLS, M.PIC]), material=st.sampled_from([M.NEO_HOOKEAN, M.FIXED_COROTATED]),
                P=st.integers(1, 60), spread=st.floats(0.0, 0.3))
