@@ -220,13 +220,17 @@ mpm_status mpm_debug_bins(mpm_ctx* ctx, int32_t* cell_keys, int32_t* block_keys,
  * allocates nothing: all of its work memory (two particle-state buffers,
  * the binning tables, two grids per instance) is carved out of one fixed,
  * file-scope device array of 8 MiB inside the library, which every GPU that
- * loads the library holds until the process exits.  It performs no
+ * loads the library holds until the process exits.  It makes no
  * cudaMalloc, cudaFree or other allocating call.
  *
  *   cfg          as for mpm_init (1..64 instances); copied per call.
- *   x, v, F, C   device arrays in the layout of mpm_set_state, read as the
- *                starting state and overwritten with the state after n_steps
- *                steps (caller's particle order).  C may be NULL (zero).
+ *   x, v, F, C   device (or managed) arrays in the layout of mpm_set_state,
+ *                read as the starting state and overwritten with the state
+ *                after n_steps steps (caller's particle order).  C may be
+ *                NULL (zero).  Host pointers are rejected (MPM_EINVAL); the
+ *                lengths cannot be checked here: each array must hold
+ *                P x dim (x, v) or P x dim x dim (F, C) floats, P =
+ *                inst_offsets[n_inst].
  *   status_out   if not NULL, the call synchronises `stream` and stores the
  *                MPM_STATUS_* bits raised during the call.
  *
@@ -236,11 +240,16 @@ mpm_status mpm_debug_bins(mpm_ctx* ctx, int32_t* cell_keys, int32_t* block_keys,
  * example a 2D block of 4096 particles on a 128^2 grid needs about 1 MiB, a
  * 3D scene on a 32^3 grid with 16384 particles about 5 MiB); larger
  * configurations are rejected with MPM_EINVAL and a message giving the bytes
- * needed.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) once for that device; make that first call before
- * any stream capture.  All calls share the one array and every call clears
- * the parts that must start at zero, so calls whose work overlaps on the GPU
- * (other streams, other host threads) race: serialise them.
+ * needed.  Every argument is checked before anything is enqueued, so a
+ * rejected call leaves the shared array untouched.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) once for
+ * that device; with lazy module loading that lookup may be the moment the
+ * driver loads the library's device code and commits the 8 MiB array, so
+ * make the first call at set-up time, before any stream capture.  Each call
+ * copies its per-instance constants from host memory and, with status_out,
+ * synchronises the stream.  All calls share the one array and every call
+ * clears the parts that must start at zero, so calls whose work overlaps on
+ * the GPU (other streams, other host threads) race: serialise them.
  */
 mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F, float* C, int n_steps,
                             uint32_t* status_out, void* stream);
@@ -538,7 +547,10 @@ mpm_status rom_debug_quadrature(rom_ctx* ctx, int32_t* n_points, float* x_points
  * that the draw missed, appended group by group in ascending id (min_samples in [1, 32]; the
  * paper finds 5 enough); kinematic samples take their prescribed velocity as trial velocity.
  * n_groups = 0 removes them.  Resets the grid and the step graph (call before stepping, then
- * set the state).  Synchronous.  Errors: MPM_EINVAL.
+ * set the state).  Synchronous.  Errors: MPM_EINVAL (bad arguments, group ids outside
+ * [-1, n_groups), non-finite velocities) is detected before the context changes and leaves it as
+ * it was; MPM_ENOMEM / MPM_ECUDA after that point leave the context without its kinematic
+ * buffers, and rom_step then returns MPM_EINVAL until a later rom_set_kinematic succeeds.
  */
 mpm_status rom_set_kinematic(rom_ctx* ctx, const int32_t* group, int32_t n_groups, const float* velocities,
                              int32_t min_samples, void* stream);

@@ -1454,6 +1454,31 @@ mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F,
     MPM_CHECK_ARG(cfg->inst_offsets[k + 1] >= cfg->inst_offsets[k], "inst_offsets must be non-decreasing");
   const int64_t P64 = cfg->inst_offsets[cfg->n_inst];
   MPM_CHECK_ARG(P64 >= 1 && P64 < (1ll << 30), "particle count out of range");
+  // per-instance Lame parameters and offsets, checked before anything is enqueued: a rejected
+  // call touches nothing on the device (the scratch is shared with every other call)
+  float2 ml[64];
+  int64_t offs[65];
+  for (int k = 0; k < cfg->n_inst; ++k) {
+    const double E = cfg->E[k], nu = cfg->nu[k];
+    MPM_CHECK_ARG(E > 0 && nu > -1 && nu < 0.5, "E must be > 0 and -1 < nu < 0.5");
+    ml[k] = make_float2((float)(E / (2 * (1 + nu))), (float)(E * nu / ((1 + nu) * (1 - 2 * nu))));
+  }
+  for (int k = 0; k <= cfg->n_inst; ++k) offs[k] = cfg->inst_offsets[k];
+  // the state arrays are read and written by kernels: they must be device (or managed) memory
+  {
+    const void* arrs[4] = {x, v, F, C};
+    const char* names[4] = {"x", "v", "F", "C"};
+    for (int a = 0; a < 4; ++a) {
+      if (!arrs[a]) continue;
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, arrs[a]) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(MPM_EINVAL, std::string("mpm_step_noalloc: ") + names[a] + " is not a CUDA pointer");
+      }
+      MPM_CHECK_ARG(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged,
+                    std::string("mpm_step_noalloc: ") + names[a] + " must be device or managed memory");
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   void* scratch = nullptr;
   MPM_TRY(noalloc_scratch(&scratch));
@@ -1514,14 +1539,6 @@ mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F,
   MPM_CUDA_TRY(cudaMemsetAsync(c.tile_state, 0, sizeof(unsigned long long) * c.n_scan_tiles, s));
   MPM_CUDA_TRY(cudaMemsetAsync(c.n_work, 0, sizeof(int32_t), s));
   MPM_CUDA_TRY(cudaMemsetAsync(c.status, 0, sizeof(uint32_t), s));
-  float2 ml[64];
-  int64_t offs[65];
-  for (int k = 0; k < c.n_inst; ++k) {
-    const double E = cfg->E[k], nu = cfg->nu[k];
-    MPM_CHECK_ARG(E > 0 && nu > -1 && nu < 0.5, "E must be > 0 and -1 < nu < 0.5");
-    ml[k] = make_float2((float)(E / (2 * (1 + nu))), (float)(E * nu / ((1 + nu) * (1 - 2 * nu))));
-  }
-  for (int k = 0; k <= c.n_inst; ++k) offs[k] = cfg->inst_offsets[k];
   MPM_CUDA_TRY(cudaMemcpyAsync(c.mu_lam, ml, sizeof(float2) * c.n_inst, cudaMemcpyHostToDevice, s));
   MPM_CUDA_TRY(cudaMemcpyAsync(c.d_offs, offs, sizeof(int64_t) * (c.n_inst + 1), cudaMemcpyHostToDevice, s));
   DevParams& p = c.dp;

@@ -1471,6 +1471,9 @@ struct rom_ctx {
   float* outE = nullptr;        // (d + 2, cap_q, d) decoder rows at the quadrature points
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
+  // set while rom_set_kinematic replaces buffers; still set if it failed half way, after which
+  // rom_step refuses to run (the step would read buffers that are gone)
+  bool reconfig_failed = false;
 };
 
 namespace {
@@ -1943,6 +1946,7 @@ mpm_status rom_get_state(rom_ctx* c, double* xhat, double* vhat, double* xhat_pr
 mpm_status rom_step(rom_ctx* c, int n_steps, void* stream) {
   MPM_CHECK_ARG(c, "null context");
   MPM_CHECK_ARG(n_steps >= 0, "n_steps >= 0");
+  MPM_CHECK_ARG(!c->reconfig_failed, "a failed rom_set_kinematic left the context without its buffers");
   cudaStream_t s = (cudaStream_t)stream;
   if (!c->graph) {
     // capture one step on a private stream; every launch reads its dynamic
@@ -2041,8 +2045,44 @@ mpm_status rom_set_kinematic(rom_ctx* c, const int32_t* group, int32_t n_groups,
                              int32_t min_samples, void* stream) {
   MPM_CHECK_ARG(c, "null context");
   MPM_CHECK_ARG(n_groups >= 0, "n_groups >= 0");
+  const bool on = n_groups > 0 && group;
+  if (on) {
+    MPM_CHECK_ARG(velocities, "velocities of the kinematic groups");
+    MPM_CHECK_ARG(min_samples >= 1 && min_samples <= kMaxKin, "min_samples in [1, 32]");
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const int P = c->P, NS = c->d == 2 ? 9 : 27;
+  // read and check everything before the context changes: a rejected call leaves it as it was
+  std::vector<int32_t> h, off, ids;
+  std::vector<float> v3;
+  if (on) {
+    h.resize(P);
+    std::vector<float> hv((size_t)n_groups * c->d);
+    MPM_CUDA_TRY(cudaMemcpyAsync(h.data(), group, sizeof(int32_t) * P, cudaMemcpyDefault, s));
+    MPM_CUDA_TRY(cudaMemcpyAsync(hv.data(), velocities, sizeof(float) * hv.size(), cudaMemcpyDefault, s));
+    MPM_CUDA_TRY(cudaStreamSynchronize(s));
+    off.assign(n_groups + 1, 0);
+    for (int p = 0; p < P; ++p) {
+      MPM_CHECK_ARG(h[p] >= -1 && h[p] < n_groups, "group ids in [-1, n_groups)");
+      if (h[p] >= 0) ++off[h[p] + 1];
+    }
+    for (float vv : hv) MPM_CHECK_ARG(std::isfinite(vv), "finite group velocities");
+    for (int g = 0; g < n_groups; ++g) off[g + 1] += off[g];
+    ids.resize(off[n_groups]);
+    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    for (int p = 0; p < P; ++p)
+      if (h[p] >= 0) ids[fill[h[p]]++] = p;   // ascending within each group
+    v3.assign((size_t)n_groups * 3, 0.f);
+    for (int g = 0; g < n_groups; ++g)
+      for (int a = 0; a < c->d; ++a) v3[(size_t)3 * g + a] = hv[(size_t)c->d * g + a];
+  }
+  // from here on the buffers the captured step reads are replaced: drop the graph first, and
+  // mark the context unusable until every buffer is in place again
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->reconfig_failed = true;
   cudaFree(c->kin_group);
   cudaFree(c->kin_vel);
   cudaFree(c->kg_off);
@@ -2061,27 +2101,7 @@ mpm_status rom_set_kinematic(rom_ctx* c, const int32_t* group, int32_t n_groups,
   c->dv.n_groups = 0;
   c->dv.m_kin = 0;
   int k_cap = c->k;
-  if (n_groups > 0 && group) {
-    MPM_CHECK_ARG(velocities, "velocities of the kinematic groups");
-    MPM_CHECK_ARG(min_samples >= 1 && min_samples <= kMaxKin, "min_samples in [1, 32]");
-    std::vector<int32_t> h(P);
-    std::vector<float> hv((size_t)n_groups * c->d);
-    MPM_CUDA_TRY(cudaMemcpyAsync(h.data(), group, sizeof(int32_t) * P, cudaMemcpyDefault, s));
-    MPM_CUDA_TRY(cudaMemcpyAsync(hv.data(), velocities, sizeof(float) * hv.size(), cudaMemcpyDefault, s));
-    MPM_CUDA_TRY(cudaStreamSynchronize(s));
-    std::vector<int32_t> off(n_groups + 1, 0), ids;
-    for (int p = 0; p < P; ++p) {
-      MPM_CHECK_ARG(h[p] >= -1 && h[p] < n_groups, "group ids in [-1, n_groups)");
-      if (h[p] >= 0) ++off[h[p] + 1];
-    }
-    for (int g = 0; g < n_groups; ++g) off[g + 1] += off[g];
-    ids.resize(off[n_groups]);
-    std::vector<int32_t> fill(off.begin(), off.end() - 1);
-    for (int p = 0; p < P; ++p)
-      if (h[p] >= 0) ids[fill[h[p]]++] = p;   // ascending within each group
-    std::vector<float> v3((size_t)n_groups * 3, 0.f);
-    for (int g = 0; g < n_groups; ++g)
-      for (int a = 0; a < c->d; ++a) v3[(size_t)3 * g + a] = hv[(size_t)c->d * g + a];
+  if (on) {
     mpm_status st;
     if ((st = ralloc(&c->kin_group, P)) != MPM_OK) return st;
     if ((st = ralloc(&c->kin_vel, v3.size())) != MPM_OK) return st;
@@ -2102,10 +2122,11 @@ mpm_status rom_set_kinematic(rom_ctx* c, const int32_t* group, int32_t n_groups,
     c->dv.m_kin = min_samples;
     k_cap = std::min(P, c->k + min_samples * n_groups);
   }
-  // the basis-node list and the step graph depend on the sample capacity
+  // the basis-node list depends on the sample capacity
   if (k_cap != c->k_cap) {
     cudaFree(c->nodes);
     c->nodes = nullptr;
+    c->dv.nodes = nullptr;
     mpm_status st = ralloc(&c->nodes, (size_t)k_cap * NS);
     if (st != MPM_OK) return st;
     c->dv.nodes = c->nodes;
@@ -2118,10 +2139,7 @@ mpm_status rom_set_kinematic(rom_ctx* c, const int32_t* group, int32_t n_groups,
     // the Eulerian quadrature cells around the larger sample set
     if (c->eulerian && (st = rom_alloc_quadrature(c, k_cap)) != MPM_OK) return st;
   }
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  c->reconfig_failed = false;
   return MPM_OK;
 }
 

@@ -152,8 +152,22 @@ def step_noalloc(scene_cfg, x, v, F, C_=None, n_steps=1, stream=None):
     """mpm_step_noalloc through the C ABI: steps the state held in the caller's CUDA tensors
     x (P, d), v (P, d), F (P, d, d), C (P, d, d) in place, using only the library's fixed
     device scratch (no allocation).  `scene_cfg` is an MPM context's configuration source:
-    a synth.scenes.Scene.  Returns the status bits raised during the call."""
+    a synth.scenes.Scene.  Returns the status bits raised during the call.
+
+    The kernels write these tensors in place and the C entry point cannot see their lengths, so
+    every one must be a contiguous float32 CUDA tensor on the current device holding exactly
+    P*d (x, v) or P*d*d (F, C) elements, P = inst_offsets[-1]; anything else raises ValueError
+    before the call."""
     sc = scene_cfg
+    P, d = int(np.asarray(sc.inst_offsets)[-1]), int(sc.dim)
+    dev = torch.cuda.current_device()
+    for name, t, n in (("x", x, P * d), ("v", v, P * d), ("F", F, P * d * d), ("C", C_, P * d * d)):
+        if t is None and name == "C":
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"step_noalloc: {name} must be a CUDA tensor on the current device")
+        if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"step_noalloc: {name} must be contiguous float32 with {n} elements")
     E = np.ascontiguousarray(np.atleast_1d(sc.E), np.float32)
     nu = np.ascontiguousarray(np.atleast_1d(sc.nu), np.float32)
     offs = np.ascontiguousarray(sc.inst_offsets, np.int64)

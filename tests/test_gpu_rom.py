@@ -441,3 +441,42 @@ def test_rom_create_rejects_a_decoder_of_other_widths():
         st = lib.rom_create(C.byref(cfg), dec._h, X.ctypes.data, X.shape[0], C.byref(out))
         assert st == _abi.MPM_EINVAL and not out.value, field
         assert "decoder's d and r" in lib.mpm_last_error().decode()
+
+
+def test_rejected_kinematic_call_leaves_the_stepping_context_intact():
+    """rom_set_kinematic checks its group ids and velocities before it frees or replaces any buffer
+    the captured step graph reads: after a rejected call (group id out of range), the context
+    steps on exactly as an untouched twin does."""
+    from paper_2109_12390_gb300 import _abi
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.rom import ROM
+    sc = S.clamped_bar_2d(side=32)
+    X = sc.x
+    p = S.near_identity_decoder(21, 2, 4, 1, X_min=X.min(0), X_range=X.max(0) - X.min(0), eps=3e-3)
+    dec = Decoder.from_params(p)
+    dec.set_precision(True)
+    roms = [ROM.from_scene(dec, sc, n_samples=48, seed=6, projection=1) for _ in range(2)]
+    rng = np.random.default_rng(6)
+    xh = 0.3 * rng.normal(size=4)
+    vh = rng.normal(size=4)
+    for rom in roms:
+        rom.set_kinematic(sc.kin_group, sc.kin_vel, min_samples=5)
+        rom.set_state(xh, vh, xh - sc.dt * vh, 0)
+        rom.step(2)                          # the step graph is captured here
+    bad = sc.kin_group.copy()
+    bad[7] = 5                               # only groups 0 and 1 exist
+    with pytest.raises(_abi.MpmError) as e:
+        roms[0].set_kinematic(bad, sc.kin_vel, min_samples=5)
+    assert e.value.status == _abi.MPM_EINVAL
+    with pytest.raises(_abi.MpmError):
+        roms[0].set_kinematic(sc.kin_group, np.full_like(sc.kin_vel, np.nan), min_samples=5)
+    for rom in roms:
+        rom.step(3)
+        assert rom.status() == 0
+    a, b = roms[0].get_state(), roms[1].get_state()
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert a[3] == b[3] == 5
+    for rom in roms:
+        rom.close()
+    dec.close()
