@@ -602,6 +602,21 @@ typedef struct snapshot_desc {
 } snapshot_desc;
 
 /*
+ * Input and output scaling of Appendix B, computed on the device from a
+ * snapshot store: per coordinate a, X_min[a] and X_range[a] = max - min of
+ * the reference positions X (all inst_offsets[n_inst] particles), and the
+ * mean and standard deviation (population, 1/N) of the positions x of every
+ * snapshot row.  Sets the decoder's scaling to {X_min, X_range, mean, std}
+ * (the layout of decoder_set_params' norm) and re-packs its derived weight
+ * images; the network parameters are unchanged.  sd->X and sd->x must be
+ * device (or managed) pointers; inst_offsets and snap_inst are host arrays.
+ * Asynchronous on `stream` (its work memory is allocated and freed in
+ * stream order).  Errors: MPM_EINVAL (dim mismatch, empty store, host pointers,
+ * snap_inst out of range).
+ */
+mpm_status decoder_fit_scaling(mpm_decoder* dec, const snapshot_desc* snaps, void* stream);
+
+/*
  *   lambda_F, lambda_v  penalty weights of the deformation-gradient and
  *                       velocity terms of the loss.
  *   dt_snap             time between a snapshot and its successor (the

@@ -19,7 +19,9 @@ tangent penalties need) for the training gradients.
 Pins (tests/test_oracle_decoder.py): tangents against central differences;
 a linear (identity-activation) network whose Jacobians are exactly its weight
 blocks; loss gradients against central differences of the loss; Adam's
-closed-form behaviour under a constant gradient.
+closed-form behaviour under a constant gradient; the Appendix B scaling maps the training X
+onto [0, 1] with both ends attained and standardises the snapshot positions (zero mean, unit
+population variance), checked by brute force on small sets.
 """
 from __future__ import annotations
 
@@ -234,3 +236,17 @@ def lr_schedule(step, n_steps, lr0=1e-3, lr1=1e-6):
     if n_steps <= 1:
         return lr0
     return lr0 * (lr1 / lr0) ** (step / (n_steps - 1))
+
+
+def appendix_b_scaling(X, x):
+    """Input and output scaling of Appendix B, by definition: per coordinate, the minimum and the
+    range (max - min) of the reference positions X (n, d), and the mean and the population
+    standard deviation (1/N) of the positions x (N, d) of every snapshot row.  Returns
+    (X_min, X_range, out_shift, out_scale), the fields the decoder's input and output maps use."""
+    X = np.asarray(X, np.float64)
+    x = np.asarray(x, np.float64)
+    lo = X.min(axis=0)
+    hi = X.max(axis=0)
+    mean = x.sum(axis=0) / x.shape[0]
+    std = np.sqrt(((x - mean) ** 2).sum(axis=0) / x.shape[0])
+    return lo, hi - lo, mean, std

@@ -110,6 +110,7 @@ SIGNATURES = [
     ("rom_set_kinematic", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     ("rom_decode_points", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("metric_accumulate", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    ("decoder_fit_scaling", C.c_int, [C.c_void_p, C.POINTER(SnapshotDesc), C.c_void_p]),
     ("trainer_create", C.c_int, [C.c_void_p, C.POINTER(TrainConfig), C.POINTER(SnapshotDesc), C.c_void_p,
                                  C.POINTER(C.c_void_p)]),
     ("trainer_destroy", None, [C.c_void_p]),

@@ -653,6 +653,109 @@ struct trainer_ctx {
   cudaGraphExec_t graph_noupdate = nullptr;
 };
 
+
+// ---------------------------------------------------------------------------------------------
+// Input and output scaling of Appendix B: per coordinate, min-max of the reference positions X
+// and mean / standard deviation of every snapshot position x.  Pass 1: per-block minimum and
+// maximum of X and FP64 sum of x; pass 2: FP64 sum of (x - mean)^2 with the pass-1 mean.  One
+// block reduces the partials after each pass.
+// ---------------------------------------------------------------------------------------------
+constexpr int kScaleThreads = 256;
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;   // valid in thread 0
+}
+
+__device__ __forceinline__ float block_minmax(float v, bool is_max, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float u = __shfl_down_sync(0xffffffffu, v, o);
+    v = is_max ? fmaxf(v, u) : fminf(v, u);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  float t = v;
+  if (threadIdx.x == 0)
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = is_max ? fmaxf(t, sh[w]) : fminf(t, sh[w]);
+  return t;   // valid in thread 0
+}
+
+// pass 0: part[b] = {min X_a, max X_a, sum x_a}, pass 1: part[b] = {sum (x_a - mean_a)^2}
+__global__ void __launch_bounds__(kScaleThreads) scale_partials(int pass, int d, const float* __restrict__ X,
+                                                                int64_t nX, const float* __restrict__ x, int64_t nx,
+                                                                const double* __restrict__ mean, double* part) {
+  __shared__ double shd[kScaleThreads / 32];
+  __shared__ float shf[kScaleThreads / 32];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int a = 0; a < d; ++a) {
+    if (pass == 0) {
+      float lo = INFINITY, hi = -INFINITY;
+      for (int64_t i = i0; i < nX; i += stride) {
+        const float u = X[i * d + a];
+        lo = fminf(lo, u);
+        hi = fmaxf(hi, u);
+      }
+      double s = 0.0;
+      for (int64_t i = i0; i < nx; i += stride) s += (double)x[i * d + a];
+      lo = block_minmax(lo, false, shf);
+      hi = block_minmax(hi, true, shf);
+      s = block_sum_d(s, shd);
+      if (threadIdx.x == 0) {
+        part[(size_t)blockIdx.x * 3 * d + 3 * a + 0] = lo;
+        part[(size_t)blockIdx.x * 3 * d + 3 * a + 1] = hi;
+        part[(size_t)blockIdx.x * 3 * d + 3 * a + 2] = s;
+      }
+    } else {
+      const double m = mean[a];
+      double s = 0.0;
+      for (int64_t i = i0; i < nx; i += stride) {
+        const double e = (double)x[i * d + a] - m;
+        s = fma(e, e, s);
+      }
+      s = block_sum_d(s, shd);
+      if (threadIdx.x == 0) part[(size_t)blockIdx.x * d + a] = s;
+    }
+  }
+}
+
+// one thread per coordinate: reduce the partials; pass 0 leaves the mean in stats[0..d), pass 1
+// writes the decoder's scaling {X_min, X_range, mean, std} (as floats) into norm
+__global__ void scale_finish(int pass, int d, int n_part, int64_t nx, const double* part, double* stats,
+                             float* norm) {
+  const int a = threadIdx.x;
+  if (a >= d) return;
+  if (pass == 0) {
+    double lo = INFINITY, hi = -INFINITY, s = 0.0;
+    for (int b = 0; b < n_part; ++b) {
+      lo = fmin(lo, part[(size_t)b * 3 * d + 3 * a + 0]);
+      hi = fmax(hi, part[(size_t)b * 3 * d + 3 * a + 1]);
+      s += part[(size_t)b * 3 * d + 3 * a + 2];
+    }
+    stats[a] = s / (double)nx;
+    stats[d + a] = lo;
+    stats[2 * d + a] = hi;
+  } else {
+    double ss = 0.0;
+    for (int b = 0; b < n_part; ++b) ss += part[(size_t)b * d + a];
+    norm[a] = (float)stats[d + a];
+    norm[d + a] = (float)(stats[2 * d + a] - stats[d + a]);
+    norm[2 * d + a] = (float)stats[a];
+    norm[3 * d + a] = (float)sqrt(ss / (double)nx);
+  }
+}
+
 namespace {
 
 mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
@@ -782,6 +885,47 @@ mpm_status capture(trainer_ctx* c, int update, cudaGraphExec_t* out) {
 }  // namespace
 
 extern "C" {
+
+mpm_status decoder_fit_scaling(mpm_decoder* dec, const snapshot_desc* sd, void* stream) {
+  MPM_CHECK_ARG(dec && sd && sd->X && sd->x && sd->inst_offsets && sd->snap_inst, "null argument");
+  MPM_CHECK_ARG(sd->dim == dec->d, "snapshot dim differs from the decoder's");
+  MPM_CHECK_ARG(sd->n_inst >= 1 && sd->n_snap >= 1, "empty snapshot store");
+  for (const void* ptr : {(const void*)sd->X, (const void*)sd->x}) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(MPM_EINVAL, "decoder_fit_scaling: X and x must be device pointers");
+    }
+    MPM_CHECK_ARG(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged,
+                  "decoder_fit_scaling: X and x must be device (or managed) pointers");
+  }
+  int64_t nx = 0;
+  for (int s = 0; s < sd->n_snap; ++s) {
+    const int inst = sd->snap_inst[s];
+    MPM_CHECK_ARG(inst >= 0 && inst < sd->n_inst, "snap_inst out of range");
+    nx += sd->inst_offsets[inst + 1] - sd->inst_offsets[inst];
+  }
+  const int64_t nX = sd->inst_offsets[sd->n_inst];
+  MPM_CHECK_ARG(nX >= 1 && nx >= 1, "no particles");
+  const int d = dec->d;
+  cudaStream_t s = (cudaStream_t)stream;
+  int devn = 0, n_sm = 0;
+  MPM_CUDA_TRY(cudaGetDevice(&devn));
+  MPM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, devn));
+  const int blocks = std::max(1, std::min<int>(n_sm * 4, (int)((std::max(nX, nx) + kScaleThreads - 1) / kScaleThreads)));
+  double* mem = nullptr;
+  MPM_CUDA_TRY(cudaMallocAsync((void**)&mem, sizeof(double) * ((size_t)blocks * 3 * d + 3 * d), s));
+  double* part = mem;
+  double* stats = mem + (size_t)blocks * 3 * d;
+  scale_partials<<<blocks, kScaleThreads, 0, s>>>(0, d, sd->X, nX, sd->x, nx, nullptr, part);
+  scale_finish<<<1, 32, 0, s>>>(0, d, blocks, nx, part, stats, nullptr);
+  scale_partials<<<blocks, kScaleThreads, 0, s>>>(1, d, sd->X, nX, sd->x, nx, stats, part);
+  scale_finish<<<1, 32, 0, s>>>(1, d, blocks, nx, part, stats, dec->norm);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(mem, s);
+  if (e != cudaSuccess) return set_error(MPM_ECUDA, std::string("decoder_fit_scaling: ") + cudaGetErrorString(e));
+  return decoder_refresh(dec, s);
+}
 
 mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snapshot_desc* sd, const float* latents0,
                           trainer_ctx** out) {

@@ -70,6 +70,12 @@ class Decoder:
         self._keep = (f(params), f(norm))
         _abi.check(_abi.lib().decoder_set_params(self._h, _ptr(self._keep[0]), _ptr(self._keep[1]), _stream(stream)))
 
+    def fit_scaling(self, snaps, stream=None):
+        """Appendix B scaling from a snapshot dict (device X and x): decoder_fit_scaling."""
+        from .train import snapshot_desc
+        sd = snapshot_desc(snaps)
+        _abi.check(_abi.lib().decoder_fit_scaling(self._h, C.byref(sd), _stream(stream)))
+
     def get_params(self, params=None, norm=None, stream=None):
         _abi.check(_abi.lib().decoder_get_params(self._h, _ptr(params), _ptr(norm), _stream(stream)))
 

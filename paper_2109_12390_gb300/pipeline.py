@@ -19,16 +19,20 @@ from .train import Trainer, generate_snapshots
 
 
 def decoder_for_snapshots(snaps, r, seed=0, width=128, n_hidden=5, activation=0):
-    """Xavier-initialised decoder (Appendix B) with min-max input scaling over the training X
-    and output standardisation over the snapshot positions."""
+    """Xavier-initialised decoder (seeded initial weights) whose Appendix B scaling (min-max of
+    the training X, standardisation of the snapshot positions) is computed by the library from
+    the snapshots (decoder_fit_scaling).  Returns the decoder and its initial parameters with
+    the fitted scaling read back."""
     import synth.scenes as S
-    X = snaps["X"].cpu().numpy().astype(np.float64)
-    x = snaps["x"]
-    mean = x.mean(0).double().cpu().numpy()
-    std = x.std(0).double().cpu().numpy()
-    p = S.xavier_decoder(seed, snaps["dim"], r, width, n_hidden, activation, X_min=X.min(0),
-                         X_range=X.max(0) - X.min(0), out_shift=mean, out_scale=std)
-    return Decoder.from_params(p), p
+    d = snaps["dim"]
+    p = S.xavier_decoder(seed, d, r, width, n_hidden, activation)
+    dec = Decoder.from_params(p)
+    dec.fit_scaling(snaps)
+    norm = torch.empty(4 * d, dtype=torch.float32, device="cuda")
+    dec.get_params(None, norm)
+    nm = norm.cpu().numpy().astype(np.float64)
+    p.X_min, p.X_range, p.out_shift, p.out_scale = nm[:d], nm[d:2 * d], nm[2 * d:3 * d], nm[3 * d:]
+    return dec, p
 
 
 def train(snaps, decoder, *, steps, batch=65536, lambda_F=100.0, lambda_v=0.01, lr0=1e-3, lr1=1e-6, seed=0,

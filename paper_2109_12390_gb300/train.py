@@ -50,6 +50,13 @@ def generate_snapshots(scene, n_steps, every, device="cuda"):
                 status=status, steps_between=every, dt_snap=every * float(np.float32(scene.dt)))
 
 
+def snapshot_desc(snaps):
+    """The C snapshot_desc of a snapshot dict (pointers into its arrays, which the caller keeps alive)."""
+    return _abi.SnapshotDesc(snaps["dim"], snaps["n_inst"], _vp(snaps["inst_offsets"]), _vp(snaps["X"]),
+                             snaps["n_snap"], _vp(snaps["snap_inst"]), _vp(snaps["snap_next"]),
+                             _vp(snaps["x"]), _vp(snaps["v"]), _vp(snaps["F"]))
+
+
 class Trainer:
     def __init__(self, decoder, snaps, *, lambda_F=100.0, lambda_v=0.01, dt_snap, lr0=1e-3, lr1=1e-6,
                  batch=65536, total_steps=10000, seed=0, latents0=None, encoder_subset=0):
@@ -57,9 +64,7 @@ class Trainer:
         self.decoder = decoder
         self.snaps = snaps
         self._keep = [snaps["inst_offsets"], snaps["snap_inst"], snaps["snap_next"]]
-        sd = _abi.SnapshotDesc(snaps["dim"], snaps["n_inst"], _vp(snaps["inst_offsets"]), _vp(snaps["X"]),
-                               snaps["n_snap"], _vp(snaps["snap_inst"]), _vp(snaps["snap_next"]),
-                               _vp(snaps["x"]), _vp(snaps["v"]), _vp(snaps["F"]))
+        sd = snapshot_desc(snaps)
         cfg = _abi.TrainConfig(lambda_F, lambda_v, dt_snap, lr0, lr1, batch, total_steps, seed, encoder_subset)
         self.cfg = cfg
         lat = None if latents0 is None else np.ascontiguousarray(latents0, np.float32)

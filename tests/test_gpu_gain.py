@@ -7,7 +7,9 @@ GPU snapshots against the same method without it, on a held-out 2D impact scene.
   dg/dX is one constant matrix, so it moves the body as a translation of a fixed shape).
 
 All three run the same reduced step (Algorithms 2, 3, 5, 6) for 2000 steps (fall and floor
-impact) and are scored by the accumulated relative position error against the full-order run.
+impact) with the settings of the benchmark (FP32 decoder calls, ridge 0.1 on the increments,
+reference gradient) and are scored by the accumulated relative position error against the
+full-order run.  The trained network must beat both.
 """
 import numpy as np
 import pytest
@@ -15,7 +17,7 @@ import pytest
 import synth.scenes as S
 
 pytestmark = pytest.mark.gpu
-TRAIN_STEPS = 3000
+TRAIN_STEPS = 6000
 STEPS = 2000
 
 
@@ -31,7 +33,7 @@ def test_trained_decoder_beats_untrained_and_linear_manifold():
     sc = S.block_2d(seed=4, side=64, dt=5e-5, origin=(0.375, 0.06), E=E, v0=v0)
     fx, _, fstat = PL.fom_positions(sc, STEPS)
     assert fstat == 0
-    settings = dict(n_samples=256, seed=4, projection=0, ridge=1e-1)
+    settings = dict(n_samples=256, seed=4, projection=0, ridge=1e-1, f_reference=1)
     errs = {}
     for name, act, steps in (("trained", 0, TRAIN_STEPS), ("linear", 1, TRAIN_STEPS), ("untrained", 0, 0)):
         dec, _ = PL.decoder_for_snapshots(snaps, 16, seed=0, activation=act)
@@ -39,11 +41,10 @@ def test_trained_decoder_beats_untrained_and_linear_manifold():
             tr, hist, _ = PL.train(snaps, dec, steps=steps)
             assert np.isfinite(hist[-1][1])
             tr.close()
+        dec.set_precision(True)
         errs[name] = PL.rom_error(dec, sc, fx, **settings).error_percent
     print("accumulated relative position error (%)", errs)
     # the untrained network does not represent the motion at all
     assert errs["trained"] < 0.1 * errs["untrained"], errs
-    # the linear manifold is reported, not bounded: its dg/dX is one constant matrix (a rigid
-    # translation model), which is exact at rest and close for this stiff block's fall, so it
-    # carries none of the gradient error that the trained network's stress sees
-    assert np.isfinite(errs["linear"])
+    # and the nonlinear manifold beats the linear one trained on the same snapshots for as long
+    assert errs["trained"] < errs["linear"], errs

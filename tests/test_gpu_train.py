@@ -109,3 +109,37 @@ def test_adam_first_step_and_loss_decrease():
     assert step == 300
     assert tr.status() == 0
     assert loss1 < 0.5 * loss0
+
+
+def test_fit_scaling_matches_appendix_b_definition():
+    """decoder_fit_scaling (Appendix B min-max of X, mean / population std of the snapshot
+    positions) against the oracle's definition on the same FP32 values, over a store with
+    uneven instances; then the decoder's outputs use exactly that scaling."""
+    import torch
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
+    sc = S.batch_2d(seed=5, n_inst=3)
+    d, P = 2, sc.n_particles
+    rng = np.random.default_rng(5)
+    J = 3
+    xs = sc.x[None] + 0.02 * rng.normal(size=(J, P, d)) + np.array([0.1, -0.05])
+    snaps = dict(dim=d, n_inst=3, inst_offsets=np.ascontiguousarray(sc.inst_offsets, np.int64),
+                 X=torch.from_numpy(sc.x.astype(np.float32)).cuda(), n_snap=J * 3,
+                 snap_inst=np.array([s % 3 for s in range(J * 3)], np.int32),
+                 snap_next=np.array([s + 3 if s + 3 < J * 3 else -1 for s in range(J * 3)], np.int32),
+                 x=torch.from_numpy(xs.reshape(-1, d).astype(np.float32)).cuda(), v=None, F=None)
+    p = S.xavier_decoder(1, d, 4, 128, 2, OD.ELU)
+    dec = Decoder.from_params(p)
+    dec.fit_scaling(snaps)
+    norm = torch.empty(4 * d, dtype=torch.float32, device="cuda")
+    dec.get_params(None, norm)
+    got = norm.cpu().numpy().astype(np.float64)
+    want = np.concatenate(OD.appendix_b_scaling(sc.x.astype(np.float32), xs.reshape(-1, d).astype(np.float32)))
+    assert rel(got[:2 * d], want[:2 * d]) == 0.0          # min and range of FP32 values: exact
+    assert rel(got[2 * d:], want[2 * d:]) < 1e-6          # FP64 sums, one FP32 rounding
+    p.X_min, p.X_range, p.out_shift, p.out_scale = want[:d], want[d:2 * d], want[2 * d:3 * d], want[3 * d:]
+    X = sc.x[:64].astype(np.float32)
+    xh = rng.normal(size=4).astype(np.float32)
+    out = dec.eval(torch.from_numpy(X).cuda(), torch.from_numpy(xh[None]).cuda(), [PRIMAL]).cpu().numpy()[0]
+    ref = OD.decode(p, X.astype(np.float64), xh.astype(np.float64))
+    assert rel(out, ref) < TOL
+    dec.close()

@@ -200,3 +200,30 @@ def test_jacobians_over_random_architectures():
         np.testing.assert_allclose(jv, np.einsum("pij,j->pi", Jq, u), rtol=1e-12, atol=1e-13)
 
     check()
+
+
+def test_appendix_b_scaling_maps_inputs_to_unit_box_and_standardises_outputs():
+    """Pins of the Appendix B scaling: the min-max map sends the training X into [0, 1] with 0 and
+    1 attained per coordinate; the output map standardises the snapshot positions (mean 0,
+    population variance 1); both against brute-force loops on a small set."""
+    rng = np.random.default_rng(7)
+    X = rng.uniform(-0.3, 2.0, size=(37, 3)) * np.array([1.0, 0.2, 5.0])
+    x = rng.normal(size=(211, 3)) * np.array([0.1, 3.0, 1e-3]) + np.array([0.5, -2.0, 7.0])
+    lo, rg, mean, std = D.appendix_b_scaling(X, x)
+    Xn = (X - lo) / rg
+    assert Xn.min() >= 0.0 and Xn.max() <= 1.0
+    np.testing.assert_allclose(Xn.min(0), 0.0, atol=1e-15)
+    np.testing.assert_allclose(Xn.max(0), 1.0, rtol=1e-15)
+    z = (x - mean) / std
+    np.testing.assert_allclose(z.mean(0), 0.0, atol=1e-10)   # x - mean rounds at 7e-16 / 1e-3
+    np.testing.assert_allclose((z ** 2).mean(0), 1.0, rtol=1e-12)
+    for a in range(3):
+        m = 0.0
+        for i in range(len(x)):
+            m += x[i, a]
+        m /= len(x)
+        v = 0.0
+        for i in range(len(x)):
+            v += (x[i, a] - m) ** 2
+        assert abs(std[a] - np.sqrt(v / len(x))) <= 1e-12 * std[a]
+        assert lo[a] == min(X[:, a]) and abs(lo[a] + rg[a] - max(X[:, a])) <= 4e-16 * abs(max(X[:, a]))
