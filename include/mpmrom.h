@@ -182,6 +182,15 @@ mpm_status mpm_step_profiled(mpm_ctx* ctx, int n_steps, void* flush_buf, size_t 
                              void* stream);
 
 /*
+ * mpm_step with CUDA events only at step boundaries (none between a step's
+ * kernels), for measuring whole steps: as mpm_step_profiled, with the device
+ * duration in milliseconds of step k written to step_ms[k] (host array of
+ * n_steps floats).
+ */
+mpm_status mpm_step_timed(mpm_ctx* ctx, int n_steps, void* flush_buf, size_t flush_bytes, float* step_ms,
+                          void* stream);
+
+/*
  * Kinematic (essential, Dirichlet) boundaries: group[p] (n_particles int32, host or device, the
  * caller's particle order; -1 = free) assigns particles to n_groups groups with prescribed
  * velocities (n_groups, dim floats).  After every grid-to-particle transfer a particle of group g
@@ -638,6 +647,15 @@ mpm_status decoder_fit_scaling(mpm_decoder* dec, const snapshot_desc* snaps, voi
  *                       6 and stride 2 (ELU) down to the last length >= 32, a
  *                       32-wide ELU layer and a linear layer to r.  dim x n in
  *                       [32, 8192].  Weights Xavier-uniform from `seed`.
+ *   shard_index,        data-parallel training (shard_count > 1): this context
+ *   shard_count         draws draws shard_index * batch .. (shard_index + 1) *
+ *                       batch - 1 of the step's minibatch of shard_count * batch
+ *                       points, and normalises its loss and gradients by the
+ *                       whole minibatch, so that the sum of the shards'
+ *                       gradients is the gradient of the whole minibatch; the
+ *                       shards then add their gradients (an all-reduce) between
+ *                       trainer_compute_gradients and trainer_apply_gradients.
+ *                       shard_count 0 or 1: one process owns the minibatch.
  */
 typedef struct train_config {
   float lambda_F;
@@ -649,6 +667,8 @@ typedef struct train_config {
   int64_t total_steps;
   uint64_t seed;
   int32_t encoder_subset;
+  int32_t shard_index;
+  int32_t shard_count;
 } train_config;
 
 typedef struct trainer_ctx trainer_ctx;
@@ -671,7 +691,25 @@ void trainer_destroy(trainer_ctx* ctx);
  */
 mpm_status decoder_train(trainer_ctx* ctx, int n_steps, void* stream);
 
-/* Loss of the last step (mean over the batch) and the step count.  Synchronous. */
+/*
+ * Data-parallel training, one optimisation step in two calls.
+ * trainer_compute_gradients: this shard's minibatch draw, forward and backward
+ * (as decoder_train without the update); copies the gradients of the decoder
+ * parameters (decoder_num_params floats) and of the latent table (n_snap x r)
+ * or, with the encoder, of the encoder parameters, into g_params and g_second
+ * (device buffers of the sizes trainer_gradient_sizes gives), and zeroes the
+ * context's own accumulators.  The caller adds the shards' gradients (an
+ * all-reduce over the shards) and passes the sums to
+ * trainer_apply_gradients, which takes the Adam step of decoder_train with
+ * them (same learning-rate schedule and step count).  Asynchronous on
+ * `stream`.  With one shard, compute + apply is one decoder_train step.
+ */
+mpm_status trainer_gradient_sizes(const trainer_ctx* ctx, int64_t* n_params, int64_t* n_second);
+mpm_status trainer_compute_gradients(trainer_ctx* ctx, float* g_params, float* g_second, void* stream);
+mpm_status trainer_apply_gradients(trainer_ctx* ctx, const float* g_params, const float* g_second, void* stream);
+
+/* Loss of the last step (mean over the whole minibatch; with shards, this shard's part of that
+ * mean) and the step count.  Synchronous. */
 mpm_status trainer_loss(trainer_ctx* ctx, double* loss, int64_t* step, void* stream);
 
 /* Copies the latents (n_snap, r) out (host or device pointer): the table, or the

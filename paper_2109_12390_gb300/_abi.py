@@ -59,7 +59,7 @@ class SnapshotDesc(C.Structure):
 class TrainConfig(C.Structure):
     _fields_ = [("lambda_F", C.c_float), ("lambda_v", C.c_float), ("dt_snap", C.c_float), ("lr0", C.c_float),
                 ("lr1", C.c_float), ("batch", C.c_int32), ("total_steps", C.c_int64), ("seed", C.c_uint64),
-                ("encoder_subset", C.c_int32)]
+                ("encoder_subset", C.c_int32), ("shard_index", C.c_int32), ("shard_count", C.c_int32)]
 
 
 class MpmError(RuntimeError):
@@ -80,6 +80,7 @@ SIGNATURES = [
     ("mpm_step", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("mpm_set_kinematic", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("mpm_step_profiled", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_float), C.c_void_p]),
+    ("mpm_step_timed", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_float), C.c_void_p]),
     ("mpm_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
     ("mpm_debug_bins", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("mpm_num_block_keys", C.c_int64, [C.c_void_p]),
@@ -115,6 +116,9 @@ SIGNATURES = [
                                  C.POINTER(C.c_void_p)]),
     ("trainer_destroy", None, [C.c_void_p]),
     ("decoder_train", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    ("trainer_gradient_sizes", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    ("trainer_compute_gradients", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("trainer_apply_gradients", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("trainer_loss", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_void_p]),
     ("trainer_get_latents", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("trainer_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),

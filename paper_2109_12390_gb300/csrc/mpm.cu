@@ -86,15 +86,6 @@ __device__ __forceinline__ void node_velocity(float4 mp, const int node[D], cons
   grid_node_velocity<D>(mp, node, p.n, p.bc, p.bc_width, p.dt, p.g, v);
 }
 
-// Tile of nodes [b0 - lo_pad, b0 + B + hi_pad)^D, flattened row-major.
-template <int D, int T>
-__device__ __forceinline__ int tile_index(const int rel[D]) {
-  int t = 0;
-#pragma unroll
-  for (int a = 0; a < D; ++a) t = t * T + rel[a];
-  return t;
-}
-
 template <int D>
 __device__ __forceinline__ int64_t grid_index(const int node[D], int inst, const DevParams& p) {
   int64_t g = 0;
@@ -107,20 +98,17 @@ __device__ __forceinline__ void atomic_add_node(float4* addr, float4 val) {
   atomicAdd(addr, val);  // vector red.global (sm_90+)
 }
 
-// Particle-to-grid contribution of one particle into the shared tile (or, if
-// its stencil leaves the tile, straight into the global grid).
+// Particle-to-grid contribution of one particle straight into the global grid (a
+// particle that moved more than one cell out of its work item's block: rare).
 //   MLS:  m_i += w m;  p_i += w (m v + A (x_i - x_p)),  A = m C - dt V0 (4/dx^2) tau
 //   PIC:  m_i += w m;  p_i += w m v - dt V0 tau grad N_i
-template <int D, int TRANSFER, int TP>
+template <int D, int TRANSFER>
 __device__ __forceinline__ void scatter_particle(const float x[D], const float v[D], const float C[D * D],
-                                                 const float tau[D * D], const int tile_lo[D], int inst,
-                                                 float* s_m, float* s_p, float4* grid, uint8_t* touched,
+                                                 const float tau[D * D], int inst, float4* grid, uint8_t* touched,
                                                  const DevParams& p, uint32_t* status) {
-  constexpr int B = Blk<D>::B;
-  constexpr int NT = (D == 2) ? TP * TP : TP * TP * TP;
   int base[D];
   float w[D][3], dw[D][3], fx[D];
-  bool out_of_grid = false, in_tile = true;
+  bool out_of_grid = false;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     base[a] = stencil_base(x[a], p.inv_dx);
@@ -128,8 +116,6 @@ __device__ __forceinline__ void scatter_particle(const float x[D], const float v
     bspline_w(fx[a], w[a]);
     if (TRANSFER == MPM_TRANSFER_PIC) bspline_dw(fx[a], dw[a]);
     out_of_grid |= (base[a] < 0) | (base[a] + 2 > p.n - 1);
-    int r = base[a] - tile_lo[a];
-    in_tile &= (r >= 0) & (r + 2 < TP);
   }
   if (out_of_grid) {
     raise_status(status, STATUS_OUT_OF_GRID);
@@ -196,46 +182,36 @@ __device__ __forceinline__ void scatter_particle(const float x[D], const float v
         mom[a] = wt * p.mass * v[a] - k * f;
       }
     }
-    if (in_tile) {
-      int rel[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) rel[a] = base[a] + off[a] - tile_lo[a];
-      int t = tile_index<D, TP>(rel);
-      atomicAdd(&s_m[t], wt * p.mass);
-#pragma unroll
-      for (int a = 0; a < D; ++a) atomicAdd(&s_p[a * NT + t], mom[a]);
-    } else {
-      int node[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) node[a] = base[a] + off[a];
-      float4 val = make_float4(wt * p.mass, mom[0], D > 1 ? mom[1] : 0.f, D > 2 ? mom[D - 1] : 0.f);
-      atomic_add_node(&grid[grid_index<D>(node, inst, p)], val);
-      uint8_t* f = &touched[key_of_base<D>(node, inst, p)];
-      if (*f == 0) *f = 1;
-    }
-  }
-}
-
-// Flushes a shared P2G tile into the global grid (non-empty nodes only) and
-// flags the grid blocks it wrote.
-template <int D, int TP>
-__device__ __forceinline__ void flush_tile(const float* s_m, const float* s_p, const int tile_lo[D], int inst,
-                                           float4* grid, uint8_t* touched, const DevParams& p) {
-  constexpr int NT = (D == 2) ? TP * TP : TP * TP * TP;
-  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
-    float m = s_m[t];
-    if (m == 0.f) continue;
     int node[D];
-    int r = t;
 #pragma unroll
-    for (int a = D - 1; a >= 0; --a) {
-      node[a] = tile_lo[a] + r % TP;
-      r /= TP;
-    }
-    float4 val = make_float4(m, s_p[t], D > 1 ? s_p[NT + t] : 0.f, D > 2 ? s_p[2 * NT + t] : 0.f);
+    for (int a = 0; a < D; ++a) node[a] = base[a] + off[a];
+    float4 val = make_float4(wt * p.mass, mom[0], D > 1 ? mom[1] : 0.f, D > 2 ? mom[D - 1] : 0.f);
     atomic_add_node(&grid[grid_index<D>(node, inst, p)], val);
     uint8_t* f = &touched[key_of_base<D>(node, inst, p)];
     if (*f == 0) *f = 1;
+  }
+}
+
+// Flags the grid blocks named by a mask of written blocks: bit (d_0 + 1) 3^(D-1) + ... +
+// (d_{D-1} + 1) for the block at offset d in {-1, 0, 1}^D from the item's block (the nodes a work
+// item's particles reach lie in those), one plain store per written block.
+template <int D>
+__device__ __forceinline__ void flag_blocks(unsigned bits, const int b0[D], int inst, uint8_t* touched,
+                                            const DevParams& p) {
+  constexpr int B = Blk<D>::B;
+  const int t = threadIdx.x;
+  if (t < (D == 2 ? 9 : 27) && ((bits >> t) & 1u)) {
+    int bb[D];
+    int r = t;
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      bb[a] = b0[a] / B + (r % 3) - 1;
+      r /= 3;
+    }
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) k = k * p.nb + bb[a];
+    touched[(size_t)inst * p.nblk + k] = 1;
   }
 }
 
@@ -259,26 +235,24 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
                                                         int32_t* counts, uint32_t* status) {
   constexpr int B = Blk<D>::B;
   constexpr int TG = B + 2;  // grid-to-particle tile: nodes [b0, b0 + B + 2)
-  constexpr int TP = B + 4;  // particle-to-grid tile: nodes [b0 - 1, b0 + B + 3)
   constexpr int TC = B + 2;  // particle-to-grid cells (stencil bases) [b0 - 1, b0 + B + 1)
   constexpr int NG = (D == 2) ? TG * TG : TG * TG * TG;
-  constexpr int NT = (D == 2) ? TP * TP : TP * TP * TP;
   constexpr int NC = (D == 2) ? TC * TC : TC * TC * TC;
   constexpr int DD = D * D;
   constexpr int PD = 2 * D + DD;                 // per-particle P2G record
   constexpr int NSLAB = 3;                       // tasks per cell (leading stencil offset)
   __shared__ float4 s_v4[NG];
-  __shared__ float s_m[NT];
-  __shared__ float s_p[D * NT];
   __shared__ int s_cnt[NC];
   __shared__ int s_off[NC + 1];
   __shared__ int s_cells[NC];
   __shared__ int s_nne;
+  __shared__ unsigned s_tmask;   // grid blocks written by the item's flush
   __shared__ float s_rec[kChunk * PD];
 
   const int nw = *n_work;
   const int P = p.P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tmask = 0u;
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
     const int4 item = work[w];  // {key, start, count, -}
     const int key = item.x;
@@ -294,6 +268,20 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
     int tile_lo[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) tile_lo[a] = b0[a] - 1;
+    const int j = item.y + threadIdx.x;
+    const bool active = threadIdx.x < item.z;
+    // the particle's gather (binned order -> state) is issued before the node tile, so that its
+    // two dependent HBM latencies overlap the tile's
+    int s_src = 0, pid = 0;
+    float x[D], F[DD];
+    if (active) {
+      s_src = perm[j];
+#pragma unroll
+      for (int a = 0; a < D; ++a) x[a] = src.base[(size_t)a * P + s_src];
+#pragma unroll
+      for (int i = 0; i < DD; ++i) F[i] = src.base[(size_t)(2 * D + i) * P + s_src];
+      pid = src.id[s_src];
+    }
     // grid-to-particle tile with the grid update of Algorithm 1 applied on load
     if (!FIRST) {
       for (int t = threadIdx.x; t < NG; t += blockDim.x) {
@@ -311,27 +299,16 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
         s_v4[t] = make_float4(v[0], v[1], D > 2 ? v[2] : 0.f, 0.f);
       }
     }
-    for (int t = threadIdx.x; t < NT; t += blockDim.x) {
-      s_m[t] = 0.f;
-#pragma unroll
-      for (int a = 0; a < D; ++a) s_p[a * NT + t] = 0.f;
-    }
     for (int t = threadIdx.x; t < NC; t += blockDim.x) s_cnt[t] = 0;
     __syncthreads();
 
-    const int j = item.y + threadIdx.x;
-    const bool active = threadIdx.x < item.z;
+    if (threadIdx.x == 0) s_tmask = 0u;   // every thread read the previous item's mask before the barrier
     int new_key = -1;
     int lc = -1, rank = 0;
     float rec[PD];
     if (active) {
-      const int s = perm[j];
-      float x[D], v[D], F[DD], C[DD];
-#pragma unroll
-      for (int a = 0; a < D; ++a) x[a] = src.base[(size_t)a * P + s];
-#pragma unroll
-      for (int i = 0; i < DD; ++i) F[i] = src.base[(size_t)(2 * D + i) * P + s];
-      const int pid = src.id[s];
+      const int s = s_src;
+      float v[D], C[DD];
       if (FIRST) {
 #pragma unroll
         for (int a = 0; a < D; ++a) v[a] = src.base[(size_t)(D + a) * P + s];
@@ -511,7 +488,7 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
         raise_status(status, STATUS_OUT_OF_GRID);
       } else if (!in_cells) {
         // moved more than one cell out of the block: scatter straight to the global grid
-        scatter_particle<D, TRANSFER, TP>(x, v, C, tau, tile_lo, inst, s_m, s_p, grid_nxt, touched_nxt, p, status);
+        scatter_particle<D, TRANSFER>(x, v, C, tau, inst, grid_nxt, touched_nxt, p, status);
       } else {
         int cidx = 0;
 #pragma unroll
@@ -591,7 +568,10 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
     __syncthreads();
     // cell-owner accumulation: one task per (non-empty cell, leading stencil
     // offset o0) sums its cell's particles in registers over the 3 (2D) or
-    // 3 x 3 (3D) stencil nodes with that offset, then adds them to the tile
+    // 3 x 3 (3D) stencil nodes with that offset, then adds each node's sums to
+    // the global grid with one vector reduction (native in L2; shared-memory
+    // float atomics are compare-and-swap loops on this GPU)
+    unsigned tbits = 0u;
     const int n_tasks = s_nne * NSLAB;
     for (int task = threadIdx.x; task < n_tasks; task += blockDim.x) {
       const int cell = s_cells[task / NSLAB];
@@ -676,24 +656,29 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
           }
         }
       }
-      // add the task's nodes to the shared tile: tile node = cell + offset (tile starts at b0 - 1)
+      // add the task's nodes to the grid: node = cell + offset (cells start at b0 - 1)
 #pragma unroll
       for (int o1 = 0; o1 < NROW; ++o1)
 #pragma unroll
         for (int kk = 0; kk < 3; ++kk) {
-          int trel[D];
-          trel[0] = crel[0] + o0;
-          if (D == 3) trel[1] = crel[1] + o1;
-          trel[D - 1] = crel[D - 1] + kk;
-          const int t = tile_index<D, TP>(trel);
-          atomicAdd(&s_m[t], am[o1][kk]);
+          if (am[o1][kk] == 0.f) continue;
+          int node[D];
+          node[0] = tile_lo[0] + crel[0] + o0;
+          if (D == 3) node[1] = tile_lo[1] + crel[1] + o1;
+          node[D - 1] = tile_lo[D - 1] + crel[D - 1] + kk;
+          atomic_add_node(&grid_nxt[grid_index<D>(node, inst, p)],
+                          make_float4(am[o1][kk], ap[o1][kk][0], D > 1 ? ap[o1][kk][1] : 0.f,
+                                      D > 2 ? ap[o1][kk][D - 1] : 0.f));
+          int bit = 0;
 #pragma unroll
-          for (int a = 0; a < D; ++a) atomicAdd(&s_p[a * NT + t], ap[o1][kk][a]);
+          for (int a = 0; a < D; ++a) bit = bit * 3 + (node[a] / B - b0[a] / B + 1);
+          tbits |= 1u << bit;
         }
     }
+    tbits = __reduce_or_sync(0xffffffffu, tbits);
+    if (lane == 0 && tbits) atomicOr(&s_tmask, tbits);
     __syncthreads();
-    flush_tile<D, TP>(s_m, s_p, tile_lo, inst, grid_nxt, touched_nxt, p);
-    __syncthreads();
+    flag_blocks<D>(s_tmask, b0, inst, touched_nxt, p);
   }
 }
 
@@ -1386,6 +1371,41 @@ mpm_status mpm_step_profiled(mpm_ctx* c, int n_steps, void* flush_buf, size_t fl
       for (int q = 0; q < 3; ++q) cudaEventElapsedTime(&kernel_ms[4 * k + q], e[q], e[q + 1]);
       cudaEventElapsedTime(&kernel_ms[4 * k + 3], e[0], e[3]);
     }
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (st != MPM_OK) return st;
+  MPM_CUDA_TRY(cudaGetLastError());
+  return MPM_OK;
+}
+
+mpm_status mpm_step_timed(mpm_ctx* c, int n_steps, void* flush_buf, size_t flush_bytes, float* step_ms,
+                          void* stream) {
+  MPM_CHECK_ARG(c && step_ms, "null argument");
+  MPM_CHECK_ARG(c->loaded, "mpm_set_state must be called first");
+  MPM_CHECK_ARG(n_steps >= 0, "n_steps must be >= 0");
+  MPM_CHECK_ARG(flush_bytes == 0 || flush_buf, "flush_buf is null");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<cudaEvent_t> ev((size_t)2 * n_steps, nullptr);
+  mpm_status st = MPM_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) st = set_error(MPM_ECUDA, "cudaEventCreate");
+  for (int k = 0; k < n_steps && st == MPM_OK; ++k) {
+    if (k > 0 && flush_bytes > 0 && cudaMemsetAsync(flush_buf, k & 0xff, flush_bytes, s) != cudaSuccess) {
+      st = set_error(MPM_ECUDA, "flush memset");
+      break;
+    }
+    cudaEventRecord(ev[2 * k], s);
+    st = launch_fused<false>(c, s);
+    if (st != MPM_OK) break;
+    c->cur = 1 - c->cur;
+    st = launch_scan_permute(c, s, /*clear_consumed=*/true);
+    c->g = 1 - c->g;
+    cudaEventRecord(ev[2 * k + 1], s);
+  }
+  if (st == MPM_OK && n_steps > 0) {
+    if (cudaEventSynchronize(ev.back()) != cudaSuccess) st = set_error(MPM_ECUDA, "event sync");
+    for (int k = 0; k < n_steps && st == MPM_OK; ++k) cudaEventElapsedTime(&step_ms[k], ev[2 * k], ev[2 * k + 1]);
   }
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);

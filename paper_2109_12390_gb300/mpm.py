@@ -105,6 +105,14 @@ class MPM:
         _abi.check(_abi.lib().mpm_step_profiled(self._h, int(n_steps), fb, nb, out, _stream(stream)))
         return np.frombuffer(out, np.float32).reshape(n_steps, 4).copy()
 
+    def step_timed(self, n_steps, flush=None, stream=None):
+        """mpm_step_timed: n_steps steps with events at step boundaries only; returns (n_steps,) ms."""
+        out = (C.c_float * max(1, n_steps))()
+        fb = None if flush is None else C.c_void_p(flush.data_ptr())
+        nb = 0 if flush is None else flush.numel() * flush.element_size()
+        _abi.check(_abi.lib().mpm_step_timed(self._h, int(n_steps), fb, nb, out, _stream(stream)))
+        return np.frombuffer(out, np.float32)[:n_steps].copy()
+
     def status(self, clear=True, stream=None):
         w = C.c_uint32()
         _abi.check(_abi.lib().mpm_status_word(self._h, C.byref(w), int(clear), _stream(stream)))

@@ -1,0 +1,197 @@
+"""FP32 parity bounds derived from the measured sensitivity of each quantity (test infrastructure).
+
+The GPU path computes in FP32, the oracle in FP64.  The stated bound is 1e-5, norm-wise relative.
+Some quantities amplify FP32 rounding, and no FP32 computation can meet 1e-5 on them:
+- a difference of nearly equal terms, such as F - R in the stress or the increment of a latent;
+- a least-squares solve with an ill-conditioned Jacobian;
+- a trajectory whose stress waves carry rounding from step to step.
+
+For each such quantity the bound is K times its measured sensitivity, never below 1e-5.  The FP64
+oracle is run again on perturbed inputs:
+- for a single evaluation, every input (latents, positions, velocities, the decoder's biases and
+  scaling) is multiplied by 1 +- u, with u = 2^-24 (one unit in the last place of FP32) and
+  random signs, and the decoder's weights by 1 +- sqrt(n) u, n the layer's fan-in (the
+  backward error of its FP32 dot products, below);
+- for a trajectory, the state is rounded to FP32 after every step, which is the rounding FP32
+  storage alone forces.
+The perturbed run's deviation from the plain oracle is the sensitivity.
+
+K = 10.  The GPU also rounds the result of every operation, not only its inputs.  The
+probabilistic error bound of an n-term FP32 dot product grows like sqrt(n) u (Higham and Mary,
+SIAM J. Sci. Comput. 2019).  With the decoder's hidden width n = 128 that is sqrt(128) ~ 11 units
+of rounding; the 27-term sums of the 3D transfer give sqrt(27) ~ 5.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle.mpm as OM
+
+U32 = 2.0 ** -24
+K = 10.0
+FLOOR = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def bound(sens):
+    """The parity bound for a quantity of measured sensitivity `sens` (1e-5 at least)."""
+    return max(FLOOR, K * float(sens))
+
+
+def f32(a):
+    """The FP32 value of every element, held in FP64 (the inputs the GPU actually uses)."""
+    return np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
+
+
+def perturb(a, rng):
+    """a (1 +- u) elementwise, random signs: one FP32 unit in the last place."""
+    a = np.asarray(a, np.float64)
+    return a * (1.0 + U32 * rng.choice((-1.0, 1.0), size=a.shape))
+
+
+def f32_decoder(p):
+    """The decoder with every parameter and scaling field rounded to FP32 (the GPU's copy)."""
+    q = p.copy()
+    q.W = [f32(w) for w in q.W]
+    q.b = [f32(v) for v in q.b]
+    q.X_min, q.X_range, q.out_shift, q.out_scale = (f32(q.X_min), f32(q.X_range), f32(q.out_shift),
+                                                    f32(q.out_scale))
+    return q
+
+
+def perturb_decoder(p, rng):
+    """The decoder with the backward error of its FP32 evaluation: each layer's weights perturbed
+    by sqrt(n) u with random signs (n its fan-in; the probabilistic backward error of an n-term
+    FP32 dot product accumulated in order, Higham and Mary 2019), biases and scaling by u."""
+    q = p.copy()
+    q.W = [w * (1.0 + np.sqrt(w.shape[1]) * U32 * rng.choice((-1.0, 1.0), size=w.shape)) for w in q.W]
+    q.b = [perturb(v, rng) for v in q.b]
+    q.X_min, q.X_range, q.out_shift, q.out_scale = (perturb(q.X_min, rng), perturb(q.X_range, rng),
+                                                    perturb(q.out_shift, rng), perturb(q.out_scale, rng))
+    return q
+
+
+def sensitivity(fn, args, rng=None, decoder_args=()):
+    """Relative deviation of fn(*args) when every float array argument is perturbed by one FP32
+    ulp (decoder arguments, given by position in decoder_args, have all their parameters
+    perturbed).  Integer arrays (index sets) and scalars are passed unchanged."""
+    rng = np.random.default_rng(12345) if rng is None else rng
+    base = fn(*args)
+    pert = []
+    for i, a in enumerate(args):
+        if i in decoder_args:
+            pert.append(perturb_decoder(a, rng))
+        elif isinstance(a, np.ndarray) and a.dtype.kind == "f":
+            pert.append(perturb(a, rng))
+        else:
+            pert.append(a)
+    return rel(fn(*pert), base), base
+
+
+def fom_fp32_storage_run(sc, steps):
+    """The FP64 oracle run of `steps` steps with the particle state rounded to FP32 before the
+    first step and after every step."""
+    run = sc.copy()
+    for name in ("x", "v", "F", "C"):
+        setattr(run, name, f32(getattr(run, name)))
+    for _ in range(steps):
+        OM.step(run, 1)
+        for name in ("x", "v", "F", "C"):
+            setattr(run, name, f32(getattr(run, name)))
+    return run
+
+
+def c_scale(ref):
+    """C is a velocity gradient: it is measured against max(|C|, |v| / dx), so that rounding-level
+    C (a rigid motion) is not divided by rounding."""
+    return max(np.linalg.norm(ref.C), np.linalg.norm(ref.v) / ref.dx)
+
+
+def fom_errors(x, v, F, Cm, ref):
+    errs = dict(x=rel(x, ref.x), v=rel(v, ref.v), F=rel(F, ref.F))
+    errs["C"] = float(np.linalg.norm(np.asarray(Cm, np.float64) - ref.C) / c_scale(ref))
+    return errs
+
+
+def fom_bounds(sc, ref, steps):
+    """Per-quantity bounds for an N-step full-order trajectory from `sc` whose plain FP64 oracle
+    result is `ref`: the sensitivity is the FP32-storage run's deviation from `ref`."""
+    run = fom_fp32_storage_run(sc, steps)
+    sens = fom_errors(run.x, run.v, run.F, run.C, ref)
+    return {k: bound(s) for k, s in sens.items()}, sens
+
+
+# ----------------------------------------------------------------------------- reduced step
+# The GPU's reduced step consumes FP32 copies of the decoder's parameters, of the reference
+# positions and of the latent state; the oracle is given exactly those values (f32_*), so that
+# the comparison measures the GPU's arithmetic, and the bound its sensitivity.
+
+
+def check_trial_velocity(p, rs, xh, vh, samples, x_all, got, label=""):
+    """v_trial of Algorithm 5 (the oracle's local step on the GPU's own decoded positions x_all
+    and sample set) within the derived bound; returns the oracle's v_trial."""
+    import dataclasses
+
+    import oracle.rom as OR
+    rs32 = dataclasses.replace(rs, X=f32(rs.X))
+
+    def fn(pp, X_, x_, v_, xa_):
+        return OR.local_dynamics(pp, dataclasses.replace(rs32, X=X_), x_, v_, samples, xa_)[0]
+
+    sens, ref = sensitivity(fn, (f32_decoder(p), rs32.X, f32(xh), f32(vh), np.asarray(x_all, np.float64)),
+                            decoder_args=(0,))
+    err = rel(got, ref)
+    print(f"{label} v_trial error {err:.3e} sensitivity {sens:.3e} bound {bound(sens):.3e}")
+    assert err < bound(sens), (label, err, sens)
+    return ref
+
+
+# Every normal-equations solve of the GPU carries a ridge of at least 1e-10 tr(J^T J) / r (the
+# minimum-norm limit for rank-deficient J^T J), on the increment from the previous value; the
+# oracle is given the same problem.
+RIDGE_FLOOR = 1e-10
+
+
+def check_velocity_projection(p, Xs, xh, v_trial, got, label="", ridge=0.0, vhat_n=None):
+    """vhat of the velocity least-squares fit (on the GPU's own trial velocities), as the
+    increment from vhat_n (zero if None) with ridge max(ridge, 1e-10)."""
+    ridge = max(ridge, RIDGE_FLOOR)
+    import oracle.rom as OR
+
+    def fn(pp, X_, x_, v_):
+        return OR.project_velocity(pp, X_, x_, v_, ridge=ridge, vhat_n=vhat_n)
+
+    sens, ref = sensitivity(fn, (f32_decoder(p), f32(Xs), f32(xh), np.asarray(v_trial, np.float64)),
+                            decoder_args=(0,))
+    err = rel(got, ref)
+    print(f"{label} vhat error {err:.3e} sensitivity {sens:.3e} bound {bound(sens):.3e}")
+    assert err < bound(sens), (label, err, sens)
+    return ref
+
+
+def check_gauss_newton_increment(p, Xs, xh, xh_prev, v_trial, dt, got_xh1, iters=3, label="", ridge=0.0):
+    """xhat_{n+1} - xhat_n of Algorithm 6 (Gauss-Newton from 2 xhat_n - xhat_{n-1} towards the
+    trial positions g(X; xhat_n) + dt v_trial, on the GPU's own trial velocities).  The GPU forms
+    the residual as [g(xhat_k) - g(xhat_n)] - dt v_trial (secant rows), never rounding the trial
+    positions themselves, so the perturbed inputs are the decoder, X, xhat_n, v_trial and the
+    initial guess, and the trial positions follow from them in FP64."""
+    import oracle.decoder as OD
+    import oracle.rom as OR
+    dt32 = float(np.float32(dt))
+    init = 2 * np.asarray(xh, np.float64) - np.asarray(xh_prev, np.float64)
+
+    def fn(pp, X_, xh_, vt_, i_):
+        x_trial = OD.decode(pp, X_, xh_) + dt32 * vt_
+        return OR.gauss_newton(pp, X_, x_trial, i_, iters, ridge=max(ridge, RIDGE_FLOOR))[0] - xh_
+
+    sens, ref = sensitivity(fn, (f32_decoder(p), f32(Xs), np.asarray(xh, np.float64),
+                                 np.asarray(v_trial, np.float64), init), decoder_args=(0,))
+    err = rel(np.asarray(got_xh1) - xh, ref)
+    print(f"{label} GN increment error {err:.3e} sensitivity {sens:.3e} bound {bound(sens):.3e}")
+    assert err < bound(sens), (label, err, sens)
+    return ref + xh

@@ -3,7 +3,9 @@
 Tolerance: 2e-2 relative, norm-wise per quantity, for the BF16 square layers
 (FP32 accumulation); the network output is compared without the output shift
 (out_shift would otherwise hide errors of the learned part).  FP32-only paths
-(linear decoder, one hidden layer) are held to 1e-5.
+(linear decoder, one hidden layer, the CUDA-core path) are held to 1e-5.  Second-derivative
+(mixed) rows: in FP32 at 1e-5 away from the ELU'' jump at z = 0; in BF16 against a bound derived
+from the oracle evaluated with the GPU's BF16 operand rounding.
 """
 import numpy as np
 import pytest
@@ -82,15 +84,69 @@ def test_jvp_and_secant_rows():
         assert rel(sec, ref) < TOL_BF16, scale
 
 
-# A second derivative through four BF16 layers: its terms act''(z)(W u)(W t) and act'(z)(W m)
-# partly cancel, so the BF16 rounding of the layer inputs costs more than for first
-# derivatives.  Rounding the same network's square-layer inputs and weights to BF16 in an FP64
-# evaluation gives 6.0e-2 norm-wise for the d = 2 case below; the bound leaves margin for that.
-TOL_MIXED_BF16 = 1e-1
+def _bf16(a):
+    """Round to the nearest BF16 value (ties to even), held in FP64."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("d,n_hidden,tol", [(2, 5, TOL_MIXED_BF16), (3, 5, TOL_MIXED_BF16), (2, 1, 1e-5),
-                                            (3, 1, 1e-5)])
+def _velocity_gradient_bf16_operands(p, X, xh, u):
+    """The oracle's forward-over-forward dv/dX with the operands the tensor-core path rounds to
+    BF16 rounded the same way: the weights of the square hidden layers and every row that enters
+    them (activations, latent and X tangents, mixed tangents).  The first and last layers stay in
+    FP64, as they are FP32 on the GPU."""
+    d, r = p.d, p.r
+    h = np.concatenate([(X - p.X_min) / p.X_range, xh], axis=1)
+    n = len(h)
+    s = np.concatenate([np.zeros((n, d)), np.broadcast_to(u, (n, r))], axis=1)
+    ts = [np.broadcast_to(np.concatenate([np.eye(d)[k] / p.X_range, np.zeros(r)]), (n, d + r)) for k in range(d)]
+    ms = [np.zeros((n, d + r)) for _ in range(d)]
+    L = len(p.W)
+    for l in range(L):
+        W = p.W[l]
+        if 0 < l < L - 1:
+            W = _bf16(W)
+            h, s = _bf16(h), _bf16(s)
+            ts = [_bf16(t) for t in ts]
+            ms = [_bf16(m) for m in ms]
+        z = h @ W.T + p.b[l]
+        zs, zt, zm = s @ W.T, [t @ W.T for t in ts], [m @ W.T for m in ms]
+        if l < L - 1:
+            a1, a2 = OD.act_d1(z, p.activation), OD.act_d2(z, p.activation)
+            h = OD.act(z, p.activation)
+            s = a1 * zs
+            ts = [a1 * q for q in zt]
+            ms = [a2 * zs * q + a1 * mq for q, mq in zip(zt, zm)]
+        else:
+            s, ms = zs, zm
+    return np.stack([m * p.out_scale for m in ms], axis=-1)
+
+
+def _mixed_bf16_bound(p, Xr, xh, uu, G):
+    """Bound of the BF16 mixed rows: a second derivative through four BF16 layers, whose terms
+    act''(z)(W u)(W t) and act'(z)(W m) partly cancel and whose act'' jumps at z = 0, so the BF16
+    rounding of the operands costs far more than for first derivatives.  The sensitivity is the
+    deviation of the oracle evaluated with exactly the GPU's BF16 operand rounding; the GPU's
+    remaining difference is its FP32 accumulation order, so twice that (at least 2e-2) bounds it."""
+    sens = rel(_velocity_gradient_bf16_operands(p, Xr, xh, uu), G)
+    return max(TOL_BF16, 2.0 * sens), sens
+
+
+def _away_from_kink(p, Xr, xh, band):
+    """Points whose every hidden pre-activation z lies outside |z| < band * RMS(z of its layer):
+    ELU'' jumps at z = 0 (1 below, 0 above), so at a point with a pre-activation within rounding
+    of 0 the FP32 and FP64 evaluations may take opposite sides, and both values are correct
+    second derivatives of the one-sided branches.  Mixed rows are compared at the other points."""
+    _, _, rec = OD.forward(p, Xr, xh, keep=True)
+    ok = np.ones(len(Xr), bool)
+    for l in range(len(p.W) - 1):
+        z = rec[l][1]
+        ok &= (np.abs(z) >= band * np.sqrt(np.mean(z * z))).all(axis=1)
+    return ok
+
+
+@pytest.mark.parametrize("d,n_hidden,tol", [(2, 5, None), (3, 5, None), (2, 1, 1e-5), (3, 1, 1e-5)])
 def test_mixed_rows_velocity_gradient(d, n_hidden, tol):
     """Mixed rows d/dX_k of the JVP row against the oracle's forward-over-forward dv/dX:
     5 hidden layers on the tensor cores (BF16), one hidden layer in FP32.  The JVP and
@@ -110,10 +166,18 @@ def test_mixed_rows_velocity_gradient(d, n_hidden, tol):
     uu = u.astype(np.float32).astype(np.float64)[idx]
     v, G = OD.velocity_gradient(p, Xr, xh, uu)
     _, JX, _ = OD.jacobians(p, Xr, xh)
-    tol1 = min(tol, TOL_BF16)
+    tol1 = TOL_BF16 if tol is None else tol
     assert rel(np.stack(out[1:1 + d], -1), JX) < tol1
     assert rel(out[1 + d], v) < tol1
-    assert rel(np.stack(out[2 + d:], -1), G) < tol
+    if tol is None:
+        tol, sens = _mixed_bf16_bound(p, Xr, xh, uu, G)
+        print(f"BF16 mixed rows: error {rel(np.stack(out[2 + d:], -1), G):.3e}, operand-rounding sensitivity "
+              f"{sens:.3e}, bound {tol:.3e}")
+        assert rel(np.stack(out[2 + d:], -1), G) < tol
+    else:
+        ok = _away_from_kink(p, Xr, xh, 1e-5)
+        assert ok.mean() > 0.95, ok.mean()
+        assert rel(np.stack(out[2 + d:], -1)[ok], G[ok]) < tol
 
 
 def test_mixed_rows_of_affine_network_vanish_and_need_partners():
@@ -158,9 +222,11 @@ def test_fp32_cuda_core_path_deep_decoder(d, r, n):
     assert rel(out[0] - 0.5, g - 0.5) < 1e-5
     assert rel(np.stack(out[1:1 + d], -1), JX) < 1e-5
     assert rel(out[1 + d], v) < 1e-5
-    # ELU'' jumps at z = 0 (0 above, 1 below): features whose FP32 and FP64 pre-activations fall on
-    # opposite sides of 0 differ by O(1) there, so the mixed rows are held to 1e-2 norm-wise
-    assert rel(np.stack(out[2 + d:], -1), G) < 1e-2
+    # ELU'' jumps at z = 0: mixed rows are compared at 1e-5 at the points whose pre-activations
+    # are all clear of the kink by far more than FP32 rounding
+    ok = _away_from_kink(p, Xr, xh, 1e-5)
+    assert ok.mean() > 0.95, ok.mean()
+    assert rel(np.stack(out[2 + d:], -1)[ok], G[ok]) < 1e-5
     out2 = dec.eval(Xg, latg, [PRIMAL] + [dec.dxhat(j) for j in range(r)], lat_idx=idxg).cpu().numpy()
     assert rel(np.stack(out2[1:], -1), Jq) < 1e-5
     sec = dec.eval(Xg, latg, [PRIMAL, SECANT], lat_idx=idxg, dirs=ug).cpu().numpy()[1]
@@ -198,7 +264,7 @@ def test_identity_activation_tensor_path_is_weight_product():
     out = dec.eval(Xg, latg, [PRIMAL] + [dec.dxhat(j) for j in range(r)]).cpu().numpy()
     prod = p.W[3] @ p.W[2] @ p.W[1] @ p.W[0]
     Jq = np.stack(out[1:], -1)
-    np.testing.assert_allclose(Jq, np.broadcast_to(0.1 * prod[:, d:], Jq.shape), rtol=3e-2, atol=3e-3)
+    assert rel(Jq, np.broadcast_to(0.1 * prod[:, d:], Jq.shape)) < TOL_BF16
 
 
 def test_reconstruction_size_sampled():

@@ -3,12 +3,16 @@
 * sample set: bit-exact (same SplitMix64 definition on both sides);
 * basis / neighbour sets: bit-exact, the oracle evaluated on the GPU's own decoded
   FP32 positions (a floating-point decision taken in the same precision);
-* v_trial, vhat, xhat increments: 2e-2 relative (BF16 decoder) norm-wise; FP32-only
-  decoders (linear) 1e-5.
+* v_trial, vhat, xhat increments: 2e-2 relative (BF16 decoder) norm-wise; on the FP32 decoder
+  path 1e-5, or, for quantities that amplify FP32 rounding (the stress's F - R, least-squares
+  fits with ill-conditioned latent Jacobians, latent increments far below the latent's size), K
+  times the oracle's measured sensitivity to one FP32 rounding of its inputs
+  (tests/fp32_bounds.py).
 """
 import numpy as np
 import pytest
 
+import fp32_bounds as FB
 import oracle.decoder as OD
 import oracle.mpm as OM
 import oracle.rom as OR
@@ -139,24 +143,20 @@ def test_one_step_projection_fp32_decoder(projection):
     dbg = rom.debug()
     xa = dbg["x_all"].astype(np.float64)
     assert rel(xa, OD.decode(p, sc.x, xh)) < 1e-6
-    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
-    assert rel(dbg["v_trial"], v_trial) < 1e-4
+    FB.check_trial_velocity(p, rs, xh, vh, dbg["samples"], xa, dbg["v_trial"], "fp32 1 layer")
     Xs = sc.x[dbg["samples"]]
     vt = dbg["v_trial"].astype(np.float64)
-    vh_ref = OR.project_velocity(p, Xs, xh, vt)
     xh1, vh1, _, _ = rom.get_state()
-    assert rel(vh1, vh_ref) < 1e-4
+    FB.check_velocity_projection(p, Xs, xh, vt, vh1, "fp32 1 layer", vhat_n=vh)
     if projection:
         np.testing.assert_allclose(xh1, xh + float(np.float32(sc.dt)) * vh1, rtol=1e-12, atol=1e-14)
     else:
-        x_trial_ref = OD.decode(p, Xs, xh) + float(np.float32(sc.dt)) * vt
         # (the oracle's no-decrease flag is not compared: on this FP32-derived target the last
         # iteration sits at the residual's rounding floor, where either outcome is correct)
-        xh_ref, _ = OR.gauss_newton(p, Xs, x_trial_ref, 2 * xh - xp, 3)
-        assert rel(xh1 - xh, xh_ref - xh) < 1e-3
+        FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="fp32 1 layer")
 
 
-@pytest.mark.parametrize("n_hidden,tol", [(1, 1e-4), (5, TOL_BF16)])
+@pytest.mark.parametrize("n_hidden,tol", [(1, None), (5, TOL_BF16)])
 def test_one_step_affine_quadrature_velocity(n_hidden, tol):
     """MLS local step with the decoded affine velocity C = (dv/dX) F^-1 on the quadrature
     points: v_trial against the oracle's, and different from the C = 0 step of Algorithm 5."""
@@ -165,14 +165,17 @@ def test_one_step_affine_quadrature_velocity(n_hidden, tol):
     assert rom.status() & ~ALLOWED_RANDOM == 0
     dbg = rom.debug()
     xa = dbg["x_all"].astype(np.float64)
-    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
-    assert rel(dbg["v_trial"], v_trial) < tol
+    if n_hidden == 1:
+        v_trial = FB.check_trial_velocity(p, rs, xh, vh, dbg["samples"], xa, dbg["v_trial"], "affine")
+    else:
+        v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
+        assert rel(dbg["v_trial"], v_trial) < tol
     rs.affine = "zero"
     v_zero, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
     assert rel(v_zero, v_trial) > 1e-2   # the affine term is not negligible here (3-4 %)
 
 
-@pytest.mark.parametrize("n_hidden,tol", [(1, 1e-4), (5, TOL_BF16)])
+@pytest.mark.parametrize("n_hidden,tol", [(1, None), (5, TOL_BF16)])
 def test_one_step_reference_gradient(n_hidden, tol):
     """f_reference: the stress uses (dg/dX)(xhat_n) [(dg/dX)(xhat_ref)]^-1; v_trial against the
     oracle with the same reference, and different from the uncorrected step."""
@@ -186,12 +189,16 @@ def test_one_step_reference_gradient(n_hidden, tol):
     assert rom.status() & ~ALLOWED_RANDOM == 0
     dbg = rom.debug()
     xa = dbg["x_all"].astype(np.float64)
-    rs.F_ref_inv = OR.reference_inverse(p, sc.x, xref)
-    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
-    assert rel(dbg["v_trial"], v_trial) < tol
+    if n_hidden == 1:
+        rs.F_ref_inv = OR.reference_inverse(FB.f32_decoder(p), FB.f32(sc.x), xref)
+        v_trial = FB.check_trial_velocity(p, rs, xh, vh, dbg["samples"], xa, dbg["v_trial"], "reference")
+    else:
+        rs.F_ref_inv = OR.reference_inverse(p, sc.x, xref)
+        v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
+        assert rel(dbg["v_trial"], v_trial) < tol
     rs.F_ref_inv = None
     v_plain, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
-    assert rel(v_plain, v_trial) > 10 * min(tol, 1e-3)
+    assert rel(v_plain, v_trial) > 10 * min(tol or 1e-4, 1e-3)
 
 
 @pytest.mark.parametrize("projection", [0, 1])
@@ -211,17 +218,17 @@ def test_one_step_fp32_deep_decoder(projection):
     assert rel(xa - p.out_shift, OD.decode(p, sc.x, xh) - p.out_shift) < 1e-5
     basis, neigh = OR.neighbourhood(xa, dbg["samples"], sc.dx, sc.n_grid)
     np.testing.assert_array_equal(dbg["neigh"], neigh)
-    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
-    assert rel(dbg["v_trial"], v_trial) < 1e-4
+    FB.check_trial_velocity(p, rs, xh, vh, dbg["samples"], xa, dbg["v_trial"], "fp32 5 layers")
     Xs = sc.x[dbg["samples"]]
     vt = dbg["v_trial"].astype(np.float64)
-    vh_ref = OR.project_velocity(p, Xs, xh, vt)
     xh1, vh1, _, _ = rom.get_state()
-    assert rel(vh1, vh_ref) < 1e-3
+    FB.check_velocity_projection(p, Xs, xh, vt, vh1, "fp32 5 layers", vhat_n=vh)
+    if not projection:
+        FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="fp32 5 layers")
 
 
-@pytest.mark.parametrize("n_hidden,tol", [(1, 1e-4), (5, 1e-4)])
-def test_one_step_3d(n_hidden, tol):
+@pytest.mark.parametrize("n_hidden", [1, 5])
+def test_one_step_3d(n_hidden):
     """The reduced step in 3D (27-node stencils, 3 x 3 gradients, gravity): sample and neighbour
     sets bit-exact, v_trial and the velocity projection against the FP64 oracle (FP32 decoder)."""
     import torch
@@ -253,11 +260,10 @@ def test_one_step_3d(n_hidden, tol):
     np.testing.assert_array_equal(dbg["neigh"], neigh)
     rs = _rom_scene(sc, k, 13)
     rs.projection = "velocity-only"
-    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
-    assert rel(dbg["v_trial"], v_trial) < tol
-    vh_ref = OR.project_velocity(p, sc.x[dbg["samples"]], xh, dbg["v_trial"].astype(np.float64))
+    FB.check_trial_velocity(p, rs, xh, vh, dbg["samples"], xa, dbg["v_trial"], f"3d {n_hidden} layers")
     _, vh1, _, _ = rom.get_state()
-    assert rel(vh1, vh_ref) < 1e-3
+    FB.check_velocity_projection(p, sc.x[dbg["samples"]], xh, dbg["v_trial"].astype(np.float64), vh1,
+                                 f"3d {n_hidden} layers", vhat_n=vh)
 
 
 def test_fit_initial_condition():
@@ -270,11 +276,16 @@ def test_fit_initial_condition():
     _, _, Jq = OD.jacobians(p, sc.x, xh_true)
     v_true = np.random.default_rng(2).normal(size=p.r)
     V0 = np.einsum("pij,j->pi", Jq, v_true)
+    rom.close()
+    dec.set_precision(True)
+    rom = ROM.from_scene(dec, sc, n_samples=64, seed=7)
     rom.fit_initial(target, V0, iters=30)
     xh0, vh0, xprev, step = rom.get_state()
     assert step == 0
-    assert rel(OD.decode(p, sc.x, xh0) - p.out_shift, target - p.out_shift) < TOL_BF16
-    assert rel(np.einsum("pij,j->pi", Jq, vh0), V0) < 5e-2
+    # the fitted latent reproduces the decoder's own targets to FP32 accuracy
+    assert rel(OD.decode(p, sc.x, xh0) - p.out_shift, target - p.out_shift) < 1e-5
+    # the velocity fit at the GPU's own latent: least squares over all particles
+    FB.check_velocity_projection(p, sc.x, xh0, V0, vh0, "initial fit")
     np.testing.assert_allclose(xprev, xh0 - float(np.float32(sc.dt)) * vh0, rtol=1e-12, atol=1e-15)
 
 
@@ -306,11 +317,12 @@ def test_config4_scale_one_step_parity():
     assert rel(xa - p.out_shift, OD.decode(p, sc.x, xh) - p.out_shift) < 1e-5
     basis, neigh = OR.neighbourhood(xa, dbg["samples"], sc.dx, sc.n_grid)
     np.testing.assert_array_equal(dbg["neigh"], neigh)
-    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], xa)
-    assert rel(dbg["v_trial"], v_trial) < 1e-4
-    vh_ref = OR.project_velocity(p, sc.x[dbg["samples"]], xh, dbg["v_trial"].astype(np.float64))
-    _, vh1, _, _ = rom.get_state()
-    assert rel(vh1, vh_ref) < 1e-3
+    FB.check_trial_velocity(p, rs, xh, vh, dbg["samples"], xa, dbg["v_trial"], "config 4 size")
+    Xs = sc.x[dbg["samples"]]
+    vt = dbg["v_trial"].astype(np.float64)
+    xh1, vh1, _, _ = rom.get_state()
+    FB.check_velocity_projection(p, Xs, xh, vt, vh1, "config 4 size", vhat_n=vh)
+    FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="config 4 size")
 
 
 def test_metric_accumulate():
@@ -378,8 +390,7 @@ def test_samples_cover_every_particle_and_empty_calls():
     np.testing.assert_array_equal(dbg["samples"], np.arange(sc.n_particles))
     assert len(dbg["neigh"]) == 0
     rs.n_samples = sc.n_particles
-    v_trial, _, _, _ = OR.local_dynamics(p, rs, xh, vh, dbg["samples"], dbg["x_all"].astype(np.float64))
-    assert rel(dbg["v_trial"], v_trial) < 1e-4
+    FB.check_trial_velocity(p, rs, xh, vh, dbg["samples"], dbg["x_all"], dbg["v_trial"], "all samples")
     out = rom.decode_points(torch.empty((0, 2), dtype=torch.float32, device="cuda"))
     assert out.shape == (0, 2)
     rom.close()
@@ -417,8 +428,7 @@ def test_kinematic_samples_and_trial_velocities():
         xa = dbg["x_all"].astype(np.float64)
         basis, neigh = OR.neighbourhood(xa, dbg["samples"], sc.dx, sc.n_grid)
         np.testing.assert_array_equal(dbg["neigh"], neigh)
-        v_trial, _, _, _ = OR.local_dynamics(p, rs, xh_n, vh_n, dbg["samples"], xa)
-        assert rel(dbg["v_trial"], v_trial) < 1e-4
+        FB.check_trial_velocity(p, rs, xh_n, vh_n, dbg["samples"], xa, dbg["v_trial"], f"kinematic step {step}")
     rom.close()
 
 
@@ -479,4 +489,57 @@ def test_rejected_kinematic_call_leaves_the_stepping_context_intact():
     assert a[3] == b[3] == 5
     for rom in roms:
         rom.close()
+    dec.close()
+
+
+def test_reduced_trajectory_20_steps_deep_elu_decoder():
+    """The reduced model at the benchmark's size and launch configuration (4096 particles, 256
+    samples, r = 16, 5 hidden ELU layers on the FP32 decoder path, 3 Gauss-Newton iterations with
+    backtracking) for 20 steps against the FP64 oracle's own trajectory from the same state.  After
+    every step: the latent displacement xhat_n - xhat_0, the latent velocity and the decoded
+    positions of all particles.  Bounds: 1e-5, or K times the deviation of the oracle's trajectory
+    when the decoder and the initial latents are perturbed by one FP32 ulp."""
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.rom import ROM
+    sc = S.block_2d(side=64, dt=5e-5, origin=(0.375, 0.3), E=200.0)
+    X = sc.x
+    r, k, seed = 16, 256, 31
+    p = FB.f32_decoder(S.near_identity_decoder(seed, 2, r, 5, X_min=X.min(0), X_range=X.max(0) - X.min(0),
+                                               eps=1e-3))
+    dec = Decoder.from_params(p)
+    dec.set_precision(True)
+    rom = ROM.from_scene(dec, sc, n_samples=k, seed=seed)
+    rng = np.random.default_rng(seed)
+    xh0 = FB.f32(0.2 * rng.normal(size=r))
+    vh0 = FB.f32(0.5 * rng.normal(size=r))
+    xp0 = xh0 - float(np.float32(sc.dt)) * vh0
+    rom.set_state(xh0, vh0, xp0, 0)
+    rs = _rom_scene(sc, k, seed)
+    rs.X = FB.f32(rs.X)
+    rs.dt = float(np.float32(sc.dt))    # the GPU's step in FP32
+    rs.ridge = FB.RIDGE_FLOOR           # the floor every GPU normal-equations solve carries
+    st = OR.RomState(xhat=xh0.copy(), vhat=vh0.copy(), xhat_prev=xp0.copy())
+    prng = np.random.default_rng(seed + 1)
+    p_p = FB.perturb_decoder(p, prng)
+    xh0_p = FB.perturb(xh0, prng)
+    st_p = OR.RomState(xhat=xh0_p.copy(), vhat=FB.perturb(vh0, prng), xhat_prev=xp0.copy())
+    worst = {}
+    for n in range(1, 21):
+        st = OR.rom_step(p, rs, st)
+        st_p = OR.rom_step(p_p, rs, st_p)
+        rom.step(1)
+        xh, vh, _, step = rom.get_state()
+        assert step == n and rom.status() == 0
+        x_gpu = rom.decode_all().cpu().numpy()
+        x_ref = OD.decode(p, rs.X, st.xhat)
+        checks = (("latent displacement", xh - xh0, st.xhat - xh0, st_p.xhat - xh0_p),
+                  ("latent velocity", vh, st.vhat, st_p.vhat),
+                  ("decoded positions", x_gpu - p.out_shift, x_ref - p.out_shift,
+                   OD.decode(p_p, rs.X, st_p.xhat) - p.out_shift))
+        for name, got, ref, pert in checks:
+            err, sens = rel(got, ref), FB.rel(pert, ref)
+            worst[name] = max(worst.get(name, 0.0), err / FB.bound(sens))
+            assert err < FB.bound(sens), (n, name, err, sens)
+    print("largest error / bound over 20 steps:", worst)
+    rom.close()
     dec.close()
