@@ -76,13 +76,14 @@ struct Batch {
 
 // ------------------------------------------------------------- sampler
 __global__ void train_sample(Store st, Batch b, const float* latents, float dt_snap, uint64_t seed,
-                             const int64_t* step, double* loss) {
+                             const int64_t* step, double* loss, int64_t i_offset) {
   const int d = st.d, r = st.r;
   const int64_t total = st.snap_base[st.n_snap];
   const uint64_t s0 = tr_splitmix(seed, (uint64_t)*step);
   if (blockIdx.x == 0 && threadIdx.x == 0) *loss = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b.B; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t h = tr_splitmix(s0, (uint64_t)i);
+    // draw i_offset + i of the step's minibatch (a data-parallel shard holds a contiguous range)
+    const uint64_t h = tr_splitmix(s0, (uint64_t)(i + i_offset));
     const int64_t g = (int64_t)(h % (uint64_t)total);
     // snapshot containing pair g: largest s with snap_base[s] <= g
     int lo = 0, hi = st.n_snap - 1;
@@ -116,6 +117,7 @@ __global__ void train_sample(Store st, Batch b, const float* latents, float dt_s
 
 // ------------------------------------------------------------- backward
 struct BwdArgs {
+  float n_norm;   // points of the whole minibatch (over all data-parallel shards)
   int d, r, n_hidden, n_tc, act, R, Pt;
   int64_t n, rows_total;
   const float* W0;      // (W, d + r)
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
           w = a.lamv;
         }
         if (h == 0) my_loss += (double)w * e * e;
-        ybar[i] = 2.f * w * e * scale[i] / (float)a.n;
+        ybar[i] = 2.f * w * e * scale[i] / a.n_norm;
       }
     }
     if (h == 0)
@@ -605,6 +607,8 @@ struct trainer_ctx {
   train_config cfg{};
   int d = 0, r = 0, R = 0, Pt = 0, n_sm = 0;
   int64_t B = 0, n_tiles = 0, rows_total = 0, n_snap = 0;
+  int64_t i_offset = 0;   // first draw of this shard in the step's minibatch
+  float n_norm = 0.f;     // points of the whole minibatch (batch x shards)
   Store st{};
   Batch b{};
   // device buffers
@@ -758,6 +762,8 @@ __global__ void scale_finish(int pass, int d, int n_part, int64_t nx, const doub
 
 namespace {
 
+mpm_status train_launch_update(trainer_ctx* c, cudaStream_t s);
+
 mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
   mpm_decoder* dec = c->dec;
   const int d = c->d, r = c->r;
@@ -767,7 +773,8 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
     mpm_status se = enc_forward(c->E, c->enc_p, c->U, c->n_snap, c->latents, c->n_sm, s);
     if (se != MPM_OK) return se;
   }
-  train_sample<<<blocks, 256, 0, s>>>(c->st, c->b, c->latents, c->cfg.dt_snap, c->cfg.seed, c->step, c->loss);
+  train_sample<<<blocks, 256, 0, s>>>(c->st, c->b, c->latents, c->cfg.dt_snap, c->cfg.seed, c->step, c->loss,
+                                      c->i_offset);
   MPM_CUDA_TRY(cudaGetLastError());
   int kinds[8];
   kinds[0] = 0;
@@ -785,6 +792,7 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
   a.R = c->R;
   a.Pt = c->Pt;
   a.n = c->B;
+  a.n_norm = c->n_norm;
   a.rows_total = c->rows_total;
   const int L = (int)dec->w_off.size();
   a.W0 = dec->params + dec->w_off[0];
@@ -831,8 +839,17 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
     st = enc_backward(c->E, c->enc_p, c->U, c->n_snap, c->g_lat, c->enc_g, c->n_sm, s);
     if (st != MPM_OK) return st;
   }
-  if (update) {
-    // Adam on the decoder and on the latent table or the encoder
+  if (update) return train_launch_update(c, s);
+  return MPM_OK;
+}
+
+// Adam on the decoder and on the latent table or the encoder (the gradients are consumed and
+// zeroed), re-pack of the weight images, step count.
+mpm_status train_launch_update(trainer_ctx* c, cudaStream_t s) {
+  mpm_decoder* dec = c->dec;
+  const int r = c->r;
+  mpm_status st = MPM_OK;
+  {
     const int64_t n0 = dec->n_params, n1 = c->enc ? (int64_t)c->E.n_params : c->n_snap * r;
     float* p1 = c->enc ? c->enc_p : c->latents;
     float* g1 = c->enc ? c->enc_g : c->g_lat;
@@ -937,6 +954,8 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   MPM_CHECK_ARG(sd->n_snap >= 1 && sd->snap_inst && sd->snap_next && sd->x && sd->v && sd->F, "snapshots");
   MPM_CHECK_ARG(cfg->batch >= 1 && cfg->dt_snap > 0 && cfg->lr0 > 0 && cfg->lr1 > 0, "batch, dt_snap, lr");
   MPM_CHECK_ARG(dec->r <= 32, "latent dimension <= 32");
+  MPM_CHECK_ARG(cfg->shard_count >= 0 && cfg->shard_index >= 0 && cfg->shard_index < std::max(1, cfg->shard_count),
+                "shard_index must be in [0, shard_count)");
   auto* c = new trainer_ctx();
   c->dec = dec;
   c->cfg = *cfg;
@@ -945,6 +964,8 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   c->R = c->d + 2;
   c->Pt = 128 / c->R;
   c->B = cfg->batch;
+  c->i_offset = (int64_t)cfg->shard_index * cfg->batch;
+  c->n_norm = (float)((double)cfg->batch * std::max(1, cfg->shard_count));
   c->n_tiles = (c->B + c->Pt - 1) / c->Pt;
   c->rows_total = c->n_tiles * 128;
   c->n_snap = sd->n_snap;
@@ -1124,8 +1145,40 @@ mpm_status trainer_loss(trainer_ctx* c, double* loss, int64_t* step, void* strea
   MPM_CUDA_TRY(cudaMemcpyAsync(&h, c->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (step) MPM_CUDA_TRY(cudaMemcpyAsync(step, c->step, sizeof(int64_t), cudaMemcpyDefault, s));
   MPM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (loss) *loss = h / (double)c->B;
+  if (loss) *loss = h / (double)c->n_norm;
   return MPM_OK;
+}
+
+mpm_status trainer_gradient_sizes(const trainer_ctx* c, int64_t* n_params, int64_t* n_second) {
+  MPM_CHECK_ARG(c, "null context");
+  if (n_params) *n_params = c->dec->n_params;
+  if (n_second) *n_second = c->enc ? (int64_t)c->E.n_params : c->n_snap * c->r;
+  return MPM_OK;
+}
+
+mpm_status trainer_compute_gradients(trainer_ctx* c, float* g_params, float* g_second, void* stream) {
+  MPM_CHECK_ARG(c && g_params && g_second, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  mpm_status st = train_launch_step(c, s, 0);
+  if (st != MPM_OK) return st;
+  const size_t n1 = c->enc ? (size_t)c->E.n_params : (size_t)c->n_snap * c->r;
+  float* g1 = c->enc ? c->enc_g : c->g_lat;
+  MPM_CUDA_TRY(cudaMemcpyAsync(g_params, c->gparams, sizeof(float) * c->dec->n_params, cudaMemcpyDeviceToDevice, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(g_second, g1, sizeof(float) * n1, cudaMemcpyDeviceToDevice, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->gparams, 0, sizeof(float) * c->dec->n_params, s));
+  MPM_CUDA_TRY(cudaMemsetAsync(c->g_lat, 0, sizeof(float) * c->n_snap * c->r, s));
+  if (c->enc) MPM_CUDA_TRY(cudaMemsetAsync(c->enc_g, 0, sizeof(float) * c->E.n_params, s));
+  return MPM_OK;
+}
+
+mpm_status trainer_apply_gradients(trainer_ctx* c, const float* g_params, const float* g_second, void* stream) {
+  MPM_CHECK_ARG(c && g_params && g_second, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n1 = c->enc ? (size_t)c->E.n_params : (size_t)c->n_snap * c->r;
+  float* g1 = c->enc ? c->enc_g : c->g_lat;
+  MPM_CUDA_TRY(cudaMemcpyAsync(c->gparams, g_params, sizeof(float) * c->dec->n_params, cudaMemcpyDeviceToDevice, s));
+  MPM_CUDA_TRY(cudaMemcpyAsync(g1, g_second, sizeof(float) * n1, cudaMemcpyDeviceToDevice, s));
+  return train_launch_update(c, s);
 }
 
 mpm_status trainer_get_latents(trainer_ctx* c, float* latents, void* stream) {
@@ -1165,7 +1218,7 @@ mpm_status trainer_gradients(trainer_ctx* c, float* g_params, float* g_latents, 
   MPM_CUDA_TRY(cudaMemsetAsync(c->g_lat, 0, sizeof(float) * c->n_snap * c->r, s));
   if (c->enc) MPM_CUDA_TRY(cudaMemsetAsync(c->enc_g, 0, sizeof(float) * c->E.n_params, s));
   MPM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (loss) *loss = h / (double)c->B;
+  if (loss) *loss = h / (double)c->n_norm;
   return MPM_OK;
 }
 

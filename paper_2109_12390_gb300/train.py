@@ -59,13 +59,17 @@ def snapshot_desc(snaps):
 
 class Trainer:
     def __init__(self, decoder, snaps, *, lambda_F=100.0, lambda_v=0.01, dt_snap, lr0=1e-3, lr1=1e-6,
-                 batch=65536, total_steps=10000, seed=0, latents0=None, encoder_subset=0):
+                 batch=65536, total_steps=10000, seed=0, latents0=None, encoder_subset=0, shard_index=0,
+                 shard_count=1):
+        """batch: this context's points per step; with shard_count > 1 it is one data-parallel shard
+        (draws shard_index * batch ... of a minibatch of shard_count * batch points)."""
         L = _abi.lib()
         self.decoder = decoder
         self.snaps = snaps
         self._keep = [snaps["inst_offsets"], snaps["snap_inst"], snaps["snap_next"]]
         sd = snapshot_desc(snaps)
-        cfg = _abi.TrainConfig(lambda_F, lambda_v, dt_snap, lr0, lr1, batch, total_steps, seed, encoder_subset)
+        cfg = _abi.TrainConfig(lambda_F, lambda_v, dt_snap, lr0, lr1, batch, total_steps, seed, encoder_subset,
+                               int(shard_index), int(shard_count))
         self.cfg = cfg
         lat = None if latents0 is None else np.ascontiguousarray(latents0, np.float32)
         h = C.c_void_p()
@@ -88,6 +92,24 @@ class Trainer:
 
     def step(self, n_steps=1, stream=None):
         _abi.check(_abi.lib().decoder_train(self._h, int(n_steps), _stream(stream)))
+
+    def gradient_buffers(self):
+        """Device tensors sized for this trainer's gradients: (decoder parameters, latent table or
+        encoder parameters)."""
+        n0, n1 = C.c_int64(), C.c_int64()
+        _abi.check(_abi.lib().trainer_gradient_sizes(self._h, C.byref(n0), C.byref(n1)))
+        return (torch.empty(n0.value, dtype=torch.float32, device="cuda"),
+                torch.empty(n1.value, dtype=torch.float32, device="cuda"))
+
+    def compute_gradients(self, g_params, g_second, stream=None):
+        """This shard's forward and backward of the next step: gradients into the two tensors."""
+        assert g_params.is_cuda and g_second.is_cuda and g_params.dtype == torch.float32
+        _abi.check(_abi.lib().trainer_compute_gradients(self._h, _vp(g_params), _vp(g_second), _stream(stream)))
+
+    def apply_gradients(self, g_params, g_second, stream=None):
+        """The Adam step with the given (summed over the shards) gradients."""
+        assert g_params.is_cuda and g_second.is_cuda and g_params.dtype == torch.float32
+        _abi.check(_abi.lib().trainer_apply_gradients(self._h, _vp(g_params), _vp(g_second), _stream(stream)))
 
     def loss(self, stream=None):
         l = C.c_double()
