@@ -55,10 +55,11 @@ PRE_ROLL = 600
 # the working precision); the FP64 correction is reported as a variant
 HEADLINE_POLAR_EFT = 1
 # DRAM bytes (read + write) of one launch of the fused step kernel on this workload, from one ncu
-# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum).  It is below the
-# algorithmic traffic: the written state is still in L2 when the kernel ends, and in that capture
-# part of the state reads were served by L2 as well
-FUSED_DRAM_BYTES_NCU = 16_779_776
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum; first timed step
+# after the pre-roll).  Reads: x, F, particle id and binning permutation (56 B per particle) and
+# the node tiles; v and C are not read (G2P recomputes them).  The written state is still in the
+# write-back L2 when the kernel ends.
+FUSED_DRAM_BYTES_NCU = 16_754_432 + 618_496
 
 
 def _dist():
