@@ -568,6 +568,26 @@ mpm_status rom_set_kinematic(rom_ctx* ctx, const int32_t* group, int32_t n_group
 mpm_status rom_decode_all(rom_ctx* ctx, float* x_out, void* stream);
 
 /*
+ * Batched serving: n reduced-order contexts (each with its own scene, sample
+ * count, latent dimension and decoder) stepped by one CUDA graph launch.
+ * rom_batch_create captures one step of every context and makes the captures
+ * independent child graphs of one graph; rom_batch_step launches it n_steps
+ * times on `stream`, each launch advancing every context by one step exactly
+ * as rom_step would (the branches run concurrently on the GPU).  The contexts
+ * stay owned by the caller and must outlive the batch; each may appear once.
+ * State calls (rom_set_state, rom_get_state, rom_decode_*) act on the members
+ * as usual between launches.  Calls that change a member's step
+ * (rom_set_kinematic, rom_set_reference, rom_fit_initial with the reference
+ * gradient) make rom_batch_step return MPM_EINVAL until the batch is rebuilt.
+ * A member stepped on its own while a batch launch runs races with it.  Errors:
+ * MPM_EINVAL, MPM_ECUDA.
+ */
+typedef struct rom_batch rom_batch;
+mpm_status rom_batch_create(rom_ctx* const* ctxs, int32_t n, rom_batch** out);
+mpm_status rom_batch_step(rom_batch* batch, int n_steps, void* stream);
+void rom_batch_destroy(rom_batch* batch);
+
+/*
  * g(X; xhat_n) at n reference positions X (n, dim) that need not be particles of
  * the context: the decoder is defined on the whole reference domain, so the
  * reduced state can be rendered at any resolution (the zero-shot

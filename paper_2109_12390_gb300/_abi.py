@@ -109,6 +109,9 @@ SIGNATURES = [
     ("rom_debug_quadrature", C.c_int, [C.c_void_p, C.POINTER(C.c_int32)] + [C.c_void_p] * 4 + [C.c_void_p]),
     ("rom_decode_all", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("rom_set_kinematic", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
+    ("rom_batch_create", C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    ("rom_batch_step", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    ("rom_batch_destroy", None, [C.c_void_p]),
     ("rom_decode_points", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("metric_accumulate", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("decoder_fit_scaling", C.c_int, [C.c_void_p, C.POINTER(SnapshotDesc), C.c_void_p]),

@@ -1474,6 +1474,17 @@ struct rom_ctx {
   // set while rom_set_kinematic replaces buffers; still set if it failed half way, after which
   // rom_step refuses to run (the step would read buffers that are gone)
   bool reconfig_failed = false;
+  // incremented whenever the step's kernel arguments change (its captured graph is dropped); a
+  // batch built from this context refuses to run once it differs from the value it recorded
+  uint64_t generation = 0;
+};
+
+// Many reduced-order contexts stepped by one graph launch: each context's step graph is a child
+// graph of one parent graph, all children independent (parallel branches).
+struct rom_batch {
+  std::vector<rom_ctx*> ctx;
+  std::vector<uint64_t> gen;
+  cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -1943,6 +1954,73 @@ mpm_status rom_get_state(rom_ctx* c, double* xhat, double* vhat, double* xhat_pr
   return MPM_OK;
 }
 
+// Captures one step of context c (on its private stream) into a graph.
+static mpm_status rom_capture_step(rom_ctx* c, cudaGraph_t* out) {
+  cudaGraph_t g = nullptr;
+  MPM_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  mpm_status st = rom_launch_step(c, c->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (st != MPM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return set_error(MPM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  *out = g;
+  return MPM_OK;
+}
+
+mpm_status rom_batch_create(rom_ctx* const* ctxs, int32_t n, rom_batch** out) {
+  MPM_CHECK_ARG(ctxs && out && n >= 1, "null argument or n < 1");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    MPM_CHECK_ARG(ctxs[i], "null context in the batch");
+    MPM_CHECK_ARG(!ctxs[i]->reconfig_failed, "a failed rom_set_kinematic left a context without its buffers");
+    for (int j = 0; j < i; ++j)
+      MPM_CHECK_ARG(ctxs[j] != ctxs[i], "a context appears twice in the batch (its steps would race)");
+  }
+  cudaGraph_t parent = nullptr;
+  MPM_CUDA_TRY(cudaGraphCreate(&parent, 0));
+  mpm_status st = MPM_OK;
+  for (int i = 0; i < n && st == MPM_OK; ++i) {
+    cudaGraph_t g = nullptr;
+    st = rom_capture_step(ctxs[i], &g);
+    if (st != MPM_OK) break;
+    cudaGraphNode_t node;
+    const cudaError_t e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, g);   // clones g
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) st = set_error(MPM_ECUDA, std::string("child graph: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (st == MPM_OK) {
+    const cudaError_t e = cudaGraphInstantiate(&exec, parent, 0);
+    if (e != cudaSuccess) st = set_error(MPM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  cudaGraphDestroy(parent);
+  if (st != MPM_OK) return st;
+  auto* b = new rom_batch();
+  b->ctx.assign(ctxs, ctxs + n);
+  for (int i = 0; i < n; ++i) b->gen.push_back(ctxs[i]->generation);
+  b->exec = exec;
+  *out = b;
+  return MPM_OK;
+}
+
+mpm_status rom_batch_step(rom_batch* b, int n_steps, void* stream) {
+  MPM_CHECK_ARG(b, "null batch");
+  MPM_CHECK_ARG(n_steps >= 0, "n_steps >= 0");
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    MPM_CHECK_ARG(b->ctx[i]->generation == b->gen[i] && !b->ctx[i]->reconfig_failed,
+                  "a context of the batch was reconfigured after the batch was built: rebuild the batch");
+  for (int k = 0; k < n_steps; ++k) MPM_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  return MPM_OK;
+}
+
+void rom_batch_destroy(rom_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  delete b;
+}
+
 mpm_status rom_step(rom_ctx* c, int n_steps, void* stream) {
   MPM_CHECK_ARG(c, "null context");
   MPM_CHECK_ARG(n_steps >= 0, "n_steps >= 0");
@@ -2082,6 +2160,7 @@ mpm_status rom_set_kinematic(rom_ctx* c, const int32_t* group, int32_t n_groups,
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
+  ++c->generation;
   c->reconfig_failed = true;
   cudaFree(c->kin_group);
   cudaFree(c->kin_vel);
@@ -2178,6 +2257,7 @@ mpm_status rom_set_reference(rom_ctx* c, const double* xhat_ref, void* stream) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
+  ++c->generation;
   return MPM_OK;
 }
 

@@ -137,3 +137,34 @@ def rom_error(decoder, scene, fom_xs, *, n_samples=256, seed=4, gn_iters=3, proj
     rom.close()
     return RomRun(error_percent=100.0 * float(np.sqrt(num / den)), rom_steps_per_s=rate, fom_steps_per_s=float("nan"),
                   status=status, steps=steps, error_percent_at=at)
+
+
+def build_serving_batch(decoders, roms, concurrency):
+    """Sets the decoders' expected concurrency (the FP32 tiling of their calls) and captures the
+    batch of reduced-order contexts (one graph launch per step for all of them)."""
+    from .rom import RomBatch
+    for dec in decoders:
+        dec.set_concurrency(int(concurrency))
+    return RomBatch(roms)
+
+
+def autotune_serving(decoders, roms, candidates=(1, 8, 32, 128, 512), trial_steps=4):
+    """Decoder tiling for batched serving, chosen by measurement: for each candidate concurrency k
+    (how many decoder calls are expected to run at once, which sets how many SMs one call's tiles
+    spread over), capture the batch and time `trial_steps` batch steps on the device.  Returns
+    (best k, {k: ms per batch step}).  The trial steps advance the contexts."""
+    times = {}
+    for k in candidates:
+        if k > max(1, len(roms)) and k != candidates[0]:
+            continue
+        batch = build_serving_batch(decoders, roms, k)
+        batch.step(1)                       # first launch: graph upload
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        batch.step(trial_steps)
+        b.record()
+        torch.cuda.synchronize()
+        times[int(k)] = a.elapsed_time(b) / trial_steps
+        batch.close()
+    best = min(times, key=times.get)
+    return best, times

@@ -153,3 +153,29 @@ class ROM:
 def metric_accumulate(a, b, acc, stream=None):
     """acc (2,) float64 CUDA tensor += [sum (a - b)^2, sum b^2] (Section 5 error metric)."""
     _abi.check(_abi.lib().metric_accumulate(_ptr(a), _ptr(b), a.numel(), _p64(acc), _stream(stream)))
+
+
+class RomBatch:
+    """Many reduced-order contexts stepped by one CUDA graph launch (rom_batch_create / step).
+    The ROM objects must stay alive while the batch exists."""
+
+    def __init__(self, roms):
+        self.roms = list(roms)
+        arr = (C.c_void_p * len(self.roms))(*[r._h.value for r in self.roms])
+        h = C.c_void_p()
+        _abi.check(_abi.lib().rom_batch_create(arr, len(self.roms), C.byref(h)))
+        self._h = h
+
+    def step(self, n_steps=1, stream=None):
+        _abi.check(_abi.lib().rom_batch_step(self._h, int(n_steps), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.lib().rom_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -577,3 +577,56 @@ def test_normal_equations_solve_matches_fp64_on_the_gpu_jacobian():
     assert err < max(2.0 ** -40 * kappa, 1e-12)
     rom.close()
     dec.close()
+
+
+def test_batch_of_contexts_steps_as_each_context_alone():
+    """Batched serving: three reduced-order contexts with different scenes, sample counts and latent
+    sizes (two decoders) stepped by one graph launch per step end where twin contexts stepped one
+    by one end.  The float atomics of the local transfer make two runs of one context differ; a
+    third group measures that run-to-run difference, and the batch is held to 1e-5 or 10 times
+    it.  Once a member is reconfigured, the batch refuses to step until it is rebuilt."""
+    from paper_2109_12390_gb300 import _abi
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.rom import ROM, RomBatch
+    scenes = [S.block_2d(side=24, dt=5e-5, origin=(0.3, 0.4), E=20.0),
+              S.block_2d(side=32, dt=5e-5, origin=(0.45, 0.3), E=40.0),
+              S.block_2d(side=16, dt=5e-5, origin=(0.5, 0.5), E=30.0)]
+    decs = {}
+    for r, nh in ((4, 1), (6, 5)):
+        X = scenes[0].x
+        p = S.near_identity_decoder(40 + r, 2, r, nh, X_min=X.min(0) - 0.2, X_range=X.max(0) - X.min(0) + 0.4,
+                                    eps=3e-3)
+        decs[r] = Decoder.from_params(p)
+        decs[r].set_precision(True)
+    plan = [(scenes[0], 4, 24), (scenes[1], 6, 48), (scenes[2], 4, 64)]
+    rng = np.random.default_rng(12)
+    members, twins, twins2, states = [], [], [], []
+    for i, (sc, r, k) in enumerate(plan):
+        xh, vh = 0.2 * rng.normal(size=r), rng.normal(size=r)
+        states.append((xh, vh, xh - sc.dt * vh))
+        for group in (members, twins, twins2):
+            rom = ROM.from_scene(decs[r], sc, n_samples=k, seed=20 + i, projection=i % 2)
+            rom.set_state(*states[-1], 0)
+            group.append(rom)
+    batch = RomBatch(members)
+    batch.step(3)
+    for rom in twins + twins2:
+        rom.step(3)
+    for a, b, c in zip(members, twins, twins2):
+        sa, sb, sc_ = a.get_state(), b.get_state(), c.get_state()
+        assert sa[3] == sb[3] == 3
+        for q in (0, 1):
+            noise = rel(sc_[q], sb[q])
+            assert rel(sa[q], sb[q]) < max(1e-5, 10 * noise), (q, rel(sa[q], sb[q]), noise)
+        assert a.status() == 0
+    members[1].set_kinematic(None, None)      # changes the member's step: the batch is stale
+    with pytest.raises(_abi.MpmError) as e:
+        batch.step(1)
+    assert e.value.status == _abi.MPM_EINVAL
+    batch.close()
+    batch = RomBatch(members)                 # rebuilt: steps again
+    batch.step(1)
+    assert members[1].get_state()[3] == 4
+    batch.close()
+    for rom in members + twins + twins2:
+        rom.close()
