@@ -215,6 +215,15 @@ __device__ __forceinline__ void flag_blocks(unsigned bits, const int b0[D], int 
   }
 }
 
+// Programmatic dependent launch: the step's kernels are launched so that the next one may be
+// scheduled while this one drains.  Every step kernel first waits until the previous grid has
+// completed and its writes are visible (a no-op when launched without the attribute), then lets
+// its own dependents be scheduled.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void count_key_aggregated(int key, int32_t* counts) {
   unsigned active = __activemask();
   unsigned peers = __match_any_sync(active, key);
@@ -249,6 +258,7 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
   __shared__ unsigned s_tmask;   // grid blocks written by the item's flush
   __shared__ float s_rec[kChunk * PD];
 
+  pdl_enter();
   const int nw = *n_work;
   const int P = p.P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -705,6 +715,7 @@ __global__ void __launch_bounds__(kScanTile) mpm_scan(int n_keys, int P, int32_t
                                                        unsigned long long* tile_state, uint32_t* status) {
   __shared__ int s_a[32], s_b[32];
   __shared__ long long s_prefix[2];
+  pdl_enter();
   const int tile = blockIdx.x;
   const int k = tile * kScanTile + threadIdx.x;
   const int c = k < n_keys ? counts[k] : 0;
@@ -807,6 +818,7 @@ __global__ void mpm_permute(DevParams p, const int32_t* __restrict__ key, const 
   constexpr int B = Blk<D>::B;
   constexpr int BN = (D == 2) ? B * B : B * B * B;
   const int stride = gridDim.x * blockDim.x;
+  pdl_enter();
   // the scan that produced `offsets` has finished: reset its look-back words
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_tiles; q += stride) tile_state[q] = 0ull;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i - (int)threadIdx.x < p.P; i += stride) {
@@ -999,6 +1011,22 @@ mpm_status dalloc(T** p, size_t count) {
     if (_s != MPM_OK) return _s; \
   } while (0)
 
+// Launches a step kernel with programmatic stream serialization (see pdl_enter).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, (KArgs)args...);
+}
+
 template <int D, int MAT, int TR, bool FIRST, int POLAR>
 mpm_status launch_fused_t(mpm_ctx* c, cudaStream_t s) {
   StateView src{c->state[c->cur], c->id[c->cur]};
@@ -1006,9 +1034,9 @@ mpm_status launch_fused_t(mpm_ctx* c, cudaStream_t s) {
   float4* gcur = c->grid[c->g];
   float4* gnxt = FIRST ? c->grid[c->g] : c->grid[1 - c->g];
   uint8_t* tn = FIRST ? c->touched[c->g] : c->touched[1 - c->g];
-  mpm_g2p2g<D, MAT, TR, FIRST, POLAR><<<c->fused_grid, kChunk, 0, s>>>(
-      c->dp, src, dst, c->perm, c->work, c->n_work, gcur, gnxt, tn, c->key, c->counts, c->status);
-  MPM_CUDA_TRY(cudaGetLastError());
+  MPM_CUDA_TRY(launch_pdl(mpm_g2p2g<D, MAT, TR, FIRST, POLAR>, c->fused_grid, kChunk, s, c->dp, src, dst,
+                          (const int32_t*)c->perm, (const int4*)c->work, (const int32_t*)c->n_work,
+                          (const float4*)gcur, gnxt, tn, c->key, c->counts, c->status));
   return MPM_OK;
 }
 
@@ -1030,19 +1058,19 @@ mpm_status launch_fused(mpm_ctx* c, cudaStream_t s) {
 }
 
 mpm_status launch_scan_permute(mpm_ctx* c, cudaStream_t s, bool clear_consumed) {
-  mpm_scan<<<c->n_scan_tiles, kScanTile, 0, s>>>(c->n_keys, c->P, c->counts, c->offsets, c->cursor, c->work,
-                                                 c->n_work, c->max_work, c->tile_state, c->status);
-  MPM_CUDA_TRY(cudaGetLastError());
+  MPM_CUDA_TRY(launch_pdl(mpm_scan, c->n_scan_tiles, kScanTile, s, c->n_keys, c->P, c->counts, c->offsets, c->cursor,
+                          c->work, c->n_work, c->max_work, c->tile_state, c->status));
   int blocks = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 8));
   float4* gclr = clear_consumed ? c->grid[c->g] : nullptr;
   uint8_t* tclr = clear_consumed ? c->touched[c->g] : nullptr;
   if (c->D == 2)
-    mpm_permute<2><<<blocks, 256, 0, s>>>(c->dp, c->key, c->offsets, c->cursor, c->perm, gclr, tclr, c->tile_state,
-                                          c->n_scan_tiles);
+    MPM_CUDA_TRY(launch_pdl(mpm_permute<2>, blocks, 256, s, c->dp, (const int32_t*)c->key,
+                            (const int32_t*)c->offsets, c->cursor, c->perm, gclr, tclr, c->tile_state,
+                            c->n_scan_tiles));
   else
-    mpm_permute<3><<<blocks, 256, 0, s>>>(c->dp, c->key, c->offsets, c->cursor, c->perm, gclr, tclr, c->tile_state,
-                                          c->n_scan_tiles);
-  MPM_CUDA_TRY(cudaGetLastError());
+    MPM_CUDA_TRY(launch_pdl(mpm_permute<3>, blocks, 256, s, c->dp, (const int32_t*)c->key,
+                            (const int32_t*)c->offsets, c->cursor, c->perm, gclr, tclr, c->tile_state,
+                            c->n_scan_tiles));
   return MPM_OK;
 }
 
