@@ -470,6 +470,56 @@ def rom_batch_serving(dec16, snaps, n_inst=384, steps=40, n_recon_inst=64):
                                "error_how": "full-particle BF16 decode of the r = 16 members vs their FOM runs"}}
 
 
+def rom_large_p_3d(steps=5):
+    """The reduced step where hyper-reduction is meant to pay: the 3D benchmark cube (262,144
+    particles, 128^3) with the Eulerian quadrature (Algorithm 4, whose decoder work does not grow
+    with the particle count) at 256 and 32 samples, the Lagrangian quadrature at 256, against the
+    full-order step on the same scene.  The decoder is an untrained near-identity 3 + 16 -> 128 x 5
+    -> 3 ELU network on the FP32 path: the reduced steps/s are timings, the error is not scored."""
+    import torch
+    import oracle.decoder as OD
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.mpm import MPM
+    from paper_2109_12390_gb300.rom import ROM
+    sc = S.cube_3d()
+    X = sc.x
+    p = S.near_identity_decoder(3, 3, 16, 5, X_min=X.min(0) - 0.05, X_range=X.max(0) - X.min(0) + 0.1, eps=1e-3)
+    dec = Decoder.from_params(p)
+    dec.set_precision(True)
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    fom = MPM.from_scene(sc, polar_eft=HEADLINE_POLAR_EFT)
+    fom.load_numpy(sc.x, sc.v, sc.F, sc.C)
+    fom.step(5)
+    a, b = ev()
+    a.record()
+    fom.step(50)
+    b.record()
+    torch.cuda.synchronize()
+    fom_ms = a.elapsed_time(b) / 50
+    fom.close()
+    out = {"particles": sc.n_particles, "fom_steps_per_s": 1e3 / fom_ms, "decoder": "untrained near-identity, FP32",
+           "runs": []}
+    for quad, k in ((1, 256), (1, 32), (0, 256)):
+        rom = ROM.from_scene(dec, sc, n_samples=k, seed=5, projection=0, quadrature=quad)
+        rom.fit_initial(sc.x, sc.v, iters=5)
+        rom.step(1)
+        torch.cuda.synchronize()
+        a, b = ev()
+        a.record()
+        rom.step(steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        run = {"quadrature": "eulerian" if quad else "lagrangian", "n_samples": k, "rom_steps_per_s": 1e3 / ms,
+               "rom_ms_per_step": ms, "fom_over_rom": ms / fom_ms, "status_word": rom.status()}
+        if quad:
+            run["quadrature_points"] = int(rom.quadrature_points()["x"].shape[0])
+        out["runs"].append(run)
+        rom.close()
+    dec.close()
+    return out
+
+
 def rom_leg(r=16, train_steps=None, steps=None):
     """Snapshots from the GPU full-order model, decoder training on the GPU, reduced-order runs on
     held-out scenes and their accumulated position error (Section 5) against the full-order runs;
@@ -551,10 +601,12 @@ def rom_leg(r=16, train_steps=None, steps=None):
     cpu = cpu_baseline_rom(dec, tests[0]["scene"], r)
     serving = rom_serving(dec, n_inst=8, steps=min(200, steps))
     batched_serving = rom_batch_serving(dec, snaps)
+    large_p = rom_large_p_3d()
     return {
         "cpu_baseline": cpu,
         "serving": serving,
         "batched_serving": batched_serving,
+        "large_p_3d": large_p,
         "scene": "2D neo-Hookean block 64x64 (4096 particles), 128^2 grid, nu=0.3, dt=5e-5, sticky walls, floor "
                  f"impact; decoder 2+{r}->128x5->2 ELU trained on {ROM_TRAIN_INSTANCES} trajectories, "
                  f"(E, v0) ~ U[5e3,1.5e4] x U[-0.5,0.5]^2; {len(tests)} held-out test draws",
