@@ -62,7 +62,9 @@ __global__ void decoder_simt(DecArgs a) {
     float y[3] = {0.f, 0.f, 0.f};
     if (a.linear) {
       // an affine map has no mixed second derivative
-      for (int i = 0; i < a.d; ++i) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (i >= a.d) break;
         float z = 0.f;
         if (ri.cls != 3)
           for (int c = 0; c < K; ++c) z = fmaf(a.W0[i * K + c], ri.cls == 0 ? in[c] : dir[c], z);
@@ -80,13 +82,19 @@ __global__ void decoder_simt(DecArgs a) {
         else if (ri.cls == 1) h = act_d1(a.act, z) * zd;
         else if (ri.cls == 2) h = act_sec(a.act, z, zd);
         else h = act_d2(a.act, z) * zd * mixed_t0(a, a.W0 + c * K, ri.kind);
-        for (int i = 0; i < a.d; ++i) y[i] = fmaf(a.Wout[i * kW + c], h, y[i]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (i < a.d) y[i] = fmaf(a.Wout[i * kW + c], h, y[i]);
       }
       if (ri.cls == 0)
-        for (int i = 0; i < a.d; ++i) y[i] += a.bout[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (i < a.d) y[i] += a.bout[i];
     }
     float* o = a.out + ((int64_t)k * a.n + ri.p) * a.d;   // kind stride = capacity a.n
-    for (int i = 0; i < a.d; ++i) o[i] = y[i] * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (i < a.d) o[i] = y[i] * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
   }
 }
 
@@ -296,7 +304,9 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         }
         if (last) {
           // output layer fused into the last epilogue (FP32), partial over this half's columns
-          for (int o = 0; o < a.d; ++o) {
+#pragma unroll
+          for (int o = 0; o < 3; ++o) {   // compile-time bound: y stays in registers
+            if (o >= a.d) break;
             float sacc = 0.f;
 #pragma unroll
             for (int i = 0; i < 32; ++i) sacc = fmaf(sWout[o * kW + ch * 32 + i], acc[i], sacc);
@@ -313,13 +323,17 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
     if (tail->abort) break;
     // combine the two column halves of the output layer
     if (h == 1) {
-      for (int o = 0; o < a.d; ++o) ypart[rw * 3 + o] = y[o];
+#pragma unroll
+      for (int o = 0; o < 3; ++o)
+        if (o < a.d) ypart[rw * 3 + o] = y[o];
     }
     __syncthreads();
     if (h == 0 && ri.cls >= 0) {
       const int kidx = rw / a.Pt;  // position of this row's kind in `kinds`
       float* o = a.out + ((int64_t)kidx * a.n + ri.p) * a.d;
-      for (int i = 0; i < a.d; ++i) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (i >= a.d) break;
         float v = y[i] + ypart[rw * 3 + i] + (ri.cls == 0 ? __ldg(&a.bout[i]) : 0.f);
         o[i] = v * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
       }
@@ -615,7 +629,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
       for (int kk = 0; kk < kW / TPR; ++kk) {
         const int k = part + TPR * kk;
         const float h = A0[f32_slot<TR>(k, slot)];
-        for (int i = 0; i < a.d; ++i) y[i] = fmaf(sWout[i * kW + k], h, y[i]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (i < a.d) y[i] = fmaf(sWout[i * kW + k], h, y[i]);
       }
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -624,7 +640,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
       if (part == 0 && fr.kidx >= 0) {
         const RowInfo& ri = fr.ri;
         float* o = a.out + ((int64_t)fr.kidx * a.n + ri.p) * a.d;
-        for (int i = 0; i < a.d; ++i) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          if (i >= a.d) break;
           const float v = y[i] + (ri.cls == 0 ? a.bout[i] : 0.f);
           o[i] = v * a.norm[3 * a.d + i] + (ri.cls == 0 ? a.norm[2 * a.d + i] : 0.f);
         }

@@ -141,6 +141,7 @@ struct BwdArgs {
 };
 
 constexpr int kExchRows = 104;
+constexpr int kBwdMaxR = 5;           // rows per point in training: primal, d <= 3 tangents, JVP
 constexpr int kExchStride = kW + 1;   // padded row stride: lanes of a warp hit distinct banks
 
 // 256 threads: warps w and w + 4 read the same tensor-memory lane group; thread
@@ -202,7 +203,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
     float ybar[3] = {0.f, 0.f, 0.f};
     if (valid) {
       const float* o = a.fwd + ((int64_t)k * a.n + p) * d;
-      for (int i = 0; i < d; ++i) {
+      // loops over the d <= 3 output components have compile-time bounds: with the runtime bound
+      // the small register arrays they index (ybar, acc) are placed in local memory
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (i >= d) break;
         float e, w;
         if (k == 0) {
           e = o[i] - a.b.tx[p * d + i];
@@ -233,10 +238,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float av = __bfloat162float(hv[j]);
-          for (int i = 0; i < d; ++i) acc[i] = fmaf(sy[(64 * rh + c + j) * 3 + i], av, acc[i]);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            if (i < d) acc[i] = fmaf(sy[(64 * rh + c + j) * 3 + i], av, acc[i]);
         }
       }
-      for (int i = 0; i < d; ++i) atomicAdd(&a.gparams[a.gWout_off + i * kW + f], acc[i]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < d) atomicAdd(&a.gparams[a.gWout_off + i * kW + f], acc[i]);
       if (t < d) {
         float sb = 0.f;
         for (int q2 = 0; q2 < Pt; ++q2) sb += sy[q2 * 3 + t];
@@ -266,7 +275,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             float sacc = 0.f;
-            for (int o = 0; o < d; ++o) sacc = fmaf(__ldg(&a.Wout[o * kW + ch * 32 + i]), ybar[o], sacc);
+#pragma unroll
+            for (int o = 0; o < 3; ++o)
+              if (o < d) sacc = fmaf(__ldg(&a.Wout[o * kW + ch * 32 + i]), ybar[o], sacc);
             hb[i] = sacc;
           }
         }
@@ -294,7 +305,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
           for (int i = 0; i < 32; ++i) {
             const int f = ch * 32 + i;
             float sacc = act_d1(a.act, zpv[i]) * hb[i];
-            for (int kk = 1; kk < R; ++kk) sacc += exch[((kk - 1) * Pt + q) * kExchStride + f];
+            // compile-time bound (R <= kBwdMaxR): with the runtime bound this loop, inside the
+            // unrolled feature loop, ran about 1,000 cycles per feature
+#pragma unroll
+            for (int kk = 1; kk < kBwdMaxR; ++kk)
+              if (kk < R) sacc += exch[((kk - 1) * Pt + q) * kExchStride + f];
             zb[i] = sacc;
           }
         } else if (cls < 0) {
