@@ -536,6 +536,18 @@ mpm_status rom_debug(rom_ctx* ctx, int32_t* qlist, int32_t* counts, float* x_all
                      float* x_trial, void* stream);
 
 /*
+ * Line-search choices of the last step's Gauss-Newton iterations (Algorithm 6, backtracking):
+ * picks (16 int32, host or device) receives for iteration i < *n_iters the m of the accepted step
+ * length 2^-m (the first of the trials 2^0 .. 2^-10 meeting the sufficient-decrease condition), or
+ * -1 when none did and the iterate stayed; entries from *n_iters on are unspecified.  *n_iters
+ * (host) is cfg.gn_iters, or 0 with the velocity-only projection (no line search).  Where the
+ * condition's margin is at the rounding level of the FP32 residual rows, either choice is a
+ * correct outcome; tests compare the oracle run with these choices.  Synchronous.  Errors:
+ * MPM_EINVAL for a NULL argument.
+ */
+mpm_status rom_debug_line_search(rom_ctx* ctx, int32_t* picks, int32_t* n_iters, void* stream);
+
+/*
  * Eulerian quadrature of the last step (cfg.quadrature = 1; synchronous; any
  * output pointer may be NULL): the number of points n_points, their positions
  * x_points and reference positions X_points (n_points, dim), mass and

@@ -377,29 +377,43 @@ def project_velocity(dec, Xs, xhat_n, v_trial, ridge=0.0, vhat_n=None):
     return vhat_n + lstsq(J, v_trial.reshape(-1) - J @ vhat_n, ridge)
 
 
-def gauss_newton(dec, Xs, x_trial, xhat0, iters, c=1e-4, max_halvings=10, ridge=0.0):
+def gauss_newton(dec, Xs, x_trial, xhat0, iters, c=1e-4, max_halvings=10, ridge=0.0, steps=None, record=None):
     """Eq. nonlinear_projection:pos by Gauss-Newton with backtracking; returns (xhat, no_decrease).
-    With ridge > 0 every step solves the ridge-regularised linearised problem."""
+    With ridge > 0 every step solves the ridge-regularised linearised problem.
+
+    Backtracking tries alpha = 1, 1/2, ... and takes the first alpha with sufficient decrease,
+    ||r(xhat + alpha delta)||^2 <= f0 + c alpha slope.  With `steps` (one entry per iteration: the
+    m of the step 2^-m to take, or -1 for none) that choice is given instead of searched for, so
+    that a run whose choices were made at a different precision can be replayed.  `record`, a list,
+    receives per iteration a dict with f0, slope and f: the objective at every trial 2^-m, m = 0 ..
+    max_halvings (evaluated only when record is given)."""
     xh = np.array(xhat0, np.float64)
     flag = False
     target = x_trial.reshape(-1)
-    for _ in range(iters):
+    for it in range(iters):
         g, _, Jq = D.jacobians(dec, Xs, xh)
         res = g.reshape(-1) - target
         J = Jq.reshape(-1, dec.r)
         delta = lstsq(J, -res, ridge)
         f0 = res @ res
         slope = 2.0 * res @ (J @ delta)
-        alpha = 1.0
-        accepted = False
-        for _h in range(max_halvings + 1):
-            r1 = D.decode(dec, Xs, xh + alpha * delta).reshape(-1) - target
-            if r1 @ r1 <= f0 + c * alpha * slope:
-                accepted = True
-                break
-            alpha *= 0.5
-        if accepted:
-            xh = xh + alpha * delta
+
+        def objective(m):
+            r1 = D.decode(dec, Xs, xh + 0.5 ** m * delta).reshape(-1) - target
+            return r1 @ r1
+
+        if record is not None:
+            record.append(dict(f0=f0, slope=slope, f=np.array([objective(m) for m in range(max_halvings + 1)])))
+        if steps is not None:
+            pick = int(steps[it])
+        else:
+            pick = -1
+            for m in range(max_halvings + 1):
+                if objective(m) <= f0 + c * 0.5 ** m * slope:
+                    pick = m
+                    break
+        if pick >= 0:
+            xh = xh + 0.5 ** pick * delta
         elif np.linalg.norm(delta) > 1e-10 * (1.0 + np.linalg.norm(xh)):
             flag = True
     return xh, flag

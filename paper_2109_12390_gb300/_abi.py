@@ -106,6 +106,7 @@ SIGNATURES = [
     ("rom_step", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("rom_status_word", C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_int, C.c_void_p]),
     ("rom_debug", C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),
+    ("rom_debug_line_search", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
     ("rom_debug_quadrature", C.c_int, [C.c_void_p, C.POINTER(C.c_int32)] + [C.c_void_p] * 4 + [C.c_void_p]),
     ("rom_decode_all", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("rom_set_kinematic", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),

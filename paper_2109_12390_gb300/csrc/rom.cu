@@ -63,6 +63,7 @@ void decoder_shape(const mpm_decoder* dec, int* d, int* r);
 namespace mpmrom {
 
 constexpr int kLS = 11;          // line-search trials 2^0 .. 2^-10
+constexpr int kMaxGnIters = 16;   // cfg.gn_iters <= 16
 constexpr int kMaxRl = 32;       // latent dimension bound of the solver
 constexpr int kNormBlock = 256;
 
@@ -915,6 +916,7 @@ struct RomSolve {
   double* acc;       // normal-equation accumulators: r(r+1)/2 + r + 1
   double* fls;       // line-search objectives (kLS)
   uint32_t* counter; // last-CTA counters [0] normal, [1] line search
+  int32_t* picks;    // per Gauss-Newton iteration of the last step: accepted trial m (step 2^-m), -1 none
   // FP32 copies fed to the decoder
   float* xh32;       // xhat_n
   float* vh32;       // vhat_n
@@ -1297,7 +1299,8 @@ __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, c
 // also commits the step.
 __global__ void __launch_bounds__(kNormBlock) rom_linesearch(RomDev R, RomSolve S, const float* __restrict__ dec,
                                                              int64_t cap, int mode, const float* __restrict__ target,
-                                                             int final_iter, double armijo_c, int n_rows_override) {
+                                                             int final_iter, double armijo_c, int n_rows_override,
+                                                             int iter) {
   const int d = R.d, r = R.r;
   const int nP = n_rows_override > 0 ? n_rows_override : R.counts[0];
   const int per = nP * d;
@@ -1355,6 +1358,7 @@ __global__ void __launch_bounds__(kNormBlock) rom_linesearch(RomDev R, RomSolve 
     for (int i = 0; i < r; ++i) xn += S.xk[i] * S.xk[i];
     if (pick < 0 && dn > 1e-8 * (1.0 + sqrt(xn)) && -0.5 * slope > 1e-3 * f0)
       raise_status(R.status, STATUS_GN_NO_DECREASE);
+    if (iter >= 0 && iter < kMaxGnIters) S.picks[iter] = pick;
     s_pick = pick;
   }
   __syncthreads();
@@ -1450,6 +1454,7 @@ struct rom_ctx {
   double* solve_mem = nullptr;
   float* solve32 = nullptr;
   uint32_t* counters = nullptr;
+  int32_t* picks = nullptr;        // line-search choices of the last step (kMaxGnIters)
   // kinematic boundaries: sample capacity k_cap = k + m_kin x n_groups
   int k_cap = 0;
   int32_t* kin_group = nullptr;
@@ -1632,7 +1637,7 @@ mpm_status rom_launch_step(rom_ctx* c, cudaStream_t s) {
                             1 + kLS, c->outLS, s);
     if (st != MPM_OK) return st;
     rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, c->k_cap, NE_GN, nullptr,
-                                              it == c->cfg.gn_iters - 1, 1e-4, 0);
+                                              it == c->cfg.gn_iters - 1, 1e-4, 0, it);
     MPM_CUDA_TRY(cudaGetLastError());
   }
   return MPM_OK;
@@ -1700,7 +1705,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   MPM_CHECK_ARG(cfg->dim == 2 || cfg->dim == 3, "dim must be 2 or 3");
   MPM_CHECK_ARG(n_particles >= 1 && n_particles < (1 << 30), "particle count");
   MPM_CHECK_ARG(cfg->n_samples >= 1, "n_samples >= 1");
-  MPM_CHECK_ARG(cfg->gn_iters >= 1 && cfg->gn_iters <= 16, "gn_iters in [1, 16]");
+  MPM_CHECK_ARG(cfg->gn_iters >= 1 && cfg->gn_iters <= kMaxGnIters, "gn_iters in [1, 16]");
   MPM_CHECK_ARG(cfg->projection == 0 || cfg->projection == 1, "projection: 0 position-velocity, 1 velocity-only");
   MPM_CHECK_ARG(cfg->latent_dim >= 1 && cfg->latent_dim <= kMaxRl, "latent dimension in [1, 32]");
   int dec_d = 0, dec_r = 0;
@@ -1771,6 +1776,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   if ((st = ralloc(&c->solve_mem, n64)) != MPM_OK) return st;
   if ((st = ralloc(&c->solve32, (size_t)4 * r + 2 * kLS * r)) != MPM_OK) return st;
   if ((st = ralloc(&c->counters, 2)) != MPM_OK) return st;
+  if ((st = ralloc(&c->picks, kMaxGnIters)) != MPM_OK) return st;
   MPM_CUDA_TRY(cudaMemcpy(c->X, X, sizeof(float) * P * d, cudaMemcpyDefault));
   MPM_CUDA_TRY(cudaMemcpy(c->nP_all, &c->P, sizeof(int32_t), cudaMemcpyHostToDevice));
   RomDev& v = c->dv;
@@ -1859,6 +1865,7 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   S.acc = m + 6 * r + 3;
   S.fls = S.acc + n_acc;
   S.counter = c->counters;
+  S.picks = c->picks;
   float* f = c->solve32;
   S.xh32 = f;
   S.vh32 = f + r;
@@ -1908,6 +1915,7 @@ void rom_destroy(rom_ctx* c) {
   cudaFree(c->solve_mem);
   cudaFree(c->solve32);
   cudaFree(c->counters);
+  cudaFree(c->picks);
   delete c;
 }
 
@@ -2067,6 +2075,15 @@ mpm_status rom_debug(rom_ctx* c, int32_t* qlist, int32_t* counts, float* x_all, 
   if (v_trial) MPM_CUDA_TRY(cudaMemcpyAsync(v_trial, c->v_trial, sizeof(float) * c->k_cap * c->d, cudaMemcpyDefault, s));
   if (x_trial) MPM_CUDA_TRY(cudaMemcpyAsync(x_trial, c->x_trial, sizeof(float) * c->k_cap * c->d, cudaMemcpyDefault, s));
   MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return MPM_OK;
+}
+
+mpm_status rom_debug_line_search(rom_ctx* c, int32_t* picks, int32_t* n_iters, void* stream) {
+  MPM_CHECK_ARG(c && picks && n_iters, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  MPM_CUDA_TRY(cudaMemcpyAsync(picks, c->picks, sizeof(int32_t) * kMaxGnIters, cudaMemcpyDefault, s));
+  MPM_CUDA_TRY(cudaStreamSynchronize(s));
+  *n_iters = c->cfg.projection == 1 ? 0 : c->cfg.gn_iters;
   return MPM_OK;
 }
 
@@ -2292,7 +2309,7 @@ mpm_status rom_fit_initial(rom_ctx* c, const float* target, const float* V0, int
     st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, P, c->sv.ls_base32, c->sv.ls_dir32, kls, 1 + kLS,
                             c->outLS, s);
     if (st != MPM_OK) break;
-    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, P, NE_FIT, tgt, 0, 1e-4, P);
+    rom_linesearch<<<kLS, kNormBlock, 0, s>>>(c->dv, c->sv, c->outLS, P, NE_FIT, tgt, 0, 1e-4, P, -1);
   }
   // velocity fit at the fitted xhat_0 (Eq. essentialSpecInt, second line)
   if (st == MPM_OK) {

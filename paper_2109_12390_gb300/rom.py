@@ -120,6 +120,13 @@ class ROM:
             return dict(samples=q[:nP].copy(), neigh=q[:0].copy(), n_points=nQ, v_trial=vt, x_trial=xt)
         return dict(samples=q[:nP].copy(), neigh=q[nP:nQ].copy(), x_all=xa, v_trial=vt, x_trial=xt)
 
+    def line_search_picks(self, stream=None):
+        """Per Gauss-Newton iteration of the last step, the m of the accepted step 2^-m (-1: none)."""
+        picks = np.empty(16, np.int32)
+        n = C.c_int32()
+        _abi.check(_abi.lib().rom_debug_line_search(self._h, _ptr(picks), C.byref(n), _stream(stream)))
+        return picks[:n.value].copy()
+
     def quadrature_points(self, stream=None):
         """Eulerian quadrature of the last step: dict of x (points), X (reference positions), mass, V0."""
         d, n = self.d, self.cfg.n_grid

@@ -174,23 +174,75 @@ def check_velocity_projection(p, Xs, xh, v_trial, got, label="", ridge=0.0, vhat
     return ref
 
 
-def check_gauss_newton_increment(p, Xs, xh, xh_prev, v_trial, dt, got_xh1, iters=3, label="", ridge=0.0):
+def line_search_band(p, rec, dt_v):
+    """Rounding band of the sufficient-decrease margins f(2^-m) - f0 - c 2^-m slope of one
+    Gauss-Newton iteration (rec: the oracle's record of it).  The GPU forms every residual row
+    from an FP32 secant s = g(xhat) - g(xhat_n) (r = s - dt v_trial), whose relative error is that
+    of an n-term FP32 dot product, sqrt(n) u (n the widest fan-in).  An error e in the rows moves
+    |r|^2 by 2 r.e to first order, at most 2 |r| |e| <= 2 sqrt(n) u |r| (|r| + |dt v_trial|); the
+    band is K times that for the trial and for f0 together."""
+    n = max(w.shape[1] for w in p.W)
+    rs = np.sqrt(np.maximum(rec["f"], 0.0))
+    r0 = np.sqrt(max(rec["f0"], 0.0))
+    return 2.0 * K * np.sqrt(n) * U32 * (rs * (rs + dt_v) + r0 * (r0 + dt_v))
+
+
+def check_line_search_picks(p, records, picks, dt_v, c=1e-4, label=""):
+    """Every line-search choice of the GPU is a valid outcome of the backtracking rule in exact
+    arithmetic up to the rounding band: each trial before the chosen one fails the condition or
+    lies within the band, and the chosen one meets it or lies within the band (with -1, none is
+    chosen, so every trial fails or lies within the band).  Returns the number of choices that
+    differ from the FP64 one (possible only within the band)."""
+    open_choices = 0
+    for i, (m, rec) in enumerate(zip(picks, records)):
+        f = rec["f"]
+        margins = f - (rec["f0"] + c * 0.5 ** np.arange(len(f)) * rec["slope"])
+        band = line_search_band(p, rec, dt_v)
+        last = int(m) if m >= 0 else len(f)
+        assert np.all(margins[:last] > -band[:last]), (label, i, m, margins[:last], band[:last])
+        if m >= 0:
+            assert margins[m] <= band[m], (label, i, m, margins[m], band[m])
+        first = int(np.argmax(margins <= 0)) if np.any(margins <= 0) else -1
+        open_choices += int(first != m)
+    return open_choices
+
+
+def check_gauss_newton_increment(p, Xs, xh, xh_prev, v_trial, dt, got_xh1, iters=3, label="", ridge=0.0,
+                                 picks=None):
     """xhat_{n+1} - xhat_n of Algorithm 6 (Gauss-Newton from 2 xhat_n - xhat_{n-1} towards the
     trial positions g(X; xhat_n) + dt v_trial, on the GPU's own trial velocities).  The GPU forms
     the residual as [g(xhat_k) - g(xhat_n)] - dt v_trial (secant rows), never rounding the trial
     positions themselves, so the perturbed inputs are the decoder, X, xhat_n, v_trial and the
-    initial guess, and the trial positions follow from them in FP64."""
+    initial guess, and the trial positions follow from them in FP64.
+
+    Backtracking is a discrete choice the GPU makes on its FP32 residual rows.  Once an iteration
+    has reached the rounding level of those rows, the sufficient-decrease margin of a trial can be
+    smaller than their rounding, and the GPU and the FP64 oracle may then take different step
+    lengths, both correct; the increments differ by a fraction of that iteration's step.  With
+    `picks` (the GPU's choices, ROM.line_search_picks) every choice is checked to be valid within
+    the rounding band, and the oracle replays the GPU's choices."""
     import oracle.decoder as OD
     import oracle.rom as OR
     dt32 = float(np.float32(dt))
     init = 2 * np.asarray(xh, np.float64) - np.asarray(xh_prev, np.float64)
+    pf = f32_decoder(p)
+    Xs32 = f32(Xs)
+    vt = np.asarray(v_trial, np.float64)
+    xh = np.asarray(xh, np.float64)
+    rid = max(ridge, RIDGE_FLOOR)
+    if picks is not None:
+        records = []
+        x_trial = OD.decode(pf, Xs32, xh) + dt32 * vt
+        OR.gauss_newton(pf, Xs32, x_trial, init, iters, ridge=rid, steps=picks, record=records)
+        n_open = check_line_search_picks(pf, records, picks, dt32 * np.linalg.norm(vt), label=label)
+        print(f"{label} line-search choices {[int(m) for m in picks]}, {n_open} of them other than the FP64 "
+              f"choice, within the rounding band")
 
     def fn(pp, X_, xh_, vt_, i_):
         x_trial = OD.decode(pp, X_, xh_) + dt32 * vt_
-        return OR.gauss_newton(pp, X_, x_trial, i_, iters, ridge=max(ridge, RIDGE_FLOOR))[0] - xh_
+        return OR.gauss_newton(pp, X_, x_trial, i_, iters, ridge=rid, steps=picks)[0] - xh_
 
-    sens, ref = sensitivity(fn, (f32_decoder(p), f32(Xs), np.asarray(xh, np.float64),
-                                 np.asarray(v_trial, np.float64), init), decoder_args=(0,))
+    sens, ref = sensitivity(fn, (pf, Xs32, xh, vt, init), decoder_args=(0,))
     err = rel(np.asarray(got_xh1) - xh, ref)
     print(f"{label} GN increment error {err:.3e} sensitivity {sens:.3e} bound {bound(sens):.3e}")
     assert err < bound(sens), (label, err, sens)

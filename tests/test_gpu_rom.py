@@ -153,7 +153,8 @@ def test_one_step_projection_fp32_decoder(projection):
     else:
         # (the oracle's no-decrease flag is not compared: on this FP32-derived target the last
         # iteration sits at the residual's rounding floor, where either outcome is correct)
-        FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="fp32 1 layer")
+        FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="fp32 1 layer",
+                                        picks=rom.line_search_picks())
 
 
 @pytest.mark.parametrize("n_hidden,tol", [(1, None), (5, TOL_BF16)])
@@ -224,7 +225,8 @@ def test_one_step_fp32_deep_decoder(projection):
     xh1, vh1, _, _ = rom.get_state()
     FB.check_velocity_projection(p, Xs, xh, vt, vh1, "fp32 5 layers", vhat_n=vh)
     if not projection:
-        FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="fp32 5 layers")
+        FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="fp32 5 layers",
+                                        picks=rom.line_search_picks())
 
 
 @pytest.mark.parametrize("n_hidden", [1, 5])
@@ -322,7 +324,8 @@ def test_config4_scale_one_step_parity():
     vt = dbg["v_trial"].astype(np.float64)
     xh1, vh1, _, _ = rom.get_state()
     FB.check_velocity_projection(p, Xs, xh, vt, vh1, "config 4 size", vhat_n=vh)
-    FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="config 4 size")
+    FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="config 4 size",
+                                        picks=rom.line_search_picks())
 
 
 def test_metric_accumulate():

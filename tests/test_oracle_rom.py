@@ -137,6 +137,39 @@ def test_gauss_newton_reaches_the_nonlinear_least_squares_minimiser():
     assert np.all(np.diff(obj) <= 0) and obj[-1] < 1e-2 * obj[0]
 
 
+def test_gauss_newton_record_and_replay_of_line_search_choices():
+    """Algorithm 6's backtracking: the record of each iteration lists the objective at every trial
+    2^-m; the search took the first trial with sufficient decrease; the next iteration's f0
+    (formed from the decoder's value at the new iterate, not from the record) equals the chosen
+    trial's objective; replaying the choices reproduces the searched run exactly; and a far start
+    makes the search halve at least once."""
+    rng = np.random.default_rng(31)
+    d, r = 2, 3
+    X = rng.uniform(0.3, 0.6, size=(20, d))
+    dec = S.xavier_decoder(7, d, r, 16, 2, D.ELU, X_min=X.min(0), X_range=X.max(0) - X.min(0),
+                           out_scale=np.full(d, 0.2), bias_scale=0.2)
+    target = D.decode(dec, X, rng.normal(size=r)) + 0.002 * rng.normal(size=(20, d))
+    x0 = 3.0 * rng.normal(size=r)
+    rec = []
+    xh, _ = R.gauss_newton(dec, X, target, x0, iters=6, record=rec)
+    picks = []
+    for it in rec:
+        ok = it["f"] <= it["f0"] + 1e-4 * 0.5 ** np.arange(len(it["f"])) * it["slope"]
+        picks.append(int(np.argmax(ok)) if ok.any() else -1)
+    assert max(picks) > 0
+    for i in range(len(rec) - 1):
+        if picks[i] >= 0:
+            assert rec[i + 1]["f0"] == pytest.approx(rec[i]["f"][picks[i]], rel=1e-12)
+    xr, _ = R.gauss_newton(dec, X, target, x0, iters=6, steps=picks)
+    np.testing.assert_array_equal(xr, xh)
+    # a different choice gives a different (and here worse) result
+    other = list(picks)
+    other[0] = picks[0] + 1
+    xo, _ = R.gauss_newton(dec, X, target, x0, iters=1, steps=other[:1])
+    x1, _ = R.gauss_newton(dec, X, target, x0, iters=1)
+    assert not np.array_equal(xo, x1)
+
+
 def test_velocity_only_matches_position_velocity_to_second_order():
     rng = np.random.default_rng(1)
     d, r = 2, 3
