@@ -43,7 +43,15 @@
 
 namespace mpmrom {
 
-constexpr int kChunk = 256;  // particles per work item = threads per CTA
+constexpr int kChunk = 256;           // threads per CTA of the fused kernel
+constexpr int kSlots = 2;             // particles per thread
+constexpr int kItem = kSlots * kChunk; // particles per work item at most
+
+// Dynamic shared memory of the fused kernel: per slot its P2G record (2 D + D^2 floats), its
+// position in cell order, its cell and its rank within the cell.
+template <int D>
+constexpr int fused_dyn_smem() { return kItem * ((2 * D + D * D) * 4 + 3 * 2); }
+static_assert(fused_dyn_smem<3>() <= 48 * 1024, "the fused kernel launches without raising its shared-memory limit");
 
 template <int D> struct Blk;
 template <> struct Blk<2> { static constexpr int B = 8; };
@@ -215,6 +223,20 @@ __device__ __forceinline__ void flag_blocks(unsigned bits, const int b0[D], int 
   }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
+// L2 prefetch of the lines of particle s that the fused kernel's gather reads (x, F, id).
+template <int D>
+__device__ __forceinline__ void prefetch_state(const StateView& src, int s, int P) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) prefetch_l2(&src.base[(size_t)a * P + s]);
+#pragma unroll
+  for (int i = 0; i < D * D; ++i) prefetch_l2(&src.base[(size_t)(2 * D + i) * P + s]);
+  prefetch_l2(&src.id[s]);
+}
+
 // Programmatic dependent launch: the step's kernels are launched so that the next one may be
 // scheduled while this one drains.  Every step kernel first waits until the previous grid has
 // completed and its writes are visible (a no-op when launched without the attribute), then lets
@@ -256,7 +278,11 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
   __shared__ int s_cells[NC];
   __shared__ int s_nne;
   __shared__ unsigned s_tmask;   // grid blocks written by the item's flush
-  __shared__ float s_rec[kChunk * PD];
+  extern __shared__ __align__(16) float s_dyn[];
+  float* s_rec = s_dyn;                      // P2G records by slot
+  short* s_idx = (short*)(s_rec + kItem * PD); // slots in cell order
+  short* s_lc = s_idx + kItem;                 // cell of each slot (-1: none)
+  short* s_rank = s_lc + kItem;                // rank of the slot within its cell
 
   pdl_enter();
   const int nw = *n_work;
@@ -278,19 +304,23 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
     int tile_lo[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) tile_lo[a] = b0[a] - 1;
-    const int j = item.y + threadIdx.x;
-    const bool active = threadIdx.x < item.z;
-    // the particle's gather (binned order -> state) is issued before the node tile, so that its
-    // two dependent HBM latencies overlap the tile's
+    // kSlots particles per thread: slots threadIdx.x + sl kChunk of the item.  The first slot's
+    // gather (binned order -> state) is issued before the node tile, so that its two dependent HBM
+    // latencies overlap the tile's; the other slots' lines are fetched into L2.
     int s_src = 0, pid = 0;
     float x[D], F[DD];
-    if (active) {
-      s_src = perm[j];
+    if (threadIdx.x < item.z) {
+      s_src = perm[item.y + threadIdx.x];
 #pragma unroll
       for (int a = 0; a < D; ++a) x[a] = src.base[(size_t)a * P + s_src];
 #pragma unroll
       for (int i = 0; i < DD; ++i) F[i] = src.base[(size_t)(2 * D + i) * P + s_src];
       pid = src.id[s_src];
+    }
+#pragma unroll
+    for (int sl = 1; sl < kSlots; ++sl) {
+      if (threadIdx.x + sl * kChunk < item.z)
+        prefetch_state<D>(src, perm[item.y + threadIdx.x + sl * kChunk], P);
     }
     // grid-to-particle tile with the grid update of Algorithm 1 applied on load
     if (!FIRST) {
@@ -313,6 +343,19 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
     __syncthreads();
 
     if (threadIdx.x == 0) s_tmask = 0u;   // every thread read the previous item's mask before the barrier
+#pragma unroll 1
+    for (int sl = 0; sl < kSlots; ++sl) {
+    const int slot = threadIdx.x + sl * kChunk;
+    const int j = item.y + slot;
+    const bool active = slot < item.z;
+    if (sl > 0 && active) {
+      s_src = perm[j];
+#pragma unroll
+      for (int a = 0; a < D; ++a) x[a] = src.base[(size_t)a * P + s_src];
+#pragma unroll
+      for (int i = 0; i < DD; ++i) F[i] = src.base[(size_t)(2 * D + i) * P + s_src];
+      pid = src.id[s_src];
+    }
     int new_key = -1;
     int lc = -1, rank = 0;
     float rec[PD];
@@ -532,7 +575,17 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
         }
       }
     }
+    if (lc >= 0) {
+      float* dstr = s_rec + (size_t)slot * PD;
+#pragma unroll
+      for (int i = 0; i < PD; ++i) dstr[i] = rec[i];
+    }
+    if (active) {
+      s_lc[slot] = (short)lc;
+      s_rank[slot] = (short)rank;
+    }
     if (!FIRST) count_key_aggregated(new_key, counts);
+    }  // slots
     __syncthreads();
     // exclusive scan of the cell counts and list of non-empty cells (warp 0)
     if (warp == 0) {
@@ -570,10 +623,14 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
       }
     }
     __syncthreads();
-    if (lc >= 0) {
-      float* dstr = s_rec + (size_t)(s_off[lc] + rank) * PD;
+    // counting sort of the slots by cell
 #pragma unroll
-      for (int i = 0; i < PD; ++i) dstr[i] = rec[i];
+    for (int sl = 0; sl < kSlots; ++sl) {
+      const int slot = threadIdx.x + sl * kChunk;
+      if (slot < item.z) {
+        const int lc = s_lc[slot];
+        if (lc >= 0) s_idx[s_off[lc] + s_rank[slot]] = (short)slot;
+      }
     }
     __syncthreads();
     // cell-owner accumulation: one task per (non-empty cell, leading stencil
@@ -607,7 +664,7 @@ __global__ void __launch_bounds__(kChunk, 3) mpm_g2p2g(DevParams p, StateView sr
         }
       const int q1 = s_off[cell + 1];
       for (int q = s_off[cell]; q < q1; ++q) {
-        const float* rr = s_rec + (size_t)q * PD;
+        const float* rr = s_rec + (size_t)s_idx[q] * PD;
         float wl[3], wlast[3], wmid[3];
         bspline_w(rr[0], wl);
         bspline_w(rr[D - 1], wlast);
@@ -719,7 +776,7 @@ __global__ void __launch_bounds__(kScanTile) mpm_scan(int n_keys, int P, int32_t
   const int tile = blockIdx.x;
   const int k = tile * kScanTile + threadIdx.x;
   const int c = k < n_keys ? counts[k] : 0;
-  const int nw = (c + kChunk - 1) / kChunk;
+  const int nw = (c + kItem - 1) / kItem;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int a = c, b = nw;
 #pragma unroll
@@ -794,7 +851,9 @@ __global__ void __launch_bounds__(kScanTile) mpm_scan(int n_keys, int P, int32_t
   if (k < n_keys) {
     offsets[k] = off;
     for (int q = 0; q < nw; ++q) {
-      if (woff < max_work) work[woff] = make_int4(k, off + q * kChunk, min(kChunk, c - q * kChunk), 0);
+      // nw items of near-equal size (at most kItem particles each)
+      const int lo = (int)((long long)q * c / nw), hi = (int)((long long)(q + 1) * c / nw);
+      if (woff < max_work) work[woff] = make_int4(k, off + lo, hi - lo, 0);
       ++woff;
     }
     counts[k] = 0;
@@ -1013,11 +1072,11 @@ mpm_status dalloc(T** p, size_t count) {
 
 // Launches a step kernel with programmatic stream serialization (see pdl_enter).
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1034,7 +1093,8 @@ mpm_status launch_fused_t(mpm_ctx* c, cudaStream_t s) {
   float4* gcur = c->grid[c->g];
   float4* gnxt = FIRST ? c->grid[c->g] : c->grid[1 - c->g];
   uint8_t* tn = FIRST ? c->touched[c->g] : c->touched[1 - c->g];
-  MPM_CUDA_TRY(launch_pdl(mpm_g2p2g<D, MAT, TR, FIRST, POLAR>, c->fused_grid, kChunk, s, c->dp, src, dst,
+  MPM_CUDA_TRY(launch_pdl(mpm_g2p2g<D, MAT, TR, FIRST, POLAR>, c->fused_grid, kChunk, fused_dyn_smem<D>(), s, c->dp,
+                          src, dst,
                           (const int32_t*)c->perm, (const int4*)c->work, (const int32_t*)c->n_work,
                           (const float4*)gcur, gnxt, tn, c->key, c->counts, c->status));
   return MPM_OK;
@@ -1058,17 +1118,17 @@ mpm_status launch_fused(mpm_ctx* c, cudaStream_t s) {
 }
 
 mpm_status launch_scan_permute(mpm_ctx* c, cudaStream_t s, bool clear_consumed) {
-  MPM_CUDA_TRY(launch_pdl(mpm_scan, c->n_scan_tiles, kScanTile, s, c->n_keys, c->P, c->counts, c->offsets, c->cursor,
+  MPM_CUDA_TRY(launch_pdl(mpm_scan, c->n_scan_tiles, kScanTile, 0, s, c->n_keys, c->P, c->counts, c->offsets, c->cursor,
                           c->work, c->n_work, c->max_work, c->tile_state, c->status));
   int blocks = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 8));
   float4* gclr = clear_consumed ? c->grid[c->g] : nullptr;
   uint8_t* tclr = clear_consumed ? c->touched[c->g] : nullptr;
   if (c->D == 2)
-    MPM_CUDA_TRY(launch_pdl(mpm_permute<2>, blocks, 256, s, c->dp, (const int32_t*)c->key,
+    MPM_CUDA_TRY(launch_pdl(mpm_permute<2>, blocks, 256, 0, s, c->dp, (const int32_t*)c->key,
                             (const int32_t*)c->offsets, c->cursor, c->perm, gclr, tclr, c->tile_state,
                             c->n_scan_tiles));
   else
-    MPM_CUDA_TRY(launch_pdl(mpm_permute<3>, blocks, 256, s, c->dp, (const int32_t*)c->key,
+    MPM_CUDA_TRY(launch_pdl(mpm_permute<3>, blocks, 256, 0, s, c->dp, (const int32_t*)c->key,
                             (const int32_t*)c->offsets, c->cursor, c->perm, gclr, tclr, c->tile_state,
                             c->n_scan_tiles));
   return MPM_OK;
@@ -1175,7 +1235,7 @@ mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
-  c->max_work = ceil_div(c->P, kChunk) + std::min(c->n_keys, c->P) + 1;
+  c->max_work = ceil_div(c->P, kItem) + std::min(c->n_keys, c->P) + 1;
 
   const int D = c->D, DD = D * D;
   const size_t comps = 2 * D + 2 * DD;
@@ -1551,7 +1611,7 @@ mpm_status mpm_step_noalloc(const mpm_config* cfg, float* x, float* v, float* F,
   int dev = 0;
   MPM_CUDA_TRY(cudaGetDevice(&dev));
   MPM_CUDA_TRY(cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev));
-  c.max_work = ceil_div(c.P, kChunk) + std::min(c.n_keys, c.P) + 1;
+  c.max_work = ceil_div(c.P, kItem) + std::min(c.n_keys, c.P) + 1;
   c.n_scan_tiles = ceil_div(c.n_keys, kScanTile);
   const int D = c.D, DD = D * D;
   const size_t comps = 2 * D + 2 * DD;
