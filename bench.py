@@ -400,8 +400,8 @@ def rom_batch_serving(dec16, snaps, n_inst=384, steps=40, n_recon_inst=64):
         plan.append((r, k, sc))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    best_k, tune = PL.autotune_serving(list(decs.values()), roms)
-    batch = PL.build_serving_batch(list(decs.values()), roms, best_k)
+    (best_prec, best_k), tune = PL.autotune_serving(list(decs.values()), roms)
+    batch = PL.build_serving_batch(list(decs.values()), roms, best_k, best_prec)
     batch.step(1)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -459,8 +459,10 @@ def rom_batch_serving(dec16, snaps, n_inst=384, steps=40, n_recon_inst=64):
             "setup_seconds": setup_s,
             "reading": "the reduced step is throughput-bound on its FP32 decoder work (the batch step takes about "
                        "the sum of the instances' steps): one launch serves them all, it does not add concurrency",
-            "autotune": {"chosen_concurrency": best_k, "ms_per_batch_step": tune,
-                         "what": "decoder_set_concurrency (FP32 tiles per call) over candidate values, timed"},
+            "autotune": {"chosen_precision": {1: "FP32 CUDA cores", 2: "split BF16 tensor cores"}[best_prec],
+                         "chosen_concurrency": best_k, "ms_per_batch_step": tune,
+                         "what": "precision/concurrency: square-layer arithmetic (1 FP32 CUDA cores, 2 split "
+                                 "BF16 tensor cores) and decoder_set_concurrency (FP32 tiles per call), timed"},
             "how": "one CUDA graph launch per step: every instance's step graph a parallel branch",
             "decoders": "r = 16 trained; r = 8 and 32 untrained (Xavier, same scaling), timing only",
             "reconstruction": {"points": 4096 * 256, "bf16_ms": recon_ms,

@@ -369,8 +369,14 @@ mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void*
  * (default): BF16 x BF16 -> FP32 tcgen05 GEMMs.  fp32 = 1: FP32 GEMMs on the
  * CUDA cores from the FP32 master weights; for the reduced step's small calls,
  * whose time is set by per-tile latency rather than throughput, this costs
- * little and removes the BF16 rounding of positions and gradients.  Takes
- * effect for reduced-order contexts created afterwards.  Errors: MPM_EINVAL.
+ * little and removes the BF16 rounding of positions and gradients.  fp32 = 2:
+ * split BF16 on the tensor cores: activations and weights are each the sum of
+ * two BF16 numbers (hi = bf16(v), lo = bf16(v - hi)) and every product is
+ * A_hi W_hi + A_hi W_lo + A_lo W_hi accumulated in FP32, so each product keeps
+ * about 16 bits (relative error near 2^-16 against 2^-24 for FP32, against
+ * 2^-8 for BF16) at tensor-core throughput: for many concurrent reduced-order
+ * instances.  The first and output layers are FP32 in every mode.  Takes effect
+ * for reduced-order contexts created afterwards.  Errors: MPM_EINVAL.
  */
 mpm_status decoder_set_precision(mpm_decoder* dec, int fp32);
 

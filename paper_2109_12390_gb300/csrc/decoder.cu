@@ -115,13 +115,39 @@ __device__ __forceinline__ float elu_bf16_input(float z) {
   return z > 0.f ? z : __expf(z) - 1.0f;
 }
 
+// The operand tile of the next square layer: BF16, or (split) the BF16 pair hi = bf16(v),
+// lo = bf16(v - hi) in two tiles kLayerBytes apart.
+template <bool SPLIT>
+__device__ __forceinline__ void store_operand(uint8_t* tile, int row, int col, const float* v) {
+  if (!SPLIT) {
+    store_bf16x8(tile, row, col, v);
+  } else {
+    float hi[8], lo[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      hi[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
+      lo[i] = v[i] - hi[i];   // exact in FP32
+    }
+    store_bf16x8(tile, row, col, hi);
+    store_bf16x8(tile + kLayerBytes, row, col, lo);
+  }
+}
+
+// SPLIT = false: BF16 operands, all square layers resident in shared memory.
+// SPLIT = true: FP32-accurate square layers from split BF16 operands (hi + lo for the
+// activations and the weights), three MMAs per K step into the same FP32 accumulator,
+//   A W ~ A_hi W_hi + A_hi W_lo + A_lo W_hi,
+// the dropped A_lo W_lo term and the residuals of the splits being about 2^-16 of each product;
+// the two weight images of one layer at a time are streamed into shared memory while the
+// previous layer's epilogue runs, and the activations take the accurate exponential.
+template <bool SPLIT>
 __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled operand tiles
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* wsm = smem;                                   // n_tc x 32 KB
-  uint8_t* atile = smem + kMaxTC * kLayerBytes;          // 32 KB
-  float* xb = (float*)(atile + kLayerBytes);             // [2 halves][128 rows][33]: one chunk per half
+  uint8_t* wsm = smem;                                   // n_tc x 32 KB (split: the current layer, hi and lo)
+  uint8_t* atile = smem + (SPLIT ? 2 : kMaxTC) * kLayerBytes;  // 32 KB (split: hi and lo, 64 KB)
+  float* xb = (float*)(atile + (SPLIT ? 2 : 1) * kLayerBytes);  // [2 halves][128 rows][33]: one chunk per half
   float* ypart = xb + 2 * 128 * kXbStride;               // [128 rows][3]: output partial of half 1
   float* sW0 = ypart + 128 * 3;                          // [128][kW0Stride] first layer, zero-padded
   float* sb0 = sW0 + kW * kW0Stride;                     // [128]
@@ -156,15 +182,25 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
     for (int e = t; e < a.n_tc * kW; e += kDecThreads) sbh[e] = a.bh[e];
     for (int e = t; e < a.d * kW; e += kDecThreads) sWout[e] = a.Wout[e];
   }
-  // resident weights of the square layers
-  if (t == 0) {
-    tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(a.n_tc * kLayerBytes));
-    for (int l = 0; l < a.n_tc; ++l)
-      tc::bulk_g2s(wsm + l * kLayerBytes, a.wimg + (size_t)l * kLayerBytes, kLayerBytes, &tail->bar_w);
-  }
-  if (!tc::mbar_wait(&tail->bar_w, 0)) {
-    raise_status(a.status, STATUS_TIMEOUT);
-    atomicExch(&tail->abort, 1);
+  // resident weights of the square layers; split: the first layer's two images (thread 0 waits
+  // for them before its first MMA)
+  uint32_t w_phase = 0;
+  bool w_pending = false;   // thread 0: a weight copy is in flight
+  if (!SPLIT) {
+    if (t == 0) {
+      tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(a.n_tc * kLayerBytes));
+      for (int l = 0; l < a.n_tc; ++l)
+        tc::bulk_g2s(wsm + l * kLayerBytes, a.wimg + (size_t)l * kLayerBytes, kLayerBytes, &tail->bar_w);
+    }
+    if (!tc::mbar_wait(&tail->bar_w, 0)) {
+      raise_status(a.status, STATUS_TIMEOUT);
+      atomicExch(&tail->abort, 1);
+    }
+  } else if (t == 0) {
+    tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(2 * kLayerBytes));
+    tc::bulk_g2s(wsm, a.wimg, kLayerBytes, &tail->bar_w);
+    tc::bulk_g2s(wsm + kLayerBytes, a.wimg_lo, kLayerBytes, &tail->bar_w);
+    w_pending = true;
   }
   __syncthreads();
 
@@ -212,7 +248,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
               }
             }
           }
-          if (ri.cls == 0) hv[j] = a.act == 0 ? elu_bf16_input(z) : z;
+          if (ri.cls == 0) hv[j] = a.act == 0 ? (SPLIT ? elu(z) : elu_bf16_input(z)) : z;
           else if (ri.cls == 1) hv[j] = act_d1(a.act, z) * zd;
           else if (ri.cls == 2) hv[j] = act_sec(a.act, z, zd);
           else hv[j] = act_d2(a.act, z) * zd * mixed_t0(a, w0r, ri.kind);
@@ -223,7 +259,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         }
         if (a.astore) a.astore[(int64_t)c * a.rows_total + tile * 128 + rw] = __float2bfloat16_rn(hv[j]);
       }
-      store_bf16x8(atile, rw, c0, hv);
+      store_operand<SPLIT>(atile, rw, c0, hv);
     }
 
     float y[3] = {0.f, 0.f, 0.f};
@@ -234,12 +270,31 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
       __syncthreads();
       if (t == 0) {
         tc::tc_fence_after();
-        const uint32_t a_base = tc::smem_addr(atile), b_base = tc::smem_addr(wsm + l * kLayerBytes);
+        bool w_ok = true;
+        if (SPLIT && w_pending) {
+          w_ok = tc::mbar_wait(&tail->bar_w, w_phase);
+          w_phase ^= 1u;
+          w_pending = false;
+          if (!w_ok) {
+            raise_status(a.status, STATUS_TIMEOUT);
+            atomicExch(&tail->abort, 1);
+          }
+        }
+        if (w_ok) {
+          const uint32_t a_base = tc::smem_addr(atile);
+          const uint32_t b_base = tc::smem_addr(wsm + (SPLIT ? 0 : l * kLayerBytes));
 #pragma unroll
-        for (int k = 0; k < kW / 16; ++k) {
-          const uint32_t koff = (uint32_t)((k >> 2) * (kW * 128) + (k & 3) * 32);
-          tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + koff), tc::smem_desc_sw128(b_base + koff), idesc,
-                       k > 0 ? 1u : 0u);
+          for (int k = 0; k < kW / 16; ++k) {
+            const uint32_t koff = (uint32_t)((k >> 2) * (kW * 128) + (k & 3) * 32);
+            tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + koff), tc::smem_desc_sw128(b_base + koff), idesc,
+                         k > 0 ? 1u : 0u);
+            if (SPLIT) {
+              tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + koff),
+                           tc::smem_desc_sw128(b_base + kLayerBytes + koff), idesc, 1u);
+              tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + kLayerBytes + koff),
+                           tc::smem_desc_sw128(b_base + koff), idesc, 1u);
+            }
+          }
         }
         tc::mma_commit(&tail->bar_mma);
       }
@@ -248,6 +303,17 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         atomicExch(&tail->abort, 1);
       }
       mma_phase ^= 1u;
+      if (SPLIT && t == 0 && a.n_tc > 1 && !tail->abort) {
+        // the MMAs have read the buffer: stream the next layer's images (this tile's next layer, or
+        // the first layer of the CTA's next tile) while the epilogue runs
+        const int nl = (l + 1) % a.n_tc;
+        if (l + 1 < a.n_tc || tile + gridDim.x < n_tiles) {
+          tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(2 * kLayerBytes));
+          tc::bulk_g2s(wsm, a.wimg + (size_t)nl * kLayerBytes, kLayerBytes, &tail->bar_w);
+          tc::bulk_g2s(wsm + kLayerBytes, a.wimg_lo + (size_t)nl * kLayerBytes, kLayerBytes, &tail->bar_w);
+          w_pending = true;
+        }
+      }
       tc::tc_fence_after();
       __syncthreads();
       if (tail->abort) break;
@@ -280,7 +346,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         if (ri.cls == 0) {
           if (a.act == 0) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[i] = elu_bf16_input(acc[i]);
+            for (int i = 0; i < 32; ++i) acc[i] = SPLIT ? elu(acc[i]) : elu_bf16_input(acc[i]);
           }
         } else if (ri.cls == 1) {
 #pragma unroll
@@ -314,7 +380,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; j += 8) store_bf16x8(atile, rw, ch * 32 + j, acc + j);
+          for (int j = 0; j < 32; j += 8) store_operand<SPLIT>(atile, rw, ch * 32 + j, acc + j);
         }
         if (a.R > 1) __syncthreads();
       }
@@ -340,6 +406,8 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
     }
     __syncthreads();
   }
+  // a weight copy still in flight (an aborted tile loop) lands before the CTA exits
+  if (SPLIT && t == 0 && w_pending) (void)tc::mbar_wait(&tail->bar_w, w_phase);
   __syncthreads();
   tc::tc_fence_after();
   if (warp == 0) tc::tmem_free<kW>(tmem);
@@ -670,15 +738,19 @@ __global__ void decoder_transpose(const float* W, int n_layers, float* WT) {
 }
 
 // Packs the square-layer weights (FP32, (out, in) row-major) into BF16 images
-// in the 128-byte swizzled K-major layout the MMA reads.
-__global__ void decoder_pack(const float* W, int n_layers, int64_t stride, uint8_t* img) {
+// in the 128-byte swizzled K-major layout the MMA reads: img = bf16(w) and, when
+// img_lo is set, img_lo = bf16(w - bf16(w)) (the split operands).
+__global__ void decoder_pack(const float* W, int n_layers, int64_t stride, uint8_t* img, uint8_t* img_lo) {
   const int64_t total = (int64_t)n_layers * kW * kW;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     int l = (int)(i / (kW * kW));
     int rem = (int)(i % (kW * kW));
     int row = rem / kW, k = rem % kW;
-    __nv_bfloat16 v = __float2bfloat16_rn(W[l * stride + rem]);
-    *reinterpret_cast<__nv_bfloat16*>(img + (size_t)l * kLayerBytes + tc::sw128_offset(row, k, kW)) = v;
+    const float w = W[l * stride + rem];
+    const __nv_bfloat16 v = __float2bfloat16_rn(w);
+    const size_t o = (size_t)l * kLayerBytes + tc::sw128_offset(row, k, kW);
+    *reinterpret_cast<__nv_bfloat16*>(img + o) = v;
+    if (img_lo) *reinterpret_cast<__nv_bfloat16*>(img_lo + o) = __float2bfloat16_rn(w - __bfloat162float(v));
   }
 }
 
@@ -690,8 +762,8 @@ using namespace mpmrom;
 
 namespace {
 
-size_t dec_smem_bytes() {
-  return 1024 + kMaxTC * kLayerBytes + kLayerBytes +
+size_t dec_smem_bytes(bool split) {
+  return 1024 + (split ? 2 : kMaxTC) * kLayerBytes + (split ? 2 : 1) * kLayerBytes +
          (2 * 128 * kXbStride + 128 * 3 + kW * kW0Stride + kW + kMaxTC * kW + 3 * kW) * sizeof(float) +
          sizeof(DecSmemTail);
 }
@@ -709,7 +781,8 @@ mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {
                                  cudaMemcpyDeviceToDevice, s));
   }
   decoder_pack<<<std::max(1, std::min(dec->n_sm * 4, dec->n_tc * 64)), 256, 0, s>>>(dec->wsq, dec->n_tc,
-                                                                                    (int64_t)kW * kW, dec->wimg);
+                                                                                    (int64_t)kW * kW, dec->wimg,
+                                                                                    dec->wimg_lo);
   MPM_CUDA_TRY(cudaGetLastError());
   decoder_transpose<<<16, 256, 0, s>>>(dec->wsq, dec->n_tc, dec->wsqT);
   MPM_CUDA_TRY(cudaGetLastError());
@@ -764,7 +837,8 @@ mpm_status decoder_create(const decoder_desc* desc, mpm_decoder** out) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&dec->n_sm, cudaDevAttrMultiProcessorCount, dev);
-  dec->smem = dec_smem_bytes();
+  dec->smem = dec_smem_bytes(false);
+  dec->smem_split = dec_smem_bytes(true);
   cudaError_t e = cudaMalloc((void**)&dec->params, sizeof(float) * dec->n_params);
   if (e == cudaSuccess) e = cudaMalloc((void**)&dec->norm, sizeof(float) * 4 * dec->d);
   if (e == cudaSuccess) e = cudaMalloc((void**)&dec->status, sizeof(uint32_t));
@@ -772,11 +846,15 @@ mpm_status decoder_create(const decoder_desc* desc, mpm_decoder** out) {
     e = cudaMalloc((void**)&dec->wsq, sizeof(float) * dec->n_tc * kW * kW);
     if (e == cudaSuccess) e = cudaMalloc((void**)&dec->bsq, sizeof(float) * dec->n_tc * kW);
     if (e == cudaSuccess) e = cudaMalloc((void**)&dec->wimg, (size_t)dec->n_tc * kLayerBytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dec->wimg_lo, (size_t)dec->n_tc * kLayerBytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&dec->wsqT, sizeof(float) * dec->n_tc * kW * kW);
   }
   if (e == cudaSuccess) e = cudaMemset(dec->params, 0, sizeof(float) * dec->n_params);
   if (e == cudaSuccess) e = cudaMemset(dec->status, 0, sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(decoder_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec->smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(decoder_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec->smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(decoder_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec->smem_split);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(decoder_f32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec_f32_smem_bytes());
   if (e == cudaSuccess)
@@ -796,6 +874,7 @@ void decoder_destroy(mpm_decoder* dec) {
   cudaFree(dec->wsq);
   cudaFree(dec->bsq);
   cudaFree(dec->wimg);
+  cudaFree(dec->wimg_lo);
   cudaFree(dec->wsqT);
   cudaFree(dec->status);
   delete dec;
@@ -812,7 +891,7 @@ mpm_status decoder_set_concurrency(mpm_decoder* dec, int k) {
 
 mpm_status decoder_set_precision(mpm_decoder* dec, int fp32) {
   MPM_CHECK_ARG(dec, "null decoder");
-  MPM_CHECK_ARG(fp32 == 0 || fp32 == 1, "fp32: 0 or 1");
+  MPM_CHECK_ARG(fp32 >= 0 && fp32 <= 2, "precision: 0 BF16, 1 FP32 CUDA cores, 2 split BF16 tensor cores");
   dec->fp32 = fp32;
   return MPM_OK;
 }
@@ -867,6 +946,7 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   a.bout = dec->params + dec->b_off[L - 1];
   a.norm = dec->norm;
   a.wimg = dec->wimg;
+  a.wimg_lo = dec->wimg_lo;
   a.wsq = dec->wsq;
   a.wsqT = dec->wsqT;
   a.X = X;
@@ -921,7 +1001,7 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
     int64_t rows = n * R;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, dec->n_sm * 8));
     decoder_simt<<<blocks, 128, 0, s>>>(a);
-  } else if (dec->fp32 && !a.zstore) {
+  } else if (dec->fp32 == 1 && !a.zstore) {
     MPM_CHECK_ARG(R <= kF32Rows, "the FP32 path takes at most 64 row kinds");
     int64_t tiles;
     bool small = false;
@@ -948,7 +1028,10 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   } else {
     const int64_t tiles = (n + a.Pt - 1) / a.Pt;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));
-    decoder_tc<<<blocks, kDecThreads, dec->smem, s>>>(a);
+    if (dec->fp32 == 2 && !a.zstore)
+      decoder_tc<true><<<blocks, kDecThreads, dec->smem_split, s>>>(a);
+    else
+      decoder_tc<false><<<blocks, kDecThreads, dec->smem, s>>>(a);
   }
   MPM_CUDA_TRY(cudaGetLastError());
   return MPM_OK;

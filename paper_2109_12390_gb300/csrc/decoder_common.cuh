@@ -26,6 +26,7 @@ struct DecArgs {
   const float* bout;  // (d)
   const float* norm;  // X_min[d], X_range[d], out_shift[d], out_scale[d]
   const uint8_t* wimg;
+  const uint8_t* wimg_lo;   // bf16(w - bf16(w)) images (split operands)
   const float* wsq;   // (n_tc, W, W) FP32 square-layer weights, (out, in) row-major
   const float* wsqT;  // (n_tc, W, W) the same transposed, (in, out) row-major
   const float* X;
@@ -239,10 +240,12 @@ struct mpm_decoder {
   float* bsq = nullptr;               // their biases (n_tc, W)
   float* wsqT = nullptr;              // transposed FP32 copies (n_tc, W, W) for the CUDA-core path
   uint8_t* wimg = nullptr;            // BF16 swizzled images
+  uint8_t* wimg_lo = nullptr;         // residual images bf16(w - bf16(w)) for the split-BF16 path
   uint32_t* status = nullptr;
   int n_sm = 0;
   size_t smem = 0;
-  int fp32 = 0;                       // evaluate square layers in FP32 on the CUDA cores
+  size_t smem_split = 0;
+  int fp32 = 0;                       // square layers: 0 BF16 tensor cores, 1 FP32 CUDA cores, 2 split BF16 tensor cores
   int concurrency = 1;                // expected concurrent calls (FP32 tiling)
 };
 

@@ -92,9 +92,10 @@ class Decoder:
         return out
 
     def set_precision(self, fp32):
-        """fp32=True: square layers in FP32 on the CUDA cores (decoder_eval and reduced-order
-        contexts created afterwards); False: BF16 tensor cores."""
-        _abi.check(_abi.lib().decoder_set_precision(self._h, int(bool(fp32))))
+        """Square-layer arithmetic of decoder_eval and of reduced-order contexts created afterwards:
+        False / 0 BF16 tensor cores, True / 1 FP32 CUDA cores, 2 split BF16 (hi + lo operands,
+        three products) on the tensor cores."""
+        _abi.check(_abi.lib().decoder_set_precision(self._h, int(fp32)))
 
     def set_concurrency(self, k):
         """Expected number of concurrent calls on different streams (FP32 tiling; see

@@ -139,32 +139,41 @@ def rom_error(decoder, scene, fom_xs, *, n_samples=256, seed=4, gn_iters=3, proj
                   status=status, steps=steps, error_percent_at=at)
 
 
-def build_serving_batch(decoders, roms, concurrency):
-    """Sets the decoders' expected concurrency (the FP32 tiling of their calls) and captures the
-    batch of reduced-order contexts (one graph launch per step for all of them)."""
+def build_serving_batch(decoders, roms, concurrency, precision=None):
+    """Sets the decoders' expected concurrency (the FP32 tiling of their calls) and, if given, their
+    square-layer arithmetic (1 FP32 CUDA cores, 2 split BF16 tensor cores), then captures the batch
+    of reduced-order contexts (one graph launch per step for all of them)."""
     from .rom import RomBatch
     for dec in decoders:
         dec.set_concurrency(int(concurrency))
+        if precision is not None:
+            dec.set_precision(int(precision))
     return RomBatch(roms)
 
 
-def autotune_serving(decoders, roms, candidates=(1, 8, 32, 128, 512), trial_steps=4):
-    """Decoder tiling for batched serving, chosen by measurement: for each candidate concurrency k
-    (how many decoder calls are expected to run at once, which sets how many SMs one call's tiles
-    spread over), capture the batch and time `trial_steps` batch steps on the device.  Returns
-    (best k, {k: ms per batch step}).  The trial steps advance the contexts."""
+def autotune_serving(decoders, roms, candidates=(1, 8, 32, 128, 512), precisions=(1, 2), trial_steps=4):
+    """Decoder arithmetic and tiling for batched serving, chosen by measurement: for the FP32
+    CUDA-core arithmetic each candidate concurrency k (how many decoder calls are expected to run
+    at once, which sets how many SMs one call's tiles spread over), and the split-BF16 tensor-core
+    arithmetic (128-row tiles, no tiling choice); each configuration's batch is captured and
+    `trial_steps` batch steps are timed on the device.  Returns ((precision, k) of the fastest,
+    {"precision/k": ms per batch step}).  The trial steps advance the contexts."""
     times = {}
-    for k in candidates:
-        if k > max(1, len(roms)) and k != candidates[0]:
-            continue
-        batch = build_serving_batch(decoders, roms, k)
+    configs = []
+    for prec in precisions:
+        for k in (candidates if prec == 1 else candidates[:1]):
+            if k > max(1, len(roms)) and k != candidates[0]:
+                continue
+            configs.append((int(prec), int(k)))
+    for prec, k in configs:
+        batch = build_serving_batch(decoders, roms, k, prec)
         batch.step(1)                       # first launch: graph upload
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         batch.step(trial_steps)
         b.record()
         torch.cuda.synchronize()
-        times[int(k)] = a.elapsed_time(b) / trial_steps
+        times[(prec, k)] = a.elapsed_time(b) / trial_steps
         batch.close()
     best = min(times, key=times.get)
-    return best, times
+    return best, {f"{p}/{k}": t for (p, k), t in times.items()}

@@ -76,16 +76,38 @@ def perturb_decoder(p, rng):
     return q
 
 
-def sensitivity(fn, args, rng=None, decoder_args=()):
+# Split-BF16 square layers (decoder precision 2): each activation and weight is hi + lo with
+# hi = bf16(v) (|v - hi| <= 2^-9 |v|) and lo the BF16 rounding of v - hi (error <= 2^-18 |v|), and
+# the product keeps A_hi W_hi + A_hi W_lo + A_lo W_hi: the two operand residuals and the dropped
+# A_lo W_lo term are each at most 2^-18 of the product.
+SPLIT_PRODUCT = 3.0 * 2.0 ** -18
+
+
+def perturb_decoder_split(p, rng):
+    """The backward error of the split-BF16 evaluation: the FP32 model of perturb_decoder, with
+    the weights of the square hidden layers (all but the first and the output layer) perturbed
+    by SPLIT_PRODUCT with random signs instead (the error of each product, which does not
+    accumulate over the sum beyond the FP32 rounding already in the model)."""
+    q = perturb_decoder(p, rng)
+    for l in range(1, len(p.W) - 1):
+        q.W[l] = p.W[l] * (1.0 + SPLIT_PRODUCT * rng.choice((-1.0, 1.0), size=p.W[l].shape))
+    return q
+
+
+DECODER_MODELS = {"fp32": perturb_decoder, "split": perturb_decoder_split}
+
+
+def sensitivity(fn, args, rng=None, decoder_args=(), model="fp32"):
     """Relative deviation of fn(*args) when every float array argument is perturbed by one FP32
     ulp (decoder arguments, given by position in decoder_args, have all their parameters
-    perturbed).  Integer arrays (index sets) and scalars are passed unchanged."""
+    perturbed by the backward error of the decoder arithmetic `model`).  Integer arrays (index
+    sets) and scalars are passed unchanged."""
     rng = np.random.default_rng(12345) if rng is None else rng
     base = fn(*args)
     pert = []
     for i, a in enumerate(args):
         if i in decoder_args:
-            pert.append(perturb_decoder(a, rng))
+            pert.append(DECODER_MODELS[model](a, rng))
         elif isinstance(a, np.ndarray) and a.dtype.kind == "f":
             pert.append(perturb(a, rng))
         else:
@@ -132,7 +154,7 @@ def fom_bounds(sc, ref, steps):
 # the comparison measures the GPU's arithmetic, and the bound its sensitivity.
 
 
-def check_trial_velocity(p, rs, xh, vh, samples, x_all, got, label=""):
+def check_trial_velocity(p, rs, xh, vh, samples, x_all, got, label="", model="fp32"):
     """v_trial of Algorithm 5 (the oracle's local step on the GPU's own decoded positions x_all
     and sample set) within the derived bound; returns the oracle's v_trial."""
     import dataclasses
@@ -144,7 +166,7 @@ def check_trial_velocity(p, rs, xh, vh, samples, x_all, got, label=""):
         return OR.local_dynamics(pp, dataclasses.replace(rs32, X=X_), x_, v_, samples, xa_)[0]
 
     sens, ref = sensitivity(fn, (f32_decoder(p), rs32.X, f32(xh), f32(vh), np.asarray(x_all, np.float64)),
-                            decoder_args=(0,))
+                            decoder_args=(0,), model=model)
     err = rel(got, ref)
     print(f"{label} v_trial error {err:.3e} sensitivity {sens:.3e} bound {bound(sens):.3e}")
     assert err < bound(sens), (label, err, sens)
@@ -157,7 +179,7 @@ def check_trial_velocity(p, rs, xh, vh, samples, x_all, got, label=""):
 RIDGE_FLOOR = 1e-10
 
 
-def check_velocity_projection(p, Xs, xh, v_trial, got, label="", ridge=0.0, vhat_n=None):
+def check_velocity_projection(p, Xs, xh, v_trial, got, label="", ridge=0.0, vhat_n=None, model="fp32"):
     """vhat of the velocity least-squares fit (on the GPU's own trial velocities), as the
     increment from vhat_n (zero if None) with ridge max(ridge, 1e-10)."""
     ridge = max(ridge, RIDGE_FLOOR)
@@ -167,14 +189,14 @@ def check_velocity_projection(p, Xs, xh, v_trial, got, label="", ridge=0.0, vhat
         return OR.project_velocity(pp, X_, x_, v_, ridge=ridge, vhat_n=vhat_n)
 
     sens, ref = sensitivity(fn, (f32_decoder(p), f32(Xs), f32(xh), np.asarray(v_trial, np.float64)),
-                            decoder_args=(0,))
+                            decoder_args=(0,), model=model)
     err = rel(got, ref)
     print(f"{label} vhat error {err:.3e} sensitivity {sens:.3e} bound {bound(sens):.3e}")
     assert err < bound(sens), (label, err, sens)
     return ref
 
 
-def line_search_band(p, rec, dt_v):
+def line_search_band(p, rec, dt_v, model="fp32"):
     """Rounding band of the sufficient-decrease margins f(2^-m) - f0 - c 2^-m slope of one
     Gauss-Newton iteration (rec: the oracle's record of it).  The GPU forms every residual row
     from an FP32 secant s = g(xhat) - g(xhat_n) (r = s - dt v_trial), whose relative error is that
@@ -182,12 +204,13 @@ def line_search_band(p, rec, dt_v):
     |r|^2 by 2 r.e to first order, at most 2 |r| |e| <= 2 sqrt(n) u |r| (|r| + |dt v_trial|); the
     band is K times that for the trial and for f0 together."""
     n = max(w.shape[1] for w in p.W)
+    rel_row = np.sqrt(n) * U32 if model == "fp32" else SPLIT_PRODUCT
     rs = np.sqrt(np.maximum(rec["f"], 0.0))
     r0 = np.sqrt(max(rec["f0"], 0.0))
-    return 2.0 * K * np.sqrt(n) * U32 * (rs * (rs + dt_v) + r0 * (r0 + dt_v))
+    return 2.0 * K * rel_row * (rs * (rs + dt_v) + r0 * (r0 + dt_v))
 
 
-def check_line_search_picks(p, records, picks, dt_v, c=1e-4, label=""):
+def check_line_search_picks(p, records, picks, dt_v, c=1e-4, label="", model="fp32"):
     """Every line-search choice of the GPU is a valid outcome of the backtracking rule in exact
     arithmetic up to the rounding band: each trial before the chosen one fails the condition or
     lies within the band, and the chosen one meets it or lies within the band (with -1, none is
@@ -197,7 +220,7 @@ def check_line_search_picks(p, records, picks, dt_v, c=1e-4, label=""):
     for i, (m, rec) in enumerate(zip(picks, records)):
         f = rec["f"]
         margins = f - (rec["f0"] + c * 0.5 ** np.arange(len(f)) * rec["slope"])
-        band = line_search_band(p, rec, dt_v)
+        band = line_search_band(p, rec, dt_v, model)
         last = int(m) if m >= 0 else len(f)
         assert np.all(margins[:last] > -band[:last]), (label, i, m, margins[:last], band[:last])
         if m >= 0:
@@ -208,7 +231,7 @@ def check_line_search_picks(p, records, picks, dt_v, c=1e-4, label=""):
 
 
 def check_gauss_newton_increment(p, Xs, xh, xh_prev, v_trial, dt, got_xh1, iters=3, label="", ridge=0.0,
-                                 picks=None):
+                                 picks=None, model="fp32"):
     """xhat_{n+1} - xhat_n of Algorithm 6 (Gauss-Newton from 2 xhat_n - xhat_{n-1} towards the
     trial positions g(X; xhat_n) + dt v_trial, on the GPU's own trial velocities).  The GPU forms
     the residual as [g(xhat_k) - g(xhat_n)] - dt v_trial (secant rows), never rounding the trial
@@ -234,7 +257,7 @@ def check_gauss_newton_increment(p, Xs, xh, xh_prev, v_trial, dt, got_xh1, iters
         records = []
         x_trial = OD.decode(pf, Xs32, xh) + dt32 * vt
         OR.gauss_newton(pf, Xs32, x_trial, init, iters, ridge=rid, steps=picks, record=records)
-        n_open = check_line_search_picks(pf, records, picks, dt32 * np.linalg.norm(vt), label=label)
+        n_open = check_line_search_picks(pf, records, picks, dt32 * np.linalg.norm(vt), label=label, model=model)
         print(f"{label} line-search choices {[int(m) for m in picks]}, {n_open} of them other than the FP64 "
               f"choice, within the rounding band")
 
@@ -242,7 +265,7 @@ def check_gauss_newton_increment(p, Xs, xh, xh_prev, v_trial, dt, got_xh1, iters
         x_trial = OD.decode(pp, X_, xh_) + dt32 * vt_
         return OR.gauss_newton(pp, X_, x_trial, i_, iters, ridge=rid, steps=picks)[0] - xh_
 
-    sens, ref = sensitivity(fn, (pf, Xs32, xh, vt, init), decoder_args=(0,))
+    sens, ref = sensitivity(fn, (pf, Xs32, xh, vt, init), decoder_args=(0,), model=model)
     err = rel(np.asarray(got_xh1) - xh, ref)
     print(f"{label} GN increment error {err:.3e} sensitivity {sens:.3e} bound {bound(sens):.3e}")
     assert err < bound(sens), (label, err, sens)

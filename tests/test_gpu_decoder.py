@@ -237,6 +237,58 @@ def test_fp32_cuda_core_path_deep_decoder(d, r, n):
     assert 1e-6 < rel(out3[0] - 0.5, g - 0.5) < TOL_BF16
 
 
+@pytest.mark.parametrize("d,r,n", [(2, 16, 1000), (3, 8, 333), (2, 16, 37)])
+def test_split_bf16_tensor_path_deep_decoder(d, r, n):
+    """decoder_set_precision(2): split-BF16 square layers on the tensor cores.  Every row kind
+    (primal, tangents, JVP, latent Jacobian, secant, mixed) against the FP64 oracle within the bound
+    derived from the split arithmetic's backward error (square-layer products perturbed by
+    3 * 2^-18, the rest by the FP32 model; 10 times the oracle's response, at least 1e-5); mixed
+    rows away from the ELU'' jump by more than that error.  The split path must also be well
+    inside the BF16 path's error on the same call."""
+    import fp32_bounds as FB
+    from paper_2109_12390_gb300.decoder import Decoder, PRIMAL, JVP, SECANT, dX, mixed
+    p = _dec_params(d, r, seed=51)
+    dec = Decoder.from_params(p)
+    X, lat, idx = _points(n, d, r, n_lat=3, seed=52)
+    u = 0.3 * np.random.default_rng(53).normal(size=lat.shape)
+    Xg, latg, idxg, ug = _gpu(X.astype(np.float32), lat.astype(np.float32), idx, u.astype(np.float32))
+    Xr = X.astype(np.float32).astype(np.float64)
+    xh = lat.astype(np.float32).astype(np.float64)[idx]
+    uu = u.astype(np.float32).astype(np.float64)[idx]
+    pf = FB.f32_decoder(p)
+    kinds = [PRIMAL] + [dX(k) for k in range(d)] + [JVP] + [mixed(dX(k)) for k in range(d)]
+    dec.set_precision(2)
+    out = dec.eval(Xg, latg, kinds, lat_idx=idxg, dirs=ug).cpu().numpy()
+    out2 = dec.eval(Xg, latg, [PRIMAL] + [dec.dxhat(j) for j in range(r)], lat_idx=idxg).cpu().numpy()
+    sec = dec.eval(Xg, latg, [PRIMAL, SECANT], lat_idx=idxg, dirs=ug).cpu().numpy()[1]
+    assert dec.status() == 0
+
+    def quantities(pp, X_, xh_, uu_):
+        g, JX, Jq = OD.jacobians(pp, X_, xh_)
+        v, G = OD.velocity_gradient(pp, X_, xh_, uu_)
+        return dict(g=g - pp.out_shift, JX=JX, v=v, Jq=Jq, sec=OD.decode(pp, X_, xh_ + uu_) - OD.decode(pp, X_, xh_), G=G)
+
+    ref = quantities(pf, Xr, xh, uu)
+    rng = np.random.default_rng(54)
+    pert = quantities(FB.perturb_decoder_split(pf, rng), FB.perturb(Xr, rng), FB.perturb(xh, rng), FB.perturb(uu, rng))
+    # the split arithmetic moves a pre-activation by up to about 1e-4 of its layer's RMS: points
+    # with one inside 3e-4 RMS of the kink are left out of the mixed rows (about a fifth here,
+    # with 640 pre-activations per point)
+    ok = _away_from_kink(p, Xr, xh, 3e-4)
+    assert ok.sum() >= min(n, 10) and ok.mean() > 0.4, ok.mean()
+    got = dict(g=out[0] - p.out_shift, JX=np.stack(out[1:1 + d], -1), v=out[1 + d], Jq=np.stack(out2[1:], -1),
+               sec=sec, G=np.stack(out[2 + d:], -1))
+    for k in got:
+        sel = ok if k == "G" else slice(None)
+        sens = rel(pert[k][sel], ref[k][sel])
+        err = rel(got[k][sel], ref[k][sel])
+        print(f"split {k}: error {err:.3e} sensitivity {sens:.3e} bound {FB.bound(sens):.3e}")
+        assert err < FB.bound(sens), (k, err, sens)
+    dec.set_precision(0)
+    bf = dec.eval(Xg, latg, [PRIMAL], lat_idx=idxg).cpu().numpy()[0]
+    assert rel(got["g"], ref["g"]) < 0.05 * rel(bf - p.out_shift, ref["g"])
+
+
 def test_linear_and_single_hidden_layer_fp32():
     from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
     for n_hidden, act in [(0, OD.IDENTITY), (1, OD.ELU)]:

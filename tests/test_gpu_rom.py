@@ -300,15 +300,17 @@ def test_config4_scale_step_runs():
     assert step == 20 and np.isfinite(xh1).all()
 
 
-def test_config4_scale_one_step_parity():
+@pytest.mark.parametrize("precision,model", [(1, "fp32"), (2, "split")])
+def test_config4_scale_one_step_parity(precision, model):
     """The reduced step at the benchmark's size and launch configuration (4096 particles, 256
-    samples, r = 16, 5 hidden layers on the FP32 decoder path, 3 Gauss-Newton iterations):
-    sample and neighbour sets bit-exact, the decoded positions, the trial velocities of the local
-    step and the velocity projection against the FP64 oracle."""
+    samples, r = 16, 5 hidden layers, 3 Gauss-Newton iterations), with the FP32 CUDA-core decoder
+    and with the split-BF16 tensor-core decoder: sample and neighbour sets bit-exact, the decoded
+    positions, the trial velocities of the local step, the velocity projection and the
+    Gauss-Newton increment against the FP64 oracle, within the bounds of each arithmetic."""
     from paper_2109_12390_gb300.rom import ROM
     sc, p, dec, rom, rs, xh, vh, xp = _elu_setup(seed=11, side=64, r=16, k=256)
     rom.close()
-    dec.set_precision(True)
+    dec.set_precision(precision)
     rom = ROM.from_scene(dec, sc, n_samples=256, seed=11)
     rom.set_state(xh, vh, xp, 0)
     rom.step(1)
@@ -316,16 +318,21 @@ def test_config4_scale_one_step_parity():
     dbg = rom.debug()
     np.testing.assert_array_equal(dbg["samples"], OR.sample_set(11, 0, 0, len(sc.x), 256))
     xa = dbg["x_all"].astype(np.float64)
-    assert rel(xa - p.out_shift, OD.decode(p, sc.x, xh) - p.out_shift) < 1e-5
+    label = f"config 4 size {model}"
+    sens, ref = FB.sensitivity(lambda pp, X_, x_: OD.decode(pp, X_, x_) - pp.out_shift,
+                               (FB.f32_decoder(p), FB.f32(sc.x), FB.f32(xh)), decoder_args=(0,), model=model)
+    err = rel(xa - p.out_shift, ref)
+    print(f"{label} decoded positions error {err:.3e} sensitivity {sens:.3e}")
+    assert err < FB.bound(sens)
     basis, neigh = OR.neighbourhood(xa, dbg["samples"], sc.dx, sc.n_grid)
     np.testing.assert_array_equal(dbg["neigh"], neigh)
-    FB.check_trial_velocity(p, rs, xh, vh, dbg["samples"], xa, dbg["v_trial"], "config 4 size")
+    FB.check_trial_velocity(p, rs, xh, vh, dbg["samples"], xa, dbg["v_trial"], label, model=model)
     Xs = sc.x[dbg["samples"]]
     vt = dbg["v_trial"].astype(np.float64)
     xh1, vh1, _, _ = rom.get_state()
-    FB.check_velocity_projection(p, Xs, xh, vt, vh1, "config 4 size", vhat_n=vh)
-    FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label="config 4 size",
-                                        picks=rom.line_search_picks())
+    FB.check_velocity_projection(p, Xs, xh, vt, vh1, label, vhat_n=vh, model=model)
+    FB.check_gauss_newton_increment(p, Xs, xh, xp, vt, sc.dt, xh1, label=label,
+                                    picks=rom.line_search_picks(), model=model)
 
 
 def test_metric_accumulate():
