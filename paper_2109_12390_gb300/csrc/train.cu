@@ -470,92 +470,137 @@ __global__ void __launch_bounds__(128, 1) train_dw_gemm(const __nv_bfloat16* zbs
   if (warp == 0) tc::tmem_free<kW>(tmem);
 }
 
-// First-layer weight gradient: dW0[f][j] = sum_rows zb0[f][row] in_row[j]
-// (in_row: normalised input for primal rows, the input direction for tangent rows).
+// First-layer weight gradient dW0[f][j] = sum_rows zbar0[f][row] in[row][j] and the latent
+// adjoints of the primal rows (d loss / d xhat) and of the JVP rows (d loss / d u),
+// sum_f zbar0[f][row] W0[f][d + j], from one pass over zbar0.  in[row] is the layer-0 input of
+// the row: [Xn, xhat] (primal), e_k / X_range_k (X tangent k), [0, u] (JVP).
+// One 128-row training tile at a time (rows k Pt + q: kind k of point q): its 128 x 128 block of
+// zbar0 is staged in shared memory by float4 loads (512 contiguous bytes per feature), the
+// points' inputs beside it.  Thread (f, half) sums the weight gradient of feature f over half
+// of the tile's points in registers for every tile the CTA takes, and adds it to dW0 once;
+// the latent adjoints take (row, 4 latents) per thread.
 constexpr int kMaxIn = 40;
-// First-layer weight gradient dW0[f][j] = sum_rows zbar0[f][row] in[row][j] and the
-// latent adjoints of the primal rows (d loss / d xhat) and of the JVP rows
-// (d loss / d u), sum_f zbar0[f][row] W0[f][d + j], from one pass over zbar0 in
-// chunks of 32 rows staged in shared memory.  in[row] is the layer-0 input of
-// the row: [Xn, xhat] (primal), e_k / X_range_k (X tangent), [0, u] (JVP).
-constexpr int kDw0Rows = 32;
-__global__ void __launch_bounds__(256) train_dw0_lat(const float* zb0, int64_t rows_total, Batch b, int d, int r,
-                                                     int R, int Pt, const float* norm, const float* W0, float* gW0,
-                                                     float* g_lat_pt, float* g_u_pt) {
-  __shared__ float sz[kW][kDw0Rows + 1];
-  __shared__ float sin_[kDw0Rows][kMaxIn + 1];
-  __shared__ float sWl[kW][33];
-  const int t = threadIdx.x;
+constexpr int kDw0Stride = 132;       // floats per staged feature row (128 rows + pad; float4 aligned)
+constexpr int kDw0MaxPt = 64;         // points per tile (R >= 2)
+template <int D>
+__global__ void __launch_bounds__(256) train_dw0_lat(const float* zb0, int64_t rows_total, Batch b, int r, int Pt,
+                                                     const float* norm, const float* W0, float* gW0, float* g_lat_pt,
+                                                     float* g_u_pt) {
+  constexpr int d = D;
+  extern __shared__ __align__(16) float dsm[];
+  float* sz = dsm;                                   // [128 f][kDw0Stride]: zbar0 of the tile's rows
+  float* sin0 = sz + kW * kDw0Stride;                // [kDw0MaxPt][kMaxIn]: primal inputs of the points
+  float* su = sin0 + kDw0MaxPt * kMaxIn;             // [kDw0MaxPt][32]: JVP directions
+  float* sWl = su + kDw0MaxPt * 32;                  // [128][33]: latent columns of W0
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int K = d + r;
-  for (int e = t; e < kW * r; e += blockDim.x) sWl[e / r][e % r] = W0[(e / r) * K + d + (e % r)];
+  for (int e = t; e < kW * r; e += blockDim.x) sWl[(e / r) * 33 + e % r] = W0[(e / r) * K + d + (e % r)];
   const int f = t & (kW - 1), half = t >> 7;
+  const int q_lo = half ? (Pt + 1) / 2 : 0, q_hi = half ? Pt : (Pt + 1) / 2;
+  float inv_range[D];
+#pragma unroll
+  for (int a2 = 0; a2 < D; ++a2) inv_range[a2] = 1.f / norm[D + a2];
   float acc[kMaxIn];
 #pragma unroll
   for (int j = 0; j < kMaxIn; ++j) acc[j] = 0.f;
-  const int64_t n_chunks = (rows_total + kDw0Rows - 1) / kDw0Rows;
-  for (int64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
-    const int64_t row0 = chunk * kDw0Rows;
-    __syncthreads();
-    for (int e = t; e < kW * kDw0Rows; e += blockDim.x) {
-      const int ff = e / kDw0Rows, rr = e % kDw0Rows;
-      sz[ff][rr] = row0 + rr < rows_total ? zb0[(int64_t)ff * rows_total + row0 + rr] : 0.f;
+  const int64_t n_tiles = rows_total / 128;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * 128;
+    __syncthreads();   // the previous tile's staged values are consumed
+    // zbar0 rows of the tile: warp w stages features w, w + 8, ..., one float4 per lane
+    for (int ff = warp; ff < kW; ff += 8) {
+      const float4 v = *reinterpret_cast<const float4*>(zb0 + (int64_t)ff * rows_total + row0 + 4 * lane);
+      *reinterpret_cast<float4*>(sz + ff * kDw0Stride + 4 * lane) = v;
     }
-    for (int e = t; e < kDw0Rows * K; e += blockDim.x) {
-      const int rr = e / K, j = e % K;
-      const int64_t gr = row0 + rr;
-      const int64_t tile = gr / 128;
-      const int tr = (int)(gr % 128), k = tr / Pt, q = tr % Pt;
-      const int64_t p = tile * Pt + q;
+    // the points' primal inputs [Xn, xhat] and JVP directions
+    for (int e = t; e < Pt * kMaxIn; e += blockDim.x) {
+      const int q = e / kMaxIn, j = e % kMaxIn;
+      const int64_t pnt = tile * Pt + q;
       float in = 0.f;
-      if (gr < rows_total && k < R && p < b.B) {
-        if (k == 0) in = j < d ? (b.X[p * d + j] - norm[j]) / norm[d + j] : b.xh[p * r + (j - d)];
-        else if (k <= d) in = (j == k - 1) ? 1.f / norm[d + k - 1] : 0.f;
-        else in = j < d ? 0.f : b.u[p * r + (j - d)];
+      if (pnt < b.B && j < K) in = j < d ? (b.X[pnt * d + j] - norm[j]) / norm[d + j] : b.xh[pnt * r + (j - d)];
+      sin0[q * kMaxIn + j] = in;
+    }
+    for (int e = t; e < Pt * 32; e += blockDim.x) {
+      const int q = e >> 5, j = e & 31;
+      const int64_t pnt = tile * Pt + q;
+      su[e] = (pnt < b.B && j < r) ? b.u[pnt * r + j] : 0.f;
+    }
+    __syncthreads();
+    // (a) weight gradient of feature f over this thread's points (rows of invalid points are zero)
+    const float* zf = sz + f * kDw0Stride;
+    for (int q = q_lo; q < q_hi; ++q) {
+      const float zp = zf[q];                        // primal row
+      const float* in = sin0 + q * kMaxIn;
+#pragma unroll
+      for (int j = 0; j < kMaxIn; j += 4) {
+        if (j < K) {
+          const float4 v = *reinterpret_cast<const float4*>(in + j);
+          acc[j] = fmaf(zp, v.x, acc[j]);
+          acc[j + 1] = fmaf(zp, v.y, acc[j + 1]);
+          acc[j + 2] = fmaf(zp, v.z, acc[j + 2]);
+          acc[j + 3] = fmaf(zp, v.w, acc[j + 3]);
+        }
       }
-      sin_[rr][j] = in;
-    }
-    __syncthreads();
-    // (a) weight gradient: this thread's feature over its half of the rows
-#pragma unroll 4
-    for (int rr = 16 * half; rr < 16 * half + 16; ++rr) {
-      const float z = sz[f][rr];
 #pragma unroll
-      for (int j = 0; j < kMaxIn; ++j)
-        if (j < K) acc[j] = fmaf(z, sin_[rr][j], acc[j]);
+      for (int a2 = 0; a2 < D; ++a2)                 // X-tangent rows: one input each
+        acc[a2] = fmaf(zf[(1 + a2) * Pt + q], inv_range[a2], acc[a2]);
+      const float zj = zf[(D + 1) * Pt + q];         // JVP row: [0, u] (u zero-padded to 32)
+      const float* uq = su + q * 32;
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) {
+        if (j < r) {
+          const float4 v = *reinterpret_cast<const float4*>(uq + j);
+          acc[D + j] = fmaf(zj, v.x, acc[D + j]);
+          acc[D + j + 1] = fmaf(zj, v.y, acc[D + j + 1]);
+          acc[D + j + 2] = fmaf(zj, v.z, acc[D + j + 2]);
+          acc[D + j + 3] = fmaf(zj, v.w, acc[D + j + 3]);
+        }
+      }
     }
-    // (b) latent adjoints of primal and JVP rows
-    for (int o = t; o < kDw0Rows * r; o += blockDim.x) {
-      const int rr = o / r, j = o % r;
-      const int64_t gr = row0 + rr;
-      const int64_t tile = gr / 128;
-      const int tr = (int)(gr % 128), k = tr / Pt, q = tr % Pt;
-      const int64_t p = tile * Pt + q;
-      if (gr >= rows_total || p >= b.B || !(k == 0 || k == d + 1)) continue;
-      float v = 0.f;
+    // (b) latent adjoints of the primal (k = 0) and JVP (k = d + 1) rows: (row, 4 latents) per thread
+    const int n_groups = (r + 3) / 4;
+    for (int o = t; o < 2 * Pt * n_groups; o += blockDim.x) {
+      const int g = o % n_groups, rr = o / n_groups;
+      const int q = rr % Pt, jvp = rr / Pt;
+      const int64_t pnt = tile * Pt + q;
+      const int row = (jvp ? d + 1 : 0) * Pt + q;
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
 #pragma unroll 8
-      for (int ff = 0; ff < kW; ++ff) v = fmaf(sz[ff][rr], sWl[ff][j], v);
-      if (k == 0) g_lat_pt[p * r + j] = v;
-      else g_u_pt[p * r + j] = v;
+      for (int ff = 0; ff < kW; ++ff) {
+        const float z = sz[ff * kDw0Stride + row];
+        const float* w = sWl + ff * 33 + 4 * g;
+        v0 = fmaf(z, w[0], v0);
+        v1 = fmaf(z, w[1], v1);
+        v2 = fmaf(z, w[2], v2);
+        v3 = fmaf(z, w[3], v3);
+      }
+      if (pnt < b.B) {
+        float* dst = (jvp ? g_u_pt : g_lat_pt) + pnt * r + 4 * g;
+        const int nj = min(4, r - 4 * g);
+        if (nj > 0) dst[0] = v0;
+        if (nj > 1) dst[1] = v1;
+        if (nj > 2) dst[2] = v2;
+        if (nj > 3) dst[3] = v3;
+      }
     }
   }
-  // combine the two row halves of each feature, then one atomic per weight
+  // combine the two halves of each feature, then one atomic per weight
   __syncthreads();
-  float* red = &sz[0][0];   // reused as [128][33]: two passes of 32 inputs
+  float* red = sz;   // reused as [128][kMaxIn + 1]
+  if (half == 1) {
 #pragma unroll
-  for (int j0 = 0; j0 < kMaxIn; j0 += 32) {
-    if (half == 1) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j0 + j < kMaxIn) red[f * 33 + j] = acc[j0 + j];
-    }
-    __syncthreads();
-    if (half == 0) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j0 + j < K) atomicAdd(&gW0[f * K + j0 + j], acc[j0 + j] + red[f * 33 + j]);
-    }
-    __syncthreads();
+    for (int j = 0; j < kMaxIn; ++j) red[f * (kMaxIn + 1) + j] = acc[j];
   }
+  __syncthreads();
+  if (half == 0) {
+#pragma unroll
+    for (int j = 0; j < kMaxIn; ++j)
+      if (j < K) atomicAdd(&gW0[f * K + j], acc[j] + red[f * (kMaxIn + 1) + j]);
+  }
+}
+
+size_t dw0_smem_bytes() {
+  return (size_t)(kW * kDw0Stride + kDw0MaxPt * kMaxIn + kDw0MaxPt * 32 + kW * 33) * sizeof(float);
 }
 
 __global__ void train_lat_scatter(Batch b, int r, const float* g_lat_pt, const float* g_u_pt, float dt_snap,
@@ -843,9 +888,14 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
     train_dw_gemm<<<g, 128, 0, s>>>(c->zbstore, c->astore, c->rows_total, kps, c->gparams, c->d_w_off, c->status);
     MPM_CUDA_TRY(cudaGetLastError());
   }
-  train_dw0_lat<<<c->n_sm * 4, 256, 0, s>>>(c->zb0, c->rows_total, c->b, d, r, c->R, c->Pt, dec->norm,
-                                           dec->params + dec->w_off[0], c->gparams + dec->w_off[0], c->g_lat_pt,
-                                           c->g_u_pt);
+  if (d == 2)
+    train_dw0_lat<2><<<c->n_sm * 2, 256, dw0_smem_bytes(), s>>>(c->zb0, c->rows_total, c->b, r, c->Pt, dec->norm,
+                                                               dec->params + dec->w_off[0], c->gparams + dec->w_off[0],
+                                                               c->g_lat_pt, c->g_u_pt);
+  else
+    train_dw0_lat<3><<<c->n_sm * 2, 256, dw0_smem_bytes(), s>>>(c->zb0, c->rows_total, c->b, r, c->Pt, dec->norm,
+                                                               dec->params + dec->w_off[0], c->gparams + dec->w_off[0],
+                                                               c->g_lat_pt, c->g_u_pt);
   MPM_CUDA_TRY(cudaGetLastError());
   train_lat_scatter<<<blocks, 256, 0, s>>>(c->b, r, c->g_lat_pt, c->g_u_pt, c->cfg.dt_snap, c->g_lat);
   MPM_CUDA_TRY(cudaGetLastError());
@@ -1120,6 +1170,8 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   c->bwd_smem = 1024 + kMaxTC * kLayerBytes + kLayerBytes + (size_t)kExchRows * kExchStride * 4 + 128 * 3 * 4 + kW * 4 +
                 sizeof(DecSmemTail);
   MPM_CUDA_TRY(cudaFuncSetAttribute(train_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->bwd_smem));
+  MPM_CUDA_TRY(cudaFuncSetAttribute(train_dw0_lat<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw0_smem_bytes()));
+  MPM_CUDA_TRY(cudaFuncSetAttribute(train_dw0_lat<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw0_smem_bytes()));
   train_pack_transposed<<<std::max(1, dec->n_tc * 64), 256>>>(dec->params, c->d_w_off, dec->n_tc, c->wtimg);
   MPM_CUDA_TRY(cudaGetLastError());
   MPM_CUDA_TRY(cudaDeviceSynchronize());
