@@ -59,7 +59,7 @@ HEADLINE_POLAR_EFT = 1
 # after the pre-roll).  Reads: x, F, particle id and binning permutation (56 B per particle) and
 # the node tiles; v and C are not read (G2P recomputes them).  The written state is still in the
 # write-back L2 when the kernel ends.
-FUSED_DRAM_BYTES_NCU = 16_754_432 + 618_496
+FUSED_DRAM_BYTES_NCU = 16_716_800 + 45_824
 
 
 def _dist():
