@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         float z = sb0[c], zd = 0.f;
         const float* w0r = sW0 + c * kW0Stride;
         if (ri.cls >= 0) {
+          const bool directional = ri.cls != 0;   // primal rows have no directional part
 #pragma unroll
           for (int i4 = 0; i4 < kW0Stride / 4; ++i4) {
             if (4 * i4 < K0) {   // padded weights are zero, as are in[] and dir[] beyond K0
@@ -234,13 +235,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
               z = fmaf(w.y, in[4 * i4 + 1], z);
               z = fmaf(w.z, in[4 * i4 + 2], z);
               z = fmaf(w.w, in[4 * i4 + 3], z);
-            }
-          }
-          if (ri.cls != 0) {   // the directional part: primal rows have none
-#pragma unroll
-            for (int i4 = 0; i4 < kW0Stride / 4; ++i4) {
-              if (4 * i4 < K0) {
-                const float4 w = *reinterpret_cast<const float4*>(w0r + 4 * i4);
+              if (directional) {
                 zd = fmaf(w.x, dir[4 * i4 + 0], zd);
                 zd = fmaf(w.y, dir[4 * i4 + 1], zd);
                 zd = fmaf(w.z, dir[4 * i4 + 2], zd);

@@ -981,6 +981,42 @@ __global__ void mpm_store(DevParams p, StateView src, float* x, float* v, float*
   }
 }
 
+// Binned position of every particle id (the inverse of src.id), for writes in the caller's order.
+__global__ void mpm_inverse_ids(int P, const int32_t* __restrict__ id, int32_t* inv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) inv[id[i]] = i;
+}
+
+// Internal SoA -> one caller array of rows (P, ncomp) holding components comp0 .. comp0 + ncomp - 1,
+// in the caller's particle order: each thread writes four consecutive floats of the flattened
+// array (one 16-byte store when `out` is 16-byte aligned), so that a warp's stores are 512
+// contiguous bytes: the form in which writes to host memory over the chip-to-chip link are whole
+// lines.
+__global__ void mpm_store_rows(int P, StateView src, const int32_t* __restrict__ inv, float* out, int comp0,
+                               int ncomp) {
+  const int64_t total = (int64_t)P * ncomp;
+  const bool vec = ((uintptr_t)out & 15u) == 0;
+  for (int64_t e0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); e0 < total;
+       e0 += 4 * (int64_t)gridDim.x * blockDim.x) {
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t e = e0 + k;
+      v[k] = 0.f;
+      if (e < total) {
+        const int q = (int)(e / ncomp), c = (int)(e % ncomp);
+        v[k] = src.base[(size_t)(comp0 + c) * P + inv[q]];
+      }
+    }
+    if (vec && e0 + 3 < total) {
+      *reinterpret_cast<float4*>(out + e0) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (e0 + k < total) out[e0 + k] = v[k];
+    }
+  }
+}
+
 template <int D>
 __global__ void mpm_bins(DevParams p, StateView src, const int32_t* key, int32_t* cell_keys, int32_t* block_keys) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += gridDim.x * blockDim.x) {
@@ -1048,6 +1084,7 @@ struct mpm_ctx {
   int64_t* d_offs = nullptr;
   uint32_t* status = nullptr;
   float* staging = nullptr;  // AoS x, v, F, C
+  int32_t* inv_id = nullptr; // binned position of every particle id (get_state)
   int32_t* kin_group = nullptr;  // kinematic group per particle (caller's order = particle id)
   float* kin_vel = nullptr;      // prescribed velocity per group (3 floats each)
   int cur = 0, g = 0;
@@ -1263,6 +1300,7 @@ mpm_status mpm_init(const mpm_config* cfg, mpm_ctx** out) {
   if ((st = dalloc(&c->d_offs, c->n_inst + 1)) != MPM_OK) return fail(st);
   if ((st = dalloc(&c->status, 1)) != MPM_OK) return fail(st);
   if ((st = dalloc(&c->staging, comps * c->P)) != MPM_OK) return fail(st);
+  if ((st = dalloc(&c->inv_id, c->P)) != MPM_OK) return fail(st);
   std::vector<float2> ml(c->n_inst);
   for (int k = 0; k < c->n_inst; ++k) {
     double E = c->E[k], nu = c->nu[k];
@@ -1325,6 +1363,7 @@ void mpm_destroy(mpm_ctx* c) {
   cudaFree(c->d_offs);
   cudaFree(c->status);
   cudaFree(c->staging);
+  cudaFree(c->inv_id);
   cudaFree(c->kin_group);
   cudaFree(c->kin_vel);
   delete c;
@@ -1365,20 +1404,52 @@ mpm_status mpm_set_kinematic(mpm_ctx* c, const int32_t* group, int32_t n_groups,
   return MPM_OK;
 }
 
+// A pointer through which kernels may access `p` directly: device or managed memory, or page-locked
+// host memory mapped into the device's address space (read over the host link by the kernel
+// itself); nullptr for pageable host memory, which is staged by a copy.
+static const void* device_view(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    // the mapping covers the allocation: offset of p within it
+    return (const uint8_t*)at.devicePointer + ((const uint8_t*)p - (const uint8_t*)at.hostPointer);
+  }
+  return nullptr;
+}
+
 mpm_status mpm_set_state(mpm_ctx* c, const float* x, const float* v, const float* F, const float* C, void* stream) {
   MPM_CHECK_ARG(c && x && v && F, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int D = c->D, DD = D * D;
   const size_t P = c->P;
-  float* sx = c->staging;
-  float* sv = sx + P * D;
-  float* sF = sv + P * D;
-  float* sC = sF + P * DD;
-  MPM_CUDA_TRY(cudaMemcpyAsync(sx, x, sizeof(float) * P * D, cudaMemcpyDefault, s));
-  MPM_CUDA_TRY(cudaMemcpyAsync(sv, v, sizeof(float) * P * D, cudaMemcpyDefault, s));
-  MPM_CUDA_TRY(cudaMemcpyAsync(sF, F, sizeof(float) * P * DD, cudaMemcpyDefault, s));
+  // device-accessible inputs are read by the load kernel directly; the others are staged
+  const float* sx = (const float*)device_view(x);
+  const float* sv = (const float*)device_view(v);
+  const float* sF = (const float*)device_view(F);
+  const float* sC = (const float*)device_view(C);
+  float* stage = c->staging;
+  if (!sx) {
+    MPM_CUDA_TRY(cudaMemcpyAsync(stage, x, sizeof(float) * P * D, cudaMemcpyDefault, s));
+    sx = stage;
+  }
+  if (!sv) {
+    MPM_CUDA_TRY(cudaMemcpyAsync(stage + P * D, v, sizeof(float) * P * D, cudaMemcpyDefault, s));
+    sv = stage + P * D;
+  }
+  if (!sF) {
+    MPM_CUDA_TRY(cudaMemcpyAsync(stage + 2 * P * D, F, sizeof(float) * P * DD, cudaMemcpyDefault, s));
+    sF = stage + 2 * P * D;
+  }
   const bool zeroC = (C == nullptr) || c->transfer == MPM_TRANSFER_PIC;
-  if (!zeroC) MPM_CUDA_TRY(cudaMemcpyAsync(sC, C, sizeof(float) * P * DD, cudaMemcpyDefault, s));
+  if (!zeroC && !sC) {
+    MPM_CUDA_TRY(cudaMemcpyAsync(stage + 2 * P * D + P * DD, C, sizeof(float) * P * DD, cudaMemcpyDefault, s));
+    sC = stage + 2 * P * D + P * DD;
+  }
   // a fresh start: both grids zero, no pending clears
   for (int b = 0; b < 2; ++b) {
     MPM_CUDA_TRY(cudaMemsetAsync(c->grid[b], 0, sizeof(float4) * (size_t)c->n_inst * c->gnodes, s));
@@ -1507,21 +1578,47 @@ mpm_status mpm_get_state(mpm_ctx* c, float* x, float* v, float* F, float* C, voi
   cudaStream_t s = (cudaStream_t)stream;
   const int D = c->D, DD = D * D;
   const size_t P = c->P;
-  float* sx = c->staging;
-  float* sv = sx + P * D;
-  float* sF = sv + P * D;
-  float* sC = sF + P * DD;
   StateView src{c->state[c->cur], c->id[c->cur]};
   int blocks = std::max(1, std::min(ceil_div(c->P, 256), c->n_sm * 8));
-  if (D == 2)
-    mpm_store<2><<<blocks, 256, 0, s>>>(c->dp, src, sx, sv, sF, sC);
-  else
-    mpm_store<3><<<blocks, 256, 0, s>>>(c->dp, src, sx, sv, sF, sC);
-  MPM_CUDA_TRY(cudaGetLastError());
-  if (x) MPM_CUDA_TRY(cudaMemcpyAsync(x, sx, sizeof(float) * P * D, cudaMemcpyDefault, s));
-  if (v) MPM_CUDA_TRY(cudaMemcpyAsync(v, sv, sizeof(float) * P * D, cudaMemcpyDefault, s));
-  if (F) MPM_CUDA_TRY(cudaMemcpyAsync(F, sF, sizeof(float) * P * DD, cudaMemcpyDefault, s));
-  if (C) MPM_CUDA_TRY(cudaMemcpyAsync(C, sC, sizeof(float) * P * DD, cudaMemcpyDefault, s));
+  // device-accessible outputs are written by the kernels directly, in the caller's order
+  float* const outs[4] = {x, v, F, C};
+  float* views[4];
+  bool any_view = false, any_staged = false;
+  for (int k = 0; k < 4; ++k) {
+    views[k] = (float*)device_view(outs[k]);
+    any_view |= views[k] != nullptr;
+    any_staged |= outs[k] != nullptr && views[k] == nullptr;
+  }
+  if (any_view) {
+    mpm_inverse_ids<<<blocks, 256, 0, s>>>(c->P, src.id, c->inv_id);
+    MPM_CUDA_TRY(cudaGetLastError());
+    const int comp0[4] = {0, D, 2 * D, 2 * D + DD}, ncomp[4] = {D, D, DD, DD};
+    for (int k = 0; k < 4; ++k) {
+      if (!views[k]) continue;
+      const int64_t n4 = ((int64_t)P * ncomp[k] + 3) / 4;
+      const int b = (int)std::max<int64_t>(1, std::min<int64_t>((n4 + 255) / 256, (int64_t)c->n_sm * 8));
+      mpm_store_rows<<<b, 256, 0, s>>>(c->P, src, c->inv_id, views[k], comp0[k], ncomp[k]);
+      MPM_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  if (any_staged) {
+    float* sx = c->staging;
+    float* sv = sx + P * D;
+    float* sF = sv + P * D;
+    float* sC = sF + P * DD;
+    float* st[4] = {sx, sv, sF, sC};
+    for (int k = 0; k < 4; ++k)
+      if (!outs[k] || views[k]) st[k] = nullptr;
+    if (D == 2)
+      mpm_store<2><<<blocks, 256, 0, s>>>(c->dp, src, st[0], st[1], st[2], st[3]);
+    else
+      mpm_store<3><<<blocks, 256, 0, s>>>(c->dp, src, st[0], st[1], st[2], st[3]);
+    MPM_CUDA_TRY(cudaGetLastError());
+    const size_t bytes[4] = {sizeof(float) * P * D, sizeof(float) * P * D, sizeof(float) * P * DD,
+                             sizeof(float) * P * DD};
+    for (int k = 0; k < 4; ++k)
+      if (st[k]) MPM_CUDA_TRY(cudaMemcpyAsync(outs[k], st[k], bytes[k], cudaMemcpyDefault, s));
+  }
   return MPM_OK;
 }
 

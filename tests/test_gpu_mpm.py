@@ -414,3 +414,60 @@ def test_kinematic_boundaries_clamped_bar():
     # the prescribed rows impose a velocity jump at the boundary whose stress waves carry FP32
     # rounding into the free particles' velocities: bounds derived from the oracle's sensitivity
     _compare(ctx, ref, sc, 100)
+
+
+def test_state_transfer_paths_agree():
+    """mpm_set_state / mpm_get_state with pageable host arrays (staged by copies), page-locked host
+    tensors (read and written by the kernels directly over the host link) and CUDA tensors: the
+    round trip of a loaded state returns it bit for bit through every pair of paths; after three
+    steps the state read through every output path (and through an output view that is not
+    16-byte aligned) is bit-identical; states loaded through different paths agree after three
+    steps up to the order of the float atomics."""
+    import torch
+    from paper_2109_12390_gb300.mpm import MPM
+    sc = S.cube_3d(seed=5, side=12, n_grid=32)
+    P, d = len(sc.x), sc.dim
+    host = [np.ascontiguousarray(a, np.float32).reshape(P, -1) for a in (sc.x, sc.v, sc.F, sc.C)]
+
+    def buffers(kind):
+        if kind == "pageable":
+            return [np.empty_like(a) for a in host]
+        return [torch.empty(a.shape, dtype=torch.float32, device="cuda" if kind == "cuda" else "cpu",
+                            pin_memory=(kind == "pinned")) for a in host]
+
+    def numpy(bufs):
+        return [b if isinstance(b, np.ndarray) else b.cpu().numpy() for b in bufs]
+
+    kinds = ("pageable", "pinned", "cuda")
+    stepped = []
+    for kin in kinds:
+        ctx = MPM.from_scene(sc)
+        ins = host if kin == "pageable" else [torch.from_numpy(a).pin_memory() if kin == "pinned"
+                                              else torch.from_numpy(a).cuda() for a in host]
+        ctx.set_state(*ins)
+        for kout in kinds:
+            outs = buffers(kout)
+            ctx.get_state(*outs)
+            torch.cuda.synchronize()
+            for a, b in zip(numpy(outs), host):
+                np.testing.assert_array_equal(a, b)
+        ctx.step(3)
+        reads = []
+        for kout in kinds:
+            outs = buffers(kout)
+            ctx.get_state(*outs)
+            torch.cuda.synchronize()
+            reads.append(numpy(outs))
+        buf = torch.empty(P * d + 1, dtype=torch.float32, pin_memory=True)
+        ctx.get_state(buf[1:].view(P, d))      # starts 4 bytes into a page-locked buffer
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(buf[1:].numpy().reshape(P, d), reads[0][0])
+        for r in reads[1:]:
+            for a, b in zip(r, reads[0]):
+                np.testing.assert_array_equal(a, b)
+        assert ctx.status() == 0
+        stepped.append(reads[0])
+        ctx.close()
+    for r in stepped[1:]:
+        for a, b in zip(r, stepped[0]):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * np.abs(b).max())
