@@ -423,10 +423,13 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 // Per tile:
 //   layer 0       512 / TR threads per row, each 128 TR / 512 columns; inputs
 //                 staged in shared memory first
-//   square layer  128 x TR x 128 FP32 GEMM from shared memory: warp w < TR / 4
-//                 owns slots 4 w .. 4 w + 3, lane l features 4 l .. 4 l + 3
-//                 (one float4 of activations, one of weights per k); weights
-//                 double-buffered from a transposed copy by asynchronous copies
+//   square layer  128 x TR x 128 FP32 GEMM from shared memory: TR / 4 warps,
+//                 warp w features (512 / TR) w .. + 512 / TR - 1 of every slot,
+//                 lane = (slot group of 4, feature group of 4): per k one float4
+//                 of activations and one of weights (two or three shared-memory
+//                 wavefronts per warp for 16 FMAs per lane); weights
+//                 double-buffered from a transposed copy by asynchronous copies;
+//                 activations by warps w < TR / 4, slots 4 w .. 4 w + 3
 //   exchange      pre-activations to a second buffer (row-major, float4 quads
 //                 permuted per row group); derivative rows read the primal
 //                 (and, for mixed rows, JVP and tangent) rows' values as float4
@@ -516,7 +519,7 @@ __device__ __forceinline__ F32Row f32_row(const DecArgs& a, int slot, int64_t ti
 
 template <int TR>
 __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
-  constexpr int G = TR / 4;                   // row groups = GEMM warps
+  constexpr int G = TR / 4;                   // 4-slot groups = GEMM warps = activation warps
   constexpr int TPR = kF32Threads / TR;       // threads per row in layer 0 and the output layer
   constexpr int CPT = kW / TPR;               // layer-0 columns per thread
   extern __shared__ __align__(16) float fsm[];
@@ -527,6 +530,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   float* sb0 = W0T + kW0Stride * kW;          // [128]
   float* sbh = sb0 + kW;                      // [kMaxTC][128]
   float* sWout = sbh + kMaxTC * kW;           // [3][128]
+  F32Row* srow = reinterpret_cast<F32Row*>(sWout + 3 * kW);        // [TR] the tile's rows
+  int64_t* sxrow = reinterpret_cast<int64_t*>(srow + kF32Rows);    // [TR] their X rows
+  int* sli = reinterpret_cast<int*>(sxrow + kF32Rows);             // [TR] their latent rows
   float* IN = A1;                             // [TR][kF32In] normalised inputs (layer 0 only)
   float* DIR = A1 + kF32Rows * kF32In;        // [TR][kF32In] input directions
   const int t = threadIdx.x;
@@ -556,24 +562,33 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
   const int64_t n_pts = dec_count(a);
   const int64_t n_tiles = a.f32_U ? (n_pts * a.R + a.f32_U - 1) / a.f32_U : (n_pts + a.Pt - 1) / a.Pt;
   const int warp = t >> 5, lane = t & 31;
-  const int f0 = 4 * lane;                    // square layers: features f0 .. f0 + 3, slots 4 warp .. 4 warp + 3
+  const int f0 = 4 * lane;                    // activations: features f0 .. f0 + 3 of slots 4 warp .. 4 warp + 3
   const int rw = t % TR, cg = t / TR;         // layer 0: slot rw, columns CPT cg .. CPT cg + CPT - 1
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     if (a.n_tc > 0) prefetch(0);
-    // ---- inputs of the tile's rows
+    // ---- the tile's rows (integer divisions once per slot) and their inputs
+    if (t < TR) {
+      const F32Row fr = f32_row(a, t, tile, n_pts);
+      srow[t] = fr;
+      int64_t xrow = 0;
+      int li = 0;
+      if (fr.ri.cls >= 0) row_source(a, fr.ri, xrow, li);
+      sxrow[t] = xrow;
+      sli[t] = li;
+    }
+    __syncthreads();
     for (int e = t; e < TR * K0; e += kF32Threads) {
       const int slot = e / K0, i = e - slot * K0;
-      const F32Row fr = f32_row(a, slot, tile, n_pts);
+      const F32Row& fr = srow[slot];
       float vin = 0.f, vdir = 0.f;
-      if (fr.ri.cls >= 0) row_input_elem(a, fr.ri, i, vin, vdir);
+      if (fr.ri.cls >= 0) row_input_from(a, fr.ri, sxrow[slot], sli[slot], i, vin, vdir);
       IN[slot * kF32In + i] = vin;
       DIR[slot * kF32In + i] = vdir;
     }
     __syncthreads();
     // ---- layer 0 (FP32)
     {
-      const F32Row fr = f32_row(a, rw, tile, n_pts);
-      const RowInfo& ri = fr.ri;
+      const RowInfo ri = srow[rw].ri;
       float z[CPT], zd[CPT];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
@@ -611,25 +626,27 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
         A0[f32_slot<TR>(col, rw)] = hv;
       }
     }
-    // slot bookkeeping of this warp's 4 GEMM slots
-    F32Row rows[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) rows[j] = f32_row(a, (4 * warp + j) % TR, tile, n_pts);
     for (int l = 0; l < a.n_tc; ++l) {
       cp_async_wait_all();
       __syncthreads();                                  // A0 complete, weights of layer l landed, A1 free
       if (l + 1 < a.n_tc) prefetch(l + 1);              // overlaps the GEMM below
-      float acc[4][4];
       if (warp < G) {
+        // GEMM: lane (sg, fg) of warp w computes slots 4 sg .. 4 sg + 3 and features
+        // fbase .. fbase + 3 (fbase = (512 / TR) w + 4 fg): per k one float4 of activations (eight
+        // or sixteen distinct in the warp) and one of weights (four or two distinct)
+        constexpr int FG = 128 / TR;                  // feature groups per warp
+        const int sg = lane / FG, fg = lane % FG;
+        const int fbase = (512 / TR) * warp + 4 * fg;
         const float* Wt = Wt0 + (l & 1) * kW * kW;
+        float acc[4][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
           for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
 #pragma unroll 8
         for (int k = 0; k < kW; ++k) {
-          const float4 av = *reinterpret_cast<const float4*>(A0 + k * TR + 4 * (warp ^ (k & (G - 1))));
-          const float4 wv = *reinterpret_cast<const float4*>(Wt + k * kW + f0);
+          const float4 av = *reinterpret_cast<const float4*>(A0 + k * TR + 4 * (sg ^ (k & (G - 1))));
+          const float4 wv = *reinterpret_cast<const float4*>(Wt + k * kW + fbase);
           const float ar[4] = {av.x, av.y, av.z, av.w};
           const float wr[4] = {wv.x, wv.y, wv.z, wv.w};
 #pragma unroll
@@ -638,31 +655,35 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
             for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(ar[j], wr[i], acc[j][i]);
         }
         // pre-activations (bias on primal rows) to A1
-        const float4 b4 = *reinterpret_cast<const float4*>(sbh + l * kW + f0);
+        const float4 b4 = *reinterpret_cast<const float4*>(sbh + l * kW + fbase);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (rows[j].ri.cls == 0) {
+          if (srow[4 * sg + j].ri.cls == 0) {
             acc[j][0] += b4.x;
             acc[j][1] += b4.y;
             acc[j][2] += b4.z;
             acc[j][3] += b4.w;
           }
-          *reinterpret_cast<float4*>(A1 + f32_zslot(4 * warp + j, f0)) =
+          *reinterpret_cast<float4*>(A1 + f32_zslot(4 * sg + j, fbase)) =
               make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
         }
       }
       __syncthreads();                                  // A1 complete, every GEMM has read A0
       if (warp < G) {
-        // activations of the next layer into A0; derivative rows read their partners' values
+        // activations of the next layer into A0 (warp w: slots 4 w .. 4 w + 3); derivative rows
+        // read their partners' pre-activations
+        float h[4][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const F32Row& fr = rows[j];
+          const F32Row& fr = srow[4 * warp + j];
+          const float4 z4 = *reinterpret_cast<const float4*>(A1 + f32_zslot(4 * warp + j, f0));
+          const float zr[4] = {z4.x, z4.y, z4.z, z4.w};
           if (fr.ri.cls == 0) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[j][i] = act_f32path(a.act, acc[j][i]);
+            for (int i = 0; i < 4; ++i) h[j][i] = act_f32path(a.act, zr[i]);
           } else if (fr.ri.cls < 0) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+            for (int i = 0; i < 4; ++i) h[j][i] = 0.f;
           } else {
             const float4 q4 = *reinterpret_cast<const float4*>(A1 + f32_zslot(fr.qs, f0));
             float4 a4 = q4, c4 = q4;
@@ -670,23 +691,23 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
               a4 = *reinterpret_cast<const float4*>(A1 + f32_zslot(fr.as, f0));
               c4 = *reinterpret_cast<const float4*>(A1 + f32_zslot(fr.bs, f0));
             }
-            acc[j][0] = f32_deriv_act(a.act, fr.ri.cls, acc[j][0], q4.x, a4.x, c4.x);
-            acc[j][1] = f32_deriv_act(a.act, fr.ri.cls, acc[j][1], q4.y, a4.y, c4.y);
-            acc[j][2] = f32_deriv_act(a.act, fr.ri.cls, acc[j][2], q4.z, a4.z, c4.z);
-            acc[j][3] = f32_deriv_act(a.act, fr.ri.cls, acc[j][3], q4.w, a4.w, c4.w);
+            h[j][0] = f32_deriv_act(a.act, fr.ri.cls, zr[0], q4.x, a4.x, c4.x);
+            h[j][1] = f32_deriv_act(a.act, fr.ri.cls, zr[1], q4.y, a4.y, c4.y);
+            h[j][2] = f32_deriv_act(a.act, fr.ri.cls, zr[2], q4.z, a4.z, c4.z);
+            h[j][3] = f32_deriv_act(a.act, fr.ri.cls, zr[3], q4.w, a4.w, c4.w);
           }
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
           *reinterpret_cast<float4*>(A0 + f32_slot<TR>(f0 + i, 4 * warp)) =
-              make_float4(acc[0][i], acc[1][i], acc[2][i], acc[3][i]);
+              make_float4(h[0][i], h[1][i], h[2][i], h[3][i]);
       }
     }
     __syncthreads();                                    // A0 complete
     // ---- output layer (FP32): TPR threads per row, k interleaved, combined by shuffles
     {
       const int slot = t / TPR, part = t % TPR;
-      const F32Row fr = f32_row(a, slot, tile, n_pts);
+      const F32Row fr = srow[slot];
       float y[3] = {0.f, 0.f, 0.f};
 #pragma unroll 4
       for (int kk = 0; kk < kW / TPR; ++kk) {
@@ -764,7 +785,8 @@ size_t dec_smem_bytes(bool split) {
 }
 
 size_t dec_f32_smem_bytes() {
-  return (size_t)(2 * kW * kF32Rows + 2 * kW * kW + kW0Stride * kW + kW + kMaxTC * kW + 3 * kW) * sizeof(float);
+  return (size_t)(2 * kW * kF32Rows + 2 * kW * kW + kW0Stride * kW + kW + kMaxTC * kW + 3 * kW) * sizeof(float) +
+         kF32Rows * (sizeof(F32Row) + sizeof(int64_t) + sizeof(int));
 }
 
 mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {

@@ -175,17 +175,22 @@ __device__ __forceinline__ void row_inputs(const DecArgs& a, const RowInfo& ri, 
   }
 }
 
-// Entry i (< d + r) of row_inputs: normalised input and direction of one row.
-__device__ __forceinline__ void row_input_elem(const DecArgs& a, const RowInfo& ri, int i, float& vin, float& vdir) {
-  const int d = a.d, r = a.r;
-  int64_t xrow = ri.p;
-  int li = a.lat ? a.lat[ri.p] : (a.lat_per_point ? (int)ri.p : 0);
+// Row of X and latent row of the point of `ri`.
+__device__ __forceinline__ void row_source(const DecArgs& a, const RowInfo& ri, int64_t& xrow, int& li) {
+  xrow = ri.p;
+  li = a.lat ? a.lat[ri.p] : (a.lat_per_point ? (int)ri.p : 0);
   if (a.n_dev) {
     const int cnt = max(*a.n_dev, 1);
     xrow = ri.p % cnt;
     li = (int)(ri.p / cnt);
     if (a.idx) xrow = a.idx[xrow];
   }
+}
+
+// Input i of the row's layer-0 input and direction, from its point's sources (row_source).
+__device__ __forceinline__ void row_input_from(const DecArgs& a, const RowInfo& ri, int64_t xrow, int li, int i,
+                                               float& vin, float& vdir) {
+  const int d = a.d, r = a.r;
   vin = i < d ? (a.X[xrow * d + i] - a.norm[i]) / a.norm[d + i] : a.latents[(int64_t)li * r + (i - d)];
   vdir = 0.f;
   if (ri.cls == 1) {
@@ -194,6 +199,14 @@ __device__ __forceinline__ void row_input_elem(const DecArgs& a, const RowInfo& 
   } else if ((ri.cls == 2 || ri.cls == 3) && i >= d) {
     vdir = a.dirs[dir_offset(a, ri.kind, li) + (i - d)];
   }
+}
+
+// Entry i (< d + r) of row_inputs: normalised input and direction of one row.
+__device__ __forceinline__ void row_input_elem(const DecArgs& a, const RowInfo& ri, int i, float& vin, float& vdir) {
+  int64_t xrow;
+  int li;
+  row_source(a, ri, xrow, li);
+  row_input_from(a, ri, xrow, li, i, vin, vdir);
 }
 
 // Layer-0 tangent of a mixed row along input b (the normalised X axes scale by
