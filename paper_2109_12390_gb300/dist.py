@@ -1,8 +1,11 @@
 """Multi-process helpers for running the step on several GPUs of one node (one process per GPU).
 
 The full-order and reduced-order steps do not exchange data between GPUs: a batch of independent
-instances is split into contiguous ranges of whole instances (`shard_instances`), and the only
-collective is the reduction of timings or error sums (`max_over_ranks`, `sum_over_ranks`).
+instances is split into contiguous ranges of whole instances (`shard_instances`, `scene_shard`),
+and the only collective of a run is the reduction of timings or error sums (`max_over_ranks`,
+`sum_over_ranks`).  Batched snapshot generation (`generate_snapshots_sharded`) steps each rank's
+instances alone, then gathers the snapshot stores once so that every rank holds the whole store,
+in instance order, for data-parallel training.
 Decoder training is data-parallel: each rank draws a contiguous range of the step's minibatch
 (`shard_minibatch`), its gradients are normalised by the whole minibatch, and one sum over the
 ranks (`allreduce_gradients`) of the decoder's and the latents' gradients precedes every update
@@ -79,3 +82,63 @@ def train_data_parallel(trainer, n_steps: int) -> None:
         trainer.compute_gradients(g_params, g_second)
         allreduce_gradients(g_params, g_second)
         trainer.apply_gradients(g_params, g_second)
+
+
+def scene_shard(scene, rank: int, world: int):
+    """This rank's whole instances of a batched scene (a contiguous range, shard_instances): the
+    sub-scene and its (lo, hi) instance range."""
+    lo, hi = shard_instances(scene.n_inst, rank, world)
+    return scene.subset_instances(range(lo, hi)), (lo, hi)
+
+
+def gather_instance_rows(local: torch.Tensor) -> torch.Tensor:
+    """All ranks' (J, P_rank, c) arrays of per-particle rows, concatenated along the particle axis
+    in rank order (the instance order of scene_shard): one all-gather of arrays padded to the
+    largest shard.  Returns `local` itself on one rank."""
+    import torch.distributed as dist
+    rank, world = _world()
+    if world == 1:
+        return local
+    n = torch.tensor([local.shape[1]], dtype=torch.int64, device=local.device)
+    sizes = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(sizes, n)
+    sizes = [int(t.item()) for t in sizes]
+    pmax = max(sizes)
+    pad = torch.zeros((local.shape[0], pmax, local.shape[2]), dtype=local.dtype, device=local.device)
+    pad[:, :local.shape[1]] = local
+    parts = [torch.empty_like(pad) for _ in range(world)]
+    dist.all_gather(parts, pad)
+    return torch.cat([p[:, :m] for p, m in zip(parts, sizes)], dim=1)
+
+
+def generate_snapshots_sharded(scene, n_steps: int, every: int, device="cuda"):
+    """Batched snapshot generation over the ranks: each rank steps its own whole instances
+    (scene_shard, no exchange while stepping), then x, v and F are gathered once
+    (gather_instance_rows) so that every rank returns the store of the whole scene, in the layout
+    of train.generate_snapshots.  The status word is OR-ed over the ranks."""
+    import numpy as np
+    import torch.distributed as dist
+    from .train import generate_snapshots
+    rank, world = _world()
+    if world == 1:
+        return generate_snapshots(scene, n_steps, every, device)
+    sub, _ = scene_shard(scene, rank, world)
+    part = generate_snapshots(sub, n_steps, every, device)
+    J = n_steps // every + 1
+    d = scene.dim
+    full = {k: gather_instance_rows(part[k].reshape(J, -1, part[k].shape[-1])).reshape(-1, part[k].shape[-1])
+            for k in ("x", "v", "F")}
+    st = torch.tensor([int(part["status"])], dtype=torch.int64, device=part["x"].device)
+    words = [torch.zeros_like(st) for _ in range(world)]
+    dist.all_gather(words, st)
+    status = 0
+    for w in words:
+        status |= int(w.item())
+    n_inst = scene.n_inst
+    S = J * n_inst
+    snap_inst = np.array([s % n_inst for s in range(S)], np.int32)
+    snap_next = np.array([s + n_inst if s + n_inst < S else -1 for s in range(S)], np.int32)
+    return dict(dim=d, n_inst=n_inst, inst_offsets=np.ascontiguousarray(scene.inst_offsets, np.int64),
+                X=torch.from_numpy(scene.x.astype(np.float32)).to(device), n_snap=S, snap_inst=snap_inst,
+                snap_next=snap_next, x=full["x"], v=full["v"], F=full["F"], status=status,
+                steps_between=every, dt_snap=part["dt_snap"])

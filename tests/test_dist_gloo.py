@@ -130,3 +130,55 @@ def test_two_gloo_ranks_data_parallel_gradients_equal_the_whole_minibatch():
     want = np.concatenate([g.ravel() for g in gW + gb] + [gl.ravel()])
     for _, got in out:
         np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+
+
+def _shard_worker(rank, world, port, q):
+    import numpy as np
+    import oracle.mpm as OM
+    import synth.scenes as S
+    from paper_2109_12390_gb300.dist import gather_instance_rows, scene_shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sc = S.batch_2d(seed=9, n_inst=5, count_range=(60, 200), n_grid=32, origin_y=0.1)
+    sub, (lo, hi) = scene_shard(sc, rank, world)
+    J = 3
+    xs = []
+    for j in range(J):
+        if j:
+            OM.step(sub, 4)
+        xs.append(sub.x.copy())
+    local = torch.from_numpy(np.stack(xs))                     # (J, P_rank, d)
+    full = gather_instance_rows(local)
+    q.put((rank, lo, hi, full.numpy()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_a_batched_run_and_gather_rows():
+    """Instance sharding of a batched full-order run: two gloo ranks step their own whole instances
+    with the FP64 oracle (no exchange while stepping) and gather the per-particle rows once; both
+    ranks then hold exactly the rows of the unsharded run, in instance order."""
+    import numpy as np
+    import oracle.mpm as OM
+    import synth.scenes as S
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=300) for _ in procs), key=lambda o: o[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    sc = S.batch_2d(seed=9, n_inst=5, count_range=(60, 200), n_grid=32, origin_y=0.1)
+    ref = []
+    for j in range(3):
+        if j:
+            OM.step(sc, 4)
+        ref.append(sc.x.copy())
+    ref = np.stack(ref)
+    assert [(o[1], o[2]) for o in out] == [(0, 3), (3, 5)]
+    for o in out:
+        np.testing.assert_array_equal(o[3], ref)

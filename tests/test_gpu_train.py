@@ -190,3 +190,27 @@ def test_data_parallel_shards_sum_to_the_whole_minibatch():
     for t in shards:
         assert t.loss()[1] == 1 and t.status() == 0
     np.testing.assert_array_equal(shards[0].latents(), shards[1].latents())
+
+
+def test_instance_sharded_snapshots_match_the_whole_batch():
+    """Batched snapshot generation sharded by whole instances (dist.scene_shard), the shards run one
+    after the other on this GPU as two ranks would run them: concatenated in rank order, the
+    snapshots equal those of the whole batch in one context up to the order of float atomics (the
+    bound is ten times the difference between two runs of the whole batch, at least 1e-6 of the
+    state's scale)."""
+    import torch
+    from paper_2109_12390_gb300.dist import scene_shard
+    from paper_2109_12390_gb300.train import generate_snapshots
+    sc = S.batch_2d(seed=9, n_inst=5, count_range=(3000, 9000), n_grid=128, origin_y=0.06)
+    steps, every = 200, 50
+    J = steps // every + 1
+    full = generate_snapshots(sc, steps, every)
+    twin = generate_snapshots(sc, steps, every)
+    assert full["status"] == 0
+    parts = [generate_snapshots(scene_shard(sc, r, 2)[0], steps, every) for r in range(2)]
+    for key, c in (("x", 2), ("v", 2), ("F", 4)):
+        cat = torch.cat([p[key].reshape(J, -1, c) for p in parts], dim=1).reshape(-1, c).cpu().numpy()
+        ref = full[key].cpu().numpy()
+        noise = np.abs(twin[key].cpu().numpy() - ref).max()
+        scale = np.abs(ref).max()
+        assert np.abs(cat - ref).max() <= max(10 * noise, 1e-6 * scale), key
