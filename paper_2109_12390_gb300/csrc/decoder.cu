@@ -219,39 +219,58 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 
     // ---- layer 0 on the CUDA cores (FP32), this thread's 64 columns, 8 at a time
     for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 8) {
-      float hv[8];
+      // the 8 columns' sums advance together over the inputs (16 independent chains), so that
+      // their FMAs and the broadcast weight loads overlap instead of running column by column
+      float z[8], zd[8], hv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        z[j] = sb0[c0 + j];
+        zd[j] = 0.f;
+      }
+      if (ri.cls == 0) {   // primal rows: no directional part
+#pragma unroll
+        for (int i4 = 0; i4 < kW0Stride / 4; ++i4) {
+          if (4 * i4 < K0) {   // padded weights are zero, as are in[] and dir[] beyond K0
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float4 w = *reinterpret_cast<const float4*>(sW0 + (c0 + j) * kW0Stride + 4 * i4);
+              z[j] = fmaf(w.x, in[4 * i4 + 0], z[j]);
+              z[j] = fmaf(w.y, in[4 * i4 + 1], z[j]);
+              z[j] = fmaf(w.z, in[4 * i4 + 2], z[j]);
+              z[j] = fmaf(w.w, in[4 * i4 + 3], z[j]);
+            }
+          }
+        }
+      } else if (ri.cls > 0) {
+#pragma unroll
+        for (int i4 = 0; i4 < kW0Stride / 4; ++i4) {
+          if (4 * i4 < K0) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float4 w = *reinterpret_cast<const float4*>(sW0 + (c0 + j) * kW0Stride + 4 * i4);
+              z[j] = fmaf(w.x, in[4 * i4 + 0], z[j]);
+              z[j] = fmaf(w.y, in[4 * i4 + 1], z[j]);
+              z[j] = fmaf(w.z, in[4 * i4 + 2], z[j]);
+              z[j] = fmaf(w.w, in[4 * i4 + 3], z[j]);
+              zd[j] = fmaf(w.x, dir[4 * i4 + 0], zd[j]);
+              zd[j] = fmaf(w.y, dir[4 * i4 + 1], zd[j]);
+              zd[j] = fmaf(w.z, dir[4 * i4 + 2], zd[j]);
+              zd[j] = fmaf(w.w, dir[4 * i4 + 3], zd[j]);
+            }
+          }
+        }
+      }
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int c = c0 + j;
-        float z = sb0[c], zd = 0.f;
-        const float* w0r = sW0 + c * kW0Stride;
-        if (ri.cls >= 0) {
-          const bool directional = ri.cls != 0;   // primal rows have no directional part
-#pragma unroll
-          for (int i4 = 0; i4 < kW0Stride / 4; ++i4) {
-            if (4 * i4 < K0) {   // padded weights are zero, as are in[] and dir[] beyond K0
-              const float4 w = *reinterpret_cast<const float4*>(w0r + 4 * i4);
-              z = fmaf(w.x, in[4 * i4 + 0], z);
-              z = fmaf(w.y, in[4 * i4 + 1], z);
-              z = fmaf(w.z, in[4 * i4 + 2], z);
-              z = fmaf(w.w, in[4 * i4 + 3], z);
-              if (directional) {
-                zd = fmaf(w.x, dir[4 * i4 + 0], zd);
-                zd = fmaf(w.y, dir[4 * i4 + 1], zd);
-                zd = fmaf(w.z, dir[4 * i4 + 2], zd);
-                zd = fmaf(w.w, dir[4 * i4 + 3], zd);
-              }
-            }
-          }
-          if (ri.cls == 0) hv[j] = a.act == 0 ? (SPLIT ? elu(z) : elu_bf16_input(z)) : z;
-          else if (ri.cls == 1) hv[j] = act_d1(a.act, z) * zd;
-          else if (ri.cls == 2) hv[j] = act_sec(a.act, z, zd);
-          else hv[j] = act_d2(a.act, z) * zd * mixed_t0(a, w0r, ri.kind);
-          if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + rw] = ri.cls == 0 ? z : zd;
-        } else {
-          hv[j] = 0.f;
-          if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + rw] = 0.f;
-        }
+        float zv = 0.f;
+        if (ri.cls < 0) hv[j] = 0.f;
+        else if (ri.cls == 0) hv[j] = a.act == 0 ? (SPLIT ? elu(z[j]) : elu_bf16_input(z[j])) : z[j];
+        else if (ri.cls == 1) hv[j] = act_d1(a.act, z[j]) * zd[j];
+        else if (ri.cls == 2) hv[j] = act_sec(a.act, z[j], zd[j]);
+        else hv[j] = act_d2(a.act, z[j]) * zd[j] * mixed_t0(a, sW0 + c * kW0Stride, ri.kind);
+        if (ri.cls >= 0) zv = ri.cls == 0 ? z[j] : zd[j];
+        if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + rw] = zv;
         if (a.astore) a.astore[(int64_t)c * a.rows_total + tile * 128 + rw] = __float2bfloat16_rn(hv[j]);
       }
       store_operand<SPLIT>(atile, rw, c0, hv);
