@@ -142,7 +142,15 @@ struct BwdArgs {
 
 constexpr int kExchRows = 104;
 constexpr int kBwdMaxR = 5;           // rows per point in training: primal, d <= 3 tangents, JVP
-constexpr int kExchStride = kW + 1;   // padded row stride: lanes of a warp hit distinct banks
+constexpr int kChunkStride = 33;      // padded row stride of one 32-feature chunk: distinct banks
+
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_groups() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // 256 threads: warps w and w + 4 read the same tensor-memory lane group; thread
 // t owns tile row rw = 32 (w % 4) + lane and the feature half h = w / 4
@@ -154,15 +162,16 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* wt = smem;                                 // n_tc x 32 KB (transposed square weights)
   uint8_t* atile = smem + kMaxTC * kLayerBytes;       // 32 KB
-  float* exch = (float*)(atile + kLayerBytes);        // kExchRows x 129
-  float* sy = exch + kExchRows * kExchStride;         // 128 x 3
+  float* exch = (float*)(atile + kLayerBytes);        // [2 halves][kExchRows][33]: tangent-row terms of the chunk
+  float* stg = exch + 2 * kExchRows * kChunkStride;   // [2 halves][128 rows][33]: pre-activations of the chunk
+  float* sy = stg + 2 * 128 * kChunkStride;           // 128 x 3
   float* sbias = sy + 128 * 3;                        // 128
   DecSmemTail* tail = (DecSmemTail*)(sbias + kW);
   __shared__ double s_loss[8];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int rw = (warp & 3) * 32 + lane;              // tile row / tensor-memory lane
   const int h = warp >> 2;                            // feature half
-  const int d = a.d, r = a.r, R = a.R, Pt = a.Pt;
+  const int d = a.d, R = a.R, Pt = a.Pt;
 
   if (t == 0) {
     tc::mbar_init(&tail->bar_w, 1);
@@ -198,7 +207,17 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
     const int64_t p = tile * Pt + q;
     const bool valid = (k < R) && (p < a.n);
     const int cls = !valid ? -1 : (k == 0 ? 0 : 1);
-    const int64_t gr = row0 + rw, gp = row0 + q;
+    const int64_t gr = row0 + rw;
+    // this row's pre-activations of (layer lz, chunk chz) into the staging buffer, copied
+    // asynchronously (one chunk ahead of its use, so that the loads overlap the current chunk)
+    float* my_stg = stg + (h * 128 + rw) * kChunkStride;
+    auto prefetch_z = [&](int lz, int chz) {
+      const float* src = a.zstore + ((int64_t)lz * kW + chz * 32) * a.rows_total + gr;
+#pragma unroll 8
+      for (int i = 0; i < 32; ++i) cp_async4(my_stg + i, src + (int64_t)i * a.rows_total);
+      cp_async_commit_group();
+    };
+    prefetch_z(a.n_hidden - 1, 2 * h);
     // ---- output layer: residual adjoints ybar (FP32)
     float ybar[3] = {0.f, 0.f, 0.f};
     if (valid) {
@@ -263,9 +282,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
         mma_phase ^= 1u;
         tc::tc_fence_after();
       }
+      cp_async_wait_groups();   // this row's staged pre-activations of the chunk have landed
       __syncthreads();
       if (tail->abort) break;
-      const float* zl = a.zstore + (int64_t)l * kW * a.rows_total;
       for (int i2 = 0; i2 < 2; ++i2) {
         const int ch = 2 * h + i2;
         float hb[32];
@@ -282,34 +301,35 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
           }
         }
         float zb[32];
-        // pre-activations of this chunk: the point's primal z (every row) and the row's own
-        // tangent zdot (tangent rows), all loads issued before the exchange barrier
-        float zpv[32], zrv[32];
-        if (cls >= 0) {
+        // pre-activations of this chunk from the staging buffer: the row's own (z for primal
+        // rows, zdot for tangent rows) and, for tangent rows, their point's primal z (row q)
+        float zown[32];
+        const float* hstg = stg + h * 128 * kChunkStride;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) zpv[i] = zl[(int64_t)(ch * 32 + i) * a.rows_total + gp];
-        }
+        for (int i = 0; i < 32; ++i) zown[i] = my_stg[i];
+        float* hexch = exch + h * kExchRows * kChunkStride;
         if (cls == 1) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) zrv[i] = zl[(int64_t)(ch * 32 + i) * a.rows_total + gr];
-#pragma unroll
           for (int i = 0; i < 32; ++i) {
-            const int f = ch * 32 + i;
-            zb[i] = act_d1(a.act, zpv[i]) * hb[i];
-            exch[(rw - Pt) * kExchStride + f] = act_d2(a.act, zpv[i]) * zrv[i] * hb[i];
+            const float zp = hstg[q * kChunkStride + i];
+            zb[i] = act_d1(a.act, zp) * hb[i];
+            hexch[(rw - Pt) * kChunkStride + i] = act_d2(a.act, zp) * zown[i] * hb[i];
           }
         }
         __syncthreads();
+        // every row has read the staged chunk: stage the next one (this layer's other chunk of
+        // this half, or the next layer's first)
+        if (i2 == 0) prefetch_z(l, ch + 1);
+        else if (l > 0) prefetch_z(l - 1, 2 * h);
         if (cls == 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            const int f = ch * 32 + i;
-            float sacc = act_d1(a.act, zpv[i]) * hb[i];
+            float sacc = act_d1(a.act, zown[i]) * hb[i];
             // compile-time bound (R <= kBwdMaxR): with the runtime bound this loop, inside the
             // unrolled feature loop, ran about 1,000 cycles per feature
 #pragma unroll
             for (int kk = 1; kk < kBwdMaxR; ++kk)
-              if (kk < R) sacc += exch[((kk - 1) * Pt + q) * kExchStride + f];
+              if (kk < R) sacc += hexch[((kk - 1) * Pt + q) * kChunkStride + i];
             zb[i] = sacc;
           }
         } else if (cls < 0) {
@@ -348,6 +368,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) zs[(int64_t)(ch * 32 + i) * a.rows_total] = zb[i];
         }
+        if (i2 == 0) cp_async_wait_groups();   // the next chunk's staging has landed
         __syncthreads();
       }
       // bias gradient of layer l (sbias was filled before the last barrier)
@@ -387,6 +408,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
     for (int w = 0; w < kBwdThreads / 32; ++w) tot += s_loss[w];
     atomicAdd(a.loss, tot);
   }
+  cp_async_wait_groups();   // no staging copy outlives the CTA (an aborted sweep)
   tc::tc_fence_after();
   if (warp == 0) tc::tmem_free<kW>(tmem);
 }
@@ -1167,8 +1189,8 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   c->st.x = c->sx;
   c->st.v = c->sv;
   c->st.F = c->sF;
-  c->bwd_smem = 1024 + kMaxTC * kLayerBytes + kLayerBytes + (size_t)kExchRows * kExchStride * 4 + 128 * 3 * 4 + kW * 4 +
-                sizeof(DecSmemTail);
+  c->bwd_smem = 1024 + kMaxTC * kLayerBytes + kLayerBytes + (size_t)(2 * kExchRows + 2 * 128) * kChunkStride * 4 +
+                128 * 3 * 4 + kW * 4 + sizeof(DecSmemTail);
   MPM_CUDA_TRY(cudaFuncSetAttribute(train_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->bwd_smem));
   MPM_CUDA_TRY(cudaFuncSetAttribute(train_dw0_lat<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw0_smem_bytes()));
   MPM_CUDA_TRY(cudaFuncSetAttribute(train_dw0_lat<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw0_smem_bytes()));
