@@ -284,7 +284,8 @@ mpm_status mpm_debug_grid(mpm_ctx* ctx, float* mass, float* momentum, float* vel
 
 /*
  *   d           spatial dimension (2 or 3).
- *   r           latent dimension (d + r <= 40).
+ *   r           latent dimension (d + r <= 40; with r > 36 every evaluation runs in FP32 on
+ *               the CUDA cores, as the tensor-core kernel holds 36 latents).
  *   width       hidden width; must be 128 when n_hidden >= 1.
  *   n_hidden    number of hidden (activated) layers, 0..5.  0 is the linear
  *               manifold of Section 5 (one linear map, no activation).

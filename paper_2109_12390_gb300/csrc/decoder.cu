@@ -174,9 +174,11 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
   // every row of every tile)
   {
     const int K0s = a.d + a.r;
+    // the tensor-core input layout (row_inputs_tc): coordinates at 0 .. 3, latents from kTcLat
     for (int e = t; e < kW * kW0Stride; e += kDecThreads) {
-      const int c = e / kW0Stride, i = e % kW0Stride;
-      sW0[e] = i < K0s ? a.W0[c * K0s + i] : 0.f;
+      const int c = e / kW0Stride, ii = e % kW0Stride;
+      const int i = ii < kTcLat ? (ii < a.d ? ii : -1) : (ii - kTcLat < a.r ? a.d + ii - kTcLat : -1);
+      sW0[e] = i >= 0 ? a.W0[c * K0s + i] : 0.f;
     }
     for (int e = t; e < kW; e += kDecThreads) sb0[e] = a.b0[e];
     for (int e = t; e < a.n_tc * kW; e += kDecThreads) sbh[e] = a.bh[e];
@@ -208,14 +210,14 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
   uint32_t mma_phase = 0;
   const int64_t n_pts = dec_count(a);
   const int64_t n_tiles = (n_pts + a.Pt - 1) / a.Pt;
-  const int K0 = a.d + a.r;
+  const int K0 = kTcLat + a.r;                           // first-layer inputs in the padded layout
   float* xh = xb + h * 128 * kXbStride;                  // this half's exchange buffer
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !tail->abort; tile += gridDim.x) {
     const int64_t first = tile * a.Pt;
     const RowInfo ri = row_info(a, rw, first, n_pts);
     float in[40], dir[40];
-    if (ri.cls >= 0) row_inputs(a, ri, in, dir);
+    if (ri.cls >= 0) row_inputs_tc(a, ri, in, dir);
 
     // ---- layer 0 on the CUDA cores (FP32), this thread's 64 columns, 8 at a time
     for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 8) {
@@ -268,7 +270,11 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         else if (ri.cls == 0) hv[j] = a.act == 0 ? (SPLIT ? elu(z[j]) : elu_bf16_input(z[j])) : z[j];
         else if (ri.cls == 1) hv[j] = act_d1(a.act, z[j]) * zd[j];
         else if (ri.cls == 2) hv[j] = act_sec(a.act, z[j], zd[j]);
-        else hv[j] = act_d2(a.act, z[j]) * zd[j] * mixed_t0(a, sW0 + c * kW0Stride, ri.kind);
+        else {
+          const int b = ri.kind - KIND_MIXED - 1;   // input of the mixed derivative, padded layout below
+          const float t0 = b < a.d ? sW0[c * kW0Stride + b] / a.norm[a.d + b] : sW0[c * kW0Stride + kTcLat + b - a.d];
+          hv[j] = act_d2(a.act, z[j]) * zd[j] * t0;
+        }
         if (ri.cls >= 0) zv = ri.cls == 0 ? z[j] : zd[j];
         if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + rw] = zv;
         if (a.astore) a.astore[(int64_t)c * a.rows_total + tile * 128 + rw] = __float2bfloat16_rn(hv[j]);
@@ -1033,11 +1039,14 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
     MPM_CHECK_ARG(!a.zstore || dec->n_tc > 0, "training stores need square hidden layers");
     MPM_CHECK_ARG(!a.zstore || !has_mixed, "training stores take no mixed rows");
   }
+  // the tensor-core kernel's input layout holds r <= 36 latents (decoder_create allows d + r <= 40):
+  // larger latents take the FP32 kernel
+  const bool f32_path = (dec->fp32 == 1 || dec->r > 40 - kTcLat) && !a.zstore;
   if (dec->n_tc == 0) {
     int64_t rows = n * R;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, dec->n_sm * 8));
     decoder_simt<<<blocks, 128, 0, s>>>(a);
-  } else if (dec->fp32 == 1 && !a.zstore) {
+  } else if (f32_path) {
     MPM_CHECK_ARG(R <= kF32Rows, "the FP32 path takes at most 64 row kinds");
     int64_t tiles;
     bool small = false;

@@ -176,6 +176,55 @@ __device__ __forceinline__ void row_inputs(const DecArgs& a, const RowInfo& ri, 
 }
 
 // Row of X and latent row of the point of `ri`.
+__device__ __forceinline__ void row_source(const DecArgs& a, const RowInfo& ri, int64_t& xrow, int& li);
+
+// Input vector and direction of one row in the tensor-core kernel's layout: the d normalised
+// coordinates at entries 0 .. 3 (zero-padded), the r <= 36 latents from entry 4, so that the
+// latent part sits at a fixed offset and is loaded as float4 when r is a multiple of 4.
+constexpr int kTcLat = 4;   // offset of the latent part
+__device__ __forceinline__ void row_inputs_tc(const DecArgs& a, const RowInfo& ri, float* in, float* dir) {
+  const int d = a.d, r = a.r;
+  int64_t xrow;
+  int li;
+  row_source(a, ri, xrow, li);
+#pragma unroll
+  for (int i = 0; i < kTcLat; ++i) {
+    in[i] = i < d ? (a.X[xrow * d + i] - a.norm[i]) / a.norm[d + i] : 0.f;
+    dir[i] = (i < d && ri.cls == 1 && ri.kind == i + 1) ? 1.f / a.norm[d + i] : 0.f;
+  }
+  const float* lat = a.latents + (int64_t)li * r;
+  const bool has_dir = (ri.cls == 1 && ri.kind == KIND_JVP) || ri.cls == 2 || ri.cls == 3;
+  const float* dv = has_dir ? a.dirs + dir_offset(a, ri.kind, li) : lat;
+  const bool vec = (r & 3) == 0 && (((uintptr_t)lat | (uintptr_t)dv) & 15u) == 0;
+  const int lat_tangent = (ri.cls == 1 && ri.kind > d && ri.kind <= d + r) ? ri.kind - 1 - d : -1;
+#pragma unroll
+  for (int q = 0; q < (40 - kTcLat) / 4; ++q) {
+    float lv[4] = {0.f, 0.f, 0.f, 0.f}, dvv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (4 * q < r) {
+      if (vec) {
+        const float4 l4 = *reinterpret_cast<const float4*>(lat + 4 * q);
+        lv[0] = l4.x; lv[1] = l4.y; lv[2] = l4.z; lv[3] = l4.w;
+        if (has_dir) {
+          const float4 d4 = *reinterpret_cast<const float4*>(dv + 4 * q);
+          dvv[0] = d4.x; dvv[1] = d4.y; dvv[2] = d4.z; dvv[3] = d4.w;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (4 * q + c < r) {
+            lv[c] = lat[4 * q + c];
+            if (has_dir) dvv[c] = dv[4 * q + c];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      in[kTcLat + 4 * q + c] = lv[c];
+      dir[kTcLat + 4 * q + c] = (4 * q + c == lat_tangent) ? 1.f : dvv[c];
+    }
+  }
+}
 __device__ __forceinline__ void row_source(const DecArgs& a, const RowInfo& ri, int64_t& xrow, int& li) {
   xrow = ri.p;
   li = a.lat ? a.lat[ri.p] : (a.lat_per_point ? (int)ri.p : 0);

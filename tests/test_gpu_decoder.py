@@ -40,8 +40,10 @@ def _gpu(*arrays):
     return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrays]
 
 
-@pytest.mark.parametrize("d,r,n", [(2, 16, 1000), (3, 16, 777), (2, 8, 1), (3, 32, 300)])
+@pytest.mark.parametrize("d,r,n", [(2, 16, 1000), (3, 16, 777), (2, 8, 1), (3, 32, 300), (3, 13, 200), (2, 38, 50)])
 def test_forward_and_jacobians(d, r, n):
+    """Includes r = 13 (latents loaded one by one rather than as float4) and r = 38 (beyond the
+    tensor-core kernel's 36-latent input layout: the FP32 kernel)."""
     import torch
     from paper_2109_12390_gb300.decoder import Decoder, PRIMAL
     p = _dec_params(d, r)
