@@ -265,7 +265,6 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int c = c0 + j;
-        float zv = 0.f;
         if (ri.cls < 0) hv[j] = 0.f;
         else if (ri.cls == 0) hv[j] = a.act == 0 ? (SPLIT ? elu(z[j]) : elu_bf16_input(z[j])) : z[j];
         else if (ri.cls == 1) hv[j] = act_d1(a.act, z[j]) * zd[j];
@@ -275,8 +274,8 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
           const float t0 = b < a.d ? sW0[c * kW0Stride + b] / a.norm[a.d + b] : sW0[c * kW0Stride + kTcLat + b - a.d];
           hv[j] = act_d2(a.act, z[j]) * zd[j] * t0;
         }
-        if (ri.cls >= 0) zv = ri.cls == 0 ? z[j] : zd[j];
-        if (a.zstore) a.zstore[(int64_t)c * a.rows_total + tile * 128 + rw] = zv;
+        if (a.dstore && ri.cls == 0)
+          a.dstore[(int64_t)c * a.rows_total + tile * 128 + rw] = __float2bfloat16_rn(act_slope_record(a.act, z[j]));
         if (a.astore) a.astore[(int64_t)c * a.rows_total + tile * 128 + rw] = __float2bfloat16_rn(hv[j]);
       }
       store_operand<SPLIT>(atile, rw, c0, hv);
@@ -343,13 +342,13 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         const int ch = 2 * h + i2;
         float acc[32];
         tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + ch * 32, acc);
-        // training: keep the pre-activation (z for primal rows, zdot for tangent rows)
-        float* zs = a.zstore ? a.zstore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + rw : nullptr;
-        if (zs) {
+        // training: the primal rows' activation slopes (the backward's act' and act'' terms)
+        if (a.dstore && ri.cls == 0) {
+          __nv_bfloat16* ds = a.dstore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + rw;
 #pragma unroll
           for (int i = 0; i < 32; ++i)
-            zs[(int64_t)(ch * 32 + i) * a.rows_total] =
-                ri.cls < 0 ? 0.f : acc[i] + (ri.cls == 0 ? bl[ch * 32 + i] : 0.f);
+            ds[(int64_t)(ch * 32 + i) * a.rows_total] =
+                __float2bfloat16_rn(act_slope_record(a.act, acc[i] + bl[ch * 32 + i]));
         }
         if (ri.cls == 0) {
 #pragma unroll
@@ -1033,15 +1032,15 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   a.n_rep = n_rep;
   if (extra) {
     a.lat_per_point = extra->lat_per_point;
-    a.zstore = extra->zstore;
+    a.dstore = extra->dstore;
     a.astore = extra->astore;
     a.rows_total = extra->rows_total;
-    MPM_CHECK_ARG(!a.zstore || dec->n_tc > 0, "training stores need square hidden layers");
-    MPM_CHECK_ARG(!a.zstore || !has_mixed, "training stores take no mixed rows");
+    MPM_CHECK_ARG(!a.dstore || dec->n_tc > 0, "training stores need square hidden layers");
+    MPM_CHECK_ARG(!a.dstore || !has_mixed, "training stores take no mixed rows");
   }
   // the tensor-core kernel's input layout holds r <= 36 latents (decoder_create allows d + r <= 40):
   // larger latents take the FP32 kernel
-  const bool f32_path = (dec->fp32 == 1 || dec->r > 40 - kTcLat) && !a.zstore;
+  const bool f32_path = (dec->fp32 == 1 || dec->r > 40 - kTcLat) && !a.dstore;
   if (dec->n_tc == 0) {
     int64_t rows = n * R;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, dec->n_sm * 8));
@@ -1073,7 +1072,7 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   } else {
     const int64_t tiles = (n + a.Pt - 1) / a.Pt;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));
-    if (dec->fp32 == 2 && !a.zstore)
+    if (dec->fp32 == 2 && !a.dstore)
       decoder_tc<true><<<blocks, kDecThreads, dec->smem_split, s>>>(a);
     else
       decoder_tc<false><<<blocks, kDecThreads, dec->smem, s>>>(a);
@@ -1086,13 +1085,13 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
 
 namespace mpmrom {
 // Training forward: one latent and one JVP direction per point; stores the
-// per-layer pre-activations and activations of every tile row.
+// per-layer activations of every tile row and the primal rows' activation slopes.
 mpm_status decoder_launch_train(const mpm_decoder* dec, const float* X, const float* latents, const float* dirs,
-                                const int* kinds, int R, int64_t n, float* out, float* zstore,
+                                const int* kinds, int R, int64_t n, float* out, __nv_bfloat16* dstore,
                                 __nv_bfloat16* astore, int64_t rows_total, cudaStream_t s) {
   DecArgs extra{};
   extra.lat_per_point = 1;
-  extra.zstore = zstore;
+  extra.dstore = dstore;
   extra.astore = astore;
   extra.rows_total = rows_total;
   return decoder_launch(dec, X, nullptr, latents, dirs, kinds, R, n, out, nullptr, nullptr, 1, s, &extra);

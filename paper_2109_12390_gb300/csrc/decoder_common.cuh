@@ -55,10 +55,11 @@ struct DecArgs {
   int f32_U;
   // direction blocks per latent row in `dirs` (KIND_SECANT_DIR rows; 1 otherwise)
   int n_dirs;
-  // training: per hidden layer l, pre-activations z (FP32) and activations a
-  // (BF16) of every tile row, stored feature-major: [l][feature][row], row =
-  // tile * 128 + t, rows_total = n_tiles * 128
-  float* zstore;
+  // training: per hidden layer l, stored feature-major [l][feature][row] (row =
+  // tile * 128 + t, rows_total = n_tiles * 128), BF16: dstore the primal rows'
+  // activation slope act'(z), or -1 where z >= 0 (slope 1, no curvature term;
+  // other rows not written), astore every row's activation a
+  __nv_bfloat16* dstore;
   __nv_bfloat16* astore;
   int64_t rows_total;
 };
@@ -85,6 +86,9 @@ __device__ __forceinline__ float elu_secant(float z, float dz) {
 }
 
 __device__ __forceinline__ float act_f(int act, float z) { return act == 0 ? elu(z) : z; }
+// The training record of a primal pre-activation: ELU's slope exp(z) where z < 0 (the
+// curvature there equals it), -1 elsewhere (slope 1, no curvature)
+__device__ __forceinline__ float act_slope_record(int act, float z) { return (act == 0 && z < 0.f) ? __expf(z) : -1.f; }
 __device__ __forceinline__ float act_d1(int act, float z) { return act == 0 ? elu_d1(z) : 1.f; }
 __device__ __forceinline__ float act_d2(int act, float z) { return act == 0 ? elu_d2(z) : 0.f; }
 __device__ __forceinline__ float act_sec(int act, float z, float dz) { return act == 0 ? elu_secant(z, dz) : dz; }

@@ -6,10 +6,13 @@
 //                    (seed, step, i), uniform over all pairs), gather of X,
 //                    latents, JVP directions and targets
 //   decoder_tc       forward (tensor cores), storing every hidden layer's
-//                    pre-activations (FP32) and activations (BF16) feature-major
+//                    activations and the primal rows' activation slopes (BF16,
+//                    feature-major)
 //   train_bwd_tc     loss residuals and output-layer gradients (FP32), then the
 //                    reverse sweep: z_bar = act'(z) h_bar + act''(z) sum_j zdot_j t_bar_j
-//                    for primal rows, zdot_bar = act'(z) t_bar for tangent rows
+//                    for primal rows, zdot_bar = act'(z) t_bar for tangent rows; for
+//                    ELU act''(z) zdot_j = [z < 0] a_j, the tangent row's stored
+//                    activation, so the slope record and the activations suffice
 //                    (exchanged through shared memory), next adjoint rows by a
 //                    tcgen05 GEMM with the transposed weights resident in shared
 //                    memory; layer 0 and the latent adjoints in FP32
@@ -36,7 +39,7 @@
 
 namespace mpmrom {
 mpm_status decoder_launch_train(const mpm_decoder* dec, const float* X, const float* latents, const float* dirs,
-                                const int* kinds, int R, int64_t n, float* out, float* zstore,
+                                const int* kinds, int R, int64_t n, float* out, __nv_bfloat16* dstore,
                                 __nv_bfloat16* astore, int64_t rows_total, cudaStream_t s);
 
 __device__ __forceinline__ uint64_t tr_splitmix(uint64_t state, uint64_t k) {
@@ -123,7 +126,7 @@ struct BwdArgs {
   const float* W0;      // (W, d + r)
   const float* Wout;    // (d, W)
   const float* norm;
-  const float* zstore;
+  const __nv_bfloat16* dstore;   // primal rows' activation slopes (act_slope_record), feature-major
   const __nv_bfloat16* astore;
   const uint8_t* wtimg;
   const float* fwd;     // (R, n, d)
@@ -163,8 +166,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
   uint8_t* wt = smem;                                 // n_tc x 32 KB (transposed square weights)
   uint8_t* atile = smem + kMaxTC * kLayerBytes;       // 32 KB
   float* exch = (float*)(atile + kLayerBytes);        // [2 halves][kExchRows][33]: tangent-row terms of the chunk
-  float* stg = exch + 2 * kExchRows * kChunkStride;   // [2 halves][128 rows][33]: pre-activations of the chunk
-  float* sy = stg + 2 * 128 * kChunkStride;           // 128 x 3
+  __nv_bfloat16* sD = (__nv_bfloat16*)(exch + 2 * kExchRows * kChunkStride);  // [64 f][128 rows] slopes
+  __nv_bfloat16* sA = sD + 64 * 128;                  // [64 f][128 rows] activations (f: 32 h + feature of chunk)
+  float* sy = (float*)(sA + 64 * 128);                // 128 x 3
   float* sbias = sy + 128 * 3;                        // 128
   DecSmemTail* tail = (DecSmemTail*)(sbias + kW);
   __shared__ double s_loss[8];
@@ -208,16 +212,21 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
     const bool valid = (k < R) && (p < a.n);
     const int cls = !valid ? -1 : (k == 0 ? 0 : 1);
     const int64_t gr = row0 + rw;
-    // this row's pre-activations of (layer lz, chunk chz) into the staging buffer, copied
-    // asynchronously (one chunk ahead of its use, so that the loads overlap the current chunk)
-    float* my_stg = stg + (h * 128 + rw) * kChunkStride;
-    auto prefetch_z = [&](int lz, int chz) {
-      const float* src = a.zstore + ((int64_t)lz * kW + chz * 32) * a.rows_total + gr;
-#pragma unroll 8
-      for (int i = 0; i < 32; ++i) cp_async4(my_stg + i, src + (int64_t)i * a.rows_total);
+    // the slopes and activations of step i2z of layer lz (chunk 2 hh + i2z of each half hh) for
+    // the tile's 128 rows, copied asynchronously into the staging buffers in 4-byte words (two
+    // rows of one feature) one step ahead of their use, so that the loads overlap the current step
+    auto prefetch_z = [&](int lz, int i2z) {
+#pragma unroll 4
+      for (int k2 = 0; k2 < 32; ++k2) {
+        const int w = t + kBwdThreads * k2;                    // 2 arrays x 64 features x 64 row pairs
+        const int arr = w >> 12, fl = (w >> 6) & 63, rp = w & 63;
+        const int fg = (2 * (fl >> 5) + i2z) * 32 + (fl & 31);   // global feature
+        const __nv_bfloat16* src = (arr ? a.astore : a.dstore) + ((int64_t)lz * kW + fg) * a.rows_total + row0 + 2 * rp;
+        cp_async4((arr ? sA : sD) + fl * 128 + 2 * rp, src);
+      }
       cp_async_commit_group();
     };
-    prefetch_z(a.n_hidden - 1, 2 * h);
+    prefetch_z(a.n_hidden - 1, 0);
     // ---- output layer: residual adjoints ybar (FP32)
     float ybar[3] = {0.f, 0.f, 0.f};
     if (valid) {
@@ -282,7 +291,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
         mma_phase ^= 1u;
         tc::tc_fence_after();
       }
-      cp_async_wait_groups();   // this row's staged pre-activations of the chunk have landed
+      cp_async_wait_groups();   // this thread's staging copies of the step have landed
       __syncthreads();
       if (tail->abort) break;
       for (int i2 = 0; i2 < 2; ++i2) {
@@ -301,30 +310,32 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
           }
         }
         float zb[32];
-        // pre-activations of this chunk from the staging buffer: the row's own (z for primal
-        // rows, zdot for tangent rows) and, for tangent rows, their point's primal z (row q)
-        float zown[32];
-        const float* hstg = stg + h * 128 * kChunkStride;
+        // the point's primal slope record s (row q): act'(z) = s, or 1 where s < 0; for tangent
+        // rows the curvature term act''(z) zdot is the row's own activation where s >= 0 (z < 0)
+        float sown[32];
+        const __nv_bfloat16* hD = sD + (h * 32) * 128;
+        const __nv_bfloat16* hA = sA + (h * 32) * 128;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) zown[i] = my_stg[i];
+        for (int i = 0; i < 32; ++i) sown[i] = __bfloat162float(hD[i * 128 + rw]);
         float* hexch = exch + h * kExchRows * kChunkStride;
         if (cls == 1) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            const float zp = hstg[q * kChunkStride + i];
-            zb[i] = act_d1(a.act, zp) * hb[i];
-            hexch[(rw - Pt) * kChunkStride + i] = act_d2(a.act, zp) * zown[i] * hb[i];
+            const float sp = __bfloat162float(hD[i * 128 + q]);
+            const float at = __bfloat162float(hA[i * 128 + rw]);
+            zb[i] = (sp < 0.f ? 1.f : sp) * hb[i];
+            hexch[(rw - Pt) * kChunkStride + i] = (sp >= 0.f ? at : 0.f) * hb[i];
           }
         }
         __syncthreads();
-        // every row has read the staged chunk: stage the next one (this layer's other chunk of
-        // this half, or the next layer's first)
-        if (i2 == 0) prefetch_z(l, ch + 1);
-        else if (l > 0) prefetch_z(l - 1, 2 * h);
+        // every row has read the staged step: stage the next one (this layer's other chunk of
+        // each half, or the next layer's first)
+        if (i2 == 0) prefetch_z(l, 1);
+        else if (l > 0) prefetch_z(l - 1, 0);
         if (cls == 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            float sacc = act_d1(a.act, zown[i]) * hb[i];
+            float sacc = (sown[i] < 0.f ? 1.f : sown[i]) * hb[i];
             // compile-time bound (R <= kBwdMaxR): with the runtime bound this loop, inside the
             // unrolled feature loop, ran about 1,000 cycles per feature
 #pragma unroll
@@ -712,7 +723,7 @@ struct trainer_ctx {
   float* batch_mem = nullptr;
   int32_t* batch_idx = nullptr;
   float* fwd = nullptr;
-  float* zstore = nullptr;
+  __nv_bfloat16* dstore = nullptr;   // primal rows' activation slopes (n_hidden, W, rows)
   __nv_bfloat16* astore = nullptr;
   __nv_bfloat16* zbstore = nullptr;
   float* zb0 = nullptr;
@@ -862,7 +873,7 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
   kinds[0] = 0;
   for (int a = 0; a < d; ++a) kinds[1 + a] = 1 + a;
   kinds[1 + d] = 1000;
-  mpm_status st = decoder_launch_train(dec, c->b.X, c->b.xh, c->b.u, kinds, c->R, c->B, c->fwd, c->zstore, c->astore,
+  mpm_status st = decoder_launch_train(dec, c->b.X, c->b.xh, c->b.u, kinds, c->R, c->B, c->fwd, c->dstore, c->astore,
                                        c->rows_total, s);
   if (st != MPM_OK) return st;
   BwdArgs a{};
@@ -880,7 +891,7 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
   a.W0 = dec->params + dec->w_off[0];
   a.Wout = dec->params + dec->w_off[L - 1];
   a.norm = dec->norm;
-  a.zstore = c->zstore;
+  a.dstore = c->dstore;
   a.astore = c->astore;
   a.wtimg = c->wtimg;
   a.fwd = c->fwd;
@@ -1166,7 +1177,7 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   // activation stores
   const size_t rows = (size_t)c->rows_total;
   if ((st = talloc(&c->fwd, (size_t)c->R * B * d)) != MPM_OK) return st;
-  if ((st = talloc(&c->zstore, (size_t)dec->n_hidden * kW * rows)) != MPM_OK) return st;
+  if ((st = talloc(&c->dstore, (size_t)dec->n_hidden * kW * rows)) != MPM_OK) return st;
   if ((st = talloc(&c->astore, (size_t)dec->n_hidden * kW * rows)) != MPM_OK) return st;
   if ((st = talloc(&c->zbstore, (size_t)dec->n_tc * kW * rows)) != MPM_OK) return st;
   if ((st = talloc(&c->zb0, (size_t)kW * rows)) != MPM_OK) return st;
@@ -1189,8 +1200,8 @@ mpm_status trainer_create(mpm_decoder* dec, const train_config* cfg, const snaps
   c->st.x = c->sx;
   c->st.v = c->sv;
   c->st.F = c->sF;
-  c->bwd_smem = 1024 + kMaxTC * kLayerBytes + kLayerBytes + (size_t)(2 * kExchRows + 2 * 128) * kChunkStride * 4 +
-                128 * 3 * 4 + kW * 4 + sizeof(DecSmemTail);
+  c->bwd_smem = 1024 + kMaxTC * kLayerBytes + kLayerBytes + (size_t)2 * kExchRows * kChunkStride * 4 +
+                2 * 64 * 128 * 2 + 128 * 3 * 4 + kW * 4 + sizeof(DecSmemTail);
   MPM_CUDA_TRY(cudaFuncSetAttribute(train_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->bwd_smem));
   MPM_CUDA_TRY(cudaFuncSetAttribute(train_dw0_lat<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw0_smem_bytes()));
   MPM_CUDA_TRY(cudaFuncSetAttribute(train_dw0_lat<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw0_smem_bytes()));
@@ -1210,7 +1221,7 @@ void trainer_destroy(trainer_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->snap_base, c->snap_inst, c->snap_next, c->inst_off, c->X, c->sx, c->sv, c->sF, c->latents,
                   c->g_lat, c->m_lat, c->v_lat, c->gparams, c->m_par, c->v_par, c->batch_mem, c->batch_idx, c->fwd,
-                  c->zstore, c->astore, c->zbstore, c->zb0, c->g_lat_pt, c->g_u_pt, c->wtimg, c->d_w_off, c->step,
+                  c->dstore, c->astore, c->zbstore, c->zb0, c->g_lat_pt, c->g_u_pt, c->wtimg, c->d_w_off, c->step,
                   c->loss, c->status, c->U, c->enc_p, c->enc_g, c->enc_m, c->enc_v, c->enc_ss, c->enc_work};
   for (void* p : bufs) cudaFree(p);
   delete c;
