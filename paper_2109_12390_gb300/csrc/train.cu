@@ -493,8 +493,9 @@ __global__ void __launch_bounds__(128, 1) train_dw_gemm(const __nv_bfloat16* zbs
     for (int ch = 0; ch < kW / 32; ++ch) {
       float v[32];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, v);
+      float4* g4 = reinterpret_cast<float4*>(g + t * kW + ch * 32);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) atomicAdd(&g[t * kW + ch * 32 + i], v[i]);
+      for (int i = 0; i < 8; ++i) atomicAdd(g4 + i, make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
     }
   }
   tc::tc_fence_before();
@@ -914,7 +915,9 @@ mpm_status train_launch_step(trainer_ctx* c, cudaStream_t s, int update) {
   train_bwd_tc<<<bw, kBwdThreads, c->bwd_smem, s>>>(a);
   MPM_CUDA_TRY(cudaGetLastError());
   if (dec->n_tc > 0) {
-    const int splits = std::max(1, c->n_sm / dec->n_tc);
+    // four CTAs per SM (32 KB of shared memory and 128 TMEM columns each), so that four K blocks'
+    // loads are in flight per SM; the splits' partial sums meet in vector reductions
+    const int splits = std::max(1, 4 * c->n_sm / dec->n_tc);
     int64_t kps = (c->rows_total + splits - 1) / splits;
     kps = (kps + 63) / 64 * 64;
     dim3 g(dec->n_tc, (unsigned)((c->rows_total + kps - 1) / kps));
