@@ -77,12 +77,22 @@ __device__ __forceinline__ float expm1_small(float x) {
   return expm1f(x);
 }
 
-// act(z + dz) - act(z) without cancellation on the negative branch
+// act(z + dz) - act(z) without cancellation on the negative branch.  The common cases (both ends
+// positive: dz; both negative with a small increment: e^z times the Taylor polynomial of
+// expm1(dz)) are evaluated without branches, so that the lanes of a warp, whose features take
+// different cases, do not run them one after another; the rest (ends of opposite sign, or an
+// increment of 1/32 or more) takes the branch, with the same arithmetic as the case split.
 __device__ __forceinline__ float elu_secant(float z, float dz) {
-  float z1 = z + dz;
-  if (z > 0.f && z1 > 0.f) return dz;
-  if (z <= 0.f && z1 <= 0.f) return __expf(z) * expm1_small(dz);
-  return elu(z1) - elu(z);
+  const float z1 = z + dz;
+  const bool pos = (z > 0.f) & (z1 > 0.f);
+  const bool neg = (z <= 0.f) & (z1 <= 0.f);
+  const bool small = fabsf(dz) < 0.03125f;
+  const float poly =
+      dz * fmaf(0.5f * dz, fmaf(dz * (1.f / 3.f), fmaf(0.25f * dz, fmaf(0.2f * dz, fmaf(dz, 1.f / 6.f, 1.f), 1.f), 1.f), 1.f),
+                1.f);
+  float res = pos ? dz : __expf(fminf(z, 0.f)) * poly;
+  if (!pos && !(neg && small)) res = neg ? __expf(z) * expm1f(dz) : elu(z1) - elu(z);
+  return res;
 }
 
 __device__ __forceinline__ float act_f(int act, float z) { return act == 0 ? elu(z) : z; }
