@@ -693,14 +693,16 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
         }
       }
       __syncthreads();                                  // A1 complete, every GEMM has read A0
-      if (warp < G) {
-        // activations of the next layer into A0 (warp w: slots 4 w .. 4 w + 3); derivative rows
-        // read their partners' pre-activations
-        float h[4][4];
+      {
+        // activations of the next layer into A0: every warp takes SPW = TR / 16 slots (warp w:
+        // slots SPW w ..), so that the short dependent chains of the activations run on all
+        // sixteen warps; derivative rows read their partners' pre-activations
+        constexpr int SPW = TR / 16;
+        float h[SPW][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const F32Row& fr = srow[4 * warp + j];
-          const float4 z4 = *reinterpret_cast<const float4*>(A1 + f32_zslot(4 * warp + j, f0));
+        for (int j = 0; j < SPW; ++j) {
+          const F32Row& fr = srow[SPW * warp + j];
+          const float4 z4 = *reinterpret_cast<const float4*>(A1 + f32_zslot(SPW * warp + j, f0));
           const float zr[4] = {z4.x, z4.y, z4.z, z4.w};
           if (fr.ri.cls == 0) {
 #pragma unroll
@@ -722,9 +724,14 @@ __global__ void __launch_bounds__(kF32Threads, 1) decoder_f32(DecArgs a) {
           }
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          *reinterpret_cast<float4*>(A0 + f32_slot<TR>(f0 + i, 4 * warp)) =
-              make_float4(h[0][i], h[1][i], h[2][i], h[3][i]);
+        for (int i = 0; i < 4; ++i) {
+          if (SPW == 4) {
+            *reinterpret_cast<float4*>(A0 + f32_slot<TR>(f0 + i, 4 * warp)) =
+                make_float4(h[0][i], h[1][i], h[2 % SPW][i], h[3 % SPW][i]);
+          } else {
+            *reinterpret_cast<float2*>(A0 + f32_slot<TR>(f0 + i, SPW * warp)) = make_float2(h[0][i], h[1 % SPW][i]);
+          }
+        }
       }
     }
     __syncthreads();                                    // A0 complete
