@@ -147,10 +147,12 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* wsm = smem;                                   // n_tc x 32 KB (split: the current layer, hi and lo)
   uint8_t* atile = smem + (SPLIT ? 2 : kMaxTC) * kLayerBytes;  // 32 KB (split: hi and lo, 64 KB)
-  float* xb = (float*)(atile + (SPLIT ? 2 : 1) * kLayerBytes);  // [2 halves][128 rows][33]: one chunk per half
+  // first layer: FP32 [128][kW0Stride], zero-padded (CUDA cores), or its 16 KB split BF16 image
+  uint8_t* w0s = atile + (SPLIT ? 2 : 1) * kLayerBytes;
+  float* sW0 = (float*)w0s;
+  float* xb = sW0 + kW * kW0Stride;                      // [2 halves][128 rows][33]: one chunk per half
   float* ypart = xb + 2 * 128 * kXbStride;               // [128 rows][3]: output partial of half 1
-  float* sW0 = ypart + 128 * 3;                          // [128][kW0Stride] first layer, zero-padded
-  float* sb0 = sW0 + kW * kW0Stride;                     // [128]
+  float* sb0 = ypart + 128 * 3;                          // [128]
   float* sbh = sb0 + kW;                                 // [kMaxTC][128] square-layer biases
   float* sWout = sbh + kMaxTC * kW;                      // [3][128] output layer
   DecSmemTail* tail = (DecSmemTail*)(sWout + 3 * kW);
@@ -170,12 +172,18 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
   tc::tc_fence_after();
   const uint32_t tmem = tail->tmem;
 
-  // FP32 first layer, biases and output layer staged in shared memory (read by
+  // The first layer runs on the tensor cores when its inputs fit 32 entries of the padded layout:
+  // z = W0 [in] from split BF16 pairs, in_hi W0_hi + in_hi W0_lo + in_lo W0_hi (FP32 accumulate),
+  // the dropped products and the residuals of the splits about 2^-16 of each product.
+  const int K0 = kTcLat + a.r;                           // first-layer inputs in the padded layout
+  const bool l0_tc = !SPLIT && a.w0img != nullptr && K0 <= 32;
+
+  // FP32 first layer (CUDA-core form), biases and output layer staged in shared memory (read by
   // every row of every tile)
   {
     const int K0s = a.d + a.r;
     // the tensor-core input layout (row_inputs_tc): coordinates at 0 .. 3, latents from kTcLat
-    for (int e = t; e < kW * kW0Stride; e += kDecThreads) {
+    for (int e = t; e < (l0_tc ? 0 : kW * kW0Stride); e += kDecThreads) {
       const int c = e / kW0Stride, ii = e % kW0Stride;
       const int i = ii < kTcLat ? (ii < a.d ? ii : -1) : (ii - kTcLat < a.r ? a.d + ii - kTcLat : -1);
       sW0[e] = i >= 0 ? a.W0[c * K0s + i] : 0.f;
@@ -190,9 +198,10 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
   bool w_pending = false;   // thread 0: a weight copy is in flight
   if (!SPLIT) {
     if (t == 0) {
-      tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(a.n_tc * kLayerBytes));
+      tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(a.n_tc * kLayerBytes + (l0_tc ? kLayerBytes / 2 : 0)));
       for (int l = 0; l < a.n_tc; ++l)
         tc::bulk_g2s(wsm + l * kLayerBytes, a.wimg + (size_t)l * kLayerBytes, kLayerBytes, &tail->bar_w);
+      if (l0_tc) tc::bulk_g2s(w0s, a.w0img, kLayerBytes / 2, &tail->bar_w);
     }
     if (!tc::mbar_wait(&tail->bar_w, 0)) {
       raise_status(a.status, STATUS_TIMEOUT);
@@ -210,7 +219,6 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
   uint32_t mma_phase = 0;
   const int64_t n_pts = dec_count(a);
   const int64_t n_tiles = (n_pts + a.Pt - 1) / a.Pt;
-  const int K0 = kTcLat + a.r;                           // first-layer inputs in the padded layout
   float* xh = xb + h * 128 * kXbStride;                  // this half's exchange buffer
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !tail->abort; tile += gridDim.x) {
@@ -219,6 +227,23 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
     float in[40], dir[40];
     if (ri.cls >= 0) row_inputs_tc(a, ri, in, dir);
 
+    if (l0_tc) {
+      // ---- the first layer's operand row: the primal rows' input, the tangent and secant rows'
+      // direction (their pre-activation tangent or increment), zero for the mixed rows (the first
+      // layer is linear: their second-order part starts at zero) and the unused rows; half 0
+      // stores the high parts at columns 0 .. 31, half 1 the low parts at 32 .. 63
+#pragma unroll
+      for (int c0 = 0; c0 < 32; c0 += 8) {
+        float p[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float v = ri.cls == 0 ? in[c0 + j] : (ri.cls == 1 || ri.cls == 2) ? dir[c0 + j] : 0.f;
+          const float hi = __bfloat162float(__float2bfloat16_rn(v));
+          p[j] = h == 0 ? hi : v - hi;
+        }
+        store_bf16x8(atile, rw, 32 * h + c0, p);
+      }
+    } else
     // ---- layer 0 on the CUDA cores (FP32), this thread's 64 columns, 8 at a time
     for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 8) {
       // the 8 columns' sums advance together over the inputs (16 independent chains), so that
@@ -282,7 +307,8 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
     }
 
     float y[3] = {0.f, 0.f, 0.f};
-    for (int l = 0; l < a.n_tc; ++l) {
+    // layer -1 is the first layer when it runs on the tensor cores
+    for (int l = l0_tc ? -1 : 0; l < a.n_tc; ++l) {
       // make the generic-proxy writes of the operand tile visible to the tensor core
       tc::fence_async_smem();
       tc::tc_fence_before();
@@ -299,7 +325,18 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
             atomicExch(&tail->abort, 1);
           }
         }
-        if (w_ok) {
+        if (w_ok && l < 0) {
+          // two K steps of 16 over the 32 padded inputs; hi at byte 0 of a row, lo at byte 64
+          const uint32_t a_base = tc::smem_addr(atile), b_base = tc::smem_addr(w0s);
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const uint32_t hi = (uint32_t)(k * 32), lo = (uint32_t)(64 + k * 32);
+            tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + hi), tc::smem_desc_sw128(b_base + hi), idesc,
+                         k > 0 ? 1u : 0u);
+            tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + hi), tc::smem_desc_sw128(b_base + lo), idesc, 1u);
+            tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + lo), tc::smem_desc_sw128(b_base + hi), idesc, 1u);
+          }
+        } else if (w_ok) {
           const uint32_t a_base = tc::smem_addr(atile);
           const uint32_t b_base = tc::smem_addr(wsm + (SPLIT ? 0 : l * kLayerBytes));
 #pragma unroll
@@ -337,7 +374,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
       __syncthreads();
       if (tail->abort) break;
       const bool last = (l == a.n_tc - 1);
-      const float* bl = sbh + l * kW;
+      const float* bl = l < 0 ? sb0 : sbh + l * kW;
       for (int i2 = 0; i2 < 2; ++i2) {
         const int ch = 2 * h + i2;
         float acc[32];
@@ -801,6 +838,22 @@ __global__ void decoder_pack(const float* W, int n_layers, int64_t stride, uint8
   }
 }
 
+// Packs the first layer (FP32, (W, d + r) row-major) for the tensor cores: row c of the image
+// holds bf16(w) of the padded inputs (coordinates at 0 .. 3, latents from kTcLat) at K 0 .. 31
+// and bf16(w - bf16(w)) at K 32 .. 63, zero where no input sits, in the 128-byte swizzled
+// K-major layout (one 16 KB atom column).
+__global__ void decoder_pack_w0(const float* W0, int d, int r, uint8_t* img) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kW * 32; e += gridDim.x * blockDim.x) {
+    const int c = e / 32, ii = e % 32;
+    const int i = ii < kTcLat ? (ii < d ? ii : -1) : (ii - kTcLat < r ? d + ii - kTcLat : -1);
+    const float w = i >= 0 ? W0[c * (d + r) + i] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+    *reinterpret_cast<__nv_bfloat16*>(img + tc::sw128_offset(c, ii, kW)) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(img + tc::sw128_offset(c, 32 + ii, kW)) =
+        __float2bfloat16_rn(w - __bfloat162float(hi));
+  }
+}
+
 }  // namespace mpmrom
 
 using namespace mpmrom;
@@ -834,6 +887,10 @@ mpm_status refresh_derived_impl(mpm_decoder* dec, cudaStream_t s) {
   MPM_CUDA_TRY(cudaGetLastError());
   decoder_transpose<<<16, 256, 0, s>>>(dec->wsq, dec->n_tc, dec->wsqT);
   MPM_CUDA_TRY(cudaGetLastError());
+  if (dec->w0img) {
+    decoder_pack_w0<<<16, 256, 0, s>>>(dec->params + dec->w_off[0], dec->d, dec->r, dec->w0img);
+    MPM_CUDA_TRY(cudaGetLastError());
+  }
   return MPM_OK;
 }
 
@@ -896,6 +953,7 @@ mpm_status decoder_create(const decoder_desc* desc, mpm_decoder** out) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&dec->wimg, (size_t)dec->n_tc * kLayerBytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&dec->wimg_lo, (size_t)dec->n_tc * kLayerBytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&dec->wsqT, sizeof(float) * dec->n_tc * kW * kW);
+    if (e == cudaSuccess && kTcLat + dec->r <= 32) e = cudaMalloc((void**)&dec->w0img, (size_t)kLayerBytes / 2);
   }
   if (e == cudaSuccess) e = cudaMemset(dec->params, 0, sizeof(float) * dec->n_params);
   if (e == cudaSuccess) e = cudaMemset(dec->status, 0, sizeof(uint32_t));
@@ -924,6 +982,7 @@ void decoder_destroy(mpm_decoder* dec) {
   cudaFree(dec->wimg);
   cudaFree(dec->wimg_lo);
   cudaFree(dec->wsqT);
+  cudaFree(dec->w0img);
   cudaFree(dec->status);
   delete dec;
 }
@@ -995,6 +1054,7 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
   a.norm = dec->norm;
   a.wimg = dec->wimg;
   a.wimg_lo = dec->wimg_lo;
+  a.w0img = dec->w0img;
   a.wsq = dec->wsq;
   a.wsqT = dec->wsqT;
   a.X = X;

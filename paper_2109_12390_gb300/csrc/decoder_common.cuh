@@ -27,6 +27,10 @@ struct DecArgs {
   const float* norm;  // X_min[d], X_range[d], out_shift[d], out_scale[d]
   const uint8_t* wimg;
   const uint8_t* wimg_lo;   // bf16(w - bf16(w)) images (split operands)
+  // first layer as split BF16 pairs for the tensor cores (inputs of at most 32 entries in the
+  // padded layout): rows = output features, hi at K 0 .. 31 and lo at K 32 .. 63 of one
+  // 128-byte swizzled row; null when the first layer runs on the CUDA cores
+  const uint8_t* w0img;
   const float* wsq;   // (n_tc, W, W) FP32 square-layer weights, (out, in) row-major
   const float* wsqT;  // (n_tc, W, W) the same transposed, (in, out) row-major
   const float* X;
@@ -317,6 +321,7 @@ struct mpm_decoder {
   float* wsqT = nullptr;              // transposed FP32 copies (n_tc, W, W) for the CUDA-core path
   uint8_t* wimg = nullptr;            // BF16 swizzled images
   uint8_t* wimg_lo = nullptr;         // residual images bf16(w - bf16(w)) for the split-BF16 path
+  uint8_t* w0img = nullptr;           // first-layer split image (16 KB) when kTcLat + r <= 32
   uint32_t* status = nullptr;
   int n_sm = 0;
   size_t smem = 0;
