@@ -301,7 +301,6 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         }
         if (a.dstore && ri.cls == 0)
           a.dstore[(int64_t)c * a.rows_total + tile * 128 + rw] = __float2bfloat16_rn(act_slope_record(a.act, z[j]));
-        if (a.astore) a.astore[(int64_t)c * a.rows_total + tile * 128 + rw] = __float2bfloat16_rn(hv[j]);
       }
       store_operand<SPLIT>(atile, rw, c0, hv);
     }
@@ -354,6 +353,10 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         }
         tc::mma_commit(&tail->bar_mma);
       }
+      // training: the previous layer's activations leave the operand tile while the tensor core
+      // reads it (both are reads; the barrier after the wait orders them before the next writes)
+      if (!SPLIT && a.astore && l > (l0_tc ? -1 : 0))
+        copy_out_tile(a.astore + (int64_t)l * kW * a.rows_total, a.rows_total, atile, tile, t);
       if (!tc::mbar_wait(&tail->bar_mma, mma_phase)) {
         raise_status(a.status, STATUS_TIMEOUT);
         atomicExch(&tail->abort, 1);
@@ -379,14 +382,6 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         const int ch = 2 * h + i2;
         float acc[32];
         tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + ch * 32, acc);
-        // training: the primal rows' activation slopes (the backward's act' and act'' terms)
-        if (a.dstore && ri.cls == 0) {
-          __nv_bfloat16* ds = a.dstore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + rw;
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            ds[(int64_t)(ch * 32 + i) * a.rows_total] =
-                __float2bfloat16_rn(act_slope_record(a.act, acc[i] + bl[ch * 32 + i]));
-        }
         if (ri.cls == 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[i] += bl[ch * 32 + i];
@@ -396,6 +391,25 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) xh[rw * kXbStride + i] = acc[i];
           __syncthreads();
+          // training: the primal rows' activation slopes (the backward's act' and act'' terms), from
+          // the published pre-activations, spread over the half's four warps: feature = lane, 8 rows
+          // per thread, one 16-byte store of 8 rows of one feature (the training calls have R > 1)
+          if (a.dstore) {
+            for (int k = warp & 3; 8 * k < a.Pt; k += 4) {
+              float v[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) v[j] = act_slope_record(a.act, xh[(8 * k + j) * kXbStride + lane]);
+              __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+              __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+              uint4 u;
+              u.x = *reinterpret_cast<uint32_t*>(&p0);
+              u.y = *reinterpret_cast<uint32_t*>(&p1);
+              u.z = *reinterpret_cast<uint32_t*>(&p2);
+              u.w = *reinterpret_cast<uint32_t*>(&p3);
+              *reinterpret_cast<uint4*>(a.dstore + ((int64_t)(l + 1) * kW + ch * 32 + lane) * a.rows_total +
+                                        tile * 128 + 8 * k) = u;
+            }
+          }
         }
         // the primal row of point q is tile row q (kind index 0)
         const float* zq = xh + ri.q * kXbStride;
@@ -419,11 +433,6 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[i] = 0.f;
         }
-        if (a.astore) {
-          __nv_bfloat16* as = a.astore + (int64_t)(l + 1) * kW * a.rows_total + tile * 128 + rw;
-#pragma unroll
-          for (int i = 0; i < 32; ++i) as[(int64_t)(ch * 32 + i) * a.rows_total] = __float2bfloat16_rn(acc[i]);
-        }
         if (last) {
           // output layer fused into the last epilogue (FP32), partial over this half's columns
 #pragma unroll
@@ -434,7 +443,9 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
             for (int i = 0; i < 32; ++i) sacc = fmaf(sWout[o * kW + ch * 32 + i], acc[i], sacc);
             y[o] += sacc;
           }
-        } else {
+        }
+        // the next layer's operand tile; in training also the last layer's, for the copy-out
+        if (!last || (!SPLIT && a.astore)) {
 #pragma unroll
           for (int j = 0; j < 32; j += 8) store_operand<SPLIT>(atile, rw, ch * 32 + j, acc + j);
         }
@@ -450,6 +461,9 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
         if (o < a.d) ypart[rw * 3 + o] = y[o];
     }
     __syncthreads();
+    // training: the last layer's activations (the barrier at the end of the tile orders these
+    // reads before the next tile's first operand writes)
+    if (!SPLIT && a.astore) copy_out_tile(a.astore + (int64_t)a.n_tc * kW * a.rows_total, a.rows_total, atile, tile, t);
     if (h == 0 && ri.cls >= 0) {
       const int kidx = rw / a.Pt;  // position of this row's kind in `kinds`
       float* o = a.out + ((int64_t)kidx * a.n + ri.p) * a.d;
@@ -1104,6 +1118,7 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
     a.rows_total = extra->rows_total;
     MPM_CHECK_ARG(!a.dstore || dec->n_tc > 0, "training stores need square hidden layers");
     MPM_CHECK_ARG(!a.dstore || !has_mixed, "training stores take no mixed rows");
+    MPM_CHECK_ARG(!a.dstore || R > 1, "training stores need the tangent rows (R > 1)");
   }
   // the tensor-core kernel's input layout holds r <= 36 latents (decoder_create allows d + r <= 40):
   // larger latents take the FP32 kernel

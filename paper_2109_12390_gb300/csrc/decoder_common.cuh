@@ -304,6 +304,35 @@ __device__ __forceinline__ void store_bf16x8(uint8_t* tile, int row, int col, co
 }
 
 
+__device__ __forceinline__ uint32_t u4_word(const uint4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Copies a 128 x 128 BF16 operand tile (row-major, 128-byte swizzled, as the MMA reads it) to a
+// feature-major store, dst[feature * rows_total + tile * 128 + row], with the CTA's 256 threads:
+// each moves an 8 x 8 block (8 rows x 8 features) by eight 16-byte shared loads (the 8 threads
+// of a quarter warp read 8 different 16-byte columns: no bank conflict), a register transpose
+// and eight 16-byte stores of 8 rows of one feature.
+__device__ __forceinline__ void copy_out_tile(__nv_bfloat16* dst, int64_t rows_total, const uint8_t* tile_smem,
+                                              int64_t tile, int t) {
+  const int fg = (t & 7) + 8 * (t >> 7), rg = (t >> 3) & 15;   // feature group 0 .. 15, row group 0 .. 15
+  uint4 u[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) u[j] = *reinterpret_cast<const uint4*>(tile_smem + tc::sw128_offset(8 * rg + j, 8 * fg, kW));
+  __nv_bfloat16* base = dst + (int64_t)(8 * fg) * rows_total + tile * 128 + 8 * rg;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    // feature e of the group sits in word e / 2 of each row's 16 bytes, low half for even e
+    const uint32_t sel = (e & 1) ? 0x7632u : 0x5410u;
+    uint4 o;
+    o.x = __byte_perm(u4_word(u[0], e >> 1), u4_word(u[1], e >> 1), sel);
+    o.y = __byte_perm(u4_word(u[2], e >> 1), u4_word(u[3], e >> 1), sel);
+    o.z = __byte_perm(u4_word(u[4], e >> 1), u4_word(u[5], e >> 1), sel);
+    o.w = __byte_perm(u4_word(u[6], e >> 1), u4_word(u[7], e >> 1), sel);
+    *reinterpret_cast<uint4*>(base + (int64_t)e * rows_total) = o;
+  }
+}
+
 }  // namespace mpmrom
 
 #include <vector>

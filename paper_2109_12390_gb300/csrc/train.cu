@@ -369,9 +369,6 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
         if (l >= 1) {
 #pragma unroll
           for (int j = 0; j < 32; j += 8) store_bf16x8(atile, rw, ch * 32 + j, zb + j);
-          __nv_bfloat16* zs = a.zbstore + (int64_t)(l - 1) * kW * a.rows_total + gr;
-#pragma unroll
-          for (int i = 0; i < 32; ++i) zs[(int64_t)(ch * 32 + i) * a.rows_total] = __float2bfloat16_rn(zb[i]);
         } else {
           // first-layer adjoints (FP32); the first-layer weight gradient and the latent
           // adjoints are formed from them by train_dw0_lat
@@ -403,6 +400,10 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
           }
           tc::mma_commit(&tail->bar_mma);
         }
+        // the adjoints of layer l (BF16, for the weight-gradient GEMMs) leave the operand tile while
+        // the tensor core reads it; the barrier after the next wait orders these reads before the
+        // next writes of the tile
+        copy_out_tile(a.zbstore + (int64_t)(l - 1) * kW * a.rows_total, a.rows_total, atile, tile, t);
       }
     }
     if (tail->abort) break;
