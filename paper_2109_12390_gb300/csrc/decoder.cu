@@ -398,7 +398,12 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
             for (int k = warp & 3; 8 * k < a.Pt; k += 4) {
               float v[8];
 #pragma unroll
-              for (int j = 0; j < 8; ++j) v[j] = act_slope_record(a.act, xh[(8 * k + j) * kXbStride + lane]);
+              for (int j = 0; j < 8; ++j) {
+                // in place: the primal rows' slopes replace their pre-activations in the exchange
+                float* e = xh + (8 * k + j) * kXbStride + lane;
+                v[j] = act_slope_record(a.act, *e);
+                *e = v[j];
+              }
               __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
               __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
               uint4 u;
@@ -409,11 +414,26 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
               *reinterpret_cast<uint4*>(a.dstore + ((int64_t)(l + 1) * kW + ch * 32 + lane) * a.rows_total +
                                         tile * 128 + 8 * k) = u;
             }
+            __syncthreads();
           }
         }
         // the primal row of point q is tile row q (kind index 0)
         const float* zq = xh + ri.q * kXbStride;
-        if (ri.cls == 0) {
+        if (a.dstore) {
+          // training (primal and tangent rows only): the slope s of the primal row, e^z where z < 0
+          // and -1 elsewhere, gives both activations without another exponential: ELU(z) = s - 1
+          // (z where s < 0), act'(z) = s (1 where s < 0); the same values as below
+          if (ri.cls == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[i] = zq[i] < 0.f ? acc[i] : zq[i] - 1.0f;
+          } else if (ri.cls == 1) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[i] *= zq[i] < 0.f ? 1.0f : zq[i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+          }
+        } else if (ri.cls == 0) {
           if (a.act == 0) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) acc[i] = SPLIT ? elu(acc[i]) : elu_bf16_input(acc[i]);
@@ -1119,6 +1139,10 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
     MPM_CHECK_ARG(!a.dstore || dec->n_tc > 0, "training stores need square hidden layers");
     MPM_CHECK_ARG(!a.dstore || !has_mixed, "training stores take no mixed rows");
     MPM_CHECK_ARG(!a.dstore || R > 1, "training stores need the tangent rows (R > 1)");
+    for (int k = 0; k < R && a.dstore; ++k)
+      MPM_CHECK_ARG(a.kinds[k] == KIND_PRIMAL || (a.kinds[k] >= 1 && a.kinds[k] <= dec->d + dec->r) ||
+                        a.kinds[k] == KIND_JVP,
+                    "training stores take primal, tangent and JVP rows only");
   }
   // the tensor-core kernel's input layout holds r <= 36 latents (decoder_create allows d + r <= 40):
   // larger latents take the FP32 kernel

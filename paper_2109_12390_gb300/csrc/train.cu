@@ -147,8 +147,8 @@ constexpr int kExchRows = 104;
 constexpr int kBwdMaxR = 5;           // rows per point in training: primal, d <= 3 tangents, JVP
 constexpr int kChunkStride = 33;      // padded row stride of one 32-feature chunk: distinct banks
 
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
                "l"(gmem_src)
                : "memory");
 }
@@ -212,17 +212,19 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
     const bool valid = (k < R) && (p < a.n);
     const int cls = !valid ? -1 : (k == 0 ? 0 : 1);
     const int64_t gr = row0 + rw;
-    // the slopes and activations of step i2z of layer lz (chunk 2 hh + i2z of each half hh) for
-    // the tile's 128 rows, copied asynchronously into the staging buffers in 4-byte words (two
-    // rows of one feature) one step ahead of their use, so that the loads overlap the current step
+    // the slopes and activations of step i2z of layer lz (chunk 2 hh + i2z of each half hh),
+    // copied asynchronously into the staging buffers in 16-byte pieces (8 rows of one feature) one
+    // step ahead of their use, so that the loads overlap the current step: the activations of the
+    // tile's 128 rows, the slope records of its first 32 rows only (the primal rows, Pt <= 32)
     auto prefetch_z = [&](int lz, int i2z) {
-#pragma unroll 4
-      for (int k2 = 0; k2 < 32; ++k2) {
-        const int w = t + kBwdThreads * k2;                    // 2 arrays x 64 features x 64 row pairs
-        const int arr = w >> 12, fl = (w >> 6) & 63, rp = w & 63;
+#pragma unroll
+      for (int k2 = 0; k2 < 5; ++k2) {
+        const int w = t + kBwdThreads * k2;                    // 64 features x (16 + 4) pieces
+        const bool act = w < 64 * 16;
+        const int fl = act ? w >> 4 : (w - 64 * 16) >> 2, c8 = act ? w & 15 : w & 3;
         const int fg = (2 * (fl >> 5) + i2z) * 32 + (fl & 31);   // global feature
-        const __nv_bfloat16* src = (arr ? a.astore : a.dstore) + ((int64_t)lz * kW + fg) * a.rows_total + row0 + 2 * rp;
-        cp_async4((arr ? sA : sD) + fl * 128 + 2 * rp, src);
+        const __nv_bfloat16* src = (act ? a.astore : a.dstore) + ((int64_t)lz * kW + fg) * a.rows_total + row0 + 8 * c8;
+        cp_async16((act ? sA : sD) + fl * 128 + 8 * c8, src);
       }
       cp_async_commit_group();
     };
@@ -260,6 +262,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
       const __nv_bfloat16* al = a.astore + (int64_t)(a.n_hidden - 1) * kW * a.rows_total + (int64_t)f * a.rows_total +
                                 row0 + 64 * rh;
       float acc[3] = {0.f, 0.f, 0.f};
+      // unrolled: the eight 16-byte loads of the stored activations are in flight together
+#pragma unroll
       for (int c = 0; c < 64; c += 8) {
         const uint4 u = *reinterpret_cast<const uint4*>(al + c);
         const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&u);
@@ -315,8 +319,10 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_tc(BwdArgs a) {
         float sown[32];
         const __nv_bfloat16* hD = sD + (h * 32) * 128;
         const __nv_bfloat16* hA = sA + (h * 32) * 128;
+        if (cls == 0) {   // before the barrier: the staging buffer is refilled after it
 #pragma unroll
-        for (int i = 0; i < 32; ++i) sown[i] = __bfloat162float(hD[i * 128 + rw]);
+          for (int i = 0; i < 32; ++i) sown[i] = __bfloat162float(hD[i * 128 + rw]);
+        }
         float* hexch = exch + h * kExchRows * kChunkStride;
         if (cls == 1) {
 #pragma unroll
