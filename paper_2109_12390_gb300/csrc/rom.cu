@@ -1017,69 +1017,81 @@ __device__ bool chol_solve(double* A, double* b, int r) {
 // Converges when cond(A) is well below 1 / FP32 epsilon; returns false (A and b untouched) if the
 // FP32 factorisation breaks down or 8 sweeps do not converge, and the caller falls back to
 // chol_solve.  On success b holds the solution.
-__device__ bool chol_solve_refined(const double* A, double* b, int r) {
-  __shared__ float L[kMaxRl * kMaxRl];
-  __shared__ float s_rd[kMaxRl];
-  __shared__ float s_v[kMaxRl];
+// The factor lives in registers: lane i holds row i of L (KR >= r entries, unrolled loops with
+// compile-time bounds), the columns pass between lanes by shuffles, and a copy of L in shared
+// memory gives each lane its column for the back substitution.
+template <int KR>
+__device__ bool chol_solve_refined_reg(const double* A, double* b, int r) {
+  __shared__ float Lsm[kMaxRl * (kMaxRl + 1)];
   __shared__ double s_x[kMaxRl];
   __shared__ int s_ok;
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    for (int e = lane; e < r * r; e += 32) L[e] = (float)A[e];
-    __syncwarp();
-    int ok = 1;
-    for (int j = 0; j < r; ++j) {
-      const float piv = L[j * r + j];
-      if (!(piv > 0.f) || !(piv < 3.0e38f)) {
-        ok = 0;
-        break;
+    float Lr[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) Lr[k] = (lane < r && k < r) ? (float)A[lane * r + k] : 0.f;
+    float rd = 0.f;   // 1 / L[lane][lane]
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < KR; ++j) {
+      if (j < r && ok) {
+        const float piv = __shfl_sync(0xffffffffu, Lr[j], j);
+        if (!(piv > 0.f) || !(piv < 3.0e38f)) {
+          ok = false;   // uniform: every lane sees the same pivot
+        } else {
+          const float y = rsqrtf(piv);
+          const float l = lane > j ? Lr[j] * y : 0.f;
+          if (lane == j) {
+            Lr[j] = piv * y;
+            rd = y;
+          } else if (lane > j) {
+            Lr[j] = l;
+          }
+#pragma unroll
+          for (int k = j + 1; k < KR; ++k) {
+            if (k < r) {
+              const float lk = __shfl_sync(0xffffffffu, l, k);
+              if (lane >= k) Lr[k] = fmaf(-l, lk, Lr[k]);
+            }
+          }
+        }
       }
-      const float y = rsqrtf(piv);
-      const int i = j + 1 + lane;
-      float l = 0.f;
-      if (i < r) {
-        l = L[i * r + j] * y;
-        L[i * r + j] = l;
-      }
-      if (lane == 0) {
-        L[j * r + j] = piv * y;
-        s_rd[j] = y;
-      }
-      __syncwarp();
-      if (i < r)
-        for (int k = j + 1; k <= i; ++k) L[i * r + k] -= l * L[k * r + j];
-      __syncwarp();
     }
     int conv = 0;
     if (ok) {
-      if (lane < r) {
-        s_x[lane] = 0.0;
-        s_v[lane] = (float)b[lane];
-      }
+#pragma unroll
+      for (int k = 0; k < KR; ++k) Lsm[lane * (kMaxRl + 1) + k] = Lr[k];
+      __syncwarp();
+      float Lc[KR];   // column `lane` of L: Lc[i] = L[i][lane]
+#pragma unroll
+      for (int i = 0; i < KR; ++i) Lc[i] = Lsm[i * (kMaxRl + 1) + lane];
+      if (lane < r) s_x[lane] = 0.0;
+      float v = lane < r ? (float)b[lane] : 0.f;
       __syncwarp();
       for (int sweep = 0; sweep < 8 && !conv; ++sweep) {
-        // L L^T d = v (FP32), d overwrites v
-        for (int k = 0; k < r; ++k) {
-          const float yk = s_v[k] * s_rd[k];
-          __syncwarp();
-          if (lane == 0) s_v[k] = yk;
-          const int i = k + 1 + lane;
-          if (i < r) s_v[i] -= L[i * r + k] * yk;
-          __syncwarp();
+        // L L^T d = v (FP32), d in v: forward by columns, backward by rows of L
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+          if (k < r) {
+            const float yk = __shfl_sync(0xffffffffu, v * rd, k);
+            if (lane == k) v = yk;
+            else if (lane > k) v = fmaf(-Lr[k], yk, v);
+          }
         }
-        for (int i = r - 1; i >= 0; --i) {
-          const float xi = s_v[i] * s_rd[i];
-          __syncwarp();
-          if (lane == 0) s_v[i] = xi;
-          if (lane < i) s_v[lane] -= L[i * r + lane] * xi;
-          __syncwarp();
+#pragma unroll
+        for (int i = KR - 1; i >= 0; --i) {
+          if (i < r) {
+            const float xi = __shfl_sync(0xffffffffu, v * rd, i);
+            if (lane == i) v = xi;
+            else if (lane < i) v = fmaf(-Lc[i], xi, v);
+          }
         }
         // x += d; residual b - A x in FP64 (four independent partial sums per row)
         float dmax = 0.f, xmax = 0.f;
         if (lane < r) {
-          const double xn = s_x[lane] + (double)s_v[lane];
+          const double xn = s_x[lane] + (double)v;
           s_x[lane] = xn;
-          dmax = fabsf(s_v[lane]);
+          dmax = fabsf(v);
           xmax = fabsf((float)xn);
         }
         __syncwarp();
@@ -1093,7 +1105,7 @@ __device__ bool chol_solve_refined(const double* A, double* b, int r) {
             p3 = fma(A[lane * r + jj + 3], s_x[jj + 3], p3);
           }
           for (; jj < r; ++jj) p0 = fma(A[lane * r + jj], s_x[jj], p0);
-          s_v[lane] = (float)(b[lane] - ((p0 + p1) + (p2 + p3)));
+          v = (float)(b[lane] - ((p0 + p1) + (p2 + p3)));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -1109,6 +1121,12 @@ __device__ bool chol_solve_refined(const double* A, double* b, int r) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+__device__ bool chol_solve_refined(const double* A, double* b, int r) {
+  if (r <= 8) return chol_solve_refined_reg<8>(A, b, r);
+  if (r <= 16) return chol_solve_refined_reg<16>(A, b, r);
+  return chol_solve_refined_reg<kMaxRl>(A, b, r);
 }
 
 __global__ void __launch_bounds__(kNormBlock) rom_normal(RomDev R, RomSolve S, const float* __restrict__ dec,
