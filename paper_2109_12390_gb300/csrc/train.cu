@@ -532,10 +532,13 @@ __global__ void __launch_bounds__(256) train_dw0_lat(const float* zb0, int64_t r
   float* sz = dsm;                                   // [128 f][kDw0Stride]: zbar0 of the tile's rows
   float* sin0 = sz + kW * kDw0Stride;                // [kDw0MaxPt][kMaxIn]: primal inputs of the points
   float* su = sin0 + kDw0MaxPt * kMaxIn;             // [kDw0MaxPt][32]: JVP directions
-  float* sWl = su + kDw0MaxPt * 32;                  // [128][33]: latent columns of W0
+  float* sWl = su + kDw0MaxPt * 32;                  // [128][36]: latent columns of W0 (float4 rows)
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int K = d + r;
-  for (int e = t; e < kW * r; e += blockDim.x) sWl[(e / r) * 33 + e % r] = W0[(e / r) * K + d + (e % r)];
+  for (int e = t; e < kW * 36; e += blockDim.x) {
+    const int ff = e / 36, j = e % 36;
+    sWl[e] = j < r ? W0[ff * K + d + j] : 0.f;
+  }
   const int f = t & (kW - 1), half = t >> 7;
   const int q_lo = half ? (Pt + 1) / 2 : 0, q_hi = half ? Pt : (Pt + 1) / 2;
   float inv_range[D];
@@ -569,7 +572,51 @@ __global__ void __launch_bounds__(256) train_dw0_lat(const float* zb0, int64_t r
     __syncthreads();
     // (a) weight gradient of feature f over this thread's points (rows of invalid points are zero)
     const float* zf = sz + f * kDw0Stride;
-    for (int q = q_lo; q < q_hi; ++q) {
+    // four points at a time with float4 reads of the staged adjoints where the rows allow it (a
+    // quarter warp's 16-byte reads then fall in distinct banks; the scalar reads of lanes 132
+    // floats apart conflict 4 ways)
+    const bool vec4 = (Pt & 3) == 0 && (q_lo & 3) == 0 && (q_hi & 3) == 0;
+    for (int q4 = q_lo; vec4 && q4 < q_hi; q4 += 4) {
+      const float4 zp4 = *reinterpret_cast<const float4*>(zf + q4);
+      float4 zt4[D];
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) zt4[a2] = *reinterpret_cast<const float4*>(zf + (1 + a2) * Pt + q4);
+      const float4 zj4 = *reinterpret_cast<const float4*>(zf + (D + 1) * Pt + q4);
+#pragma unroll
+      for (int u4 = 0; u4 < 4; ++u4) {
+        const int q = q4 + u4;
+        const float zp = u4 == 0 ? zp4.x : u4 == 1 ? zp4.y : u4 == 2 ? zp4.z : zp4.w;
+        const float zj = u4 == 0 ? zj4.x : u4 == 1 ? zj4.y : u4 == 2 ? zj4.z : zj4.w;
+        const float* in = sin0 + q * kMaxIn;
+#pragma unroll
+        for (int j = 0; j < kMaxIn; j += 4) {
+          if (j < K) {
+            const float4 v = *reinterpret_cast<const float4*>(in + j);
+            acc[j] = fmaf(zp, v.x, acc[j]);
+            acc[j + 1] = fmaf(zp, v.y, acc[j + 1]);
+            acc[j + 2] = fmaf(zp, v.z, acc[j + 2]);
+            acc[j + 3] = fmaf(zp, v.w, acc[j + 3]);
+          }
+        }
+#pragma unroll
+        for (int a2 = 0; a2 < D; ++a2) {
+          const float zt = u4 == 0 ? zt4[a2].x : u4 == 1 ? zt4[a2].y : u4 == 2 ? zt4[a2].z : zt4[a2].w;
+          acc[a2] = fmaf(zt, inv_range[a2], acc[a2]);
+        }
+        const float* uq = su + q * 32;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          if (j < r) {
+            const float4 v = *reinterpret_cast<const float4*>(uq + j);
+            acc[D + j] = fmaf(zj, v.x, acc[D + j]);
+            acc[D + j + 1] = fmaf(zj, v.y, acc[D + j + 1]);
+            acc[D + j + 2] = fmaf(zj, v.z, acc[D + j + 2]);
+            acc[D + j + 3] = fmaf(zj, v.w, acc[D + j + 3]);
+          }
+        }
+      }
+    }
+    for (int q = q_lo; !vec4 && q < q_hi; ++q) {
       const float zp = zf[q];                        // primal row
       const float* in = sin0 + q * kMaxIn;
 #pragma unroll
@@ -609,11 +656,11 @@ __global__ void __launch_bounds__(256) train_dw0_lat(const float* zb0, int64_t r
 #pragma unroll 8
       for (int ff = 0; ff < kW; ++ff) {
         const float z = sz[ff * kDw0Stride + row];
-        const float* w = sWl + ff * 33 + 4 * g;
-        v0 = fmaf(z, w[0], v0);
-        v1 = fmaf(z, w[1], v1);
-        v2 = fmaf(z, w[2], v2);
-        v3 = fmaf(z, w[3], v3);
+        const float4 w = *reinterpret_cast<const float4*>(sWl + ff * 36 + 4 * g);
+        v0 = fmaf(z, w.x, v0);
+        v1 = fmaf(z, w.y, v1);
+        v2 = fmaf(z, w.z, v2);
+        v3 = fmaf(z, w.w, v3);
       }
       if (pnt < b.B) {
         float* dst = (jvp ? g_u_pt : g_lat_pt) + pnt * r + 4 * g;
@@ -641,7 +688,7 @@ __global__ void __launch_bounds__(256) train_dw0_lat(const float* zb0, int64_t r
 }
 
 size_t dw0_smem_bytes() {
-  return (size_t)(kW * kDw0Stride + kDw0MaxPt * kMaxIn + kDw0MaxPt * 32 + kW * 33) * sizeof(float);
+  return (size_t)(kW * kDw0Stride + kDw0MaxPt * kMaxIn + kDw0MaxPt * 32 + kW * 36) * sizeof(float);
 }
 
 __global__ void train_lat_scatter(Batch b, int r, const float* g_lat_pt, const float* g_u_pt, float dt_snap,
