@@ -504,6 +504,198 @@ __global__ void __launch_bounds__(kDecThreads, 1) decoder_tc(DecArgs a) {
 }
 
 // --------------------------------------------------------------------------
+// Tensor-core decoder for calls of primal rows only (one row kind), inputs of at most 32
+// entries in the padded layout, BF16 operands: two 128-row tiles in flight per CTA.  512
+// threads in two groups of eight warps; each group runs decoder_tc's tile loop (split-BF16 first
+// layer, square layers, fused output layer) on its own operand tile, tensor-memory columns, MMA
+// barrier and named barrier, so that one group's epilogue overlaps the other group's MMAs.  The
+// weights and the first layer's split image are resident once per CTA.  Same arithmetic, in the
+// same order, as decoder_tc<false>.
+// --------------------------------------------------------------------------
+constexpr int kPrimThreads = 512;
+
+struct __align__(8) PrimSmemTail {
+  uint64_t bar_w;
+  uint64_t bar_mma[2];
+  uint32_t tmem;
+  int abort[2];   // per group: set before a group barrier, read after it
+};
+
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 256;" ::"r"(1 + g) : "memory"); }
+
+__global__ void __launch_bounds__(kPrimThreads, 1) decoder_tc_primal(DecArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* wsm = smem;                                   // kMaxTC x 32 KB square layers
+  uint8_t* w0s = smem + kMaxTC * kLayerBytes;            // 16 KB first-layer split image
+  uint8_t* atiles = w0s + kLayerBytes / 2;               // 2 x 32 KB operand tiles, one per group
+  float* ypart = (float*)(atiles + 2 * kLayerBytes);     // [2 groups][128 rows][3]
+  float* sb0 = ypart + 2 * 128 * 3;                      // [128]
+  float* sbh = sb0 + kW;                                 // [kMaxTC][128]
+  float* sWout = sbh + kMaxTC * kW;                      // [3][128]
+  PrimSmemTail* tail = (PrimSmemTail*)(sWout + 3 * kW);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int g = warp >> 3, tg = t & 255;                 // group, thread within the group
+  const int rw = (warp & 3) * 32 + lane;                 // tile row / tensor-memory lane
+  const int h = (warp >> 2) & 1;                         // column half
+  uint8_t* atile = atiles + g * kLayerBytes;
+  float* yp = ypart + g * 128 * 3;
+
+  if (t == 0) {
+    tc::mbar_init(&tail->bar_w, 1);
+    tc::mbar_init(&tail->bar_mma[0], 1);
+    tc::mbar_init(&tail->bar_mma[1], 1);
+    tail->abort[0] = 0;
+    tail->abort[1] = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc<2 * kW>(&tail->tmem);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tail->tmem + (uint32_t)(g * kW);   // this group's 128 columns
+
+  for (int e = t; e < kW; e += kPrimThreads) sb0[e] = a.b0[e];
+  for (int e = t; e < a.n_tc * kW; e += kPrimThreads) sbh[e] = a.bh[e];
+  for (int e = t; e < a.d * kW; e += kPrimThreads) sWout[e] = a.Wout[e];
+  if (t == 0) {
+    tc::mbar_expect_tx(&tail->bar_w, (uint32_t)(a.n_tc * kLayerBytes + kLayerBytes / 2));
+    for (int l = 0; l < a.n_tc; ++l)
+      tc::bulk_g2s(wsm + l * kLayerBytes, a.wimg + (size_t)l * kLayerBytes, kLayerBytes, &tail->bar_w);
+    tc::bulk_g2s(w0s, a.w0img, kLayerBytes / 2, &tail->bar_w);
+  }
+  if (!tc::mbar_wait(&tail->bar_w, 0)) {
+    raise_status(a.status, STATUS_TIMEOUT);
+    tail->abort[0] = 1;
+    tail->abort[1] = 1;
+  }
+  __syncthreads();
+
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kW);
+  uint32_t mma_phase = 0;
+  const int64_t n_pts = dec_count(a);
+  const int64_t n_tiles = (n_pts + 127) / 128;
+  for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < n_tiles && !tail->abort[g]; tile += 2 * (int64_t)gridDim.x) {
+    const int64_t first = tile * 128;
+    const RowInfo ri = row_info(a, rw, first, n_pts);
+    {
+      float in[40], dir[40];
+      if (ri.cls >= 0) row_inputs_tc(a, ri, in, dir);
+      // the first layer's operand row: half 0 stores the high parts at columns 0 .. 31, half 1
+      // the low parts at 32 .. 63; zero for rows past the end
+#pragma unroll
+      for (int c0 = 0; c0 < 32; c0 += 8) {
+        float p[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float v = ri.cls == 0 ? in[c0 + j] : 0.f;
+          const float hi = __bfloat162float(__float2bfloat16_rn(v));
+          p[j] = h == 0 ? hi : v - hi;
+        }
+        store_bf16x8(atile, rw, 32 * h + c0, p);
+      }
+    }
+    float y[3] = {0.f, 0.f, 0.f};
+    for (int l = -1; l < a.n_tc; ++l) {
+      tc::fence_async_smem();
+      tc::tc_fence_before();
+      group_sync(g);
+      if (tg == 0) {
+        tc::tc_fence_after();
+        const uint32_t a_base = tc::smem_addr(atile);
+        if (l < 0) {
+          const uint32_t b_base = tc::smem_addr(w0s);
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const uint32_t hi = (uint32_t)(k * 32), lo = (uint32_t)(64 + k * 32);
+            tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + hi), tc::smem_desc_sw128(b_base + hi), idesc,
+                         k > 0 ? 1u : 0u);
+            tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + hi), tc::smem_desc_sw128(b_base + lo), idesc, 1u);
+            tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + lo), tc::smem_desc_sw128(b_base + hi), idesc, 1u);
+          }
+        } else {
+          const uint32_t b_base = tc::smem_addr(wsm + l * kLayerBytes);
+#pragma unroll
+          for (int k = 0; k < kW / 16; ++k) {
+            const uint32_t koff = (uint32_t)((k >> 2) * (kW * 128) + (k & 3) * 32);
+            tc::mma_bf16(tmem, tc::smem_desc_sw128(a_base + koff), tc::smem_desc_sw128(b_base + koff), idesc,
+                         k > 0 ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&tail->bar_mma[g]);
+      }
+      if (!tc::mbar_wait(&tail->bar_mma[g], mma_phase)) {
+        raise_status(a.status, STATUS_TIMEOUT);
+        tail->abort[g] = 1;
+      }
+      mma_phase ^= 1u;
+      tc::tc_fence_after();
+      group_sync(g);
+      if (tail->abort[g]) break;
+      const bool last = (l == a.n_tc - 1);
+      const float* bl = l < 0 ? sb0 : sbh + l * kW;
+      for (int i2 = 0; i2 < 2; ++i2) {
+        const int ch = 2 * h + i2;
+        float acc[32];
+        tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + ch * 32, acc);
+        if (ri.cls == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            const float4 b4 = *reinterpret_cast<const float4*>(bl + ch * 32 + i);
+            acc[i] += b4.x;
+            acc[i + 1] += b4.y;
+            acc[i + 2] += b4.z;
+            acc[i + 3] += b4.w;
+          }
+          if (a.act == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[i] = elu_bf16_input(acc[i]);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+        }
+        if (last) {
+#pragma unroll
+          for (int o = 0; o < 3; ++o) {   // compile-time bound: y stays in registers
+            if (o >= a.d) break;
+            float sacc = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sacc = fmaf(sWout[o * kW + ch * 32 + i], acc[i], sacc);
+            y[o] += sacc;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; j += 8) store_bf16x8(atile, rw, ch * 32 + j, acc + j);
+        }
+      }
+      tc::tc_fence_before();
+    }
+    if (tail->abort[g]) break;
+    // combine the two column halves of the output layer
+    if (h == 1) {
+#pragma unroll
+      for (int o = 0; o < 3; ++o)
+        if (o < a.d) yp[rw * 3 + o] = y[o];
+    }
+    group_sync(g);
+    if (h == 0 && ri.cls >= 0) {
+      float* o = a.out + ri.p * a.d;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (i >= a.d) break;
+        const float v = y[i] + yp[rw * 3 + i] + __ldg(&a.bout[i]);
+        o[i] = v * a.norm[3 * a.d + i] + a.norm[2 * a.d + i];
+      }
+    }
+    group_sync(g);
+  }
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_free<2 * kW>(tail->tmem);
+}
+
+// --------------------------------------------------------------------------
 // FP32 decoder on the CUDA cores, for calls whose rows are too few to keep the
 // tensor cores busy and whose results need FP32 accuracy (the reduced step's
 // positions and gradients).  Same row kinds as decoder_tc; one persistent CTA
@@ -902,6 +1094,11 @@ size_t dec_smem_bytes(bool split) {
          sizeof(DecSmemTail);
 }
 
+size_t dec_primal_smem_bytes() {
+  return 1024 + kMaxTC * kLayerBytes + kLayerBytes / 2 + 2 * kLayerBytes +
+         (2 * 128 * 3 + kW + kMaxTC * kW + 3 * kW) * sizeof(float) + sizeof(PrimSmemTail);
+}
+
 size_t dec_f32_smem_bytes() {
   return (size_t)(2 * kW * kF32Rows + 2 * kW * kW + kW0Stride * kW + kW + kMaxTC * kW + 3 * kW) * sizeof(float) +
          kF32Rows * (sizeof(F32Row) + sizeof(int64_t) + sizeof(int));
@@ -995,6 +1192,9 @@ mpm_status decoder_create(const decoder_desc* desc, mpm_decoder** out) {
     e = cudaFuncSetAttribute(decoder_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec->smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(decoder_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec->smem_split);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(decoder_tc_primal, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dec_primal_smem_bytes());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(decoder_f32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec_f32_smem_bytes());
   if (e == cudaSuccess)
@@ -1175,6 +1375,12 @@ static mpm_status decoder_launch(const mpm_decoder* dec, const float* X, const i
       decoder_f32<32><<<blocks, kF32Threads, dec_f32_smem_bytes(), s>>>(a);
     else
       decoder_f32<64><<<blocks, kF32Threads, dec_f32_smem_bytes(), s>>>(a);
+  } else if (dec->fp32 == 0 && R == 1 && a.kinds[0] == KIND_PRIMAL && !a.dstore && !a.astore && dec->w0img &&
+             kTcLat + dec->r <= 32) {
+    // primal rows only: two tiles in flight per CTA
+    const int64_t tiles = (n + 127) / 128;
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 1) / 2, dec->n_sm));
+    decoder_tc_primal<<<blocks, kPrimThreads, dec_primal_smem_bytes(), s>>>(a);
   } else {
     const int64_t tiles = (n + a.Pt - 1) / a.Pt;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dec->n_sm));
