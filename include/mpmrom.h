@@ -350,7 +350,10 @@ enum {
  *            DECODER_PRIMAL.
  *   out      (R, n, d): out[k][p] = the quantity of kinds[k] at point p.
  * The square hidden layers run as BF16 x BF16 -> FP32 tcgen05 GEMMs; the
- * first layer (K = d + r) and the output layer (N = d) in FP32.
+ * output layer (N = d) in FP32; the first layer (K = d + r) on the tensor
+ * cores in split BF16 when r <= 28 (inputs and weights each hi + lo, three
+ * products per K step, about 2^-16 relative error per product, so the input
+ * coordinates keep far more than BF16 resolution), otherwise in FP32.
  * Derivative rows propagate with the primal pre-activations of the same
  * point (forward-mode chain rule); secant rows propagate the exact
  * difference act(z + dz) - act(z), so they resolve latent increments far
@@ -376,7 +379,8 @@ mpm_status decoder_status_word(mpm_decoder* dec, uint32_t* out, int clear, void*
  * A_hi W_hi + A_hi W_lo + A_lo W_hi accumulated in FP32, so each product keeps
  * about 16 bits (relative error near 2^-16 against 2^-24 for FP32, against
  * 2^-8 for BF16) at tensor-core throughput: for many concurrent reduced-order
- * instances.  The first and output layers are FP32 in every mode.  Takes effect
+ * instances.  The output layer is FP32 in every mode, the first layer FP32 in
+ * modes 1 and 2 and split BF16 in mode 0 (FP32 there when r > 28).  Takes effect
  * for reduced-order contexts created afterwards.  Errors: MPM_EINVAL.
  */
 mpm_status decoder_set_precision(mpm_decoder* dec, int fp32);
