@@ -118,6 +118,11 @@ struct RomDev {
   const int32_t* kg_ids;     // particles of each group, ascending
   int n_groups, m_kin;
   uint32_t* sel_bits;        // ((P + 31) / 32) sample membership of the current step
+  // neighbour test on every SM for P > kSelMaxBits (rom_nb_flags, rom_nb_list)
+  int nb_multi;
+  uint32_t* smp_bits;        // ((P + 31) / 32) samples of the step
+  uint32_t* nb_bits;         // ((P + 31) / 32) neighbours of the step
+  int32_t* nb_cnt;           // (grid of rom_nb_flags) neighbours per CTA
 };
 
 // Inverse of a small matrix by its adjugate (F of a quadrature point, det F > 0).
@@ -184,6 +189,35 @@ __device__ __forceinline__ int node_linear(const int node[D], int n) {
 // ------------------------------------------------------------ rom_select
 constexpr int kMaxKin = 32;          // samples forced from one kinematic group, at most
 constexpr int kSelMaxBits = 65536;   // particles whose neighbour decisions rom_select keeps in shared memory
+
+// Algorithm 3's neighbour test of particle p: a node of its stencil carries the step's stamp (is
+// in the basis set I).  The stencil's stamps are loaded together (independent loads).
+template <int D>
+__device__ __forceinline__ bool nb_hit(const RomDev& R, int p, uint32_t stamp, bool flag_out_of_grid) {
+  constexpr int NS = (D == 2) ? 9 : 27;
+  int base[D];
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int b = stencil_base(R.x_all[(size_t)p * D + a], R.inv_dx);
+    ok &= (b >= 0) & (b + 2 <= R.n - 1);
+    base[a] = min(max(b, 0), R.n - 3);
+  }
+  if (!ok && flag_out_of_grid) raise_status(R.status, STATUS_OUT_OF_GRID);
+  uint32_t st[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    int node[D];
+    node[0] = base[0] + (D == 2 ? s / 3 : s / 9);
+    node[D - 1] = base[D - 1] + s % 3;
+    if (D == 3) node[1] = base[1] + (s / 3) % 3;
+    st[s] = R.stamp[node_linear<D>(node, R.n)];
+  }
+  bool hit = false;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) hit |= st[s] == stamp;
+  return hit;
+}
 
 template <int D>
 __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
@@ -409,30 +443,27 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
     }
     return smp;
   };
-  auto neighbour_hit = [&](int p, bool flag_out_of_grid) {
-    int base[D];
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const int b = stencil_base(R.x_all[(size_t)p * D + a], R.inv_dx);
-      ok &= (b >= 0) & (b + 2 <= R.n - 1);
-      base[a] = min(max(b, 0), R.n - 3);
+  auto neighbour_hit = [&](int p, bool flag_out_of_grid) { return nb_hit<D>(R, p, stamp, flag_out_of_grid); };
+  if (R.nb_multi) {
+    // large P: the neighbour test runs on every SM (rom_nb_flags, rom_nb_list); here only the
+    // samples' membership bits for it
+    const int nw = (P + 31) / 32;
+    if (R.n_groups > 0) {
+      for (int w = t; w < nw; w += T) R.smp_bits[w] = R.sel_bits[w];
+    } else {
+      for (int w = t; w < nw; w += T) R.smp_bits[w] = 0u;
+      __syncthreads();
+      for (int i = t; i < nP; i += T) {
+        const int q = R.qlist[i];
+        atomicOr(&R.smp_bits[q >> 5], 1u << (q & 31));
+      }
     }
-    if (!ok && flag_out_of_grid) raise_status(R.status, STATUS_OUT_OF_GRID);
-    uint32_t st[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      int node[D];
-      node[0] = base[0] + (D == 2 ? s / 3 : s / 9);
-      node[D - 1] = base[D - 1] + s % 3;
-      if (D == 3) node[1] = base[1] + (s / 3) % 3;
-      st[s] = R.stamp[node_linear<D>(node, R.n)];
+    if (t == 0) {
+      R.counts[0] = nP;
+      R.counts[2] = nP * NS;
     }
-    bool hit = false;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) hit |= st[s] == stamp;
-    return hit;
-  };
+    return;
+  }
   const bool keep_bits = P <= kSelMaxBits;
   for (int w = t; w < (P + 31) / 32 && keep_bits; w += T) s_nbits[w] = 0u;
   __syncthreads();
@@ -459,6 +490,66 @@ __global__ void __launch_bounds__(1024) rom_select(RomDev R) {
     R.counts[0] = nP;
     R.counts[1] = nP + n_nb;
     R.counts[2] = nP * NS;
+  }
+}
+
+// Neighbour set N for large P, on every SM: warp w tests the 32 particles of bit word w (samples
+// excluded) and writes the word of their decisions; per-CTA counts for rom_nb_list.
+template <int D>
+__global__ void __launch_bounds__(256) rom_nb_flags(RomDev R) {
+  __shared__ int s_warp[32];
+  const int P = R.P, nw = (P + 31) / 32;
+  const uint32_t stamp = (uint32_t)(*R.step + 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wpc = (nw + gridDim.x - 1) / gridDim.x;
+  const int w0 = min((int)blockIdx.x * wpc, nw), w1 = min(w0 + wpc, nw);
+  int cnt = 0;
+  for (int w = w0 + warp; w < w1; w += blockDim.x / 32) {
+    const int p = 32 * w + lane;
+    bool hit = false;
+    if (p < P && !((R.smp_bits[w] >> lane) & 1u)) hit = nb_hit<D>(R, p, stamp, true);
+    const uint32_t bits = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) {
+      R.nb_bits[w] = bits;
+      cnt += __popc(bits);
+    }
+  }
+  int total;
+  (void)block_exclusive_scan(cnt, &total, s_warp);
+  if (threadIdx.x == 0) R.nb_cnt[blockIdx.x] = total;
+}
+
+// The neighbour ids in ascending order after the samples: each CTA's words (the same split as
+// rom_nb_flags) from the offset of the CTAs before it, 256 words at a time.
+template <int D>
+__global__ void __launch_bounds__(256) rom_nb_list(RomDev R) {
+  __shared__ int s_warp[32];
+  const int P = R.P, nw = (P + 31) / 32;
+  const int wpc = (nw + gridDim.x - 1) / gridDim.x;
+  const int w0 = min((int)blockIdx.x * wpc, nw), w1 = min(w0 + wpc, nw);
+  int before = 0, all = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const int c = R.nb_cnt[b];
+    all += c;
+    if (b < (int)blockIdx.x) before += c;
+  }
+  int n_before, n_all;
+  (void)block_exclusive_scan(before, &n_before, s_warp);
+  (void)block_exclusive_scan(all, &n_all, s_warp);
+  const int nP = R.counts[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) R.counts[1] = nP + n_all;
+  int base = nP + n_before;
+  for (int w = w0; w < w1; w += blockDim.x) {
+    const int my = w + threadIdx.x;
+    uint32_t bits = my < w1 ? R.nb_bits[my] : 0u;
+    int chunk;
+    int pos = base + block_exclusive_scan(__popc(bits), &chunk, s_warp);
+    while (bits) {
+      const int j = __ffs(bits) - 1;
+      bits &= bits - 1;
+      R.qlist[pos++] = 32 * my + j;
+    }
+    base += chunk;
   }
 }
 
@@ -1455,6 +1546,10 @@ struct rom_ctx {
   float* x_all_buf = nullptr;
   bool merged = false;          // one decode of all particles serves positions and quadrature rows
   int32_t* qlist = nullptr;
+  uint32_t* smp_bits = nullptr;  // large P: neighbour test on every SM
+  uint32_t* nb_bits = nullptr;
+  int32_t* nb_cnt = nullptr;
+  int nb_ctas = 0;
   int32_t* counts = nullptr;
   int32_t* nodes = nullptr;
   uint32_t* stamp = nullptr;
@@ -1529,12 +1624,22 @@ mpm_status rom_launch_lagrangian(rom_ctx* c, const int* kq, int Rq, bool affine,
     st = decoder_launch_dev(c->dec, c->X, nullptr, c->nP_all, 1, c->P, c->sv.xh32, nullptr, k_primal, 1, c->x_all, s);
     if (st != MPM_OK) return st;
   }
-  // 2. samples, basis set, neighbours
+  // 2. samples, basis set, neighbours (for large P the neighbour test on every SM)
   if (d == 2)
     rom_select<2><<<1, 1024, 0, s>>>(c->dv);
   else
     rom_select<3><<<1, 1024, 0, s>>>(c->dv);
   MPM_CUDA_TRY(cudaGetLastError());
+  if (c->dv.nb_multi) {
+    if (d == 2) {
+      rom_nb_flags<2><<<c->nb_ctas, 256, 0, s>>>(c->dv);
+      rom_nb_list<2><<<c->nb_ctas, 256, 0, s>>>(c->dv);
+    } else {
+      rom_nb_flags<3><<<c->nb_ctas, 256, 0, s>>>(c->dv);
+      rom_nb_list<3><<<c->nb_ctas, 256, 0, s>>>(c->dv);
+    }
+    MPM_CUDA_TRY(cudaGetLastError());
+  }
   if (!c->merged) {
     // 3. F and v at the quadrature points Q
     st = decoder_launch_dev(c->dec, c->X, c->qlist, c->counts + 1, 1, c->P, c->sv.xh32, c->sv.vh32, kq, Rq, c->outQ,
@@ -1768,6 +1873,12 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   if ((st = ralloc(&c->X, (size_t)P * d)) != MPM_OK) return st;
   if ((st = ralloc(&c->x_all_buf, (size_t)P * d)) != MPM_OK) return st;
   if ((st = ralloc(&c->qlist, P)) != MPM_OK) return st;
+  if (P > kSelMaxBits) {
+    c->nb_ctas = std::max(1, c->n_sm * 4);
+    if ((st = ralloc(&c->smp_bits, (size_t)(P + 31) / 32)) != MPM_OK) return st;
+    if ((st = ralloc(&c->nb_bits, (size_t)(P + 31) / 32)) != MPM_OK) return st;
+    if ((st = ralloc(&c->nb_cnt, (size_t)c->nb_ctas)) != MPM_OK) return st;
+  }
   if ((st = ralloc(&c->counts, 4)) != MPM_OK) return st;
   if ((st = ralloc(&c->nodes, (size_t)k * NS)) != MPM_OK) return st;
   if ((st = ralloc(&c->stamp, gn)) != MPM_OK) return st;
@@ -1863,6 +1974,10 @@ mpm_status rom_create(const rom_config* cfg, const mpm_decoder* dec, const float
   v.x_all = c->x_all;
   v.q_by_pid = c->merged ? 1 : 0;
   v.qlist = c->qlist;
+  v.nb_multi = c->nb_bits ? 1 : 0;
+  v.smp_bits = c->smp_bits;
+  v.nb_bits = c->nb_bits;
+  v.nb_cnt = c->nb_cnt;
   v.counts = c->counts;
   v.nodes = c->nodes;
   v.stamp = c->stamp;
@@ -1916,6 +2031,9 @@ void rom_destroy(rom_ctx* c) {
   cudaFree(c->occ);
   cudaFree(c->outE);
   cudaFree(c->qlist);
+  cudaFree(c->smp_bits);
+  cudaFree(c->nb_bits);
+  cudaFree(c->nb_cnt);
   cudaFree(c->counts);
   cudaFree(c->nodes);
   cudaFree(c->stamp);

@@ -384,6 +384,36 @@ def test_super_resolution_decoding_and_finer_reduced_model():
     romf.close()
 
 
+def test_large_p_neighbour_set_on_every_sm_3d():
+    """More particles than the single-CTA selection keeps decisions for (a 48^3 cube, 110,592
+    particles > 65,536): the neighbour test of Algorithm 3 runs on every SM (rom_nb_flags,
+    rom_nb_list); sample and neighbour sets bit-exact against the oracle's, in ascending order."""
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.rom import ROM
+    sc = S.cube_3d(seed=2, side=48, n_grid=128, dt=5e-5, bottom=0.3)
+    X = sc.x
+    assert len(X) > 65536
+    r, k = 16, 256
+    p = S.near_identity_decoder(21, 3, r, 5, X_min=X.min(0) - 0.05, X_range=X.max(0) - X.min(0) + 0.1, eps=1e-3)
+    dec = Decoder.from_params(p)
+    dec.set_precision(True)
+    rom = ROM.from_scene(dec, sc, n_samples=k, seed=21, projection=1)
+    rng = np.random.default_rng(21)
+    xh = 0.3 * rng.normal(size=r)
+    vh = rng.normal(size=r)
+    rom.set_state(xh, vh, xh - sc.dt * vh, 0)
+    rom.step(1)
+    assert rom.status() & ~ALLOWED_RANDOM == 0
+    dbg = rom.debug()
+    np.testing.assert_array_equal(dbg["samples"], OR.sample_set(21, 0, 0, len(X), k))
+    xa = dbg["x_all"].astype(np.float64)
+    basis, neigh = OR.neighbourhood(xa, dbg["samples"], sc.dx, sc.n_grid)
+    assert len(neigh) > 1000
+    np.testing.assert_array_equal(dbg["neigh"], neigh)
+    rom.close()
+    dec.close()
+
+
 def test_samples_cover_every_particle_and_empty_calls():
     """n_samples >= P: every particle is a sample, the neighbour set is empty, and the step is the
     oracle's; zero-point decode calls are valid no-ops."""
