@@ -414,6 +414,34 @@ def test_large_p_neighbour_set_on_every_sm_3d():
     dec.close()
 
 
+def test_large_p_neighbour_set_on_every_sm_2d():
+    """The same in 2D: one 300 x 300 block (90,000 particles) on the 256^2 grid."""
+    from paper_2109_12390_gb300.decoder import Decoder
+    from paper_2109_12390_gb300.rom import ROM
+    sc = S.batch_2d(seed=4, n_inst=1, fixed_side=300, n_grid=256, origin_y=0.2)
+    X = sc.x
+    assert len(X) > 65536
+    r, k = 16, 256
+    p = S.near_identity_decoder(22, 2, r, 5, X_min=X.min(0) - 0.05, X_range=X.max(0) - X.min(0) + 0.1, eps=1e-3)
+    dec = Decoder.from_params(p)
+    dec.set_precision(True)
+    rom = ROM.from_scene(dec, sc, n_samples=k, seed=22, projection=1)
+    rng = np.random.default_rng(22)
+    xh = 0.3 * rng.normal(size=r)
+    vh = rng.normal(size=r)
+    rom.set_state(xh, vh, xh - sc.dt * vh, 0)
+    rom.step(1)
+    assert rom.status() & ~ALLOWED_RANDOM == 0
+    dbg = rom.debug()
+    np.testing.assert_array_equal(dbg["samples"], OR.sample_set(22, 0, 0, len(X), k))
+    xa = dbg["x_all"].astype(np.float64)
+    basis, neigh = OR.neighbourhood(xa, dbg["samples"], sc.dx, sc.n_grid)
+    assert len(neigh) > 1000
+    np.testing.assert_array_equal(dbg["neigh"], neigh)
+    rom.close()
+    dec.close()
+
+
 def test_samples_cover_every_particle_and_empty_calls():
     """n_samples >= P: every particle is a sample, the neighbour set is empty, and the step is the
     oracle's; zero-point decode calls are valid no-ops."""
